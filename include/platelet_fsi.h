@@ -1,0 +1,243 @@
+/*
+ * platelet_fsi.h -- C ABI of the B300 (sm_103a) platelet fluid-structure step.
+ *
+ * The library computes, per time step, the coupled loop of Wu, Xu, Kim and
+ * Alber's multiscale platelet-adhesion model (flow chart of Fig. 1; order
+ * stated in Section 3 and at the end of Section 3.4.2):
+ *   membrane_forces  hybrid membrane + wall repulsion   (Section 3.1, Eq. 2-11; 3.4.1)
+ *   bonds_forces     GPIb-alpha / vWF-A1 bond springs    (Section 3.2, Eq. 14)
+ *   ib_spread        Lagrangian force -> lattice force   (Section 3.4.2, Eq. 32, 34-36)
+ *   lb_step          D3Q19 BGK + Guo forcing             (Section 3.3, Eq. 16-21)
+ *   ib_interp        lattice velocity -> node velocity   (Section 3.4.2, Eq. 31, 33)
+ *   bonds_step       Monte-Carlo rupture and formation   (Section 3.2, Eq. 12-13)
+ *   sim_step         all of the above, in that order, replayed as CUDA graphs
+ *
+ * Units: lattice units throughout (spacing h = 1, time step dt = 1, reference
+ * density 1).  Grid (nx, ny, nz): x, y periodic; halfway bounce-back walls at
+ * z = -1/2 (still) and z = nz - 1/2 (moving with u_top).  Cell (i, j, k) has
+ * the linear index (k*ny + j)*nx + i; the cell centre is at (i, j, k).
+ *
+ * Memory: every device array is owned by the caller (allocate, keep alive,
+ * free); the library stores raw pointers in opaque handles and never
+ * allocates or frees device memory.  Where a call needs internal storage, a
+ * *_query_workspace call gives its size and the caller passes a device block
+ * of that size (256-byte aligned).  Host arrays are read during the call only.
+ *
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Calls only enqueue work, except where stated ("synchronises").
+ *
+ * Errors: every call returns PFSI_OK (0) or a negative PFSI_ERR_* code;
+ * pfsi_last_error() gives a one-line description (per thread).  Argument
+ * errors are detected before anything is enqueued.
+ */
+#ifndef PLATELET_FSI_H
+#define PLATELET_FSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFSI_OK 0
+#define PFSI_ERR_ARG (-1)      /* invalid argument (null pointer, bad size, misaligned buffer) */
+#define PFSI_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed */
+#define PFSI_ERR_CAPACITY (-6) /* a device-side list overflowed (see bonds_status) */
+
+/* Copies the calling thread's last error message into buf (NUL-terminated,
+ * truncated to len).  Returns the length of the full message. */
+int pfsi_last_error(char* buf, size_t len);
+/* Library version as 10000*major + 100*minor + patch. */
+int pfsi_version(void);
+
+/* ===================================================================== *
+ * Lattice Boltzmann, Section 3.3
+ * ===================================================================== */
+typedef struct {
+    int nx, ny, nz;   /* grid; each >= 1, nz >= 2 */
+    float tau;        /* BGK relaxation time (Eq. 16), > 0.5 */
+    float u_top[3];   /* velocity of the top wall; u_top[2] must be 0 */
+    float body[3];    /* uniform body-force density added in every cell */
+} lb_params;
+
+typedef struct {
+    size_t f_bytes;    /* one population buffer: 19 * n_cells float */
+    size_t g_bytes;    /* force field: n_cells float4 (fx, fy, fz, unused) */
+    size_t v_bytes;    /* velocity field: n_cells float4 (vx, vy, vz, rho) */
+    size_t flag_bytes; /* row flags: ny * nz uint32 */
+    long long n_cells;
+} lb_sizes;
+
+typedef struct lb_ctx lb_ctx;
+
+/* Byte sizes of the buffers lb_create needs. */
+int lb_query_sizes(const lb_params* p, lb_sizes* out);
+
+/* Creates a lattice on caller-owned device buffers.
+ * f_a, f_b: two population buffers, structure of arrays f[q][cell], q in the
+ *   paper's D3Q19 numbering (0-based: 0..5 axes +x,-x,+y,-y,+z,-z; 6..17 the
+ *   face diagonals in the order fixed by Eq. 23-30; 18 rest).  They hold the
+ *   post-collision distribution stored as f - w_q (w_q of Eq. 21).
+ * g: force density per cell (float4, w unused).  Must be zero on entry where
+ *   the row flag is clear; lb_step zeroes it where it consumed it.
+ * v: written by lb_step in flagged rows: (v, rho) with v = u + g/(2 rho).
+ * row_flags: one uint32 per (j, k) row; ib_spread sets, ib_interp clears.
+ * All buffers 16-byte aligned.  lb_create clears g and the flags (enqueued on
+ * the legacy default stream; synchronises). */
+int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, float* v,
+              uint32_t* row_flags, lb_ctx** out);
+int lb_destroy(lb_ctx* ctx);
+
+/* Writes the developed shear profile u_x = u_top (k + 1/2)/nz (equilibrium
+ * plus its first-order non-equilibrium part, post-collision) into the current
+ * population buffer.  u_top = 0 gives the fluid at rest. */
+int lb_init_shear(lb_ctx* ctx, void* stream);
+
+/* nsteps lattice Boltzmann steps (Eq. 16-20): pull streaming with periodic x,
+ * y and halfway bounce-back at the z walls (moving-wall term at the top),
+ * then BGK collision with Guo's forcing term (Eq. 19, read with the
+ * (c c^T - c_s^2 I) tensor and the corrected velocity v).  The force of a
+ * cell is body + g where its row is flagged.  Swaps the current buffer. */
+int lb_step(lb_ctx* ctx, int nsteps, void* stream);
+
+/* Device pointer of the buffer holding the current (post-collision) state. */
+int lb_current(const lb_ctx* ctx, float** f);
+
+/* Sum over all cells of rho and of rho*u (u = momentum of the current
+ * post-collision state / rho), accumulated in FP64 on the device into the
+ * caller's device scratch dev_scratch4 (4 doubles).
+ * out_host[4] = {sum rho, sum rho ux, sum rho uy, sum rho uz}.  Synchronises. */
+int lb_moments_fp64(lb_ctx* ctx, double* dev_scratch4, double* out_host, void* stream);
+
+/* ===================================================================== *
+ * Immersed boundary, Section 3.4.2 (Eq. 33-36, 4-point cosine kernel)
+ * ===================================================================== */
+/* g[cell] += F_m phi(x - X_m) phi(y - Y_m) phi(z - Z_m) over the 4x4x4
+ * support of every node (Eq. 34-35, h = 1); the support wraps in x, y and is
+ * cut at the walls.  Sets the row flags of the cells touched.
+ * X: device double[3][M] (structure of arrays), F: device float[3][M]. */
+int ib_spread(lb_ctx* ctx, const double* X, const float* F, int M, void* stream);
+
+/* U_m = sum over the support of v phi phi phi (Eq. 33) with v from the last
+ * lb_step; if advect != 0, X += U (Eq. 31, forward Euler, dt = 1).  Clears
+ * the row flags of the cells visited.  U: device float[3][M]. */
+int ib_interp(lb_ctx* ctx, double* X, float* U, int M, int advect, void* stream);
+
+/* ===================================================================== *
+ * Hybrid membrane, Section 3.1 (+ wall repulsion of Section 3.4.1)
+ * ===================================================================== */
+typedef struct {
+    float k_spring;     /* Eq. 2-3 spring constant */
+    float k_s, k_t;     /* Eq. 4 global / local area moduli */
+    float k_v;          /* Eq. 5 volume modulus */
+    float k_b;          /* bending: k_b (1 - cos(theta - theta0)) per edge (Eq. 6 reading) */
+    float morse_D;      /* SCE Morse pairs: D[(1 - exp(-a (r - r0)))^2 - 1] */
+    float morse_a;
+    float rep_F0;       /* wall repulsion F = F0 tau e^{-tau eps}/(1 - e^{-tau eps}) */
+    float rep_tau;
+    float rep_eps_min;  /* gap clamp */
+    float z_wall;       /* wall plane (-1/2) */
+} mem_params;
+
+typedef struct mem_ctx mem_ctx;
+
+/* Workspace bytes for a mesh of n_nodes nodes (membrane nodes and interior
+ * SCE elements), n_tri outward-oriented triangles tri[3*n_tri] (host), n_pairs
+ * Morse pairs and n_plt platelets. */
+int membrane_query_workspace(int n_nodes, int n_tri, const int* tri, int n_pairs, int n_plt,
+                             size_t* bytes);
+
+/* Builds the per-node gather lists and the rest state (edge lengths, triangle
+ * and total areas, volumes, rest dihedral angles, Morse rest distances) from
+ * the rest shape X0 (host double[3][n_nodes]) into the device workspace.
+ * node_plt: platelet of each node; is_membrane: 1 for surface nodes (wall
+ * repulsion), 0 for SCE elements.  pairs: host int[2*n_pairs].  Synchronises. */
+int membrane_create(const mem_params* p, int n_nodes, int n_tri, const int* tri, int n_pairs,
+                    const int* pairs, int n_plt, const int* node_plt,
+                    const unsigned char* is_membrane, const double* X0, void* workspace,
+                    size_t ws_bytes, mem_ctx** out);
+int membrane_destroy(mem_ctx* ctx);
+int membrane_set_params(mem_ctx* ctx, const mem_params* p);
+
+/* F = -grad(H_SCE + H_area + H_volume + H_bend + H_Morse) + F_wall  (Eq. 11,
+ * read with the minus sign of Eq. 3).  X: device double[3][n_nodes]; F:
+ * device float[3][n_nodes], overwritten. */
+int membrane_forces(mem_ctx* ctx, const double* X, float* F, void* stream);
+
+/* Per-platelet total area and volume of X (FP64 on the device).
+ * out_host[2*n_plt] = {S_0, V_0, S_1, V_1, ...}.  Synchronises. */
+int membrane_measure(mem_ctx* ctx, const double* X, double* out_host, void* stream);
+
+/* ===================================================================== *
+ * Stochastic adhesion (DAM), Section 3.2
+ * ===================================================================== */
+typedef struct {
+    int lig_i0, lig_j0, lig_ni, lig_nj; /* ligand patch: lattice nodes (i, j) at z = z_wall */
+    int box_nx, box_ny;                 /* periodic lengths */
+    int max_per_ligand;                 /* receptor sites per vWF (4), 1..32 */
+    double z_wall;
+    double sigma, l_b, d_capture;       /* Eq. 13-14; d_capture < 1 */
+    double gamma, kT;                   /* Eq. 12-13 */
+    double kon0_dt, koff0_dt;           /* k_on0 dt, k_off0 dt */
+    uint64_t seed;                      /* Philox4x32-10 key */
+} bond_params;
+
+typedef struct bond_ctx bond_ctx;
+
+int bonds_query_workspace(const bond_params* p, int n_sites, size_t* bytes);
+
+/* Receptor sites are barycentric points: site s lies on triangle
+ * site_tri[s] (of tri[3*n_tri]) with weights (w0, w1, 1 - w0 - w1),
+ * site_w[2s], site_w[2s+1].  bound[s] = ligand id (j - lig_j0)*lig_ni +
+ * (i - lig_i0) or -1; lig_count[l] = bonds of ligand l.  All device arrays. */
+int bonds_create(const bond_params* p, int n_sites, const int* site_tri, const double* site_w,
+                 const int* tri, int* bound, int* lig_count, void* workspace, size_t ws_bytes,
+                 bond_ctx** out);
+int bonds_destroy(bond_ctx* ctx);
+
+/* F += bond spring forces (Eq. 14 read as -sigma (|x_b| - l_b) x_b/|x_b|,
+ * x_b from the ligand to the receptor), split over the triangle's nodes by
+ * the barycentric weights.  X: device double[3][M]; F: device float[3][M]. */
+int bonds_forces(bond_ctx* ctx, const double* X, float* F, int M, void* stream);
+
+/* One Monte-Carlo update at time step `step`: rupture of bound sites with
+ * P_r = 1 - exp(-k_off dt), Bell k_off (Eq. 12); then each site free at the
+ * start of the step tests the ligands of the 2x2 nodes around it that are
+ * within d_capture and below capacity with P_f = 1 - exp(-k_on dt), k_on of
+ * Eq. 13, proposing to the lowest ligand id that succeeded; each ligand
+ * accepts proposals in ascending site id up to max_per_ligand.  Uniforms
+ * come from Philox4x32-10 keyed by seed with counter (site, step lo, step
+ * hi, purpose): purpose 0 rupture, 1 + (2 dj + di) formation. */
+int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* stream);
+
+/* Cumulative event counts and overflow status.  out_host[3] = {ruptures,
+ * formations, overflowed proposals}.  Synchronises.  A nonzero overflow means
+ * a ligand received more than 64 proposals in one step (then only the first
+ * 64 in arrival order were considered) and returns PFSI_ERR_CAPACITY. */
+int bonds_status(bond_ctx* ctx, long long* out_host);
+
+/* ===================================================================== *
+ * Coupled step (Fig. 1)
+ * ===================================================================== */
+typedef struct sim_ctx sim_ctx;
+
+/* Ties a lattice, a membrane mesh and a bond set to the node arrays
+ * X (double[3][M]), F, U (float[3][M]).  bonds may be NULL (no adhesion).
+ * first_step is the step index of the first sim_step (Philox counter). */
+int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, float* F, float* U, int M,
+               uint64_t first_step, sim_ctx** out);
+int sim_destroy(sim_ctx* ctx);
+
+/* nsteps coupled steps: membrane_forces, bonds_forces, ib_spread, lb_step,
+ * ib_interp with advection, bonds_step.  The sequence of one step is captured
+ * once into a CUDA graph per lattice-buffer parity and replayed. */
+int sim_step(sim_ctx* ctx, int nsteps, void* stream);
+
+/* Index of the next step (first_step + steps taken). */
+int sim_step_index(const sim_ctx* ctx, uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,316 @@
+// bonds.cu -- stochastic GPIb-alpha / vWF-A1 adhesion (Section 3.2) for sm_103a.
+//
+// Per step, three kernels:
+//   rupture  (one thread per site)    bound sites break with P_r = 1 - exp(-k_off dt),
+//                                     k_off = k_off0 exp(gamma F_b / kT), F_b = sigma |x_b - l_b| (Eq. 12)
+//   propose  (one thread per site)    sites free at the start of the step test the
+//                                     ligands of the 2x2 lattice nodes around them
+//                                     (within d_capture, below capacity) with
+//                                     P_f = 1 - exp(-k_on dt), k_on of Eq. 13, and
+//                                     propose to the lowest ligand id that succeeded
+//   resolve  (one thread per ligand)  accepts its proposals in ascending site id up
+//                                     to max_per_ligand bonds (at most 4 receptor
+//                                     sites per vWF)
+// so the outcome does not depend on thread scheduling.  Draws are Philox4x32-10
+// keyed by the seed with counter (site, step, purpose).  The decision path
+// (receptor position, bond length, rates) is FP64 with explicitly rounded
+// operations in the order of the plain restatement, so that an event differs
+// only when a uniform lands within an ulp of its probability.
+#include "pfsi_internal.cuh"
+
+namespace pfsi {
+
+namespace {
+
+__device__ __forceinline__ double site_coord(const double* __restrict__ X, int M, int d, int a, int b,
+                                            int c, double w0, double w1)
+{
+    const double w2 = __dsub_rn(__dsub_rn(1.0, w0), w1);
+    return __dadd_rn(__dadd_rn(__dmul_rn(w0, X[d * M + a]), __dmul_rn(w1, X[d * M + b])),
+                     __dmul_rn(w2, X[d * M + c]));
+}
+
+__device__ __forceinline__ double min_image(double d, int L)
+{
+    const double Ld = (double)L;
+    return __dsub_rn(d, __dmul_rn(Ld, floor(__dadd_rn(__ddiv_rn(d, Ld), 0.5))));
+}
+
+__device__ __forceinline__ double norm3_rn(double a, double b, double c)
+{
+    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c)));
+}
+
+struct SitePos {
+    double x, y, z;
+};
+
+__device__ __forceinline__ SitePos site_position(const BondCtx& c, const double* __restrict__ X, int M, int s)
+{
+    const int t = c.site_tri[s];
+    const int a = c.tri[3 * t], b = c.tri[3 * t + 1], cc = c.tri[3 * t + 2];
+    const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
+    return {site_coord(X, M, 0, a, b, cc, w0, w1), site_coord(X, M, 1, a, b, cc, w0, w1),
+            site_coord(X, M, 2, a, b, cc, w0, w1)};
+}
+
+// vector from ligand `lig` to the receptor (minimum image in x, y)
+__device__ __forceinline__ void bond_vector(const bond_params& p, const SitePos& r, int lig, double* d)
+{
+    const int li = lig % p.lig_ni, lj = lig / p.lig_ni;
+    d[0] = min_image(__dsub_rn(r.x, (double)(p.lig_i0 + li)), p.box_nx);
+    d[1] = min_image(__dsub_rn(r.y, (double)(p.lig_j0 + lj)), p.box_ny);
+    d[2] = __dsub_rn(r.z, p.z_wall);
+}
+
+__device__ __forceinline__ uint64_t current_step(const unsigned long long* step_dev, uint64_t step_host)
+{
+    return step_dev ? (uint64_t)*step_dev : step_host;
+}
+
+__global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __restrict__ F, int M)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.R) return;
+    const int lig = c.bound[s];
+    if (lig < 0) return;
+    const SitePos r = site_position(c, X, M, s);
+    double d[3];
+    bond_vector(c.p, r, lig, d);
+    const double xb = norm3_rn(d[0], d[1], d[2]);
+    const double coef = -c.p.sigma * (xb - c.p.l_b) / xb;
+    const int t = c.site_tri[s];
+    const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
+    const float w[3] = {(float)w0, (float)w1, (float)(1.0 - w0 - w1)};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int node = c.tri[3 * t + k];
+#pragma unroll
+        for (int dd = 0; dd < 3; ++dd) atomicAdd(&F[dd * M + node], w[k] * (float)(coef * d[dd]));
+    }
+}
+
+__global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
+                               const unsigned long long* __restrict__ step_dev)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.R) return;
+    const int lig = c.bound[s];
+    if (lig < 0) return;
+    const uint64_t step = current_step(step_dev, step_host);
+    const SitePos r = site_position(c, X, M, s);
+    double d[3];
+    bond_vector(c.p, r, lig, d);
+    const double Fb = __dmul_rn(c.p.sigma, fabs(__dsub_rn(norm3_rn(d[0], d[1], d[2]), c.p.l_b)));
+    const double koff_dt = __dmul_rn(c.p.koff0_dt, exp(__ddiv_rn(__dmul_rn(c.p.gamma, Fb), c.p.kT)));
+    const double Pr = -expm1(-koff_dt);
+    if (uniform53(c.p.seed, (uint32_t)s, step, 0u) < Pr) {
+        c.bound[s] = -2;  // free, but not before the next step
+        atomicSub(&c.lig_count[lig], 1);
+        atomicAdd(&c.counters[0], 1ull);
+    }
+}
+
+__global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
+                               const unsigned long long* __restrict__ step_dev)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.R) return;
+    const int b = c.bound[s];
+    if (b == -2) {
+        c.bound[s] = -1;
+        return;
+    }
+    if (b >= 0) return;
+    const bond_params& p = c.p;
+    const uint64_t step = current_step(step_dev, step_host);
+    const SitePos r = site_position(c, X, M, s);
+    const double bx = (double)p.box_nx, by = (double)p.box_ny;
+    const double xw = __dsub_rn(r.x, __dmul_rn(bx, floor(__ddiv_rn(r.x, bx))));
+    const double yw = __dsub_rn(r.y, __dmul_rn(by, floor(__ddiv_rn(r.y, by))));
+    const int i0 = (int)floor(xw), j0 = (int)floor(yw);
+    int best = -1;
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+            const int gi = (i0 + di) % p.box_nx, gj = (j0 + dj) % p.box_ny;
+            if (gi < p.lig_i0 || gi >= p.lig_i0 + p.lig_ni) continue;
+            if (gj < p.lig_j0 || gj >= p.lig_j0 + p.lig_nj) continue;
+            const int lig = (gj - p.lig_j0) * p.lig_ni + (gi - p.lig_i0);
+            if (c.lig_count[lig] >= p.max_per_ligand) continue;
+            double d[3];
+            bond_vector(p, r, lig, d);
+            const double xb = norm3_rn(d[0], d[1], d[2]);
+            if (!(xb < p.d_capture)) continue;
+            const double dev = fabs(__dsub_rn(xb, p.l_b));
+            const double ex = __ddiv_rn(__dmul_rn(__dmul_rn(p.sigma, dev), __dsub_rn(p.gamma, __dmul_rn(0.5, dev))), p.kT);
+            const double kon_dt = __dmul_rn(p.kon0_dt, exp(ex));
+            const double Pf = -expm1(-kon_dt);
+            const double u = uniform53(p.seed, (uint32_t)s, step, (uint32_t)(1 + 2 * dj + di));
+            if (u < Pf && (best < 0 || lig < best)) best = lig;
+        }
+    if (best >= 0) {
+        const int slot = atomicAdd(&c.nprop[best], 1);
+        if (slot < kMaxCand)
+            c.cand[best * kMaxCand + slot] = s;
+        else
+            atomicAdd(&c.counters[2], 1ull);
+    }
+}
+
+__global__ void k_bond_resolve(BondCtx c, unsigned long long* __restrict__ step_dev)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (step_dev && l == 0) *step_dev += 1ull;
+    if (l >= c.L) return;
+    const int n = c.nprop[l];
+    if (n == 0) return;
+    const int m = n < kMaxCand ? n : kMaxCand;
+    int* cand = c.cand + l * kMaxCand;
+    // insertion sort by site id (short lists)
+    for (int a = 1; a < m; ++a) {
+        const int key = cand[a];
+        int b = a - 1;
+        while (b >= 0 && cand[b] > key) {
+            cand[b + 1] = cand[b];
+            --b;
+        }
+        cand[b + 1] = key;
+    }
+    int cnt = c.lig_count[l];
+    int acc = 0;
+    for (int a = 0; a < m && cnt < c.p.max_per_ligand; ++a) {
+        c.bound[cand[a]] = l;
+        ++cnt;
+        ++acc;
+    }
+    c.lig_count[l] = cnt;
+    c.nprop[l] = 0;
+    if (acc) atomicAdd(&c.counters[1], (unsigned long long)acc);
+}
+
+inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+// workspace: nprop[L], cand[L * kMaxCand], counters[4]
+size_t ws_bytes_for(int L)
+{
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(sizeof(int) * (size_t)L) + al(sizeof(int) * (size_t)L * kMaxCand) + al(4 * sizeof(unsigned long long));
+}
+
+}  // namespace
+
+int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s)
+{
+    if (c->R == 0) return PFSI_OK;
+    k_bond_forces<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, F, M);
+    return check_launch("bonds_forces");
+}
+
+int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
+                      unsigned long long* step_dev, cudaStream_t s)
+{
+    if (c->R > 0) {
+        k_bond_rupture<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, M, step_host, step_dev);
+        int rc = check_launch("bonds_step: rupture");
+        if (rc) return rc;
+        k_bond_propose<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, M, step_host, step_dev);
+        rc = check_launch("bonds_step: propose");
+        if (rc) return rc;
+    }
+    k_bond_resolve<<<blocks_for(c->L > 0 ? c->L : 1, 256), 256, 0, s>>>(*c, step_dev);
+    return check_launch("bonds_step: resolve");
+}
+
+}  // namespace pfsi
+
+using namespace pfsi;
+
+static int check_bond_params(const bond_params* p, const char* who)
+{
+    if (!p) return set_error(PFSI_ERR_ARG, std::string(who) + ": null parameters");
+    if (p->lig_ni < 1 || p->lig_nj < 1 || p->box_nx < 1 || p->box_ny < 1 || p->lig_i0 < 0 || p->lig_j0 < 0 ||
+        p->lig_i0 + p->lig_ni > p->box_nx || p->lig_j0 + p->lig_nj > p->box_ny)
+        return set_error(PFSI_ERR_ARG, std::string(who) + ": ligand patch outside the box");
+    if (p->max_per_ligand < 1 || p->max_per_ligand > 32)
+        return set_error(PFSI_ERR_ARG, std::string(who) + ": max_per_ligand must be 1..32");
+    if (!(p->d_capture < 1.0))
+        return set_error(PFSI_ERR_ARG, std::string(who) + ": d_capture must be below one lattice spacing");
+    if (!(p->kT > 0.0)) return set_error(PFSI_ERR_ARG, std::string(who) + ": kT must be positive");
+    return PFSI_OK;
+}
+
+extern "C" int bonds_query_workspace(const bond_params* p, int n_sites, size_t* bytes)
+{
+    int rc = check_bond_params(p, "bonds_query_workspace");
+    if (rc) return rc;
+    if (!bytes || n_sites < 0) return set_error(PFSI_ERR_ARG, "bonds_query_workspace: bad argument");
+    *bytes = ws_bytes_for(p->lig_ni * p->lig_nj);
+    return PFSI_OK;
+}
+
+extern "C" int bonds_create(const bond_params* p, int n_sites, const int* site_tri, const double* site_w,
+                            const int* tri, int* bound, int* lig_count, void* ws, size_t ws_bytes,
+                            bond_ctx** out)
+{
+    int rc = check_bond_params(p, "bonds_create");
+    if (rc) return rc;
+    if (!out || !ws || n_sites < 0 || (n_sites > 0 && (!site_tri || !site_w || !tri || !bound)) || !lig_count)
+        return set_error(PFSI_ERR_ARG, "bonds_create: bad argument");
+    if (!aligned(ws, 256)) return set_error(PFSI_ERR_ARG, "bonds_create: workspace must be 256-byte aligned");
+    const int L = p->lig_ni * p->lig_nj;
+    if (ws_bytes < ws_bytes_for(L)) return set_error(PFSI_ERR_ARG, "bonds_create: workspace too small");
+    bond_ctx* c = new bond_ctx();
+    c->p = *p;
+    c->R = n_sites;
+    c->L = L;
+    c->site_tri = site_tri;
+    c->site_w = site_w;
+    c->tri = tri;
+    c->bound = bound;
+    c->lig_count = lig_count;
+    char* base = static_cast<char*>(ws);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    c->nprop = reinterpret_cast<int*>(base);
+    c->cand = reinterpret_cast<int*>(base + al(sizeof(int) * L));
+    c->counters = reinterpret_cast<unsigned long long*>(base + al(sizeof(int) * L) + al(sizeof(int) * (size_t)L * kMaxCand));
+    rc = check_cuda(cudaMemsetAsync(c->nprop, 0, sizeof(int) * L, 0), "bonds_create: clear");
+    if (!rc) rc = check_cuda(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), 0), "bonds_create: clear");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(0), "bonds_create: synchronise");
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int bonds_destroy(bond_ctx* c)
+{
+    delete c;
+    return PFSI_OK;
+}
+
+extern "C" int bonds_forces(bond_ctx* c, const double* X, float* F, int M, void* stream)
+{
+    if (!c || !X || !F || M < 0) return set_error(PFSI_ERR_ARG, "bonds_forces: bad argument");
+    return launch_bonds_forces(c, X, F, M, as_stream(stream));
+}
+
+extern "C" int bonds_step(bond_ctx* c, const double* X, int M, uint64_t step, void* stream)
+{
+    if (!c || !X || M < 0) return set_error(PFSI_ERR_ARG, "bonds_step: bad argument");
+    return launch_bonds_step(c, X, M, step, nullptr, as_stream(stream));
+}
+
+extern "C" int bonds_status(bond_ctx* c, long long* out_host)
+{
+    if (!c || !out_host) return set_error(PFSI_ERR_ARG, "bonds_status: null argument");
+    unsigned long long h[3];
+    int rc = check_cuda(cudaMemcpy(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost), "bonds_status: copy");
+    if (rc) return rc;
+    for (int k = 0; k < 3; ++k) out_host[k] = (long long)h[k];
+    if (h[2]) return set_error(PFSI_ERR_CAPACITY, "bonds_status: a ligand received more than 64 proposals in one step");
+    return PFSI_OK;
+}

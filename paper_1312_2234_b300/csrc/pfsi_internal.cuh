@@ -1,0 +1,152 @@
+// pfsi_internal.cuh -- internal declarations shared by the CUDA translation
+// units of the platelet fluid-structure library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/platelet_fsi.h"
+
+namespace pfsi {
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const std::string& msg);
+int check_cuda(cudaError_t e, const char* what);
+int check_launch(const char* what);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ---------------------------------------------------------------- D3Q19
+// Directions in the paper's numbering (0-based), fixed by Eq. 23-30:
+// 0..5 = +x,-x,+y,-y,+z,-z; 6..17 face diagonals; 18 rest.  constexpr
+// functions so that unrolled loops fold them to immediates.
+__host__ __device__ __forceinline__ constexpr int cxq(int q)
+{
+    return (q == 0 || q == 6 || q == 7 || q == 8 || q == 9)        ? 1
+           : (q == 1 || q == 10 || q == 11 || q == 12 || q == 13) ? -1
+                                                                   : 0;
+}
+__host__ __device__ __forceinline__ constexpr int cyq(int q)
+{
+    return (q == 2 || q == 6 || q == 10 || q == 14 || q == 15)     ? 1
+           : (q == 3 || q == 7 || q == 11 || q == 16 || q == 17) ? -1
+                                                                  : 0;
+}
+__host__ __device__ __forceinline__ constexpr int czq(int q)
+{
+    return (q == 4 || q == 8 || q == 12 || q == 14 || q == 16)     ? 1
+           : (q == 5 || q == 9 || q == 13 || q == 15 || q == 17) ? -1
+                                                                  : 0;
+}
+__host__ __device__ __forceinline__ constexpr int oppq(int q)
+{
+    return q == 18 ? 18
+           : q < 6 ? (q ^ 1)
+           : q == 6 ? 11 : q == 11 ? 6 : q == 7 ? 10 : q == 10 ? 7
+           : q == 8 ? 13 : q == 13 ? 8 : q == 9 ? 12 : q == 12 ? 9
+           : q == 14 ? 17 : q == 17 ? 14 : q == 15 ? 16 : 15;
+}
+// Eq. 21 weights
+__host__ __device__ __forceinline__ constexpr float wq(int q)
+{
+    return q < 6 ? (1.0f / 18.0f) : q < 18 ? (1.0f / 36.0f) : (1.0f / 3.0f);
+}
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers 0xD2511F53,
+// 0xCD9E8D57, key schedule by the Weyl constants 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+// 53-bit uniform in [0,1) for (site, step, purpose) under key `seed`.
+__device__ __forceinline__ double uniform53(uint64_t seed, uint32_t site, uint64_t step,
+                                            uint32_t purpose)
+{
+    const uint4 r = philox4x32_10(make_uint4(site, (uint32_t)step, (uint32_t)(step >> 32), purpose),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint64_t bits = ((uint64_t)r.x << 21) | (uint64_t)(r.y >> 11);
+    return (double)bits * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------- contexts
+struct LbCtx {
+    lb_params p;
+    long long N;
+    float* f[2];
+    int cur;             // index of the buffer holding the current state
+    float4* g;
+    float4* v;
+    uint32_t* flags;
+};
+
+struct MemCtx {
+    mem_params p;
+    int n, nt, ne, np, nplt;
+    // device views into the workspace
+    const int* tri;        // [3*nt]
+    const int* tri_plt;    // [nt]
+    const float* tri_S0;   // [nt]
+    const int4* edge;      // [ne] (i, j, k, l), chain k-i-j-l, l < 0 for a boundary edge
+    const float* edge_L0;  // [ne]
+    const float2* edge_cs0;// [ne] (cos, sin) of the rest torsion angle
+    const float* pair_r0;  // [np]
+    const int* spr_off;    // [n+1] node -> (neighbour, edge)
+    const int2* spr;
+    const int* tri_off;    // [n+1] node -> (a, b, triangle) with (node, a, b) outward
+    const int4* trl;
+    const int* dih_off;    // [n+1] node -> 4*edge + role (role 0..3 = k, i, j, l)
+    const int* dih;
+    const int* mor_off;    // [n+1] node -> (partner, pair)
+    const int2* mor;
+    const int* node_plt;   // [n]
+    const uint8_t* is_mem; // [n]
+    const double* plt_S0;  // [nplt]
+    const double* plt_V0;  // [nplt]
+    const int* plt_anchor; // [nplt]
+    double* acc;           // [2*nplt] scratch: S, V accumulators
+};
+
+struct BondCtx {
+    bond_params p;
+    int R;                 // sites
+    int L;                 // ligands
+    const int* site_tri;
+    const double* site_w;
+    const int* tri;
+    int* bound;
+    int* lig_count;
+    // workspace
+    int* nprop;            // [L] proposals this step
+    int* cand;             // [L * kMaxCand]
+    unsigned long long* counters;  // [4]: ruptures, formations, overflow, step (sim)
+};
+constexpr int kMaxCand = 64;
+
+// Launchers used by sim.cu (defined next to their kernels).
+int launch_lb_step(LbCtx* c, cudaStream_t s);
+int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, cudaStream_t s);
+int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, cudaStream_t s);
+int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s);
+int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
+// step_dev: device step counter (advanced by one after the update) or null
+// to use step_host.
+int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
+                      unsigned long long* step_dev, cudaStream_t s);
+
+}  // namespace pfsi
+
+struct lb_ctx : pfsi::LbCtx {};
+struct mem_ctx : pfsi::MemCtx {};
+struct bond_ctx : pfsi::BondCtx {};

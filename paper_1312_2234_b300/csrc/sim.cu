@@ -1,0 +1,132 @@
+// sim.cu -- the coupled per-step loop (flow chart of Fig. 1) as CUDA graphs.
+//
+// One step = membrane forces (+ wall term) -> bond forces -> spreading ->
+// lattice Boltzmann -> interpolation and advection -> adhesion update.  The
+// kernel sequence of a step is captured once per lattice-buffer parity (the
+// two graphs differ only in which population buffer they read) on a private
+// capture stream and then replayed on the caller's stream, so a step costs
+// one graph launch on the host.  The Philox step index lives in device memory
+// (advanced by the last kernel of a step), so replays need no host updates.
+#include "pfsi_internal.cuh"
+
+namespace pfsi {
+
+struct SimCtx {
+    LbCtx* lb;
+    MemCtx* mem;
+    BondCtx* bonds;
+    double* X;
+    float* F;
+    float* U;
+    int M;
+    uint64_t step;
+    cudaStream_t cap;
+    cudaGraphExec_t exec[2];
+};
+
+namespace {
+
+int enqueue_step(SimCtx* c, cudaStream_t s)
+{
+    int rc = launch_membrane_forces(c->mem, c->X, c->F, s);
+    if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
+    if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, s);
+    if (!rc) rc = launch_lb_step(c->lb, s);
+    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, s);
+    if (!rc && c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
+    return rc;
+}
+
+int capture(SimCtx* c, int parity)
+{
+    const int saved = c->lb->cur;
+    c->lb->cur = parity;
+    int rc = check_cuda(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "sim: begin capture");
+    if (rc) {
+        c->lb->cur = saved;
+        return rc;
+    }
+    const int rc_enq = enqueue_step(c, c->cap);
+    cudaGraph_t graph = nullptr;
+    rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
+    c->lb->cur = saved;
+    if (rc_enq) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc_enq;
+    }
+    if (rc) return rc;
+    rc = check_cuda(cudaGraphInstantiate(&c->exec[parity], graph, 0), "sim: instantiate");
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
+}  // namespace
+
+}  // namespace pfsi
+
+using namespace pfsi;
+
+struct sim_ctx : pfsi::SimCtx {};
+
+extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, float* F, float* U, int M,
+                          uint64_t first_step, sim_ctx** out)
+{
+    if (!lb || !mem || !X || !F || !U || !out || M < 1) return set_error(PFSI_ERR_ARG, "sim_create: bad argument");
+    if (mem->n != M) return set_error(PFSI_ERR_ARG, "sim_create: node count differs from the membrane mesh");
+    sim_ctx* c = new sim_ctx();
+    c->lb = lb;
+    c->mem = mem;
+    c->bonds = bonds;
+    c->X = X;
+    c->F = F;
+    c->U = U;
+    c->M = M;
+    c->step = first_step;
+    c->exec[0] = c->exec[1] = nullptr;
+    int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
+    if (!rc && bonds) {
+        const unsigned long long s = first_step;
+        rc = check_cuda(cudaMemcpy(bonds->counters + 3, &s, sizeof(s), cudaMemcpyHostToDevice), "sim_create: step");
+    }
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int sim_destroy(sim_ctx* c)
+{
+    if (!c) return PFSI_OK;
+    for (int k = 0; k < 2; ++k)
+        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return PFSI_OK;
+}
+
+extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
+{
+    if (!c || nsteps < 0) return set_error(PFSI_ERR_ARG, "sim_step: bad argument");
+    cudaStream_t s = as_stream(stream);
+    for (int k = 0; k < nsteps; ++k) {
+        const int parity = c->lb->cur;
+        if (!c->exec[parity]) {
+            const int rc = capture(c, parity);
+            if (rc) return rc;
+        }
+        const int rc = check_cuda(cudaGraphLaunch(c->exec[parity], s), "sim_step: graph launch");
+        if (rc) return rc;
+        c->lb->cur ^= 1;
+        c->step += 1;
+    }
+    return PFSI_OK;
+}
+
+extern "C" int sim_step_index(const sim_ctx* c, uint64_t* out)
+{
+    if (!c || !out) return set_error(PFSI_ERR_ARG, "sim_step_index: null argument");
+    *out = c->step;
+    return PFSI_OK;
+}

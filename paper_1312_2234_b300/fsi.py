@@ -1,0 +1,414 @@
+"""Thin ctypes binding of the C ABI in include/platelet_fsi.h.
+
+Functions keep the C names and only marshal arguments: torch tensors become
+device pointers, the current torch CUDA stream becomes the cudaStream_t.
+Every computation runs in libplatelet_fsi.so; if the library has not been
+built, or a call fails, a RuntimeError is raised (there is no fallback).
+
+The classes at the end (:class:`Lattice`, :class:`Membrane`, :class:`Bonds`,
+:class:`Simulation`) allocate the caller-owned device buffers with torch and
+hold the handles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libplatelet_fsi.so")
+_lib = None
+
+c_int, c_double, c_float, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_float, ctypes.c_size_t, ctypes.c_void_p
+c_uint64, c_longlong = ctypes.c_uint64, ctypes.c_longlong
+
+
+class lb_params(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("tau", c_float),
+                ("u_top", c_float * 3), ("body", c_float * 3)]
+
+
+class lb_sizes(ctypes.Structure):
+    _fields_ = [("f_bytes", c_size_t), ("g_bytes", c_size_t), ("v_bytes", c_size_t),
+                ("flag_bytes", c_size_t), ("n_cells", c_longlong)]
+
+
+class mem_params(ctypes.Structure):
+    _fields_ = [(n, c_float) for n in ("k_spring", "k_s", "k_t", "k_v", "k_b", "morse_D", "morse_a",
+                                        "rep_F0", "rep_tau", "rep_eps_min", "z_wall")]
+
+
+class bond_params(ctypes.Structure):
+    _fields_ = [("lig_i0", c_int), ("lig_j0", c_int), ("lig_ni", c_int), ("lig_nj", c_int),
+                ("box_nx", c_int), ("box_ny", c_int), ("max_per_ligand", c_int),
+                ("z_wall", c_double), ("sigma", c_double), ("l_b", c_double), ("d_capture", c_double),
+                ("gamma", c_double), ("kT", c_double), ("kon0_dt", c_double), ("koff0_dt", c_double),
+                ("seed", c_uint64)]
+
+
+P = c_void_p
+_SIGS = {
+    "pfsi_last_error": [ctypes.c_char_p, c_size_t],
+    "pfsi_version": [],
+    "lb_query_sizes": [ctypes.POINTER(lb_params), ctypes.POINTER(lb_sizes)],
+    "lb_create": [ctypes.POINTER(lb_params), P, P, P, P, P, ctypes.POINTER(P)],
+    "lb_destroy": [P],
+    "lb_init_shear": [P, P],
+    "lb_step": [P, c_int, P],
+    "lb_current": [P, ctypes.POINTER(P)],
+    "lb_moments_fp64": [P, P, ctypes.POINTER(c_double), P],
+    "ib_spread": [P, P, P, c_int, P],
+    "ib_interp": [P, P, P, c_int, c_int, P],
+    "membrane_query_workspace": [c_int, c_int, P, c_int, c_int, ctypes.POINTER(c_size_t)],
+    "membrane_create": [ctypes.POINTER(mem_params), c_int, c_int, P, c_int, P, c_int, P, P, P, P,
+                        c_size_t, ctypes.POINTER(P)],
+    "membrane_destroy": [P],
+    "membrane_set_params": [P, ctypes.POINTER(mem_params)],
+    "membrane_forces": [P, P, P, P],
+    "membrane_measure": [P, P, ctypes.POINTER(c_double), P],
+    "bonds_query_workspace": [ctypes.POINTER(bond_params), c_int, ctypes.POINTER(c_size_t)],
+    "bonds_create": [ctypes.POINTER(bond_params), c_int, P, P, P, P, P, P, c_size_t, ctypes.POINTER(P)],
+    "bonds_destroy": [P],
+    "bonds_forces": [P, P, P, c_int, P],
+    "bonds_step": [P, P, c_int, c_uint64, P],
+    "bonds_status": [P, ctypes.POINTER(c_longlong)],
+    "sim_create": [P, P, P, P, P, P, c_int, c_uint64, ctypes.POINTER(P)],
+    "sim_destroy": [P],
+    "sim_step": [P, c_int, P],
+    "sim_step_index": [P, ctypes.POINTER(c_uint64)],
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libplatelet_fsi.so is not built: run `python -m paper_1312_2234_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = c_int
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().pfsi_last_error(buf, 1024)
+    return buf.value.decode()
+
+
+def _ok(rc, what):
+    if rc != 0:
+        raise RuntimeError("%s failed (%d): %s" % (what, rc, last_error()))
+
+
+def _call(name, *args):
+    _ok(getattr(lib(), name)(*args), name)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous()
+        return c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return c_void_p(t.ctypes.data)
+    return t
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- C-named calls
+def lb_query_sizes(p):
+    s = lb_sizes()
+    _call("lb_query_sizes", ctypes.byref(p), ctypes.byref(s))
+    return s
+
+
+def lb_create(p, f_a, f_b, g, v, flags):
+    h = c_void_p()
+    _call("lb_create", ctypes.byref(p), _ptr(f_a), _ptr(f_b), _ptr(g), _ptr(v), _ptr(flags), ctypes.byref(h))
+    return h
+
+
+def lb_destroy(h):
+    _call("lb_destroy", h)
+
+
+def lb_init_shear(h, stream=None):
+    _call("lb_init_shear", h, _stream(stream))
+
+
+def lb_step(h, nsteps=1, stream=None):
+    _call("lb_step", h, int(nsteps), _stream(stream))
+
+
+def lb_current(h):
+    out = c_void_p()
+    _call("lb_current", h, ctypes.byref(out))
+    return out.value
+
+
+def lb_moments_fp64(h, scratch, stream=None):
+    out = (c_double * 4)()
+    _call("lb_moments_fp64", h, _ptr(scratch), out, _stream(stream))
+    return np.array(out[:])
+
+
+def ib_spread(h, X, F, M, stream=None):
+    _call("ib_spread", h, _ptr(X), _ptr(F), int(M), _stream(stream))
+
+
+def ib_interp(h, X, U, M, advect=True, stream=None):
+    _call("ib_interp", h, _ptr(X), _ptr(U), int(M), int(bool(advect)), _stream(stream))
+
+
+def membrane_query_workspace(n_nodes, tri, n_pairs, n_plt):
+    b = c_size_t()
+    tri = np.ascontiguousarray(tri, dtype=np.int32).ravel()
+    _call("membrane_query_workspace", int(n_nodes), tri.size // 3, _ptr(tri), int(n_pairs), int(n_plt), ctypes.byref(b))
+    return b.value
+
+
+def membrane_create(p, n_nodes, tri, pairs, n_plt, node_plt, is_membrane, X0, ws):
+    tri = np.ascontiguousarray(tri, dtype=np.int32).ravel()
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).ravel()
+    node_plt = np.ascontiguousarray(node_plt, dtype=np.int32)
+    is_mem = np.ascontiguousarray(is_membrane, dtype=np.uint8)
+    X0 = np.ascontiguousarray(X0, dtype=np.float64).ravel()
+    h = c_void_p()
+    _call("membrane_create", ctypes.byref(p), int(n_nodes), tri.size // 3, _ptr(tri), pairs.size // 2, _ptr(pairs),
+          int(n_plt), _ptr(node_plt), _ptr(is_mem), _ptr(X0), _ptr(ws), ws.numel() * ws.element_size(),
+          ctypes.byref(h))
+    return h
+
+
+def membrane_destroy(h):
+    _call("membrane_destroy", h)
+
+
+def membrane_set_params(h, p):
+    _call("membrane_set_params", h, ctypes.byref(p))
+
+
+def membrane_forces(h, X, F, stream=None):
+    _call("membrane_forces", h, _ptr(X), _ptr(F), _stream(stream))
+
+
+def membrane_measure(h, X, n_plt, stream=None):
+    out = (c_double * (2 * n_plt))()
+    _call("membrane_measure", h, _ptr(X), out, _stream(stream))
+    return np.array(out[:]).reshape(n_plt, 2)
+
+
+def bonds_query_workspace(p, n_sites):
+    b = c_size_t()
+    _call("bonds_query_workspace", ctypes.byref(p), int(n_sites), ctypes.byref(b))
+    return b.value
+
+
+def bonds_create(p, n_sites, site_tri, site_w, tri, bound, lig_count, ws):
+    h = c_void_p()
+    _call("bonds_create", ctypes.byref(p), int(n_sites), _ptr(site_tri), _ptr(site_w), _ptr(tri), _ptr(bound),
+          _ptr(lig_count), _ptr(ws), ws.numel() * ws.element_size(), ctypes.byref(h))
+    return h
+
+
+def bonds_destroy(h):
+    _call("bonds_destroy", h)
+
+
+def bonds_forces(h, X, F, M, stream=None):
+    _call("bonds_forces", h, _ptr(X), _ptr(F), int(M), _stream(stream))
+
+
+def bonds_step(h, X, M, step, stream=None):
+    _call("bonds_step", h, _ptr(X), int(M), int(step), _stream(stream))
+
+
+def bonds_status(h):
+    out = (c_longlong * 3)()
+    rc = lib().bonds_status(h, out)
+    return rc, [int(x) for x in out]
+
+
+def sim_create(lb, mem, bonds, X, F, U, M, first_step=0):
+    h = c_void_p()
+    _call("sim_create", lb, mem, bonds, _ptr(X), _ptr(F), _ptr(U), int(M), int(first_step), ctypes.byref(h))
+    return h
+
+
+def sim_destroy(h):
+    _call("sim_destroy", h)
+
+
+def sim_step(h, nsteps=1, stream=None):
+    _call("sim_step", h, int(nsteps), _stream(stream))
+
+
+def sim_step_index(h):
+    out = c_uint64()
+    _call("sim_step_index", h, ctypes.byref(out))
+    return out.value
+
+
+# ---------------------------------------------------------------- owners
+def _bytes(n, device):
+    # torch's caching allocator returns blocks aligned to at least 512 bytes
+    t = torch.empty(max(int(n), 1), dtype=torch.uint8, device=device)
+    assert t.data_ptr() % 256 == 0
+    return t
+
+
+class Lattice:
+    """D3Q19 lattice with caller-owned (torch) buffers."""
+
+    def __init__(self, nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0), device="cuda"):
+        self.p = lb_params(nx, ny, nz, tau, (c_float * 3)(*u_top), (c_float * 3)(*body))
+        s = lb_query_sizes(self.p)
+        self.N = int(s.n_cells)
+        self.shape = (nz, ny, nx)
+        self.f = [torch.empty(19, self.N, dtype=torch.float32, device=device) for _ in range(2)]
+        self.g = torch.zeros(self.N, 4, dtype=torch.float32, device=device)
+        self.v = torch.zeros(self.N, 4, dtype=torch.float32, device=device)
+        self.flags = torch.zeros(ny * nz, dtype=torch.int32, device=device)
+        self.scratch = torch.zeros(4, dtype=torch.float64, device=device)
+        self.h = lb_create(self.p, self.f[0], self.f[1], self.g, self.v, self.flags)
+
+    def current(self):
+        ptr = lb_current(self.h)
+        return self.f[0] if ptr == self.f[0].data_ptr() else self.f[1]
+
+    def init_shear(self):
+        lb_init_shear(self.h)
+
+    def step(self, n=1):
+        lb_step(self.h, n)
+
+    def moments_fp64(self):
+        return lb_moments_fp64(self.h, self.scratch)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.lb_destroy(self.h)
+            self.h = None
+
+
+def mem_params_from(d):
+    return mem_params(*[float(d[n]) for n, _ in mem_params._fields_])
+
+
+def bond_params_from(d):
+    return bond_params(int(d["lig_i0"]), int(d["lig_j0"]), int(d["lig_ni"]), int(d["lig_nj"]),
+                       int(d["box_nx"]), int(d["box_ny"]), int(d["max_per_ligand"]), float(d["z_wall"]),
+                       float(d["sigma"]), float(d["l_b"]), float(d["d_capture"]), float(d["gamma"]),
+                       float(d["kT"]), float(d["kon0_dt"]), float(d["koff0_dt"]), int(d["seed"]))
+
+
+class Membrane:
+    """Membrane mesh (rest state from X0) in a caller-owned workspace."""
+
+    def __init__(self, params, mesh, device="cuda"):
+        n = int(mesh["X0"].size // 3)
+        self.n = n
+        self.n_plt = int(mesh["n_plt"])
+        self.p = mem_params_from(params)
+        pairs = np.asarray(mesh["pairs"], dtype=np.int32).reshape(-1, 2)
+        ws_bytes = membrane_query_workspace(n, mesh["tri"], len(pairs), self.n_plt)
+        self.ws = _bytes(ws_bytes, device)
+        self.h = membrane_create(self.p, n, mesh["tri"], pairs, self.n_plt, mesh["node_plt"],
+                                 mesh["is_membrane"], mesh["X0"], self.ws)
+
+    def forces(self, X, F):
+        membrane_forces(self.h, X, F)
+
+    def measure(self, X):
+        return membrane_measure(self.h, X, self.n_plt)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.membrane_destroy(self.h)
+            self.h = None
+
+
+class Bonds:
+    """Receptor sites and bond state on the device."""
+
+    def __init__(self, params, site_tri, site_w, tri_dev, bound, lig_count, device="cuda"):
+        self.p = bond_params_from(params)
+        self.R = int(len(site_tri))
+        n_tri = int(tri_dev.numel() // 3)
+        st = np.asarray(site_tri)
+        sw = np.asarray(site_w, dtype=np.float64).reshape(-1, 2)
+        bd = np.asarray(bound)
+        if self.R and (st.min() < 0 or st.max() >= n_tri):
+            raise ValueError("receptor site on a triangle id outside [0, %d)" % n_tri)
+        if self.R and (sw.min() < 0 or (sw.sum(1) > 1 + 1e-12).any()):
+            raise ValueError("barycentric weights must be >= 0 with w0 + w1 <= 1")
+        if self.R and (bd.min() < -1 or bd.max() >= self.p.lig_ni * self.p.lig_nj):
+            raise ValueError("bound ligand id out of range")
+        self.site_tri = torch.as_tensor(np.ascontiguousarray(site_tri, dtype=np.int32), device=device)
+        self.site_w = torch.as_tensor(np.ascontiguousarray(site_w, dtype=np.float64).ravel(), device=device)
+        self.tri = tri_dev
+        self.bound = torch.as_tensor(np.ascontiguousarray(bound, dtype=np.int32), device=device).clone()
+        self.lig_count = torch.as_tensor(np.ascontiguousarray(lig_count, dtype=np.int32), device=device).clone()
+        self.ws = _bytes(bonds_query_workspace(self.p, self.R), device)
+        self.h = bonds_create(self.p, self.R, self.site_tri, self.site_w, self.tri, self.bound, self.lig_count,
+                              self.ws)
+
+    def forces(self, X, F, M):
+        bonds_forces(self.h, X, F, M)
+
+    def step(self, X, M, step):
+        bonds_step(self.h, X, M, step)
+
+    def status(self):
+        return bonds_status(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.bonds_destroy(self.h)
+            self.h = None
+
+
+class Simulation:
+    """The coupled step on one workload (see :mod:`paper_1312_2234_b300.workload`)."""
+
+    def __init__(self, w, device="cuda", first_step=0):
+        g = w["grid"]
+        self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device)
+        self.lattice.init_shear()
+        self.membrane = Membrane(w["membrane"], w["mesh"], device)
+        self.M = int(w["M"])
+        self.X = torch.as_tensor(np.ascontiguousarray(w["X"], dtype=np.float64), device=device).clone()
+        self.F = torch.zeros(3 * self.M, dtype=torch.float32, device=device)
+        self.U = torch.zeros(3 * self.M, dtype=torch.float32, device=device)
+        self.tri = torch.as_tensor(np.ascontiguousarray(w["mesh"]["tri"], dtype=np.int32).ravel(), device=device)
+        self.bonds = None
+        if len(w["sites"]["tri"]) > 0:
+            self.bonds = Bonds(w["bonds"], w["sites"]["tri"], w["sites"]["w"], self.tri, w["bound"],
+                               w["lig_count"], device)
+        self.h = sim_create(self.lattice.h, self.membrane.h, self.bonds.h if self.bonds else None,
+                            self.X, self.F, self.U, self.M, first_step)
+
+    def step(self, n=1, stream=None):
+        sim_step(self.h, n, stream)
+
+    @property
+    def step_index(self):
+        return sim_step_index(self.h)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.sim_destroy(self.h)
+            self.h = None

@@ -1,0 +1,96 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+that include/platelet_fsi.h declares; host-side validation rejects bad
+arguments before anything reaches the device (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1312_2234_b300 import build, fsi, workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return fsi.lib()
+
+
+def declared():
+    h = open(os.path.join(ROOT, "include", "platelet_fsi.h")).read()
+    return re.findall(r"^\s*int\s+(\w+)\s*\(", h, re.M)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 20
+    for n in ("lb_create", "lb_step", "ib_interp", "ib_spread", "membrane_forces", "bonds_step", "sim_step"):
+        assert n in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert missing == []
+    assert set(fsi._SIGS) == set(names)
+    assert L.pfsi_version() >= 100
+
+
+def test_lb_query_sizes_validation(L):
+    s = fsi.lb_sizes()
+    p = fsi.lb_params(128, 64, 64, 0.8, (ctypes.c_float * 3)(0, 0, 0), (ctypes.c_float * 3)(0, 0, 0))
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == 0
+    N = 128 * 64 * 64
+    assert s.n_cells == N and s.f_bytes == 19 * 4 * N and s.g_bytes == 16 * N and s.flag_bytes == 4 * 64 * 64
+    p.nz = 1
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
+    assert "nz" in fsi.last_error()
+    p.nz, p.nx = 64, 2 ** 20
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
+    assert L.lb_query_sizes(None, ctypes.byref(s)) == -1
+
+
+def test_lb_create_rejects_bad_buffers(L):
+    p = fsi.lb_params(8, 8, 8, 0.8, (ctypes.c_float * 3)(0, 0, 0), (ctypes.c_float * 3)(0, 0, 0))
+    h = ctypes.c_void_p()
+    assert L.lb_create(ctypes.byref(p), None, None, None, None, None, ctypes.byref(h)) == -1
+    fake = ctypes.c_void_p(0x1000)
+    odd = ctypes.c_void_p(0x1004)
+    assert L.lb_create(ctypes.byref(p), odd, fake, fake, fake, fake, ctypes.byref(h)) == -1
+    assert "aligned" in fsi.last_error()
+    p.tau = 0.5
+    assert L.lb_create(ctypes.byref(p), fake, fake, fake, fake, fake, ctypes.byref(h)) == -1
+    assert "tau" in fsi.last_error()
+
+
+def test_membrane_workspace_query_and_validation(L):
+    w = workload.config_small()
+    m = w["mesh"]
+    nb = fsi.membrane_query_workspace(w["M"], m["tri"], len(m["pairs"]), 1)
+    assert nb > 0 and nb % 256 == 0
+    bad = np.array(m["tri"], copy=True)
+    bad[0, 0] = w["M"] + 5
+    with pytest.raises(RuntimeError, match="out of range"):
+        fsi.membrane_query_workspace(w["M"], bad, 0, 1)
+    flipped = np.array(m["tri"], copy=True)
+    flipped[0] = flipped[0, [0, 2, 1]]
+    with pytest.raises(RuntimeError, match="orient"):
+        fsi.membrane_query_workspace(w["M"], flipped, 0, 1)
+
+
+def test_bond_workspace_query_and_validation(L):
+    w = workload.config_small()
+    p = fsi.bond_params_from(w["bonds"])
+    assert fsi.bonds_query_workspace(p, 100) >= 256 * 16 * 4
+    p.lig_i0 = 30
+    with pytest.raises(RuntimeError, match="patch"):
+        fsi.bonds_query_workspace(p, 100)
+    p = fsi.bond_params_from(dict(w["bonds"], d_capture=1.5))
+    with pytest.raises(RuntimeError, match="d_capture"):
+        fsi.bonds_query_workspace(p, 100)
+
+
+def test_product_path_fails_loudly_without_the_library(monkeypatch):
+    monkeypatch.setattr(fsi, "_lib", None)
+    monkeypatch.setattr(fsi, "LIB_PATH", "/nonexistent/libplatelet_fsi.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        fsi.lib()

@@ -1,0 +1,89 @@
+"""GPU parity of the coupled step sim_step (Fig. 1 order) against the oracle's
+coupled loop on the same seeded workloads: node positions (as displacement
+from the start), node velocities and forces, populations; bond states are
+compared exactly in a window where the positions agree to FP32 rounding."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1312_2234_b300 import fsi, workload
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def f32_workload(w):
+    """The oracle gets the FP32-rounded parameters the device uses."""
+    w = dict(w)
+    w["membrane"] = {k: (float(np.float32(v)) if isinstance(v, float) else v) for k, v in w["membrane"].items()}
+    g = dict(w["grid"])
+    g["tau"] = float(np.float32(g["tau"]))
+    g["u_top"] = tuple(float(np.float32(u)) for u in g["u_top"])
+    w["grid"] = g
+    return w
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def compare(w, steps, tol=TOL):
+    w = f32_workload(w)
+    sim = fsi.Simulation(w)
+    ora = oracle.Sim(w)
+    X0 = w["X"].copy()
+    sim.step(steps)
+    for _ in range(steps):
+        ora.step()
+    torch.cuda.synchronize()
+    Xg = sim.X.cpu().numpy()
+    assert rel_err(Xg - X0, ora.X - X0) < tol
+    assert rel_err(sim.U.cpu().numpy(), ora.U) < tol
+    assert rel_err(sim.F.cpu().numpy(), ora.F) < 10 * tol
+    _, wq = oracle.lattice()
+    fg = sim.lattice.current().cpu().numpy()
+    assert rel_err(fg, ora.f.reshape(19, -1) - wq[:, None]) < tol
+    assert sim.step_index == steps
+    return sim, ora
+
+
+def test_tiny_many_steps():
+    compare(workload.tiny(seed=3, shear=3.0e4), 200)
+
+
+def test_small_config_window():
+    compare(workload.config_small(seed=0), 100)
+
+
+def test_channel_config_sampled_window():
+    compare(workload.config_channel(seed=0), 3)
+
+
+def test_bonds_in_coupled_run():
+    w = workload.tiny(seed=4, shear=2.0e3, n_sites=400, gap=0.05)
+    w["bonds"].update(kon0_dt=0.2, koff0_dt=0.01, sigma=0.05, kT=0.02, gamma=0.05)
+    sim, ora = compare(w, 15)
+    gb = sim.bonds.bound.cpu().numpy()
+    assert (ora.bound >= 0).sum() > 5
+    assert np.array_equal(gb, ora.bound)
+    assert np.array_equal(sim.bonds.lig_count.cpu().numpy(), ora.lig_count)
+
+
+def test_graph_replay_matches_single_calls():
+    """sim_step (graph replay) against the same C-ABI calls made one by one."""
+    w = f32_workload(workload.tiny(seed=5, shear=1.0e4, n_sites=200, gap=0.05))
+    w["bonds"].update(kon0_dt=0.2, koff0_dt=0.01, sigma=0.05, kT=0.02, gamma=0.05)
+    a = fsi.Simulation(w)
+    b = fsi.Simulation(w)
+    a.step(8)
+    for step in range(8):
+        fsi.membrane_forces(b.membrane.h, b.X, b.F)
+        fsi.bonds_forces(b.bonds.h, b.X, b.F, b.M)
+        fsi.ib_spread(b.lattice.h, b.X, b.F, b.M)
+        fsi.lb_step(b.lattice.h, 1)
+        fsi.ib_interp(b.lattice.h, b.X, b.U, b.M, advect=True)
+        fsi.bonds_step(b.bonds.h, b.X, b.M, step)
+    torch.cuda.synchronize()
+    assert rel_err(a.X.cpu().numpy() - w["X"], b.X.cpu().numpy() - w["X"]) < 1e-6
+    assert np.array_equal(a.bonds.bound.cpu().numpy(), b.bonds.bound.cpu().numpy())
