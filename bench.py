@@ -37,7 +37,7 @@ METRIC = "coupled MLUPS + membrane-node updates/s, % HBM roofline, vs plain FP32
 WORKLOAD = ("channel 128x64x64 D3Q19 Couette, shear 1000/s, tau 0.8; 10 platelets x (2562 membrane nodes "
             "+ 800 SCE), 5000 receptor sites each, ligand patch 64x32; plain FP32 (FP64 positions)")
 LB_BYTES_PER_CELL = 152          # 19 float loads + 19 float stores
-KERNELS_PER_STEP = 10            # zero, reduce, membrane, bond forces, spread, lb, interp, rupture, propose, resolve
+KERNELS_PER_STEP = 10            # split, elements, nodes, bond forces, spread, lb, interp, rupture, propose, resolve
 
 
 def log(*a):
@@ -238,7 +238,7 @@ def run_native(args, rank, ws):
     # restore the lattice parity used by the captured graphs
     if len(lb_ms) % 2:
         fsi.lb_step(lat.h, 1)
-    lb_s = statistics.mean(lb_ms) / 1e3
+    lb_s = statistics.median(lb_ms) / 1e3
     lb_bytes = LB_BYTES_PER_CELL * N
     peaks = measured_peaks()
     if peaks:
@@ -298,6 +298,42 @@ def run_native(args, rank, ws):
     print(json.dumps(line), flush=True)
 
 
+def run_lb_only(args):
+    """The lattice kernel alone on a grid of the caller's size (profiling aid:
+    a grid larger than L2 makes its DRAM figures meaningful).  Prints one
+    JSON line with its event-timed duration and algorithmic bandwidth."""
+    import torch
+    from paper_1312_2234_b300 import fsi
+
+    nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+    lat = fsi.Lattice(nx, ny, nz, 0.8, (1e-3, 0.0, 0.0))
+    lat.init_shear()
+    N = nx * ny * nz
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    small = 2 * 76 * N < 2 * 126e6
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fsi.lb_step(lat.h, 1)
+    ms = []
+    for k in range(args.steps):
+        if small:
+            flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fsi.lb_step(lat.h, 1)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms) / 1e3
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    gbs = LB_BYTES_PER_CELL * N / t / 1e9
+    print(json.dumps({"kernel": "k_lb_step", "grid": [nx, ny, nz], "cells": N, "median_ms": 1e3 * t,
+                      "min_ms": min(ms), "GLUPS": N / t / 1e9, "GBps": gbs, "peak_GBps": peak,
+                      "frac": gbs / peak, "l2_flushed": small}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,9 +341,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
+    ap.add_argument("--kernel", default=None, choices=[None, "lb"], help="time one kernel alone")
+    ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.kernel == "lb":
+        run_lb_only(args)
+        return
     rank, ws = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, ws)

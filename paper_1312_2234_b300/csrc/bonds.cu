@@ -123,6 +123,15 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
     }
     if (b >= 0) return;
     const bond_params& p = c.p;
+    // Out of reach of every ligand: the bond length is at least the height
+    // above the wall plane (the margin covers the last-ulp rounding of the
+    // norm), so skipping here cannot change a decision.
+    {
+        const int t = c.site_tri[s];
+        const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
+        const double z = site_coord(X, M, 2, c.tri[3 * t], c.tri[3 * t + 1], c.tri[3 * t + 2], w0, w1);
+        if (fabs(__dsub_rn(z, p.z_wall)) > p.d_capture * (1.0 + 1e-12)) return;
+    }
     const uint64_t step = current_step(step_dev, step_host);
     const SitePos r = site_position(c, X, M, s);
     const double bx = (double)p.box_nx, by = (double)p.box_ny;

@@ -194,6 +194,8 @@ extern "C" int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, f
         return set_error(PFSI_ERR_ARG, "lb_create: buffers must be 16-byte aligned");
     if (!(p->tau > 0.5f)) return set_error(PFSI_ERR_ARG, "lb_create: tau must exceed 1/2");
     if (p->u_top[2] != 0.0f) return set_error(PFSI_ERR_ARG, "lb_create: the top wall cannot move along z");
+    rc = ib_prepare();
+    if (rc) return rc;
     lb_ctx* c = new lb_ctx();
     c->p = *p;
     c->N = sz.n_cells;

@@ -94,14 +94,15 @@ struct LbCtx {
 struct MemCtx {
     mem_params p;
     int n, nt, ne, np, nplt;
-    // device views into the workspace
-    const int* tri;        // [3*nt]
-    const int* tri_plt;    // [nt]
-    const float* tri_S0;   // [nt]
-    const int4* edge;      // [ne] (i, j, k, l), chain k-i-j-l, l < 0 for a boundary edge
-    const float* edge_L0;  // [ne]
-    const float2* edge_cs0;// [ne] (cos, sin) of the rest torsion angle
-    const float* pair_r0;  // [np]
+    // device views into the workspace; (h, l) pairs are double-float values
+    const int* tri;            // [3*nt]
+    const int* tri_plt;        // [nt]
+    const float4* tri_rest;    // [2*nt] (|e1|^2 h,l, |e2|^2 h,l), (e1.e2 h,l, S0, 1/S0)
+    const int4* edge;          // [ne] (i, j, k, l), chain k-i-j-l, l < 0 for a boundary edge
+    const float4* edge_rest;   // [ne] (L0^2 h, L0^2 l, L0, -)
+    const float4* edge_phi0;   // [ne] (cos phi0 h,l, sin phi0 h,l)
+    const int* pair;           // [2*np]
+    const float4* pair_rest;   // [np] (r0^2 h, r0^2 l, r0, -)
     const int* spr_off;    // [n+1] node -> (neighbour, edge)
     const int2* spr;
     const int* tri_off;    // [n+1] node -> (a, b, triangle) with (node, a, b) outward
@@ -112,10 +113,15 @@ struct MemCtx {
     const int2* mor;
     const int* node_plt;   // [n]
     const uint8_t* is_mem; // [n]
-    const double* plt_S0;  // [nplt]
-    const double* plt_V0;  // [nplt]
+    const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
     const int* plt_anchor; // [nplt]
-    double* acc;           // [2*nplt] scratch: S, V accumulators
+    // scratch, rewritten by every call
+    double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
+    float* xh;             // [3n] positions, high floats
+    float* xl;             // [3n] positions, low floats
+    float2* esc;           // [ne] spring magnitude, bending dE/dphi
+    float* tsc;            // [nt] local-area coefficient k_t (S_t - S0_t)/S0_t
+    float* msc;            // [np] Morse magnitude
 };
 
 struct BondCtx {
@@ -133,6 +139,9 @@ struct BondCtx {
     unsigned long long* counters;  // [4]: ruptures, formations, overflow, step (sim)
 };
 constexpr int kMaxCand = 64;
+
+// One-time kernel attributes (large dynamic shared memory) of the IB kernels.
+int ib_prepare();
 
 // Launchers used by sim.cu (defined next to their kernels).
 int launch_lb_step(LbCtx* c, cudaStream_t s);

@@ -150,6 +150,8 @@ def random_rotation(rng):
 
 def sce_points(n, a, c, rng, shrink=0.8):
     """n points uniform inside the ellipsoid (a, a, c) scaled by ``shrink``."""
+    if n == 0:
+        return np.zeros((0, 3))
     out = []
     while len(out) < n:
         p = rng.uniform(-1.0, 1.0, size=(4 * n + 16, 3))

@@ -1,8 +1,11 @@
 """GPU parity of ib_spread / ib_interp (Section 3.4.2, Eq. 33-36) against the
 FP64 oracle: nodes across the periodic seams, on cell centres, next to and
-inside the wall layers; spreading accumulates with FP32 atomics (any order),
-so the spread field is compared within 1e-5 of its largest entry.  Row flags
-are set exactly on the rows of the supports and cleared by interpolation."""
+inside the wall layers (scattered nodes: the per-node path), and the
+platelet meshes of the channel workload (the shared-memory tile path);
+spreading accumulates with FP32 atomics (any order), so the spread field is
+compared within 1e-5 of its largest entry.  Row flags cover the support rows
+(every row of a chunk's box when the chunk is tiled) and interpolation
+clears them all."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +30,7 @@ def nodes(rng, nx, ny, nz, M):
     return X
 
 
-def expected_rows(X, ny, nz):
+def support_rows(X, ny, nz):
     rows = set()
     for m in range(X.shape[1]):
         by, bz = int(np.floor(X[1, m])) - 1, int(np.floor(X[2, m])) - 1
@@ -39,11 +42,38 @@ def expected_rows(X, ny, nz):
     return rows
 
 
-@pytest.mark.parametrize("dims,M", [((29, 21, 17), 700), ((128, 64, 64), 33620)])
+def expected_rows(X, ny, nz, chunk=256, cap=4096):
+    """Rows the spreading kernel flags: per chunk of 256 nodes, every row of the
+    supports' bounding box when it fits the 4096-cell tile, else the support
+    rows."""
+    rows = set()
+    for s0 in range(0, X.shape[1], chunk):
+        Xc = X[:, s0:s0 + chunk]
+        b = np.floor(Xc).astype(np.int64) - 1
+        z0, z1 = max(b[2].min(), 0), min(b[2].max() + 3, nz - 1)
+        ex, ey, ez = b[0].max() + 4 - b[0].min(), b[1].max() + 4 - b[1].min(), z1 - z0 + 1
+        if ez > 0 and ex * ey * ez <= cap:
+            rows |= {k * ny + j % ny for k in range(z0, z1 + 1) for j in range(b[1].min(), b[1].max() + 4)}
+        else:
+            rows |= support_rows(Xc, ny, nz)
+    return rows
+
+
+def platelet_nodes():
+    from paper_1312_2234_b300 import workload
+    w = workload.config_channel(seed=1)
+    return w["X"].reshape(3, -1).copy(), (128, 64, 64)
+
+
+@pytest.mark.parametrize("dims,M", [((29, 21, 17), 700), ((128, 64, 64), 33620), ("platelets", 0)])
 def test_spread_parity_and_flags(dims, M):
-    nx, ny, nz = dims
     rng = np.random.default_rng(11)
-    X = nodes(rng, nx, ny, nz, M)
+    if dims == "platelets":
+        X, dims = platelet_nodes()
+        M = X.shape[1]
+    else:
+        X = nodes(rng, *dims, M)
+    nx, ny, nz = dims
     F = rng.standard_normal((3, M)).astype(np.float32)
     lat = fsi.Lattice(nx, ny, nz, 0.8)
     Xd = torch.from_numpy(np.ascontiguousarray(X).ravel()).cuda()
@@ -59,12 +89,16 @@ def test_spread_parity_and_flags(dims, M):
     assert set(np.nonzero(flags)[0].tolist()) == expected_rows(X, ny, nz)
 
 
-@pytest.mark.parametrize("dims,M", [((29, 21, 17), 700), ((128, 64, 64), 33620)])
+@pytest.mark.parametrize("dims,M", [((29, 21, 17), 700), ((128, 64, 64), 33620), ("platelets", 0)])
 def test_interp_parity_advect_and_flag_clear(dims, M):
+    rng = np.random.default_rng(12)
+    if dims == "platelets":
+        X, dims = platelet_nodes()
+        M = X.shape[1]
+    else:
+        X = nodes(rng, *dims, M)
     nx, ny, nz = dims
     N = nx * ny * nz
-    rng = np.random.default_rng(12)
-    X = nodes(rng, nx, ny, nz, M)
     lat = fsi.Lattice(nx, ny, nz, 0.8)
     v = rng.standard_normal((N, 4)).astype(np.float32) * 1e-3
     lat.v.copy_(torch.from_numpy(v))

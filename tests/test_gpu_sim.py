@@ -40,7 +40,15 @@ def compare(w, steps, tol=TOL):
     Xg = sim.X.cpu().numpy()
     assert rel_err(Xg - X0, ora.X - X0) < tol
     assert rel_err(sim.U.cpu().numpy(), ora.U) < tol
-    assert rel_err(sim.F.cpu().numpy(), ora.F) < 10 * tol
+    # FP32 forces at the tiny strains of a coupled run: relative bound plus an
+    # absolute floor ~2^-24 of (k + k_s + k_t) x rest length per node term
+    X0m = w["mesh"]["X0"].reshape(3, -1)
+    t = np.asarray(w["mesh"]["tri"])
+    mean_edge = float(np.mean(np.linalg.norm(X0m[:, t[:, 0]] - X0m[:, t[:, 1]], axis=0)))
+    mp = w["membrane"]
+    floor = 2e-6 * (mp["k_spring"] + mp["k_s"] + mp["k_t"]) * mean_edge
+    dF = np.max(np.abs(sim.F.cpu().numpy() - ora.F))
+    assert dF <= tol * np.max(np.abs(ora.F)) + floor, (dF, np.max(np.abs(ora.F)), floor)
     _, wq = oracle.lattice()
     fg = sim.lattice.current().cpu().numpy()
     assert rel_err(fg, ora.f.reshape(19, -1) - wq[:, None]) < tol
