@@ -7,19 +7,25 @@
 // (cells with k outside [0, nz) are skipped), so spreading and interpolation
 // stay adjoint.
 //
-// Blocking: a block takes a chunk of 256 consecutive nodes (consecutive nodes
-// of a platelet mesh lie close together) and the bounding box of their 4x4x4
-// supports.  When the box fits the shared-memory tile (4096 cells):
-//   spreading  accumulates the chunk's F_m * w in the tile with shared
-//              atomics, then adds each nonzero tile cell to the float4 force
-//              field with one vector reduction (red.global.add.v4.f32): ~10
-//              global reductions per node instead of 64;
-//   interp     loads the velocity of the box into the tile once and gathers
-//              every node's 64 weights from shared memory.
-// Otherwise the block falls back to per-node global reductions / gathers.
-// Both kernels take the same decision for the same positions, and flag /
-// clear the same rows: every row of the box (a superset of the support rows),
-// so the lattice step writes the velocity wherever interpolation will read.
+// Blocking: a block of 512 threads takes a chunk of 256 consecutive nodes
+// (consecutive nodes of a platelet mesh lie close together).  Each thread of
+// the first half stages one node (support origin, weights, force); then each
+// warp walks its share of the chunk one node at a time with lane l on support
+// cell (a, b, c) = (l & 3, (l >> 2) & 3, (l >> 4) + {0, 2}), so one
+// instruction touches 32 distinct cells.  When the bounding box of the
+// chunk's supports fits the shared tile (three float planes, strides padded
+// so that those 32 cells fall in 32 different banks):
+//   spreading  accumulates in the tile with shared atomics, then adds every
+//              nonzero tile cell to the float4 force field with one vector
+//              reduction (red.global.add.v4.f32): ~4 global reductions per
+//              node of a platelet instead of 64;
+//   interp     loads the box's velocity into the tile once; each node's 64
+//              weighted values are summed across the warp with shuffles.
+// Otherwise (e.g. a chunk that straddles two platelets) the block works on the
+// global arrays directly, with the same lane-per-cell mapping.  Both kernels
+// take the same decision for the same positions and flag / clear the same
+// rows: every row of the box (a superset of the support rows), so the lattice
+// step writes the velocity wherever interpolation will read it.
 #include <climits>
 
 #include "pfsi_internal.cuh"
@@ -28,9 +34,11 @@ namespace pfsi {
 
 namespace {
 
-constexpr int kChunk = 256;
-constexpr int kTileCells = 4096;
-constexpr size_t kTileBytes = kTileCells * sizeof(float4);
+constexpr int kChunk = 256;                 // nodes per block
+constexpr int kThreads = 512;               // threads per block
+constexpr int kWarps = kThreads / 32;
+constexpr int kTileFloats = 3 * 4096;       // three planes of up to 4096 cells
+constexpr size_t kTileBytes = kTileFloats * sizeof(float);
 
 __device__ __forceinline__ float phi4(float r) { return 0.25f * (1.0f + cospif(0.5f * r)); }
 
@@ -40,39 +48,44 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-struct Node {
-    int bx, by, bz;              // unwrapped cell of support offset 0 on each axis
-    float wx[4], wy[4], wz[4];
+struct Stage {
+    int bx[kChunk], by[kChunk], bz[kChunk];
+    float w[12][kChunk];  // wx[0..3], wy[0..3], wz[0..3]
+    float f[3][kChunk];
 };
 
-__device__ __forceinline__ void node_support(double x, double y, double z, Node& s)
+__device__ __forceinline__ void stage_node(Stage& st, int j, double x, double y, double z)
 {
     const double fx = floor(x), fy = floor(y), fz = floor(z);
     const float tx = (float)(x - fx), ty = (float)(y - fy), tz = (float)(z - fz);
-    s.bx = (int)fx - 1;
-    s.by = (int)fy - 1;
-    s.bz = (int)fz - 1;
+    st.bx[j] = (int)fx - 1;
+    st.by[j] = (int)fy - 1;
+    st.bz[j] = (int)fz - 1;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        s.wx[a] = phi4((float)(a - 1) - tx);
-        s.wy[a] = phi4((float)(a - 1) - ty);
-        s.wz[a] = phi4((float)(a - 1) - tz);
+        st.w[a][j] = phi4((float)(a - 1) - tx);
+        st.w[4 + a][j] = phi4((float)(a - 1) - ty);
+        st.w[8 + a][j] = phi4((float)(a - 1) - tz);
     }
 }
 
 struct Box {
-    int x0, y0, z0;   // unwrapped origin; z0 clipped to the walls
-    int ex, ey, ez;   // extents (ez after clipping, may be <= 0)
+    int x0, y0, z0;    // unwrapped origin; z0 clipped to the walls
+    int ex, ey, ez;    // extents (ez after clipping, may be <= 0)
+    int sx, sy;        // padded x stride and y extent of the tile
     bool tiled;
 };
 
-// Bounding box of the supports of the block's active nodes.
-__device__ Box block_box(const Node& s, bool active, int nz)
+// Bounding box of the staged supports (nodes [0, nodes)); also a barrier for
+// the staging writes.
+__device__ Box block_box(const Stage& st, int nodes, int nz)
 {
-    __shared__ int red[6][kChunk / 32];
+    __shared__ int red[6][kWarps];
     __shared__ Box box;
-    int v[6] = {active ? s.bx : INT_MAX, active ? s.by : INT_MAX, active ? s.bz : INT_MAX,
-                active ? s.bx : INT_MIN, active ? s.by : INT_MIN, active ? s.bz : INT_MIN};
+    const int j = threadIdx.x;
+    const bool on = j < nodes;
+    int v[6] = {on ? st.bx[j] : INT_MAX, on ? st.by[j] : INT_MAX, on ? st.bz[j] : INT_MAX,
+                on ? st.bx[j] : INT_MIN, on ? st.by[j] : INT_MIN, on ? st.bz[j] : INT_MIN};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -84,7 +97,7 @@ __device__ Box block_box(const Node& s, bool active, int nz)
     __syncthreads();
     if (threadIdx.x == 0) {
         int r[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 0; w < kWarps; ++w) {
             for (int k = 0; k < 3; ++k) r[k] = min(r[k], red[k][w]);
             for (int k = 3; k < 6; ++k) r[k] = max(r[k], red[k][w]);
         }
@@ -96,165 +109,170 @@ __device__ Box block_box(const Node& s, bool active, int nz)
         b.ex = r[3] + 4 - r[0];
         b.ey = r[4] + 4 - r[1];
         b.ez = z1 - z0 + 1;
-        b.tiled = b.ez > 0 && (long long)b.ex * b.ey * b.ez <= kTileCells;
+        // strides: sx = 4 (mod 16) and sx * sy = 16 (mod 32) put the 32 cells
+        // of one node's half-support in 32 different banks
+        b.sx = ((b.ex + 11) / 16) * 16 + 4;
+        b.sy = ((b.ey + 3) / 8) * 8 + 4;
+        if (b.ey <= 4) b.sy = 4;
+        b.tiled = b.ez > 0 && b.ex <= 1024 && b.ey <= 1024 &&
+                  (long long)b.sx * b.sy * b.ez * 3 <= kTileFloats;
         box = b;
     }
     __syncthreads();
     return box;
 }
 
-__global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
-                                                      int M, float4* __restrict__ g,
-                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz)
+__global__ void __launch_bounds__(kThreads) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
+                                                        int M, float4* __restrict__ g,
+                                                        uint32_t* __restrict__ flags, int nx, int ny, int nz)
 {
-    extern __shared__ float4 tile[];
-    const int m = blockIdx.x * kChunk + threadIdx.x;
-    const bool active = m < M;
-    Node s;
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (active) {
-        node_support(X[m], X[M + m], X[2 * M + m], s);
-        fx = F[m];
-        fy = F[M + m];
-        fz = F[2 * M + m];
+    extern __shared__ float tile[];
+    __shared__ Stage st;
+    const int m0 = blockIdx.x * kChunk;
+    const int nodes = min(kChunk, M - m0);
+    if (threadIdx.x < nodes) {
+        const int m = m0 + threadIdx.x;
+        stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
+        st.f[0][threadIdx.x] = F[m];
+        st.f[1][threadIdx.x] = F[M + m];
+        st.f[2][threadIdx.x] = F[2 * M + m];
     }
-    const Box b = block_box(s, active, nz);
+    const Box b = block_box(st, nodes, nz);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
+    const int plane = b.sx * b.sy * b.ez;
     if (b.tiled) {
-        const int cells = b.ex * b.ey * b.ez;
-        for (int i = threadIdx.x; i < cells; i += kChunk) tile[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = threadIdx.x; i < 3 * plane; i += kThreads) tile[i] = 0.f;
         __syncthreads();
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int k = s.bz + c - b.z0;
-                if (k < 0 || k >= b.ez) continue;
-#pragma unroll
-                for (int bb = 0; bb < 4; ++bb) {
-                    const float wyz = s.wy[bb] * s.wz[c];
-                    float* row = reinterpret_cast<float*>(tile + ((size_t)k * b.ey + (s.by + bb - b.y0)) * b.ex +
-                                                          (s.bx - b.x0));
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const float w = s.wx[a] * wyz;
-                        atomicAdd(row + 4 * a + 0, fx * w);
-                        atomicAdd(row + 4 * a + 1, fy * w);
-                        atomicAdd(row + 4 * a + 2, fz * w);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const int x0 = wrap(b.x0, nx), y0 = wrap(b.y0, ny);
-        for (int i = threadIdx.x; i < cells; i += kChunk) {
-            const float4 val = tile[i];
-            const int a = i % b.ex, rest = i / b.ex, bb = rest % b.ey, c = rest / b.ey;
-            if (a == 0) flags[(b.z0 + c) * ny + wrap(y0 + bb, ny)] = 1u;
-            if (val.x != 0.f || val.y != 0.f || val.z != 0.f) {
-                const int gi = wrap(x0 + a, nx), gj = wrap(y0 + bb, ny);
-                atomicAdd(g + ((size_t)(b.z0 + c) * ny + gj) * nx + gi, val);
-            }
-        }
-        return;
     }
-    if (!active) return;
-    // fallback: per-node global reductions
+    for (int j = warp; j < nodes; j += kWarps) {
+        const float fx = st.f[0][j], fy = st.f[1][j], fz = st.f[2][j];
+        const float wxy = st.w[la][j] * st.w[4 + lb][j];
+        const int bx = st.bx[j], by = st.by[j], bz = st.bz[j];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int k = s.bz + c;
-        if (k < 0 || k >= nz) continue;
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-            const int row = k * ny + wrap(s.by + bb, ny);
-            flags[row] = 1u;
-            const float wyz = s.wy[bb] * s.wz[c];
-            float4* base = g + (size_t)row * nx;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float w = s.wx[a] * wyz;
-                atomicAdd(base + wrap(s.bx + a, nx), make_float4(fx * w, fy * w, fz * w, 0.0f));
+        for (int h = 0; h < 2; ++h) {
+            const int c = lc + 2 * h;
+            const float w = wxy * st.w[8 + c][j];
+            if (b.tiled) {
+                const int k = bz + c - b.z0;
+                if (k < 0 || k >= b.ez) continue;
+                const int i = (k * b.sy + (by + lb - b.y0)) * b.sx + (bx + la - b.x0);
+                atomicAdd(tile + i, fx * w);
+                atomicAdd(tile + plane + i, fy * w);
+                atomicAdd(tile + 2 * plane + i, fz * w);
+            } else {
+                const int k = bz + c;
+                if (k < 0 || k >= nz) continue;
+                const int row = k * ny + wrap(by + lb, ny);
+                if (la == 0) flags[row] = 1u;
+                atomicAdd(g + (size_t)row * nx + wrap(bx + la, nx), make_float4(fx * w, fy * w, fz * w, 0.0f));
             }
+        }
+    }
+    if (!b.tiled) return;
+    __syncthreads();
+    // flush: one warp per tile row
+    const int x0 = wrap(b.x0, nx), y0 = wrap(b.y0, ny);
+    for (int r = warp; r < b.ey * b.ez; r += kWarps) {
+        const int bb = r % b.ey, c = r / b.ey;
+        const int grow = (b.z0 + c) * ny + wrap(y0 + bb, ny);
+        if (lane == 0) flags[grow] = 1u;
+        const int base = (c * b.sy + bb) * b.sx;
+        for (int a = lane; a < b.ex; a += 32) {
+            const float4 val = make_float4(tile[base + a], tile[plane + base + a], tile[2 * plane + base + a], 0.f);
+            if (val.x != 0.f || val.y != 0.f || val.z != 0.f)
+                atomicAdd(g + (size_t)grow * nx + wrap(x0 + a, nx), val);
         }
     }
 }
 
-__global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
-                                                      const float4* __restrict__ v,
-                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz,
-                                                      int advect)
+__global__ void __launch_bounds__(kThreads) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
+                                                        const float4* __restrict__ v,
+                                                        uint32_t* __restrict__ flags, int nx, int ny, int nz,
+                                                        int advect)
 {
-    extern __shared__ float4 tile[];
-    const int m = blockIdx.x * kChunk + threadIdx.x;
-    const bool active = m < M;
-    Node s;
-    double x = 0.0, y = 0.0, z = 0.0;
-    if (active) {
-        x = X[m];
-        y = X[M + m];
-        z = X[2 * M + m];
-        node_support(x, y, z, s);
+    extern __shared__ float tile[];
+    __shared__ Stage st;
+    const int m0 = blockIdx.x * kChunk;
+    const int nodes = min(kChunk, M - m0);
+    if (threadIdx.x < nodes) {
+        const int m = m0 + threadIdx.x;
+        stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
     }
-    const Box b = block_box(s, active, nz);
-    float ux = 0.f, uy = 0.f, uz = 0.f;
+    const Box b = block_box(st, nodes, nz);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
+    const int plane = b.sx * b.sy * b.ez;
     if (b.tiled) {
-        const int cells = b.ex * b.ey * b.ez;
+        // fill: one warp per tile row; clear the rows' flags
         const int x0 = wrap(b.x0, nx), y0 = wrap(b.y0, ny);
-        for (int i = threadIdx.x; i < cells; i += kChunk) {
-            const int a = i % b.ex, rest = i / b.ex, bb = rest % b.ey, c = rest / b.ey;
-            const int row = (b.z0 + c) * ny + wrap(y0 + bb, ny);
-            tile[i] = v[(size_t)row * nx + wrap(x0 + a, nx)];
+        for (int r = warp; r < b.ey * b.ez; r += kWarps) {
+            const int bb = r % b.ey, c = r / b.ey;
+            const int grow = (b.z0 + c) * ny + wrap(y0 + bb, ny);
+            const int base = (c * b.sy + bb) * b.sx;
+            for (int a = lane; a < b.ex; a += 32) {
+                const float4 val = v[(size_t)grow * nx + wrap(x0 + a, nx)];
+                tile[base + a] = val.x;
+                tile[plane + base + a] = val.y;
+                tile[2 * plane + base + a] = val.z;
+            }
+            if (lane == 0) flags[grow] = 0u;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < b.ey * b.ez; i += kChunk)
-            flags[(b.z0 + i / b.ey) * ny + wrap(y0 + i % b.ey, ny)] = 0u;
-        if (!active) return;
+    }
+    for (int j = warp; j < nodes; j += kWarps) {
+        const float wxy = st.w[la][j] * st.w[4 + lb][j];
+        const int bx = st.bx[j], by = st.by[j], bz = st.bz[j];
+        float ux = 0.f, uy = 0.f, uz = 0.f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = s.bz + c - b.z0;
-            if (k < 0 || k >= b.ez) continue;
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const float wyz = s.wy[bb] * s.wz[c];
-                const float4* row = tile + ((size_t)k * b.ey + (s.by + bb - b.y0)) * b.ex + (s.bx - b.x0);
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float w = s.wx[a] * wyz;
-                    const float4 vv = row[a];
-                    ux += w * vv.x;
-                    uy += w * vv.y;
-                    uz += w * vv.z;
-                }
+        for (int h = 0; h < 2; ++h) {
+            const int c = lc + 2 * h;
+            const float w = wxy * st.w[8 + c][j];
+            if (b.tiled) {
+                const int k = bz + c - b.z0;
+                if (k < 0 || k >= b.ez) continue;
+                const int i = (k * b.sy + (by + lb - b.y0)) * b.sx + (bx + la - b.x0);
+                ux += w * tile[i];
+                uy += w * tile[plane + i];
+                uz += w * tile[2 * plane + i];
+            } else {
+                const int k = bz + c;
+                if (k < 0 || k >= nz) continue;
+                const int row = k * ny + wrap(by + lb, ny);
+                const float4 vv = v[(size_t)row * nx + wrap(bx + la, nx)];
+                ux += w * vv.x;
+                uy += w * vv.y;
+                uz += w * vv.z;
             }
         }
-    } else {
-        if (!active) return;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = s.bz + c;
-            if (k < 0 || k >= nz) continue;
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const int row = k * ny + wrap(s.by + bb, ny);
-                const float wyz = s.wy[bb] * s.wz[c];
-                const float4* base = v + (size_t)row * nx;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const float w = s.wx[a] * wyz;
-                    const float4 vv = base[wrap(s.bx + a, nx)];
-                    ux += w * vv.x;
-                    uy += w * vv.y;
-                    uz += w * vv.z;
-                }
-                flags[row] = 0u;
+        for (int o = 16; o > 0; o >>= 1) {
+            ux += __shfl_xor_sync(0xffffffffu, ux, o);
+            uy += __shfl_xor_sync(0xffffffffu, uy, o);
+            uz += __shfl_xor_sync(0xffffffffu, uz, o);
+        }
+        if (lane == 0) {
+            const int m = m0 + j;
+            U[m] = ux;
+            U[M + m] = uy;
+            U[2 * M + m] = uz;
+            if (advect) {
+                X[m] += (double)ux;
+                X[M + m] += (double)uy;
+                X[2 * M + m] += (double)uz;
             }
         }
     }
-    U[m] = ux;
-    U[M + m] = uy;
-    U[2 * M + m] = uz;
-    if (advect) {
-        X[m] = x + (double)ux;
-        X[M + m] = y + (double)uy;
-        X[2 * M + m] = z + (double)uz;
+    if (b.tiled) return;
+    // fallback path: clear the support rows (after every warp has read them)
+    __syncthreads();
+    for (int j = warp; j < nodes; j += kWarps) {
+        if (la != 0) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = st.bz[j] + lc + 2 * h;
+            if (k >= 0 && k < nz) flags[k * ny + wrap(st.by[j] + lb, ny)] = 0u;
+        }
     }
 }
 
@@ -273,16 +291,16 @@ int ib_prepare()
 int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
-    k_ib_spread<<<(M + kChunk - 1) / kChunk, kChunk, kTileBytes, s>>>(X, F, M, c->g, c->flags, c->p.nx, c->p.ny,
-                                                                       c->p.nz);
+    k_ib_spread<<<(M + kChunk - 1) / kChunk, kThreads, kTileBytes, s>>>(X, F, M, c->g, c->flags, c->p.nx, c->p.ny,
+                                                                         c->p.nz);
     return check_launch("ib_spread");
 }
 
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
-    k_ib_interp<<<(M + kChunk - 1) / kChunk, kChunk, kTileBytes, s>>>(X, U, M, c->v, c->flags, c->p.nx, c->p.ny,
-                                                                       c->p.nz, advect);
+    k_ib_interp<<<(M + kChunk - 1) / kChunk, kThreads, kTileBytes, s>>>(X, U, M, c->v, c->flags, c->p.nx, c->p.ny,
+                                                                         c->p.nz, advect);
     return check_launch("ib_interp");
 }
 

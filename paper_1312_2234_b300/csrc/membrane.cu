@@ -18,10 +18,14 @@
 //             phi - phi0, r - r0, the platelet's area change and volume) in
 //             double-float arithmetic (ff.cuh), so forces keep ~7 digits at
 //             any strain, and adds the per-platelet sums in FP64;
-//   nodes     one thread per node gathers those scalars times FP32
-//             directions over its own lists of springs, triangles, dihedral
-//             roles and Morse partners: each force is written once, without
-//             atomics, in a fixed order.
+//             The same threads turn the scalars into FP32 force vectors, one
+//             per (element, vertex): spring + bending for the four vertices
+//             of an edge's dihedral chain, area gradients per triangle corner,
+//             the Morse force per pair;
+//   nodes     one thread per node sums its element contributions from its
+//             own lists (independent loads, no atomics, fixed order) and
+//             applies the per-platelet global area and volume terms and the
+//             wall repulsion.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -39,10 +43,12 @@ namespace {
 // ------------------------------------------------------------------ host topology
 struct Topology {
     std::vector<int4> edge;   // (i, j, k, l)
-    std::vector<int> spr_off, tri_off, dih_off, mor_off;
-    std::vector<int2> spr, mor;
-    std::vector<int4> trl;
-    std::vector<int> dih;
+    // per-node lists of element slots:
+    //   esl: 4*edge + slot, slot 0..3 = vertex k, i, j, l of the edge's chain
+    //   tcl: 4*triangle + corner, corner 0..2
+    //   psl: 2*pair + side, side 0/1 = first/second node of the pair
+    std::vector<int> esl_off, tcl_off, psl_off;
+    std::vector<int> esl, tcl, psl;
 };
 
 int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topology& T,
@@ -95,94 +101,57 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
         s = e;
     }
     const int ne = (int)T.edge.size();
-    // counting sort into per-node lists
-    auto csr = [n](std::vector<int>& off, const std::vector<int>& owner) {
+    // per-node lists by counting sort
+    auto csr = [n](std::vector<int>& off, std::vector<int>& list, const std::vector<int2>& owner_code) {
         off.assign(n + 1, 0);
-        for (int o : owner) off[o + 1]++;
+        for (const int2& oc : owner_code) off[oc.x + 1]++;
         for (int v = 0; v < n; ++v) off[v + 1] += off[v];
+        list.assign(owner_code.size(), 0);
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (const int2& oc : owner_code) list[fill[oc.x]++] = oc.y;
     };
-    std::vector<int> owner;
-    // springs
-    owner.clear();
+    std::vector<int2> oc;
     for (int e = 0; e < ne; ++e) {
-        owner.push_back(T.edge[e].x);
-        owner.push_back(T.edge[e].y);
-    }
-    csr(T.spr_off, owner);
-    T.spr.assign(owner.size(), make_int2(0, 0));
-    {
-        std::vector<int> fill(T.spr_off.begin(), T.spr_off.end() - 1);
-        for (int e = 0; e < ne; ++e) {
-            T.spr[fill[T.edge[e].x]++] = make_int2(T.edge[e].y, e);
-            T.spr[fill[T.edge[e].y]++] = make_int2(T.edge[e].x, e);
+        const int4 q = T.edge[e];
+        oc.push_back(make_int2(q.x, 4 * e + 1));
+        oc.push_back(make_int2(q.y, 4 * e + 2));
+        if (q.w >= 0) {
+            oc.push_back(make_int2(q.z, 4 * e + 0));
+            oc.push_back(make_int2(q.w, 4 * e + 3));
         }
     }
-    // triangles, rotated so that the node comes first (orientation kept)
-    owner.clear();
-    for (int t = 0; t < 3 * nt; ++t) owner.push_back(tri[t]);
-    csr(T.tri_off, owner);
-    T.trl.assign(owner.size(), make_int4(0, 0, 0, 0));
-    {
-        std::vector<int> fill(T.tri_off.begin(), T.tri_off.end() - 1);
-        for (int t = 0; t < nt; ++t)
-            for (int r = 0; r < 3; ++r) {
-                const int a = tri[3 * t + r], b = tri[3 * t + (r + 1) % 3], c = tri[3 * t + (r + 2) % 3];
-                T.trl[fill[a]++] = make_int4(b, c, t, 0);
-            }
+    csr(T.esl_off, T.esl, oc);
+    oc.clear();
+    for (int t = 0; t < nt; ++t)
+        for (int r = 0; r < 3; ++r) oc.push_back(make_int2(tri[3 * t + r], 4 * t + r));
+    csr(T.tcl_off, T.tcl, oc);
+    oc.clear();
+    for (int q = 0; q < np; ++q) {
+        oc.push_back(make_int2(pairs[2 * q], 2 * q));
+        oc.push_back(make_int2(pairs[2 * q + 1], 2 * q + 1));
     }
-    // dihedral roles: chain k-i-j-l, role 0..3
-    owner.clear();
-    for (int e = 0; e < ne; ++e)
-        if (T.edge[e].w >= 0) {
-            owner.push_back(T.edge[e].z);
-            owner.push_back(T.edge[e].x);
-            owner.push_back(T.edge[e].y);
-            owner.push_back(T.edge[e].w);
-        }
-    csr(T.dih_off, owner);
-    T.dih.assign(owner.size(), 0);
-    {
-        std::vector<int> fill(T.dih_off.begin(), T.dih_off.end() - 1);
-        for (int e = 0; e < ne; ++e)
-            if (T.edge[e].w >= 0) {
-                const int v[4] = {T.edge[e].z, T.edge[e].x, T.edge[e].y, T.edge[e].w};
-                for (int r = 0; r < 4; ++r) T.dih[fill[v[r]]++] = 4 * e + r;
-            }
-    }
-    // Morse partners
-    owner.clear();
-    for (int s = 0; s < 2 * np; ++s) owner.push_back(pairs[s]);
-    csr(T.mor_off, owner);
-    T.mor.assign(owner.size(), make_int2(0, 0));
-    {
-        std::vector<int> fill(T.mor_off.begin(), T.mor_off.end() - 1);
-        for (int s = 0; s < np; ++s) {
-            T.mor[fill[pairs[2 * s]]++] = make_int2(pairs[2 * s + 1], s);
-            T.mor[fill[pairs[2 * s + 1]]++] = make_int2(pairs[2 * s], s);
-        }
-    }
+    csr(T.psl_off, T.psl, oc);
     return PFSI_OK;
 }
 
 // Workspace layout: consecutive 256-byte aligned slices.
 enum Slice {
-    S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_SPR_OFF,
-    S_SPR, S_TRI_OFF, S_TRL, S_DIH_OFF, S_DIH, S_MOR_OFF, S_MOR, S_NODE_PLT, S_IS_MEM, S_PLT_REST,
-    S_PLT_ANCHOR, S_ACC, S_XH, S_XL, S_ESC, S_TSC, S_MSC, S_COUNT
+    S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
+    S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_COUNT
 };
 struct Layout {
     size_t off[S_COUNT];
     size_t total;
 };
 
-Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_spr, size_t n_trl, size_t n_dih,
-                   size_t n_mor)
+Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t n_tcl, size_t n_psl)
 {
     const size_t N = n, T = nt, E = ne, P = np, Q = nplt;
     const size_t bytes[S_COUNT] = {
-        12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 8 * n_spr,
-        4 * (N + 1), 16 * n_trl, 4 * (N + 1), 4 * n_dih, 4 * (N + 1), 8 * n_mor, 4 * N, N, 32 * Q,
-        4 * Q, 16 * Q, 12 * N, 12 * N, 8 * E, 4 * T, 4 * P};
+        12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
+        4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 16 * Q, 12 * N, 12 * N,
+        64 * E, 64 * T, 16 * P};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -252,16 +221,38 @@ __global__ void __launch_bounds__(256) k_mem_split(const double* __restrict__ X,
     if (t < nacc) acc[t] = 0.0;
 }
 
-// Pass 2: the cancelling scalars, one thread per edge, triangle or Morse pair.
+// Torsion gradient of the chain r1-r2-r3-r4 (Blondel and Karplus 1996), FP32,
+// positions relative to r2.  g[0..3] = d phi / d r_a.
+__device__ __forceinline__ void torsion_grad(float3 r1, float3 r3, float3 r4, float3 g[4])
+{
+    const float3 Fv = r1, G = make_float3(-r3.x, -r3.y, -r3.z), H = f3sub(r4, r3);
+    const float3 A = f3cross(Fv, G), B = f3cross(H, G);
+    const float A2 = f3dot(A, A), B2 = f3dot(B, B), gn = sqrtf(f3dot(G, G));
+    const float FG = f3dot(Fv, G) / (A2 * gn), HG = f3dot(H, G) / (B2 * gn);
+    const float ka = gn / A2, kb = gn / B2;
+    g[0] = make_float3(-ka * A.x, -ka * A.y, -ka * A.z);
+    g[3] = make_float3(kb * B.x, kb * B.y, kb * B.z);
+    g[1] = make_float3((ka + FG) * A.x - HG * B.x, (ka + FG) * A.y - HG * B.y, (ka + FG) * A.z - HG * B.z);
+    g[2] = make_float3(-FG * A.x + (HG - kb) * B.x, -FG * A.y + (HG - kb) * B.y, -FG * A.z + (HG - kb) * B.z);
+}
+
+__device__ __forceinline__ float3 ff3_float(ff3 a) { return make_float3(ff_float(a.x), ff_float(a.y), ff_float(a.z)); }
+
+// Pass 2: one thread per edge, triangle or Morse pair.
 //   edge:     spring magnitude k (|R| - L0)/|R| with |R|^2 - L0^2 in
 //             double-float; bending dE/dphi = k_b sin(phi - phi0) with
 //             sin(phi - phi0) = (y cos phi0 - x sin phi0)/(|A||B|), where for the
-//             chain k-i-j-l  A = F x G, B = H x G, x = A.B, y = |G| (H.A).
+//             chain k-i-j-l  A = F x G, B = H x G, x = A.B, y = |G| (H.A);
+//             writes the force on each of k, i, j, l (spring on i, j; bending
+//             -dE/dphi grad phi on all four).
 //   triangle: S_t - S0_t from 4(S^2 - S0^2) = da b + a0 db - dc (c + c0),
 //             a = |e1|^2, b = |e2|^2, c = e1.e2 (da, db, dc in double-float);
-//             adds S_t - S0_t and the tetrahedron volume (1/6)(X_a - X_o).(e1 x e2)
-//             to its platelet's FP64 sums.
-//   pair:     Morse magnitude 2 D a (1 - e^{-a d}) e^{-a d}/r, d = r - r0 likewise.
+//             writes per corner dS_t/dX (w = local coefficient k_t (S_t - S0_t)/S0_t)
+//             and n/6 = (e1 x e2)/6 (dV/dX of every corner); adds S_t - S0_t and
+//             the tetrahedron volume (1/6)(X_a - X_o).(e1 x e2) to its platelet's
+//             FP64 sums.
+//   pair:     Morse force on the first node, 2 D a (1 - e^{-a d}) e^{-a d} R/r,
+//             d = r - r0 likewise.
 __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,17 +267,32 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
         const float qs = ff3_sqnorm_minus(dij, {er.x, er.y});
         const float r = sqrtf(er.x + qs);
         const float spring = P.k_spring * (qs / (r + er.z)) / r;
-        float bend = 0.f;
-        if (q.w >= 0 && P.k_b != 0.f) {
-            const ff3 Fv = X.diff(q.z, q.x), G = ff3_neg(dij), H = X.diff(q.w, q.y);
-            const ff3 A = ff3_cross(Fv, G), B = ff3_cross(H, G);
-            const ff x = ff3_dot(A, B);
-            const ff y = ff_mul(ff_sqrt(ff_add({er.x, er.y}, {qs, 0.f})), ff3_dot(H, A));
-            const float4 ph = c.edge_phi0[t];
-            const ff num = ff_sub(ff_mul(y, {ph.x, ph.y}), ff_mul(x, {ph.z, ph.w}));
-            bend = P.k_b * ff_float(num) / sqrtf(x.h * x.h + y.h * y.h);
+        const float3 r3 = ff3_float(dij);
+        const float3 fs = make_float3(spring * r3.x, spring * r3.y, spring * r3.z);
+        float4* out = c.eout + 4 * (size_t)t;
+        if (q.w >= 0) {
+            float dE = 0.f;
+            const ff3 Fv = X.diff(q.z, q.x), H = X.diff(q.w, q.y);
+            if (P.k_b != 0.f) {
+                const ff3 G = ff3_neg(dij);
+                const ff3 A = ff3_cross(Fv, G), B = ff3_cross(H, G);
+                const ff x = ff3_dot(A, B);
+                const ff y = ff_mul(ff_sqrt(ff_add({er.x, er.y}, {qs, 0.f})), ff3_dot(H, A));
+                const float4 ph = c.edge_phi0[t];
+                const ff num = ff_sub(ff_mul(y, {ph.x, ph.y}), ff_mul(x, {ph.z, ph.w}));
+                dE = P.k_b * ff_float(num) / sqrtf(x.h * x.h + y.h * y.h);
+            }
+            float3 g[4];
+            const float3 r1 = ff3_float(Fv), r4 = f3sub(ff3_float(H), make_float3(-r3.x, -r3.y, -r3.z));
+            torsion_grad(r1, r3, r4, g);
+            out[0] = make_float4(-dE * g[0].x, -dE * g[0].y, -dE * g[0].z, 0.f);
+            out[1] = make_float4(fs.x - dE * g[1].x, fs.y - dE * g[1].y, fs.z - dE * g[1].z, 0.f);
+            out[2] = make_float4(-fs.x - dE * g[2].x, -fs.y - dE * g[2].y, -fs.z - dE * g[2].z, 0.f);
+            out[3] = make_float4(-dE * g[3].x, -dE * g[3].y, -dE * g[3].z, 0.f);
+        } else {
+            out[1] = make_float4(fs.x, fs.y, fs.z, 0.f);
+            out[2] = make_float4(-fs.x, -fs.y, -fs.z, 0.f);
         }
-        c.esc[t] = make_float2(spring, bend);
     } else if (t < c.ne + c.nt) {
         const int k = t - c.ne;
         const int a = c.tri[3 * k], b = c.tri[3 * k + 1], cc = c.tri[3 * k + 2];
@@ -299,7 +305,19 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
         const float four = da * (r0.z + db) + r0.x * db - dc * ((r1.x + dc) + r1.x);
         const float S0 = r1.z, dS2 = 0.25f * four;
         const float ds = dS2 / (sqrtf(S0 * S0 + dS2) + S0);
-        c.tsc[k] = P.k_t * ds * r1.w;
+        const float tsc = P.k_t * ds * r1.w;
+        const float3 f1 = ff3_float(e1), f2 = ff3_float(e2);
+        const float3 nn = f3cross(f1, f2);
+        const float inv = 0.5f * rsqrtf(f3dot(nn, nn));
+        const float3 nh = make_float3(nn.x * inv, nn.y * inv, nn.z * inv);  // nhat / 2
+        const float3 ga = f3cross(nh, f3sub(f2, f1));
+        const float3 gb = f3cross(nh, make_float3(-f2.x, -f2.y, -f2.z));
+        const float3 gc = f3cross(nh, f1);
+        float4* out = c.tout + 4 * (size_t)k;
+        out[0] = make_float4(ga.x, ga.y, ga.z, tsc);
+        out[1] = make_float4(gb.x, gb.y, gb.z, tsc);
+        out[2] = make_float4(gc.x, gc.y, gc.z, tsc);
+        out[3] = make_float4(nn.x * (1.0f / 6.0f), nn.y * (1.0f / 6.0f), nn.z * (1.0f / 6.0f), 0.f);
         const ff v6 = ff3_dot(X.diff(a, c.plt_anchor[plt]), ff3_cross(e1, e2));
         dS = (double)ds;
         V = ((double)v6.h + (double)v6.l) * (1.0 / 6.0);
@@ -307,10 +325,13 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
         const int s = t - c.ne - c.nt;
         const int i = c.pair[2 * s], j = c.pair[2 * s + 1];
         const float4 pr = c.pair_rest[s];
-        const float qs = ff3_sqnorm_minus(X.diff(j, i), {pr.x, pr.y});
+        const ff3 d = X.diff(j, i);
+        const float qs = ff3_sqnorm_minus(d, {pr.x, pr.y});
         const float r = sqrtf(pr.x + qs);
         const float ad = P.morse_a * (qs / (r + pr.z));
-        c.msc[s] = 2.0f * P.morse_D * P.morse_a * (-expm1f(-ad)) * expf(-ad) / r;
+        const float sc = 2.0f * P.morse_D * P.morse_a * (-expm1f(-ad)) * expf(-ad) / r;
+        const float3 R = ff3_float(d);
+        c.pout[s] = make_float4(sc * R.x, sc * R.y, sc * R.z, 0.f);
     }
     // per-platelet sums; triangles of a platelet are contiguous
     const int p0 = __shfl_sync(0xffffffffu, plt, 0);
@@ -331,88 +352,67 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
     }
 }
 
-// Pass 3: one thread per node gathers its terms: the precise scalars of pass
-// 2 times FP32 directions.  No atomics, fixed order.
+// Pass 3: one thread per node sums its element contributions and applies the
+// per-platelet global area and volume coefficients and the wall repulsion.
 __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx c)
 {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= c.n) return;
     const int n = c.n;
-    const Split X{c.xh, c.xl, n};
     const mem_params P = c.p;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-
-    // Eq. 3 springs: F_i = k (|R| - L0) R/|R|, R = X_j - X_i
-    for (int s = c.spr_off[v]; s < c.spr_off[v + 1]; ++s) {
-        const int2 e = c.spr[s];
-        const float sc = c.esc[e.y].x;
-        const float3 R = X.rel(e.x, v);
-        fx += sc * R.x;
-        fy += sc * R.y;
-        fz += sc * R.z;
+    {
+        // batches of four independent loads keep several requests in flight
+        int s = c.esl_off[v];
+        const int e = c.esl_off[v + 1];
+        for (; s + 4 <= e; s += 4) {
+            const int4 k = make_int4(c.esl[s], c.esl[s + 1], c.esl[s + 2], c.esl[s + 3]);
+            const float4 f0 = c.eout[k.x], f1 = c.eout[k.y], f2 = c.eout[k.z], f3 = c.eout[k.w];
+            fx += (f0.x + f1.x) + (f2.x + f3.x);
+            fy += (f0.y + f1.y) + (f2.y + f3.y);
+            fz += (f0.z + f1.z) + (f2.z + f3.z);
+        }
+        for (; s < e; ++s) {
+            const float4 f = c.eout[c.esl[s]];
+            fx += f.x;
+            fy += f.y;
+            fz += f.z;
+        }
     }
-
-    // Eq. 4-5: dS_t/dX_i = (1/2) nhat x (X_b - X_a) for the outward triangle
-    // (i, a, b); dV/dX_i = (1/6) sum (X_a - X_i) x (X_b - X_i) over the fan.
+    // Eq. 4-5: F -= (k_t (S_t - S0_t)/S0_t + k_s (S - S0)/S0) dS_t/dX + k_v (V - V0)/V0 dV/dX
     const int plt = c.node_plt[v];
     const double* pr = c.plt_rest + 4 * plt;  // S0, V0, 1/S0, 1/V0
     const float cSg = (float)((double)P.k_s * c.acc[2 * plt] * pr[2]);
     const float cV = (float)((double)P.k_v * (c.acc[2 * plt + 1] - pr[1]) * pr[3]);
-    for (int s = c.tri_off[v]; s < c.tri_off[v + 1]; ++s) {
-        const int4 t = c.trl[s];
-        const float3 e1 = X.rel(t.x, v), e2 = X.rel(t.y, v);
-        const float3 nn = f3cross(e1, e2);
-        const float inv = rsqrtf(f3dot(nn, nn));
-        const float3 gS = f3cross(make_float3(nn.x * inv, nn.y * inv, nn.z * inv), f3sub(e2, e1));
-        const float cS = c.tsc[t.z] + cSg;
-        fx -= 0.5f * cS * gS.x + cV * nn.x * (1.0f / 6.0f);
-        fy -= 0.5f * cS * gS.y + cV * nn.y * (1.0f / 6.0f);
-        fz -= 0.5f * cS * gS.z + cV * nn.z * (1.0f / 6.0f);
-    }
-
-    // bending: F -= dE/dphi grad(phi) for this node's role in the chain
-    // k-i-j-l (Blondel and Karplus 1996 gradient of the torsion angle)
-    if (P.k_b != 0.f) {
-        for (int s = c.dih_off[v]; s < c.dih_off[v + 1]; ++s) {
-            const int code = c.dih[s];
-            const int e = code >> 2, role = code & 3;
-            const int4 q = c.edge[e];
-            const float3 r1 = X.rel(q.z, v), r2 = X.rel(q.x, v), r3 = X.rel(q.y, v), r4 = X.rel(q.w, v);
-            const float3 Fv = f3sub(r1, r2), G = f3sub(r2, r3), H = f3sub(r4, r3);
-            const float3 A = f3cross(Fv, G), B = f3cross(H, G);
-            const float A2 = f3dot(A, A), B2 = f3dot(B, B), gn = sqrtf(f3dot(G, G));
-            float ca = 0.f, cb = 0.f;  // grad = ca A + cb B
-            if (role == 0) {
-                ca = -gn / A2;
-            } else if (role == 3) {
-                cb = gn / B2;
-            } else {
-                const float FG = f3dot(Fv, G) / (A2 * gn), HG = f3dot(H, G) / (B2 * gn);
-                if (role == 1) {
-                    ca = gn / A2 + FG;
-                    cb = -HG;
-                } else {
-                    ca = -FG;
-                    cb = -gn / B2 + HG;
-                }
-            }
-            const float dE = c.esc[e].y;
-            fx -= dE * (ca * A.x + cb * B.x);
-            fy -= dE * (ca * A.y + cb * B.y);
-            fz -= dE * (ca * A.z + cb * B.z);
+    {
+        int s = c.tcl_off[v];
+        const int e = c.tcl_off[v + 1];
+        for (; s + 2 <= e; s += 2) {
+            const int k0 = c.tcl[s], k1 = c.tcl[s + 1];
+            const float4 g0 = c.tout[k0], n0 = c.tout[k0 | 3], g1 = c.tout[k1], n1 = c.tout[k1 | 3];
+            const float c0 = g0.w + cSg, c1 = g1.w + cSg;
+            fx -= (c0 * g0.x + cV * n0.x) + (c1 * g1.x + cV * n1.x);
+            fy -= (c0 * g0.y + cV * n0.y) + (c1 * g1.y + cV * n1.y);
+            fz -= (c0 * g0.z + cV * n0.z) + (c1 * g1.z + cV * n1.z);
+        }
+        for (; s < e; ++s) {
+            const int code = c.tcl[s];
+            const float4 g = c.tout[code];
+            const float4 n6 = c.tout[code | 3];
+            const float cS = g.w + cSg;
+            fx -= cS * g.x + cV * n6.x;
+            fy -= cS * g.y + cV * n6.y;
+            fz -= cS * g.z + cV * n6.z;
         }
     }
-
-    // Morse pairs: F_i = (dU/dr)/r R, R = X_j - X_i
-    for (int s = c.mor_off[v]; s < c.mor_off[v + 1]; ++s) {
-        const int2 pr2 = c.mor[s];
-        const float sc = c.msc[pr2.y];
-        const float3 R = X.rel(pr2.x, v);
-        fx += sc * R.x;
-        fy += sc * R.y;
-        fz += sc * R.z;
+    for (int s = c.psl_off[v]; s < c.psl_off[v + 1]; ++s) {
+        const int code = c.psl[s];
+        const float4 f = c.pout[code >> 1];
+        const float sg = (code & 1) ? -1.f : 1.f;
+        fx += sg * f.x;
+        fy += sg * f.y;
+        fz += sg * f.z;
     }
-
     // wall repulsion on surface nodes (Section 3.4.1)
     if (c.is_mem[v] && P.rep_F0 != 0.f) {
         const float eps = fmaxf((c.xh[2 * n + v] - P.z_wall) + c.xl[2 * n + v], P.rep_eps_min);
@@ -460,8 +460,8 @@ extern "C" int membrane_query_workspace(int n_nodes, int n_tri, const int* tri, 
     std::string err;
     int rc = build_topology(n_nodes, n_tri, tri, 0, nullptr, T, err);
     if (rc) return set_error(rc, "membrane_query_workspace: " + err);
-    const Layout L = make_layout(n_nodes, n_tri, (int)T.edge.size(), n_pairs, n_plt, T.spr.size(),
-                                 T.trl.size(), T.dih.size(), 2 * (size_t)n_pairs);
+    const Layout L = make_layout(n_nodes, n_tri, (int)T.edge.size(), n_pairs, n_plt, T.esl.size(), T.tcl.size(),
+                                 2 * (size_t)n_pairs);
     *bytes = L.total;
     return PFSI_OK;
 }
@@ -484,7 +484,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     int rc = build_topology(n, nt, tri, np, pairs, T, err);
     if (rc) return set_error(rc, "membrane_create: " + err);
     const int ne = (int)T.edge.size();
-    const Layout L = make_layout(n, nt, ne, np, nplt, T.spr.size(), T.trl.size(), T.dih.size(), T.mor.size());
+    const Layout L = make_layout(n, nt, ne, np, nplt, T.esl.size(), T.tcl.size(), T.psl.size());
     if (ws_bytes < L.total) return set_error(PFSI_ERR_ARG, "membrane_create: workspace too small");
     for (int t = 0; t < nt; ++t)
         for (int r = 1; r < 3; ++r)
@@ -590,14 +590,12 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_EDGE_PHI0, edge_phi0.data(), sizeof(float4) * ne);
     if (!rc) rc = up(S_PAIR, pairs, sizeof(int) * 2 * (size_t)np);
     if (!rc) rc = up(S_PAIR_REST, pair_rest.data(), sizeof(float4) * np);
-    if (!rc) rc = up(S_SPR_OFF, T.spr_off.data(), sizeof(int) * (n + 1));
-    if (!rc) rc = up(S_SPR, T.spr.data(), sizeof(int2) * T.spr.size());
-    if (!rc) rc = up(S_TRI_OFF, T.tri_off.data(), sizeof(int) * (n + 1));
-    if (!rc) rc = up(S_TRL, T.trl.data(), sizeof(int4) * T.trl.size());
-    if (!rc) rc = up(S_DIH_OFF, T.dih_off.data(), sizeof(int) * (n + 1));
-    if (!rc) rc = up(S_DIH, T.dih.data(), sizeof(int) * T.dih.size());
-    if (!rc) rc = up(S_MOR_OFF, T.mor_off.data(), sizeof(int) * (n + 1));
-    if (!rc) rc = up(S_MOR, T.mor.data(), sizeof(int2) * T.mor.size());
+    if (!rc) rc = up(S_ESL_OFF, T.esl_off.data(), sizeof(int) * (n + 1));
+    if (!rc) rc = up(S_ESL, T.esl.data(), sizeof(int) * T.esl.size());
+    if (!rc) rc = up(S_TCL_OFF, T.tcl_off.data(), sizeof(int) * (n + 1));
+    if (!rc) rc = up(S_TCL, T.tcl.data(), sizeof(int) * T.tcl.size());
+    if (!rc) rc = up(S_PSL_OFF, T.psl_off.data(), sizeof(int) * (n + 1));
+    if (!rc) rc = up(S_PSL, T.psl.data(), sizeof(int) * T.psl.size());
     if (!rc) rc = up(S_NODE_PLT, node_plt, sizeof(int) * n);
     if (!rc) rc = up(S_IS_MEM, mem_v.data(), n);
     if (!rc) rc = up(S_PLT_REST, plt_rest.data(), sizeof(double) * plt_rest.size());
@@ -620,14 +618,12 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->edge_phi0 = reinterpret_cast<const float4*>(at(S_EDGE_PHI0));
     c->pair = reinterpret_cast<const int*>(at(S_PAIR));
     c->pair_rest = reinterpret_cast<const float4*>(at(S_PAIR_REST));
-    c->spr_off = reinterpret_cast<const int*>(at(S_SPR_OFF));
-    c->spr = reinterpret_cast<const int2*>(at(S_SPR));
-    c->tri_off = reinterpret_cast<const int*>(at(S_TRI_OFF));
-    c->trl = reinterpret_cast<const int4*>(at(S_TRL));
-    c->dih_off = reinterpret_cast<const int*>(at(S_DIH_OFF));
-    c->dih = reinterpret_cast<const int*>(at(S_DIH));
-    c->mor_off = reinterpret_cast<const int*>(at(S_MOR_OFF));
-    c->mor = reinterpret_cast<const int2*>(at(S_MOR));
+    c->esl_off = reinterpret_cast<const int*>(at(S_ESL_OFF));
+    c->esl = reinterpret_cast<const int*>(at(S_ESL));
+    c->tcl_off = reinterpret_cast<const int*>(at(S_TCL_OFF));
+    c->tcl = reinterpret_cast<const int*>(at(S_TCL));
+    c->psl_off = reinterpret_cast<const int*>(at(S_PSL_OFF));
+    c->psl = reinterpret_cast<const int*>(at(S_PSL));
     c->node_plt = reinterpret_cast<const int*>(at(S_NODE_PLT));
     c->is_mem = reinterpret_cast<const uint8_t*>(at(S_IS_MEM));
     c->plt_rest = reinterpret_cast<const double*>(at(S_PLT_REST));
@@ -635,9 +631,9 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->acc = reinterpret_cast<double*>(at(S_ACC));
     c->xh = reinterpret_cast<float*>(at(S_XH));
     c->xl = reinterpret_cast<float*>(at(S_XL));
-    c->esc = reinterpret_cast<float2*>(at(S_ESC));
-    c->tsc = reinterpret_cast<float*>(at(S_TSC));
-    c->msc = reinterpret_cast<float*>(at(S_MSC));
+    c->eout = reinterpret_cast<float4*>(at(S_EOUT));
+    c->tout = reinterpret_cast<float4*>(at(S_TOUT));
+    c->pout = reinterpret_cast<float4*>(at(S_POUT));
     *out = c;
     return PFSI_OK;
 }

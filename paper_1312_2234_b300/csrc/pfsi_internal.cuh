@@ -103,14 +103,12 @@ struct MemCtx {
     const float4* edge_phi0;   // [ne] (cos phi0 h,l, sin phi0 h,l)
     const int* pair;           // [2*np]
     const float4* pair_rest;   // [np] (r0^2 h, r0^2 l, r0, -)
-    const int* spr_off;    // [n+1] node -> (neighbour, edge)
-    const int2* spr;
-    const int* tri_off;    // [n+1] node -> (a, b, triangle) with (node, a, b) outward
-    const int4* trl;
-    const int* dih_off;    // [n+1] node -> 4*edge + role (role 0..3 = k, i, j, l)
-    const int* dih;
-    const int* mor_off;    // [n+1] node -> (partner, pair)
-    const int2* mor;
+    const int* esl_off;    // [n+1] node -> 4*edge + slot (chain vertex k, i, j, l)
+    const int* esl;
+    const int* tcl_off;    // [n+1] node -> 4*triangle + corner
+    const int* tcl;
+    const int* psl_off;    // [n+1] node -> 2*pair + side
+    const int* psl;
     const int* node_plt;   // [n]
     const uint8_t* is_mem; // [n]
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
@@ -119,9 +117,9 @@ struct MemCtx {
     double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
     float* xh;             // [3n] positions, high floats
     float* xl;             // [3n] positions, low floats
-    float2* esc;           // [ne] spring magnitude, bending dE/dphi
-    float* tsc;            // [nt] local-area coefficient k_t (S_t - S0_t)/S0_t
-    float* msc;            // [np] Morse magnitude
+    float4* eout;          // [4*ne] force on chain vertex k, i, j, l of each edge
+    float4* tout;          // [4*nt] dS_t/dX per corner (w: k_t (S_t - S0_t)/S0_t), n/6
+    float4* pout;          // [np] Morse force on the first node of each pair
 };
 
 struct BondCtx {
