@@ -7,20 +7,22 @@
 // (cells with k outside [0, nz) are skipped), so spreading and interpolation
 // stay adjoint.
 //
-// Blocking: a block of 512 threads takes a chunk of 256 consecutive nodes
-// (consecutive nodes of a platelet mesh lie close together).  Each thread of
+// Blocking: a block of 512 threads takes a chunk of up to 256 consecutive
+// nodes (consecutive nodes of a platelet mesh lie close together; the coupled
+// step passes chunks that never straddle two platelets, the public calls use
+// fixed chunks of 256).  Each thread of
 // the first half stages one node (support origin, weights, force); then each
 // warp walks its share of the chunk one node at a time with lane l on support
 // cell (a, b, c) = (l & 3, (l >> 2) & 3, (l >> 4) + {0, 2}), so one
 // instruction touches 32 distinct cells.  When the bounding box of the
-// chunk's supports fits the shared tile (three float planes, strides padded
-// so that those 32 cells fall in 32 different banks):
+// chunk's supports fits the shared tile (three float planes of 4096 cells):
 //   spreading  accumulates in the tile with shared atomics, then adds every
 //              nonzero tile cell to the float4 force field with one vector
 //              reduction (red.global.add.v4.f32): ~4 global reductions per
 //              node of a platelet instead of 64;
 //   interp     loads the box's velocity into the tile once; each node's 64
-//              weighted values are summed across the warp with shuffles.
+//              weighted values are summed across the warp with shuffles and
+//              the staging threads write U (and advance X) afterwards.
 // Otherwise (e.g. a chunk that straddles two platelets) the block works on the
 // global arrays directly, with the same lane-per-cell mapping.  Both kernels
 // take the same decision for the same positions and flag / clear the same
@@ -72,7 +74,7 @@ __device__ __forceinline__ void stage_node(Stage& st, int j, double x, double y,
 struct Box {
     int x0, y0, z0;    // unwrapped origin; z0 clipped to the walls
     int ex, ey, ez;    // extents (ez after clipping, may be <= 0)
-    int sx, sy;        // padded x stride and y extent of the tile
+    int sx, sy;        // x stride and y extent of the tile
     bool tiled;
 };
 
@@ -109,27 +111,32 @@ __device__ Box block_box(const Stage& st, int nodes, int nz)
         b.ex = r[3] + 4 - r[0];
         b.ey = r[4] + 4 - r[1];
         b.ez = z1 - z0 + 1;
-        // strides: sx = 4 (mod 16) and sx * sy = 16 (mod 32) put the 32 cells
-        // of one node's half-support in 32 different banks
-        b.sx = ((b.ex + 11) / 16) * 16 + 4;
-        b.sy = ((b.ey + 3) / 8) * 8 + 4;
-        if (b.ey <= 4) b.sy = 4;
-        b.tiled = b.ez > 0 && b.ex <= 1024 && b.ey <= 1024 &&
-                  (long long)b.sx * b.sy * b.ez * 3 <= kTileFloats;
+        b.sx = b.ex;
+        b.sy = b.ey;
+        b.tiled = b.ez > 0 && b.ex <= 4096 && b.ey <= 4096 && (long long)b.ex * b.ey * b.ez * 3 <= kTileFloats;
         box = b;
     }
     __syncthreads();
     return box;
 }
 
+// chunk of the block: from the table (start, count) or the fixed 256-node split
+__device__ __forceinline__ int2 block_chunk(const int2* __restrict__ chunks, int M)
+{
+    if (chunks) return chunks[blockIdx.x];
+    const int m0 = blockIdx.x * kChunk;
+    return make_int2(m0, min(kChunk, M - m0));
+}
+
 __global__ void __launch_bounds__(kThreads) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
-                                                        int M, float4* __restrict__ g,
-                                                        uint32_t* __restrict__ flags, int nx, int ny, int nz)
+                                                        int M, const int2* __restrict__ chunks,
+                                                        float4* __restrict__ g, uint32_t* __restrict__ flags,
+                                                        int nx, int ny, int nz)
 {
     extern __shared__ float tile[];
     __shared__ Stage st;
-    const int m0 = blockIdx.x * kChunk;
-    const int nodes = min(kChunk, M - m0);
+    const int2 ch = block_chunk(chunks, M);
+    const int m0 = ch.x, nodes = ch.y;
     if (threadIdx.x < nodes) {
         const int m = m0 + threadIdx.x;
         stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
@@ -187,14 +194,16 @@ __global__ void __launch_bounds__(kThreads) k_ib_spread(const double* __restrict
 }
 
 __global__ void __launch_bounds__(kThreads) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
+                                                        const int2* __restrict__ chunks,
                                                         const float4* __restrict__ v,
                                                         uint32_t* __restrict__ flags, int nx, int ny, int nz,
                                                         int advect)
 {
     extern __shared__ float tile[];
     __shared__ Stage st;
-    const int m0 = blockIdx.x * kChunk;
-    const int nodes = min(kChunk, M - m0);
+    __shared__ float su[3][kChunk];
+    const int2 ch = block_chunk(chunks, M);
+    const int m0 = ch.x, nodes = ch.y;
     if (threadIdx.x < nodes) {
         const int m = m0 + threadIdx.x;
         stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
@@ -252,20 +261,25 @@ __global__ void __launch_bounds__(kThreads) k_ib_interp(double* __restrict__ X, 
             uz += __shfl_xor_sync(0xffffffffu, uz, o);
         }
         if (lane == 0) {
-            const int m = m0 + j;
-            U[m] = ux;
-            U[M + m] = uy;
-            U[2 * M + m] = uz;
-            if (advect) {
-                X[m] += (double)ux;
-                X[M + m] += (double)uy;
-                X[2 * M + m] += (double)uz;
-            }
+            su[0][j] = ux;
+            su[1][j] = uy;
+            su[2][j] = uz;
         }
     }
-    if (b.tiled) return;
-    // fallback path: clear the support rows (after every warp has read them)
     __syncthreads();
+    if (threadIdx.x < nodes) {
+        const int j = threadIdx.x, m = m0 + j;
+        const float ux = su[0][j], uy = su[1][j], uz = su[2][j];
+        U[m] = ux;
+        U[M + m] = uy;
+        U[2 * M + m] = uz;
+        if (advect) {
+            X[m] += (double)ux;
+            X[M + m] += (double)uy;
+            X[2 * M + m] += (double)uz;
+        }
+    }
+    // fallback path: clear the support rows (after every warp has read them)
     for (int j = warp; j < nodes; j += kWarps) {
         if (la != 0) continue;
 #pragma unroll
@@ -288,19 +302,22 @@ int ib_prepare()
     return rc;
 }
 
-int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, cudaStream_t s)
+int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, int n_chunks,
+                     cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
-    k_ib_spread<<<(M + kChunk - 1) / kChunk, kThreads, kTileBytes, s>>>(X, F, M, c->g, c->flags, c->p.nx, c->p.ny,
-                                                                         c->p.nz);
+    const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
+    k_ib_spread<<<blocks, kThreads, kTileBytes, s>>>(X, F, M, chunks, c->g, c->flags, c->p.nx, c->p.ny, c->p.nz);
     return check_launch("ib_spread");
 }
 
-int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, cudaStream_t s)
+int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,
+                     cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
-    k_ib_interp<<<(M + kChunk - 1) / kChunk, kThreads, kTileBytes, s>>>(X, U, M, c->v, c->flags, c->p.nx, c->p.ny,
-                                                                         c->p.nz, advect);
+    const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
+    k_ib_interp<<<blocks, kThreads, kTileBytes, s>>>(X, U, M, chunks, c->v, c->flags, c->p.nx, c->p.ny, c->p.nz,
+                                                     advect);
     return check_launch("ib_interp");
 }
 
@@ -312,12 +329,12 @@ extern "C" int ib_spread(lb_ctx* c, const double* X, const float* F, int M, void
 {
     if (!c || M < 0 || (M > 0 && (!X || !F))) return set_error(PFSI_ERR_ARG, "ib_spread: bad argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "ib_spread: misaligned arrays");
-    return launch_ib_spread(c, X, F, M, as_stream(stream));
+    return launch_ib_spread(c, X, F, M, nullptr, 0, as_stream(stream));
 }
 
 extern "C" int ib_interp(lb_ctx* c, double* X, float* U, int M, int advect, void* stream)
 {
     if (!c || M < 0 || (M > 0 && (!X || !U))) return set_error(PFSI_ERR_ARG, "ib_interp: bad argument");
     if (!aligned(X, 8) || !aligned(U, 4)) return set_error(PFSI_ERR_ARG, "ib_interp: misaligned arrays");
-    return launch_ib_interp(c, X, U, M, advect, as_stream(stream));
+    return launch_ib_interp(c, X, U, M, advect, nullptr, 0, as_stream(stream));
 }

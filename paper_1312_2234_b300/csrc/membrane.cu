@@ -138,8 +138,9 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
 enum Slice {
     S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
-    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_COUNT
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_COUNT
 };
+constexpr int kIbChunk = 256;  // nodes per block of the IB kernels
 struct Layout {
     size_t off[S_COUNT];
     size_t total;
@@ -151,7 +152,7 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
     const size_t bytes[S_COUNT] = {
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
         4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 16 * Q, 12 * N, 12 * N,
-        64 * E, 64 * T, 16 * P};
+        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q)};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -575,6 +576,20 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
         plt_rest[4 * q + 3] = V0[q] > 0.0 ? 1.0 / V0[q] : 0.0;
     }
     std::vector<uint8_t> mem_v(is_membrane, is_membrane + n);
+    // IB chunk table: runs of one platelet, at most kIbChunk nodes each
+    std::vector<int2> chunks;
+    for (int v = 0; v < n;) {
+        int e = v + 1;
+        while (e < n && node_plt[e] == node_plt[v] && e - v < kIbChunk) ++e;
+        chunks.push_back(make_int2(v, e - v));
+        v = e;
+    }
+    {
+        int runs = 1;
+        for (int v = 1; v < n; ++v) runs += node_plt[v] != node_plt[v - 1];
+        if (runs != nplt)
+            return set_error(PFSI_ERR_ARG, "membrane_create: the nodes of each platelet must be contiguous");
+    }
 
     char* base = static_cast<char*>(ws);
     auto up = [&](int slice, const void* src, size_t bytes) -> int {
@@ -600,6 +615,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_IS_MEM, mem_v.data(), n);
     if (!rc) rc = up(S_PLT_REST, plt_rest.data(), sizeof(double) * plt_rest.size());
     if (!rc) rc = up(S_PLT_ANCHOR, anchor.data(), sizeof(int) * nplt);
+    if (!rc) rc = up(S_CHUNKS, chunks.data(), sizeof(int2) * chunks.size());
     if (rc) return rc;
 
     mem_ctx* c = new mem_ctx();
@@ -628,6 +644,8 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->is_mem = reinterpret_cast<const uint8_t*>(at(S_IS_MEM));
     c->plt_rest = reinterpret_cast<const double*>(at(S_PLT_REST));
     c->plt_anchor = reinterpret_cast<const int*>(at(S_PLT_ANCHOR));
+    c->chunks = reinterpret_cast<const int2*>(at(S_CHUNKS));
+    c->n_chunks = (int)chunks.size();
     c->acc = reinterpret_cast<double*>(at(S_ACC));
     c->xh = reinterpret_cast<float*>(at(S_XH));
     c->xl = reinterpret_cast<float*>(at(S_XL));

@@ -112,6 +112,8 @@ struct MemCtx {
     const int* node_plt;   // [n]
     const uint8_t* is_mem; // [n]
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
+    const int2* chunks;    // [n_chunks] (first node, count <= 256), runs of one platelet
+    int n_chunks;
     const int* plt_anchor; // [nplt]
     // scratch, rewritten by every call
     double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
@@ -143,8 +145,13 @@ int ib_prepare();
 
 // Launchers used by sim.cu (defined next to their kernels).
 int launch_lb_step(LbCtx* c, cudaStream_t s);
-int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, cudaStream_t s);
-int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, cudaStream_t s);
+// chunks: optional device table of (first node, count <= 256) per block, used
+// by the coupled step so that no block straddles two platelets; null = fixed
+// chunks of 256 consecutive nodes.
+int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, int n_chunks,
+                     cudaStream_t s);
+int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,
+                     cudaStream_t s);
 int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s);
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
 // step_dev: device step counter (advanced by one after the update) or null

@@ -30,9 +30,9 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
 {
     int rc = launch_membrane_forces(c->mem, c->X, c->F, s);
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
-    if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, s);
+    if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc) rc = launch_lb_step(c->lb, s);
-    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, s);
+    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
     return rc;
 }

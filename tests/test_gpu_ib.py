@@ -44,17 +44,15 @@ def support_rows(X, ny, nz):
 
 def expected_rows(X, ny, nz, chunk=256, cap=4096):
     """Rows the spreading kernel flags: per chunk of 256 nodes, every row of the
-    supports' bounding box when the box, with its padded strides, fits the
-    4096-cell tile; else the support rows."""
+    supports' bounding box when the box fits the 4096-cell tile, else the
+    support rows."""
     rows = set()
     for s0 in range(0, X.shape[1], chunk):
         Xc = X[:, s0:s0 + chunk]
         b = np.floor(Xc).astype(np.int64) - 1
         z0, z1 = max(b[2].min(), 0), min(b[2].max() + 3, nz - 1)
         ex, ey, ez = b[0].max() + 4 - b[0].min(), b[1].max() + 4 - b[1].min(), z1 - z0 + 1
-        sx = ((ex + 11) // 16) * 16 + 4
-        sy = 4 if ey <= 4 else ((ey + 3) // 8) * 8 + 4
-        if ez > 0 and ex <= 1024 and ey <= 1024 and sx * sy * ez <= cap:
+        if ez > 0 and ex * ey * ez <= cap:
             rows |= {k * ny + j % ny for k in range(z0, z1 + 1) for j in range(b[1].min(), b[1].max() + 4)}
         else:
             rows |= support_rows(Xc, ny, nz)
