@@ -2,32 +2,31 @@
 //
 // Kernel: phi(r) = (1 + cos(pi r / 2)) / 4 (Eq. 36, h = 1).  With r measured
 // from the cell below-left of the node, the four offsets of each axis are
-// -1 - t, -t, 1 - t, 2 - t (t in [0,1)), all inside |r| <= 2, so the weights
-// need no branch.  The support wraps in x and y and is cut at the walls
-// (cells with k outside [0, nz) are skipped), so spreading and interpolation
-// stay adjoint.
+// -1 - t, -t, 1 - t, 2 - t (t in [0,1)), all inside |r| <= 2.  With
+// theta = pi t / 2 the four cosines are -sin, cos, sin, -cos of theta, so
+// one sincospi per axis gives the weights
+//   (1 - sin)/4, (1 + cos)/4, (1 + sin)/4, (1 - cos)/4.
+// The support wraps in x and y and is cut at the walls (cells with k outside
+// [0, nz) are skipped), so spreading and interpolation stay adjoint.
 //
-// Blocking: a block of 512 threads takes a chunk of up to 256 consecutive
-// nodes (consecutive nodes of a platelet mesh lie close together; the coupled
-// step passes chunks that never straddle two platelets, the public calls use
-// fixed chunks of 256).  Each thread of
-// the first half stages one node (support origin, weights, force); then each
-// warp walks its share of the chunk one node at a time with lane l on support
-// cell (a, b, c) = (l & 3, (l >> 2) & 3, (l >> 4) + {0, 2}), so one
-// instruction touches 32 distinct cells.  When the bounding box of the
-// chunk's supports fits the shared tile (three float planes of 4096 cells):
-//   spreading  accumulates in the tile with shared atomics, then adds every
+// Blocking: a block of 128 threads takes a chunk of up to 128 consecutive
+// nodes, one thread per node (consecutive nodes of a platelet mesh lie close
+// together; the coupled step passes chunks that never straddle two
+// platelets, the public calls use fixed chunks of 128).  When the bounding
+// box of the chunk's supports fits the shared tile (4096 cells):
+//   spreading  adds F_m * w into the tile (three float planes) with shared
+//              atomics, each lane starting its 16 support rows at a
+//              lane-dependent row so that neighbouring nodes of a warp seldom
+//              hit one address in the same instruction; then adds every
 //              nonzero tile cell to the float4 force field with one vector
-//              reduction (red.global.add.v4.f32): ~4 global reductions per
-//              node of a platelet instead of 64;
-//   interp     loads the box's velocity into the tile once; each node's 64
-//              weighted values are summed across the warp with shuffles and
-//              the staging threads write U (and advance X) afterwards.
-// Otherwise (e.g. a chunk that straddles two platelets) the block works on the
-// global arrays directly, with the same lane-per-cell mapping.  Both kernels
-// take the same decision for the same positions and flag / clear the same
-// rows: every row of the box (a superset of the support rows), so the lattice
-// step writes the velocity wherever interpolation will read it.
+//              reduction (red.global.add.v4.f32): ~6 global reductions per
+//              node instead of 64;
+//   interp     loads the box's velocity into the tile (float4 cells) once
+//              and gathers every node's 64 weighted values from it.
+// Otherwise the block works on the global arrays directly.  Both kernels take
+// the same decision for the same positions and flag / clear the same rows:
+// every row of the box (a superset of the support rows), so the lattice step
+// writes the velocity wherever interpolation will read it.
 #include <climits>
 
 #include "pfsi_internal.cuh"
@@ -36,13 +35,10 @@ namespace pfsi {
 
 namespace {
 
-constexpr int kChunk = 256;                 // nodes per block
-constexpr int kThreads = 512;               // threads per block
-constexpr int kWarps = kThreads / 32;
-constexpr int kTileFloats = 3 * 4096;       // three planes of up to 4096 cells
-constexpr size_t kTileBytes = kTileFloats * sizeof(float);
-
-__device__ __forceinline__ float phi4(float r) { return 0.25f * (1.0f + cospif(0.5f * r)); }
+constexpr int kChunk = kIbChunk;            // nodes (= threads) per block
+constexpr int kWarps = kChunk / 32;
+constexpr int kTileCells = 4096;
+constexpr size_t kTileBytes = kTileCells * sizeof(float4);
 
 __device__ __forceinline__ int wrap(int i, int n)
 {
@@ -50,44 +46,42 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-struct Stage {
-    int bx[kChunk], by[kChunk], bz[kChunk];
-    float w[12][kChunk];  // wx[0..3], wy[0..3], wz[0..3]
-    float f[3][kChunk];
+struct Node {
+    int bx, by, bz;                 // unwrapped cell of support offset 0 on each axis
+    float wx[4], wy[4], wz[4];
 };
 
-__device__ __forceinline__ void stage_node(Stage& st, int j, double x, double y, double z)
+__device__ __forceinline__ void weights(double x, int& b, float* w)
 {
-    const double fx = floor(x), fy = floor(y), fz = floor(z);
-    const float tx = (float)(x - fx), ty = (float)(y - fy), tz = (float)(z - fz);
-    st.bx[j] = (int)fx - 1;
-    st.by[j] = (int)fy - 1;
-    st.bz[j] = (int)fz - 1;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        st.w[a][j] = phi4((float)(a - 1) - tx);
-        st.w[4 + a][j] = phi4((float)(a - 1) - ty);
-        st.w[8 + a][j] = phi4((float)(a - 1) - tz);
-    }
+    const double f = floor(x);
+    b = (int)f - 1;
+    float s, c;
+    sincospif(0.5f * (float)(x - f), &s, &c);
+    w[0] = 0.25f * (1.0f - s);
+    w[1] = 0.25f * (1.0f + c);
+    w[2] = 0.25f * (1.0f + s);
+    w[3] = 0.25f * (1.0f - c);
+}
+
+__device__ __forceinline__ void node_support(double x, double y, double z, Node& s)
+{
+    weights(x, s.bx, s.wx);
+    weights(y, s.by, s.wy);
+    weights(z, s.bz, s.wz);
 }
 
 struct Box {
     int x0, y0, z0;    // unwrapped origin; z0 clipped to the walls
     int ex, ey, ez;    // extents (ez after clipping, may be <= 0)
-    int sx, sy;        // x stride and y extent of the tile
     bool tiled;
 };
 
-// Bounding box of the staged supports (nodes [0, nodes)); also a barrier for
-// the staging writes.
-__device__ Box block_box(const Stage& st, int nodes, int nz)
+__device__ Box block_box(const Node& s, bool on, int nz)
 {
     __shared__ int red[6][kWarps];
     __shared__ Box box;
-    const int j = threadIdx.x;
-    const bool on = j < nodes;
-    int v[6] = {on ? st.bx[j] : INT_MAX, on ? st.by[j] : INT_MAX, on ? st.bz[j] : INT_MAX,
-                on ? st.bx[j] : INT_MIN, on ? st.by[j] : INT_MIN, on ? st.bz[j] : INT_MIN};
+    int v[6] = {on ? s.bx : INT_MAX, on ? s.by : INT_MAX, on ? s.bz : INT_MAX,
+                on ? s.bx : INT_MIN, on ? s.by : INT_MIN, on ? s.bz : INT_MIN};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -111,16 +105,14 @@ __device__ Box block_box(const Stage& st, int nodes, int nz)
         b.ex = r[3] + 4 - r[0];
         b.ey = r[4] + 4 - r[1];
         b.ez = z1 - z0 + 1;
-        b.sx = b.ex;
-        b.sy = b.ey;
-        b.tiled = b.ez > 0 && b.ex <= 4096 && b.ey <= 4096 && (long long)b.ex * b.ey * b.ez * 3 <= kTileFloats;
+        b.tiled = b.ez > 0 && b.ex <= kTileCells && b.ey <= kTileCells &&
+                  (long long)b.ex * b.ey * b.ez <= kTileCells;
         box = b;
     }
     __syncthreads();
     return box;
 }
 
-// chunk of the block: from the table (start, count) or the fixed 256-node split
 __device__ __forceinline__ int2 block_chunk(const int2* __restrict__ chunks, int M)
 {
     if (chunks) return chunks[blockIdx.x];
@@ -128,165 +120,200 @@ __device__ __forceinline__ int2 block_chunk(const int2* __restrict__ chunks, int
     return make_int2(m0, min(kChunk, M - m0));
 }
 
-__global__ void __launch_bounds__(kThreads) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
-                                                        int M, const int2* __restrict__ chunks,
-                                                        float4* __restrict__ g, uint32_t* __restrict__ flags,
-                                                        int nx, int ny, int nz)
+// Walk the tile rows (bb, c) of the box, one warp per row; calls
+// f(tile row index, global row index, x of lane's first cell) with wrapped
+// global coordinates computed incrementally.
+template <class Fn>
+__device__ __forceinline__ void for_rows(const Box& b, int nx, int ny, Fn f)
+{
+    const int warp = threadIdx.x >> 5;
+    const int y0 = wrap(b.y0, ny);
+    int bb = warp % b.ey, c = warp / b.ey;
+    int gy = y0 + bb;
+    while (gy >= ny) gy -= ny;
+    for (int r = warp; r < b.ey * b.ez; r += kWarps) {
+        f(r, (b.z0 + c) * ny + gy);
+        bb += kWarps;
+        gy += kWarps;
+        while (bb >= b.ey) {
+            bb -= b.ey;
+            gy -= b.ey;
+            ++c;
+        }
+        while (gy >= ny) gy -= ny;
+        while (gy < 0) gy += ny;
+    }
+}
+
+__global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
+                                                      int M, const int2* __restrict__ chunks,
+                                                      float4* __restrict__ g, uint32_t* __restrict__ flags,
+                                                      int nx, int ny, int nz)
 {
     extern __shared__ float tile[];
-    __shared__ Stage st;
+    __shared__ float swy[4][kChunk], swz[4][kChunk];
     const int2 ch = block_chunk(chunks, M);
-    const int m0 = ch.x, nodes = ch.y;
-    if (threadIdx.x < nodes) {
-        const int m = m0 + threadIdx.x;
-        stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
-        st.f[0][threadIdx.x] = F[m];
-        st.f[1][threadIdx.x] = F[M + m];
-        st.f[2][threadIdx.x] = F[2 * M + m];
-    }
-    const Box b = block_box(st, nodes, nz);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
-    const int plane = b.sx * b.sy * b.ez;
-    if (b.tiled) {
-        for (int i = threadIdx.x; i < 3 * plane; i += kThreads) tile[i] = 0.f;
-        __syncthreads();
-    }
-    for (int j = warp; j < nodes; j += kWarps) {
-        const float fx = st.f[0][j], fy = st.f[1][j], fz = st.f[2][j];
-        const float wxy = st.w[la][j] * st.w[4 + lb][j];
-        const int bx = st.bx[j], by = st.by[j], bz = st.bz[j];
+    const int m = ch.x + threadIdx.x;
+    const bool on = (int)threadIdx.x < ch.y;
+    Node s;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (on) {
+        node_support(X[m], X[M + m], X[2 * M + m], s);
+        fx = F[m];
+        fy = F[M + m];
+        fz = F[2 * M + m];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lc + 2 * h;
-            const float w = wxy * st.w[8 + c][j];
-            if (b.tiled) {
-                const int k = bz + c - b.z0;
-                if (k < 0 || k >= b.ez) continue;
-                const int i = (k * b.sy + (by + lb - b.y0)) * b.sx + (bx + la - b.x0);
-                atomicAdd(tile + i, fx * w);
-                atomicAdd(tile + plane + i, fy * w);
-                atomicAdd(tile + 2 * plane + i, fz * w);
-            } else {
-                const int k = bz + c;
-                if (k < 0 || k >= nz) continue;
-                const int row = k * ny + wrap(by + lb, ny);
-                if (la == 0) flags[row] = 1u;
-                atomicAdd(g + (size_t)row * nx + wrap(bx + la, nx), make_float4(fx * w, fy * w, fz * w, 0.0f));
-            }
+        for (int a = 0; a < 4; ++a) {
+            swy[a][threadIdx.x] = s.wy[a];
+            swz[a][threadIdx.x] = s.wz[a];
         }
     }
-    if (!b.tiled) return;
-    __syncthreads();
-    // flush: one warp per tile row
-    const int x0 = wrap(b.x0, nx), y0 = wrap(b.y0, ny);
-    for (int r = warp; r < b.ey * b.ez; r += kWarps) {
-        const int bb = r % b.ey, c = r / b.ey;
-        const int grow = (b.z0 + c) * ny + wrap(y0 + bb, ny);
-        if (lane == 0) flags[grow] = 1u;
-        const int base = (c * b.sy + bb) * b.sx;
-        for (int a = lane; a < b.ex; a += 32) {
-            const float4 val = make_float4(tile[base + a], tile[plane + base + a], tile[2 * plane + base + a], 0.f);
-            if (val.x != 0.f || val.y != 0.f || val.z != 0.f)
-                atomicAdd(g + (size_t)grow * nx + wrap(x0 + a, nx), val);
+    const Box b = block_box(s, on, nz);
+    const int lane = threadIdx.x & 31;
+    if (b.tiled) {
+        const int plane = b.ex * b.ey * b.ez;
+        for (int i = threadIdx.x; i < 3 * plane; i += kChunk) tile[i] = 0.f;
+        __syncthreads();
+        if (on) {
+            const int ox = s.bx - b.x0, oy = s.by - b.y0, oz = s.bz - b.z0;
+            for (int q = 0; q < 16; ++q) {
+                const int rr = (q + lane) & 15;           // lane-rotated support row
+                const int bb = rr & 3, c = rr >> 2;
+                const int k = oz + c;
+                if (k < 0 || k >= b.ez) continue;
+                const float wyz = swy[bb][threadIdx.x] * swz[c][threadIdx.x];
+                float* row = tile + (k * b.ey + oy + bb) * b.ex + ox;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float w = s.wx[a] * wyz;
+                    atomicAdd(row + a, fx * w);
+                    atomicAdd(row + plane + a, fy * w);
+                    atomicAdd(row + 2 * plane + a, fz * w);
+                }
+            }
+        }
+        __syncthreads();
+        const int x0 = wrap(b.x0, nx);
+        for_rows(b, nx, ny, [&](int r, int grow) {
+            if (lane == 0) flags[grow] = 1u;
+            const float* trow = tile + r * b.ex;
+            float4* grow_p = g + (size_t)grow * nx;
+            for (int a = lane; a < b.ex; a += 32) {
+                const float4 val = make_float4(trow[a], trow[plane + a], trow[2 * plane + a], 0.f);
+                if (val.x != 0.f || val.y != 0.f || val.z != 0.f) {
+                    int gx = x0 + a;
+                    while (gx >= nx) gx -= nx;
+                    atomicAdd(grow_p + gx, val);
+                }
+            }
+        });
+        return;
+    }
+    if (!on) return;
+    // fallback: per-node global reductions
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int k = s.bz + c;
+        if (k < 0 || k >= nz) continue;
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+            const int row = k * ny + wrap(s.by + bb, ny);
+            flags[row] = 1u;
+            const float wyz = s.wy[bb] * s.wz[c];
+            float4* base = g + (size_t)row * nx;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float w = s.wx[a] * wyz;
+                atomicAdd(base + wrap(s.bx + a, nx), make_float4(fx * w, fy * w, fz * w, 0.0f));
+            }
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
-                                                        const int2* __restrict__ chunks,
-                                                        const float4* __restrict__ v,
-                                                        uint32_t* __restrict__ flags, int nx, int ny, int nz,
-                                                        int advect)
+__global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
+                                                      const int2* __restrict__ chunks,
+                                                      const float4* __restrict__ v,
+                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz,
+                                                      int advect)
 {
-    extern __shared__ float tile[];
-    __shared__ Stage st;
-    __shared__ float su[3][kChunk];
+    extern __shared__ float4 tile4[];
     const int2 ch = block_chunk(chunks, M);
-    const int m0 = ch.x, nodes = ch.y;
-    if (threadIdx.x < nodes) {
-        const int m = m0 + threadIdx.x;
-        stage_node(st, threadIdx.x, X[m], X[M + m], X[2 * M + m]);
+    const int m = ch.x + threadIdx.x;
+    const bool on = (int)threadIdx.x < ch.y;
+    Node s;
+    double x = 0.0, y = 0.0, z = 0.0;
+    if (on) {
+        x = X[m];
+        y = X[M + m];
+        z = X[2 * M + m];
+        node_support(x, y, z, s);
     }
-    const Box b = block_box(st, nodes, nz);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int la = lane & 3, lb = (lane >> 2) & 3, lc = lane >> 4;
-    const int plane = b.sx * b.sy * b.ez;
+    const Box b = block_box(s, on, nz);
+    const int lane = threadIdx.x & 31;
+    float ux = 0.f, uy = 0.f, uz = 0.f;
     if (b.tiled) {
-        // fill: one warp per tile row; clear the rows' flags
-        const int x0 = wrap(b.x0, nx), y0 = wrap(b.y0, ny);
-        for (int r = warp; r < b.ey * b.ez; r += kWarps) {
-            const int bb = r % b.ey, c = r / b.ey;
-            const int grow = (b.z0 + c) * ny + wrap(y0 + bb, ny);
-            const int base = (c * b.sy + bb) * b.sx;
+        const int x0 = wrap(b.x0, nx);
+        for_rows(b, nx, ny, [&](int r, int grow) {
+            const float4* vrow = v + (size_t)grow * nx;
+            float4* trow = tile4 + r * b.ex;
             for (int a = lane; a < b.ex; a += 32) {
-                const float4 val = v[(size_t)grow * nx + wrap(x0 + a, nx)];
-                tile[base + a] = val.x;
-                tile[plane + base + a] = val.y;
-                tile[2 * plane + base + a] = val.z;
+                int gx = x0 + a;
+                while (gx >= nx) gx -= nx;
+                trow[a] = vrow[gx];
             }
             if (lane == 0) flags[grow] = 0u;
-        }
+        });
         __syncthreads();
-    }
-    for (int j = warp; j < nodes; j += kWarps) {
-        const float wxy = st.w[la][j] * st.w[4 + lb][j];
-        const int bx = st.bx[j], by = st.by[j], bz = st.bz[j];
-        float ux = 0.f, uy = 0.f, uz = 0.f;
+        if (!on) return;
+        const int ox = s.bx - b.x0, oy = s.by - b.y0, oz = s.bz - b.z0;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int c = lc + 2 * h;
-            const float w = wxy * st.w[8 + c][j];
-            if (b.tiled) {
-                const int k = bz + c - b.z0;
-                if (k < 0 || k >= b.ez) continue;
-                const int i = (k * b.sy + (by + lb - b.y0)) * b.sx + (bx + la - b.x0);
-                ux += w * tile[i];
-                uy += w * tile[plane + i];
-                uz += w * tile[2 * plane + i];
-            } else {
-                const int k = bz + c;
-                if (k < 0 || k >= nz) continue;
-                const int row = k * ny + wrap(by + lb, ny);
-                const float4 vv = v[(size_t)row * nx + wrap(bx + la, nx)];
-                ux += w * vv.x;
-                uy += w * vv.y;
-                uz += w * vv.z;
+        for (int c = 0; c < 4; ++c) {
+            const int k = oz + c;
+            if (k < 0 || k >= b.ez) continue;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const float wyz = s.wy[bb] * s.wz[c];
+                const float4* row = tile4 + (k * b.ey + oy + bb) * b.ex + ox;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float w = s.wx[a] * wyz;
+                    const float4 vv = row[a];
+                    ux += w * vv.x;
+                    uy += w * vv.y;
+                    uz += w * vv.z;
+                }
             }
         }
+    } else {
+        if (!on) return;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ux += __shfl_xor_sync(0xffffffffu, ux, o);
-            uy += __shfl_xor_sync(0xffffffffu, uy, o);
-            uz += __shfl_xor_sync(0xffffffffu, uz, o);
-        }
-        if (lane == 0) {
-            su[0][j] = ux;
-            su[1][j] = uy;
-            su[2][j] = uz;
+        for (int c = 0; c < 4; ++c) {
+            const int k = s.bz + c;
+            if (k < 0 || k >= nz) continue;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+                const int row = k * ny + wrap(s.by + bb, ny);
+                const float wyz = s.wy[bb] * s.wz[c];
+                const float4* base = v + (size_t)row * nx;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float w = s.wx[a] * wyz;
+                    const float4 vv = base[wrap(s.bx + a, nx)];
+                    ux += w * vv.x;
+                    uy += w * vv.y;
+                    uz += w * vv.z;
+                }
+                flags[row] = 0u;
+            }
         }
     }
-    __syncthreads();
-    if (threadIdx.x < nodes) {
-        const int j = threadIdx.x, m = m0 + j;
-        const float ux = su[0][j], uy = su[1][j], uz = su[2][j];
-        U[m] = ux;
-        U[M + m] = uy;
-        U[2 * M + m] = uz;
-        if (advect) {
-            X[m] += (double)ux;
-            X[M + m] += (double)uy;
-            X[2 * M + m] += (double)uz;
-        }
-    }
-    // fallback path: clear the support rows (after every warp has read them)
-    for (int j = warp; j < nodes; j += kWarps) {
-        if (la != 0) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = st.bz[j] + lc + 2 * h;
-            if (k >= 0 && k < nz) flags[k * ny + wrap(st.by[j] + lb, ny)] = 0u;
-        }
+    U[m] = ux;
+    U[M + m] = uy;
+    U[2 * M + m] = uz;
+    if (advect) {
+        X[m] = x + (double)ux;
+        X[M + m] = y + (double)uy;
+        X[2 * M + m] = z + (double)uz;
     }
 }
 
@@ -307,7 +334,7 @@ int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_spread<<<blocks, kThreads, kTileBytes, s>>>(X, F, M, chunks, c->g, c->flags, c->p.nx, c->p.ny, c->p.nz);
+    k_ib_spread<<<blocks, kChunk, kTileBytes, s>>>(X, F, M, chunks, c->g, c->flags, c->p.nx, c->p.ny, c->p.nz);
     return check_launch("ib_spread");
 }
 
@@ -316,8 +343,8 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_interp<<<blocks, kThreads, kTileBytes, s>>>(X, U, M, chunks, c->v, c->flags, c->p.nx, c->p.ny, c->p.nz,
-                                                     advect);
+    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, c->v, c->flags, c->p.nx, c->p.ny, c->p.nz,
+                                                   advect);
     return check_launch("ib_interp");
 }
 

@@ -140,7 +140,6 @@ enum Slice {
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
     S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_COUNT
 };
-constexpr int kIbChunk = 256;  // nodes per block of the IB kernels
 struct Layout {
     size_t off[S_COUNT];
     size_t total;

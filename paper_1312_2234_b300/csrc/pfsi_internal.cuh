@@ -112,7 +112,7 @@ struct MemCtx {
     const int* node_plt;   // [n]
     const uint8_t* is_mem; // [n]
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
-    const int2* chunks;    // [n_chunks] (first node, count <= 256), runs of one platelet
+    const int2* chunks;    // [n_chunks] (first node, count <= kIbChunk), runs of one platelet
     int n_chunks;
     const int* plt_anchor; // [nplt]
     // scratch, rewritten by every call
@@ -140,14 +140,18 @@ struct BondCtx {
 };
 constexpr int kMaxCand = 64;
 
+// Nodes per block of the IB kernels (also the largest chunk of the membrane's
+// chunk table).
+constexpr int kIbChunk = 128;
+
 // One-time kernel attributes (large dynamic shared memory) of the IB kernels.
 int ib_prepare();
 
 // Launchers used by sim.cu (defined next to their kernels).
 int launch_lb_step(LbCtx* c, cudaStream_t s);
-// chunks: optional device table of (first node, count <= 256) per block, used
+// chunks: optional device table of (first node, count <= kIbChunk) per block, used
 // by the coupled step so that no block straddles two platelets; null = fixed
-// chunks of 256 consecutive nodes.
+// chunks of kIbChunk consecutive nodes.
 int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, int n_chunks,
                      cudaStream_t s);
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,

@@ -42,8 +42,8 @@ def support_rows(X, ny, nz):
     return rows
 
 
-def expected_rows(X, ny, nz, chunk=256, cap=4096):
-    """Rows the spreading kernel flags: per chunk of 256 nodes, every row of the
+def expected_rows(X, ny, nz, chunk=128, cap=4096):
+    """Rows the spreading kernel flags: per chunk of 128 nodes, every row of the
     supports' bounding box when the box fits the 4096-cell tile, else the
     support rows."""
     rows = set()
