@@ -42,17 +42,17 @@ def support_rows(X, ny, nz):
     return rows
 
 
-def expected_rows(X, ny, nz, chunk=128, cap=4096):
+def expected_rows(X, nx, ny, nz, chunk=128, cap=4096):
     """Rows the spreading kernel flags: per chunk of 128 nodes, every row of the
-    supports' bounding box when the box fits the 4096-cell tile, else the
-    support rows."""
+    supports' bounding box when the box fits the 4096-cell tile and is no
+    wider than the grid, else the support rows."""
     rows = set()
     for s0 in range(0, X.shape[1], chunk):
         Xc = X[:, s0:s0 + chunk]
         b = np.floor(Xc).astype(np.int64) - 1
         z0, z1 = max(b[2].min(), 0), min(b[2].max() + 3, nz - 1)
         ex, ey, ez = b[0].max() + 4 - b[0].min(), b[1].max() + 4 - b[1].min(), z1 - z0 + 1
-        if ez > 0 and ex * ey * ez <= cap:
+        if ez > 0 and ex <= nx and ey <= ny and ex * ey * ez <= cap:
             rows |= {k * ny + j % ny for k in range(z0, z1 + 1) for j in range(b[1].min(), b[1].max() + 4)}
         else:
             rows |= support_rows(Xc, ny, nz)
@@ -86,7 +86,7 @@ def test_spread_parity_and_flags(dims, M):
     assert rel_err(gg[:, :3].T.ravel(), g) < TOL
     assert np.all(gg[:, 3] == 0)
     flags = lat.flags.cpu().numpy()
-    assert set(np.nonzero(flags)[0].tolist()) == expected_rows(X, ny, nz)
+    assert set(np.nonzero(flags)[0].tolist()) == expected_rows(X, nx, ny, nz)
 
 
 @pytest.mark.parametrize("dims,M", [((29, 21, 17), 700), ((128, 64, 64), 33620), ("platelets", 0)])
