@@ -169,6 +169,25 @@ int membrane_forces(mem_ctx* ctx, const double* X, float* F, void* stream);
  * out_host[2*n_plt] = {S_0, V_0, S_1, V_1, ...}.  Synchronises. */
 int membrane_measure(mem_ctx* ctx, const double* X, double* out_host, void* stream);
 
+/* No-allocation variant of membrane_measure.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory (a
+ * host application whose own allocator owns every device buffer, or a loop in
+ * which cudaMalloc is forbidden) and still want the per-platelet area and
+ * volume of a membrane context they have built.  It writes the same
+ * out_host[2*n_plt] = {S_0, V_0, ...} as membrane_measure (FP64 sums of the
+ * triangle areas and tetrahedron volumes) without using the context's
+ * scratch: it accumulates in a library-owned static device array of
+ * PFSI_STATIC_MAX_PLATELETS x 2 doubles (128 KiB), which every GPU that loads
+ * the library holds until the process exits.  It allocates and frees nothing.
+ * Contexts with more than PFSI_STATIC_MAX_PLATELETS platelets are rejected
+ * with PFSI_ERR_ARG.  The first call on a device (with that device current)
+ * looks up the array's device address; make that first call before any stream
+ * capture.  Every call shares the one array and clears it first: calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  Synchronises on `stream`. */
+#define PFSI_STATIC_MAX_PLATELETS 8192
+int membrane_measure_static(mem_ctx* ctx, const double* X, double* out_host, void* stream);
+
 /* ===================================================================== *
  * Stochastic adhesion (DAM), Section 3.2
  * ===================================================================== */

@@ -68,6 +68,7 @@ _SIGS = {
     "membrane_set_params": [P, ctypes.POINTER(mem_params)],
     "membrane_forces": [P, P, P, P],
     "membrane_measure": [P, P, ctypes.POINTER(c_double), P],
+    "membrane_measure_static": [P, P, ctypes.POINTER(c_double), P],
     "bonds_query_workspace": [ctypes.POINTER(bond_params), c_int, ctypes.POINTER(c_size_t)],
     "bonds_create": [ctypes.POINTER(bond_params), c_int, P, P, P, P, P, P, c_size_t, ctypes.POINTER(P)],
     "bonds_destroy": [P],
@@ -208,6 +209,14 @@ def membrane_forces(h, X, F, stream=None):
 def membrane_measure(h, X, n_plt, stream=None):
     out = (c_double * (2 * n_plt))()
     _call("membrane_measure", h, _ptr(X), out, _stream(stream))
+    return np.array(out[:]).reshape(n_plt, 2)
+
+
+def membrane_measure_static(h, X, n_plt, stream=None):
+    """membrane_measure without the context's scratch (library-owned static
+    device array; for callers that cannot allocate device memory)."""
+    out = (c_double * (2 * n_plt))()
+    _call("membrane_measure_static", h, _ptr(X), out, _stream(stream))
     return np.array(out[:]).reshape(n_plt, 2)
 
 
