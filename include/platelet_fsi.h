@@ -256,6 +256,15 @@ int sim_step(sim_ctx* ctx, int nsteps, void* stream);
 /* Index of the next step (first_step + steps taken). */
 int sim_step_index(const sim_ctx* ctx, uint64_t* out);
 
+/* Measurement aid (no paper counterpart): on != 0 records two CUDA events
+ * around the lattice Boltzmann kernel inside the step graph (the graphs are
+ * recaptured), so that each step measures that kernel where it runs, inside
+ * the coupled step.  on = 0 removes them. */
+int sim_time_lb(sim_ctx* ctx, int on);
+/* Milliseconds between those two events in the most recent step.
+ * Synchronises on the second event. */
+int sim_lb_ms(sim_ctx* ctx, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

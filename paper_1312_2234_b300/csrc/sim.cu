@@ -22,6 +22,7 @@ struct SimCtx {
     uint64_t step;
     cudaStream_t cap;
     cudaGraphExec_t exec[2];
+    cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
 };
 
 namespace {
@@ -31,7 +32,11 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     int rc = launch_membrane_forces(c->mem, c->X, c->F, s);
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
+    if (!rc && c->lb_ev[0])
+        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[0], s, cudaEventRecordExternal), "sim: lb timing event");
     if (!rc) rc = launch_lb_step(c->lb, s);
+    if (!rc && c->lb_ev[1])
+        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
     if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
     return rc;
@@ -83,6 +88,7 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->M = M;
     c->step = first_step;
     c->exec[0] = c->exec[1] = nullptr;
+    c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc && bonds) {
         const unsigned long long s = first_step;
@@ -102,6 +108,8 @@ extern "C" int sim_destroy(sim_ctx* c)
     for (int k = 0; k < 2; ++k)
         if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
     if (c->cap) cudaStreamDestroy(c->cap);
+    for (int k = 0; k < 2; ++k)
+        if (c->lb_ev[k]) cudaEventDestroy(c->lb_ev[k]);
     delete c;
     return PFSI_OK;
 }
@@ -122,6 +130,34 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
         c->step += 1;
     }
     return PFSI_OK;
+}
+
+extern "C" int sim_time_lb(sim_ctx* c, int on)
+{
+    if (!c) return set_error(PFSI_ERR_ARG, "sim_time_lb: null context");
+    const bool want = on != 0;
+    if (want == (c->lb_ev[0] != nullptr)) return PFSI_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+        c->exec[k] = nullptr;
+        if (c->lb_ev[k]) cudaEventDestroy(c->lb_ev[k]);
+        c->lb_ev[k] = nullptr;
+    }
+    if (!want) return PFSI_OK;
+    for (int k = 0; k < 2; ++k) {
+        const int rc = check_cuda(cudaEventCreate(&c->lb_ev[k]), "sim_time_lb: event");
+        if (rc) return rc;
+    }
+    return PFSI_OK;
+}
+
+extern "C" int sim_lb_ms(sim_ctx* c, float* ms)
+{
+    if (!c || !ms) return set_error(PFSI_ERR_ARG, "sim_lb_ms: null argument");
+    if (!c->lb_ev[0]) return set_error(PFSI_ERR_ARG, "sim_lb_ms: timing is off (sim_time_lb)");
+    int rc = check_cuda(cudaEventSynchronize(c->lb_ev[1]), "sim_lb_ms: synchronise");
+    if (!rc) rc = check_cuda(cudaEventElapsedTime(ms, c->lb_ev[0], c->lb_ev[1]), "sim_lb_ms: elapsed");
+    return rc;
 }
 
 extern "C" int sim_step_index(const sim_ctx* c, uint64_t* out)

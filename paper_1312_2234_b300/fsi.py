@@ -79,6 +79,8 @@ _SIGS = {
     "sim_destroy": [P],
     "sim_step": [P, c_int, P],
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
+    "sim_time_lb": [P, c_int],
+    "sim_lb_ms": [P, ctypes.POINTER(ctypes.c_float)],
 }
 
 
@@ -268,6 +270,16 @@ def sim_step(h, nsteps=1, stream=None):
 def sim_step_index(h):
     out = c_uint64()
     _call("sim_step_index", h, ctypes.byref(out))
+    return out.value
+
+
+def sim_time_lb(h, on=True):
+    _call("sim_time_lb", h, int(bool(on)))
+
+
+def sim_lb_ms(h):
+    out = ctypes.c_float()
+    _call("sim_lb_ms", h, ctypes.byref(out))
     return out.value
 
 
