@@ -37,6 +37,7 @@ METRIC = "coupled MLUPS + membrane-node updates/s, % HBM roofline, vs plain FP32
 WORKLOAD = ("channel 128x64x64 D3Q19 Couette, shear 1000/s, tau 0.8; 10 platelets x (2562 membrane nodes "
             "+ 800 SCE), 5000 receptor sites each, ligand patch 64x32; plain FP32 (FP64 positions)")
 LB_BYTES_PER_CELL = 152          # 19 float loads + 19 float stores
+LB_BYTES_PER_CELL_MIXED = 108    # 19 16-bit f^neq + one float4 (v, rho - 1), each read and written
 KERNELS_PER_STEP = 10            # split, elements, nodes, bond forces, spread, lb, interp, rupture, propose, resolve
 
 
@@ -224,6 +225,14 @@ def run_native(args, rank, ws):
     total_s = reduce_max(sum(step_ms) / 1e3, ws)
     ms_per_step = 1e3 * total_s / args.steps
 
+    # the same workload on mixed-precision lattice storage, timed the same
+    # way, and its deviation from this FP32 run after the same number of
+    # steps from the same initial state
+    snap = {"X": sim.X.cpu().numpy(), "U": sim.U.cpu().numpy(),
+            "bound": sim.bonds.bound.cpu().numpy() if sim.bonds else None}
+    mixed = {} if args.no_mixed else {s: run_mixed(args, w, s, dev, flush, stream, snap, ws)
+                                      for s in ("bf16", "fp16")}
+
     # the dominant kernel where it runs: after the timed region, the same steps
     # with two CUDA events recorded around the lattice kernel inside the step
     # graph (cold L2 after each flush); the host waits for each step here,
@@ -290,12 +299,62 @@ def run_native(args, rank, ws):
                                "kernel inside the step graph (cold L2 after each flush; includes the "
                                "graph's event-node latency)"},
         "lb_share_of_step": (1e3 * lb_s) / ms_per_step,
+        "mixed_precision": {k: dict(v, vs_fp32=v["value"] / value) for k, v in mixed.items()},
         "cpu_baseline": base,
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_mixed(args, w, storage, dev, flush, stream, snap, ws):
+    """The coupled step with 16-bit f^neq lattice storage: value, step time,
+    the lattice kernel's roofline, and the deviation from the FP32 run."""
+    import torch
+    from paper_1312_2234_b300 import fsi
+    g = w["grid"]
+    N = g["nx"] * g["ny"] * g["nz"]
+    sim = fsi.Simulation(w, device=dev, storage=storage)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        sim.step(1)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sim.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    total_s = reduce_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3, ws)
+    X0 = np.ascontiguousarray(w["X"])
+    dX32 = snap["X"] - X0
+    err = {"displacement_rel": float(np.abs(sim.X.cpu().numpy() - snap["X"]).max() / np.abs(dX32).max()),
+           "node_velocity_rel": float(np.abs(sim.U.cpu().numpy() - snap["U"]).max() / np.abs(snap["U"]).max())}
+    if snap["bound"] is not None:
+        b = sim.bonds.bound.cpu().numpy()
+        err["bonds_fp32"] = int((snap["bound"] >= 0).sum())
+        err["bonds"] = int((b >= 0).sum())
+        err["sites_differing"] = int((b != snap["bound"]).sum())
+    fsi.sim_time_lb(sim.h, True)
+    lb_ms = []
+    for k in range(max(args.steps, 10)):
+        flush.fill_(float(k))
+        sim.step(1)
+        lb_ms.append(fsi.sim_lb_ms(sim.h))
+    fsi.sim_time_lb(sim.h, False)
+    lb_s = statistics.median(lb_ms) / 1e3
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = LB_BYTES_PER_CELL_MIXED * N / lb_s / 1e9
+    return {"value": ws * N * args.steps / total_s / 1e6, "unit": "MLUPS",
+            "ms_per_step": 1e3 * total_s / args.steps, "fp16_exponent": int(sim.lattice.p.fp16_exponent),
+            "lb_kernel": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                          "algorithmic_bytes_per_launch": LB_BYTES_PER_CELL_MIXED * N, "launch_ms": 1e3 * lb_s},
+            "error_vs_fp32_after_%d_steps" % (args.warmup + args.steps): err}
 
 
 def run_lb_only(args):
@@ -306,11 +365,12 @@ def run_lb_only(args):
     from paper_1312_2234_b300 import fsi
 
     nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
-    lat = fsi.Lattice(nx, ny, nz, 0.8, (1e-3, 0.0, 0.0))
+    lat = fsi.Lattice(nx, ny, nz, 0.8, (1e-3, 0.0, 0.0), storage=args.storage)
     lat.init_shear()
     N = nx * ny * nz
+    per_cell = LB_BYTES_PER_CELL if args.storage == "fp32" else LB_BYTES_PER_CELL_MIXED
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    small = 2 * 76 * N < 2 * 126e6
+    small = per_cell * N < 2 * 126e6
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         fsi.lb_step(lat.h, 1)
@@ -328,8 +388,8 @@ def run_lb_only(args):
     t = statistics.median(ms) / 1e3
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6400.0
-    gbs = LB_BYTES_PER_CELL * N / t / 1e9
-    print(json.dumps({"kernel": "k_lb_step", "grid": [nx, ny, nz], "cells": N, "median_ms": 1e3 * t,
+    gbs = per_cell * N / t / 1e9
+    print(json.dumps({"kernel": "k_lb_step", "storage": args.storage, "grid": [nx, ny, nz], "cells": N, "median_ms": 1e3 * t,
                       "min_ms": min(ms), "GLUPS": N / t / 1e9, "GBps": gbs, "peak_GBps": peak,
                       "frac": gbs / peak, "l2_flushed": small}), flush=True)
 
@@ -343,6 +403,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
     ap.add_argument("--kernel", default=None, choices=[None, "lb"], help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variants")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

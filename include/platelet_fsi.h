@@ -54,17 +54,24 @@ int pfsi_version(void);
 /* ===================================================================== *
  * Lattice Boltzmann, Section 3.3
  * ===================================================================== */
+#define PFSI_LB_FP32 0  /* populations stored as FP32 f - w_q */
+#define PFSI_LB_BF16 1  /* f^neq stored as BF16, (v, rho - 1) as FP32 */
+#define PFSI_LB_FP16 2  /* f^neq * 2^fp16_exponent stored as FP16, (v, rho - 1) as FP32 */
+
 typedef struct {
     int nx, ny, nz;   /* grid; each >= 1, nz >= 2 */
     float tau;        /* BGK relaxation time (Eq. 16), > 0.5 */
     float u_top[3];   /* velocity of the top wall; u_top[2] must be 0 */
     float body[3];    /* uniform body-force density added in every cell */
+    int storage;      /* PFSI_LB_FP32 (lb_create) or PFSI_LB_BF16 / PFSI_LB_FP16 (lb_create_mixed) */
+    int fp16_exponent;/* PFSI_LB_FP16: power-of-two scale of the stored f^neq, -60..60 */
 } lb_params;
 
 typedef struct {
-    size_t f_bytes;    /* one population buffer: 19 * n_cells float */
+    size_t f_bytes;    /* one population buffer: 19 * n_cells float (FP32) or 16-bit (mixed) */
     size_t g_bytes;    /* force field: n_cells float4 (fx, fy, fz, unused) */
-    size_t v_bytes;    /* velocity field: n_cells float4 (vx, vy, vz, rho) */
+    size_t v_bytes;    /* FP32: velocity field n_cells float4 (vx, vy, vz, rho);
+                          mixed: one moments buffer n_cells float4 (vx, vy, vz, rho - 1) */
     size_t flag_bytes; /* row flags: ny * nz uint32 */
     long long n_cells;
 } lb_sizes;
@@ -87,6 +94,24 @@ int lb_query_sizes(const lb_params* p, lb_sizes* out);
  * the legacy default stream; synchronises). */
 int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, float* v,
               uint32_t* row_flags, lb_ctx** out);
+
+/* Mixed-precision storage (p->storage = PFSI_LB_BF16 or PFSI_LB_FP16; no
+ * paper counterpart, a storage choice): each cell keeps its post-collision
+ * non-equilibrium part f*neq_q = (1 - 1/tau)(f_q - f_q^eq) + S_q in 16 bits
+ * (fneq_a/fneq_b, [q][cell]) and its (v, rho - 1) in FP32 (m_a/m_b, float4
+ * per cell), 108 B per cell per step instead of 152.  A pulling cell rebuilds
+ * each incoming population as f_q^eq(rho, v of the source cell) + f*neq_q.
+ * The moments buffer of the current state is the velocity field that
+ * ib_interp reads (every cell; no row-flag velocity output).  Same step as
+ * lb_create otherwise.  All buffers 16-byte aligned; g and the flags are
+ * cleared (synchronises). */
+int lb_create_mixed(const lb_params* p, void* fneq_a, void* fneq_b, float* m_a, float* m_b, float* g,
+                    uint32_t* row_flags, lb_ctx** out);
+
+/* The current post-collision state as FP32 shifted populations f - w_q,
+ * [q][cell], into f_out (device, 19 * n_cells floats): a copy for FP32
+ * storage, the reconstruction f_eq(rho, v) + f*neq for mixed storage. */
+int lb_export(lb_ctx* ctx, float* f_out, void* stream);
 int lb_destroy(lb_ctx* ctx);
 
 /* Writes the developed shear profile u_x = u_top (k + 1/2)/nz (equilibrium
@@ -101,8 +126,15 @@ int lb_init_shear(lb_ctx* ctx, void* stream);
  * cell is body + g where its row is flagged.  Swaps the current buffer. */
 int lb_step(lb_ctx* ctx, int nsteps, void* stream);
 
-/* Device pointer of the buffer holding the current (post-collision) state. */
+/* Device pointer of the buffer holding the current (post-collision) state
+ * (FP32 storage only; mixed storage returns PFSI_ERR_ARG, see lb_export). */
 int lb_current(const lb_ctx* ctx, float** f);
+
+/* Device pointer of the velocity field that ib_interp reads, float4 per
+ * cell: FP32 storage, the v buffer, (v, rho) valid in the rows flagged at
+ * the last step; mixed storage, the current moments buffer, (v, rho - 1) in
+ * every cell.  v = u + g/(2 rho) of the last step. */
+int lb_velocity(const lb_ctx* ctx, float** v);
 
 /* Sum over all cells of rho and of rho*u (u = momentum of the current
  * post-collision state / rho), accumulated in FP64 on the device into the

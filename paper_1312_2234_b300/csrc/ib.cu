@@ -373,7 +373,7 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, c->v, c->flags, c->p.nx, c->p.ny, c->p.nz,
+    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz,
                                                    advect);
     return check_launch("ib_interp");
 }

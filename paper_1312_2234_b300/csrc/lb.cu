@@ -13,7 +13,21 @@
 // force flag are uniform across the block.  Traffic per cell: 19 float
 // loads + 19 float stores (152 B), plus, in rows marked by the spreading
 // kernel, the force (16 B read, 16 B cleared) and the velocity (16 B).
+//
+// Mixed storage keeps, per cell, the post-collision non-equilibrium part
+// f*neq_q = f*_q - f_q^eq(rho, v) in 16 bits and m = (v, rho - 1) in FP32
+// (108 B per cell per step).  The state is the same as the FP32 one up to
+// the rounding of f*neq: a pulling cell rebuilds f*_q of its source cell as
+// f_q^eq(m of the source) + f*neq_q, collides in FP32 exactly as above and
+// stores its own f*neq and m.  The 18 neighbour moments a cell reads are
+// shared with its neighbours and come from L1/L2; only the own cell's m
+// travels from DRAM.
+#include <algorithm>
 #include <climits>
+#include <utility>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "pfsi_internal.cuh"
 
@@ -97,6 +111,265 @@ __global__ void __launch_bounds__(kRowBlock) k_lb_step(
     }
 }
 
+// 16-bit encodings of f*neq: BF16 as is, FP16 scaled by 2^s (get takes
+// 2^-s, put takes 2^s; both exact powers of two).
+template <int kMode>
+struct Neq;
+template <>
+struct Neq<PFSI_LB_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float get(T h, float) { return __bfloat162float(h); }
+    static __device__ __forceinline__ T put(float x, float) { return __float2bfloat16_rn(x); }
+};
+template <>
+struct Neq<PFSI_LB_FP16> {
+    using T = __half;
+    static __device__ __forceinline__ float get(T h, float inv_scale) { return __half2float(h) * inv_scale; }
+    static __device__ __forceinline__ T put(float x, float scale) { return __float2half_rn(x * scale); }
+};
+
+// f_q^eq(rho, v) - w_q (Eq. 20) from m = (v, rho - 1).
+template <int q>
+__device__ __forceinline__ float feq_shifted(float4 m)
+{
+    float cv = 0.f;
+    if (cxq(q)) cv += cxq(q) * m.x;
+    if (cyq(q)) cv += cyq(q) * m.y;
+    if (czq(q)) cv += czq(q) * m.z;
+    const float vv = m.x * m.x + m.y * m.y + m.z * m.z;
+    return wq(q) * (m.w + (1.0f + m.w) * (3.0f * cv + 4.5f * cv * cv - 1.5f * vv));
+}
+
+// Mixed kernel blocking: a block takes a 32 x 8 (x, y) column of cells and
+// marches it through kz consecutive planes.  The moments of the column plus
+// a one-cell halo are kept for the planes k - 1, k, k + 1 in a shared ring
+// of four slots (the fourth takes plane k + 2 while k computes, so one
+// barrier per plane suffices); each moment comes from L2
+// ~(340 / 256)(kz + 2) / kz times per step instead of 19 times through L1.
+// A warp is one tile row.
+//
+// The ring holds each cell's moments in the form the rebuild wants:
+// with V = 3v and P = (rho - 1) - 1.5 rho v.v,
+//   f_q^eq - w_q = w_q (P + rho (c.V)(1 + (c.V)/2)),
+// four operations per pulled population.  The collision uses the same
+// factoring (and 3F for the source term).
+constexpr int kTX = 32, kTY = 8;
+constexpr int kHX = kTX + 2, kHY = kTY + 2;
+constexpr int kPlane = kHX * kHY;
+constexpr int kTileThreads = kTX * kTY;
+constexpr int kHaloPerThread = (kPlane + kTileThreads - 1) / kTileThreads;
+constexpr int kSlots = 4;
+
+struct Ring {
+    float4 pv[kSlots][kPlane];   // (P, Vx, Vy, Vz)
+    float rho[kSlots][kPlane];
+};
+
+__device__ __forceinline__ void halo_load(const float4* __restrict__ m, int k, int plane_cells, const int* off,
+                                          float4* r)
+{
+    const float4* plane = m + (size_t)k * plane_cells;
+#pragma unroll
+    for (int u = 0; u < kHaloPerThread; ++u)
+        if (off[u] >= 0) r[u] = plane[off[u]];
+}
+
+__device__ __forceinline__ void halo_store(Ring& ring, int slot, const float4* r)
+{
+#pragma unroll
+    for (int u = 0; u < kHaloPerThread; ++u) {
+        const int h = threadIdx.x + u * kTileThreads;
+        if (h < kPlane) {
+            const float4 m = r[u];
+            const float rho = 1.0f + m.w;
+            const float vv = m.x * m.x + m.y * m.y + m.z * m.z;
+            ring.pv[slot][h] = make_float4(m.w - 1.5f * rho * vv, 3.0f * m.x, 3.0f * m.y, 3.0f * m.z);
+            ring.rho[slot][h] = rho;
+        }
+    }
+}
+
+__device__ __forceinline__ float c_dot(int q, float x, float y, float z)
+{
+    float s = 0.f;
+    if (cxq(q)) s += cxq(q) * x;
+    if (cyq(q)) s += cyq(q) * y;
+    if (czq(q)) s += czq(q) * z;
+    return s;
+}
+
+// f_q^eq - w_q of a ring cell, for direction q.
+template <int q>
+__device__ __forceinline__ float feq_ring(const Ring& ring, int slot, int h)
+{
+    const float4 a = ring.pv[slot][h];
+    const float cv = c_dot(q, a.y, a.z, a.w);
+    return wq(q) * fmaf(ring.rho[slot][h], fmaf(0.5f * cv, cv, cv), a.x);
+}
+
+// f[q] += f_q^eq of the source cell (bounce-back: the own cell's opposite
+// population, plus the moving-wall term at the top).  sm, s0, sp: ring slots
+// of the planes k - 1, k, k + 1.
+template <int q>
+__device__ __forceinline__ void add_feq(float* f, const Ring& ring, int sm, int s0, int sp, int own, int k, int nz,
+                                        float3 utop)
+{
+    if (czq(q) == 1 && k == 0) {
+        f[q] += feq_ring<oppq(q)>(ring, s0, own);
+    } else if (czq(q) == -1 && k == nz - 1) {
+        const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
+        f[q] += feq_ring<oppq(q)>(ring, s0, own) + 6.0f * wq(q) * cu;
+    } else {
+        f[q] += feq_ring<q>(ring, czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0), own - cyq(q) * kHX - cxq(q));
+    }
+}
+
+template <int... Q>
+__device__ __forceinline__ void add_feq_all(std::integer_sequence<int, Q...>, float* f, const Ring& ring, int sm,
+                                            int s0, int sp, int own, int k, int nz, float3 utop)
+{
+    (add_feq<Q>(f, ring, sm, s0, sp, own, k, nz, utop), ...);
+}
+
+// Raw 16-bit f*neq a cell of plane k pulls (bounce-back: its own opposite).
+__device__ __forceinline__ void load_neq(const uint16_t* __restrict__ nin, uint32_t* raw, int N, int k, int nz,
+                                         int nx, int ny, int i, int j, int xm, int xp, int ym, int yp)
+{
+    const int cell = (k * ny + j) * nx + i;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if ((czq(q) == 1 && k == 0) || (czq(q) == -1 && k == nz - 1)) {
+            raw[q] = nin[oppq(q) * N + cell];
+        } else {
+            const int sx = cxq(q) == 1 ? xm : (cxq(q) == -1 ? xp : i);
+            const int sy = cyq(q) == 1 ? ym : (cyq(q) == -1 ? yp : j);
+            raw[q] = nin[q * N + ((k - czq(q)) * ny + sy) * nx + sx];
+        }
+    }
+}
+
+template <int kMode>
+__device__ __forceinline__ float neq_value(uint32_t raw, float inv_scale)
+{
+    if (kMode == PFSI_LB_BF16) return __uint_as_float(raw << 16);
+    return __half2float(__ushort_as_half((unsigned short)raw)) * inv_scale;
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kTileThreads, 3) k_lb_step_mixed(
+    const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
+    float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
+    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale)
+{
+    __shared__ Ring ring;
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
+    const int i = x0 + tx, j = y0 + ty;
+    const bool live = i < nx && j < ny;
+    const int N = nx * ny * nz;
+    const int plane_cells = nx * ny;
+    const int xm = (i == 0) ? nx - 1 : i - 1;
+    const int xp = (i >= nx - 1) ? 0 : i + 1;
+    const int ym = (j == 0) ? ny - 1 : j - 1;
+    const int yp = (j >= ny - 1) ? 0 : j + 1;
+    const float keep = 1.0f - omega;
+    const float scale = 1.0f / inv_scale;
+    const int own = (ty + 1) * kHX + tx + 1;
+
+    // in-plane offsets of this thread's halo cells (wrapped in x and y)
+    int off[kHaloPerThread];
+#pragma unroll
+    for (int u = 0; u < kHaloPerThread; ++u) {
+        const int h = threadIdx.x + u * kTileThreads;
+        const int hy = h / kHX, hx = h - hy * kHX;
+        int gx = x0 + hx - 1, gy = y0 + hy - 1;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        off[u] = h < kPlane ? gy * nx + gx : -1;
+    }
+
+    float4 r[kHaloPerThread];
+    for (int p = max(z0 - 1, 0); p <= min(z0 + 1, nz - 1); ++p) {
+        halo_load(min_, p, plane_cells, off, r);
+        halo_store(ring, p & 3, r);
+    }
+    __syncthreads();
+
+    const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
+    for (int k = z0; k < z1; ++k) {
+        const bool pre = k + 2 < nz && k + 2 <= z1;
+        if (pre) halo_load(min_, k + 2, plane_cells, off, r);
+        if (live) {
+            const int cell = (k * ny + j) * nx + i;
+            uint32_t raw[19];
+            load_neq(nin, raw, N, k, nz, nx, ny, i, j, xm, xp, ym, yp);
+            float f[19];
+#pragma unroll
+            for (int q = 0; q < 19; ++q) f[q] = neq_value<kMode>(raw[q], inv_scale);
+            add_feq_all(std::make_integer_sequence<int, 19>{}, f, ring, (k + 3) & 3, k & 3, (k + 1) & 3, own, k,
+                        nz, utop);
+
+            float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+            for (int q = 0; q < 19; ++q) {
+                drho += f[q];
+                if (cxq(q)) mx += cxq(q) * f[q];
+                if (cyq(q)) my += cyq(q) * f[q];
+                if (czq(q)) mz += czq(q) * f[q];
+            }
+            const float rho = 1.0f + drho;
+            float3 F3 = F3b;
+            const bool forced = flags[k * ny + j] != 0u;
+            if (forced) {
+                const float4 gg = g[cell];
+                F3.x = fmaf(3.0f, gg.x, F3.x);
+                F3.y = fmaf(3.0f, gg.y, F3.y);
+                F3.z = fmaf(3.0f, gg.z, F3.z);
+            }
+            // V = 3v = 3 (m + F/2) / rho; F3 = 3F
+            const float i3rho = 3.0f / rho;
+            const float vx = fmaf(F3.x, 1.0f / 6.0f, mx) * i3rho;
+            const float vy = fmaf(F3.y, 1.0f / 6.0f, my) * i3rho;
+            const float vz = fmaf(F3.z, 1.0f / 6.0f, mz) * i3rho;
+            const float VV = vx * vx + vy * vy + vz * vz;                           // 9 v.v
+            const float P0 = fmaf(-rho / 6.0f, VV, drho);                            // drho - 1.5 rho v.v
+            const float vF3 = (vx * F3.x + vy * F3.y + vz * F3.z) * (1.0f / 3.0f);  // 3 v.F
+#pragma unroll
+            for (int q = 0; q < 19; ++q) {
+                const float cv = c_dot(q, vx, vy, vz);        // 3 c.v
+                const float cF = c_dot(q, F3.x, F3.y, F3.z);  // 3 c.F
+                const float feq = fmaf(rho, fmaf(0.5f * cv, cv, cv), P0);    // (f^eq - w) / w
+                const float src = fmaf(cF, cv, cF - vF3);                     // S / (w guo)
+                // post-collision minus equilibrium: (1 - omega)(f - f^eq) + S
+                const float neq = fmaf(keep, f[q], fmaf(-keep * wq(q), feq, (wq(q) * guo) * src));
+                nout[q * N + cell] = Neq<kMode>::put(neq, scale);
+            }
+            mout[cell] = make_float4(vx * (1.0f / 3.0f), vy * (1.0f / 3.0f), vz * (1.0f / 3.0f), drho);
+            if (forced) g[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (pre) halo_store(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
+        __syncthreads();
+    }
+}
+
+template <int kMode, int q>
+__device__ __forceinline__ void export_q(const typename Neq<kMode>::T* __restrict__ nin, float4 m,
+                                         float* __restrict__ fout, int N, int cell, float inv_scale)
+{
+    fout[q * N + cell] = feq_shifted<q>(m) + Neq<kMode>::get(nin[q * N + cell], inv_scale);
+}
+
+template <int kMode, int... Q>
+__global__ void k_lb_export_mixed(std::integer_sequence<int, Q...>, const typename Neq<kMode>::T* __restrict__ nin,
+                                  const float4* __restrict__ min_, float* __restrict__ fout, int N, float inv_scale)
+{
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+        const float4 m = min_[cell];
+        (export_q<kMode, Q>(nin, m, fout, N, cell, inv_scale), ...);
+    }
+}
+
 // Developed shear profile, post-collision, shifted by w_q; evaluated in FP64.
 __global__ void k_lb_init_shear(float* __restrict__ f, int nx, int ny, int nz, double tau,
                                 double ux_top, double uy_top)
@@ -146,6 +419,67 @@ __global__ void k_lb_moments(const float* __restrict__ f, int N, double* __restr
     }
 }
 
+// Mixed storage: the same developed profile as (v, 0) and the first-order
+// non-equilibrium part, evaluated in FP64.
+template <int kMode>
+__global__ void k_lb_init_shear_mixed(typename Neq<kMode>::T* __restrict__ nout, float4* __restrict__ mout, int nx,
+                                      int ny, int nz, double tau, double ux_top, double uy_top, float inv_scale)
+{
+    const int N = nx * ny * nz;
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+        const int k = cell / (nx * ny);
+        const double dux = ux_top / nz, duy = uy_top / nz;
+        mout[cell] = make_float4((float)(dux * (k + 0.5)), (float)(duy * (k + 0.5)), 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
+            const double qgrad = (double)czq(q) * (cxq(q) * dux + cyq(q) * duy);
+            nout[q * N + cell] = Neq<kMode>::put((float)(-(tau - 1.0) * w * 3.0 * qgrad), 1.0f / inv_scale);
+        }
+    }
+}
+
+// FP64 sums of rho and rho*u of the current mixed state, from the rebuilt
+// post-collision populations.
+template <int kMode>
+__global__ void k_lb_moments_mixed(const typename Neq<kMode>::T* __restrict__ nin, const float4* __restrict__ min_,
+                                   int N, double* __restrict__ acc, float inv_scale)
+{
+    double s[4] = {0, 0, 0, 0};
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+        const float4 m = min_[cell];
+        const double vx = m.x, vy = m.y, vz = m.z, d = m.w;
+        const double vv = vx * vx + vy * vy + vz * vz;
+        double sd = 0, mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
+            const double cv = cxq(q) * vx + cyq(q) * vy + czq(q) * vz;
+            const double fq = w * (d + (1.0 + d) * (3.0 * cv + 4.5 * cv * cv - 1.5 * vv)) +
+                              (double)Neq<kMode>::get(nin[q * N + cell], inv_scale);
+            sd += fq;
+            mx += cxq(q) * fq;
+            my += cyq(q) * fq;
+            mz += czq(q) * fq;
+        }
+        s[0] += 1.0 + sd;
+        s[1] += mx;
+        s[2] += my;
+        s[3] += mz;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double x = s[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&acc[c], x);
+    }
+}
+
+float inv_scale_of(const lb_params& p) { return p.storage == PFSI_LB_FP16 ? ldexpf(1.0f, -p.fp16_exponent) : 1.0f; }
+
+template <int kMode>
+using NeqT = typename Neq<kMode>::T;
+
 }  // namespace
 
 int launch_lb_step(LbCtx* c, cudaStream_t s)
@@ -155,9 +489,31 @@ int launch_lb_step(LbCtx* c, cudaStream_t s)
     const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
     const float omega = 1.0f / p.tau;
     const float guo = 1.0f - 0.5f / p.tau;
-    k_lb_step<<<grid, bx, 0, s>>>(c->f[c->cur], c->f[c->cur ^ 1], c->g, c->v, c->flags, p.nx,
-                                  p.ny, p.nz, omega, guo, make_float3(p.body[0], p.body[1], p.body[2]),
-                                  make_float3(p.u_top[0], p.u_top[1], p.u_top[2]));
+    const float3 body = make_float3(p.body[0], p.body[1], p.body[2]);
+    const float3 utop = make_float3(p.u_top[0], p.u_top[1], p.u_top[2]);
+    const int a = c->cur, b = c->cur ^ 1;
+    // mixed: 32 x 8 columns, each marching through kz planes; kz is picked so
+    // that the grid has about eight blocks per SM (fewer halo planes per
+    // cell on large grids, enough blocks on small ones)
+    const int tiles = ((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY);
+    const long long want = 148LL * 8;
+    const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
+    const dim3 mgrid((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY, (p.nz + kz - 1) / kz);
+    switch (p.storage) {
+    case PFSI_LB_BF16:
+        k_lb_step_mixed<PFSI_LB_BF16><<<mgrid, kTileThreads, 0, s>>>(
+            (const uint16_t*)c->f[a], (NeqT<PFSI_LB_BF16>*)c->f[b], c->m[a], c->m[b], c->g, c->flags, p.nx, p.ny,
+            p.nz, kz, omega, guo, body, utop, 1.0f);
+        break;
+    case PFSI_LB_FP16:
+        k_lb_step_mixed<PFSI_LB_FP16><<<mgrid, kTileThreads, 0, s>>>(
+            (const uint16_t*)c->f[a], (NeqT<PFSI_LB_FP16>*)c->f[b], c->m[a], c->m[b], c->g, c->flags, p.nx, p.ny,
+            p.nz, kz, omega, guo, body, utop, inv_scale_of(p));
+        break;
+    default:
+        k_lb_step<<<grid, bx, 0, s>>>((const float*)c->f[a], (float*)c->f[b], c->g, c->v, c->flags, p.nx, p.ny,
+                                      p.nz, omega, guo, body, utop);
+    }
     c->cur ^= 1;
     return check_launch("lb_step");
 }
@@ -174,26 +530,31 @@ extern "C" int lb_query_sizes(const lb_params* p, lb_sizes* out)
     const long long N = (long long)p->nx * p->ny * p->nz;
     if (N * 19 > (long long)INT_MAX)
         return set_error(PFSI_ERR_ARG, "lb_query_sizes: grid too large (19 * cells must fit in int32)");
+    if (p->storage != PFSI_LB_FP32 && p->storage != PFSI_LB_BF16 && p->storage != PFSI_LB_FP16)
+        return set_error(PFSI_ERR_ARG, "lb_query_sizes: unknown storage mode");
+    if (p->storage == PFSI_LB_FP16 && (p->fp16_exponent < -60 || p->fp16_exponent > 60))
+        return set_error(PFSI_ERR_ARG, "lb_query_sizes: fp16_exponent outside -60..60");
     out->n_cells = N;
-    out->f_bytes = (size_t)N * 19 * sizeof(float);
+    out->f_bytes = (size_t)N * 19 * (p->storage == PFSI_LB_FP32 ? sizeof(float) : sizeof(uint16_t));
     out->g_bytes = (size_t)N * sizeof(float4);
     out->v_bytes = (size_t)N * sizeof(float4);
     out->flag_bytes = (size_t)p->ny * p->nz * sizeof(uint32_t);
     return PFSI_OK;
 }
 
-extern "C" int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, float* v,
-                         uint32_t* row_flags, lb_ctx** out)
+namespace {
+
+int create_common(const char* who, const lb_params* p, void* f_a, void* f_b, float* m_a, float* m_b, float* g,
+                  float* v, uint32_t* row_flags, lb_ctx** out)
 {
     lb_sizes sz;
     int rc = lb_query_sizes(p, &sz);
     if (rc) return rc;
-    if (!out || !f_a || !f_b || !g || !v || !row_flags)
-        return set_error(PFSI_ERR_ARG, "lb_create: null buffer");
-    if (!aligned(f_a, 16) || !aligned(f_b, 16) || !aligned(g, 16) || !aligned(v, 16) || !aligned(row_flags, 4))
-        return set_error(PFSI_ERR_ARG, "lb_create: buffers must be 16-byte aligned");
-    if (!(p->tau > 0.5f)) return set_error(PFSI_ERR_ARG, "lb_create: tau must exceed 1/2");
-    if (p->u_top[2] != 0.0f) return set_error(PFSI_ERR_ARG, "lb_create: the top wall cannot move along z");
+    if (!(p->tau > 0.5f)) return set_error(PFSI_ERR_ARG, std::string(who) + ": tau must exceed 1/2");
+    if (p->u_top[2] != 0.0f) return set_error(PFSI_ERR_ARG, std::string(who) + ": the top wall cannot move along z");
+    if (!aligned(f_a, 16) || !aligned(f_b, 16) || !aligned(g, 16) || !aligned(v, 16) || !aligned(m_a, 16) ||
+        !aligned(m_b, 16) || !aligned(row_flags, 4))
+        return set_error(PFSI_ERR_ARG, std::string(who) + ": buffers must be 16-byte aligned");
     rc = ib_prepare();
     if (rc) return rc;
     lb_ctx* c = new lb_ctx();
@@ -204,6 +565,8 @@ extern "C" int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, f
     c->cur = 0;
     c->g = reinterpret_cast<float4*>(g);
     c->v = reinterpret_cast<float4*>(v);
+    c->m[0] = reinterpret_cast<float4*>(m_a);
+    c->m[1] = reinterpret_cast<float4*>(m_b);
     c->flags = row_flags;
     rc = check_cuda(cudaMemsetAsync(c->g, 0, sz.g_bytes, 0), "lb_create: clear g");
     if (!rc) rc = check_cuda(cudaMemsetAsync(c->flags, 0, sz.flag_bytes, 0), "lb_create: clear flags");
@@ -214,6 +577,27 @@ extern "C" int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, f
     }
     *out = c;
     return PFSI_OK;
+}
+
+}  // namespace
+
+extern "C" int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, float* v,
+                         uint32_t* row_flags, lb_ctx** out)
+{
+    if (!p || !out || !f_a || !f_b || !g || !v || !row_flags)
+        return set_error(PFSI_ERR_ARG, "lb_create: null argument");
+    if (p->storage != PFSI_LB_FP32) return set_error(PFSI_ERR_ARG, "lb_create: storage must be PFSI_LB_FP32");
+    return create_common("lb_create", p, f_a, f_b, nullptr, nullptr, g, v, row_flags, out);
+}
+
+extern "C" int lb_create_mixed(const lb_params* p, void* fneq_a, void* fneq_b, float* m_a, float* m_b, float* g,
+                               uint32_t* row_flags, lb_ctx** out)
+{
+    if (!p || !out || !fneq_a || !fneq_b || !m_a || !m_b || !g || !row_flags)
+        return set_error(PFSI_ERR_ARG, "lb_create_mixed: null argument");
+    if (p->storage != PFSI_LB_BF16 && p->storage != PFSI_LB_FP16)
+        return set_error(PFSI_ERR_ARG, "lb_create_mixed: storage must be PFSI_LB_BF16 or PFSI_LB_FP16");
+    return create_common("lb_create_mixed", p, fneq_a, fneq_b, m_a, m_b, g, nullptr, row_flags, out);
 }
 
 extern "C" int lb_destroy(lb_ctx* ctx)
@@ -227,9 +611,21 @@ extern "C" int lb_init_shear(lb_ctx* c, void* stream)
     if (!c) return set_error(PFSI_ERR_ARG, "lb_init_shear: null context");
     const int N = (int)c->N;
     const int blocks = (N + 255) / 256 < 148 * 16 ? (N + 255) / 256 : 148 * 16;
-    k_lb_init_shear<<<blocks, 256, 0, as_stream(stream)>>>(c->f[c->cur], c->p.nx, c->p.ny, c->p.nz,
-                                                           (double)c->p.tau, (double)c->p.u_top[0],
-                                                           (double)c->p.u_top[1]);
+    const lb_params& p = c->p;
+    cudaStream_t s = as_stream(stream);
+    const double tau = p.tau, ux = p.u_top[0], uy = p.u_top[1];
+    switch (p.storage) {
+    case PFSI_LB_BF16:
+        k_lb_init_shear_mixed<PFSI_LB_BF16><<<blocks, 256, 0, s>>>((NeqT<PFSI_LB_BF16>*)c->f[c->cur], c->m[c->cur],
+                                                                   p.nx, p.ny, p.nz, tau, ux, uy, 1.0f);
+        break;
+    case PFSI_LB_FP16:
+        k_lb_init_shear_mixed<PFSI_LB_FP16><<<blocks, 256, 0, s>>>((NeqT<PFSI_LB_FP16>*)c->f[c->cur], c->m[c->cur],
+                                                                   p.nx, p.ny, p.nz, tau, ux, uy, inv_scale_of(p));
+        break;
+    default:
+        k_lb_init_shear<<<blocks, 256, 0, s>>>((float*)c->f[c->cur], p.nx, p.ny, p.nz, tau, ux, uy);
+    }
     return check_launch("lb_init_shear");
 }
 
@@ -247,8 +643,40 @@ extern "C" int lb_step(lb_ctx* c, int nsteps, void* stream)
 extern "C" int lb_current(const lb_ctx* c, float** f)
 {
     if (!c || !f) return set_error(PFSI_ERR_ARG, "lb_current: null argument");
-    *f = c->f[c->cur];
+    if (c->p.storage != PFSI_LB_FP32)
+        return set_error(PFSI_ERR_ARG, "lb_current: mixed storage holds no FP32 populations (use lb_export)");
+    *f = (float*)c->f[c->cur];
     return PFSI_OK;
+}
+
+extern "C" int lb_velocity(const lb_ctx* c, float** v)
+{
+    if (!c || !v) return set_error(PFSI_ERR_ARG, "lb_velocity: null argument");
+    *v = reinterpret_cast<float*>(velocity_field(c));
+    return PFSI_OK;
+}
+
+extern "C" int lb_export(lb_ctx* c, float* f_out, void* stream)
+{
+    if (!c || !f_out) return set_error(PFSI_ERR_ARG, "lb_export: null argument");
+    if (!aligned(f_out, 4)) return set_error(PFSI_ERR_ARG, "lb_export: misaligned output");
+    cudaStream_t s = as_stream(stream);
+    const int N = (int)c->N;
+    const lb_params& p = c->p;
+    if (p.storage == PFSI_LB_FP32)
+        return check_cuda(cudaMemcpyAsync(f_out, c->f[c->cur], (size_t)N * 19 * sizeof(float),
+                                          cudaMemcpyDeviceToDevice, s),
+                          "lb_export: copy");
+    const int blocks = (N + 255) / 256 < 148 * 8 ? (N + 255) / 256 : 148 * 8;
+    if (p.storage == PFSI_LB_BF16)
+        k_lb_export_mixed<PFSI_LB_BF16><<<blocks, 256, 0, s>>>(std::make_integer_sequence<int, 19>{},
+                                                               (const NeqT<PFSI_LB_BF16>*)c->f[c->cur],
+                                                               c->m[c->cur], f_out, N, 1.0f);
+    else
+        k_lb_export_mixed<PFSI_LB_FP16><<<blocks, 256, 0, s>>>(std::make_integer_sequence<int, 19>{},
+                                                               (const NeqT<PFSI_LB_FP16>*)c->f[c->cur],
+                                                               c->m[c->cur], f_out, N, inv_scale_of(p));
+    return check_launch("lb_export");
 }
 
 extern "C" int lb_moments_fp64(lb_ctx* c, double* dev_scratch4, double* out_host, void* stream)
@@ -260,7 +688,18 @@ extern "C" int lb_moments_fp64(lb_ctx* c, double* dev_scratch4, double* out_host
     if (rc) return rc;
     const int N = (int)c->N;
     const int blocks = (N + 255) / 256 < 148 * 8 ? (N + 255) / 256 : 148 * 8;
-    k_lb_moments<<<blocks, 256, 0, s>>>(c->f[c->cur], N, dev_scratch4);
+    switch (c->p.storage) {
+    case PFSI_LB_BF16:
+        k_lb_moments_mixed<PFSI_LB_BF16><<<blocks, 256, 0, s>>>((const NeqT<PFSI_LB_BF16>*)c->f[c->cur],
+                                                                c->m[c->cur], N, dev_scratch4, 1.0f);
+        break;
+    case PFSI_LB_FP16:
+        k_lb_moments_mixed<PFSI_LB_FP16><<<blocks, 256, 0, s>>>((const NeqT<PFSI_LB_FP16>*)c->f[c->cur],
+                                                                c->m[c->cur], N, dev_scratch4, inv_scale_of(c->p));
+        break;
+    default:
+        k_lb_moments<<<blocks, 256, 0, s>>>((const float*)c->f[c->cur], N, dev_scratch4);
+    }
     rc = check_launch("lb_moments_fp64");
     if (rc) return rc;
     rc = check_cuda(cudaMemcpyAsync(out_host, dev_scratch4, 4 * sizeof(double), cudaMemcpyDeviceToHost, s),

@@ -200,11 +200,6 @@ struct Split {
         return {ff_diff(h[a], l[a], h[b], l[b]), ff_diff(h[n + a], l[n + a], h[n + b], l[n + b]),
                 ff_diff(h[2 * n + a], l[2 * n + a], h[2 * n + b], l[2 * n + b])};
     }
-    __device__ __forceinline__ float3 rel(int a, int b) const  // X_a - X_b rounded to FP32
-    {
-        return make_float3((h[a] - h[b]) + (l[a] - l[b]), (h[n + a] - h[n + b]) + (l[n + a] - l[n + b]),
-                           (h[2 * n + a] - h[2 * n + b]) + (l[2 * n + a] - l[2 * n + b]));
-    }
 };
 
 // Pass 1: split FP64 positions into hi/lo floats; clear the per-platelet sums.

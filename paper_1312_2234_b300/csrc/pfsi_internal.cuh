@@ -84,12 +84,16 @@ __device__ __forceinline__ double uniform53(uint64_t seed, uint32_t site, uint64
 struct LbCtx {
     lb_params p;
     long long N;
-    float* f[2];
+    void* f[2];          // populations: FP32 shifted f - w, or 16-bit f^neq (mixed storage)
     int cur;             // index of the buffer holding the current state
     float4* g;
-    float4* v;
+    float4* v;           // FP32 storage: (v, rho) written in forced rows
+    float4* m[2];        // mixed storage: (v, rho - 1) of every cell, with f[]
     uint32_t* flags;
 };
+
+// Velocity field the interpolation reads after a lattice step.
+inline float4* velocity_field(const LbCtx* c) { return c->p.storage ? c->m[c->cur] : c->v; }
 
 struct MemCtx {
     mem_params p;

@@ -12,6 +12,7 @@ hold the handles.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -25,9 +26,13 @@ c_int, c_double, c_float, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ct
 c_uint64, c_longlong = ctypes.c_uint64, ctypes.c_longlong
 
 
+LB_FP32, LB_BF16, LB_FP16 = 0, 1, 2
+STORAGE = {"fp32": LB_FP32, "bf16": LB_BF16, "fp16": LB_FP16}
+
+
 class lb_params(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("tau", c_float),
-                ("u_top", c_float * 3), ("body", c_float * 3)]
+                ("u_top", c_float * 3), ("body", c_float * 3), ("storage", c_int), ("fp16_exponent", c_int)]
 
 
 class lb_sizes(ctypes.Structure):
@@ -54,6 +59,9 @@ _SIGS = {
     "pfsi_version": [],
     "lb_query_sizes": [ctypes.POINTER(lb_params), ctypes.POINTER(lb_sizes)],
     "lb_create": [ctypes.POINTER(lb_params), P, P, P, P, P, ctypes.POINTER(P)],
+    "lb_create_mixed": [ctypes.POINTER(lb_params), P, P, P, P, P, P, ctypes.POINTER(P)],
+    "lb_export": [P, P, P],
+    "lb_velocity": [P, ctypes.POINTER(P)],
     "lb_destroy": [P],
     "lb_init_shear": [P, P],
     "lb_step": [P, c_int, P],
@@ -146,6 +154,23 @@ def lb_create(p, f_a, f_b, g, v, flags):
 
 def lb_destroy(h):
     _call("lb_destroy", h)
+
+
+def lb_create_mixed(p, n_a, n_b, m_a, m_b, g, flags):
+    h = c_void_p()
+    _call("lb_create_mixed", ctypes.byref(p), _ptr(n_a), _ptr(n_b), _ptr(m_a), _ptr(m_b), _ptr(g), _ptr(flags),
+          ctypes.byref(h))
+    return h
+
+
+def lb_velocity(h):
+    out = c_void_p()
+    _call("lb_velocity", h, ctypes.byref(out))
+    return out.value
+
+
+def lb_export(h, f_out, stream=None):
+    _call("lb_export", h, _ptr(f_out), _stream(stream))
 
 
 def lb_init_shear(h, stream=None):
@@ -291,24 +316,64 @@ def _bytes(n, device):
     return t
 
 
-class Lattice:
-    """D3Q19 lattice with caller-owned (torch) buffers."""
+def default_fp16_exponent(nz, tau, u_top):
+    """Power-of-two scale for FP16 f^neq storage.  The first-order
+    non-equilibrium part of a shear flow is about w tau |du/dz| (|du/dz| ~
+    |u_top| / nz); 2^s of its inverse over 4 keeps it a normal FP16 number
+    with ~2^14 of headroom for the steeper gradients near immersed bodies."""
+    grad = max(math.hypot(u_top[0], u_top[1]) / nz, 1e-6)
+    return int(max(-60, min(60, math.floor(math.log2(1.0 / (tau * grad))) - 2)))
 
-    def __init__(self, nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0), device="cuda"):
-        self.p = lb_params(nx, ny, nz, tau, (c_float * 3)(*u_top), (c_float * 3)(*body))
+
+class Lattice:
+    """D3Q19 lattice with caller-owned (torch) buffers.  storage is "fp32"
+    (shifted populations) or "bf16" / "fp16" (16-bit f^neq + FP32 moments)."""
+
+    def __init__(self, nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0), device="cuda",
+                 storage="fp32", fp16_exponent=None):
+        mode = STORAGE[storage]
+        if fp16_exponent is None:
+            fp16_exponent = default_fp16_exponent(nz, tau, u_top) if mode == LB_FP16 else 0
+        self.storage = storage
+        self.p = lb_params(nx, ny, nz, tau, (c_float * 3)(*u_top), (c_float * 3)(*body), mode, int(fp16_exponent))
         s = lb_query_sizes(self.p)
         self.N = int(s.n_cells)
         self.shape = (nz, ny, nx)
-        self.f = [torch.empty(19, self.N, dtype=torch.float32, device=device) for _ in range(2)]
         self.g = torch.zeros(self.N, 4, dtype=torch.float32, device=device)
-        self.v = torch.zeros(self.N, 4, dtype=torch.float32, device=device)
         self.flags = torch.zeros(ny * nz, dtype=torch.int32, device=device)
         self.scratch = torch.zeros(4, dtype=torch.float64, device=device)
-        self.h = lb_create(self.p, self.f[0], self.f[1], self.g, self.v, self.flags)
+        if mode == LB_FP32:
+            self.f = [torch.empty(19, self.N, dtype=torch.float32, device=device) for _ in range(2)]
+            self.v = torch.zeros(self.N, 4, dtype=torch.float32, device=device)
+            self.h = lb_create(self.p, self.f[0], self.f[1], self.g, self.v, self.flags)
+        else:
+            dt = torch.bfloat16 if mode == LB_BF16 else torch.float16
+            self.f = [torch.zeros(19, self.N, dtype=dt, device=device) for _ in range(2)]
+            self.m = [torch.zeros(self.N, 4, dtype=torch.float32, device=device) for _ in range(2)]
+            self.h = lb_create_mixed(self.p, self.f[0], self.f[1], self.m[0], self.m[1], self.g, self.flags)
+
+    @property
+    def mixed(self):
+        return self.storage != "fp32"
 
     def current(self):
+        """The live FP32 population buffer (FP32 storage only)."""
         ptr = lb_current(self.h)
         return self.f[0] if ptr == self.f[0].data_ptr() else self.f[1]
+
+    def velocity(self):
+        """The float4 velocity field ib_interp reads: (v, rho) in the last
+        step's forced rows (FP32 storage) or (v, rho - 1) everywhere (mixed)."""
+        if not self.mixed:
+            return self.v
+        ptr = lb_velocity(self.h)
+        return self.m[0] if ptr == self.m[0].data_ptr() else self.m[1]
+
+    def export(self, stream=None):
+        """The current post-collision state as FP32 shifted populations, [19, N]."""
+        out = torch.empty(19, self.N, dtype=torch.float32, device=self.g.device)
+        lb_export(self.h, out, stream)
+        return out
 
     def init_shear(self):
         lb_init_shear(self.h)
@@ -405,9 +470,10 @@ class Bonds:
 class Simulation:
     """The coupled step on one workload (see :mod:`paper_1312_2234_b300.workload`)."""
 
-    def __init__(self, w, device="cuda", first_step=0):
+    def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None):
         g = w["grid"]
-        self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device)
+        self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device,
+                               storage, fp16_exponent)
         self.lattice.init_shear()
         self.membrane = Membrane(w["membrane"], w["mesh"], device)
         self.M = int(w["M"])

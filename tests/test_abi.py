@@ -49,6 +49,47 @@ def test_lb_query_sizes_validation(L):
     assert L.lb_query_sizes(None, ctypes.byref(s)) == -1
 
 
+def test_lb_query_sizes_mixed_storage(L):
+    s = fsi.lb_sizes()
+    z = (ctypes.c_float * 3)(0, 0, 0)
+    N = 48 * 40 * 36
+    for mode in (fsi.LB_BF16, fsi.LB_FP16):
+        p = fsi.lb_params(48, 40, 36, 0.8, z, z, mode, 12)
+        assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == 0
+        assert s.f_bytes == 19 * 2 * N and s.v_bytes == 16 * N
+    p = fsi.lb_params(48, 40, 36, 0.8, z, z, 3, 0)
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
+    assert "storage" in fsi.last_error()
+    p = fsi.lb_params(48, 40, 36, 0.8, z, z, fsi.LB_FP16, 61)
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
+    assert "fp16_exponent" in fsi.last_error()
+
+
+def test_lb_create_checks_the_storage_mode(L):
+    z = (ctypes.c_float * 3)(0, 0, 0)
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    p = fsi.lb_params(8, 8, 8, 0.8, z, z, fsi.LB_BF16, 0)
+    assert L.lb_create(ctypes.byref(p), fake, fake, fake, fake, fake, ctypes.byref(h)) == -1
+    assert "PFSI_LB_FP32" in fsi.last_error()
+    p.storage = fsi.LB_FP32
+    assert L.lb_create_mixed(ctypes.byref(p), fake, fake, fake, fake, fake, fake, ctypes.byref(h)) == -1
+    assert "PFSI_LB_BF16" in fsi.last_error()
+    p.storage = fsi.LB_FP16
+    odd = ctypes.c_void_p(0x1008)
+    assert L.lb_create_mixed(ctypes.byref(p), fake, fake, odd, fake, fake, fake, ctypes.byref(h)) == -1
+    assert "aligned" in fsi.last_error()
+
+
+def test_default_fp16_exponent_keeps_shear_fneq_normal():
+    """The first-order f^neq of a Couette flow, w tau |u_top| / nz, scaled by
+    the default 2^s, lands in FP16's normal range with room above it."""
+    for u, nz, tau in [(2.2e-4, 64, 0.8), (4e-3, 19, 0.8), (0.05, 32, 1.379), (0.0, 16, 0.9)]:
+        s = fsi.default_fp16_exponent(nz, tau, (u, 0.0, 0.0))
+        fneq = (1 / 36) * tau * max(u / nz, 1e-6) * 2.0 ** s
+        assert 2.0 ** -14 < fneq < 1.0
+
+
 def test_lb_create_rejects_bad_buffers(L):
     p = fsi.lb_params(8, 8, 8, 0.8, (ctypes.c_float * 3)(0, 0, 0), (ctypes.c_float * 3)(0, 0, 0))
     h = ctypes.c_void_p()
