@@ -1,0 +1,153 @@
+"""Pins of the FP64 surrogate reference (oracle/mlp.py) against facts that do
+not come from its own formulas: the exact-erf GELU, finite differences,
+icosahedron geometry, rigid-motion invariance, the closed form of a first
+Adam step, and the linearity of the membrane force in its coefficients."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp
+from paper_1312_2234_b300 import workload
+
+
+def test_gelu_identities():
+    z = np.linspace(-6, 6, 241)
+    g = mlp.gelu(z)
+    # tanh is odd: g(z) - g(-z) = z exactly
+    assert np.allclose(g - mlp.gelu(-z), z, atol=1e-15)
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    # the tanh form stays within 1e-3 of the exact x Phi(x)
+    exact = np.array([0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0))) for x in z])
+    assert np.max(np.abs(g - exact)) < 1e-3
+    assert abs(mlp.gelu(np.array([30.0]))[0] - 30.0) < 1e-12
+    assert abs(mlp.gelu(np.array([-30.0]))[0]) < 1e-12
+
+
+def test_gelu_grad_by_central_differences():
+    z = np.linspace(-5, 5, 101)
+    h = 1e-6
+    fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
+    assert np.allclose(mlp.gelu_grad(z), fd, rtol=0, atol=1e-8)
+
+
+def ico(level):
+    U, T = workload.icosphere(level)
+    return U, T
+
+
+def test_one_rings_follow_face_orientation():
+    U, T = ico(1)
+    ring, deg = mlp.one_rings(T, len(U))
+    assert set(deg.tolist()) == {5, 6} and (deg == 5).sum() == 12
+    faces = {tuple(np.roll(f, -k)) for f in T.tolist() for k in range(3)}
+    for i in range(len(U)):
+        d = deg[i]
+        assert ring[i, 0] == min(ring[i, :d])
+        for k in range(d):
+            assert (i, ring[i, k], ring[i, (k + 1) % d]) in faces
+
+
+def test_rest_features_and_icosahedron_curvature():
+    U, T = ico(0)
+    ring, deg = mlp.one_rings(T, len(U))
+    f, R = mlp.features(U, U, ring, deg, np.arange(12))
+    assert np.all(np.abs(f[:, :18]) < 1e-14) and np.all(np.abs(f[:, 21:]) < 1e-14)
+    # regular icosahedron on the unit sphere: the five neighbours sit at
+    # polar angle acos(1/sqrt 5), so the mean neighbour offset is
+    # (1/sqrt 5 - 1) along the outward normal and the edge is sqrt(2 - 2/sqrt 5)
+    kz = (1 / math.sqrt(5) - 1) / math.sqrt(2 - 2 / math.sqrt(5))
+    assert np.allclose(f[:, 18:20], 0, atol=1e-14)
+    assert np.allclose(f[:, 20], kz, atol=1e-14)
+    # frames are orthonormal, right-handed, z outward
+    for r, i in enumerate(range(12)):
+        assert np.allclose(R[r] @ R[r].T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(R[r]) - 1) < 1e-14
+        assert R[r][2] @ U[i] > 0.99
+
+
+def rotation(rng):
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    return q * np.sign(np.linalg.det(q))
+
+
+def test_features_invariant_and_forces_equivariant_under_rigid_motion():
+    rng = np.random.default_rng(1)
+    U, T = ico(2)
+    U = U * np.array([5.0, 5.0, 1.25])
+    ring, deg = mlp.one_rings(T, len(U))
+    X = U + 0.02 * rng.standard_normal(U.shape)
+    Q = rotation(rng)
+    c = np.array([3.0, -2.0, 7.5])
+    nodes = np.arange(len(U))
+    f1, _ = mlp.features(X, U, ring, deg, nodes)
+    f2, _ = mlp.features(X @ Q.T + c, U, ring, deg, nodes)
+    assert np.allclose(f1, f2, atol=1e-12)
+    p = mlp.init_params(rng)
+    F1 = mlp.predict_forces(p, X, U, ring, deg, nodes)
+    F2 = mlp.predict_forces(p, X @ Q.T + c, U, ring, deg, nodes)
+    assert np.allclose(F2, F1 @ Q.T, atol=1e-12)
+
+
+def test_strain_features_are_stretches():
+    U, T = ico(1)
+    ring, deg = mlp.one_rings(T, len(U))
+    f, _ = mlp.features(1.01 * U, U, ring, deg, np.arange(len(U)))
+    for i in range(len(U)):
+        assert np.allclose(f[i, 21:21 + deg[i]], 0.01, atol=1e-14)
+        assert np.all(f[i, 21 + deg[i]:] == 0)
+
+
+def test_backward_matches_central_differences():
+    rng = np.random.default_rng(2)
+    p = mlp.init_params(rng)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.1 * rng.standard_normal(p[k].shape)
+    f = rng.standard_normal((7, mlp.N_IN))
+    t = rng.standard_normal((7, mlp.N_OUT))
+    o, cache = mlp.forward(p, f)
+    g = mlp.backward(p, cache, o, t)
+    h = 1e-6
+    for k in mlp.TRAINED:
+        idx = [tuple(rng.integers(0, s) for s in p[k].shape) for _ in range(6)]
+        for ix in idx:
+            old = p[k][ix]
+            p[k][ix] = old + h
+            lp = mlp.loss(mlp.forward(p, f)[0], t)
+            p[k][ix] = old - h
+            lm = mlp.loss(mlp.forward(p, f)[0], t)
+            p[k][ix] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(g[k][ix] - fd) <= 1e-7 * max(1.0, abs(fd)), (k, ix, g[k][ix], fd)
+
+
+def test_first_adam_steps_closed_form():
+    """With zero moments, bias correction makes m_hat = g and v_hat = g^2 at
+    every step while the gradient stays the same, so each step moves a
+    parameter by lr g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    p = mlp.init_params(rng)
+    g = {k: rng.standard_normal(p[k].shape) for k in mlp.TRAINED}
+    p0 = {k: p[k].copy() for k in mlp.TRAINED}
+    state = {}
+    lr, eps = 1e-3, 1e-8
+    mlp.adam_step(p, g, state, lr, eps=eps)
+    mlp.adam_step(p, g, state, lr, eps=eps)
+    for k in mlp.TRAINED:
+        step = lr * g[k] / (np.abs(g[k]) + eps)
+        assert np.allclose(p[k], p0[k] - 2 * step, rtol=0, atol=1e-12)
+
+
+def test_local_and_global_terms_split_the_membrane_force():
+    w = workload.tiny(seed=4)
+    m = w["mesh"]
+    mesh = oracle.Mesh(m["X0"], m["tri"], m["pairs"], m["node_plt"], m["is_membrane"], m["n_plt"])
+    rng = np.random.default_rng(5)
+    X = w["X"] + 0.03 * rng.standard_normal(w["X"].shape)
+    full = mesh.forces(w["membrane"], X)
+    loc = mesh.forces(mlp.local_params(w["membrane"]), X)
+    glo = mesh.forces(mlp.global_params(w["membrane"]), X)
+    assert np.allclose(loc + glo, full, rtol=0, atol=1e-12 * np.abs(full).max())
+    # the local terms vanish at rest
+    assert np.abs(mesh.forces(mlp.local_params(w["membrane"]), m["X0"])).max() < 1e-12 * np.abs(full).max()
