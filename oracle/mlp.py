@@ -24,7 +24,10 @@ The same construction on the rest positions X0 gives R0, e0_k, and the
 node's length scale l = mean_k |e0_k|.  Then
   delta_k = (R e_k - R0 e0_k) / l          18 inputs (zero for k >= d)
   kappa0  = R0 (mean_k e0_k) / l           3 inputs (rest curvature normal)
-  s_k     = |e_k| / |e0_k| - 1             6 inputs (zero for k >= d)
+  rho_k   = |e0_k| / l                     6 inputs (rest-length ratios,
+                                           zero for k >= d)
+The deformation enters through delta_k only; kappa0 and rho_k describe the
+node's rest one-ring, on which its stiffness depends.
 each multiplied by a fixed per-input scale.  The network output o (3) times a
 fixed per-component scale is the local force in the frame R, so the force is
 R^T (o * out_scale).
@@ -117,7 +120,7 @@ def features(X, X0, ring, deg, nodes):
         ell = L0.mean()
         for k in range(d):
             out[r, 3 * k:3 * k + 3] = (R @ e[k] - R0 @ e0[k]) / ell
-            out[r, 21 + k] = np.linalg.norm(e[k]) / L0[k] - 1.0
+            out[r, 21 + k] = L0[k] / ell
         out[r, 18:21] = R0 @ e0.mean(axis=0) / ell
         frames[r] = R
     return out, frames

@@ -53,7 +53,10 @@ def test_rest_features_and_icosahedron_curvature():
     U, T = ico(0)
     ring, deg = mlp.one_rings(T, len(U))
     f, R = mlp.features(U, U, ring, deg, np.arange(12))
-    assert np.all(np.abs(f[:, :18]) < 1e-14) and np.all(np.abs(f[:, 21:]) < 1e-14)
+    assert np.all(np.abs(f[:, :18]) < 1e-14)
+    # all edges of the regular icosahedron are equal: rest-length ratios 1,
+    # the sixth slot of a degree-5 node empty
+    assert np.allclose(f[:, 21:26], 1.0, atol=1e-14) and np.all(f[:, 26] == 0)
     # regular icosahedron on the unit sphere: the five neighbours sit at
     # polar angle acos(1/sqrt 5), so the mean neighbour offset is
     # (1/sqrt 5 - 1) along the outward normal and the edge is sqrt(2 - 2/sqrt 5)
@@ -90,13 +93,23 @@ def test_features_invariant_and_forces_equivariant_under_rigid_motion():
     assert np.allclose(F2, F1 @ Q.T, atol=1e-12)
 
 
-def test_strain_features_are_stretches():
+def test_uniform_dilation():
+    """Under X -> 1.01 X every edge vector grows by 1 % in an unchanged frame:
+    delta_k = 0.01 R0 e0_k / l, and the rest inputs do not move."""
     U, T = ico(1)
     ring, deg = mlp.one_rings(T, len(U))
+    f0, _ = mlp.features(U, U, ring, deg, np.arange(len(U)))
     f, _ = mlp.features(1.01 * U, U, ring, deg, np.arange(len(U)))
     for i in range(len(U)):
-        assert np.allclose(f[i, 21:21 + deg[i]], 0.01, atol=1e-14)
-        assert np.all(f[i, 21 + deg[i]:] == 0)
+        d = deg[i]
+        nb = ring[i, :d]
+        e0 = U[nb] - U[i]
+        ell = np.linalg.norm(e0, axis=1).mean()
+        R0 = mlp.frame(e0, d)
+        for k in range(d):
+            assert np.allclose(f[i, 3 * k:3 * k + 3], 0.01 * (R0 @ e0[k]) / ell, atol=1e-14)
+        assert np.allclose(f[i, 18:], f0[i, 18:], atol=1e-15)
+        assert np.all(f[i, 3 * d:18] == 0) and np.all(f[i, 21 + d:] == 0)
 
 
 def test_backward_matches_central_differences():
