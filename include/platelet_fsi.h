@@ -269,6 +269,103 @@ int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* strea
 int bonds_status(bond_ctx* ctx, long long* out_host);
 
 /* ===================================================================== *
+ * Learned membrane surrogate (no paper counterpart)
+ *
+ * A per-node network 27 -> 128 -> 128 -> 3 (GELU, tanh form) stands for the
+ * local membrane terms of Section 3.1: edge springs (Eq. 3), the local area
+ * term (Eq. 4, second term) and dihedral bending.  The global area term,
+ * volume (Eq. 5), Morse pairs and wall repulsion stay exact.  Inputs of node
+ * i, from its one-ring n_0..n_{d-1} (d <= 6, counter-clockwise seen from
+ * outside, starting at the neighbour of smallest index), e_k = X[n_k] - X[i],
+ * the frame R (rows x, y, z: z along sum e_k x e_{k+1}, x along e_0 projected
+ * on the tangent plane), the same on the rest shape (R0, e0_k) and the length
+ * l = mean |e0_k|:  (R e_k - R0 e0_k)/l (18), R0 mean(e0_k)/l (3),
+ * |e0_k|/l (6, rest-length ratios), each times in_scale; the local force is
+ * R^T (output * out_scale).
+ *
+ * Parameters: one caller-owned device buffer of PFSI_SG_PARAM_BYTES
+ * (256-byte aligned): PFSI_SG_N_FLOATS floats at offset 0 (the trained block
+ * of PFSI_SG_N_TRAINED floats, then in_scale[32], out_scale[16]), then at the
+ * next 256-byte boundary the BF16 copies the tensor cores read (refresh with
+ * sg_sync_shadows after writing the floats).  Weights are row-major
+ * [outputs][inputs]; padding rows/columns (inputs 27..31, outputs 3..15)
+ * must be zero and stay zero under training.
+ * ===================================================================== */
+#define PFSI_SG_IN 27
+#define PFSI_SG_IN_PAD 32
+#define PFSI_SG_HID 128
+#define PFSI_SG_OUT 3
+#define PFSI_SG_OUT_PAD 16
+#define PFSI_SG_W1 0          /* [128][32] */
+#define PFSI_SG_B1 4096       /* [128] */
+#define PFSI_SG_W2 4224       /* [128][128] */
+#define PFSI_SG_B2 20608      /* [128] */
+#define PFSI_SG_W3 20736      /* [16][128] */
+#define PFSI_SG_B3 22784      /* [16] */
+#define PFSI_SG_N_TRAINED 22800
+#define PFSI_SG_IN_SCALE 22800  /* [32] */
+#define PFSI_SG_OUT_SCALE 22832 /* [16] */
+#define PFSI_SG_N_FLOATS 22848
+#define PFSI_SG_PARAM_BYTES 173312
+#define PFSI_SG_BF16 0  /* BF16 operands on the tensor cores (tcgen05), FP32 accumulation */
+#define PFSI_SG_FP32 1  /* FP32 on CUDA cores: check mode */
+
+typedef struct sg_ctx sg_ctx;
+
+int sg_params_bytes(size_t* bytes);
+/* Rewrites the BF16 copies of W1, W2, W3 (and the transposed copies the
+ * backward pass reads) from the FP32 block. */
+int sg_sync_shadows(void* params, void* stream);
+
+/* Training.  feat: [batch][32] scaled inputs (BF16 for PFSI_SG_BF16, float
+ * for PFSI_SG_FP32; 16-byte aligned), target: float [batch][3] (local-frame
+ * force / out_scale), batch a multiple of 128 (pad with zero rows: they add
+ * nothing to the gradients but count in the mean).  Writes grad
+ * (PFSI_SG_N_TRAINED floats, the trained-block layout) and, if loss is not
+ * NULL, the device double *loss = mean over batch and 3 components of the
+ * squared error.  work: sg_query_work(batch) bytes, 256-byte aligned.
+ * Deterministic (fixed reduction order). */
+int sg_query_work(int batch, size_t* bytes);
+int sg_grad(const void* params, const void* feat, const float* target, int batch, int mode, float* grad,
+            double* loss, void* work, size_t work_bytes, void* stream);
+/* Device error flag of the last sg_grad on this workspace (1: a bounded wait
+ * on the tensor cores gave up).  Synchronises. */
+int sg_work_status(void* work, int batch, int* flag);
+/* One Adam step (Kingma and Ba) of the trained block with moments m, v
+ * (PFSI_SG_N_TRAINED floats each, zero before the first step), step count
+ * t >= 1; refreshes the BF16 copies. */
+int sg_adam(void* params, const float* grad, float* m, float* v, float lr, float beta1, float beta2, float eps,
+            int t, void* stream);
+
+/* Mesh context: one-rings and rest one-ring data of the membrane nodes
+ * (nodes of the triangles; is_membrane may be NULL), computed on the host in
+ * FP64 from X0 (double[3][n_nodes]); tri int[3*n_tri] outward oriented, each
+ * one-ring closed with 3..6 neighbours.  mode: PFSI_SG_BF16 or PFSI_SG_FP32
+ * for sg_membrane_forces.  ws: sg_query_workspace(n_nodes) bytes, 256-byte
+ * aligned, caller-owned (also holds the inference activations). */
+int sg_query_workspace(int n_nodes, size_t* bytes);
+int sg_create(int n_nodes, int n_tri, const int* tri, const double* X0, const unsigned char* is_membrane, int mode,
+              void* ws, size_t ws_bytes, sg_ctx** out);
+int sg_destroy(sg_ctx* ctx);
+/* Number of surrogate nodes (rows) and, optionally, the device array of their
+ * node ids (rows padded to a multiple of 128 with -1). */
+int sg_rows(const sg_ctx* ctx, int* rows, const int** node);
+/* Scaled inputs of every surrogate node at positions X (double[3][n]) into
+ * feat ([rows][32]; BF16 or float by the context's mode; NULL: the
+ * context's own buffer) and frames (float [rows][9], rows of R; NULL: own). */
+int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* frames, void* stream);
+/* F = exact global terms (membrane_forces with the spring, local-area and
+ * bending coefficients set to zero) + surrogate local forces. */
+int sg_membrane_forces(sg_ctx* ctx, const void* params, mem_ctx* mem, const double* X, float* F, void* stream);
+/* Training targets from a force field F (float[3][n], e.g. membrane_forces
+ * with only the local coefficients): target[r] = (R F[node_r]) / out_scale,
+ * float [rows][3]; frames from sg_features (NULL: the context's own). */
+int sg_targets(const sg_ctx* ctx, const void* params, const float* F, const float* frames, float* target,
+               void* stream);
+/* Device error flag of the context's tensor-core kernels.  Synchronises. */
+int sg_status(const sg_ctx* ctx, int* flag);
+
+/* ===================================================================== *
  * Coupled step (Fig. 1)
  * ===================================================================== */
 typedef struct sim_ctx sim_ctx;
@@ -287,6 +384,11 @@ int sim_step(sim_ctx* ctx, int nsteps, void* stream);
 
 /* Index of the next step (first_step + steps taken). */
 int sim_step_index(const sim_ctx* ctx, uint64_t* out);
+
+/* Uses the surrogate for the membrane forces of every following step
+ * (sg_membrane_forces in place of membrane_forces); sg = NULL returns to
+ * the plain solver (the fallback).  The graphs are recaptured. */
+int sim_set_surrogate(sim_ctx* ctx, sg_ctx* sg, const void* params);
 
 /* Measurement aid (no paper counterpart): on != 0 records two CUDA events
  * around the lattice Boltzmann kernel inside the step graph (the graphs are

@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
     const int n = c.n;
     const mem_params P = c.p;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    {
+    if (!c.skip_edges) {
         // batches of four independent loads keep several requests in flight
         int s = c.esl_off[v];
         const int e = c.esl_off[v + 1];
@@ -440,6 +440,17 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s)
     if (rc) return rc;
     k_mem_nodes<<<(c->n + 127) / 128, 128, 0, s>>>(F, *c);
     return check_launch("membrane_forces");
+}
+
+int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s)
+{
+    MemCtx g = *c;
+    g.p.k_spring = 0.f;
+    g.p.k_t = 0.f;
+    g.p.k_b = 0.f;
+    g.ne = 0;            // element ids start at the triangles
+    g.skip_edges = 1;
+    return launch_membrane_forces(&g, X, F, s);
 }
 
 }  // namespace pfsi

@@ -118,6 +118,7 @@ struct MemCtx {
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
     const int2* chunks;    // [n_chunks] (first node, count <= kIbChunk), runs of one platelet
     int n_chunks;
+    int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
     const int* plt_anchor; // [nplt]
     // scratch, rewritten by every call
     double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
@@ -161,11 +162,20 @@ int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,
                      cudaStream_t s);
 int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s);
+// The global terms only (global area, volume, Morse pairs, wall): what the
+// learned surrogate does not stand for.  Writes F.
+int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s);
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
 // step_dev: device step counter (advanced by one after the update) or null
 // to use step_host.
 int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                       unsigned long long* step_dev, cudaStream_t s);
+
+struct SgCtx;
+// Adds the surrogate's local membrane forces to F.
+int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float* F, cudaStream_t s);
+SgCtx* sg_internal(sg_ctx* c);
+int sg_node_count(const SgCtx* c);
 
 }  // namespace pfsi
 

@@ -23,13 +23,21 @@ struct SimCtx {
     cudaStream_t cap;
     cudaGraphExec_t exec[2];
     cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
+    SgCtx* sg;             // learned membrane surrogate, or null (plain solver)
+    const void* sg_params;
 };
 
 namespace {
 
 int enqueue_step(SimCtx* c, cudaStream_t s)
 {
-    int rc = launch_membrane_forces(c->mem, c->X, c->F, s);
+    int rc;
+    if (c->sg) {
+        rc = launch_membrane_global(c->mem, c->X, c->F, s);
+        if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->X, c->F, s);
+    } else {
+        rc = launch_membrane_forces(c->mem, c->X, c->F, s);
+    }
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->lb_ev[0])
@@ -129,6 +137,20 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
         c->lb->cur ^= 1;
         c->step += 1;
     }
+    return PFSI_OK;
+}
+
+extern "C" int sim_set_surrogate(sim_ctx* c, sg_ctx* sg, const void* params)
+{
+    if (!c || (sg && !params)) return set_error(PFSI_ERR_ARG, "sim_set_surrogate: bad argument");
+    SgCtx* g = sg ? sg_internal(sg) : nullptr;
+    if (g && sg_node_count(g) != c->M) return set_error(PFSI_ERR_ARG, "sim_set_surrogate: node count differs");
+    for (int k = 0; k < 2; ++k) {
+        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+        c->exec[k] = nullptr;
+    }
+    c->sg = g;
+    c->sg_params = params;
     return PFSI_OK;
 }
 

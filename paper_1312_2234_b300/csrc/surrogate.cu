@@ -1,0 +1,1172 @@
+// surrogate.cu -- learned membrane-force surrogate for sm_103a (no paper
+// counterpart: a 27 -> 128 -> 128 -> 3 GELU network that stands for the local
+// membrane terms of Section 3.1, springs Eq. 3, local area Eq. 4, bending).
+//
+// Features: one thread per membrane node gathers its one-ring (<= 6 cyclic
+// neighbours), builds the local frame (z along the one-ring normal
+// sum e_k x e_{k+1}, x along the first edge projected on the tangent plane)
+// and writes 27 scaled inputs (edge-vector deviations from the rest one-ring
+// in the local frames; the rest curvature normal and the rest-length ratios,
+// which describe the rest one-ring) plus the frame.
+//
+// Dense layers: one tcgen05 kernel, C = A B^T with both operands BF16 and
+// K-contiguous in global memory (every layer of the forward and backward pass
+// and every weight gradient is such a product; the backward pass keeps
+// transposed copies of the activations for that).  A CTA of 128 threads owns
+// a 128-row tile and all N <= 128 columns, stages 64-wide K chunks of A and B
+// in shared memory in the no-swizzle K-major core-matrix layout (8 rows x 16
+// bytes per core matrix, LBO = 128 B along K, SBO = 1024 B along rows), one
+// elected thread issues the kind::f16 MMAs into an FP32 TMEM accumulator and
+// commits them to an mbarrier per stage (two stages: the next chunk loads
+// while the tensor core works), and every thread then reads its row back
+// with tcgen05.ld and applies a fused epilogue (bias + GELU, GELU' product,
+// output projection to the force, or a split-K partial).  Waits on the
+// mbarriers are bounded; a timeout sets an error flag and the CTA frees its
+// TMEM and returns.
+//
+// An FP32 check path runs the same layer sequence with the same epilogues on
+// CUDA cores (plain dot products, FP32 activations), so the training pipeline
+// can be compared with the FP64 reference at FP32 precision.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "pfsi_internal.cuh"
+
+namespace pfsi {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kIn = PFSI_SG_IN, kInPad = PFSI_SG_IN_PAD, kHid = PFSI_SG_HID, kOut = PFSI_SG_OUT,
+              kOutPad = PFSI_SG_OUT_PAD;
+constexpr int kTile = 128;     // rows per CTA (MMA M)
+constexpr int kChunkK = 64;    // K per shared-memory stage
+constexpr int kMaxSplit = 148;
+
+static_assert(PFSI_SG_W1 == 0 && PFSI_SG_B1 == PFSI_SG_W1 + kHid * kInPad && PFSI_SG_W2 == PFSI_SG_B1 + kHid &&
+                  PFSI_SG_B2 == PFSI_SG_W2 + kHid * kHid && PFSI_SG_W3 == PFSI_SG_B2 + kHid &&
+                  PFSI_SG_B3 == PFSI_SG_W3 + kOutPad * kHid && PFSI_SG_N_TRAINED == PFSI_SG_B3 + kOutPad &&
+                  PFSI_SG_IN_SCALE == PFSI_SG_N_TRAINED && PFSI_SG_OUT_SCALE == PFSI_SG_IN_SCALE + kInPad &&
+                  PFSI_SG_N_FLOATS == PFSI_SG_OUT_SCALE + kOutPad,
+              "parameter layout");
+constexpr size_t kShadowOff = ((size_t)PFSI_SG_N_FLOATS * 4 + 255) / 256 * 256;
+constexpr int hW1 = 0, hW2 = hW1 + kHid * kInPad, hW3 = hW2 + kHid * kHid, hW2t = hW3 + kOutPad * kHid,
+              hW3t = hW2t + kHid * kHid, nShadow = hW3t + kHid * kOutPad;
+static_assert(kShadowOff + (size_t)nShadow * 2 == PFSI_SG_PARAM_BYTES, "parameter buffer size");
+
+struct Params {
+    const float* p;      // FP32 master block
+    const bf16* h;       // BF16 shadows
+};
+inline Params params_of(const void* buf)
+{
+    return {reinterpret_cast<const float*>(buf),
+            reinterpret_cast<const bf16*>(reinterpret_cast<const char*>(buf) + kShadowOff)};
+}
+
+// ------------------------------------------------------------------ GELU (tanh form)
+__device__ __forceinline__ float gelu_f(float z)
+{
+    const float u = 0.7978845608028654f * fmaf(0.044715f * z, z * z, z);
+    return 0.5f * z * (1.0f + tanhf(u));
+}
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    const float u = 0.7978845608028654f * fmaf(0.044715f * z, z * z, z);
+    const float t = tanhf(u);
+    const float du = 0.7978845608028654f * fmaf(3.0f * 0.044715f, z * z, 1.0f);
+    return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
+}
+
+template <class T>
+__device__ __forceinline__ T to_t(float x);
+template <>
+__device__ __forceinline__ float to_t<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ bf16 to_t<bf16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(bf16 x) { return __bfloat162float(x); }
+
+// ------------------------------------------------------------------ epilogues
+// Each is applied to one accumulator element (row, column n) of C = A B^T;
+// `split` is the K-split index of the CTA.
+
+// hidden layer: z = acc + b; h = gelu(z)
+template <class T>
+struct EpiHidden {
+    const float* bias;
+    float* Z;    // [rows][128] pre-activations (null: not kept)
+    T* H;        // [rows][128]
+    T* Ht;       // [128][ldt] (null: no transposed copy)
+    int ldt;
+    __device__ void operator()(int row, int n, float acc, int) const
+    {
+        const float z = acc + bias[n];
+        if (Z) Z[(size_t)row * kHid + n] = z;
+        const float h = gelu_f(z);
+        H[(size_t)row * kHid + n] = to_t<T>(h);
+        if (Ht) Ht[(size_t)n * ldt + row] = to_t<T>(h);
+    }
+};
+
+// output layer: o = acc + b3
+struct EpiOut {
+    const float* bias;
+    float* O;    // [rows][16]
+    __device__ void operator()(int row, int n, float acc, int) const { O[(size_t)row * kOutPad + n] = acc + bias[n]; }
+};
+
+// backward through a hidden layer: dz = acc * gelu'(z)
+template <class T>
+struct EpiBack {
+    const float* Z;
+    T* D;        // [rows][128] (null: not kept)
+    T* Dt;       // [128][ldt]
+    int ldt;
+    __device__ void operator()(int row, int n, float acc, int) const
+    {
+        const float d = acc * gelu_grad_f(Z[(size_t)row * kHid + n]);
+        if (D) D[(size_t)row * kHid + n] = to_t<T>(d);
+        Dt[(size_t)n * ldt + row] = to_t<T>(d);
+    }
+};
+
+// split-K partial of a weight gradient G (ld floats per row, size floats):
+// G[row][n] = acc, or G[n][row] = acc when transposed
+struct EpiPartial {
+    float* part;
+    int ld, size;
+    bool transpose;
+    __device__ void operator()(int row, int n, float acc, int split) const
+    {
+        float* P = part + (size_t)split * size;
+        if (transpose)
+            P[(size_t)n * ld + row] = acc;
+        else
+            P[(size_t)row * ld + n] = acc;
+    }
+};
+
+// surrogate force: F[node] += R^T (o * out_scale), o = acc + b3 (columns 0..2)
+struct EpiForce {
+    const float* bias;
+    const float* out_scale;
+    const float* frames;   // [rows][9] rows x, y, z of R
+    const int* node;       // [rows] node id, -1 for padding rows
+    float* F;              // [3][n]
+    int n;
+    __device__ void row3(int row, float o0, float o1, float o2) const
+    {
+        const int v = node[row];
+        if (v < 0) return;
+        const float* R = frames + (size_t)row * 9;
+        const float a = (o0 + bias[0]) * out_scale[0], b = (o1 + bias[1]) * out_scale[1],
+                    c = (o2 + bias[2]) * out_scale[2];
+        F[v] += R[0] * a + R[3] * b + R[6] * c;
+        F[n + v] += R[1] * a + R[4] * b + R[7] * c;
+        F[2 * n + v] += R[2] * a + R[5] * b + R[8] * c;
+    }
+};
+
+// ------------------------------------------------------------------ tcgen05 / mbarrier helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version bits 46-48 = 0b001
+    return d;                  // base offset 0, relative LBO, swizzle none
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N given.
+__host__ __device__ constexpr uint32_t idesc_bf16(int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Copy rows [0, nrows) x K range [k0, k0 + kc) of a row-major BF16 matrix
+// into the core-matrix layout of one stage (kc a multiple of 16).
+__device__ __forceinline__ void stage_fill(uint8_t* dst, const bf16* __restrict__ src, int ld, int row0, int nrows,
+                                           int k0, int kc)
+{
+    const int cpr = kc >> 3;   // 16-byte chunks per row
+    for (int q = threadIdx.x; q < nrows * cpr; q += kTile) {
+        const int r = q / cpr, kg = q - r * cpr;
+        const uint4 val = *reinterpret_cast<const uint4*>(src + (size_t)(row0 + r) * ld + k0 + 8 * kg);
+        *reinterpret_cast<uint4*>(dst + (((r >> 3) * (kChunkK / 8) + kg) << 7) + ((r & 7) << 4)) = val;
+    }
+}
+
+// C[rows x N] = A[rows x K] B[N x K]^T; grid (rows / 128, splits); each CTA
+// takes K range [split * k_per, min(K, (split + 1) * k_per)).
+template <int N, class Epi>
+__global__ void __launch_bounds__(kTile) k_gemm_tc(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
+                                                   int ldb, int K, int k_per, Epi epi, int* __restrict__ err)
+{
+    static_assert(N == 16 || N == 32 || N == 64 || N == 128, "N");
+    constexpr uint32_t kCols = N < 32 ? 32 : N;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;                                 // 2 stages x 16 KB
+    uint8_t* sB = smem + 2 * kTile * kChunkK * 2;       // 2 stages x N * 128 B
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_sh;
+
+    const int m0 = blockIdx.x * kTile;
+    const int kb = blockIdx.y * k_per, ke = min(K, kb + k_per);
+    const int nchunks = ke > kb ? (ke - kb + kChunkK - 1) / kChunkK : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&tmem_sh, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int s = c & 1;
+        if (c >= 2) ok = mbar_wait(&bar[s], ((c - 2) >> 1) & 1);   // stage s free again
+        if (!ok) break;
+        const int k0 = kb + c * kChunkK, kc = min(kChunkK, ke - k0);
+        stage_fill(sA + s * kTile * kChunkK * 2, A, lda, m0, kTile, k0, kc);
+        stage_fill(sB + s * N * kChunkK * 2, B, ldb, 0, N, k0, kc);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * kTile * kChunkK * 2), b0 = smem_u32(sB + s * N * kChunkK * 2);
+            for (int j = 0; j < kc / 16; ++j)
+                mma_bf16(tmem, smem_desc(a0 + 256 * j, 128, 1024), smem_desc(b0 + 256 * j, 128, 1024), idesc_bf16(N),
+                         (c > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&bar[s]);
+        }
+    }
+    if (ok && nchunks > 0) ok = mbar_wait(&bar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+    tc_fence_after();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = m0 + warp * 32 + lane;
+    if (ok) {
+#pragma unroll 1
+        for (int n0 = 0; n0 < N; n0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
+            if (nchunks == 0)
+                for (int j = 0; j < 16; ++j) v[j] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) epi(row, n0 + j, v[j], blockIdx.y);
+        }
+    } else if (lane == 0) {
+        atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// Output layer with the force epilogue: columns 0..2 of the row.
+template <int N>
+__global__ void __launch_bounds__(kTile) k_gemm_tc_force(const bf16* __restrict__ A, int lda,
+                                                         const bf16* __restrict__ B, int ldb, int K, EpiForce epi,
+                                                         int* __restrict__ err)
+{
+    constexpr uint32_t kCols = 32;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + 2 * kTile * kChunkK * 2;
+    __shared__ uint64_t bar[2];
+    __shared__ uint32_t tmem_sh;
+    const int m0 = blockIdx.x * kTile;
+    const int nchunks = (K + kChunkK - 1) / kChunkK;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&tmem_sh, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int s = c & 1;
+        if (c >= 2) ok = mbar_wait(&bar[s], ((c - 2) >> 1) & 1);
+        if (!ok) break;
+        const int k0 = c * kChunkK, kc = min(kChunkK, K - k0);
+        stage_fill(sA + s * kTile * kChunkK * 2, A, lda, m0, kTile, k0, kc);
+        stage_fill(sB + s * N * kChunkK * 2, B, ldb, 0, N, k0, kc);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * kTile * kChunkK * 2), b0 = smem_u32(sB + s * N * kChunkK * 2);
+            for (int j = 0; j < kc / 16; ++j)
+                mma_bf16(tmem, smem_desc(a0 + 256 * j, 128, 1024), smem_desc(b0 + 256 * j, 128, 1024), idesc_bf16(N),
+                         (c > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&bar[s]);
+        }
+    }
+    if (ok && nchunks > 0) ok = mbar_wait(&bar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+    tc_fence_after();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (ok) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
+        epi.row3(m0 + warp * 32 + lane, v[0], v[1], v[2]);
+    } else if (lane == 0) {
+        atomicExch(err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kCols);
+    }
+}
+
+// FP32 check path: one thread per output element, A(row, k) = A[row*sar + k*sak],
+// B(n, k) = B[n*sbn + k*sbk]; K range per split as in the tensor-core kernel.
+template <class Epi>
+__global__ void k_gemm_f32(const float* __restrict__ A, long long sar, long long sak, const float* __restrict__ B,
+                           long long sbn, long long sbk, int rows, int N, int K, int k_per, Epi epi)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)rows * N) return;
+    const int row = (int)(t / N), n = (int)(t % N);
+    const int kb = blockIdx.y * k_per, ke = min(K, kb + k_per);
+    float acc = 0.f;
+    for (int k = kb; k < ke; ++k) acc = fmaf(A[row * sar + k * sak], B[n * sbn + k * sbk], acc);
+    epi(row, n, acc, blockIdx.y);
+}
+
+__global__ void k_gemm_f32_force(const float* __restrict__ A, const float* __restrict__ W3, int rows, EpiForce epi)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    float o[3];
+    for (int j = 0; j < 3; ++j) {
+        float acc = 0.f;
+        for (int k = 0; k < kHid; ++k) acc = fmaf(A[(size_t)row * kHid + k], W3[j * kHid + k], acc);
+        o[j] = acc;
+    }
+    epi.row3(row, o[0], o[1], o[2]);
+}
+
+// ------------------------------------------------------------------ loss, reductions, Adam
+// dO = 2 (O - T) / (3 B) in columns 0..2 (zero in 3..15), row-major and
+// transposed; loss += sum (O - T)^2 / (3 B).
+template <class T>
+__global__ void k_sg_loss(const float* __restrict__ O, const float* __restrict__ target, int B, int rows,
+                          T* __restrict__ dO, T* __restrict__ dOt, double* __restrict__ loss)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (row < rows) {
+        for (int n = 0; n < kOutPad; ++n) {
+            float d = 0.f;
+            if (n < kOut && row < B) {
+                const float e = O[(size_t)row * kOutPad + n] - target[(size_t)row * kOut + n];
+                d = 2.0f * e / (3.0f * (float)B);
+                sq += (double)e * (double)e;
+            }
+            dO[(size_t)row * kOutPad + n] = to_t<T>(d);
+            dOt[(size_t)n * rows + row] = to_t<T>(d);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(loss, sq / (3.0 * (double)B));
+}
+
+// out[r] = sum over c < cols of M[r * ld + c] (one warp per row, fixed order)
+template <class T>
+__global__ void k_rowsum(const T* __restrict__ M, int rows, int cols, int ld, float* __restrict__ out)
+{
+    const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (r >= rows) return;
+    float s = 0.f;
+    for (int c = threadIdx.x & 31; c < cols; c += 32) s += to_f(M[(size_t)r * ld + c]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) out[r] = s;
+}
+
+__global__ void k_reduce_splits(const float* __restrict__ part, int splits, int count, float* __restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * count + i];
+    out[i] = s;
+}
+
+// features [rows][32] -> transposed copy [32][rows]
+template <class T>
+__global__ void k_transpose_in(const T* __restrict__ X, int rows, T* __restrict__ Xt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * kInPad) return;
+    const int c = t / rows, r = t - c * rows;
+    Xt[t] = X[(size_t)r * kInPad + c];
+}
+
+__global__ void k_sg_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                          float* __restrict__ v, int count, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.0f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.0f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_sg_shadows(const float* __restrict__ p, bf16* __restrict__ h)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHid * kInPad) h[hW1 + i] = __float2bfloat16_rn(p[PFSI_SG_W1 + i]);
+    if (i < kHid * kHid) {
+        h[hW2 + i] = __float2bfloat16_rn(p[PFSI_SG_W2 + i]);
+        const int r = i / kHid, c = i % kHid;   // W2t[c][r] = W2[r][c]
+        h[hW2t + c * kHid + r] = __float2bfloat16_rn(p[PFSI_SG_W2 + i]);
+    }
+    if (i < kOutPad * kHid) {
+        h[hW3 + i] = __float2bfloat16_rn(p[PFSI_SG_W3 + i]);
+        const int r = i / kHid, c = i % kHid;   // W3t[c][r] = W3[r][c]
+        h[hW3t + c * kOutPad + r] = __float2bfloat16_rn(p[PFSI_SG_W3 + i]);
+    }
+}
+
+// ------------------------------------------------------------------ features
+struct SgDev {
+    int n_nodes;          // mesh nodes
+    int rows;             // surrogate nodes
+    int rows_pad;         // multiple of 128
+    const int* node;      // [rows_pad] (-1 padding)
+    const int* ring;      // [rows][6] (-1 padding)
+    const float* rest;    // [rows][32]: c_k (18), kappa0 (3), L0_k / l (6), 1/l
+};
+
+template <class T>
+__global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float* __restrict__ in_scale,
+                              T* __restrict__ feat, float* __restrict__ frames)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int n = d.n_nodes;
+    const int v = d.node[r];
+    const double xi = X[v], yi = X[n + v], zi = X[2 * n + v];
+    float3 e[6];
+    int deg = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int nb = d.ring[6 * r + k];
+        if (nb >= 0) {
+            e[k] = make_float3((float)(X[nb] - xi), (float)(X[n + nb] - yi), (float)(X[2 * n + nb] - zi));
+            deg = k + 1;
+        } else {
+            e[k] = make_float3(0.f, 0.f, 0.f);
+        }
+    }
+    float3 nu = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k < deg) {
+            const float3 a = e[k], b = e[(k + 1) % deg];
+            nu.x += a.y * b.z - a.z * b.y;
+            nu.y += a.z * b.x - a.x * b.z;
+            nu.z += a.x * b.y - a.y * b.x;
+        }
+    }
+    const float inz = rsqrtf(nu.x * nu.x + nu.y * nu.y + nu.z * nu.z);
+    const float3 z = make_float3(nu.x * inz, nu.y * inz, nu.z * inz);
+    const float ez = e[0].x * z.x + e[0].y * z.y + e[0].z * z.z;
+    float3 x = make_float3(e[0].x - ez * z.x, e[0].y - ez * z.y, e[0].z - ez * z.z);
+    const float inx = rsqrtf(x.x * x.x + x.y * x.y + x.z * x.z);
+    x = make_float3(x.x * inx, x.y * inx, x.z * inx);
+    const float3 y = make_float3(z.y * x.z - z.z * x.y, z.z * x.x - z.x * x.z, z.x * x.y - z.y * x.x);
+    const float* rest = d.rest + 32 * (size_t)r;
+    const float inv_l = rest[27];
+    float f[kInPad];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k < deg) {
+            f[3 * k + 0] = (x.x * e[k].x + x.y * e[k].y + x.z * e[k].z) * inv_l - rest[3 * k + 0];
+            f[3 * k + 1] = (y.x * e[k].x + y.y * e[k].y + y.z * e[k].z) * inv_l - rest[3 * k + 1];
+            f[3 * k + 2] = (z.x * e[k].x + z.y * e[k].y + z.z * e[k].z) * inv_l - rest[3 * k + 2];
+        } else {
+            f[3 * k + 0] = f[3 * k + 1] = f[3 * k + 2] = 0.f;
+        }
+        f[21 + k] = rest[21 + k];
+    }
+    f[18] = rest[18];
+    f[19] = rest[19];
+    f[20] = rest[20];
+#pragma unroll
+    for (int k = kIn; k < kInPad; ++k) f[k] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kInPad; ++k) feat[(size_t)r * kInPad + k] = to_t<T>(f[k] * in_scale[k]);
+    float* R = frames + 9 * (size_t)r;
+    R[0] = x.x; R[1] = x.y; R[2] = x.z;
+    R[3] = y.x; R[4] = y.y; R[5] = y.z;
+    R[6] = z.x; R[7] = z.y; R[8] = z.z;
+}
+
+// Training targets: target[r] = (R F[node]) / out_scale (local frame).
+__global__ void k_sg_targets(SgDev d, const float* __restrict__ F, const float* __restrict__ frames,
+                             const float* __restrict__ out_scale, float* __restrict__ target)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const int v = d.node[r], n = d.n_nodes;
+    const float fx = F[v], fy = F[n + v], fz = F[2 * n + v];
+    const float* R = frames + 9 * (size_t)r;
+    target[3 * (size_t)r + 0] = (R[0] * fx + R[1] * fy + R[2] * fz) / out_scale[0];
+    target[3 * (size_t)r + 1] = (R[3] * fx + R[4] * fy + R[5] * fz) / out_scale[1];
+    target[3 * (size_t)r + 2] = (R[6] * fx + R[7] * fy + R[8] * fz) / out_scale[2];
+}
+
+// ------------------------------------------------------------------ host side
+template <int N>
+constexpr size_t gemm_smem() { return 2 * kTile * kChunkK * 2 + 2 * N * kChunkK * 2; }
+
+template <int N, class Epi>
+int smem_attr()
+{
+    return check_cuda(cudaFuncSetAttribute(k_gemm_tc<N, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)gemm_smem<N>()),
+                      "surrogate: gemm shared memory");
+}
+
+// Kernel attributes, set before any launch (and outside graph capture).
+int prepare_tc()
+{
+    int rc = smem_attr<128, EpiHidden<bf16>>();
+    if (!rc) rc = smem_attr<128, EpiBack<bf16>>();
+    if (!rc) rc = smem_attr<128, EpiPartial>();
+    if (!rc) rc = smem_attr<16, EpiOut>();
+    if (!rc) rc = smem_attr<16, EpiPartial>();
+    if (!rc) rc = smem_attr<32, EpiPartial>();
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_gemm_tc_force<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem<16>()),
+                        "surrogate: shared memory");
+    return rc;
+}
+
+template <int N, class Epi>
+int gemm_tc(const bf16* A, int lda, const bf16* B, int ldb, int rows, int K, int splits, Epi epi, int* err,
+            cudaStream_t s)
+{
+    const int k_per = ((K + splits - 1) / splits + kChunkK - 1) / kChunkK * kChunkK;
+    const int used = (K + k_per - 1) / k_per;
+    k_gemm_tc<N, Epi><<<dim3(rows / kTile, used), kTile, gemm_smem<N>(), s>>>(A, lda, B, ldb, K, k_per, epi, err);
+    return check_launch("surrogate: tensor-core layer");
+}
+
+template <class Epi>
+int gemm_f32(const float* A, long long sar, long long sak, const float* B, long long sbn, long long sbk, int rows,
+             int N, int K, int splits, Epi epi, cudaStream_t s)
+{
+    const int k_per = (K + splits - 1) / splits;
+    const int used = (K + k_per - 1) / k_per;
+    const long long total = (long long)rows * N;
+    k_gemm_f32<Epi><<<dim3((unsigned)((total + 255) / 256), used), 256, 0, s>>>(A, sar, sak, B, sbn, sbk, rows, N, K,
+                                                                                k_per, epi);
+    return check_launch("surrogate: FP32 layer");
+}
+
+int splits_for(int K) { return std::max(1, std::min(kMaxSplit, K / 256)); }
+int used_splits(int K, int splits)
+{
+    const int k_per = ((K + splits - 1) / splits + kChunkK - 1) / kChunkK * kChunkK;
+    return (K + k_per - 1) / k_per;
+}
+
+// Training workspace for a batch of `rows` (multiple of 128) samples.
+struct Work {
+    void* Xt;       // [32][rows]
+    float* Z1;      // [rows][128]
+    float* Z2;
+    void* H1;       // [rows][128]
+    void* H2;
+    void* H1t;      // [128][rows]
+    void* H2t;
+    float* O;       // [rows][16]
+    void* dO;       // [rows][16]
+    void* dOt;      // [16][rows]
+    void* dZ2;      // [rows][128]
+    void* dZ2t;     // [128][rows]
+    void* dZ1t;     // [128][rows]
+    float* part;    // [kMaxSplit][128][128]
+    double* loss;
+    int* err;
+    size_t total;
+};
+
+Work work_layout(void* base, int rows)
+{
+    const size_t R = rows;
+    const size_t sizes[] = {4 * 32 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R,
+                            4 * 128 * R, 4 * 16 * R, 4 * 16 * R, 4 * 16 * R, 4 * 128 * R, 4 * 128 * R,
+                            4 * 128 * R, 4 * (size_t)kMaxSplit * 128 * 128, 8, 4};
+    void* ptr[16];
+    size_t o = 0;
+    for (int i = 0; i < 16; ++i) {
+        ptr[i] = base ? (char*)base + o : nullptr;
+        o += (sizes[i] + 255) / 256 * 256;
+    }
+    Work w;
+    w.Xt = ptr[0];
+    w.Z1 = (float*)ptr[1];
+    w.Z2 = (float*)ptr[2];
+    w.H1 = ptr[3];
+    w.H2 = ptr[4];
+    w.H1t = ptr[5];
+    w.H2t = ptr[6];
+    w.O = (float*)ptr[7];
+    w.dO = ptr[8];
+    w.dOt = ptr[9];
+    w.dZ2 = ptr[10];
+    w.dZ2t = ptr[11];
+    w.dZ1t = ptr[12];
+    w.part = (float*)ptr[13];
+    w.loss = (double*)ptr[14];
+    w.err = (int*)ptr[15];
+    w.total = o;
+    return w;
+}
+
+// Forward + backward on a batch; gradients into g (trained-parameter layout).
+int grad_bf16(Params P, const bf16* X, const float* target, int B, int rows, float* g, Work& w, cudaStream_t s)
+{
+    bf16 *Xt = (bf16*)w.Xt, *H1 = (bf16*)w.H1, *H2 = (bf16*)w.H2, *H1t = (bf16*)w.H1t, *H2t = (bf16*)w.H2t;
+    bf16 *dO = (bf16*)w.dO, *dOt = (bf16*)w.dOt, *dZ2 = (bf16*)w.dZ2, *dZ2t = (bf16*)w.dZ2t, *dZ1t = (bf16*)w.dZ1t;
+    int rc = PFSI_OK;
+    k_transpose_in<bf16><<<(rows * kInPad + 255) / 256, 256, 0, s>>>(X, rows, Xt);
+    if ((rc = check_launch("surrogate: transpose"))) return rc;
+    if ((rc = gemm_tc<128>(X, kInPad, P.h + hW1, kInPad, rows, kInPad, 1,
+                           EpiHidden<bf16>{P.p + PFSI_SG_B1, w.Z1, H1, H1t, rows}, w.err, s)))
+        return rc;
+    if ((rc = gemm_tc<128>(H1, kHid, P.h + hW2, kHid, rows, kHid, 1,
+                           EpiHidden<bf16>{P.p + PFSI_SG_B2, w.Z2, H2, H2t, rows}, w.err, s)))
+        return rc;
+    if ((rc = gemm_tc<16>(H2, kHid, P.h + hW3, kHid, rows, kHid, 1, EpiOut{P.p + PFSI_SG_B3, w.O}, w.err, s)))
+        return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(w.loss, 0, sizeof(double), s), "surrogate: clear loss"))) return rc;
+    k_sg_loss<bf16><<<(rows + 127) / 128, 128, 0, s>>>(w.O, target, B, rows, dO, dOt, w.loss);
+    if ((rc = check_launch("surrogate: loss"))) return rc;
+    // dZ2 = (dO W3) * gelu'(Z2); dZ1 = (dZ2 W2) * gelu'(Z1)
+    if ((rc = gemm_tc<128>(dO, kOutPad, P.h + hW3t, kOutPad, rows, kOutPad, 1,
+                           EpiBack<bf16>{w.Z2, dZ2, dZ2t, rows}, w.err, s)))
+        return rc;
+    if ((rc = gemm_tc<128>(dZ2, kHid, P.h + hW2t, kHid, rows, kHid, 1, EpiBack<bf16>{w.Z1, nullptr, dZ1t, rows},
+                           w.err, s)))
+        return rc;
+    // weight gradients, split over the batch
+    const int sp = splits_for(rows);
+    const int u = used_splits(rows, sp);
+    if ((rc = gemm_tc<16>(H2t, rows, dOt, rows, kHid, rows, sp, EpiPartial{w.part, kHid, kOutPad * kHid, true}, w.err, s)))
+        return rc;
+    k_reduce_splits<<<(kOutPad * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kOutPad * kHid, g + PFSI_SG_W3);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    if ((rc = gemm_tc<128>(dZ2t, rows, H1t, rows, kHid, rows, sp, EpiPartial{w.part, kHid, kHid * kHid, false}, w.err, s)))
+        return rc;
+    k_reduce_splits<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kHid, g + PFSI_SG_W2);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    if ((rc = gemm_tc<32>(dZ1t, rows, Xt, rows, kHid, rows, sp, EpiPartial{w.part, kInPad, kHid * kInPad, false}, w.err, s)))
+        return rc;
+    k_reduce_splits<<<(kHid * kInPad + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kInPad, g + PFSI_SG_W1);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    k_rowsum<bf16><<<(kHid + 7) / 8, 256, 0, s>>>(dZ1t, kHid, rows, rows, g + PFSI_SG_B1);
+    k_rowsum<bf16><<<(kHid + 7) / 8, 256, 0, s>>>(dZ2t, kHid, rows, rows, g + PFSI_SG_B2);
+    k_rowsum<bf16><<<(kOutPad + 7) / 8, 256, 0, s>>>(dOt, kOutPad, rows, rows, g + PFSI_SG_B3);
+    return check_launch("surrogate: bias gradients");
+}
+
+int grad_f32(Params P, const float* X, const float* target, int B, int rows, float* g, Work& w, cudaStream_t s)
+{
+    float *Xt = (float*)w.Xt, *H1 = (float*)w.H1, *H2 = (float*)w.H2, *H1t = (float*)w.H1t, *H2t = (float*)w.H2t;
+    float *dO = (float*)w.dO, *dOt = (float*)w.dOt, *dZ2 = (float*)w.dZ2, *dZ2t = (float*)w.dZ2t,
+          *dZ1t = (float*)w.dZ1t;
+    const float* W1 = P.p + PFSI_SG_W1;
+    const float* W2 = P.p + PFSI_SG_W2;
+    const float* W3 = P.p + PFSI_SG_W3;
+    int rc = PFSI_OK;
+    k_transpose_in<float><<<(rows * kInPad + 255) / 256, 256, 0, s>>>(X, rows, Xt);
+    if ((rc = check_launch("surrogate: transpose"))) return rc;
+    if ((rc = gemm_f32(X, kInPad, 1, W1, kInPad, 1, rows, kHid, kInPad, 1,
+                       EpiHidden<float>{P.p + PFSI_SG_B1, w.Z1, H1, H1t, rows}, s)))
+        return rc;
+    if ((rc = gemm_f32(H1, kHid, 1, W2, kHid, 1, rows, kHid, kHid, 1,
+                       EpiHidden<float>{P.p + PFSI_SG_B2, w.Z2, H2, H2t, rows}, s)))
+        return rc;
+    if ((rc = gemm_f32(H2, kHid, 1, W3, kHid, 1, rows, kOutPad, kHid, 1, EpiOut{P.p + PFSI_SG_B3, w.O}, s)))
+        return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(w.loss, 0, sizeof(double), s), "surrogate: clear loss"))) return rc;
+    k_sg_loss<float><<<(rows + 127) / 128, 128, 0, s>>>(w.O, target, B, rows, dO, dOt, w.loss);
+    if ((rc = check_launch("surrogate: loss"))) return rc;
+    // B(n, k) = W3[k][n] (transposed view), W2[k][n]
+    if ((rc = gemm_f32(dO, kOutPad, 1, W3, 1, kHid, rows, kHid, kOutPad, 1, EpiBack<float>{w.Z2, dZ2, dZ2t, rows},
+                       s)))
+        return rc;
+    if ((rc = gemm_f32(dZ2, kHid, 1, W2, 1, kHid, rows, kHid, kHid, 1, EpiBack<float>{w.Z1, nullptr, dZ1t, rows},
+                       s)))
+        return rc;
+    const int sp = splits_for(rows);
+    const int k_per = (rows + sp - 1) / sp;
+    const int u = (rows + k_per - 1) / k_per;
+    if ((rc = gemm_f32(H2t, rows, 1, dOt, rows, 1, kHid, kOutPad, rows, sp, EpiPartial{w.part, kHid, kOutPad * kHid, true},
+                       s)))
+        return rc;
+    k_reduce_splits<<<(kOutPad * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kOutPad * kHid, g + PFSI_SG_W3);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    if ((rc = gemm_f32(dZ2t, rows, 1, H1t, rows, 1, kHid, kHid, rows, sp, EpiPartial{w.part, kHid, kHid * kHid, false}, s)))
+        return rc;
+    k_reduce_splits<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kHid, g + PFSI_SG_W2);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    if ((rc = gemm_f32(dZ1t, rows, 1, Xt, rows, 1, kHid, kInPad, rows, sp, EpiPartial{w.part, kInPad, kHid * kInPad, false},
+                       s)))
+        return rc;
+    k_reduce_splits<<<(kHid * kInPad + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kInPad, g + PFSI_SG_W1);
+    if ((rc = check_launch("surrogate: reduce"))) return rc;
+    k_rowsum<float><<<(kHid + 7) / 8, 256, 0, s>>>(dZ1t, kHid, rows, rows, g + PFSI_SG_B1);
+    k_rowsum<float><<<(kHid + 7) / 8, 256, 0, s>>>(dZ2t, kHid, rows, rows, g + PFSI_SG_B2);
+    k_rowsum<float><<<(kOutPad + 7) / 8, 256, 0, s>>>(dOt, kOutPad, rows, rows, g + PFSI_SG_B3);
+    return check_launch("surrogate: bias gradients");
+}
+
+// ------------------------------------------------------------------ mesh context (host build)
+struct Rest {
+    std::vector<int> node, ring;
+    std::vector<float> rest;
+};
+
+int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned char* is_mem, Rest& R,
+                std::string& err)
+{
+    // around node i, the face (i, a, b) (counter-clockwise) makes b follow a
+    std::vector<std::vector<std::pair<int, int>>> nxt(n);
+    for (int t = 0; t < nt; ++t) {
+        const int v[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+        for (int c = 0; c < 3; ++c) {
+            if (v[c] < 0 || v[c] >= n) {
+                err = "triangle vertex index out of range";
+                return PFSI_ERR_ARG;
+            }
+            nxt[v[c]].push_back({v[(c + 1) % 3], v[(c + 2) % 3]});
+        }
+    }
+    auto P = [&](int v, int c) { return X0[(size_t)c * n + v]; };
+    for (int i = 0; i < n; ++i) {
+        if (nxt[i].empty() || (is_mem && !is_mem[i])) continue;
+        const int d = (int)nxt[i].size();
+        if (d < 3 || d > 6) {
+            err = "a membrane node needs 3 to 6 neighbours";
+            return PFSI_ERR_ARG;
+        }
+        int start = nxt[i][0].first;
+        for (auto& pr : nxt[i]) start = std::min(start, pr.first);
+        int ring[6] = {-1, -1, -1, -1, -1, -1};
+        int cur = start, k = 0;
+        do {
+            if (k >= d) {
+                err = "open or non-manifold one-ring";
+                return PFSI_ERR_ARG;
+            }
+            ring[k++] = cur;
+            int nx = -1;
+            for (auto& pr : nxt[i])
+                if (pr.first == cur) nx = pr.second;
+            if (nx < 0) {
+                err = "open one-ring";
+                return PFSI_ERR_ARG;
+            }
+            cur = nx;
+        } while (cur != start);
+        if (k != d) {
+            err = "one-ring does not close";
+            return PFSI_ERR_ARG;
+        }
+        // rest frame (FP64)
+        double e[6][3], nu[3] = {0, 0, 0};
+        for (int q = 0; q < d; ++q)
+            for (int c = 0; c < 3; ++c) e[q][c] = P(ring[q], c) - P(i, c);
+        for (int q = 0; q < d; ++q) {
+            const double* a = e[q];
+            const double* b = e[(q + 1) % d];
+            nu[0] += a[1] * b[2] - a[2] * b[1];
+            nu[1] += a[2] * b[0] - a[0] * b[2];
+            nu[2] += a[0] * b[1] - a[1] * b[0];
+        }
+        const double nn = std::sqrt(nu[0] * nu[0] + nu[1] * nu[1] + nu[2] * nu[2]);
+        if (!(nn > 0)) {
+            err = "degenerate rest one-ring";
+            return PFSI_ERR_ARG;
+        }
+        const double z[3] = {nu[0] / nn, nu[1] / nn, nu[2] / nn};
+        const double ez = e[0][0] * z[0] + e[0][1] * z[1] + e[0][2] * z[2];
+        double x[3] = {e[0][0] - ez * z[0], e[0][1] - ez * z[1], e[0][2] - ez * z[2]};
+        const double xn = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (double& c : x) c /= xn;
+        const double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+        double L[6], ell = 0, mean[3] = {0, 0, 0};
+        for (int q = 0; q < d; ++q) {
+            L[q] = std::sqrt(e[q][0] * e[q][0] + e[q][1] * e[q][1] + e[q][2] * e[q][2]);
+            ell += L[q] / d;
+            for (int c = 0; c < 3; ++c) mean[c] += e[q][c] / d;
+        }
+        float r32[32] = {};
+        for (int q = 0; q < d; ++q) {
+            r32[3 * q + 0] = (float)((x[0] * e[q][0] + x[1] * e[q][1] + x[2] * e[q][2]) / ell);
+            r32[3 * q + 1] = (float)((y[0] * e[q][0] + y[1] * e[q][1] + y[2] * e[q][2]) / ell);
+            r32[3 * q + 2] = (float)((z[0] * e[q][0] + z[1] * e[q][1] + z[2] * e[q][2]) / ell);
+            r32[21 + q] = (float)(L[q] / ell);
+        }
+        r32[18] = (float)((x[0] * mean[0] + x[1] * mean[1] + x[2] * mean[2]) / ell);
+        r32[19] = (float)((y[0] * mean[0] + y[1] * mean[1] + y[2] * mean[2]) / ell);
+        r32[20] = (float)((z[0] * mean[0] + z[1] * mean[1] + z[2] * mean[2]) / ell);
+        r32[27] = (float)(1.0 / ell);
+        R.node.push_back(i);
+        for (int q = 0; q < 6; ++q) R.ring.push_back(ring[q]);
+        R.rest.insert(R.rest.end(), r32, r32 + 32);
+    }
+    if (R.node.empty()) {
+        err = "no membrane node with a closed one-ring";
+        return PFSI_ERR_ARG;
+    }
+    return PFSI_OK;
+}
+
+struct SgLayout {
+    size_t node, ring, rest, feat, frames, h1, h2, err, total;
+};
+SgLayout sg_layout(int rows)
+{
+    const size_t Rp = ((size_t)rows + kTile - 1) / kTile * kTile;
+    const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 32 * Rp, 4 * 32 * Rp, 4 * 9 * Rp, 4 * 128 * Rp, 4 * 128 * Rp, 4};
+    size_t off[8], o = 0;
+    for (int i = 0; i < 8; ++i) {
+        off[i] = o;
+        o += (sizes[i] + 255) / 256 * 256;
+    }
+    return {off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], o};
+}
+
+}  // namespace
+
+struct SgCtx {
+    SgDev d;
+    int mode;
+    void* ws;
+    SgLayout L;
+    bf16* feat;       // [rows_pad][32] (BF16 mode) / float (FP32 mode)
+    float* frames;    // [rows_pad][9]
+    void* h1;         // [rows_pad][128]
+    void* h2;
+    int* err;
+};
+
+// Surrogate forces added to F (the exact global terms must already be in F).
+int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float* F, cudaStream_t s)
+{
+    const Params P = params_of(params);
+    const int rows = c->d.rows_pad;
+    EpiForce ef{P.p + PFSI_SG_B3, P.p + PFSI_SG_OUT_SCALE, c->frames, c->d.node, F, c->d.n_nodes};
+    int rc;
+    if (c->mode == PFSI_SG_FP32) {
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE,
+                                                                     (float*)c->feat, c->frames);
+        if ((rc = check_launch("surrogate: features"))) return rc;
+        float *H1 = (float*)c->h1, *H2 = (float*)c->h2;
+        if ((rc = gemm_f32((const float*)c->feat, kInPad, 1, P.p + PFSI_SG_W1, kInPad, 1, rows, kHid, kInPad, 1,
+                           EpiHidden<float>{P.p + PFSI_SG_B1, nullptr, H1, nullptr, 0}, s)))
+            return rc;
+        if ((rc = gemm_f32(H1, kHid, 1, P.p + PFSI_SG_W2, kHid, 1, rows, kHid, kHid, 1,
+                           EpiHidden<float>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, s)))
+            return rc;
+        k_gemm_f32_force<<<(rows + 127) / 128, 128, 0, s>>>(H2, P.p + PFSI_SG_W3, rows, ef);
+        return check_launch("surrogate: FP32 output layer");
+    }
+    k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE, c->feat, c->frames);
+    if ((rc = check_launch("surrogate: features"))) return rc;
+    bf16 *H1 = (bf16*)c->h1, *H2 = (bf16*)c->h2;
+    if ((rc = gemm_tc<128>(c->feat, kInPad, P.h + hW1, kInPad, rows, kInPad, 1,
+                           EpiHidden<bf16>{P.p + PFSI_SG_B1, nullptr, H1, nullptr, 0}, c->err, s)))
+        return rc;
+    if ((rc = gemm_tc<128>(H1, kHid, P.h + hW2, kHid, rows, kHid, 1,
+                           EpiHidden<bf16>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, c->err, s)))
+        return rc;
+    k_gemm_tc_force<16><<<rows / kTile, kTile, gemm_smem<16>(), s>>>(H2, kHid, P.h + hW3, kHid, kHid, ef, c->err);
+    return check_launch("surrogate: output layer");
+}
+
+}  // namespace pfsi
+
+using namespace pfsi;
+
+struct sg_ctx : pfsi::SgCtx {};
+
+namespace pfsi {
+SgCtx* sg_internal(sg_ctx* c) { return c; }
+int sg_node_count(const SgCtx* c) { return c->d.n_nodes; }
+}  // namespace pfsi
+
+extern "C" int sg_params_bytes(size_t* bytes)
+{
+    if (!bytes) return set_error(PFSI_ERR_ARG, "sg_params_bytes: null argument");
+    *bytes = PFSI_SG_PARAM_BYTES;
+    return PFSI_OK;
+}
+
+extern "C" int sg_sync_shadows(void* params, void* stream)
+{
+    if (!params || !aligned(params, 256)) return set_error(PFSI_ERR_ARG, "sg_sync_shadows: bad parameter buffer");
+    const Params P = params_of(params);
+    k_sg_shadows<<<(kHid * kHid + 255) / 256, 256, 0, as_stream(stream)>>>(P.p, const_cast<bf16*>(P.h));
+    return check_launch("sg_sync_shadows");
+}
+
+extern "C" int sg_query_work(int batch, size_t* bytes)
+{
+    if (!bytes || batch < 1) return set_error(PFSI_ERR_ARG, "sg_query_work: bad argument");
+    const int rows = (batch + kTile - 1) / kTile * kTile;
+    *bytes = work_layout(nullptr, rows).total;
+    return PFSI_OK;
+}
+
+extern "C" int sg_grad(const void* params, const void* feat, const float* target, int batch, int mode, float* grad,
+                       double* loss, void* work, size_t work_bytes, void* stream)
+{
+    if (!params || !feat || !target || !grad || !work || batch < 1 || (mode != PFSI_SG_BF16 && mode != PFSI_SG_FP32))
+        return set_error(PFSI_ERR_ARG, "sg_grad: bad argument");
+    if (batch % kTile) return set_error(PFSI_ERR_ARG, "sg_grad: batch must be a multiple of 128 (pad the rows)");
+    if (!aligned(params, 256) || !aligned(work, 256) || !aligned(feat, 16))
+        return set_error(PFSI_ERR_ARG, "sg_grad: misaligned buffer");
+    Work w = work_layout(work, batch);
+    if (work_bytes < w.total) return set_error(PFSI_ERR_ARG, "sg_grad: workspace too small");
+    cudaStream_t s = as_stream(stream);
+    int rc = mode == PFSI_SG_BF16 ? prepare_tc() : PFSI_OK;
+    if (!rc) rc = check_cuda(cudaMemsetAsync(w.err, 0, sizeof(int), s), "sg_grad: clear flag");
+    if (rc) return rc;
+    const Params P = params_of(params);
+    rc = mode == PFSI_SG_BF16 ? grad_bf16(P, (const bf16*)feat, target, batch, batch, grad, w, s)
+                              : grad_f32(P, (const float*)feat, target, batch, batch, grad, w, s);
+    if (rc) return rc;
+    if (loss) rc = check_cuda(cudaMemcpyAsync(loss, w.loss, sizeof(double), cudaMemcpyDeviceToDevice, s), "sg_grad");
+    return rc;
+}
+
+extern "C" int sg_work_status(void* work, int batch, int* flag)
+{
+    if (!work || !flag || batch < 1) return set_error(PFSI_ERR_ARG, "sg_work_status: bad argument");
+    const int rows = (batch + kTile - 1) / kTile * kTile;
+    Work w = work_layout(work, rows);
+    return check_cuda(cudaMemcpy(flag, w.err, sizeof(int), cudaMemcpyDeviceToHost), "sg_work_status");
+}
+
+extern "C" int sg_adam(void* params, const float* grad, float* m, float* v, float lr, float beta1, float beta2,
+                       float eps, int t, void* stream)
+{
+    if (!params || !grad || !m || !v || t < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+        !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return set_error(PFSI_ERR_ARG, "sg_adam: bad argument");
+    if (!aligned(params, 256)) return set_error(PFSI_ERR_ARG, "sg_adam: misaligned parameter buffer");
+    cudaStream_t s = as_stream(stream);
+    const float c1 = (float)(1.0 - std::pow((double)beta1, t)), c2 = (float)(1.0 - std::pow((double)beta2, t));
+    k_sg_adam<<<(PFSI_SG_N_TRAINED + 255) / 256, 256, 0, s>>>((float*)params, grad, m, v, PFSI_SG_N_TRAINED, lr, beta1,
+                                                             beta2, eps, c1, c2);
+    int rc = check_launch("sg_adam");
+    if (rc) return rc;
+    return sg_sync_shadows(params, stream);
+}
+
+extern "C" int sg_query_workspace(int n_nodes, size_t* bytes)
+{
+    if (!bytes || n_nodes < 1) return set_error(PFSI_ERR_ARG, "sg_query_workspace: bad argument");
+    *bytes = sg_layout(n_nodes).total;
+    return PFSI_OK;
+}
+
+extern "C" int sg_create(int n_nodes, int n_tri, const int* tri, const double* X0, const unsigned char* is_membrane,
+                         int mode, void* ws, size_t ws_bytes, sg_ctx** out)
+{
+    if (!out || n_nodes < 1 || n_tri < 1 || !tri || !X0 || !ws || (mode != PFSI_SG_BF16 && mode != PFSI_SG_FP32))
+        return set_error(PFSI_ERR_ARG, "sg_create: bad argument");
+    if (!aligned(ws, 256)) return set_error(PFSI_ERR_ARG, "sg_create: workspace must be 256-byte aligned");
+    Rest R;
+    std::string err;
+    int rc = build_rings(n_nodes, n_tri, tri, X0, is_membrane, R, err);
+    if (!rc && mode == PFSI_SG_BF16) rc = prepare_tc();
+    if (rc) return set_error(rc, "sg_create: " + err);
+    const int rows = (int)R.node.size();
+    const SgLayout L = sg_layout(rows);
+    if (ws_bytes < sg_layout(n_nodes).total) return set_error(PFSI_ERR_ARG, "sg_create: workspace too small");
+    const int rows_pad = (rows + kTile - 1) / kTile * kTile;
+    R.node.resize(rows_pad, -1);
+    char* b = (char*)ws;
+    rc = check_cuda(cudaMemset(ws, 0, L.total), "sg_create: clear");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.node, R.node.data(), 4 * R.node.size(), cudaMemcpyHostToDevice), "sg_create");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.ring, R.ring.data(), 4 * R.ring.size(), cudaMemcpyHostToDevice), "sg_create");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.rest, R.rest.data(), 4 * R.rest.size(), cudaMemcpyHostToDevice), "sg_create");
+    if (rc) return rc;
+    sg_ctx* c = new sg_ctx();
+    c->d = SgDev{n_nodes, rows, rows_pad, (const int*)(b + L.node), (const int*)(b + L.ring),
+                 (const float*)(b + L.rest)};
+    c->mode = mode;
+    c->ws = ws;
+    c->L = L;
+    c->feat = (bf16*)(b + L.feat);
+    c->frames = (float*)(b + L.frames);
+    c->h1 = b + L.h1;
+    c->h2 = b + L.h2;
+    c->err = (int*)(b + L.err);
+    *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int sg_destroy(sg_ctx* c)
+{
+    delete c;
+    return PFSI_OK;
+}
+
+extern "C" int sg_rows(const sg_ctx* c, int* rows, const int** node)
+{
+    if (!c || !rows) return set_error(PFSI_ERR_ARG, "sg_rows: null argument");
+    *rows = c->d.rows;
+    if (node) *node = c->d.node;
+    return PFSI_OK;
+}
+
+extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* frames, void* stream)
+{
+    if (!c || !params || !X) return set_error(PFSI_ERR_ARG, "sg_features: null argument");
+    const Params P = params_of(params);
+    cudaStream_t s = as_stream(stream);
+    float* fr = frames ? frames : c->frames;
+    if (c->mode == PFSI_SG_FP32) {
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(
+            X, c->d, P.p + PFSI_SG_IN_SCALE, feat ? (float*)feat : (float*)c->feat, fr);
+    } else {
+        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE,
+                                                                    feat ? (bf16*)feat : c->feat, fr);
+    }
+    return check_launch("sg_features");
+}
+
+extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, const double* X, float* F,
+                                  void* stream)
+{
+    if (!c || !params || !mem || !X || !F) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: null argument");
+    if (mem->n != c->d.n_nodes) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: node count differs");
+    cudaStream_t s = as_stream(stream);
+    int rc = launch_membrane_global(mem, X, F, s);
+    if (rc) return rc;
+    return launch_surrogate_forces(c, params, X, F, s);
+}
+
+extern "C" int sg_targets(const sg_ctx* c, const void* params, const float* F, const float* frames, float* target,
+                          void* stream)
+{
+    if (!c || !params || !F || !target) return set_error(PFSI_ERR_ARG, "sg_targets: null argument");
+    const Params P = params_of(params);
+    k_sg_targets<<<(c->d.rows + 127) / 128, 128, 0, as_stream(stream)>>>(c->d, F, frames ? frames : c->frames,
+                                                                         P.p + PFSI_SG_OUT_SCALE, target);
+    return check_launch("sg_targets");
+}
+
+extern "C" int sg_status(const sg_ctx* c, int* flag)
+{
+    if (!c || !flag) return set_error(PFSI_ERR_ARG, "sg_status: null argument");
+    return check_cuda(cudaMemcpy(flag, c->err, sizeof(int), cudaMemcpyDeviceToHost), "sg_status");
+}

@@ -88,6 +88,21 @@ _SIGS = {
     "sim_step": [P, c_int, P],
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
     "sim_time_lb": [P, c_int],
+    "sim_set_surrogate": [P, P, P],
+    "sg_params_bytes": [ctypes.POINTER(c_size_t)],
+    "sg_sync_shadows": [P, P],
+    "sg_query_work": [c_int, ctypes.POINTER(c_size_t)],
+    "sg_grad": [P, P, P, c_int, c_int, P, P, P, c_size_t, P],
+    "sg_work_status": [P, c_int, ctypes.POINTER(c_int)],
+    "sg_adam": [P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, c_int, P],
+    "sg_query_workspace": [c_int, ctypes.POINTER(c_size_t)],
+    "sg_create": [c_int, c_int, P, P, P, c_int, P, c_size_t, ctypes.POINTER(P)],
+    "sg_destroy": [P],
+    "sg_rows": [P, ctypes.POINTER(c_int), ctypes.POINTER(P)],
+    "sg_features": [P, P, P, P, P, P],
+    "sg_membrane_forces": [P, P, P, P, P, P],
+    "sg_targets": [P, P, P, P, P, P],
+    "sg_status": [P, ctypes.POINTER(c_int)],
     "sim_lb_ms": [P, ctypes.POINTER(ctypes.c_float)],
 }
 
@@ -499,3 +514,147 @@ class Simulation:
         if getattr(self, "h", None) is not None and _lib is not None:
             _lib.sim_destroy(self.h)
             self.h = None
+
+
+# ---------------------------------------------------------------- learned membrane surrogate
+SG_BF16, SG_FP32 = 0, 1
+SG_MODE = {"bf16": SG_BF16, "fp32": SG_FP32}
+SG = dict(IN=27, IN_PAD=32, HID=128, OUT=3, OUT_PAD=16, W1=0, B1=4096, W2=4224, B2=20608, W3=20736, B3=22784,
+          N_TRAINED=22800, IN_SCALE=22800, OUT_SCALE=22832, N_FLOATS=22848, PARAM_BYTES=173312)
+
+
+class SurrogateParams:
+    """Caller-owned parameter buffer of the surrogate (FP32 master block +
+    BF16 copies) with its Adam moments and gradient buffer."""
+
+    def __init__(self, device="cuda"):
+        n = c_size_t()
+        _call("sg_params_bytes", ctypes.byref(n))
+        assert n.value == SG["PARAM_BYTES"]
+        self.buf = _bytes(n.value, device).zero_()
+        self.floats = self.buf[:SG["N_FLOATS"] * 4].view(torch.float32)
+        self.m = torch.zeros(SG["N_TRAINED"], dtype=torch.float32, device=device)
+        self.v = torch.zeros_like(self.m)
+        self.grad = torch.zeros_like(self.m)
+        self.t = 0
+        self.device = device
+
+    def set(self, p):
+        """p: dict of numpy arrays W1 [128][27], b1, W2, b2, W3 [3][128], b3,
+        in_scale [27], out_scale [3] (the reference's layout)."""
+        f = np.zeros(SG["N_FLOATS"], np.float32)
+        W1 = np.zeros((128, 32), np.float32)
+        W1[:, :27] = p["W1"]
+        f[SG["W1"]:SG["B1"]] = W1.ravel()
+        f[SG["B1"]:SG["W2"]] = p["b1"]
+        f[SG["W2"]:SG["B2"]] = np.asarray(p["W2"], np.float32).ravel()
+        f[SG["B2"]:SG["W3"]] = p["b2"]
+        W3 = np.zeros((16, 128), np.float32)
+        W3[:3] = p["W3"]
+        f[SG["W3"]:SG["B3"]] = W3.ravel()
+        f[SG["B3"]:SG["B3"] + 3] = p["b3"]
+        f[SG["IN_SCALE"]:SG["IN_SCALE"] + 27] = p["in_scale"]
+        f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + 3] = p["out_scale"]
+        self.floats.copy_(torch.from_numpy(f))
+        _call("sg_sync_shadows", _ptr(self.buf), None)
+
+    def get(self):
+        f = self.floats.cpu().numpy().astype(np.float64)
+        return dict(W1=f[SG["W1"]:SG["B1"]].reshape(128, 32)[:, :27].copy(), b1=f[SG["B1"]:SG["W2"]].copy(),
+                    W2=f[SG["W2"]:SG["B2"]].reshape(128, 128).copy(), b2=f[SG["B2"]:SG["W3"]].copy(),
+                    W3=f[SG["W3"]:SG["B3"]].reshape(16, 128)[:3].copy(), b3=f[SG["B3"]:SG["B3"] + 3].copy(),
+                    in_scale=f[SG["IN_SCALE"]:SG["IN_SCALE"] + 27].copy(),
+                    out_scale=f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + 3].copy())
+
+    def grads(self):
+        """The last gradient as a dict in the reference's layout."""
+        g = self.grad.cpu().numpy().astype(np.float64)
+        return dict(W1=g[SG["W1"]:SG["B1"]].reshape(128, 32)[:, :27].copy(), b1=g[SG["B1"]:SG["W2"]].copy(),
+                    W2=g[SG["W2"]:SG["B2"]].reshape(128, 128).copy(), b2=g[SG["B2"]:SG["W3"]].copy(),
+                    W3=g[SG["W3"]:SG["B3"]].reshape(16, 128)[:3].copy(), b3=g[SG["B3"]:SG["B3"] + 3].copy())
+
+
+class SurrogateBatch:
+    """Workspace of sg_grad for a fixed batch size (multiple of 128)."""
+
+    def __init__(self, batch, device="cuda"):
+        assert batch % 128 == 0
+        n = c_size_t()
+        _call("sg_query_work", int(batch), ctypes.byref(n))
+        self.batch = batch
+        self.work = _bytes(n.value, device)
+        self.nbytes = n.value
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+
+    def grad(self, params, feat, target, mode="bf16", stream=None):
+        """Gradients into params.grad; returns the device loss tensor."""
+        _call("sg_grad", _ptr(params.buf), _ptr(feat), _ptr(target), self.batch, SG_MODE[mode], _ptr(params.grad),
+              _ptr(self.loss), _ptr(self.work), self.nbytes, _stream(stream))
+        return self.loss
+
+    def status(self):
+        f = c_int()
+        _call("sg_work_status", _ptr(self.work), self.batch, ctypes.byref(f))
+        return f.value
+
+
+def sg_adam(params, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    params.t += 1
+    _call("sg_adam", _ptr(params.buf), _ptr(params.grad), _ptr(params.m), _ptr(params.v), float(lr), float(beta1),
+          float(beta2), float(eps), params.t, _stream(stream))
+
+
+class Surrogate:
+    """Surrogate mesh context (one-rings and rest data of the membrane nodes)."""
+
+    def __init__(self, mesh, mode="bf16", device="cuda"):
+        n = int(np.asarray(mesh["node_plt"]).size)
+        tri = np.ascontiguousarray(mesh["tri"], dtype=np.int32).ravel()
+        X0 = np.ascontiguousarray(mesh["X0"], dtype=np.float64)
+        ism = np.ascontiguousarray(mesh["is_membrane"], dtype=np.uint8)
+        nb = c_size_t()
+        _call("sg_query_workspace", n, ctypes.byref(nb))
+        self.ws = _bytes(nb.value, device)
+        self.mode = mode
+        self.n = n
+        h = c_void_p()
+        _call("sg_create", n, tri.size // 3, _ptr(tri), _ptr(X0), _ptr(ism), SG_MODE[mode], _ptr(self.ws), nb.value,
+              ctypes.byref(h))
+        self.h = h
+        rows = c_int()
+        node = c_void_p()
+        _call("sg_rows", self.h, ctypes.byref(rows), ctypes.byref(node))
+        self.rows = rows.value
+        self.rows_pad = (self.rows + 127) // 128 * 128
+        self.device = device
+
+    def features(self, params, X, stream=None):
+        """(feat [rows_pad][32] BF16 or float, frames [rows_pad][9])."""
+        dt = torch.bfloat16 if self.mode == "bf16" else torch.float32
+        feat = torch.zeros(self.rows_pad, 32, dtype=dt, device=self.device)
+        frames = torch.zeros(self.rows_pad, 9, dtype=torch.float32, device=self.device)
+        _call("sg_features", self.h, _ptr(params.buf), _ptr(X), _ptr(feat), _ptr(frames), _stream(stream))
+        return feat, frames
+
+    def targets(self, params, F, frames, stream=None):
+        t = torch.zeros(self.rows_pad, 3, dtype=torch.float32, device=self.device)
+        _call("sg_targets", self.h, _ptr(params.buf), _ptr(F), _ptr(frames), _ptr(t), _stream(stream))
+        return t
+
+    def forces(self, params, membrane, X, F, stream=None):
+        _call("sg_membrane_forces", self.h, _ptr(params.buf), membrane.h, _ptr(X), _ptr(F), _stream(stream))
+
+    def status(self):
+        f = c_int()
+        _call("sg_status", self.h, ctypes.byref(f))
+        return f.value
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.sg_destroy(self.h)
+            self.h = None
+
+
+def sim_set_surrogate(sim, sg, params):
+    _call("sim_set_surrogate", sim.h, sg.h if sg is not None else None,
+          _ptr(params.buf) if params is not None else None)
