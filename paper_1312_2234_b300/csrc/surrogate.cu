@@ -24,10 +24,17 @@
 // mbarriers are bounded; a timeout sets an error flag and the CTA frees its
 // TMEM and returns.
 //
+// Inference inside the coupled step is one persistent kernel per step: each
+// CTA keeps W1, W2, W3 in shared memory and, per 128-node tile, computes the
+// features into a shared input tile, runs the three layers through TMEM
+// (the GELU epilogues write BF16 activations back to shared memory for the
+// next MMA) and adds R^T (output * out_scale) to the node forces.
+//
 // An FP32 check path runs the same layer sequence with the same epilogues on
 // CUDA cores (plain dot products, FP32 activations), so the training pipeline
 // can be compared with the FP64 reference at FP32 precision.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -70,17 +77,54 @@ inline Params params_of(const void* buf)
 }
 
 // ------------------------------------------------------------------ GELU (tanh form)
+// kFast: the hardware tanh approximation (BF16 mode, where every activation is
+// rounded to BF16 right after); otherwise tanhf (FP32 check mode).
+template <bool kFast>
+__device__ __forceinline__ float tanh_t(float u)
+{
+    if (kFast) {
+        float t;
+        asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+        return t;
+    }
+    return tanhf(u);
+}
+template <bool kFast>
 __device__ __forceinline__ float gelu_f(float z)
 {
     const float u = 0.7978845608028654f * fmaf(0.044715f * z, z * z, z);
-    return 0.5f * z * (1.0f + tanhf(u));
+    return 0.5f * z * (1.0f + tanh_t<kFast>(u));
 }
+template <bool kFast>
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
     const float u = 0.7978845608028654f * fmaf(0.044715f * z, z * z, z);
-    const float t = tanhf(u);
+    const float t = tanh_t<kFast>(u);
     const float du = 0.7978845608028654f * fmaf(3.0f * 0.044715f, z * z, 1.0f);
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * du;
+}
+
+// GELU of 16 pre-activations into 8 BF16 pairs: u = z (c1 + c3 z^2),
+// g = h + h tanh(u) with h = z / 2 (hardware tanh; the result is rounded to
+// BF16 right after).
+__device__ __forceinline__ void gelu16_bf16(const float* z, uint32_t* out)
+{
+    constexpr float c1 = 0.7978845608028654f, c3 = 0.7978845608028654f * 0.044715f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float g[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float x = z[2 * q + e];
+            float t;
+            const float u = x * fmaf(c3, x * x, c1);
+            asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+            const float h = 0.5f * x;
+            g[e] = fmaf(h, t, h);
+        }
+        const __nv_bfloat162 b = __floats2bfloat162_rn(g[0], g[1]);
+        out[q] = *reinterpret_cast<const uint32_t*>(&b);
+    }
 }
 
 template <class T>
@@ -92,13 +136,45 @@ __device__ __forceinline__ bf16 to_t<bf16>(float x) { return __float2bfloat16_rn
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(bf16 x) { return __bfloat162float(x); }
 
+// 16 consecutive values of a row, stored with 16-byte vector stores.
+__device__ __forceinline__ void store16(float* dst, const float* v)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+__device__ __forceinline__ void store16(bf16* dst, const float* v)
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    reinterpret_cast<uint4*>(dst)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    reinterpret_cast<uint4*>(dst)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+__device__ __forceinline__ void load16(const float* src, float* v)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 a = reinterpret_cast<const float4*>(src)[q];
+        v[4 * q] = a.x;
+        v[4 * q + 1] = a.y;
+        v[4 * q + 2] = a.z;
+        v[4 * q + 3] = a.w;
+    }
+}
+
 // ------------------------------------------------------------------ epilogues
-// Each is applied to one accumulator element (row, column n) of C = A B^T;
-// `split` is the K-split index of the CTA.
+// operator() is applied to one accumulator element (row, column n) of
+// C = A B^T (FP32 path); row16 to 16 consecutive columns n0.. of a row
+// (tensor-core path, vector stores).  `split` is the K-split index.
 
 // hidden layer: z = acc + b; h = gelu(z)
 template <class T>
 struct EpiHidden {
+    static constexpr bool kFast = sizeof(T) == 2;
     const float* bias;
     float* Z;    // [rows][128] pre-activations (null: not kept)
     T* H;        // [rows][128]
@@ -108,9 +184,23 @@ struct EpiHidden {
     {
         const float z = acc + bias[n];
         if (Z) Z[(size_t)row * kHid + n] = z;
-        const float h = gelu_f(z);
+        const float h = gelu_f<kFast>(z);
         H[(size_t)row * kHid + n] = to_t<T>(h);
         if (Ht) Ht[(size_t)n * ldt + row] = to_t<T>(h);
+    }
+    __device__ void row16(int row, int n0, const float* v, int) const
+    {
+        float z[16], h[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            z[j] = v[j] + bias[n0 + j];
+            h[j] = gelu_f<kFast>(z[j]);
+        }
+        if (Z) store16(Z + (size_t)row * kHid + n0, z);
+        store16(H + (size_t)row * kHid + n0, h);
+        if (Ht)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) Ht[(size_t)(n0 + j) * ldt + row] = to_t<T>(h[j]);
     }
 };
 
@@ -119,20 +209,38 @@ struct EpiOut {
     const float* bias;
     float* O;    // [rows][16]
     __device__ void operator()(int row, int n, float acc, int) const { O[(size_t)row * kOutPad + n] = acc + bias[n]; }
+    __device__ void row16(int row, int n0, const float* v, int) const
+    {
+        float o[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) o[j] = v[j] + bias[n0 + j];
+        store16(O + (size_t)row * kOutPad + n0, o);
+    }
 };
 
 // backward through a hidden layer: dz = acc * gelu'(z)
 template <class T>
 struct EpiBack {
+    static constexpr bool kFast = sizeof(T) == 2;
     const float* Z;
     T* D;        // [rows][128] (null: not kept)
     T* Dt;       // [128][ldt]
     int ldt;
     __device__ void operator()(int row, int n, float acc, int) const
     {
-        const float d = acc * gelu_grad_f(Z[(size_t)row * kHid + n]);
+        const float d = acc * gelu_grad_f<kFast>(Z[(size_t)row * kHid + n]);
         if (D) D[(size_t)row * kHid + n] = to_t<T>(d);
         Dt[(size_t)n * ldt + row] = to_t<T>(d);
+    }
+    __device__ void row16(int row, int n0, const float* v, int) const
+    {
+        float z[16], d[16];
+        load16(Z + (size_t)row * kHid + n0, z);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) d[j] = v[j] * gelu_grad_f<kFast>(z[j]);
+        if (D) store16(D + (size_t)row * kHid + n0, d);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) Dt[(size_t)(n0 + j) * ldt + row] = to_t<T>(d[j]);
     }
 };
 
@@ -149,6 +257,16 @@ struct EpiPartial {
             P[(size_t)n * ld + row] = acc;
         else
             P[(size_t)row * ld + n] = acc;
+    }
+    __device__ void row16(int row, int n0, const float* v, int split) const
+    {
+        float* P = part + (size_t)split * size;
+        if (transpose) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) P[(size_t)(n0 + j) * ld + row] = v[j];
+        } else {
+            store16(P + (size_t)row * ld + n0, v);
+        }
     }
 };
 
@@ -311,8 +429,10 @@ __global__ void __launch_bounds__(kTile) k_gemm_tc(const bf16* __restrict__ A, i
     bool ok = true;
     for (int c = 0; c < nchunks && ok; ++c) {
         const int s = c & 1;
-        if (c >= 2) ok = mbar_wait(&bar[s], ((c - 2) >> 1) & 1);   // stage s free again
-        if (!ok) break;
+        if (c >= 2) {   // stage s free again (one thread polls)
+            ok = __syncthreads_and(threadIdx.x == 0 ? mbar_wait(&bar[s], ((c - 2) >> 1) & 1) : true) != 0;
+            if (!ok) break;
+        }
         const int k0 = kb + c * kChunkK, kc = min(kChunkK, ke - k0);
         stage_fill(sA + s * kTile * kChunkK * 2, A, lda, m0, kTile, k0, kc);
         stage_fill(sB + s * N * kChunkK * 2, B, ldb, 0, N, k0, kc);
@@ -327,7 +447,9 @@ __global__ void __launch_bounds__(kTile) k_gemm_tc(const bf16* __restrict__ A, i
             mma_commit(&bar[s]);
         }
     }
-    if (ok && nchunks > 0) ok = mbar_wait(&bar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
+    if (ok && nchunks > 0)
+        ok = __syncthreads_and(threadIdx.x == 0 ? mbar_wait(&bar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1)
+                                                : true) != 0;
     tc_fence_after();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = m0 + warp * 32 + lane;
@@ -338,70 +460,8 @@ __global__ void __launch_bounds__(kTile) k_gemm_tc(const bf16* __restrict__ A, i
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0, v);
             if (nchunks == 0)
                 for (int j = 0; j < 16; ++j) v[j] = 0.f;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) epi(row, n0 + j, v[j], blockIdx.y);
+            epi.row16(row, n0, v, blockIdx.y);
         }
-    } else if (lane == 0) {
-        atomicExch(err, 1);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        tc_fence_after();
-        tmem_dealloc(tmem, kCols);
-    }
-}
-
-// Output layer with the force epilogue: columns 0..2 of the row.
-template <int N>
-__global__ void __launch_bounds__(kTile) k_gemm_tc_force(const bf16* __restrict__ A, int lda,
-                                                         const bf16* __restrict__ B, int ldb, int K, EpiForce epi,
-                                                         int* __restrict__ err)
-{
-    constexpr uint32_t kCols = 32;
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + 2 * kTile * kChunkK * 2;
-    __shared__ uint64_t bar[2];
-    __shared__ uint32_t tmem_sh;
-    const int m0 = blockIdx.x * kTile;
-    const int nchunks = (K + kChunkK - 1) / kChunkK;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_barrier_init();
-    }
-    if (threadIdx.x < 32) tmem_alloc(&tmem_sh, kCols);
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_sh;
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-        const int s = c & 1;
-        if (c >= 2) ok = mbar_wait(&bar[s], ((c - 2) >> 1) & 1);
-        if (!ok) break;
-        const int k0 = c * kChunkK, kc = min(kChunkK, K - k0);
-        stage_fill(sA + s * kTile * kChunkK * 2, A, lda, m0, kTile, k0, kc);
-        stage_fill(sB + s * N * kChunkK * 2, B, ldb, 0, N, k0, kc);
-        fence_proxy_async();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + s * kTile * kChunkK * 2), b0 = smem_u32(sB + s * N * kChunkK * 2);
-            for (int j = 0; j < kc / 16; ++j)
-                mma_bf16(tmem, smem_desc(a0 + 256 * j, 128, 1024), smem_desc(b0 + 256 * j, 128, 1024), idesc_bf16(N),
-                         (c > 0 || j > 0) ? 1u : 0u);
-            mma_commit(&bar[s]);
-        }
-    }
-    if (ok && nchunks > 0) ok = mbar_wait(&bar[(nchunks - 1) & 1], ((nchunks - 1) >> 1) & 1);
-    tc_fence_after();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (ok) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), v);
-        epi.row3(m0 + warp * 32 + lane, v[0], v[1], v[2]);
     } else if (lane == 0) {
         atomicExch(err, 1);
     }
@@ -536,12 +596,10 @@ struct SgDev {
     const float* rest;    // [rows][32]: c_k (18), kappa0 (3), L0_k / l (6), 1/l
 };
 
-template <class T>
-__global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float* __restrict__ in_scale,
-                              T* __restrict__ feat, float* __restrict__ frames)
+// Scaled inputs f[32] and frame R[9] (rows x, y, z) of surrogate row r.
+__device__ __forceinline__ void node_features(const double* __restrict__ X, const SgDev& d, int r,
+                                              const float* __restrict__ in_scale, float* f, float* R)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
     const int n = d.n_nodes;
     const int v = d.node[r];
     const double xi = X[v], yi = X[n + v], zi = X[2 * n + v];
@@ -561,7 +619,8 @@ __global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (k < deg) {
-            const float3 a = e[k], b = e[(k + 1) % deg];
+            // cyclic successor without a dynamic index (keeps e[] in registers)
+            const float3 a = e[k], b = (k + 1 < deg && k < 5) ? e[k < 5 ? k + 1 : 0] : e[0];
             nu.x += a.y * b.z - a.z * b.y;
             nu.y += a.z * b.x - a.x * b.z;
             nu.z += a.x * b.y - a.y * b.x;
@@ -574,9 +633,10 @@ __global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float
     const float inx = rsqrtf(x.x * x.x + x.y * x.y + x.z * x.z);
     x = make_float3(x.x * inx, x.y * inx, x.z * inx);
     const float3 y = make_float3(z.y * x.z - z.z * x.y, z.z * x.x - z.x * x.z, z.x * x.y - z.y * x.x);
-    const float* rest = d.rest + 32 * (size_t)r;
+    float rest[32];
+    load16(d.rest + 32 * (size_t)r, rest);
+    load16(d.rest + 32 * (size_t)r + 16, rest + 16);
     const float inv_l = rest[27];
-    float f[kInPad];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (k < deg) {
@@ -594,11 +654,214 @@ __global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float
 #pragma unroll
     for (int k = kIn; k < kInPad; ++k) f[k] = 0.f;
 #pragma unroll
-    for (int k = 0; k < kInPad; ++k) feat[(size_t)r * kInPad + k] = to_t<T>(f[k] * in_scale[k]);
-    float* R = frames + 9 * (size_t)r;
+    for (int k = 0; k < kInPad; ++k) f[k] *= in_scale[k];
     R[0] = x.x; R[1] = x.y; R[2] = x.z;
     R[3] = y.x; R[4] = y.y; R[5] = y.z;
     R[6] = z.x; R[7] = z.y; R[8] = z.z;
+}
+
+template <class T>
+__global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float* __restrict__ in_scale,
+                              T* __restrict__ feat, float* __restrict__ frames)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    float f[kInPad], R[9];
+    node_features(X, d, r, in_scale, f, R);
+    store16(feat + (size_t)r * kInPad, f);
+    store16(feat + (size_t)r * kInPad + 16, f + 16);
+    float* fr = frames + 9 * (size_t)r;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fr[k] = R[k];
+}
+
+// ------------------------------------------------------------------ fused inference
+// Persistent kernel, one CTA of four warpgroups per SM.  Each warpgroup is an
+// independent pipeline over 128-row tiles: it computes the tile's features
+// into its shared input tile A0 (128 x 32), runs the three layers through its
+// 128 TMEM columns (each layer's accumulator overwrites the previous one
+// once the GELU epilogue has read it back; the epilogue writes the BF16
+// activations into its shared hidden tile A1, 128 x 128, for the next MMA)
+// and adds R^T (output * out_scale) to the node forces.  W1, W2, W3 sit once
+// per CTA in shared memory in the core-matrix layout, with the biases folded
+// in as an extra K column (the input tile carries a 1 in column 27, the
+// hidden tile in column 128; K of the hidden layers is padded to 144), so the
+// epilogue is the GELU alone.  Four pipelines per SM keep the tensor core
+// busy while the others gather features or run their epilogues.
+constexpr int kInferWG = 4;
+constexpr int kKb = kHid + 16;                 // hidden K with the bias column (128) and zero padding
+constexpr int kInferW1 = 0;
+constexpr int kInferW2 = kInferW1 + kHid * kInPad * 2;
+constexpr int kInferW3 = kInferW2 + kHid * kKb * 2;
+constexpr int kInferPipe = kInferW3 + kOutPad * kKb * 2;            // first pipeline's tile
+constexpr int kInferPipeBytes = kTile * kKb * 2;                     // A1; A0 aliases its first 8 KB
+constexpr int kInferSmem = kInferPipe + kInferWG * kInferPipeBytes;
+static_assert(kInferSmem <= 227 * 1024, "fused inference shared memory");
+
+// rows x (8 * kgroups) BF16 row-major (leading dimension ld) -> core-matrix
+// layout with dst_kgroups >= kgroups 16-byte groups per 8-row block
+__device__ __forceinline__ void load_core(uint8_t* dst, const bf16* __restrict__ src, int ld, int rows, int kgroups,
+                                          int dst_kgroups)
+{
+    for (int q = threadIdx.x; q < rows * kgroups; q += blockDim.x) {
+        const int r = q / kgroups, kg = q - r * kgroups;
+        *reinterpret_cast<uint4*>(dst + (((r >> 3) * dst_kgroups + kg) << 7) + ((r & 7) << 4)) =
+            *reinterpret_cast<const uint4*>(src + (size_t)r * ld + 8 * kg);
+    }
+}
+
+// Folded bias: K group `kg` of row r (layout with kgroups per block) holds
+// (b, 0, ..., 0); the group after it, if `tail`, zeros.
+__device__ __forceinline__ void put_bias_group(uint8_t* tile, int kgroups, int r, int kg, float b, bool tail)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(b, 0.f);
+    uint8_t* base = tile + (((r >> 3) * kgroups + kg) << 7) + ((r & 7) << 4);
+    *reinterpret_cast<uint4*>(base) = make_uint4(*reinterpret_cast<const uint32_t*>(&h), 0u, 0u, 0u);
+    if (tail) *reinterpret_cast<uint4*>(base + 128) = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// 16 values of a row into a core-matrix tile (kgroups per 8-row block)
+__device__ __forceinline__ void put_row16(uint8_t* tile, int kgroups, int row, int n0, const float* v)
+{
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    uint8_t* base = tile + (((row >> 3) * kgroups + (n0 >> 3)) << 7) + ((row & 7) << 4);
+    *reinterpret_cast<uint4*>(base) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(base + 128) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// barrier and AND-vote over the 128 threads of one warpgroup (named barrier id)
+__device__ __forceinline__ void wg_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ bool wg_and(bool v, int id)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n"
+        ".reg .pred p, q;\n"
+        "setp.ne.u32 p, %1, 0;\n"
+        "bar.red.and.pred q, %2, 128, p;\n"
+        "selp.u32 %0, 1, 0, q;\n"
+        "}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
+__global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const double* __restrict__ X, SgDev d, Params P,
+                                                                  EpiForce ef, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t bars[kInferWG];
+    __shared__ uint32_t tmem_sh;
+    const int wg = threadIdx.x >> 7, t = threadIdx.x & (kTile - 1);
+    const int bar_id = 1 + wg;
+    uint64_t* bar = &bars[wg];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kInferWG; ++k) mbar_init(&bars[k], 1);
+        fence_barrier_init();
+    }
+    if (threadIdx.x < 32) tmem_alloc(&tmem_sh, 512);
+    // weights with the biases folded in: input 27 of A0 and column 128 of the
+    // hidden tile are 1, so W1[:, 27] = b1, W2[:, 128] = b2, W3[:, 128] = b3
+    load_core(smem + kInferW1, P.h + hW1, kInPad, kHid, kInPad / 8, kInPad / 8);
+    load_core(smem + kInferW2, P.h + hW2, kHid, kHid, kHid / 8, kKb / 8);
+    load_core(smem + kInferW3, P.h + hW3, kHid, kOutPad, kHid / 8, kKb / 8);
+    __syncthreads();
+    if (threadIdx.x < kHid) {
+        const int r = threadIdx.x;
+        reinterpret_cast<bf16*>(smem + kInferW1 + (((r >> 3) * (kInPad / 8) + 3) << 7) + ((r & 7) << 4))[3] =
+            __float2bfloat16_rn(P.p[PFSI_SG_B1 + r]);
+        put_bias_group(smem + kInferW2, kKb / 8, r, kHid / 8, P.p[PFSI_SG_B2 + r], true);
+        if (r < kOutPad) put_bias_group(smem + kInferW3, kKb / 8, r, kHid / 8, P.p[PFSI_SG_B3 + r], true);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    // this warpgroup's 128 TMEM columns; a warp reads the 32 lanes of its rows
+    const uint32_t tmem = tmem_sh + (uint32_t)(wg * 128);
+    const uint32_t lanes = tmem + ((uint32_t)((t >> 5) * 32) << 16);
+    uint8_t* A1 = smem + kInferPipe + wg * kInferPipeBytes;
+    uint8_t* A0 = A1;   // the input tile lives in the hidden tile until layer 1 has read it
+    const uint32_t sW1 = smem_u32(smem + kInferW1), sW2 = smem_u32(smem + kInferW2), sW3 = smem_u32(smem + kInferW3);
+    const uint32_t sA0 = smem_u32(A0), sA1 = smem_u32(A1);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int n_tiles = d.rows_pad / kTile;
+    for (int tile = blockIdx.x * kInferWG + wg; tile < n_tiles; tile += gridDim.x * kInferWG) {
+        const int row = tile * kTile + t;
+        float f[kInPad], R[9];
+        if (row < d.rows) {
+            node_features(X, d, row, P.p + PFSI_SG_IN_SCALE, f, R);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kInPad; ++k) f[k] = 0.f;
+        }
+        f[kIn] = 1.0f;   // bias input
+        put_row16(A0, kInPad / 8, t, 0, f);
+        put_row16(A0, kInPad / 8, t, 16, f + 16);
+        for (int layer = 0; layer < 3; ++layer) {
+            fence_proxy_async();
+            tc_fence_before();
+            wg_sync(bar_id);
+            if (t == 0) {
+                tc_fence_after();
+                if (layer == 0) {
+                    for (int j = 0; j < kInPad / 16; ++j)
+                        mma_bf16(tmem, smem_desc(sA0 + 256 * j, 128, 512), smem_desc(sW1 + 256 * j, 128, 512),
+                                 idesc_bf16(kHid), j > 0 ? 1u : 0u);
+                } else {
+                    const uint32_t sW = layer == 1 ? sW2 : sW3;
+                    const uint32_t idesc = idesc_bf16(layer == 1 ? kHid : kOutPad);
+                    for (int j = 0; j < kKb / 16; ++j)
+                        mma_bf16(tmem, smem_desc(sA1 + 256 * j, 128, 128 * (kKb / 8)),
+                                 smem_desc(sW + 256 * j, 128, 128 * (kKb / 8)), idesc, j > 0 ? 1u : 0u);
+                }
+                mma_commit(bar);
+            }
+            // one thread polls the barrier; the others sleep in bar.red and
+            // leave the issue slots to the other pipelines
+            ok = wg_and(t == 0 ? mbar_wait(bar, phase) : true, bar_id);
+            phase ^= 1u;
+            tc_fence_after();
+            if (!ok || layer == 2) break;
+            // GELU epilogue: accumulator (bias included) -> BF16 activations in
+            // A1 (the MMA that read this tile has completed)
+#pragma unroll 1
+            for (int n0 = 0; n0 < kHid; n0 += 16) {
+                float v[16];
+                tmem_ld16(lanes + (uint32_t)n0, v);
+                uint32_t w[8];
+                gelu16_bf16(v, w);
+                uint8_t* base = A1 + (((t >> 3) * (kKb / 8) + (n0 >> 3)) << 7) + ((t & 7) << 4);
+                *reinterpret_cast<uint4*>(base) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(base + 128) = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+            if (layer == 0) put_bias_group(A1, kKb / 8, t, kHid / 8, 1.0f, true);
+        }
+        if (!ok) break;
+        float o[16];
+        tmem_ld16(lanes, o);
+        if (row < d.rows) {
+            const int v = ef.node[row];
+            const float a = o[0] * ef.out_scale[0], b = o[1] * ef.out_scale[1], c = o[2] * ef.out_scale[2];
+            ef.F[v] += R[0] * a + R[3] * b + R[6] * c;
+            ef.F[ef.n + v] += R[1] * a + R[4] * b + R[7] * c;
+            ef.F[2 * ef.n + v] += R[2] * a + R[5] * b + R[8] * c;
+        }
+    }
+    if (!ok && t == 0) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc_fence_after();
+        tmem_dealloc(tmem_sh, 512);
+    }
 }
 
 // Training targets: target[r] = (R F[node]) / out_scale (local frame).
@@ -637,8 +900,7 @@ int prepare_tc()
     if (!rc) rc = smem_attr<16, EpiPartial>();
     if (!rc) rc = smem_attr<32, EpiPartial>();
     if (!rc)
-        rc = check_cuda(cudaFuncSetAttribute(k_gemm_tc_force<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gemm_smem<16>()),
+        rc = check_cuda(cudaFuncSetAttribute(k_sg_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem),
                         "surrogate: shared memory");
     return rc;
 }
@@ -977,17 +1239,11 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float
         k_gemm_f32_force<<<(rows + 127) / 128, 128, 0, s>>>(H2, P.p + PFSI_SG_W3, rows, ef);
         return check_launch("surrogate: FP32 output layer");
     }
-    k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE, c->feat, c->frames);
-    if ((rc = check_launch("surrogate: features"))) return rc;
-    bf16 *H1 = (bf16*)c->h1, *H2 = (bf16*)c->h2;
-    if ((rc = gemm_tc<128>(c->feat, kInPad, P.h + hW1, kInPad, rows, kInPad, 1,
-                           EpiHidden<bf16>{P.p + PFSI_SG_B1, nullptr, H1, nullptr, 0}, c->err, s)))
-        return rc;
-    if ((rc = gemm_tc<128>(H1, kHid, P.h + hW2, kHid, rows, kHid, 1,
-                           EpiHidden<bf16>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, c->err, s)))
-        return rc;
-    k_gemm_tc_force<16><<<rows / kTile, kTile, gemm_smem<16>(), s>>>(H2, kHid, P.h + hW3, kHid, kHid, ef, c->err);
-    return check_launch("surrogate: output layer");
+    const int tiles = rows / kTile;
+    const int want = (tiles + kInferWG - 1) / kInferWG;
+    const int grid = want < 148 ? want : 148;
+    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(X, c->d, P, ef, c->err);
+    return check_launch("surrogate: fused inference");
 }
 
 }  // namespace pfsi
