@@ -126,6 +126,21 @@ int lb_init_shear(lb_ctx* ctx, void* stream);
  * cell is body + g where its row is flagged.  Swaps the current buffer. */
 int lb_step(lb_ctx* ctx, int nsteps, void* stream);
 
+/* Launch shape of lb_step (no paper counterpart; the result does not depend
+ * on it).  FP32 storage: threads per block along x, shape 0..3 = 128, 32,
+ * 64, 256 (capped at nx rounded up to 32).  Mixed storage: the (x, y) column
+ * tile of the marching kernel, shape 0..3 = 32x8, 32x4, 64x4, 16x8.  Default
+ * 0. */
+#define PFSI_LB_SHAPES 4
+int lb_set_shape(lb_ctx* ctx, int shape);
+int lb_get_shape(const lb_ctx* ctx, int* shape);
+/* Autotuner: times every shape over `reps` lattice steps each (CUDA events on
+ * `stream`, after one untimed step per shape), keeps the fastest and returns
+ * its time per step in *best_ms (may be NULL).  The lattice advances by
+ * PFSI_LB_SHAPES * (reps + 1) steps: tune before initialising the state.
+ * Synchronises. */
+int lb_autotune(lb_ctx* ctx, int reps, void* stream, float* best_ms);
+
 /* Device pointer of the buffer holding the current (post-collision) state
  * (FP32 storage only; mixed storage returns PFSI_ERR_ARG, see lb_export). */
 int lb_current(const lb_ctx* ctx, float** f);
@@ -398,6 +413,24 @@ int sim_time_lb(sim_ctx* ctx, int on);
 /* Milliseconds between those two events in the most recent step.
  * Synchronises on the second event. */
 int sim_lb_ms(sim_ctx* ctx, float* ms);
+
+/* ===================================================================== *
+ * Batches of independent chambers (no paper counterpart)
+ * ===================================================================== */
+typedef struct batch_ctx batch_ctx;
+
+/* A batch of n chambers, each a sim_ctx of its own (own lattice, mesh,
+ * bonds, parameters; all at the same lattice-buffer parity).  batch_step
+ * replays one CUDA graph that holds steps_per_graph steps of every chamber,
+ * each chamber's kernels on a parallel branch, so one launch advances all
+ * chambers and their kernels run concurrently.  Each chamber's results are
+ * those of sim_step on it alone.  The sims stay owned by the caller and must
+ * outlive the batch; do not step them on their own while the batch is in
+ * use. */
+int batch_create(sim_ctx** sims, int n, int steps_per_graph, batch_ctx** out);
+int batch_destroy(batch_ctx* ctx);
+/* nsteps (a multiple of steps_per_graph) steps of every chamber. */
+int batch_step(batch_ctx* ctx, int nsteps, void* stream);
 
 #ifdef __cplusplus
 }

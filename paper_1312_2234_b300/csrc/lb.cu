@@ -35,9 +35,10 @@ namespace pfsi {
 
 namespace {
 
-constexpr int kRowBlock = 128;
+constexpr int kRowBlock = 128;     // default threads per block along x (FP32 kernel)
+constexpr int kMaxRowBlock = 256;
 
-__global__ void __launch_bounds__(kRowBlock) k_lb_step(
+__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     const float* __restrict__ fin, float* __restrict__ fout, float4* __restrict__ g,
     float4* __restrict__ vout, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
     float omega, float guo, float3 body, float3 utop)
@@ -153,33 +154,39 @@ __device__ __forceinline__ float feq_shifted(float4 m)
 //   f_q^eq - w_q = w_q (P + rho (c.V)(1 + (c.V)/2)),
 // four operations per pulled population.  The collision uses the same
 // factoring (and 3F for the source term).
-constexpr int kTX = 32, kTY = 8;
-constexpr int kHX = kTX + 2, kHY = kTY + 2;
-constexpr int kPlane = kHX * kHY;
-constexpr int kTileThreads = kTX * kTY;
-constexpr int kHaloPerThread = (kPlane + kTileThreads - 1) / kTileThreads;
+template <int TX_, int TY_>
+struct Tile {
+    static constexpr int TX = TX_, TY = TY_;
+    static constexpr int HX = TX + 2, HY = TY + 2;
+    static constexpr int Plane = HX * HY;
+    static constexpr int Threads = TX * TY;
+    static constexpr int Halo = (Plane + Threads - 1) / Threads;
+};
 constexpr int kSlots = 4;
 
+template <class T>
 struct Ring {
-    float4 pv[kSlots][kPlane];   // (P, Vx, Vy, Vz)
-    float rho[kSlots][kPlane];
+    float4 pv[kSlots][T::Plane];   // (P, Vx, Vy, Vz)
+    float rho[kSlots][T::Plane];
 };
 
+template <class T>
 __device__ __forceinline__ void halo_load(const float4* __restrict__ m, int k, int plane_cells, const int* off,
                                           float4* r)
 {
     const float4* plane = m + (size_t)k * plane_cells;
 #pragma unroll
-    for (int u = 0; u < kHaloPerThread; ++u)
+    for (int u = 0; u < T::Halo; ++u)
         if (off[u] >= 0) r[u] = plane[off[u]];
 }
 
-__device__ __forceinline__ void halo_store(Ring& ring, int slot, const float4* r)
+template <class T>
+__device__ __forceinline__ void halo_store(Ring<T>& ring, int slot, const float4* r)
 {
 #pragma unroll
-    for (int u = 0; u < kHaloPerThread; ++u) {
-        const int h = threadIdx.x + u * kTileThreads;
-        if (h < kPlane) {
+    for (int u = 0; u < T::Halo; ++u) {
+        const int h = threadIdx.x + u * T::Threads;
+        if (h < T::Plane) {
             const float4 m = r[u];
             const float rho = 1.0f + m.w;
             const float vv = m.x * m.x + m.y * m.y + m.z * m.z;
@@ -199,8 +206,8 @@ __device__ __forceinline__ float c_dot(int q, float x, float y, float z)
 }
 
 // f_q^eq - w_q of a ring cell, for direction q.
-template <int q>
-__device__ __forceinline__ float feq_ring(const Ring& ring, int slot, int h)
+template <int q, class T>
+__device__ __forceinline__ float feq_ring(const Ring<T>& ring, int slot, int h)
 {
     const float4 a = ring.pv[slot][h];
     const float cv = c_dot(q, a.y, a.z, a.w);
@@ -210,9 +217,9 @@ __device__ __forceinline__ float feq_ring(const Ring& ring, int slot, int h)
 // f[q] += f_q^eq of the source cell (bounce-back: the own cell's opposite
 // population, plus the moving-wall term at the top).  sm, s0, sp: ring slots
 // of the planes k - 1, k, k + 1.
-template <int q>
-__device__ __forceinline__ void add_feq(float* f, const Ring& ring, int sm, int s0, int sp, int own, int k, int nz,
-                                        float3 utop)
+template <int q, class T>
+__device__ __forceinline__ void add_feq(float* f, const Ring<T>& ring, int sm, int s0, int sp, int own, int k,
+                                        int nz, float3 utop)
 {
     if (czq(q) == 1 && k == 0) {
         f[q] += feq_ring<oppq(q)>(ring, s0, own);
@@ -220,12 +227,12 @@ __device__ __forceinline__ void add_feq(float* f, const Ring& ring, int sm, int 
         const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
         f[q] += feq_ring<oppq(q)>(ring, s0, own) + 6.0f * wq(q) * cu;
     } else {
-        f[q] += feq_ring<q>(ring, czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0), own - cyq(q) * kHX - cxq(q));
+        f[q] += feq_ring<q>(ring, czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0), own - cyq(q) * T::HX - cxq(q));
     }
 }
 
-template <int... Q>
-__device__ __forceinline__ void add_feq_all(std::integer_sequence<int, Q...>, float* f, const Ring& ring, int sm,
+template <class T, int... Q>
+__device__ __forceinline__ void add_feq_all(std::integer_sequence<int, Q...>, float* f, const Ring<T>& ring, int sm,
                                             int s0, int sp, int own, int k, int nz, float3 utop)
 {
     (add_feq<Q>(f, ring, sm, s0, sp, own, k, nz, utop), ...);
@@ -255,15 +262,15 @@ __device__ __forceinline__ float neq_value(uint32_t raw, float inv_scale)
     return __half2float(__ushort_as_half((unsigned short)raw)) * inv_scale;
 }
 
-template <int kMode>
-__global__ void __launch_bounds__(kTileThreads, 3) k_lb_step_mixed(
+template <int kMode, class T>
+__global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
     const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
     float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
     int kz, float omega, float guo, float3 body, float3 utop, float inv_scale)
 {
-    __shared__ Ring ring;
-    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    __shared__ Ring<T> ring;
+    const int tx = threadIdx.x % T::TX, ty = threadIdx.x / T::TX;
+    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
     const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
     const int i = x0 + tx, j = y0 + ty;
     const bool live = i < nx && j < ny;
@@ -275,31 +282,31 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_lb_step_mixed(
     const int yp = (j >= ny - 1) ? 0 : j + 1;
     const float keep = 1.0f - omega;
     const float scale = 1.0f / inv_scale;
-    const int own = (ty + 1) * kHX + tx + 1;
+    const int own = (ty + 1) * T::HX + tx + 1;
 
     // in-plane offsets of this thread's halo cells (wrapped in x and y)
-    int off[kHaloPerThread];
+    int off[T::Halo];
 #pragma unroll
-    for (int u = 0; u < kHaloPerThread; ++u) {
-        const int h = threadIdx.x + u * kTileThreads;
-        const int hy = h / kHX, hx = h - hy * kHX;
+    for (int u = 0; u < T::Halo; ++u) {
+        const int h = threadIdx.x + u * T::Threads;
+        const int hy = h / T::HX, hx = h - hy * T::HX;
         int gx = x0 + hx - 1, gy = y0 + hy - 1;
         gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
         gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
-        off[u] = h < kPlane ? gy * nx + gx : -1;
+        off[u] = h < T::Plane ? gy * nx + gx : -1;
     }
 
-    float4 r[kHaloPerThread];
+    float4 r[T::Halo];
     for (int p = max(z0 - 1, 0); p <= min(z0 + 1, nz - 1); ++p) {
-        halo_load(min_, p, plane_cells, off, r);
-        halo_store(ring, p & 3, r);
+        halo_load<T>(min_, p, plane_cells, off, r);
+        halo_store<T>(ring, p & 3, r);
     }
     __syncthreads();
 
     const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
     for (int k = z0; k < z1; ++k) {
         const bool pre = k + 2 < nz && k + 2 <= z1;
-        if (pre) halo_load(min_, k + 2, plane_cells, off, r);
+        if (pre) halo_load<T>(min_, k + 2, plane_cells, off, r);
         if (live) {
             const int cell = (k * ny + j) * nx + i;
             uint32_t raw[19];
@@ -348,7 +355,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_lb_step_mixed(
             mout[cell] = make_float4(vx * (1.0f / 3.0f), vy * (1.0f / 3.0f), vz * (1.0f / 3.0f), drho);
             if (forced) g[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        if (pre) halo_store(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
+        if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
         __syncthreads();
     }
 }
@@ -480,39 +487,58 @@ float inv_scale_of(const lb_params& p) { return p.storage == PFSI_LB_FP16 ? ldex
 template <int kMode>
 using NeqT = typename Neq<kMode>::T;
 
+// Launch shapes (chosen by lb_set_shape / lb_autotune): FP32, threads per
+// block along x; mixed storage, the (x, y) column tile of the marching kernel.
+constexpr int kFp32Block[PFSI_LB_SHAPES] = {kRowBlock, 32, 64, 256};
+
+template <int kMode, class T>
+void launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+{
+    const lb_params& p = c->p;
+    const int a = c->cur, b = c->cur ^ 1;
+    // columns march through kz planes; kz is picked so that the grid has
+    // about eight blocks of 256 threads per SM (fewer halo planes per cell on
+    // large grids, enough blocks on small ones)
+    const int tiles = ((p.nx + T::TX - 1) / T::TX) * ((p.ny + T::TY - 1) / T::TY);
+    const long long want = 148LL * 8 * 256 / T::Threads;
+    const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
+    const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
+    k_lb_step_mixed<kMode, T><<<grid, T::Threads, 0, s>>>((const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b], c->m[a],
+                                                          c->m[b], c->g, c->flags, p.nx, p.ny, p.nz, kz, omega, guo,
+                                                          body, utop, inv_scale);
+}
+
+template <int kMode>
+void launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+{
+    switch (c->shape) {
+    case 1: launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale); break;
+    case 2: launch_mixed<kMode, Tile<64, 4>>(c, s, omega, guo, body, utop, inv_scale); break;
+    case 3: launch_mixed<kMode, Tile<16, 8>>(c, s, omega, guo, body, utop, inv_scale); break;
+    default: launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
+    }
+}
+
 }  // namespace
 
 int launch_lb_step(LbCtx* c, cudaStream_t s)
 {
     const lb_params& p = c->p;
-    const int bx = p.nx >= kRowBlock ? kRowBlock : ((p.nx + 31) / 32) * 32;
-    const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
     const float omega = 1.0f / p.tau;
     const float guo = 1.0f - 0.5f / p.tau;
     const float3 body = make_float3(p.body[0], p.body[1], p.body[2]);
     const float3 utop = make_float3(p.u_top[0], p.u_top[1], p.u_top[2]);
-    const int a = c->cur, b = c->cur ^ 1;
-    // mixed: 32 x 8 columns, each marching through kz planes; kz is picked so
-    // that the grid has about eight blocks per SM (fewer halo planes per
-    // cell on large grids, enough blocks on small ones)
-    const int tiles = ((p.nx + kTX - 1) / kTX) * ((p.ny + kTY - 1) / kTY);
-    const long long want = 148LL * 8;
-    const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
-    const dim3 mgrid((p.nx + kTX - 1) / kTX, (p.ny + kTY - 1) / kTY, (p.nz + kz - 1) / kz);
     switch (p.storage) {
-    case PFSI_LB_BF16:
-        k_lb_step_mixed<PFSI_LB_BF16><<<mgrid, kTileThreads, 0, s>>>(
-            (const uint16_t*)c->f[a], (NeqT<PFSI_LB_BF16>*)c->f[b], c->m[a], c->m[b], c->g, c->flags, p.nx, p.ny,
-            p.nz, kz, omega, guo, body, utop, 1.0f);
-        break;
-    case PFSI_LB_FP16:
-        k_lb_step_mixed<PFSI_LB_FP16><<<mgrid, kTileThreads, 0, s>>>(
-            (const uint16_t*)c->f[a], (NeqT<PFSI_LB_FP16>*)c->f[b], c->m[a], c->m[b], c->g, c->flags, p.nx, p.ny,
-            p.nz, kz, omega, guo, body, utop, inv_scale_of(p));
-        break;
-    default:
-        k_lb_step<<<grid, bx, 0, s>>>((const float*)c->f[a], (float*)c->f[b], c->g, c->v, c->flags, p.nx, p.ny,
-                                      p.nz, omega, guo, body, utop);
+    case PFSI_LB_BF16: launch_mixed_shape<PFSI_LB_BF16>(c, s, omega, guo, body, utop, 1.0f); break;
+    case PFSI_LB_FP16: launch_mixed_shape<PFSI_LB_FP16>(c, s, omega, guo, body, utop, inv_scale_of(p)); break;
+    default: {
+        const int want = kFp32Block[c->shape];
+        const int cap = ((p.nx + 31) / 32) * 32;
+        const int bx = want < cap ? want : cap;
+        const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
+        k_lb_step<<<grid, bx, 0, s>>>((const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1], c->g, c->v, c->flags,
+                                      p.nx, p.ny, p.nz, omega, guo, body, utop);
+    }
     }
     c->cur ^= 1;
     return check_launch("lb_step");
@@ -647,6 +673,56 @@ extern "C" int lb_current(const lb_ctx* c, float** f)
         return set_error(PFSI_ERR_ARG, "lb_current: mixed storage holds no FP32 populations (use lb_export)");
     *f = (float*)c->f[c->cur];
     return PFSI_OK;
+}
+
+extern "C" int lb_set_shape(lb_ctx* c, int shape)
+{
+    if (!c || shape < 0 || shape >= PFSI_LB_SHAPES) return set_error(PFSI_ERR_ARG, "lb_set_shape: bad argument");
+    c->shape = shape;
+    return PFSI_OK;
+}
+
+extern "C" int lb_get_shape(const lb_ctx* c, int* shape)
+{
+    if (!c || !shape) return set_error(PFSI_ERR_ARG, "lb_get_shape: null argument");
+    *shape = c->shape;
+    return PFSI_OK;
+}
+
+extern "C" int lb_autotune(lb_ctx* c, int reps, void* stream, float* best_ms)
+{
+    if (!c || reps < 1) return set_error(PFSI_ERR_ARG, "lb_autotune: bad argument");
+    cudaStream_t s = as_stream(stream);
+    cudaEvent_t e0, e1;
+    int rc = check_cuda(cudaEventCreate(&e0), "lb_autotune: event");
+    if (rc) return rc;
+    rc = check_cuda(cudaEventCreate(&e1), "lb_autotune: event");
+    if (rc) {
+        cudaEventDestroy(e0);
+        return rc;
+    }
+    int best = 0;
+    float best_t = 0.f;
+    for (int shape = 0; shape < PFSI_LB_SHAPES && !rc; ++shape) {
+        c->shape = shape;
+        rc = launch_lb_step(c, s);
+        if (!rc) rc = check_cuda(cudaEventRecord(e0, s), "lb_autotune: record");
+        for (int r = 0; r < reps && !rc; ++r) rc = launch_lb_step(c, s);
+        if (!rc) rc = check_cuda(cudaEventRecord(e1, s), "lb_autotune: record");
+        if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "lb_autotune: synchronise");
+        float ms = 0.f;
+        if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1), "lb_autotune: elapsed");
+        ms /= reps;
+        if (!rc && (shape == 0 || ms < best_t)) {
+            best = shape;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->shape = best;
+    if (!rc && best_ms) *best_ms = best_t;
+    return rc;
 }
 
 extern "C" int lb_velocity(const lb_ctx* c, float** v)

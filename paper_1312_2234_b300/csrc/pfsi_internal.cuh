@@ -90,6 +90,7 @@ struct LbCtx {
     float4* v;           // FP32 storage: (v, rho) written in forced rows
     float4* m[2];        // mixed storage: (v, rho - 1) of every cell, with f[]
     uint32_t* flags;
+    int shape;           // launch shape of lb_step (0: default), see lb_set_shape
 };
 
 // Velocity field the interpolation reads after a lattice step.

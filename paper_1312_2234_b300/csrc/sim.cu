@@ -7,6 +7,8 @@
 // capture stream and then replayed on the caller's stream, so a step costs
 // one graph launch on the host.  The Philox step index lives in device memory
 // (advanced by the last kernel of a step), so replays need no host updates.
+#include <vector>
+
 #include "pfsi_internal.cuh"
 
 namespace pfsi {
@@ -186,5 +188,129 @@ extern "C" int sim_step_index(const sim_ctx* c, uint64_t* out)
 {
     if (!c || !out) return set_error(PFSI_ERR_ARG, "sim_step_index: null argument");
     *out = c->step;
+    return PFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of independent chambers: one CUDA graph holds `k` steps of every
+// chamber, each chamber's kernel chain captured on its own stream (a parallel
+// branch of the graph), so a single graph launch runs all chambers
+// concurrently and the GPU overlaps their kernels.
+namespace pfsi {
+
+struct BatchCtx {
+    std::vector<SimCtx*> sims;
+    int k;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t cap;
+    cudaEvent_t fork;
+    cudaGraphExec_t exec[2];
+};
+
+namespace {
+
+void batch_free(BatchCtx* b)
+{
+    for (int k = 0; k < 2; ++k)
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+int batch_capture(BatchCtx* b, int parity)
+{
+    std::vector<int> saved;
+    for (SimCtx* c : b->sims) {
+        saved.push_back(c->lb->cur);
+        c->lb->cur = parity;
+    }
+    int rc = check_cuda(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
+    int rc_enq = PFSI_OK;
+    if (!rc) {
+        rc_enq = check_cuda(cudaEventRecord(b->fork, b->cap), "batch: fork");
+        for (size_t i = 0; i < b->sims.size() && !rc_enq; ++i) {
+            rc_enq = check_cuda(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "batch: branch");
+            for (int s = 0; s < b->k && !rc_enq; ++s) rc_enq = enqueue_step(b->sims[i], b->streams[i]);
+            if (!rc_enq) rc_enq = check_cuda(cudaEventRecord(b->join[i], b->streams[i]), "batch: join");
+            if (!rc_enq) rc_enq = check_cuda(cudaStreamWaitEvent(b->cap, b->join[i], 0), "batch: join");
+        }
+        cudaGraph_t graph = nullptr;
+        rc = check_cuda(cudaStreamEndCapture(b->cap, &graph), "batch: end capture");
+        if (!rc && !rc_enq) rc = check_cuda(cudaGraphInstantiate(&b->exec[parity], graph, 0), "batch: instantiate");
+        if (graph) cudaGraphDestroy(graph);
+    }
+    for (size_t i = 0; i < b->sims.size(); ++i) b->sims[i]->lb->cur = saved[i];
+    return rc_enq ? rc_enq : rc;
+}
+
+}  // namespace
+
+}  // namespace pfsi
+
+struct batch_ctx : pfsi::BatchCtx {};
+
+extern "C" int batch_create(sim_ctx** sims, int n, int steps_per_graph, batch_ctx** out)
+{
+    if (!sims || n < 1 || steps_per_graph < 1 || !out) return set_error(PFSI_ERR_ARG, "batch_create: bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!sims[i]) return set_error(PFSI_ERR_ARG, "batch_create: null chamber");
+        if (sims[i]->lb->cur != sims[0]->lb->cur)
+            return set_error(PFSI_ERR_ARG, "batch_create: chambers must be at the same lattice-buffer parity");
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return set_error(PFSI_ERR_ARG, "batch_create: a chamber appears twice");
+    }
+    batch_ctx* b = new batch_ctx();
+    b->k = steps_per_graph;
+    b->cap = nullptr;
+    b->fork = nullptr;
+    b->exec[0] = b->exec[1] = nullptr;
+    int rc = check_cuda(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch_create: stream");
+    if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch_create: event");
+    for (int i = 0; i < n && !rc; ++i) {
+        b->sims.push_back(sims[i]);
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        rc = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "batch_create: stream");
+        if (!rc) b->streams.push_back(s);
+        if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch_create: event");
+        if (!rc) b->join.push_back(e);
+    }
+    if (rc) {
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return PFSI_OK;
+}
+
+extern "C" int batch_destroy(batch_ctx* b)
+{
+    if (!b) return PFSI_OK;
+    batch_free(b);
+    delete b;
+    return PFSI_OK;
+}
+
+extern "C" int batch_step(batch_ctx* b, int nsteps, void* stream)
+{
+    if (!b || nsteps < 0 || nsteps % b->k) return set_error(PFSI_ERR_ARG, "batch_step: nsteps must be a multiple of steps_per_graph");
+    cudaStream_t s = as_stream(stream);
+    for (int done = 0; done < nsteps; done += b->k) {
+        const int parity = b->sims[0]->lb->cur;
+        if (!b->exec[parity]) {
+            const int rc = batch_capture(b, parity);
+            if (rc) return rc;
+        }
+        const int rc = check_cuda(cudaGraphLaunch(b->exec[parity], s), "batch_step: graph launch");
+        if (rc) return rc;
+        for (SimCtx* c : b->sims) {
+            c->lb->cur ^= (b->k & 1);
+            c->step += b->k;
+        }
+    }
     return PFSI_OK;
 }

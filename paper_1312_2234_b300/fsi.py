@@ -89,6 +89,12 @@ _SIGS = {
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
     "sim_time_lb": [P, c_int],
     "sim_set_surrogate": [P, P, P],
+    "lb_set_shape": [P, c_int],
+    "lb_get_shape": [P, ctypes.POINTER(c_int)],
+    "lb_autotune": [P, c_int, P, ctypes.POINTER(ctypes.c_float)],
+    "batch_create": [P, c_int, c_int, ctypes.POINTER(P)],
+    "batch_destroy": [P],
+    "batch_step": [P, c_int, P],
     "sg_params_bytes": [ctypes.POINTER(c_size_t)],
     "sg_sync_shadows": [P, P],
     "sg_query_work": [c_int, ctypes.POINTER(c_size_t)],
@@ -485,10 +491,12 @@ class Bonds:
 class Simulation:
     """The coupled step on one workload (see :mod:`paper_1312_2234_b300.workload`)."""
 
-    def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None):
+    def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None, tune=False):
         g = w["grid"]
         self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device,
                                storage, fp16_exponent)
+        if tune:   # pick the lattice kernel's launch shape for this grid (before the state is set)
+            self.shape, _ = lb_autotune(self.lattice)
         self.lattice.init_shear()
         self.membrane = Membrane(w["membrane"], w["mesh"], device)
         self.M = int(w["M"])
@@ -658,3 +666,39 @@ class Surrogate:
 def sim_set_surrogate(sim, sg, params):
     _call("sim_set_surrogate", sim.h, sg.h if sg is not None else None,
           _ptr(params.buf) if params is not None else None)
+
+
+# ---------------------------------------------------------------- launch shapes, batches
+def lb_autotune(lat, reps=5, stream=None):
+    """Times every launch shape of the lattice step, keeps the fastest;
+    returns (shape, ms per step).  The lattice advances: tune before init."""
+    ms = ctypes.c_float()
+    _call("lb_autotune", lat.h, int(reps), _stream(stream), ctypes.byref(ms))
+    sh = c_int()
+    _call("lb_get_shape", lat.h, ctypes.byref(sh))
+    return sh.value, ms.value
+
+
+def lb_set_shape(lat, shape):
+    _call("lb_set_shape", lat.h, int(shape))
+
+
+class Batch:
+    """Independent chambers stepped by one CUDA graph launch (each chamber's
+    kernels on a parallel branch)."""
+
+    def __init__(self, sims, steps_per_graph=1):
+        self.sims = list(sims)
+        arr = (c_void_p * len(self.sims))(*[s.h.value if isinstance(s.h, c_void_p) else s.h for s in self.sims])
+        h = c_void_p()
+        _call("batch_create", ctypes.cast(arr, c_void_p), len(self.sims), int(steps_per_graph), ctypes.byref(h))
+        self.h = h
+        self.k = steps_per_graph
+
+    def step(self, n=1, stream=None):
+        _call("batch_step", self.h, int(n), _stream(stream))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.batch_destroy(self.h)
+            self.h = None

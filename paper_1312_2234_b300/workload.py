@@ -106,6 +106,16 @@ def lattice_units(tau: float, phys: dict | None = None) -> dict:
 # ---------------------------------------------------------------------------
 def icosphere(level: int):
     """Unit icosphere: 10*4^level + 2 vertices, outward counter-clockwise faces."""
+    if level not in _ICO:
+        _ICO[level] = _icosphere(level)
+    V, F = _ICO[level]
+    return V.copy(), F.copy()
+
+
+_ICO = {}
+
+
+def _icosphere(level: int):
     t = (1.0 + 5.0 ** 0.5) / 2.0
     V = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
          (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
@@ -325,3 +335,35 @@ def tiny(seed=0, nx=24, ny=20, nz=18, level=1, n_sce=8, n_sites=40, n_plt=1, she
     return build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
                  patch=(nx // 4, ny // 4, nx // 2, ny // 2), orient=orient, gap=gap,
                  centers=centers)
+
+
+def config_batched(seed=0, n_chambers=64):
+    """Independent chambers of uneven sizes: each (nx, ny, nz) drawn from
+    48..128, wall shear from 500..3000/s, receptor count from 2000..25000,
+    membrane stiffness (spring constant and Morse depth) scaled by a factor
+    from 0.5..2; one platelet of 2562 membrane nodes and 800 SCE elements per
+    chamber, ligand patch centred on the bottom wall.  Returns the list of
+    chamber workloads."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_chambers):
+        nx, ny, nz = (int(v) for v in rng.integers(48, 129, size=3))
+        shear = float(rng.uniform(500.0, 3000.0))
+        sites = int(rng.integers(2000, 25001))
+        stiff = float(rng.uniform(0.5, 2.0))
+        out.append(build(nx, ny, nz, 0.8, shear, 1, 4, 800, sites, 1000 * seed + c, stiffness=stiff))
+    return out
+
+
+def config_surrogate(seed=0):
+    """Learned-surrogate workload: 256x128x128 channel at wall shear 1500/s,
+    100 platelets of 2562 membrane nodes (no SCE, no receptors), random
+    orientation, centroids within 3 um of the wall."""
+    return build(256, 128, 128, 0.8, 1500.0, 100, 4, 0, 0, seed)
+
+
+def config_full(seed=0, n_plt=500):
+    """Full scale: 512x256x256 channel (33.5 M cells) at wall shear 3000/s,
+    500 platelets of 2562 membrane nodes and 800 SCE elements with 5000
+    receptor sites each."""
+    return build(512, 256, 256, 0.8, 3000.0, n_plt, 4, 800, 5000, seed)
