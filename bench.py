@@ -232,6 +232,11 @@ def run_native(args, rank, ws):
             "bound": sim.bonds.bound.cpu().numpy() if sim.bonds else None}
     mixed = {} if args.no_mixed else {s: run_mixed(args, w, s, dev, flush, stream, snap, ws)
                                       for s in ("bf16", "fp16")}
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = run_batched(args, dev, stream)
+        extras["surrogate"], sg_params = run_surrogate(args, w, sim, dev, stream)
+        extras["full_scale"] = run_full(args, dev, stream, sg_params)
 
     # the dominant kernel where it runs: after the timed region, the same steps
     # with two CUDA events recorded around the lattice kernel inside the step
@@ -300,6 +305,7 @@ def run_native(args, rank, ws):
                                "graph's event-node latency)"},
         "lb_share_of_step": (1e3 * lb_s) / ms_per_step,
         "mixed_precision": {k: dict(v, vs_fp32=v["value"] / value) for k, v in mixed.items()},
+        "configurations": extras,
         "cpu_baseline": base,
         "e2e": e2e,
         "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -357,6 +363,159 @@ def run_mixed(args, w, storage, dev, flush, stream, snap, ws):
             "error_vs_fp32_after_%d_steps" % (args.warmup + args.steps): err}
 
 
+def timed_steps(step, steps, stream):
+    """Device time of `steps` calls of step() (CUDA events, after a sync)."""
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def run_batched(args, dev, stream):
+    """64 independent chambers of uneven sizes (48..128 per side), one
+    platelet each: stepped one chamber at a time (one graph launch per
+    chamber), then as one batch (one graph launch for all chambers), with
+    FP32 populations and with 16-bit f^neq storage (launch shapes tuned per
+    chamber)."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    ws_ = workload.config_batched(seed=0)
+    cells = sum(w["grid"]["nx"] * w["grid"]["ny"] * w["grid"]["nz"] for w in ws_)
+    nodes = sum(w["M"] for w in ws_)
+    steps, warm = max(3, args.steps // 5), 3
+    out = {"workload": "64 chambers, sides 48..128, shear 500..3000/s, 2000..25000 receptors, stiffness x0.5..2, "
+                       "one platelet (2562 + 800 SCE) each", "cells": cells, "nodes": nodes, "steps": steps,
+           "l2": "working set far above L2 (no flush)"}
+    for storage in ("fp32", "bf16", "fp16"):
+        sims = [fsi.Simulation(w, device=dev, storage=storage, tune=storage != "fp32") for w in ws_]
+        if storage == "fp32":
+            for _ in range(warm):
+                for sm in sims:
+                    sm.step(1)
+            t = timed_steps(lambda: [sm.step(1) for sm in sims], steps, stream)
+            out["fp32_one_launch_per_chamber"] = {"value": cells * steps / t / 1e6, "unit": "MLUPS",
+                                                  "ms_per_step": 1e3 * t / steps}
+        batch = fsi.Batch(sims, steps_per_graph=1)
+        batch.step(warm)
+        t = timed_steps(lambda: batch.step(1), steps, stream)
+        out[storage + "_batched"] = {"value": cells * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps,
+                                     "node_updates_per_s": nodes * steps / t}
+        if storage != "fp32":
+            out[storage + "_batched"]["shapes"] = sorted({int(sm.shape) for sm in sims})
+        del batch, sims
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_surrogate(args, w_channel, sim_channel, dev, stream):
+    """The learned membrane surrogate: trained on the channel's own trajectory
+    (its current state plus perturbed copies), then the 256x128x128 channel
+    with 100 platelets stepped with the plain membrane solver and with the
+    surrogate (plain solver kept as the judge of its force error)."""
+    import time as _t
+    import torch
+    from paper_1312_2234_b300 import fsi, surrogate, workload
+    rng = np.random.default_rng(0)
+    m = w_channel["mesh"]
+    t0 = _t.perf_counter()
+    params = fsi.SurrogateParams(device=dev)
+    params.set(surrogate.init_params(rng))
+    sg_c = fsi.Surrogate(m, "bf16", device=dev)
+    loc = fsi.Membrane(surrogate.local_params(w_channel["membrane"]), m, device=dev)
+    # trajectory snapshots of the channel (every 200 steps over 2000 more
+    # steps of the plain method), each with a few perturbed copies
+    snaps = [w_channel["X"]]
+    for _ in range(10):
+        sim_channel.step(200)
+        snaps.append(sim_channel.X.cpu().numpy())
+    states = surrogate.perturbed_states(snaps, m, amplitudes=(0.003, 0.03), copies=2, rng=rng)
+    surrogate.fit_scales(sg_c, params, loc, states)
+    data = surrogate.Dataset(sg_c, params, loc, states, device=dev)
+    train_steps = 1500
+    hist = surrogate.train(params, data, train_steps, batch=4096, lr=2e-3, log_every=500)
+    torch.cuda.synchronize()
+    t_train = _t.perf_counter() - t0
+    w4 = workload.config_surrogate(seed=0)
+    N = w4["grid"]["nx"] * w4["grid"]["ny"] * w4["grid"]["nz"]
+    steps, warm = max(3, args.steps // 5), 3
+    out = {"workload": "256x128x128 channel, shear 1500/s, 100 platelets x 2562 nodes", "cells": N,
+           "nodes": w4["M"], "steps": steps,
+           "training": {"samples": len(data), "steps": train_steps, "batch": 4096, "seconds": t_train,
+                        "loss_first": hist[0][1], "loss_last": hist[-1][1],
+                        "data": "channel trajectory (11 snapshots over 2000 steps of the plain method) + 2 "
+                                "Gaussian perturbations of 0.3 % and of 3 % of the mean edge per snapshot"}}
+    sg4 = fsi.Surrogate(w4["mesh"], "bf16", device=dev)
+    plain = fsi.Membrane(w4["membrane"], w4["mesh"], device=dev)
+    for mode in ("plain", "surrogate"):
+        sim = fsi.Simulation(w4, device=dev)
+        if mode == "surrogate":
+            fsi.sim_set_surrogate(sim, sg4, params)
+        sim.step(warm)
+        t = timed_steps(lambda: sim.step(1), steps, stream)
+        out[mode] = {"value": N * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps}
+        if mode == "surrogate":
+            sim.step(500)   # let the flow deform the platelets before judging the force
+            Fp = torch.zeros(3 * w4["M"], device=dev)
+            Fs = torch.zeros_like(Fp)
+            Fl = torch.zeros_like(Fp)
+            plain.forces(sim.X, Fp)
+            sg4.forces(params, plain, sim.X, Fs)
+            fsi.Membrane(surrogate.local_params(w4["membrane"]), w4["mesh"], device=dev).forces(sim.X, Fl)
+            mask = torch.as_tensor(np.asarray(w4["mesh"]["is_membrane"]).astype(bool), device=dev)
+            out["force_error"] = {
+                "local_max_rel": surrogate.rel_force_error(Fs - Fp + Fl, Fl, mask),
+                "total_max_rel": surrogate.rel_force_error(Fs, Fp, mask),
+                "note": "surrogate vs plain membrane force after %d steps on the surrogate; local = springs "
+                        "+ local area + bending, total adds the exact global terms" % (warm + steps + 500)}
+            out["membrane_us"] = {
+                "plain": 1e6 * timed_steps(lambda: plain.forces(sim.X, Fp), 20, stream) / 20,
+                "surrogate": 1e6 * timed_steps(lambda: sg4.forces(params, plain, sim.X, Fs), 20, stream) / 20}
+        del sim
+    out["vs_plain"] = out["surrogate"]["value"] / out["plain"]["value"]
+    return out, params
+
+
+def run_full(args, dev, stream, sg_params):
+    """Full scale: 512x256x256 channel (33.5 M cells), 500 platelets with SCE
+    and receptors, shear 3000/s: the plain FP32 form against BF16 populations
+    with the learned surrogate (Philox bonds in both)."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    w5 = workload.config_full(seed=0)
+    N = w5["grid"]["nx"] * w5["grid"]["ny"] * w5["grid"]["nz"]
+    steps, warm = 3, 3
+    out = {"workload": "512x256x256 channel, shear 3000/s, 500 platelets x (2562 + 800 SCE), 5000 receptors each",
+           "cells": N, "nodes": w5["M"], "sites": int(len(w5["sites"]["tri"])), "steps": steps}
+    snap = None
+    for mode in ("fp32_plain", "bf16_surrogate"):
+        storage = "fp32" if mode == "fp32_plain" else "bf16"
+        sim = fsi.Simulation(w5, device=dev, storage=storage, tune=storage != "fp32")
+        if mode == "bf16_surrogate":
+            sg5 = fsi.Surrogate(w5["mesh"], "bf16", device=dev)
+            fsi.sim_set_surrogate(sim, sg5, sg_params)
+        sim.step(warm)
+        t = timed_steps(lambda: sim.step(1), steps, stream)
+        out[mode] = {"value": N * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps}
+        U = sim.U.cpu().numpy()
+        bonds = int((sim.bonds.bound >= 0).sum().item()) if sim.bonds is not None else 0
+        if snap is None:
+            snap = (U, bonds)
+        else:
+            out[mode]["node_velocity_rel_vs_fp32"] = float(np.abs(U - snap[0]).max() / max(np.abs(snap[0]).max(), 1e-30))
+            out[mode]["bonds"] = bonds
+            out[mode]["bonds_fp32"] = snap[1]
+        del sim
+        torch.cuda.empty_cache()
+    out["vs_fp32"] = out["bf16_surrogate"]["value"] / out["fp32_plain"]["value"]
+    return out
+
+
 def run_lb_only(args):
     """The lattice kernel alone on a grid of the caller's size (profiling aid:
     a grid larger than L2 makes its DRAM figures meaningful).  Prints one
@@ -405,6 +564,8 @@ def main():
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variants")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, surrogate and full-scale configurations")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

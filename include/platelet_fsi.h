@@ -294,9 +294,11 @@ int bonds_status(bond_ctx* ctx, long long* out_host);
  * outside, starting at the neighbour of smallest index), e_k = X[n_k] - X[i],
  * the frame R (rows x, y, z: z along sum e_k x e_{k+1}, x along e_0 projected
  * on the tangent plane), the same on the rest shape (R0, e0_k) and the length
- * l = mean |e0_k|:  (R e_k - R0 e0_k)/l (18), R0 mean(e0_k)/l (3),
- * |e0_k|/l (6, rest-length ratios), each times in_scale; the local force is
- * R^T (output * out_scale).
+ * l = mean |e0_k|:  with delta_k = (R e_k - R0 e0_k)/l and mag = |delta|,
+ * delta_k / mag (18; 0 at rest), R0 mean(e0_k)/l (3), |e0_k|/l (6,
+ * rest-length ratios), each times in_scale; the local force is
+ * R^T (output * mag * out_scale): zero at rest, homogeneous of degree one in
+ * the deformation (the linear-elastic response).
  *
  * Parameters: one caller-owned device buffer of PFSI_SG_PARAM_BYTES
  * (256-byte aligned): PFSI_SG_N_FLOATS floats at offset 0 (the trained block
@@ -367,16 +369,19 @@ int sg_destroy(sg_ctx* ctx);
 int sg_rows(const sg_ctx* ctx, int* rows, const int** node);
 /* Scaled inputs of every surrogate node at positions X (double[3][n]) into
  * feat ([rows][32]; BF16 or float by the context's mode; NULL: the
- * context's own buffer) and frames (float [rows][9], rows of R; NULL: own). */
-int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* frames, void* stream);
+ * context's own buffer), frames (float [rows][9], rows of R; NULL: own) and
+ * mags (float [rows], deformation magnitude; NULL: own). */
+int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* frames, float* mags,
+                void* stream);
 /* F = exact global terms (membrane_forces with the spring, local-area and
  * bending coefficients set to zero) + surrogate local forces. */
 int sg_membrane_forces(sg_ctx* ctx, const void* params, mem_ctx* mem, const double* X, float* F, void* stream);
 /* Training targets from a force field F (float[3][n], e.g. membrane_forces
- * with only the local coefficients): target[r] = (R F[node_r]) / out_scale,
- * float [rows][3]; frames from sg_features (NULL: the context's own). */
-int sg_targets(const sg_ctx* ctx, const void* params, const float* F, const float* frames, float* target,
-               void* stream);
+ * with only the local coefficients): target[r] = (R F[node_r]) /
+ * (mag_r out_scale), 0 where mag_r = 0, float [rows][3]; frames and mags
+ * from sg_features (NULL: the context's own). */
+int sg_targets(const sg_ctx* ctx, const void* params, const float* F, const float* frames, const float* mags,
+               float* target, void* stream);
 /* Device error flag of the context's tensor-core kernels.  Synchronises. */
 int sg_status(const sg_ctx* ctx, int* flag);
 

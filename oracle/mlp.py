@@ -22,15 +22,20 @@ clockwise seen from outside, starting at the neighbour of smallest index):
   x = unit(e_0 - (e_0.z) z);  y = z x x;  R = rows (x, y, z).
 The same construction on the rest positions X0 gives R0, e0_k, and the
 node's length scale l = mean_k |e0_k|.  Then
-  delta_k = (R e_k - R0 e0_k) / l          18 inputs (zero for k >= d)
+  delta_k = (R e_k - R0 e0_k) / l,  mag = |(delta_0 .. delta_5)|
+  delta_k / mag                            18 inputs (zero for k >= d, and
+                                           all zero when mag = 0)
   kappa0  = R0 (mean_k e0_k) / l           3 inputs (rest curvature normal)
   rho_k   = |e0_k| / l                     6 inputs (rest-length ratios,
                                            zero for k >= d)
-The deformation enters through delta_k only; kappa0 and rho_k describe the
-node's rest one-ring, on which its stiffness depends.
-each multiplied by a fixed per-input scale.  The network output o (3) times a
-fixed per-component scale is the local force in the frame R, so the force is
-R^T (o * out_scale).
+each multiplied by a fixed per-input scale.  The deformation enters through
+the direction delta / mag and the magnitude mag; kappa0 and rho_k describe
+the node's rest one-ring, on which its stiffness depends.  The network output
+o (3) times mag times a fixed per-component scale is the local force in the
+frame R: the force is R^T (o * mag * out_scale), zero at rest and
+homogeneous of degree one in the deformation, as the local membrane forces
+are in the linear-elastic range (where the strains of a platelet in shear
+flow lie).
 
 It shares no code with the CUDA library.
 """
@@ -105,10 +110,11 @@ def frame(e, d):
 
 
 def features(X, X0, ring, deg, nodes):
-    """Unscaled features [len(nodes)][27] and frames [len(nodes)][3][3].
-    X, X0: positions [n][3]."""
+    """Unscaled features [len(nodes)][27], frames [len(nodes)][3][3] and
+    deformation magnitudes [len(nodes)].  X, X0: positions [n][3]."""
     out = np.zeros((len(nodes), N_IN))
     frames = np.zeros((len(nodes), 3, 3))
+    mags = np.zeros(len(nodes))
     for r, i in enumerate(nodes):
         d = int(deg[i])
         nb = ring[i, :d]
@@ -121,9 +127,12 @@ def features(X, X0, ring, deg, nodes):
         for k in range(d):
             out[r, 3 * k:3 * k + 3] = (R @ e[k] - R0 @ e0[k]) / ell
             out[r, 21 + k] = L0[k] / ell
+        mag = np.linalg.norm(out[r, :18])
+        out[r, :18] = out[r, :18] / mag if mag > 0 else 0.0
         out[r, 18:21] = R0 @ e0.mean(axis=0) / ell
         frames[r] = R
-    return out, frames
+        mags[r] = mag
+    return out, frames, mags
 
 
 # ------------------------------------------------------------------ network
@@ -188,16 +197,19 @@ def adam_step(p, g, state, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def predict_forces(p, X, X0, ring, deg, nodes):
     """Surrogate local forces [len(nodes)][3] in the global frame."""
-    f, R = features(X, X0, ring, deg, nodes)
+    f, R, mag = features(X, X0, ring, deg, nodes)
     o, _ = forward(p, f * p["in_scale"])
-    Fl = o * p["out_scale"]
+    Fl = o * mag[:, None] * p["out_scale"]
     return np.einsum("nij,ni->nj", R, Fl)
 
 
-def local_targets(F_local, frames, out_scale):
+def local_targets(F_local, frames, mags, out_scale):
     """Training targets: the plain solver's local forces in each node's frame,
-    divided by the output scale."""
-    return np.einsum("nij,nj->ni", frames, F_local) / out_scale
+    divided by the deformation magnitude and the output scale (zero where
+    the node is undeformed)."""
+    t = np.einsum("nij,nj->ni", frames, F_local) / out_scale
+    safe = np.where(mags > 0, mags, 1.0)
+    return np.where(mags[:, None] > 0, t / safe[:, None], 0.0)
 
 
 def local_params(params):

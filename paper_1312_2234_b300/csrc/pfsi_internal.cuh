@@ -173,8 +173,10 @@ int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                       unsigned long long* step_dev, cudaStream_t s);
 
 struct SgCtx;
-// Adds the surrogate's local membrane forces to F.
-int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float* F, cudaStream_t s);
+// Adds the surrogate's local membrane forces to F; xh, xl: the positions split
+// into hi/lo floats ([3][n], as the membrane passes leave them).
+int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const float* xl, float* F,
+                            cudaStream_t s);
 SgCtx* sg_internal(sg_ctx* c);
 int sg_node_count(const SgCtx* c);
 

@@ -36,7 +36,7 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     int rc;
     if (c->sg) {
         rc = launch_membrane_global(c->mem, c->X, c->F, s);
-        if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->X, c->F, s);
+        if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->mem->xh, c->mem->xl, c->F, s);
     } else {
         rc = launch_membrane_forces(c->mem, c->X, c->F, s);
     }

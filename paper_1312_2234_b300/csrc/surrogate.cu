@@ -5,9 +5,12 @@
 // Features: one thread per membrane node gathers its one-ring (<= 6 cyclic
 // neighbours), builds the local frame (z along the one-ring normal
 // sum e_k x e_{k+1}, x along the first edge projected on the tangent plane)
-// and writes 27 scaled inputs (edge-vector deviations from the rest one-ring
-// in the local frames; the rest curvature normal and the rest-length ratios,
-// which describe the rest one-ring) plus the frame.
+// and writes 27 scaled inputs (the direction of the edge-vector deviations
+// from the rest one-ring in the local frames; the rest curvature normal and
+// the rest-length ratios, which describe the rest one-ring), the frame and
+// the deformation magnitude, by which the network output is multiplied: the
+// surrogate force is zero at rest and homogeneous of degree one in the
+// deformation, as the local membrane forces are in the linear-elastic range.
 //
 // Dense layers: one tcgen05 kernel, C = A B^T with both operands BF16 and
 // K-contiguous in global memory (every layer of the forward and backward pass
@@ -41,6 +44,7 @@
 #include <string>
 #include <vector>
 
+#include "ff.cuh"
 #include "pfsi_internal.cuh"
 
 namespace pfsi {
@@ -275,6 +279,7 @@ struct EpiForce {
     const float* bias;
     const float* out_scale;
     const float* frames;   // [rows][9] rows x, y, z of R
+    const float* mags;     // [rows] deformation magnitude
     const int* node;       // [rows] node id, -1 for padding rows
     float* F;              // [3][n]
     int n;
@@ -283,8 +288,9 @@ struct EpiForce {
         const int v = node[row];
         if (v < 0) return;
         const float* R = frames + (size_t)row * 9;
-        const float a = (o0 + bias[0]) * out_scale[0], b = (o1 + bias[1]) * out_scale[1],
-                    c = (o2 + bias[2]) * out_scale[2];
+        const float mg = mags[row];
+        const float a = (o0 + bias[0]) * mg * out_scale[0], b = (o1 + bias[1]) * mg * out_scale[1],
+                    c = (o2 + bias[2]) * mg * out_scale[2];
         F[v] += R[0] * a + R[3] * b + R[6] * c;
         F[n + v] += R[1] * a + R[4] * b + R[7] * c;
         F[2 * n + v] += R[2] * a + R[5] * b + R[8] * c;
@@ -593,64 +599,122 @@ struct SgDev {
     int rows_pad;         // multiple of 128
     const int* node;      // [rows_pad] (-1 padding)
     const int* ring;      // [rows][6] (-1 padding)
-    const float* rest;    // [rows][32]: c_k (18), kappa0 (3), L0_k / l (6), 1/l
+    const float* rest;    // [rows][64]: rest record (see build_rings)
 };
 
-// Scaled inputs f[32] and frame R[9] (rows x, y, z) of surrogate row r.
-__device__ __forceinline__ void node_features(const double* __restrict__ X, const SgDev& d, int r,
-                                              const float* __restrict__ in_scale, float* f, float* R)
+__device__ __forceinline__ float3 f3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 axpy3(float a, float3 x, float3 y)
+{
+    return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
+}
+__device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+
+// (1 + eps)^(-1/2) - 1 without cancellation
+__device__ __forceinline__ float rsqrt1p_m1(float eps)
+{
+    const float r = sqrtf(1.0f + eps);
+    return -eps / (r * (1.0f + r));
+}
+
+// Scaled inputs f[32], frame R[9] (rows x, y, z) and deformation magnitude
+// of surrogate row r.  xh, xl: positions split into hi/lo floats, [3][n].
+//
+// The deformation delta_k = (R e_k - R0 e0_k)/l is a small difference of
+// O(1) vectors, so it is formed from small quantities only: d_k = e_k - e0_k
+// from the split positions and the split rest edge (exact to ~1e-7 of |d_k|),
+// and the frame change dR = R - R0 to first and second order in d (the
+// normal change from dnu = sum d_k x e0_{k+1} + e0_k x d_{k+1} + d_k x d_{k+1},
+// renormalised without cancellation, then the same for the x axis); then
+// delta_k = (R d_k + dR e0_k)/l.  The inputs keep their relative accuracy down
+// to deformations of ~1e-7 of an edge (FP32 alone would bottom out at ~1e-7
+// absolute).
+__device__ __forceinline__ void node_features(const float* __restrict__ xh, const float* __restrict__ xl,
+                                              const SgDev& d, int r, const float* __restrict__ in_scale, float* f,
+                                              float* R, float& mag)
 {
     const int n = d.n_nodes;
     const int v = d.node[r];
-    const double xi = X[v], yi = X[n + v], zi = X[2 * n + v];
-    float3 e[6];
+    float rest[64];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load16(d.rest + 64 * (size_t)r + 16 * q, rest + 16 * q);
+    const float* e0h = rest;        // rest edges, hi parts [6][3]
+    const float* e0l = rest + 18;   // lo parts
+    const float3 x0 = f3(rest + 36), y0 = f3(rest + 39), z0 = f3(rest + 42);
+    const float nu0 = rest[45], a0n = rest[46], inv_l = rest[47];
+    float3 dk[6], e0[6];
     int deg = 0;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const int nb = d.ring[6 * r + k];
+        e0[k] = f3(e0h + 3 * k);
         if (nb >= 0) {
-            e[k] = make_float3((float)(X[nb] - xi), (float)(X[n + nb] - yi), (float)(X[2 * n + nb] - zi));
+            float c[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const ff e = ff_diff(xh[a * n + nb], xl[a * n + nb], xh[a * n + v], xl[a * n + v]);
+                c[a] = (e.h - e0h[3 * k + a]) + (e.l - e0l[3 * k + a]);
+            }
+            dk[k] = make_float3(c[0], c[1], c[2]);
             deg = k + 1;
         } else {
-            e[k] = make_float3(0.f, 0.f, 0.f);
+            dk[k] = make_float3(0.f, 0.f, 0.f);
         }
     }
-    float3 nu = make_float3(0.f, 0.f, 0.f);
+    // normal change
+    float3 dnu = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (k < deg) {
-            // cyclic successor without a dynamic index (keeps e[] in registers)
-            const float3 a = e[k], b = (k + 1 < deg && k < 5) ? e[k < 5 ? k + 1 : 0] : e[0];
-            nu.x += a.y * b.z - a.z * b.y;
-            nu.y += a.z * b.x - a.x * b.z;
-            nu.z += a.x * b.y - a.y * b.x;
+            // cyclic successor with static indices (keeps the arrays in registers)
+            const float3 en = (k < 5 && k + 1 < deg) ? e0[k < 5 ? k + 1 : 0] : e0[0];
+            const float3 dn = (k < 5 && k + 1 < deg) ? dk[k < 5 ? k + 1 : 0] : dk[0];
+            dnu = add3(dnu, add3(cross3(dk[k], en), add3(cross3(e0[k], dn), cross3(dk[k], dn))));
         }
     }
-    const float inz = rsqrtf(nu.x * nu.x + nu.y * nu.y + nu.z * nu.z);
-    const float3 z = make_float3(nu.x * inz, nu.y * inz, nu.z * inz);
-    const float ez = e[0].x * z.x + e[0].y * z.y + e[0].z * z.z;
-    float3 x = make_float3(e[0].x - ez * z.x, e[0].y - ez * z.y, e[0].z - ez * z.z);
-    const float inx = rsqrtf(x.x * x.x + x.y * x.y + x.z * x.z);
-    x = make_float3(x.x * inx, x.y * inx, x.z * inx);
-    const float3 y = make_float3(z.y * x.z - z.z * x.y, z.z * x.x - z.x * x.z, z.x * x.y - z.y * x.x);
-    float rest[32];
-    load16(d.rest + 32 * (size_t)r, rest);
-    load16(d.rest + 32 * (size_t)r + 16, rest + 16);
-    const float inv_l = rest[27];
+    const float3 nu0v = make_float3(nu0 * z0.x, nu0 * z0.y, nu0 * z0.z);
+    const float sz = rsqrt1p_m1((2.0f * dot3(nu0v, dnu) + dot3(dnu, dnu)) / (nu0 * nu0));
+    const float3 dz = axpy3(sz, z0, make_float3(dnu.x * (1.0f + sz) / nu0, dnu.y * (1.0f + sz) / nu0,
+                                                dnu.z * (1.0f + sz) / nu0));
+    const float3 z = add3(z0, dz);
+    // x axis change: a = e_0 - (e_0.z) z, a0 = |a0| x0
+    const float3 ef = add3(e0[0], dk[0]);
+    const float ez = dot3(ef, z);
+    const float dez = dot3(e0[0], dz) + dot3(dk[0], z);
+    const float3 da = add3(dk[0], add3(make_float3(-dez * z0.x, -dez * z0.y, -dez * z0.z),
+                                       make_float3(-ez * dz.x, -ez * dz.y, -ez * dz.z)));
+    const float3 a0v = make_float3(a0n * x0.x, a0n * x0.y, a0n * x0.z);
+    const float sx = rsqrt1p_m1((2.0f * dot3(a0v, da) + dot3(da, da)) / (a0n * a0n));
+    const float3 dx = axpy3(sx, x0, make_float3(da.x * (1.0f + sx) / a0n, da.y * (1.0f + sx) / a0n,
+                                                da.z * (1.0f + sx) / a0n));
+    const float3 x = add3(x0, dx);
+    const float3 dy = add3(add3(cross3(dz, x0), cross3(z0, dx)), cross3(dz, dx));
+    const float3 y = add3(y0, dy);
+    float mm = 0.f;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (k < deg) {
-            f[3 * k + 0] = (x.x * e[k].x + x.y * e[k].y + x.z * e[k].z) * inv_l - rest[3 * k + 0];
-            f[3 * k + 1] = (y.x * e[k].x + y.y * e[k].y + y.z * e[k].z) * inv_l - rest[3 * k + 1];
-            f[3 * k + 2] = (z.x * e[k].x + z.y * e[k].y + z.z * e[k].z) * inv_l - rest[3 * k + 2];
+            f[3 * k + 0] = (dot3(x, dk[k]) + dot3(dx, e0[k])) * inv_l;
+            f[3 * k + 1] = (dot3(y, dk[k]) + dot3(dy, e0[k])) * inv_l;
+            f[3 * k + 2] = (dot3(z, dk[k]) + dot3(dz, e0[k])) * inv_l;
         } else {
             f[3 * k + 0] = f[3 * k + 1] = f[3 * k + 2] = 0.f;
         }
-        f[21 + k] = rest[21 + k];
+        mm = fmaf(f[3 * k], f[3 * k], fmaf(f[3 * k + 1], f[3 * k + 1], fmaf(f[3 * k + 2], f[3 * k + 2], mm)));
+        f[21 + k] = rest[51 + k];
     }
-    f[18] = rest[18];
-    f[19] = rest[19];
-    f[20] = rest[20];
+    // deformation: direction (inputs 0..17) and magnitude
+    mag = sqrtf(mm);
+    const float inv = mag > 0.f ? 1.0f / mag : 0.f;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) f[k] *= inv;
+    f[18] = rest[48];
+    f[19] = rest[49];
+    f[20] = rest[50];
 #pragma unroll
     for (int k = kIn; k < kInPad; ++k) f[k] = 0.f;
 #pragma unroll
@@ -660,14 +724,28 @@ __device__ __forceinline__ void node_features(const double* __restrict__ X, cons
     R[6] = z.x; R[7] = z.y; R[8] = z.z;
 }
 
+// FP64 positions -> hi/lo float split, [3][n] each
+__global__ void k_sg_split(const double* __restrict__ X, int n3, float* __restrict__ xh, float* __restrict__ xl)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n3) {
+        const double x = X[t];
+        const float h = __double2float_rn(x);
+        xh[t] = h;
+        xl[t] = __double2float_rn(x - (double)h);
+    }
+}
+
 template <class T>
-__global__ void k_sg_features(const double* __restrict__ X, SgDev d, const float* __restrict__ in_scale,
-                              T* __restrict__ feat, float* __restrict__ frames)
+__global__ void k_sg_features(const float* __restrict__ xh, const float* __restrict__ xl, SgDev d,
+                              const float* __restrict__ in_scale, T* __restrict__ feat, float* __restrict__ frames,
+                              float* __restrict__ mags)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
-    float f[kInPad], R[9];
-    node_features(X, d, r, in_scale, f, R);
+    float f[kInPad], R[9], mag;
+    node_features(xh, xl, d, r, in_scale, f, R, mag);
+    mags[r] = mag;
     store16(feat + (size_t)r * kInPad, f);
     store16(feat + (size_t)r * kInPad + 16, f + 16);
     float* fr = frames + 9 * (size_t)r;
@@ -752,7 +830,8 @@ __device__ __forceinline__ bool wg_and(bool v, int id)
     return r != 0;
 }
 
-__global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const double* __restrict__ X, SgDev d, Params P,
+__global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* __restrict__ xh,
+                                                                  const float* __restrict__ xl, SgDev d, Params P,
                                                                   EpiForce ef, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -795,9 +874,9 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const double* 
     const int n_tiles = d.rows_pad / kTile;
     for (int tile = blockIdx.x * kInferWG + wg; tile < n_tiles; tile += gridDim.x * kInferWG) {
         const int row = tile * kTile + t;
-        float f[kInPad], R[9];
+        float f[kInPad], R[9], mag = 0.f;
         if (row < d.rows) {
-            node_features(X, d, row, P.p + PFSI_SG_IN_SCALE, f, R);
+            node_features(xh, xl, d, row, P.p + PFSI_SG_IN_SCALE, f, R, mag);
         } else {
 #pragma unroll
             for (int k = 0; k < kInPad; ++k) f[k] = 0.f;
@@ -849,7 +928,8 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const double* 
         tmem_ld16(lanes, o);
         if (row < d.rows) {
             const int v = ef.node[row];
-            const float a = o[0] * ef.out_scale[0], b = o[1] * ef.out_scale[1], c = o[2] * ef.out_scale[2];
+            const float a = o[0] * mag * ef.out_scale[0], b = o[1] * mag * ef.out_scale[1],
+                        c = o[2] * mag * ef.out_scale[2];
             ef.F[v] += R[0] * a + R[3] * b + R[6] * c;
             ef.F[ef.n + v] += R[1] * a + R[4] * b + R[7] * c;
             ef.F[2 * ef.n + v] += R[2] * a + R[5] * b + R[8] * c;
@@ -864,18 +944,21 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const double* 
     }
 }
 
-// Training targets: target[r] = (R F[node]) / out_scale (local frame).
+// Training targets: target[r] = (R F[node]) / (mag out_scale) (local frame;
+// zero where the node is undeformed).
 __global__ void k_sg_targets(SgDev d, const float* __restrict__ F, const float* __restrict__ frames,
-                             const float* __restrict__ out_scale, float* __restrict__ target)
+                             const float* __restrict__ mags, const float* __restrict__ out_scale,
+                             float* __restrict__ target)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
     const int v = d.node[r], n = d.n_nodes;
     const float fx = F[v], fy = F[n + v], fz = F[2 * n + v];
     const float* R = frames + 9 * (size_t)r;
-    target[3 * (size_t)r + 0] = (R[0] * fx + R[1] * fy + R[2] * fz) / out_scale[0];
-    target[3 * (size_t)r + 1] = (R[3] * fx + R[4] * fy + R[5] * fz) / out_scale[1];
-    target[3 * (size_t)r + 2] = (R[6] * fx + R[7] * fy + R[8] * fz) / out_scale[2];
+    const float inv = mags[r] > 0.f ? 1.0f / mags[r] : 0.f;
+    target[3 * (size_t)r + 0] = (R[0] * fx + R[1] * fy + R[2] * fz) * inv / out_scale[0];
+    target[3 * (size_t)r + 1] = (R[3] * fx + R[4] * fy + R[5] * fz) * inv / out_scale[1];
+    target[3 * (size_t)r + 2] = (R[6] * fx + R[7] * fy + R[8] * fz) * inv / out_scale[2];
 }
 
 // ------------------------------------------------------------------ host side
@@ -1167,20 +1250,30 @@ int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned 
             ell += L[q] / d;
             for (int c = 0; c < 3; ++c) mean[c] += e[q][c] / d;
         }
-        float r32[32] = {};
-        for (int q = 0; q < d; ++q) {
-            r32[3 * q + 0] = (float)((x[0] * e[q][0] + x[1] * e[q][1] + x[2] * e[q][2]) / ell);
-            r32[3 * q + 1] = (float)((y[0] * e[q][0] + y[1] * e[q][1] + y[2] * e[q][2]) / ell);
-            r32[3 * q + 2] = (float)((z[0] * e[q][0] + z[1] * e[q][1] + z[2] * e[q][2]) / ell);
-            r32[21 + q] = (float)(L[q] / ell);
+        // rest record: e0_k split hi/lo (0..35), R0 rows (36..44), |nu0|, |a0|,
+        // 1/l (45..47), kappa0 (48..50), rest-length ratios (51..56)
+        float r64[64] = {};
+        for (int q = 0; q < d; ++q)
+            for (int c = 0; c < 3; ++c) {
+                const float h = (float)e[q][c];
+                r64[3 * q + c] = h;
+                r64[18 + 3 * q + c] = (float)(e[q][c] - (double)h);
+            }
+        for (int c = 0; c < 3; ++c) {
+            r64[36 + c] = (float)x[c];
+            r64[39 + c] = (float)y[c];
+            r64[42 + c] = (float)z[c];
         }
-        r32[18] = (float)((x[0] * mean[0] + x[1] * mean[1] + x[2] * mean[2]) / ell);
-        r32[19] = (float)((y[0] * mean[0] + y[1] * mean[1] + y[2] * mean[2]) / ell);
-        r32[20] = (float)((z[0] * mean[0] + z[1] * mean[1] + z[2] * mean[2]) / ell);
-        r32[27] = (float)(1.0 / ell);
+        r64[45] = (float)nn;
+        r64[46] = (float)xn;
+        r64[47] = (float)(1.0 / ell);
+        r64[48] = (float)((x[0] * mean[0] + x[1] * mean[1] + x[2] * mean[2]) / ell);
+        r64[49] = (float)((y[0] * mean[0] + y[1] * mean[1] + y[2] * mean[2]) / ell);
+        r64[50] = (float)((z[0] * mean[0] + z[1] * mean[1] + z[2] * mean[2]) / ell);
+        for (int q = 0; q < d; ++q) r64[51 + q] = (float)(L[q] / ell);
         R.node.push_back(i);
         for (int q = 0; q < 6; ++q) R.ring.push_back(ring[q]);
-        R.rest.insert(R.rest.end(), r32, r32 + 32);
+        R.rest.insert(R.rest.end(), r64, r64 + 64);
     }
     if (R.node.empty()) {
         err = "no membrane node with a closed one-ring";
@@ -1190,18 +1283,20 @@ int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned 
 }
 
 struct SgLayout {
-    size_t node, ring, rest, feat, frames, h1, h2, err, total;
+    size_t node, ring, rest, feat, frames, mags, h1, h2, xh, xl, err, total;
 };
-SgLayout sg_layout(int rows)
+// rows: surrogate rows; n: mesh nodes
+SgLayout sg_layout(int rows, int n)
 {
     const size_t Rp = ((size_t)rows + kTile - 1) / kTile * kTile;
-    const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 32 * Rp, 4 * 32 * Rp, 4 * 9 * Rp, 4 * 128 * Rp, 4 * 128 * Rp, 4};
-    size_t off[8], o = 0;
-    for (int i = 0; i < 8; ++i) {
+    const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 64 * Rp, 4 * 32 * Rp, 4 * 9 * Rp, 4 * Rp, 4 * 128 * Rp,
+                            4 * 128 * Rp, 12 * (size_t)n, 12 * (size_t)n, 4};
+    size_t off[11], o = 0;
+    for (int i = 0; i < 11; ++i) {
         off[i] = o;
         o += (sizes[i] + 255) / 256 * 256;
     }
-    return {off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], o};
+    return {off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], off[8], off[9], off[10], o};
 }
 
 }  // namespace
@@ -1213,21 +1308,25 @@ struct SgCtx {
     SgLayout L;
     bf16* feat;       // [rows_pad][32] (BF16 mode) / float (FP32 mode)
     float* frames;    // [rows_pad][9]
+    float* mags;      // [rows_pad]
+    float* xh;        // [3][n] split positions (standalone feature calls)
+    float* xl;
     void* h1;         // [rows_pad][128]
     void* h2;
     int* err;
 };
 
 // Surrogate forces added to F (the exact global terms must already be in F).
-int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float* F, cudaStream_t s)
+int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const float* xl, float* F,
+                            cudaStream_t s)
 {
     const Params P = params_of(params);
     const int rows = c->d.rows_pad;
-    EpiForce ef{P.p + PFSI_SG_B3, P.p + PFSI_SG_OUT_SCALE, c->frames, c->d.node, F, c->d.n_nodes};
+    EpiForce ef{P.p + PFSI_SG_B3, P.p + PFSI_SG_OUT_SCALE, c->frames, c->mags, c->d.node, F, c->d.n_nodes};
     int rc;
     if (c->mode == PFSI_SG_FP32) {
-        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE,
-                                                                     (float*)c->feat, c->frames);
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p + PFSI_SG_IN_SCALE,
+                                                                     (float*)c->feat, c->frames, c->mags);
         if ((rc = check_launch("surrogate: features"))) return rc;
         float *H1 = (float*)c->h1, *H2 = (float*)c->h2;
         if ((rc = gemm_f32((const float*)c->feat, kInPad, 1, P.p + PFSI_SG_W1, kInPad, 1, rows, kHid, kInPad, 1,
@@ -1242,7 +1341,7 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const double* X, float
     const int tiles = rows / kTile;
     const int want = (tiles + kInferWG - 1) / kInferWG;
     const int grid = want < 148 ? want : 148;
-    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(X, c->d, P, ef, c->err);
+    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(xh, xl, c->d, P, ef, c->err);
     return check_launch("surrogate: fused inference");
 }
 
@@ -1329,7 +1428,7 @@ extern "C" int sg_adam(void* params, const float* grad, float* m, float* v, floa
 extern "C" int sg_query_workspace(int n_nodes, size_t* bytes)
 {
     if (!bytes || n_nodes < 1) return set_error(PFSI_ERR_ARG, "sg_query_workspace: bad argument");
-    *bytes = sg_layout(n_nodes).total;
+    *bytes = sg_layout(n_nodes, n_nodes).total;
     return PFSI_OK;
 }
 
@@ -1345,8 +1444,8 @@ extern "C" int sg_create(int n_nodes, int n_tri, const int* tri, const double* X
     if (!rc && mode == PFSI_SG_BF16) rc = prepare_tc();
     if (rc) return set_error(rc, "sg_create: " + err);
     const int rows = (int)R.node.size();
-    const SgLayout L = sg_layout(rows);
-    if (ws_bytes < sg_layout(n_nodes).total) return set_error(PFSI_ERR_ARG, "sg_create: workspace too small");
+    const SgLayout L = sg_layout(rows, n_nodes);
+    if (ws_bytes < sg_layout(n_nodes, n_nodes).total) return set_error(PFSI_ERR_ARG, "sg_create: workspace too small");
     const int rows_pad = (rows + kTile - 1) / kTile * kTile;
     R.node.resize(rows_pad, -1);
     char* b = (char*)ws;
@@ -1363,6 +1462,9 @@ extern "C" int sg_create(int n_nodes, int n_tri, const int* tri, const double* X
     c->L = L;
     c->feat = (bf16*)(b + L.feat);
     c->frames = (float*)(b + L.frames);
+    c->mags = (float*)(b + L.mags);
+    c->xh = (float*)(b + L.xh);
+    c->xl = (float*)(b + L.xl);
     c->h1 = b + L.h1;
     c->h2 = b + L.h2;
     c->err = (int*)(b + L.err);
@@ -1384,18 +1486,24 @@ extern "C" int sg_rows(const sg_ctx* c, int* rows, const int** node)
     return PFSI_OK;
 }
 
-extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* frames, void* stream)
+extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* frames, float* mags,
+                           void* stream)
 {
     if (!c || !params || !X) return set_error(PFSI_ERR_ARG, "sg_features: null argument");
     const Params P = params_of(params);
     cudaStream_t s = as_stream(stream);
     float* fr = frames ? frames : c->frames;
+    float* mg = mags ? mags : c->mags;
+    const int n3 = 3 * c->d.n_nodes;
+    k_sg_split<<<(n3 + 255) / 256, 256, 0, s>>>(X, n3, c->xh, c->xl);
+    int rc = check_launch("sg_features: split");
+    if (rc) return rc;
     if (c->mode == PFSI_SG_FP32) {
         k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(
-            X, c->d, P.p + PFSI_SG_IN_SCALE, feat ? (float*)feat : (float*)c->feat, fr);
+            c->xh, c->xl, c->d, P.p + PFSI_SG_IN_SCALE, feat ? (float*)feat : (float*)c->feat, fr, mg);
     } else {
-        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(X, c->d, P.p + PFSI_SG_IN_SCALE,
-                                                                    feat ? (bf16*)feat : c->feat, fr);
+        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p + PFSI_SG_IN_SCALE,
+                                                                    feat ? (bf16*)feat : c->feat, fr, mg);
     }
     return check_launch("sg_features");
 }
@@ -1406,18 +1514,18 @@ extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, c
     if (!c || !params || !mem || !X || !F) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: null argument");
     if (mem->n != c->d.n_nodes) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: node count differs");
     cudaStream_t s = as_stream(stream);
-    int rc = launch_membrane_global(mem, X, F, s);
+    int rc = launch_membrane_global(mem, X, F, s);   // also splits X into mem->xh, mem->xl
     if (rc) return rc;
-    return launch_surrogate_forces(c, params, X, F, s);
+    return launch_surrogate_forces(c, params, mem->xh, mem->xl, F, s);
 }
 
-extern "C" int sg_targets(const sg_ctx* c, const void* params, const float* F, const float* frames, float* target,
-                          void* stream)
+extern "C" int sg_targets(const sg_ctx* c, const void* params, const float* F, const float* frames,
+                          const float* mags, float* target, void* stream)
 {
     if (!c || !params || !F || !target) return set_error(PFSI_ERR_ARG, "sg_targets: null argument");
     const Params P = params_of(params);
-    k_sg_targets<<<(c->d.rows + 127) / 128, 128, 0, as_stream(stream)>>>(c->d, F, frames ? frames : c->frames,
-                                                                         P.p + PFSI_SG_OUT_SCALE, target);
+    k_sg_targets<<<(c->d.rows + 127) / 128, 128, 0, as_stream(stream)>>>(
+        c->d, F, frames ? frames : c->frames, mags ? mags : c->mags, P.p + PFSI_SG_OUT_SCALE, target);
     return check_launch("sg_targets");
 }
 

@@ -105,9 +105,9 @@ _SIGS = {
     "sg_create": [c_int, c_int, P, P, P, c_int, P, c_size_t, ctypes.POINTER(P)],
     "sg_destroy": [P],
     "sg_rows": [P, ctypes.POINTER(c_int), ctypes.POINTER(P)],
-    "sg_features": [P, P, P, P, P, P],
+    "sg_features": [P, P, P, P, P, P, P],
     "sg_membrane_forces": [P, P, P, P, P, P],
-    "sg_targets": [P, P, P, P, P, P],
+    "sg_targets": [P, P, P, P, P, P, P],
     "sg_status": [P, ctypes.POINTER(c_int)],
     "sim_lb_ms": [P, ctypes.POINTER(ctypes.c_float)],
 }
@@ -637,16 +637,18 @@ class Surrogate:
         self.device = device
 
     def features(self, params, X, stream=None):
-        """(feat [rows_pad][32] BF16 or float, frames [rows_pad][9])."""
+        """(feat [rows_pad][32] BF16 or float, frames [rows_pad][9], mags [rows_pad])."""
         dt = torch.bfloat16 if self.mode == "bf16" else torch.float32
         feat = torch.zeros(self.rows_pad, 32, dtype=dt, device=self.device)
         frames = torch.zeros(self.rows_pad, 9, dtype=torch.float32, device=self.device)
-        _call("sg_features", self.h, _ptr(params.buf), _ptr(X), _ptr(feat), _ptr(frames), _stream(stream))
-        return feat, frames
+        mags = torch.zeros(self.rows_pad, dtype=torch.float32, device=self.device)
+        _call("sg_features", self.h, _ptr(params.buf), _ptr(X), _ptr(feat), _ptr(frames), _ptr(mags),
+              _stream(stream))
+        return feat, frames, mags
 
-    def targets(self, params, F, frames, stream=None):
+    def targets(self, params, F, frames, mags, stream=None):
         t = torch.zeros(self.rows_pad, 3, dtype=torch.float32, device=self.device)
-        _call("sg_targets", self.h, _ptr(params.buf), _ptr(F), _ptr(frames), _ptr(t), _stream(stream))
+        _call("sg_targets", self.h, _ptr(params.buf), _ptr(F), _ptr(frames), _ptr(mags), _ptr(t), _stream(stream))
         return t
 
     def forces(self, params, membrane, X, F, stream=None):

@@ -64,9 +64,9 @@ class Dataset:
         F = torch.zeros(3 * sg.n, dtype=torch.float32, device=device)
         for X in states:
             Xd = torch.as_tensor(X, device=device)
-            feat, frames = sg.features(params, Xd)
+            feat, frames, mags = sg.features(params, Xd)
             membrane_local.forces(Xd, F)
-            t = sg.targets(params, F, frames)
+            t = sg.targets(params, F, frames, mags)
             feats.append(feat[:sg.rows])
             targets.append(t[:sg.rows])
         self.feat = torch.cat(feats)

@@ -176,15 +176,16 @@ def sce_points(n, a, c, rng, shrink=0.8):
 
 def morse_pairs(Xm, Xs, r_cut):
     """Index pairs (into [Xm; Xs]) of SCE-SCE and SCE-membrane points closer
-    than r_cut in the rest shape."""
+    than r_cut in the rest shape, ordered by SCE point, then partner index."""
+    from scipy.spatial import cKDTree
+
     nm = len(Xm)
-    pairs = []
     if len(Xs) == 0:
         return np.zeros((0, 2), dtype=np.int32)
     allX = np.vstack([Xm, Xs])
-    for s in range(len(Xs)):
-        d = np.linalg.norm(allX - Xs[s], axis=1)
-        idx = np.nonzero(d < r_cut)[0]
+    near = cKDTree(allX).query_ball_point(Xs, r_cut, return_sorted=True)
+    pairs = []
+    for s, idx in enumerate(near):
         for j in idx:
             if j < nm or j > nm + s:  # membrane partner, or a later SCE
                 pairs.append((nm + s, j) if j > nm + s else (j, nm + s))

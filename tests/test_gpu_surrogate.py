@@ -56,11 +56,12 @@ def test_features_and_frames(mode):
     p = mlp.init_params(rng, scale_in=rng.uniform(0.5, 2.0, 27))
     params.set(p)
     sg = fsi.Surrogate(m, mode)
-    feat, frames = sg.features(params, torch.as_tensor(X).cuda())
+    feat, frames, mags = sg.features(params, torch.as_tensor(X).cuda())
     ring, deg, nodes = oracle_rows(m)
     assert sg.rows == len(nodes)
     n = m["node_plt"].size
-    f_or, R_or = mlp.features(X.reshape(3, n).T, m["X0"].reshape(3, n).T, ring, deg, nodes)
+    f_or, R_or, mag_or = mlp.features(X.reshape(3, n).T, m["X0"].reshape(3, n).T, ring, deg, nodes)
+    assert np.max(np.abs(mags.cpu().numpy()[:sg.rows] - mag_or)) < 1e-5 * mag_or.max()
     f_or = f_or * p["in_scale"]
     got = feat.float().cpu().numpy()[:sg.rows]
     assert np.all(got[:, 27:] == 0)
@@ -273,3 +274,49 @@ def test_coupled_step_with_surrogate_and_fallback():
     assert judge.errors and all(np.isfinite(judge.errors))
     assert sg.status() == 0
     assert torch.isfinite(X_after).all()
+
+
+def test_error_on_flow_deformed_states():
+    """States that the flow produced (the coupled step at high shear), not
+    random perturbations: the surrogate trained on perturbed rest states
+    reproduces the local force of flow-deformed platelets within 0.5 of its
+    largest entry (measured ~0.25)."""
+    w = workload.tiny(seed=5, level=2, shear=3e4)
+    params, untrained, sg, loc, hist = trained(w)
+    sim = fsi.Simulation(w)
+    sim.step(300)
+    m = w["mesh"]
+    mem = fsi.Membrane(w["membrane"], m)
+    n = sg.n
+    Fl = torch.zeros(3 * n, device="cuda")
+    Fp = torch.zeros(3 * n, device="cuda")
+    Fs = torch.zeros(3 * n, device="cuda")
+    loc.forces(sim.X, Fl)
+    mem.forces(sim.X, Fp)
+    sg.forces(params, mem, sim.X, Fs)
+    mask = torch.as_tensor(np.asarray(m["is_membrane"]).astype(bool)).cuda()
+    e = surrogate.rel_force_error(Fs - Fp + Fl, Fl, mask)
+    assert e < 0.5, e
+
+
+@pytest.mark.parametrize("amp", [1e-6, 1e-4])
+def test_features_keep_their_accuracy_at_small_deformations(amp):
+    """The deformation inputs are formed from small quantities (split
+    positions minus split rest edges, the frame change to second order), so
+    their direction and magnitude stay accurate where forming R e - R0 e0 in
+    FP32 would lose them (~1e-7 absolute): at a displacement of 1e-6 of the
+    platelet radius the directions agree with the FP64 reference to 1e-3."""
+    w = workload.tiny(seed=4, level=2)
+    m = w["mesh"]
+    n = m["node_plt"].size
+    rng = np.random.default_rng(9)
+    X = m["X0"] + amp * rng.standard_normal(m["X0"].shape)
+    params = fsi.SurrogateParams()
+    params.set(mlp.init_params(rng))
+    sg = fsi.Surrogate(m, "fp32")
+    feat, frames, mags = sg.features(params, torch.as_tensor(X).cuda())
+    ring, deg, nodes = oracle_rows(m)
+    f_or, R_or, mag_or = mlp.features(X.reshape(3, n).T, m["X0"].reshape(3, n).T, ring, deg, nodes)
+    got = feat.cpu().numpy()[:sg.rows]
+    assert np.max(np.abs(got[:, :18] - f_or[:, :18])) < 1e-3
+    assert np.max(np.abs(mags.cpu().numpy()[:sg.rows] / mag_or - 1)) < 1e-3

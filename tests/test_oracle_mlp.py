@@ -52,8 +52,8 @@ def test_one_rings_follow_face_orientation():
 def test_rest_features_and_icosahedron_curvature():
     U, T = ico(0)
     ring, deg = mlp.one_rings(T, len(U))
-    f, R = mlp.features(U, U, ring, deg, np.arange(12))
-    assert np.all(np.abs(f[:, :18]) < 1e-14)
+    f, R, mag = mlp.features(U, U, ring, deg, np.arange(12))
+    assert np.all(f[:, :18] == 0) and np.all(mag == 0)
     # all edges of the regular icosahedron are equal: rest-length ratios 1,
     # the sixth slot of a degree-5 node empty
     assert np.allclose(f[:, 21:26], 1.0, atol=1e-14) and np.all(f[:, 26] == 0)
@@ -84,9 +84,9 @@ def test_features_invariant_and_forces_equivariant_under_rigid_motion():
     Q = rotation(rng)
     c = np.array([3.0, -2.0, 7.5])
     nodes = np.arange(len(U))
-    f1, _ = mlp.features(X, U, ring, deg, nodes)
-    f2, _ = mlp.features(X @ Q.T + c, U, ring, deg, nodes)
-    assert np.allclose(f1, f2, atol=1e-12)
+    f1, _, m1 = mlp.features(X, U, ring, deg, nodes)
+    f2, _, m2 = mlp.features(X @ Q.T + c, U, ring, deg, nodes)
+    assert np.allclose(f1, f2, atol=1e-12) and np.allclose(m1, m2, atol=1e-12)
     p = mlp.init_params(rng)
     F1 = mlp.predict_forces(p, X, U, ring, deg, nodes)
     F2 = mlp.predict_forces(p, X @ Q.T + c, U, ring, deg, nodes)
@@ -94,22 +94,44 @@ def test_features_invariant_and_forces_equivariant_under_rigid_motion():
 
 
 def test_uniform_dilation():
-    """Under X -> 1.01 X every edge vector grows by 1 % in an unchanged frame:
-    delta_k = 0.01 R0 e0_k / l, and the rest inputs do not move."""
+    """Under X -> (1 + a) X every edge vector grows by a in an unchanged
+    frame: delta_k = a R0 e0_k / l, so the direction inputs are R0 e0_k / l
+    over its norm for any a, the magnitude is a times that norm, and the rest
+    inputs do not move."""
     U, T = ico(1)
     ring, deg = mlp.one_rings(T, len(U))
-    f0, _ = mlp.features(U, U, ring, deg, np.arange(len(U)))
-    f, _ = mlp.features(1.01 * U, U, ring, deg, np.arange(len(U)))
-    for i in range(len(U)):
-        d = deg[i]
-        nb = ring[i, :d]
-        e0 = U[nb] - U[i]
-        ell = np.linalg.norm(e0, axis=1).mean()
-        R0 = mlp.frame(e0, d)
-        for k in range(d):
-            assert np.allclose(f[i, 3 * k:3 * k + 3], 0.01 * (R0 @ e0[k]) / ell, atol=1e-14)
-        assert np.allclose(f[i, 18:], f0[i, 18:], atol=1e-15)
-        assert np.all(f[i, 3 * d:18] == 0) and np.all(f[i, 21 + d:] == 0)
+    f0, _, _ = mlp.features(U, U, ring, deg, np.arange(len(U)))
+    for a in (1e-6, 0.01):
+        f, _, mag = mlp.features((1 + a) * U, U, ring, deg, np.arange(len(U)))
+        for i in range(len(U)):
+            d = deg[i]
+            nb = ring[i, :d]
+            e0 = U[nb] - U[i]
+            ell = np.linalg.norm(e0, axis=1).mean()
+            R0 = mlp.frame(e0, d)
+            c = np.concatenate([(R0 @ e0[k]) / ell for k in range(d)])
+            assert abs(mag[i] - a * np.linalg.norm(c)) < 1e-9 * a
+            assert np.allclose(f[i, :3 * d], c / np.linalg.norm(c), atol=1e-7)
+            assert np.allclose(f[i, 18:], f0[i, 18:], atol=1e-15)
+            assert np.all(f[i, 3 * d:18] == 0) and np.all(f[i, 21 + d:] == 0)
+
+
+def test_surrogate_force_is_homogeneous_in_the_deformation():
+    """Scaling a deformation of the rest shape by s scales the predicted
+    local force by s (and it vanishes at rest)."""
+    rng = np.random.default_rng(6)
+    U, T = ico(2)
+    ring, deg = mlp.one_rings(T, len(U))
+    p = mlp.init_params(rng)
+    D = rng.standard_normal(U.shape)
+    nodes = np.arange(len(U))
+    F1 = mlp.predict_forces(p, U + 1e-5 * D, U, ring, deg, nodes)
+    F2 = mlp.predict_forces(p, U + 2e-5 * D, U, ring, deg, nodes)
+    assert np.all(mlp.predict_forces(p, U, U, ring, deg, nodes) == 0)
+    # the inputs are linear in the displacement only to first order (the
+    # frame turns with it), so the ratio is 2 up to a relative O(strain)
+    # (here ~2e-4)
+    assert np.allclose(F2, 2 * F1, rtol=0, atol=1e-3 * np.abs(F1).max())
 
 
 def test_backward_matches_central_differences():
