@@ -553,6 +553,36 @@ def run_lb_only(args):
                       "frac": gbs / peak, "l2_flushed": small}), flush=True)
 
 
+def run_surrogate_only(args):
+    """The surrogate membrane force alone on the 256x128x128 channel's
+    256,200 membrane nodes (profiling aid; untrained weights, which do not
+    change the work): event-timed per call, split into the exact global part
+    and the fused tensor-core inference."""
+    import torch
+    from paper_1312_2234_b300 import fsi, surrogate, workload
+    w = workload.config_surrogate(seed=0)
+    m = w["mesh"]
+    n = w["M"]
+    mem = fsi.Membrane(w["membrane"], m)
+    glob = fsi.Membrane(surrogate.local_params(w["membrane"]), m)
+    sg = fsi.Surrogate(m, "bf16")
+    params = fsi.SurrogateParams()
+    params.set(surrogate.init_params(np.random.default_rng(0)))
+    X = torch.as_tensor(w["X"] + 1e-3 * np.random.default_rng(1).standard_normal(w["X"].shape)).cuda()
+    F = torch.zeros(3 * n, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        sg.forces(params, mem, X, F)
+        mem.forces(X, F)
+    t_sg = timed_steps(lambda: sg.forces(params, mem, X, F), args.steps, stream) / args.steps
+    t_plain = timed_steps(lambda: mem.forces(X, F), args.steps, stream) / args.steps
+    flop = 2 * (32 * 128 + 144 * 128 + 144 * 16) * sg.rows
+    print(json.dumps({"kernel": "k_sg_infer + exact global membrane terms", "nodes": n, "rows": sg.rows,
+                      "surrogate_us": 1e6 * t_sg, "plain_us": 1e6 * t_plain,
+                      "tensor_flop_per_call": flop, "status": sg.status()}), flush=True)
+    del glob
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -560,7 +590,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
-    ap.add_argument("--kernel", default=None, choices=[None, "lb"], help="time one kernel alone")
+    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate"], help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variants")
@@ -571,6 +601,9 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.kernel == "lb":
         run_lb_only(args)
+        return
+    if args.kernel == "surrogate":
+        run_surrogate_only(args)
         return
     rank, ws = dist_setup()
     if args.impl == "reference":
