@@ -22,10 +22,10 @@
 //             per (element, vertex): spring + bending for the four vertices
 //             of an edge's dihedral chain, area gradients per triangle corner,
 //             the Morse force per pair;
-//   nodes     one thread per node sums its element contributions from its
-//             own lists (independent loads, no atomics, fixed order) and
-//             applies the per-platelet global area and volume terms and the
-//             wall repulsion.
+//   nodes     four lanes per node sum its element contributions from its own
+//             lists (strided, independent loads, no atomics; a fixed shuffle
+//             reduction) and apply the per-platelet global area and volume
+//             terms and the wall repulsion.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -349,48 +349,35 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
 
 // Pass 3: one thread per node sums its element contributions and applies the
 // per-platelet global area and volume coefficients and the wall repulsion.
+// kNodeLanes lanes per node share its element slots (strided), then reduce by
+// shuffles in a fixed order; the first lane adds the wall term and writes.
+constexpr int kNodeLanes = 4;
+
 __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx c)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= c.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = t / kNodeLanes, q = t % kNodeLanes;
+    const bool on = v < c.n;
     const int n = c.n;
     const mem_params P = c.p;
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (!c.skip_edges) {
-        // batches of four independent loads keep several requests in flight
-        int s = c.esl_off[v];
+    if (on && !c.skip_edges) {
         const int e = c.esl_off[v + 1];
-        for (; s + 4 <= e; s += 4) {
-            const int4 k = make_int4(c.esl[s], c.esl[s + 1], c.esl[s + 2], c.esl[s + 3]);
-            const float4 f0 = c.eout[k.x], f1 = c.eout[k.y], f2 = c.eout[k.z], f3 = c.eout[k.w];
-            fx += (f0.x + f1.x) + (f2.x + f3.x);
-            fy += (f0.y + f1.y) + (f2.y + f3.y);
-            fz += (f0.z + f1.z) + (f2.z + f3.z);
-        }
-        for (; s < e; ++s) {
+        for (int s = c.esl_off[v] + q; s < e; s += kNodeLanes) {
             const float4 f = c.eout[c.esl[s]];
             fx += f.x;
             fy += f.y;
             fz += f.z;
         }
     }
-    // Eq. 4-5: F -= (k_t (S_t - S0_t)/S0_t + k_s (S - S0)/S0) dS_t/dX + k_v (V - V0)/V0 dV/dX
-    const int plt = c.node_plt[v];
-    const double* pr = c.plt_rest + 4 * plt;  // S0, V0, 1/S0, 1/V0
-    const float cSg = (float)((double)P.k_s * c.acc[2 * plt] * pr[2]);
-    const float cV = (float)((double)P.k_v * (c.acc[2 * plt + 1] - pr[1]) * pr[3]);
-    {
-        int s = c.tcl_off[v];
+    if (on) {
+        // Eq. 4-5: F -= (k_t (S_t - S0_t)/S0_t + k_s (S - S0)/S0) dS_t/dX + k_v (V - V0)/V0 dV/dX
+        const int plt = c.node_plt[v];
+        const double* pr = c.plt_rest + 4 * plt;  // S0, V0, 1/S0, 1/V0
+        const float cSg = (float)((double)P.k_s * c.acc[2 * plt] * pr[2]);
+        const float cV = (float)((double)P.k_v * (c.acc[2 * plt + 1] - pr[1]) * pr[3]);
         const int e = c.tcl_off[v + 1];
-        for (; s + 2 <= e; s += 2) {
-            const int k0 = c.tcl[s], k1 = c.tcl[s + 1];
-            const float4 g0 = c.tout[k0], n0 = c.tout[k0 | 3], g1 = c.tout[k1], n1 = c.tout[k1 | 3];
-            const float c0 = g0.w + cSg, c1 = g1.w + cSg;
-            fx -= (c0 * g0.x + cV * n0.x) + (c1 * g1.x + cV * n1.x);
-            fy -= (c0 * g0.y + cV * n0.y) + (c1 * g1.y + cV * n1.y);
-            fz -= (c0 * g0.z + cV * n0.z) + (c1 * g1.z + cV * n1.z);
-        }
-        for (; s < e; ++s) {
+        for (int s = c.tcl_off[v] + q; s < e; s += kNodeLanes) {
             const int code = c.tcl[s];
             const float4 g = c.tout[code];
             const float4 n6 = c.tout[code | 3];
@@ -399,15 +386,23 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
             fy -= cS * g.y + cV * n6.y;
             fz -= cS * g.z + cV * n6.z;
         }
+        const int ep = c.psl_off[v + 1];
+        for (int s = c.psl_off[v] + q; s < ep; s += kNodeLanes) {
+            const int code = c.psl[s];
+            const float4 f = c.pout[code >> 1];
+            const float sg = (code & 1) ? -1.f : 1.f;
+            fx += sg * f.x;
+            fy += sg * f.y;
+            fz += sg * f.z;
+        }
     }
-    for (int s = c.psl_off[v]; s < c.psl_off[v + 1]; ++s) {
-        const int code = c.psl[s];
-        const float4 f = c.pout[code >> 1];
-        const float sg = (code & 1) ? -1.f : 1.f;
-        fx += sg * f.x;
-        fy += sg * f.y;
-        fz += sg * f.z;
+#pragma unroll
+    for (int o = 1; o < kNodeLanes; o <<= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
+    if (!on || q != 0) return;
     // wall repulsion on surface nodes (Section 3.4.1)
     if (c.is_mem[v] && P.rep_F0 != 0.f) {
         const float eps = fmaxf((c.xh[2 * n + v] - P.z_wall) + c.xl[2 * n + v], P.rep_eps_min);
@@ -438,7 +433,7 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s)
 {
     int rc = launch_scalars(c, X, s);
     if (rc) return rc;
-    k_mem_nodes<<<(c->n + 127) / 128, 128, 0, s>>>(F, *c);
+    k_mem_nodes<<<(int)(((long long)c->n * kNodeLanes + 127) / 128), 128, 0, s>>>(F, *c);
     return check_launch("membrane_forces");
 }
 
