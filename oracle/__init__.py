@@ -52,7 +52,7 @@ def build(force: bool = False) -> str:
 class LBParams(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("tau", ctypes.c_double), ("u_top", ctypes.c_double * 3),
-                ("body", ctypes.c_double * 3)]
+                ("body", ctypes.c_double * 3), ("walls", ctypes.c_int)]
 
 
 class MemParams(ctypes.Structure):
@@ -134,8 +134,8 @@ def lattice():
     return c.reshape(19, 3), w
 
 
-def lb_params(nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0)):
-    return LBParams(nx, ny, nz, tau, (ctypes.c_double * 3)(*u_top), (ctypes.c_double * 3)(*body))
+def lb_params(nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0), walls=0):
+    return LBParams(nx, ny, nz, tau, (ctypes.c_double * 3)(*u_top), (ctypes.c_double * 3)(*body), int(walls))
 
 
 def lb_init_shear(p):
@@ -261,7 +261,8 @@ class Sim:
 
     def __init__(self, w):
         g = w["grid"]
-        self.p = lb_params(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)))
+        self.p = lb_params(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)),
+                           g.get("walls", 0))
         self.N = g["nx"] * g["ny"] * g["nz"]
         m = w["mesh"]
         self.mesh = Mesh(m["X0"], m["tri"], m["pairs"], m["node_plt"], m["is_membrane"], m["n_plt"])

@@ -136,12 +136,16 @@ static double guo_source(int q, double tau, const double v[3], const double F[3]
 void ora_lb_init_shear(const ora_lb_params* p, double* f)
 {
     long N = (long)p->nx * p->ny * p->nz;
-    double dudz[3] = {p->u_top[0] / p->nz, p->u_top[1] / p->nz, 0.0};
+    /* the walls sit half a link outside the end layers (bounce-back) or on
+       them (on-site) */
+    double H = p->walls ? (double)(p->nz - 1) : (double)p->nz;
+    double z0 = p->walls ? 0.0 : 0.5;
+    double dudz[3] = {p->u_top[0] / H, p->u_top[1] / H, 0.0};
     for (int k = 0; k < p->nz; ++k)
         for (int j = 0; j < p->ny; ++j)
             for (int i = 0; i < p->nx; ++i) {
                 long cell = cell_index(p, i, j, k);
-                double u[3] = {dudz[0] * (k + 0.5), dudz[1] * (k + 0.5), 0.0};
+                double u[3] = {dudz[0] * (k + z0), dudz[1] * (k + z0), 0.0};
                 for (int q = 0; q < 19; ++q) {
                     double Qgrad = 0.0; /* Q_ab d_a u_b with only d_z u_x, d_z u_y */
                     for (int b = 0; b < 2; ++b) Qgrad += (double)C[q][2] * C[q][b] * dudz[b];
@@ -151,17 +155,66 @@ void ora_lb_init_shear(const ora_lb_params* p, double* f)
             }
 }
 
+/* Index of the population with velocity (cx, cy, cz). */
+static int dir_index(int cx, int cy, int cz)
+{
+    for (int q = 0; q < 19; ++q)
+        if (C[q][0] == cx && C[q][1] == cy && C[q][2] == cz) return q;
+    return -1;
+}
+
+/* On-site velocity wall of Hecht and Harting (Eq. 23-30) on a node plane
+ * with wall velocity vw: the populations entering the fluid (c_z = +1 at the
+ * bottom, c_z = -1 at the top) are unknown after streaming and are set from
+ * the known ones.  The bottom follows Eq. 23-30 as printed (paper numbering
+ * f1..f19 = q 0..18 here); the top is their mirror image z -> -z (reading:
+ * the paper prints the bottom case only).  With s = +1 (bottom) or -1 (top):
+ *   rho = [sum_{c_z = 0} f + 2 sum_{c_z = -s} f] / (1 - s vz)        (Eq. 23)
+ *   N_x = 1/2 sum_{c_z = 0} c_x f - rho vx / 3,  N_y likewise      (Eq. 29-30)
+ *   f_q = f_opp(q) + (rho/3) c_q.v                 for c_q = (0, 0, s) (Eq. 24)
+ *   f_q = f_opp(q) + (rho/6) c_q.v - c_qx N_x - c_qy N_y  for the
+ *         diagonals with c_qz = s                               (Eq. 25-28) */
+static void onsite_wall(double* f, int s, const double* vw)
+{
+    double sum0 = 0.0, sum_out = 0.0, jx = 0.0, jy = 0.0;
+    for (int q = 0; q < 19; ++q) {
+        if (C[q][2] == 0) {
+            sum0 += f[q];
+            jx += C[q][0] * f[q];
+            jy += C[q][1] * f[q];
+        } else if (C[q][2] == -s) {
+            sum_out += f[q];
+        }
+    }
+    double rho = (sum0 + 2.0 * sum_out) / (1.0 - s * vw[2]);
+    double Nx = 0.5 * jx - rho * vw[0] / 3.0;
+    double Ny = 0.5 * jy - rho * vw[1] / 3.0;
+    for (int q = 0; q < 19; ++q) {
+        if (C[q][2] != s) continue;
+        int o = dir_index(-C[q][0], -C[q][1], -C[q][2]);
+        double cv = C[q][0] * vw[0] + C[q][1] * vw[1] + C[q][2] * vw[2];
+        if (C[q][0] == 0 && C[q][1] == 0)
+            f[q] = f[o] + rho * cv / 3.0;
+        else
+            f[q] = f[o] + rho * cv / 6.0 - C[q][0] * Nx - C[q][1] * Ny;
+    }
+}
+
 /* One lattice Boltzmann step (Eq. 16-20).  The state between steps is the
  * post-collision distribution; a step streams it (each population moves one
  * link along c_q; periodic in x and y) and then collides with BGK plus the
- * Guo source.  Reading: the z walls are halfway bounce-back (a population
- * that would enter from outside is the opposite population leaving the same
- * cell), with Ladd's moving-wall term 2 w_q rho_w (c_q . u_w)/c_s^2 at the
- * top, rho_w = rho0 = 1. */
+ * Guo source.  Walls (p->walls = 0, reading): halfway bounce-back (a
+ * population that would enter from outside is the opposite population
+ * leaving the same cell), with Ladd's moving-wall term 2 w_q rho_w (c_q .
+ * u_w)/c_s^2 at the top, rho_w = rho0 = 1.  Walls (p->walls = 1): the end
+ * layers are wall nodes whose entering populations come from onsite_wall;
+ * reading: with a force present, the wall fixes the populations' momentum
+ * rho v_w and the collision then uses v = v_w + F/(2 rho) as elsewhere. */
 void ora_lb_step(const ora_lb_params* p, const double* f_in, const double* g,
                  double* f_out, double* rho_out, double* v_out)
 {
     long N = (long)p->nx * p->ny * p->nz;
+    const double zero[3] = {0.0, 0.0, 0.0};
     for (int k = 0; k < p->nz; ++k)
         for (int j = 0; j < p->ny; ++j)
             for (int i = 0; i < p->nx; ++i) {
@@ -173,6 +226,7 @@ void ora_lb_step(const ora_lb_params* p, const double* f_in, const double* g,
                         double cu = 0.0;
                         if (sk >= p->nz)
                             cu = C[q][0] * p->u_top[0] + C[q][1] * p->u_top[1] + C[q][2] * p->u_top[2];
+                        /* on-site walls overwrite this value below */
                         f[q] = f_in[opposite(q) * N + cell] + 2.0 * W[q] * 1.0 * cu / CS2;
                     } else {
                         si = (si % p->nx + p->nx) % p->nx;
@@ -180,6 +234,8 @@ void ora_lb_step(const ora_lb_params* p, const double* f_in, const double* g,
                         f[q] = f_in[q * N + cell_index(p, si, sj, sk)];
                     }
                 }
+                if (p->walls && k == 0) onsite_wall(f, +1, zero);
+                if (p->walls && k == p->nz - 1) onsite_wall(f, -1, p->u_top);
                 /* Eq. 17-18: density and momentum. */
                 double rho = 0.0, mom[3] = {0.0, 0.0, 0.0};
                 for (int q = 0; q < 19; ++q) {

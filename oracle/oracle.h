@@ -33,11 +33,15 @@ typedef struct {
     double tau;        /* BGK relaxation time, Eq. 16 */
     double u_top[3];   /* velocity of the moving top wall */
     double body[3];    /* uniform body-force density added in every cell */
+    int walls;         /* 0: halfway bounce-back (walls at z = -1/2, nz - 1/2);
+                          1: on-site velocity walls of Eq. 23-30 (walls on the
+                          node planes k = 0 and k = nz - 1) */
 } ora_lb_params;
 
 int ora_lb_q(void);
 void ora_lb_lattice(int c[19 * 3], double w[19]);
-/* Post-collision state of a linear shear profile u_x = u_top_x (k+1/2)/nz. */
+/* Post-collision state of the linear shear profile between the walls:
+ * u = u_top (k + 1/2)/nz (bounce-back walls) or u_top k/(nz - 1) (on-site). */
 void ora_lb_init_shear(const ora_lb_params* p, double* f);
 /* One step: stream (periodic x,y; halfway bounce-back at the z walls) and
  * BGK-collide with Guo forcing.  f_in/f_out are post-collision states;

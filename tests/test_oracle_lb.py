@@ -161,3 +161,50 @@ def test_poiseuille(oracle_lib, tau, tol):
     exact = G / (2 * nu) * (k + 0.5) * (nz - 0.5 - k)
     ux = v[:N].reshape(nz, ny, nx)[:, 0, 0]
     assert np.max(np.abs(ux - exact)) / exact.max() < tol
+
+
+@pytest.mark.parametrize("nz,u_top,tau", [(9, (1e-3, 0.0, 0.0), 0.8), (12, (1e-3, -6e-4, 0.0), 1.379)])
+def test_onsite_walls_couette_is_exact(oracle_lib, nz, u_top, tau):
+    """On-site velocity walls (Eq. 23-30) on the node planes k = 0 and nz - 1:
+    started from rest, the flow converges to the linear profile
+    u = u_top k/(nz - 1) exactly (BGK with velocity walls on the nodes
+    reproduces a linear shear with no slip), and the shear initial state is
+    that profile."""
+    nx, ny = 3, 2
+    p0 = oracle_lib.lb_params(nx, ny, nz, tau, (0, 0, 0), walls=1)
+    f = oracle_lib.lb_init_shear(p0)  # rest
+    p = oracle_lib.lb_params(nx, ny, nz, tau, u_top, walls=1)
+    for _ in range(6000):
+        f, rho, v = oracle_lib.lb_step(p, f)
+    N = nx * ny * nz
+    prof = np.arange(nz) / (nz - 1)
+    for d in range(2):
+        exact = u_top[d] * prof
+        assert np.allclose(v[d * N:(d + 1) * N].reshape(nz, ny, nx), exact[:, None, None], rtol=1e-10,
+                           atol=1e-12 * abs(u_top[0]))
+    assert np.allclose(v[2 * N:], 0.0, atol=1e-11 * abs(u_top[0]))
+    assert np.allclose(rho, 1.0, atol=1e-12)
+    f0 = oracle_lib.lb_init_shear(p)
+    _, _, v0 = oracle_lib.lb_step(p, f0)
+    assert np.allclose(v0[:N].reshape(nz, ny, nx), (u_top[0] * prof)[:, None, None], rtol=1e-9, atol=1e-15)
+
+
+def test_onsite_walls_impose_the_wall_velocity(oracle_lib):
+    """For any state, the wall nodes' populations after streaming carry
+    exactly the wall velocity (no force): the rule's defining property,
+    checked on the moments rather than on its formulas."""
+    nx, ny, nz = 6, 5, 7
+    u_top = (0.015, 0.004, 0.0)
+    p = oracle_lib.lb_params(nx, ny, nz, 0.9, u_top, walls=1)
+    rng = np.random.default_rng(4)
+    f = oracle_lib.lb_init_shear(p) + 1e-3 * rng.standard_normal(19 * nx * ny * nz)
+    _, rho, v = oracle_lib.lb_step(p, f)
+    V = v.reshape(3, nz, ny, nx)
+    assert np.max(np.abs(V[:, 0])) < 1e-14
+    for d in range(3):
+        assert np.max(np.abs(V[d, nz - 1] - u_top[d])) < 1e-14
+    # the bulk is untouched by the wall mode: same result as bounce-back walls
+    pb = oracle_lib.lb_params(nx, ny, nz, 0.9, u_top, walls=0)
+    _, rho_b, v_b = oracle_lib.lb_step(pb, f)
+    inner = slice(2, nz - 2)
+    assert np.array_equal(v.reshape(3, nz, ny, nx)[:, inner], v_b.reshape(3, nz, ny, nx)[:, inner])
