@@ -65,7 +65,18 @@ typedef struct {
     float body[3];    /* uniform body-force density added in every cell */
     int storage;      /* PFSI_LB_FP32 (lb_create) or PFSI_LB_BF16 / PFSI_LB_FP16 (lb_create_mixed) */
     int fp16_exponent;/* PFSI_LB_FP16: power-of-two scale of the stored f^neq, -60..60 */
+    int walls;        /* PFSI_WALLS_BOUNCEBACK or PFSI_WALLS_ONSITE */
 } lb_params;
+
+/* z walls.  BOUNCEBACK: halfway bounce-back, walls at z = -1/2 and
+ * nz - 1/2 (moving-wall term at the top).  ONSITE: the velocity walls of
+ * Eq. 23-30 (Hecht and Harting) on the node planes k = 0 (still) and
+ * k = nz - 1 (moving with u_top): after streaming, the populations entering
+ * the fluid there are set so that the node carries the wall velocity (the
+ * top wall is the mirror image of the printed bottom case); with a force,
+ * the collision velocity is v_w + F/(2 rho) as elsewhere. */
+#define PFSI_WALLS_BOUNCEBACK 0
+#define PFSI_WALLS_ONSITE 1
 
 typedef struct {
     size_t f_bytes;    /* one population buffer: 19 * n_cells float (FP32) or 16-bit (mixed) */
@@ -114,9 +125,10 @@ int lb_create_mixed(const lb_params* p, void* fneq_a, void* fneq_b, float* m_a, 
 int lb_export(lb_ctx* ctx, float* f_out, void* stream);
 int lb_destroy(lb_ctx* ctx);
 
-/* Writes the developed shear profile u_x = u_top (k + 1/2)/nz (equilibrium
- * plus its first-order non-equilibrium part, post-collision) into the current
- * population buffer.  u_top = 0 gives the fluid at rest. */
+/* Writes the developed shear profile u = u_top (k + 1/2)/nz (bounce-back
+ * walls) or u_top k/(nz - 1) (on-site walls), equilibrium plus its
+ * first-order non-equilibrium part, post-collision, into the current state.
+ * u_top = 0 gives the fluid at rest. */
 int lb_init_shear(lb_ctx* ctx, void* stream);
 
 /* nsteps lattice Boltzmann steps (Eq. 16-20): pull streaming with periodic x,

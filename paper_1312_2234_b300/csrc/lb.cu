@@ -38,10 +38,45 @@ namespace {
 constexpr int kRowBlock = 128;     // default threads per block along x (FP32 kernel)
 constexpr int kMaxRowBlock = 256;
 
+// On-site velocity wall (Eq. 23-30, Hecht and Harting) on shifted
+// populations f~ = f - w: s = +1 at the bottom (k = 0), -1 at the top
+// (k = nz - 1, the mirror image); the populations with c_z = s entering the
+// fluid are set from the known ones so that the node carries the wall
+// velocity vw.  With the shift, rho = (1 + S~)/(1 - s vz), S~ = sum over
+// c_z = 0 of f~ + 2 sum over c_z = -s of f~ (the weights of those sets add up
+// to 1), and N_x = 1/2 sum over c_z = 0 of c_x f~ - rho vx / 3 (Eq. 29).
+template <int s>
+__device__ __forceinline__ void onsite_wall(float* f, float3 vw)
+{
+    float S = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (czq(q) == 0) {
+            S += f[q];
+            if (cxq(q)) jx += cxq(q) * f[q];
+            if (cyq(q)) jy += cyq(q) * f[q];
+        } else if (czq(q) == -s) {
+            S += 2.0f * f[q];
+        }
+    }
+    const float rho = (1.0f + S) / (1.0f - s * vw.z);
+    const float Nx = 0.5f * jx - rho * vw.x * (1.0f / 3.0f);
+    const float Ny = 0.5f * jy - rho * vw.y * (1.0f / 3.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (czq(q) != s) continue;
+        const float cv = cxq(q) * vw.x + cyq(q) * vw.y + czq(q) * vw.z;
+        if (cxq(q) == 0 && cyq(q) == 0)
+            f[q] = f[oppq(q)] + rho * cv * (1.0f / 3.0f);
+        else
+            f[q] = f[oppq(q)] + rho * cv * (1.0f / 6.0f) - cxq(q) * Nx - cyq(q) * Ny;
+    }
+}
+
 __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     const float* __restrict__ fin, float* __restrict__ fout, float4* __restrict__ g,
     float4* __restrict__ vout, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
-    float omega, float guo, float3 body, float3 utop)
+    float omega, float guo, float3 body, float3 utop, int onsite)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
@@ -68,6 +103,10 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
         } else {
             f[q] = fin[q * N + (sk * ny + sy) * nx + sx];
         }
+    }
+    if (onsite) {   // on-site walls replace the bounce-back values of the entering populations
+        if (k == 0) onsite_wall<1>(f, make_float3(0.f, 0.f, 0.f));
+        if (k == nz - 1) onsite_wall<-1>(f, utop);
     }
 
     float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
@@ -266,7 +305,7 @@ template <int kMode, class T>
 __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
     const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
     float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
-    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale)
+    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
 {
     __shared__ Ring<T> ring;
     const int tx = threadIdx.x % T::TX, ty = threadIdx.x / T::TX;
@@ -316,6 +355,10 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
             for (int q = 0; q < 19; ++q) f[q] = neq_value<kMode>(raw[q], inv_scale);
             add_feq_all(std::make_integer_sequence<int, 19>{}, f, ring, (k + 3) & 3, k & 3, (k + 1) & 3, own, k,
                         nz, utop);
+            if (onsite) {
+                if (k == 0) onsite_wall<1>(f, make_float3(0.f, 0.f, 0.f));
+                if (k == nz - 1) onsite_wall<-1>(f, utop);
+            }
 
             float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
@@ -378,14 +421,17 @@ __global__ void k_lb_export_mixed(std::integer_sequence<int, Q...>, const typena
 }
 
 // Developed shear profile, post-collision, shifted by w_q; evaluated in FP64.
+// onsite: walls on the end layers (profile u_top k/(nz - 1)); otherwise half
+// a link outside them (u_top (k + 1/2)/nz).
 __global__ void k_lb_init_shear(float* __restrict__ f, int nx, int ny, int nz, double tau,
-                                double ux_top, double uy_top)
+                                double ux_top, double uy_top, int onsite)
 {
     const int N = nx * ny * nz;
+    const double H = onsite ? (double)(nz - 1) : (double)nz, z0 = onsite ? 0.0 : 0.5;
     for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
         const int k = cell / (nx * ny);
-        const double dux = ux_top / nz, duy = uy_top / nz;
-        const double ux = dux * (k + 0.5), uy = duy * (k + 0.5);
+        const double dux = ux_top / H, duy = uy_top / H;
+        const double ux = dux * (k + z0), uy = duy * (k + z0);
         const double uu = ux * ux + uy * uy;
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
@@ -430,13 +476,15 @@ __global__ void k_lb_moments(const float* __restrict__ f, int N, double* __restr
 // non-equilibrium part, evaluated in FP64.
 template <int kMode>
 __global__ void k_lb_init_shear_mixed(typename Neq<kMode>::T* __restrict__ nout, float4* __restrict__ mout, int nx,
-                                      int ny, int nz, double tau, double ux_top, double uy_top, float inv_scale)
+                                      int ny, int nz, double tau, double ux_top, double uy_top, float inv_scale,
+                                      int onsite)
 {
     const int N = nx * ny * nz;
+    const double H = onsite ? (double)(nz - 1) : (double)nz, z0 = onsite ? 0.0 : 0.5;
     for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
         const int k = cell / (nx * ny);
-        const double dux = ux_top / nz, duy = uy_top / nz;
-        mout[cell] = make_float4((float)(dux * (k + 0.5)), (float)(duy * (k + 0.5)), 0.f, 0.f);
+        const double dux = ux_top / H, duy = uy_top / H;
+        mout[cell] = make_float4((float)(dux * (k + z0)), (float)(duy * (k + z0)), 0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
             const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
@@ -505,7 +553,7 @@ void launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body,
     const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
     k_lb_step_mixed<kMode, T><<<grid, T::Threads, 0, s>>>((const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b], c->m[a],
                                                           c->m[b], c->g, c->flags, p.nx, p.ny, p.nz, kz, omega, guo,
-                                                          body, utop, inv_scale);
+                                                          body, utop, inv_scale, p.walls);
 }
 
 template <int kMode>
@@ -537,7 +585,7 @@ int launch_lb_step(LbCtx* c, cudaStream_t s)
         const int bx = want < cap ? want : cap;
         const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
         k_lb_step<<<grid, bx, 0, s>>>((const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1], c->g, c->v, c->flags,
-                                      p.nx, p.ny, p.nz, omega, guo, body, utop);
+                                      p.nx, p.ny, p.nz, omega, guo, body, utop, p.walls);
     }
     }
     c->cur ^= 1;
@@ -560,6 +608,8 @@ extern "C" int lb_query_sizes(const lb_params* p, lb_sizes* out)
         return set_error(PFSI_ERR_ARG, "lb_query_sizes: unknown storage mode");
     if (p->storage == PFSI_LB_FP16 && (p->fp16_exponent < -60 || p->fp16_exponent > 60))
         return set_error(PFSI_ERR_ARG, "lb_query_sizes: fp16_exponent outside -60..60");
+    if (p->walls != PFSI_WALLS_BOUNCEBACK && p->walls != PFSI_WALLS_ONSITE)
+        return set_error(PFSI_ERR_ARG, "lb_query_sizes: unknown wall mode");
     out->n_cells = N;
     out->f_bytes = (size_t)N * 19 * (p->storage == PFSI_LB_FP32 ? sizeof(float) : sizeof(uint16_t));
     out->g_bytes = (size_t)N * sizeof(float4);
@@ -643,14 +693,15 @@ extern "C" int lb_init_shear(lb_ctx* c, void* stream)
     switch (p.storage) {
     case PFSI_LB_BF16:
         k_lb_init_shear_mixed<PFSI_LB_BF16><<<blocks, 256, 0, s>>>((NeqT<PFSI_LB_BF16>*)c->f[c->cur], c->m[c->cur],
-                                                                   p.nx, p.ny, p.nz, tau, ux, uy, 1.0f);
+                                                                   p.nx, p.ny, p.nz, tau, ux, uy, 1.0f, p.walls);
         break;
     case PFSI_LB_FP16:
         k_lb_init_shear_mixed<PFSI_LB_FP16><<<blocks, 256, 0, s>>>((NeqT<PFSI_LB_FP16>*)c->f[c->cur], c->m[c->cur],
-                                                                   p.nx, p.ny, p.nz, tau, ux, uy, inv_scale_of(p));
+                                                                   p.nx, p.ny, p.nz, tau, ux, uy, inv_scale_of(p),
+                                                                   p.walls);
         break;
     default:
-        k_lb_init_shear<<<blocks, 256, 0, s>>>((float*)c->f[c->cur], p.nx, p.ny, p.nz, tau, ux, uy);
+        k_lb_init_shear<<<blocks, 256, 0, s>>>((float*)c->f[c->cur], p.nx, p.ny, p.nz, tau, ux, uy, p.walls);
     }
     return check_launch("lb_init_shear");
 }

@@ -32,7 +32,8 @@ STORAGE = {"fp32": LB_FP32, "bf16": LB_BF16, "fp16": LB_FP16}
 
 class lb_params(ctypes.Structure):
     _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("tau", c_float),
-                ("u_top", c_float * 3), ("body", c_float * 3), ("storage", c_int), ("fp16_exponent", c_int)]
+                ("u_top", c_float * 3), ("body", c_float * 3), ("storage", c_int), ("fp16_exponent", c_int),
+                ("walls", c_int)]
 
 
 class lb_sizes(ctypes.Structure):
@@ -351,12 +352,13 @@ class Lattice:
     (shifted populations) or "bf16" / "fp16" (16-bit f^neq + FP32 moments)."""
 
     def __init__(self, nx, ny, nz, tau, u_top=(0.0, 0.0, 0.0), body=(0.0, 0.0, 0.0), device="cuda",
-                 storage="fp32", fp16_exponent=None):
+                 storage="fp32", fp16_exponent=None, walls=0):
         mode = STORAGE[storage]
         if fp16_exponent is None:
             fp16_exponent = default_fp16_exponent(nz, tau, u_top) if mode == LB_FP16 else 0
         self.storage = storage
-        self.p = lb_params(nx, ny, nz, tau, (c_float * 3)(*u_top), (c_float * 3)(*body), mode, int(fp16_exponent))
+        self.p = lb_params(nx, ny, nz, tau, (c_float * 3)(*u_top), (c_float * 3)(*body), mode, int(fp16_exponent),
+                           int(walls))
         s = lb_query_sizes(self.p)
         self.N = int(s.n_cells)
         self.shape = (nz, ny, nx)
@@ -494,7 +496,7 @@ class Simulation:
     def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None, tune=False):
         g = w["grid"]
         self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device,
-                               storage, fp16_exponent)
+                               storage, fp16_exponent, g.get("walls", 0))
         if tune:   # pick the lattice kernel's launch shape for this grid (before the state is set)
             self.shape, _ = lb_autotune(self.lattice)
         self.lattice.init_shear()

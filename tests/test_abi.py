@@ -63,6 +63,9 @@ def test_lb_query_sizes_mixed_storage(L):
     p = fsi.lb_params(48, 40, 36, 0.8, z, z, fsi.LB_FP16, 61)
     assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
     assert "fp16_exponent" in fsi.last_error()
+    p = fsi.lb_params(48, 40, 36, 0.8, z, z, fsi.LB_FP32, 0, 2)
+    assert L.lb_query_sizes(ctypes.byref(p), ctypes.byref(s)) == -1
+    assert "wall" in fsi.last_error()
 
 
 def test_lb_create_checks_the_storage_mode(L):

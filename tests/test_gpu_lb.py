@@ -101,3 +101,30 @@ def test_conservation_fp64_moments():
     mom = (c.T.astype(np.float64) @ F).sum(1)
     assert abs(m1[0] - F.sum()) < 1e-6 * F.sum()
     assert np.allclose(m1[1:], mom, atol=1e-6 * np.abs(F - w[:, None]).sum())
+
+
+@pytest.mark.parametrize("dims", [(37, 23, 19), (5, 3, 2)])
+def test_onsite_walls(dims):
+    """On-site velocity walls (Eq. 23-30) on the end layers, with a body
+    force and a random perturbation of the developed profile: populations
+    and velocities against the oracle after 12 steps."""
+    nx, ny, nz = dims
+    u_top = (4e-3, -1.5e-3, 0.0)
+    body = (2e-6, 0.0, -1e-6)
+    lat = fsi.Lattice(nx, ny, nz, 0.8, u_top, body, walls=1)
+    lat.init_shear()
+    p = oracle.lb_params(nx, ny, nz, float(np.float32(0.8)), tuple(float(np.float32(u)) for u in u_top),
+                         tuple(float(np.float32(b)) for b in body), walls=1)
+    f = oracle.lb_init_shear(p)
+    torch.cuda.synchronize()
+    assert rel_err(lat.current().cpu().numpy(), shifted_oracle(f)) < 1e-6
+    rng = np.random.default_rng(5)
+    pert = (1e-5 * rng.standard_normal(lat.current().shape)).astype(np.float32)
+    lat.current().add_(torch.from_numpy(pert).cuda())
+    f = f + pert.astype(np.float64).ravel()
+    n = 12
+    lat.step(n)
+    for _ in range(n):
+        f, rho, v = oracle.lb_step(p, f)
+    torch.cuda.synchronize()
+    assert rel_err(lat.current().cpu().numpy(), shifted_oracle(f)) < TOL

@@ -95,3 +95,14 @@ def test_graph_replay_matches_single_calls():
     torch.cuda.synchronize()
     assert rel_err(a.X.cpu().numpy() - w["X"], b.X.cpu().numpy() - w["X"]) < 1e-6
     assert np.array_equal(a.bonds.bound.cpu().numpy(), b.bonds.bound.cpu().numpy())
+
+
+def test_coupled_step_with_onsite_walls():
+    """The coupled step with the on-site velocity walls of Eq. 23-30 (wall
+    planes on the node layers k = 0 and nz - 1; the platelet's wall terms use
+    the plane z = 0)."""
+    w = workload.tiny(seed=6, shear=2.0e4, gap=0.8)
+    w["grid"] = dict(w["grid"], walls=1)
+    w["membrane"] = dict(w["membrane"], z_wall=0.0)
+    w["bonds"] = dict(w["bonds"], z_wall=0.0)
+    compare(w, 20)
