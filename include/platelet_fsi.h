@@ -224,6 +224,13 @@ int membrane_set_params(mem_ctx* ctx, const mem_params* p);
  * device float[3][n_nodes], overwritten. */
 int membrane_forces(mem_ctx* ctx, const double* X, float* F, void* stream);
 
+/* Centroid of every platelet's nodes (membrane and SCE) at positions X:
+ * out_dev (device, 4 * n_plt doubles, 8-byte aligned) receives the
+ * centroids in its first 3 * n_plt entries ([platelet][x, y, z]); the rest is
+ * scratch.  Enqueues only (FP64 sums; the order of the platelet sums is not
+ * fixed, so the last bit may differ between calls). */
+int membrane_centroids(mem_ctx* ctx, const double* X, double* out_dev, void* stream);
+
 /* Per-platelet total area and volume of X (FP64 on the device).
  * out_host[2*n_plt] = {S_0, V_0, S_1, V_1, ...}.  Synchronises. */
 int membrane_measure(mem_ctx* ctx, const double* X, double* out_host, void* stream);
@@ -413,6 +420,26 @@ int sim_destroy(sim_ctx* ctx);
  * ib_interp with advection, bonds_step.  The sequence of one step is captured
  * once into a CUDA graph per lattice-buffer parity and replayed. */
 int sim_step(sim_ctx* ctx, int nsteps, void* stream);
+
+/* nsteps coupled steps, recording the node positions of every step: after
+ * step k, X (double[3][M]) is copied into slot k % ring of dev_ring (device,
+ * ring * 3M doubles) on `stream`, then from there into slot k % ring of
+ * host_ring (pinned host memory, ring * 3M doubles) on a copy stream of the
+ * context, so the device-to-host copy overlaps the next step; a slot is
+ * reused only after its previous copy finished.  2 <= ring <= 64.  Returns
+ * after enqueueing; `stream` is ordered after the last copy (synchronise it
+ * before reading host_ring; slot k % ring then holds step k of the last
+ * `ring` steps). */
+int sim_step_record(sim_ctx* ctx, int nsteps, double* dev_ring, double* host_ring, int ring, void* stream);
+
+/* nsteps coupled steps, following the platelets: after step k the
+ * centroids of all platelets (membrane_centroids, computed inside the step's
+ * graph) are copied to host_out[k][n_plt][3] (pinned host memory,
+ * nsteps * 3 * n_plt doubles) on the context's copy stream, overlapping the
+ * next step.  dev_scratch: device, 8 * n_plt doubles (two slots), kept by the
+ * context's graphs until another scratch is passed.  Returns after enqueueing;
+ * `stream` is ordered after the last copy. */
+int sim_step_track(sim_ctx* ctx, int nsteps, double* dev_scratch, double* host_out, void* stream);
 
 /* Index of the next step (first_step + steps taken). */
 int sim_step_index(const sim_ctx* ctx, uint64_t* out);

@@ -676,6 +676,66 @@ extern "C" int membrane_forces(mem_ctx* c, const double* X, float* F, void* stre
     return launch_membrane_forces(c, X, F, as_stream(stream));
 }
 
+namespace pfsi {
+namespace {
+
+// Per-platelet sums of the node positions and node counts into acc[4 * nplt]
+// (x, y, z sums then counts); lanes of a warp that share a platelet reduce
+// first.
+__global__ void k_centroid_sums(const double* __restrict__ X, int n, const int* __restrict__ node_plt, int nplt,
+                                double* __restrict__ acc)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const int plt = v < n ? node_plt[v] : -1;
+    double s[3] = {0.0, 0.0, 0.0}, cnt = 0.0;
+    if (plt >= 0) {
+        s[0] = X[v];
+        s[1] = X[n + v];
+        s[2] = X[2 * n + v];
+        cnt = 1.0;
+    }
+    const int p0 = __shfl_sync(0xffffffffu, plt, 0);
+    if (__all_sync(0xffffffffu, plt == p0)) {
+        if (p0 < 0) return;
+        for (int o = 16; o > 0; o >>= 1) {
+            for (int d = 0; d < 3; ++d) s[d] += __shfl_down_sync(0xffffffffu, s[d], o);
+            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            for (int d = 0; d < 3; ++d) atomicAdd(&acc[3 * p0 + d], s[d]);
+            atomicAdd(&acc[3 * nplt + p0], cnt);
+        }
+    } else if (plt >= 0) {
+        for (int d = 0; d < 3; ++d) atomicAdd(&acc[3 * plt + d], s[d]);
+        atomicAdd(&acc[3 * nplt + plt], cnt);
+    }
+}
+
+__global__ void k_centroid_finish(double* __restrict__ acc, int nplt)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nplt) return;
+    const double c = acc[3 * nplt + p];
+    for (int d = 0; d < 3; ++d) acc[3 * p + d] = c > 0.0 ? acc[3 * p + d] / c : 0.0;
+}
+
+}  // namespace
+}  // namespace pfsi
+
+extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, void* stream)
+{
+    if (!c || !X || !out_dev) return set_error(PFSI_ERR_ARG, "membrane_centroids: null argument");
+    if (!aligned(out_dev, 8)) return set_error(PFSI_ERR_ARG, "membrane_centroids: misaligned output");
+    cudaStream_t s = as_stream(stream);
+    int rc = check_cuda(cudaMemsetAsync(out_dev, 0, 4 * sizeof(double) * c->nplt, s), "membrane_centroids: clear");
+    if (rc) return rc;
+    k_centroid_sums<<<(c->n + 255) / 256, 256, 0, s>>>(X, c->n, c->node_plt, c->nplt, out_dev);
+    rc = check_launch("membrane_centroids");
+    if (rc) return rc;
+    k_centroid_finish<<<(c->nplt + 127) / 128, 128, 0, s>>>(out_dev, c->nplt);
+    return check_launch("membrane_centroids: finish");
+}
+
 extern "C" int membrane_measure(mem_ctx* c, const double* X, double* out_host, void* stream)
 {
     if (!c || !X || !out_host) return set_error(PFSI_ERR_ARG, "membrane_measure: null argument");

@@ -27,6 +27,14 @@ struct SimCtx {
     cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
     SgCtx* sg;             // learned membrane surrogate, or null (plain solver)
     const void* sg_params;
+    // sim_step_record / sim_step_track: copy stream and per-slot events
+    // (created on first use)
+    cudaStream_t rec;
+    std::vector<cudaEvent_t> rec_ready, rec_freed;
+    // sim_step_track: step + centroids graphs per lattice parity, writing
+    // slot `parity` of trk_scratch
+    double* trk_scratch;
+    cudaGraphExec_t trk_exec[2];
 };
 
 namespace {
@@ -52,7 +60,18 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     return rc;
 }
 
-int capture(SimCtx* c, int parity)
+int enqueue_track(SimCtx* c, cudaStream_t s, int parity)
+{
+    int rc = enqueue_step(c, s);
+    if (!rc)
+        rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, c->trk_scratch + (size_t)parity * 4 * c->mem->nplt,
+                                s);
+    return rc;
+}
+
+// Captures one step (track = 0) or one step plus the platelet centroids
+// (track = 1) starting at lattice parity `parity`.
+int capture(SimCtx* c, int parity, int track = 0)
 {
     const int saved = c->lb->cur;
     c->lb->cur = parity;
@@ -61,7 +80,7 @@ int capture(SimCtx* c, int parity)
         c->lb->cur = saved;
         return rc;
     }
-    const int rc_enq = enqueue_step(c, c->cap);
+    const int rc_enq = track ? enqueue_track(c, c->cap, parity) : enqueue_step(c, c->cap);
     cudaGraph_t graph = nullptr;
     rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
     c->lb->cur = saved;
@@ -70,9 +89,19 @@ int capture(SimCtx* c, int parity)
         return rc_enq;
     }
     if (rc) return rc;
-    rc = check_cuda(cudaGraphInstantiate(&c->exec[parity], graph, 0), "sim: instantiate");
+    rc = check_cuda(cudaGraphInstantiate(track ? &c->trk_exec[parity] : &c->exec[parity], graph, 0), "sim: instantiate");
     cudaGraphDestroy(graph);
     return rc;
+}
+
+void drop_graphs(SimCtx* c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+        c->exec[k] = nullptr;
+        if (c->trk_exec[k]) cudaGraphExecDestroy(c->trk_exec[k]);
+        c->trk_exec[k] = nullptr;
+    }
 }
 
 }  // namespace
@@ -98,6 +127,8 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->M = M;
     c->step = first_step;
     c->exec[0] = c->exec[1] = nullptr;
+    c->trk_exec[0] = c->trk_exec[1] = nullptr;
+    c->trk_scratch = nullptr;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc && bonds) {
@@ -115,11 +146,13 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
 extern "C" int sim_destroy(sim_ctx* c)
 {
     if (!c) return PFSI_OK;
-    for (int k = 0; k < 2; ++k)
-        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
+    drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
     for (int k = 0; k < 2; ++k)
         if (c->lb_ev[k]) cudaEventDestroy(c->lb_ev[k]);
+    for (cudaEvent_t e : c->rec_ready) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->rec_freed) cudaEventDestroy(e);
+    if (c->rec) cudaStreamDestroy(c->rec);
     delete c;
     return PFSI_OK;
 }
@@ -142,15 +175,97 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
     return PFSI_OK;
 }
 
+extern "C" int sim_step_record(sim_ctx* c, int nsteps, double* dev_ring, double* host_ring, int ring, void* stream)
+{
+    if (!c || nsteps < 0 || !dev_ring || !host_ring || ring < 2 || ring > 64)
+        return set_error(PFSI_ERR_ARG, "sim_step_record: bad argument");
+    if (!aligned(dev_ring, 8) || !aligned(host_ring, 8)) return set_error(PFSI_ERR_ARG, "sim_step_record: misaligned ring");
+    cudaStream_t s = as_stream(stream);
+    int rc = PFSI_OK;
+    if (!c->rec) rc = check_cuda(cudaStreamCreateWithFlags(&c->rec, cudaStreamNonBlocking), "sim_step_record: stream");
+    while (!rc && (int)c->rec_ready.size() < ring) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        rc = check_cuda(cudaEventCreateWithFlags(&a, cudaEventDisableTiming), "sim_step_record: event");
+        if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&b, cudaEventDisableTiming), "sim_step_record: event");
+        if (!rc) {
+            c->rec_ready.push_back(a);
+            c->rec_freed.push_back(b);
+        }
+    }
+    if (rc) return rc;
+    const size_t bytes = (size_t)3 * c->M * sizeof(double);
+    for (int k = 0; k < nsteps && !rc; ++k) {
+        const int b = k % ring;
+        rc = sim_step(c, 1, stream);
+        if (!rc && k >= ring) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_record: wait");
+        double* snap = dev_ring + (size_t)b * 3 * c->M;
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(snap, c->X, bytes, cudaMemcpyDeviceToDevice, s), "sim_step_record: snapshot");
+        if (!rc) rc = check_cuda(cudaEventRecord(c->rec_ready[b], s), "sim_step_record: record");
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->rec, c->rec_ready[b], 0), "sim_step_record: wait");
+        if (!rc)
+            rc = check_cuda(cudaMemcpyAsync(host_ring + (size_t)b * 3 * c->M, snap, bytes, cudaMemcpyDeviceToHost, c->rec),
+                            "sim_step_record: copy");
+        if (!rc) rc = check_cuda(cudaEventRecord(c->rec_freed[b], c->rec), "sim_step_record: record");
+    }
+    // the caller's stream covers the last copies
+    for (int b = 0; b < ring && b < nsteps && !rc; ++b)
+        rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_record: join");
+    return rc;
+}
+
+extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, double* host_out, void* stream)
+{
+    if (!c || nsteps < 0 || !dev_scratch || !host_out) return set_error(PFSI_ERR_ARG, "sim_step_track: bad argument");
+    if (!aligned(dev_scratch, 8) || !aligned(host_out, 8)) return set_error(PFSI_ERR_ARG, "sim_step_track: misaligned buffer");
+    cudaStream_t s = as_stream(stream);
+    int rc = PFSI_OK;
+    if (c->trk_scratch != dev_scratch) {
+        for (int k = 0; k < 2; ++k) {
+            if (c->trk_exec[k]) cudaGraphExecDestroy(c->trk_exec[k]);
+            c->trk_exec[k] = nullptr;
+        }
+        c->trk_scratch = dev_scratch;
+    }
+    if (!c->rec) rc = check_cuda(cudaStreamCreateWithFlags(&c->rec, cudaStreamNonBlocking), "sim_step_track: stream");
+    while (!rc && c->rec_ready.size() < 2) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        rc = check_cuda(cudaEventCreateWithFlags(&a, cudaEventDisableTiming), "sim_step_track: event");
+        if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&b, cudaEventDisableTiming), "sim_step_track: event");
+        if (!rc) {
+            c->rec_ready.push_back(a);
+            c->rec_freed.push_back(b);
+        }
+    }
+    const int nplt = c->mem->nplt;
+    const size_t bytes = (size_t)3 * nplt * sizeof(double);
+    for (int k = 0; k < nsteps && !rc; ++k) {
+        const int p = c->lb->cur;   // the step's graph writes slot p of the scratch
+        if (!c->trk_exec[p]) rc = capture(c, p, 1);
+        if (!rc && k >= 2) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[p], 0), "sim_step_track: wait");
+        if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_exec[p], s), "sim_step_track: graph launch");
+        if (!rc) rc = check_cuda(cudaEventRecord(c->rec_ready[p], s), "sim_step_track: record");
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->rec, c->rec_ready[p], 0), "sim_step_track: wait");
+        if (!rc)
+            rc = check_cuda(cudaMemcpyAsync(host_out + (size_t)k * 3 * nplt, dev_scratch + (size_t)p * 4 * nplt, bytes,
+                                            cudaMemcpyDeviceToHost, c->rec),
+                            "sim_step_track: copy");
+        if (!rc) rc = check_cuda(cudaEventRecord(c->rec_freed[p], c->rec), "sim_step_track: record");
+        if (!rc) {
+            c->lb->cur ^= 1;
+            c->step += 1;
+        }
+    }
+    for (int b = 0; b < 2 && b < nsteps && !rc; ++b)
+        rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_track: join");
+    return rc;
+}
+
 extern "C" int sim_set_surrogate(sim_ctx* c, sg_ctx* sg, const void* params)
 {
     if (!c || (sg && !params)) return set_error(PFSI_ERR_ARG, "sim_set_surrogate: bad argument");
     SgCtx* g = sg ? sg_internal(sg) : nullptr;
     if (g && sg_node_count(g) != c->M) return set_error(PFSI_ERR_ARG, "sim_set_surrogate: node count differs");
-    for (int k = 0; k < 2; ++k) {
-        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
-        c->exec[k] = nullptr;
-    }
+    drop_graphs(c);
     c->sg = g;
     c->sg_params = params;
     return PFSI_OK;
@@ -161,9 +276,8 @@ extern "C" int sim_time_lb(sim_ctx* c, int on)
     if (!c) return set_error(PFSI_ERR_ARG, "sim_time_lb: null context");
     const bool want = on != 0;
     if (want == (c->lb_ev[0] != nullptr)) return PFSI_OK;
+    drop_graphs(c);
     for (int k = 0; k < 2; ++k) {
-        if (c->exec[k]) cudaGraphExecDestroy(c->exec[k]);
-        c->exec[k] = nullptr;
         if (c->lb_ev[k]) cudaEventDestroy(c->lb_ev[k]);
         c->lb_ev[k] = nullptr;
     }

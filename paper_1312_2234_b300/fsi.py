@@ -78,6 +78,7 @@ _SIGS = {
     "membrane_forces": [P, P, P, P],
     "membrane_measure": [P, P, ctypes.POINTER(c_double), P],
     "membrane_measure_static": [P, P, ctypes.POINTER(c_double), P],
+    "membrane_centroids": [P, P, P, P],
     "bonds_query_workspace": [ctypes.POINTER(bond_params), c_int, ctypes.POINTER(c_size_t)],
     "bonds_create": [ctypes.POINTER(bond_params), c_int, P, P, P, P, P, P, c_size_t, ctypes.POINTER(P)],
     "bonds_destroy": [P],
@@ -90,6 +91,8 @@ _SIGS = {
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
     "sim_time_lb": [P, c_int],
     "sim_set_surrogate": [P, P, P],
+    "sim_step_record": [P, c_int, P, P, c_int, P],
+    "sim_step_track": [P, c_int, P, P, P],
     "lb_set_shape": [P, c_int],
     "lb_get_shape": [P, ctypes.POINTER(c_int)],
     "lb_autotune": [P, c_int, P, ctypes.POINTER(ctypes.c_float)],
@@ -444,6 +447,14 @@ class Membrane:
     def measure(self, X):
         return membrane_measure(self.h, X, self.n_plt)
 
+    def centroids(self, X, out=None, stream=None):
+        """Per-platelet node centroids [n_plt][3] on the device (out: device
+        float64 buffer of 4 * n_plt, reused if given)."""
+        if out is None:
+            out = torch.empty(4 * self.n_plt, dtype=torch.float64, device=X.device)
+        _call("membrane_centroids", self.h, _ptr(X), _ptr(out), _stream(stream))
+        return out[:3 * self.n_plt].view(self.n_plt, 3)
+
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
             _lib.membrane_destroy(self.h)
@@ -515,6 +526,20 @@ class Simulation:
 
     def step(self, n=1, stream=None):
         sim_step(self.h, n, stream)
+
+    def step_record(self, n, dev_ring, host_ring, stream=None):
+        """n steps, each step's positions copied to the pinned host ring
+        [ring][3M] through the device ring [ring][3M], overlapping the next
+        step (see sim_step_record)."""
+        ring = int(host_ring.shape[0])
+        assert host_ring.is_pinned() and dev_ring.shape == host_ring.shape
+        _call("sim_step_record", self.h, int(n), _ptr(dev_ring), _ptr(host_ring), ring, _stream(stream))
+
+    def step_track(self, n, dev_scratch, host_out, stream=None):
+        """n steps; after step k the platelet centroids go to host_out[k]
+        (pinned, [n][n_plt][3] float64) through dev_scratch (device, 8 n_plt)."""
+        assert host_out.is_pinned() and host_out.shape[0] >= n
+        _call("sim_step_track", self.h, int(n), _ptr(dev_scratch), _ptr(host_out), _stream(stream))
 
     @property
     def step_index(self):

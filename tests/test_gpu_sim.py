@@ -106,3 +106,46 @@ def test_coupled_step_with_onsite_walls():
     w["membrane"] = dict(w["membrane"], z_wall=0.0)
     w["bonds"] = dict(w["bonds"], z_wall=0.0)
     compare(w, 20)
+
+
+def test_step_record_copies_every_step():
+    """sim_step_record: slot k % ring of the pinned host ring holds the
+    positions after step k (for the last `ring` steps), the same as stepping
+    one at a time and reading X back."""
+    w = workload.tiny(seed=7, shear=2.0e4)
+    a = fsi.Simulation(w)
+    b = fsi.Simulation(w)
+    M = w["M"]
+    ring, n = 3, 7
+    dev_ring = torch.empty(ring, 3 * M, dtype=torch.float64, device="cuda")
+    host_ring = torch.empty(ring, 3 * M, dtype=torch.float64).pin_memory()
+    a.step_record(n, dev_ring, host_ring)
+    torch.cuda.synchronize()
+    ref = []
+    for _ in range(n):
+        b.step(1)
+        ref.append(b.X.cpu().numpy())
+    for k in range(n - ring, n):
+        got = host_ring[k % ring].numpy()
+        assert np.abs(got - ref[k]).max() <= 1e-6 * np.abs(ref[k] - w["X"]).max() + 1e-12, k
+    assert a.step_index == n
+
+
+def test_step_track_follows_the_centroids():
+    """sim_step_track: after step k, host_out[k] holds each platelet's node
+    centroid, as stepping one at a time and averaging X per platelet."""
+    w = workload.tiny(seed=8, shear=2.0e4, n_plt=2, centers=[(6.3, 9.6, 2.2), (17.4, 9.9, 3.1)], orient="flat")
+    a = fsi.Simulation(w)
+    b = fsi.Simulation(w)
+    M = w["M"]
+    n, nplt = 5, 2
+    scratch = torch.empty(8 * nplt, dtype=torch.float64, device="cuda")
+    out = torch.zeros(n, nplt, 3, dtype=torch.float64).pin_memory()
+    a.step_track(n, scratch, out)
+    torch.cuda.synchronize()
+    plt = np.asarray(w["mesh"]["node_plt"])
+    for k in range(n):
+        b.step(1)
+        X = b.X.cpu().numpy().reshape(3, M)
+        ref = np.stack([X[:, plt == p].mean(1) for p in range(nplt)])
+        assert np.allclose(out[k].numpy(), ref, rtol=0, atol=1e-9)
