@@ -303,6 +303,48 @@ int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* strea
 int bonds_status(bond_ctx* ctx, long long* out_host);
 
 /* ===================================================================== *
+ * Finite-element bending, Section 3.1 (Eq. 6-10)
+ *
+ * The membrane is covered by quadratic six-node triangles (Eq. 7):
+ * elem6[6 e + 0..2] are an element's corners, counter-clockwise seen from
+ * outside (parametric (0,0), (1,0), (0,1)), elem6[6 e + 3..5] the nodes at
+ * the midpoints of edges 0-1, 1-2, 2-0.  One evaluation:
+ *   1. unit normal at every element node, averaged over the elements sharing
+ *      the node (sum of unit normals, normalised);
+ *   2. Eq. 9 at every element node: [dX/dxi; dX/deta; n] kappa =
+ *      [dn/dxi; dn/deta; 0] with the nodal normals interpolated by Eq. 7;
+ *      K = tr(kappa)/2 (Eq. 10) and K_G = kappa_1 kappa_2, each averaged
+ *      (plain mean) over the elements sharing the node;
+ *   3. Lap_S K: the surface gradient of K by the same system, averaged per
+ *      node, then its surface divergence, averaged per node;
+ *   4. F_i = A_i (k0/2) (Lap_S K + 2 K (K^2 - K_G)) n_i: the first variation
+ *      of H = (k0/2) int K^2 dS (Eq. 6).  The force printed after Eq. 10
+ *      lacks k0/2 and the Gaussian-curvature term, without which a sphere
+ *      would not be force-free.  A_i: one third of each of the flat
+ *      sub-triangles (0,3,5), (3,1,4), (5,4,2), (3,4,5) that touch node i.
+ * FP32 arithmetic in coordinates relative to each element's first corner;
+ * the node averages are fixed-order sums (deterministic).  Nodes of no
+ * element (SCE elements) get no force.
+ * ===================================================================== */
+typedef struct fem_ctx fem_ctx;
+
+/* Workspace bytes for n_nodes nodes and n_elem six-node elements. */
+int fem_query_workspace(int n_nodes, int n_elem, size_t* bytes);
+/* Builds the node -> element-node lists on the host and copies them and
+ * elem6 (host int[6*n_elem]) into the device workspace (caller-owned,
+ * 256-byte aligned, fem_query_workspace bytes; kept until fem_destroy).
+ * Rejects node indices outside [0, n_nodes) and elements with a repeated
+ * node (PFSI_ERR_ARG).  Synchronises. */
+int fem_create(int n_nodes, int n_elem, const int* elem6, void* ws, size_t ws_bytes, fem_ctx** out);
+int fem_destroy(fem_ctx* ctx);
+/* X: device double[3][n_nodes]; F: device float[3][n_nodes], overwritten
+ * (accumulate = 0) or added to.  Enqueues 8 kernels on `stream`. */
+int fem_bending_forces(fem_ctx* ctx, float k0, const double* X, float* F, int accumulate, void* stream);
+/* Diagnostics of the same passes: fields (device float[7][n_nodes])
+ * receives n_x, n_y, n_z, A, K, K_G, Lap_S K per node. */
+int fem_fields(fem_ctx* ctx, const double* X, float* fields, void* stream);
+
+/* ===================================================================== *
  * Learned membrane surrogate (no paper counterpart)
  *
  * A per-node network 27 -> 128 -> 128 -> 3 (GELU, tanh form) stands for the
@@ -448,6 +490,13 @@ int sim_step_index(const sim_ctx* ctx, uint64_t* out);
  * (sg_membrane_forces in place of membrane_forces); sg = NULL returns to
  * the plain solver (the fallback).  The graphs are recaptured. */
 int sim_set_surrogate(sim_ctx* ctx, sg_ctx* sg, const void* params);
+
+/* Adds the finite-element bending force (fem_bending_forces with modulus k0)
+ * to the membrane forces of every following step; give the membrane context
+ * k_b = 0 so that the dihedral term is not counted twice.  fem = NULL removes
+ * it.  The mesh must have the simulation's node count.  The graphs are
+ * recaptured. */
+int sim_set_fem_bending(sim_ctx* ctx, fem_ctx* fem, float k0);
 
 /* Measurement aid (no paper counterpart): on != 0 records two CUDA events
  * around the lattice Boltzmann kernel inside the step graph (the graphs are

@@ -268,6 +268,12 @@ class Sim:
         self.mesh = Mesh(m["X0"], m["tri"], m["pairs"], m["node_plt"], m["is_membrane"], m["n_plt"])
         self.tri = np.ascontiguousarray(m["tri"], dtype=np.int32).ravel()
         self.memp = w["membrane"]
+        # finite-element bending (Eq. 6-10) in place of the dihedral term
+        self.fem = self.memp.get("bending", "dihedral") == "fem"
+        if self.fem:
+            self.memp = dict(self.memp, k_b=0.0)
+            self.elem6 = np.asarray(m["elem6"], dtype=np.int64).reshape(-1, 6)
+            self.k0 = float(w["membrane"]["k0"])
         self.bondp = w["bonds"]
         self.site_tri = np.ascontiguousarray(w["sites"]["tri"], dtype=np.int32)
         self.site_w = np.ascontiguousarray(w["sites"]["w"], dtype=np.float64).ravel()
@@ -287,6 +293,9 @@ class Sim:
     def step(self):
         # 1. forces on the Lagrangian nodes
         self.F = self.mesh.forces(self.memp, self.X)
+        if self.fem:
+            from . import fem
+            self.F += fem.forces_soa(self.X, self.elem6, self.k0)
         bond_forces(self.bondp, self.site_tri, self.site_w, self.tri, self.bound, self.X, self.F)
         # 2. spread
         self.g = ib_spread(self.p, self.X, self.F)

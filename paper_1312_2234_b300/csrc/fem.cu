@@ -1,0 +1,364 @@
+// fem.cu -- finite-element bending of the hybrid membrane (Section 3.1,
+// Eq. 6-10): curvature from quadratic six-node triangles and the normal
+// bending force that follows from the energy of Eq. 6.
+//
+// The surface is covered by six-node elements (corners at parametric
+// (0,0), (1,0), (0,1), then the midpoints of edges 0-1, 1-2, 2-0); a nodal
+// field is interpolated on an element with the quadratic basis of Eq. 7.
+// One force evaluation is four element passes, each followed by a node pass
+// that averages the element values over the elements sharing the node (a
+// fixed-order gather through a node -> element-node list, no atomics):
+//
+//   pass 0  unit normal dX/dxi x dX/deta at every element node, and the
+//           node's share (one third) of the flat sub-triangles touching it;
+//           node: normals summed and normalised, areas summed;
+//   pass 1  Eq. 9: kappa solves [dX/dxi; dX/deta; n] kappa =
+//           [dn/dxi; dn/deta; 0] with n the nodal normals interpolated by
+//           Eq. 7.  With c0 = (a_eta x n)/det, c1 = (n x a_xi)/det (the first
+//           two columns of the inverse of the row matrix), kappa =
+//           c0 (x) dn/dxi + c1 (x) dn/deta, so K = tr(kappa)/2 (Eq. 10) and
+//           K_G = (c0.dn_xi)(c1.dn_eta) - (c0.dn_eta)(c1.dn_xi);
+//           node: means of K and K_G;
+//   pass 2  surface gradient of K: g = c0 dK/dxi + c1 dK/deta; node: mean;
+//   pass 3  surface divergence of g: c0.dg/dxi + c1.dg/deta; node: mean
+//           (= Lap_S K), then F_i = A_i (k0/2)(Lap_S K + 2K(K^2 - K_G)) n_i.
+//
+// Positions are FP64; every element works in coordinates relative to its
+// first corner (FP64 differences rounded to FP32), so the FP32 derivatives
+// do not lose the digits of the absolute position.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "pfsi_internal.cuh"
+
+namespace pfsi {
+
+struct FemCtx {
+    int n, ne;
+    const int* off;     // [n+1] node -> element-node list
+    const int* list;    // [6 ne] entries 6 e + j
+    const int* elem;    // [6 ne]
+    float4* slot;       // [6 ne] per element-node values of the current pass
+    float4* nrm;        // [n] (unit normal, area)
+    float4* curv;       // [n] (K, K_G, Lap_S K, -)
+    float4* grad;       // [n] (surface gradient of K, -)
+};
+
+namespace {
+
+constexpr int kFemThreads = 256;
+
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// d/dxi and d/deta of the six quadratic basis functions of Eq. 7 at element
+// node j (parametric (0,0), (1,0), (0,1), (1/2,0), (1/2,1/2), (0,1/2)).
+__device__ __forceinline__ void basis_derivatives(int j, float dxi[6], float deta[6])
+{
+    const float xi = (j == 1 || j == 3 || j == 4) ? (j == 1 ? 1.0f : 0.5f) : 0.0f;
+    const float eta = (j == 2 || j == 4 || j == 5) ? (j == 2 ? 1.0f : 0.5f) : 0.0f;
+    const float z = 1.0f - xi - eta;
+    dxi[0] = 1.0f - 4.0f * z;
+    dxi[1] = 4.0f * xi - 1.0f;
+    dxi[2] = 0.0f;
+    dxi[3] = 4.0f * (z - xi);
+    dxi[4] = 4.0f * eta;
+    dxi[5] = -4.0f * eta;
+    deta[0] = 1.0f - 4.0f * z;
+    deta[1] = 0.0f;
+    deta[2] = 4.0f * eta - 1.0f;
+    deta[3] = -4.0f * xi;
+    deta[4] = 4.0f * xi;
+    deta[5] = 4.0f * (z - eta);
+}
+
+struct ElemNode {
+    int idx[6];     // global nodes of the element
+    float3 d[6];    // positions relative to corner 0
+    float dxi[6], deta[6];
+    float3 a_xi, a_eta;
+};
+
+__device__ __forceinline__ void load_element(const int* __restrict__ elem, const double* __restrict__ X, int n, int e,
+                                             int j, ElemNode& E)
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) E.idx[k] = __ldg(elem + 6 * e + k);
+    const int i0 = E.idx[0];
+    const double x0 = __ldg(X + i0), y0 = __ldg(X + n + i0), z0 = __ldg(X + 2 * n + i0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int i = E.idx[k];
+        E.d[k] = make_float3((float)(__ldg(X + i) - x0), (float)(__ldg(X + n + i) - y0), (float)(__ldg(X + 2 * n + i) - z0));
+    }
+    basis_derivatives(j, E.dxi, E.deta);
+    float3 ax = make_float3(0.f, 0.f, 0.f), ae = ax;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ax = ax + E.dxi[k] * E.d[k];
+        ae = ae + E.deta[k] * E.d[k];
+    }
+    E.a_xi = ax;
+    E.a_eta = ae;
+}
+
+__device__ __forceinline__ float tri_area(float3 a, float3 b, float3 c)
+{
+    const float3 n = cross3(b - a, c - a);
+    return 0.5f * sqrtf(dot3(n, n));
+}
+
+// Columns c0, c1 of the inverse of the row matrix [a_xi; a_eta; n].
+__device__ __forceinline__ void tangential_inverse(const ElemNode& E, float3 n, float3& c0, float3& c1)
+{
+    const float3 en = cross3(E.a_eta, n);
+    const float inv = 1.0f / dot3(E.a_xi, en);
+    c0 = inv * en;
+    c1 = inv * cross3(n, E.a_xi);
+}
+
+template <int Pass>
+__global__ void __launch_bounds__(kFemThreads) k_fem_elem(FemCtx c, const double* __restrict__ X)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 6 * c.ne) return;
+    const int e = t / 6, j = t - 6 * e;
+    ElemNode E;
+    load_element(c.elem, X, c.n, e, j, E);
+    float4 out;
+    if (Pass == 0) {
+        float3 nv = cross3(E.a_xi, E.a_eta);
+        nv = rsqrtf(dot3(nv, nv)) * nv;
+        // sub-triangles (0,3,5), (3,1,4), (5,4,2), (3,4,5): corners touch one,
+        // midpoints three
+        float a = 0.f;
+        if (j == 0 || j == 3 || j == 5) a += tri_area(E.d[0], E.d[3], E.d[5]);
+        if (j == 1 || j == 3 || j == 4) a += tri_area(E.d[3], E.d[1], E.d[4]);
+        if (j == 2 || j == 4 || j == 5) a += tri_area(E.d[5], E.d[4], E.d[2]);
+        if (j >= 3) a += tri_area(E.d[3], E.d[4], E.d[5]);
+        out = make_float4(nv.x, nv.y, nv.z, a * (1.0f / 3.0f));
+    } else {
+        const float3 nj = f3(c.nrm[E.idx[j]]);
+        float3 c0, c1;
+        tangential_inverse(E, nj, c0, c1);
+        if (Pass == 1) {
+            float3 dn_xi = make_float3(0.f, 0.f, 0.f), dn_eta = dn_xi;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float3 nk = f3(c.nrm[E.idx[k]]);
+                dn_xi = dn_xi + E.dxi[k] * nk;
+                dn_eta = dn_eta + E.deta[k] * nk;
+            }
+            const float p = dot3(c0, dn_xi), q = dot3(c1, dn_eta);
+            const float r = dot3(c0, dn_eta), s = dot3(c1, dn_xi);
+            out = make_float4(0.5f * (p + q), p * q - r * s, 0.f, 0.f);
+        } else if (Pass == 2) {
+            float k_xi = 0.f, k_eta = 0.f;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float Kk = c.curv[E.idx[k]].x;
+                k_xi += E.dxi[k] * Kk;
+                k_eta += E.deta[k] * Kk;
+            }
+            const float3 g = k_xi * c0 + k_eta * c1;
+            out = make_float4(g.x, g.y, g.z, 0.f);
+        } else {
+            float3 g_xi = make_float3(0.f, 0.f, 0.f), g_eta = g_xi;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float3 gk = f3(c.grad[E.idx[k]]);
+                g_xi = g_xi + E.dxi[k] * gk;
+                g_eta = g_eta + E.deta[k] * gk;
+            }
+            out = make_float4(dot3(c0, g_xi) + dot3(c1, g_eta), 0.f, 0.f, 0.f);
+        }
+    }
+    c.slot[t] = out;
+}
+
+// Node pass: fixed-order sum over the node's element nodes.  Pass 3 also
+// writes the force (F [3][n], added if `accumulate`) and, if `fields` is
+// non-null, the nodal fields [7][n]: n_x, n_y, n_z, A, K, K_G, Lap_S K.
+template <int Pass>
+__global__ void __launch_bounds__(kFemThreads)
+    k_fem_node(FemCtx c, float k0, float* __restrict__ F, int accumulate, float* __restrict__ fields)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n) return;
+    const int b = __ldg(c.off + i), en = __ldg(c.off + i + 1);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = b; k < en; ++k) {
+        const float4 v = c.slot[__ldg(c.list + k)];
+        s.x += v.x;
+        s.y += v.y;
+        s.z += v.z;
+        s.w += v.w;
+    }
+    const int cnt = en - b;
+    const float inv = cnt > 0 ? 1.0f / (float)cnt : 0.f;
+    if (Pass == 0) {
+        const float L2 = s.x * s.x + s.y * s.y + s.z * s.z;
+        const float r = L2 > 0.f ? rsqrtf(L2) : 0.f;
+        c.nrm[i] = make_float4(r * s.x, r * s.y, r * s.z, s.w);
+    } else if (Pass == 1) {
+        c.curv[i] = make_float4(inv * s.x, inv * s.y, 0.f, 0.f);
+    } else if (Pass == 2) {
+        c.grad[i] = make_float4(inv * s.x, inv * s.y, inv * s.z, 0.f);
+    } else {
+        const float lap = inv * s.x;
+        const float4 kv = c.curv[i];
+        const float4 nv = c.nrm[i];
+        const float K = kv.x, KG = kv.y;
+        const float m = cnt > 0 ? nv.w * 0.5f * k0 * (lap + 2.0f * K * (K * K - KG)) : 0.f;
+        if (F) {
+            const float fx = m * nv.x, fy = m * nv.y, fz = m * nv.z;
+            if (accumulate) {
+                F[i] += fx;
+                F[c.n + i] += fy;
+                F[2 * c.n + i] += fz;
+            } else {
+                F[i] = fx;
+                F[c.n + i] = fy;
+                F[2 * c.n + i] = fz;
+            }
+        }
+        if (fields) {
+            const size_t n = (size_t)c.n;
+            fields[i] = nv.x;
+            fields[n + i] = nv.y;
+            fields[2 * n + i] = nv.z;
+            fields[3 * n + i] = nv.w;
+            fields[4 * n + i] = K;
+            fields[5 * n + i] = KG;
+            fields[6 * n + i] = lap;
+        }
+    }
+}
+
+struct FemLayout {
+    size_t off, list, elem, slot, nrm, curv, grad, total;
+};
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+FemLayout fem_layout(int n, int ne)
+{
+    FemLayout L;
+    size_t o = 0;
+    L.off = o;
+    o += up256(4 * (size_t)(n + 1));
+    L.list = o;
+    o += up256(4 * 6 * (size_t)ne);
+    L.elem = o;
+    o += up256(4 * 6 * (size_t)ne);
+    L.slot = o;
+    o += up256(16 * 6 * (size_t)ne);
+    L.nrm = o;
+    o += up256(16 * (size_t)n);
+    L.curv = o;
+    o += up256(16 * (size_t)n);
+    L.grad = o;
+    o += up256(16 * (size_t)n);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+int launch_fem_forces(FemCtx* c, float k0, const double* X, float* F, int accumulate, float* fields, cudaStream_t s)
+{
+    const int ge = (6 * c->ne + kFemThreads - 1) / kFemThreads;
+    const int gn = (c->n + kFemThreads - 1) / kFemThreads;
+    const FemCtx v = *c;
+    k_fem_elem<0><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_node<0><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
+    k_fem_elem<1><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_node<1><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
+    k_fem_elem<2><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_node<2><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
+    k_fem_elem<3><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_node<3><<<gn, kFemThreads, 0, s>>>(v, k0, F, accumulate, fields);
+    return check_launch("fem bending");
+}
+
+}  // namespace pfsi
+
+using namespace pfsi;
+
+struct fem_ctx {
+    FemCtx d;
+    void* ws;
+};
+
+namespace pfsi {
+FemCtx* fem_internal(fem_ctx* c) { return c ? &c->d : nullptr; }
+int fem_node_count(const FemCtx* c) { return c->n; }
+}
+
+extern "C" int fem_query_workspace(int n_nodes, int n_elem, size_t* bytes)
+{
+    if (!bytes || n_nodes < 1 || n_elem < 1) return set_error(PFSI_ERR_ARG, "fem_query_workspace: bad argument");
+    *bytes = fem_layout(n_nodes, n_elem).total;
+    return PFSI_OK;
+}
+
+extern "C" int fem_create(int n_nodes, int n_elem, const int* elem6, void* ws, size_t ws_bytes, fem_ctx** out)
+{
+    if (!out || n_nodes < 1 || n_elem < 1 || !elem6 || !ws) return set_error(PFSI_ERR_ARG, "fem_create: bad argument");
+    if (!aligned(ws, 256)) return set_error(PFSI_ERR_ARG, "fem_create: workspace must be 256-byte aligned");
+    const FemLayout L = fem_layout(n_nodes, n_elem);
+    if (ws_bytes < L.total) return set_error(PFSI_ERR_ARG, "fem_create: workspace too small");
+    std::vector<int> off(n_nodes + 1, 0), list(6 * (size_t)n_elem);
+    for (int e = 0; e < n_elem; ++e) {
+        for (int j = 0; j < 6; ++j) {
+            const int i = elem6[6 * e + j];
+            if (i < 0 || i >= n_nodes) return set_error(PFSI_ERR_ARG, "fem_create: node index out of range");
+            for (int k = 0; k < j; ++k)
+                if (elem6[6 * e + k] == i) return set_error(PFSI_ERR_ARG, "fem_create: repeated node in an element");
+            off[i + 1] += 1;
+        }
+    }
+    for (int i = 0; i < n_nodes; ++i) off[i + 1] += off[i];
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (int t = 0; t < 6 * n_elem; ++t) list[fill[elem6[t]]++] = t;   // ascending element-node order per node
+    char* b = (char*)ws;
+    int rc = check_cuda(cudaMemset(ws, 0, L.total), "fem_create: clear");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.off, off.data(), 4 * off.size(), cudaMemcpyHostToDevice), "fem_create");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.list, list.data(), 4 * list.size(), cudaMemcpyHostToDevice), "fem_create");
+    if (!rc) rc = check_cuda(cudaMemcpy(b + L.elem, elem6, 4 * 6 * (size_t)n_elem, cudaMemcpyHostToDevice), "fem_create");
+    if (rc) return rc;
+    fem_ctx* c = new fem_ctx();
+    c->d = FemCtx{n_nodes, n_elem, (const int*)(b + L.off), (const int*)(b + L.list), (const int*)(b + L.elem),
+                  (float4*)(b + L.slot), (float4*)(b + L.nrm), (float4*)(b + L.curv), (float4*)(b + L.grad)};
+    c->ws = ws;
+    *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int fem_destroy(fem_ctx* c)
+{
+    delete c;
+    return PFSI_OK;
+}
+
+extern "C" int fem_bending_forces(fem_ctx* c, float k0, const double* X, float* F, int accumulate, void* stream)
+{
+    if (!c || !X || !F) return set_error(PFSI_ERR_ARG, "fem_bending_forces: bad argument");
+    if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "fem_bending_forces: misaligned buffer");
+    return launch_fem_forces(&c->d, k0, X, F, accumulate ? 1 : 0, nullptr, as_stream(stream));
+}
+
+extern "C" int fem_fields(fem_ctx* c, const double* X, float* fields, void* stream)
+{
+    if (!c || !X || !fields) return set_error(PFSI_ERR_ARG, "fem_fields: bad argument");
+    if (!aligned(X, 8) || !aligned(fields, 4)) return set_error(PFSI_ERR_ARG, "fem_fields: misaligned buffer");
+    return launch_fem_forces(&c->d, 0.0f, X, nullptr, 0, fields, as_stream(stream));
+}

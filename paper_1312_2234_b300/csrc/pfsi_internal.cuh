@@ -180,6 +180,14 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
 SgCtx* sg_internal(sg_ctx* c);
 int sg_node_count(const SgCtx* c);
 
+struct FemCtx;
+// Finite-element bending force (Eq. 6-10): F (+)= the nodal force; fields
+// (nullable) receives the nodal normals, areas and curvatures.
+int launch_fem_forces(FemCtx* c, float k0, const double* X, float* F, int accumulate, float* fields,
+                      cudaStream_t s);
+FemCtx* fem_internal(fem_ctx* c);
+int fem_node_count(const FemCtx* c);
+
 }  // namespace pfsi
 
 struct lb_ctx : pfsi::LbCtx {};

@@ -27,6 +27,8 @@ struct SimCtx {
     cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
     SgCtx* sg;             // learned membrane surrogate, or null (plain solver)
     const void* sg_params;
+    FemCtx* fem;           // finite-element bending, or null
+    float fem_k0;
     // sim_step_record / sim_step_track: copy stream and per-slot events
     // (created on first use)
     cudaStream_t rec;
@@ -48,6 +50,7 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     } else {
         rc = launch_membrane_forces(c->mem, c->X, c->F, s);
     }
+    if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->F, 1, nullptr, s);
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->lb_ev[0])
@@ -129,6 +132,8 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->exec[0] = c->exec[1] = nullptr;
     c->trk_exec[0] = c->trk_exec[1] = nullptr;
     c->trk_scratch = nullptr;
+    c->fem = nullptr;
+    c->fem_k0 = 0.0f;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc && bonds) {
@@ -258,6 +263,17 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     for (int b = 0; b < 2 && b < nsteps && !rc; ++b)
         rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_track: join");
     return rc;
+}
+
+extern "C" int sim_set_fem_bending(sim_ctx* c, fem_ctx* fem, float k0)
+{
+    if (!c) return set_error(PFSI_ERR_ARG, "sim_set_fem_bending: bad argument");
+    FemCtx* f = fem_internal(fem);
+    if (f && fem_node_count(f) != c->M) return set_error(PFSI_ERR_ARG, "sim_set_fem_bending: node count differs");
+    drop_graphs(c);
+    c->fem = f;
+    c->fem_k0 = k0;
+    return PFSI_OK;
 }
 
 extern "C" int sim_set_surrogate(sim_ctx* c, sg_ctx* sg, const void* params)

@@ -91,6 +91,12 @@ _SIGS = {
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
     "sim_time_lb": [P, c_int],
     "sim_set_surrogate": [P, P, P],
+    "fem_query_workspace": [c_int, c_int, ctypes.POINTER(c_size_t)],
+    "fem_create": [c_int, c_int, P, P, c_size_t, ctypes.POINTER(P)],
+    "fem_destroy": [P],
+    "fem_bending_forces": [P, c_float, P, P, c_int, P],
+    "fem_fields": [P, P, P, P],
+    "sim_set_fem_bending": [P, P, c_float],
     "sim_step_record": [P, c_int, P, P, c_int, P],
     "sim_step_track": [P, c_int, P, P, P],
     "lb_set_shape": [P, c_int],
@@ -511,7 +517,12 @@ class Simulation:
         if tune:   # pick the lattice kernel's launch shape for this grid (before the state is set)
             self.shape, _ = lb_autotune(self.lattice)
         self.lattice.init_shear()
-        self.membrane = Membrane(w["membrane"], w["mesh"], device)
+        memp = w["membrane"]
+        self.fem = None
+        if memp.get("bending", "dihedral") == "fem":   # Eq. 6-10 in place of the dihedral term
+            memp = dict(memp, k_b=0.0)
+            self.fem = FemBending(w["mesh"], device)
+        self.membrane = Membrane(memp, w["mesh"], device)
         self.M = int(w["M"])
         self.X = torch.as_tensor(np.ascontiguousarray(w["X"], dtype=np.float64), device=device).clone()
         self.F = torch.zeros(3 * self.M, dtype=torch.float32, device=device)
@@ -523,6 +534,8 @@ class Simulation:
                                w["lig_count"], device)
         self.h = sim_create(self.lattice.h, self.membrane.h, self.bonds.h if self.bonds else None,
                             self.X, self.F, self.U, self.M, first_step)
+        if self.fem is not None:
+            _call("sim_set_fem_bending", self.h, self.fem.h, float(w["membrane"]["k0"]))
 
     def step(self, n=1, stream=None):
         sim_step(self.h, n, stream)
@@ -548,6 +561,40 @@ class Simulation:
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
             _lib.sim_destroy(self.h)
+            self.h = None
+
+
+# ---------------------------------------------------------------- finite-element bending
+FEM_FIELDS = ("nx", "ny", "nz", "A", "K", "KG", "lapK")
+
+
+class FemBending:
+    """Six-node element mesh of the finite-element bending term (Eq. 6-10)."""
+
+    def __init__(self, mesh, device="cuda"):
+        n = int(np.asarray(mesh["node_plt"]).size)
+        e6 = np.ascontiguousarray(mesh["elem6"], dtype=np.int32).ravel()
+        nb = c_size_t()
+        _call("fem_query_workspace", n, e6.size // 6, ctypes.byref(nb))
+        self.ws = _bytes(nb.value, device)
+        h = c_void_p()
+        _call("fem_create", n, e6.size // 6, _ptr(e6), _ptr(self.ws), nb.value, ctypes.byref(h))
+        self.h = h
+        self.n = n
+        self.device = device
+
+    def forces(self, k0, X, F, accumulate=False, stream=None):
+        _call("fem_bending_forces", self.h, float(k0), _ptr(X), _ptr(F), int(bool(accumulate)), _stream(stream))
+
+    def fields(self, X, stream=None):
+        """Nodal normals, areas and curvatures: dict of float32 device tensors."""
+        out = torch.empty(7, self.n, dtype=torch.float32, device=self.device)
+        _call("fem_fields", self.h, _ptr(X), _ptr(out), _stream(stream))
+        return {k: out[i] for i, k in enumerate(FEM_FIELDS)}
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.fem_destroy(self.h)
             self.h = None
 
 

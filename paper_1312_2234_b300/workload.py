@@ -80,6 +80,8 @@ def lattice_units(tau: float, phys: dict | None = None) -> dict:
             k_t=k_area / (E_u / h ** 2),
             k_v=k_vol / (E_u / h ** 3),
             k_b=(2.0 * k0 / math.sqrt(3.0)) / E_u,
+            k0=k0 / E_u,            # Eq. 6 modulus, for the finite-element bending
+            bending="dihedral",     # or "fem": Eq. 6-10 on quadratic six-node elements
             morse_D=k_lat / (2.0 * a_m * a_m),  # reading: 2 D a^2 = k
             morse_a=a_m,
             rep_F0=P["rep_F0"] / E_u,
@@ -106,10 +108,24 @@ def lattice_units(tau: float, phys: dict | None = None) -> dict:
 # ---------------------------------------------------------------------------
 def icosphere(level: int):
     """Unit icosphere: 10*4^level + 2 vertices, outward counter-clockwise faces."""
+    V, F, _ = icosphere_elements(level)
+    return V, F
+
+
+def icosphere_elements(level: int):
+    """Unit icosphere with its quadratic six-node elements.
+
+    Returns (V, F, E6).  For level >= 1 every triangle of the previous level
+    is split into four by its edge midpoints; E6[e] = (a, b, c, m_ab, m_bc,
+    m_ca) lists that parent triangle's corners (outward counter-clockwise)
+    and its three midpoint nodes, which is the node set of a quadratic
+    six-node triangle (corners at (xi, eta) = (0,0), (1,0), (0,1); midpoints
+    at (1/2,0), (1/2,1/2), (0,1/2)).  Level 0 has no midpoint nodes and
+    returns an empty E6."""
     if level not in _ICO:
         _ICO[level] = _icosphere(level)
-    V, F = _ICO[level]
-    return V.copy(), F.copy()
+    V, F, E6 = _ICO[level]
+    return V.copy(), F.copy(), E6.copy()
 
 
 _ICO = {}
@@ -123,6 +139,7 @@ def _icosphere(level: int):
     F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
          (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
          (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    E6 = []
     for _ in range(level):
         cache = {}
 
@@ -135,9 +152,11 @@ def _icosphere(level: int):
             return cache[key]
 
         nf = []
+        E6 = []
         for a, b, c in F:
             ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
             nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+            E6.append((a, b, c, ab, bc, ca))
         F = nf
     X = np.array(V)
     T = np.array(F, dtype=np.int32)
@@ -145,7 +164,13 @@ def _icosphere(level: int):
     n = np.cross(X[T[:, 1]] - X[T[:, 0]], X[T[:, 2]] - X[T[:, 0]])
     flip = np.einsum("ij,ij->i", n, X[T[:, 0]]) < 0
     T[flip] = T[flip][:, [0, 2, 1]]
-    return X, T
+    E = np.array(E6, dtype=np.int32).reshape(-1, 6)
+    if len(E):
+        n = np.cross(X[E[:, 1]] - X[E[:, 0]], X[E[:, 2]] - X[E[:, 0]])
+        flip = np.einsum("ij,ij->i", n, X[E[:, 0]] + X[E[:, 1]] + X[E[:, 2]]) < 0
+        # (a, c, b) with midpoints (m_ac, m_cb, m_ba)
+        E[flip] = E[flip][:, [0, 2, 1, 5, 4, 3]]
+    return X, T, E
 
 
 def random_rotation(rng):
@@ -208,14 +233,14 @@ def receptor_sites(X, T, n_sites, rng):
 def platelet_template(level, n_sce, n_sites, a_lat, aspect, rng):
     """One platelet in its body frame: membrane nodes, SCE points, triangles,
     Morse pairs and receptor sites."""
-    U, T = icosphere(level)
+    U, T, E6 = icosphere_elements(level)
     Xm = U * np.array([a_lat, a_lat, a_lat * aspect])
     Xs = sce_points(n_sce, a_lat, a_lat * aspect, rng)
     edges = np.concatenate([T[:, [0, 1]], T[:, [1, 2]], T[:, [2, 0]]])
     mean_edge = np.linalg.norm(Xm[edges[:, 0]] - Xm[edges[:, 1]], axis=1).mean()
     pairs = morse_pairs(Xm, Xs, 2.0 * mean_edge)
     st, sw = receptor_sites(Xm, T, n_sites, rng)
-    return dict(Xm=Xm, Xs=Xs, T=T, pairs=pairs, site_tri=st, site_w=sw, mean_edge=mean_edge)
+    return dict(Xm=Xm, Xs=Xs, T=T, E6=E6, pairs=pairs, site_tri=st, site_w=sw, mean_edge=mean_edge)
 
 
 # ---------------------------------------------------------------------------
@@ -241,7 +266,7 @@ def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
     if z_max is None:
         z_max = 3.0e-6 / P["h"]
     z_wall = -0.5
-    Xs_all, tris, pairs, node_plt, is_mem, site_tri, site_w = [], [], [], [], [], [], []
+    Xs_all, tris, pairs, node_plt, is_mem, site_tri, site_w, elems = [], [], [], [], [], [], [], []
     placed = []
     off = 0
     toff = 0
@@ -277,6 +302,7 @@ def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
         Xs_all.append(Y + c)
         nm = len(tp["Xm"])
         tris.append(tp["T"] + off)
+        elems.append(tp["E6"] + off)
         pairs.append(tp["pairs"] + off)
         node_plt.append(np.full(len(body), p, dtype=np.int32))
         is_mem.append(np.r_[np.ones(nm, np.uint8), np.zeros(len(tp["Xs"]), np.uint8)])
@@ -301,6 +327,7 @@ def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
                   body=(0.0, 0.0, 0.0)),
         dt=L["dt"], shear=shear,
         mesh=dict(X0=Xsoa.copy(), tri=np.concatenate(tris).astype(np.int32),
+                  elem6=np.concatenate(elems).astype(np.int32).reshape(-1, 6),
                   pairs=np.concatenate(pairs).astype(np.int32).reshape(-1, 2),
                   node_plt=np.concatenate(node_plt), is_membrane=np.concatenate(is_mem),
                   n_plt=n_plt),

@@ -133,6 +133,28 @@ def test_bond_workspace_query_and_validation(L):
         fsi.bonds_query_workspace(p, 100)
 
 
+def test_fem_workspace_and_validation(L):
+    """Six-node element lists are checked on the host before any copy."""
+    w = workload.config_small()
+    e6 = np.ascontiguousarray(w["mesh"]["elem6"], dtype=np.int32)
+    assert e6.shape == (320, 6)
+    nb = ctypes.c_size_t()
+    assert L.fem_query_workspace(w["M"], len(e6), ctypes.byref(nb)) == 0
+    assert nb.value % 256 == 0 and nb.value >= len(e6) * 6 * (16 + 8)
+    assert L.fem_query_workspace(0, len(e6), ctypes.byref(nb)) == -1
+    fake = ctypes.c_void_p(1 << 20)     # never dereferenced: validation fails first
+    h = ctypes.c_void_p()
+    for bad, msg in ((w["M"] + 1, "out of range"), (e6[0, 1], "repeated")):
+        b = e6.copy()
+        b[0, 0] = bad
+        assert L.fem_create(w["M"], len(b), b.ctypes.data_as(ctypes.c_void_p), fake, ctypes.c_size_t(nb.value),
+                            ctypes.byref(h)) == -1
+        assert msg in fsi.last_error()
+    assert L.fem_create(w["M"], len(e6), e6.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p((1 << 20) + 8),
+                        ctypes.c_size_t(nb.value), ctypes.byref(h)) == -1
+    assert "aligned" in fsi.last_error()
+
+
 def test_product_path_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(fsi, "_lib", None)
     monkeypatch.setattr(fsi, "LIB_PATH", "/nonexistent/libplatelet_fsi.so")
