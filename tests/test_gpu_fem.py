@@ -7,10 +7,13 @@ Tolerances.  The kernels work in FP32 on coordinates relative to each
 element's first corner, so each first derivative (tangents, normal
 derivatives) carries a relative rounding error of a few u = 2^-24 of the
 element's size, and each further derivative divides the error of the
-previous field by the element size s again.  Normals and areas stay within
-~1e-6; K and K_G within ~1e-5 of their largest value; Lap_S K and the force
-(three derivative levels of the positions) within 1e-3 of their largest value,
-for the platelet meshes here (s ~ 0.5, K up to ~3 lattice units^-1)."""
+previous field by the element size again: a few u for normals and areas,
+~10 u for K and K_G, ~100 u for Lap_S K and the force (three derivative
+levels of the positions), each relative to the field's largest value.
+Measured on the deformed channel meshes: 3e-7 (normals), 2e-7 (areas),
+9e-7 (K), 1.8e-6 (K_G), 5.3e-6 (Lap_S K), 5.1e-6 (force); the bounds below
+are about ten times the u-counts (1e-6, 2e-5, 5e-5).  The coupled step keeps
+the 1e-5 bound of the other coupled parity tests (measured 3e-7 .. 6e-7)."""
 import numpy as np
 import pytest
 import torch
@@ -67,9 +70,9 @@ def test_fields_and_forces_match_the_oracle():
     Fr = fem.bending_forces(X, E, k0)
     errs["F"] = rel(F.reshape(3, -1).T.cpu().numpy(), Fr)
     print("fem rel errors", errs)
-    assert errs["n"] < 2e-6 and errs["A"] < 2e-6
+    assert errs["n"] < 1e-6 and errs["A"] < 1e-6
     assert errs["K"] < 2e-5 and errs["KG"] < 2e-5
-    assert errs["lapK"] < 1e-3 and errs["F"] < 1e-3
+    assert errs["lapK"] < 5e-5 and errs["F"] < 5e-5
     # SCE nodes (no element) get nothing
     assert float(F.reshape(3, -1)[:, torch.as_tensor(~mem).cuda()].abs().max()) == 0.0
 
@@ -88,7 +91,7 @@ def test_far_from_the_origin_and_accumulate():
     fb.forces(k0, Xd, F0)
     fb.forces(k0, Xf, F1)
     scale = float(F0.abs().max())
-    assert float((F1 - F0).abs().max()) < 1e-3 * scale
+    assert float((F1 - F0).abs().max()) < 5e-5 * scale
     base = torch.randn_like(F0)
     F2 = base.clone()
     fb.forces(k0, Xd, F2, accumulate=True)
@@ -114,7 +117,7 @@ def test_coupled_step_with_fem_bending(level):
     """The coupled step with the finite-element bending in place of the
     dihedral term (modulus raised 100x so that it shapes the motion) against
     the oracle's coupled step: displacements and node velocities within
-    1e-4 of their largest entries after 10 steps."""
+    1e-5 of their largest entries after 10 steps."""
     w = workload.tiny(seed=2, level=level, n_sce=20, n_sites=60, shear=3.0e4)
     w["membrane"] = dict(w["membrane"], bending="fem", k0=100.0 * w["membrane"]["k0"])
     w = f32_workload(w)
@@ -129,6 +132,6 @@ def test_coupled_step_with_fem_bending(level):
     ex = rel(sim.X.cpu().numpy() - X0, ora.X - X0)
     eu = rel(sim.U.cpu().numpy(), ora.U)
     print("coupled fem level", level, ex, eu)
-    assert ex < 1e-4 and eu < 1e-4
+    assert ex < 1e-5 and eu < 1e-5
     if sim.bonds is not None:
         assert np.array_equal(sim.bonds.bound.cpu().numpy(), ora.bound)
