@@ -234,6 +234,7 @@ def run_native(args, rank, ws):
                                       for s in ("bf16", "fp16")}
     extras = {}
     if not args.no_extras:
+        extras["fem_bending"] = run_fem(args, w, ms_per_step, dev, flush, stream)
         extras["batched"] = run_batched(args, dev, stream)
         extras["surrogate"], sg_params = run_surrogate(args, w, sim, dev, stream)
         extras["full_scale"] = run_full(args, dev, stream, sg_params)
@@ -503,6 +504,49 @@ def run_surrogate(args, w_channel, sim_channel, dev, stream):
         del sim
     out["vs_plain"] = out["surrogate"]["value"] / out["plain"]["value"]
     return out, params
+
+
+def run_fem(args, w, ms_dihedral, dev, flush, stream):
+    """The channel's coupled step with the finite-element bending of Eq. 6-10
+    in place of the dihedral term (timed like the headline: L2 flushed before
+    every step), and the bending term alone on the channel's and on the full
+    scale's meshes (10 and 500 platelets of 1280 six-node elements)."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    wf = dict(w, membrane=dict(w["membrane"], bending="fem"))
+    sim = fsi.Simulation(wf, device=dev)
+    N = w["grid"]["nx"] * w["grid"]["ny"] * w["grid"]["nz"]
+    steps = max(3, args.steps)
+    sim.step(3)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(1)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    step_ms = float(np.mean(ms))
+    out = {"workload": "channel 128x64x64, 10 platelets: coupled step with finite-element bending",
+           "coupled": {"value": N / step_ms / 1e3, "unit": "MLUPS", "ms_per_step": step_ms,
+                       "vs_dihedral": ms_dihedral / step_ms}}
+    del sim
+    for name, wk in (("channel_mesh", w), ("full_scale_mesh", workload.config_full(seed=0))):
+        fb = fsi.FemBending(wk["mesh"], device=dev)
+        X = torch.as_tensor(np.ascontiguousarray(wk["X"], dtype=np.float64), device=dev)
+        F = torch.zeros(3 * wk["M"], dtype=torch.float32, device=dev)
+        for _ in range(3):
+            fb.forces(1e-3, X, F)
+        reps = 20
+        t = timed_steps(lambda: fb.forces(1e-3, X, F), reps, stream)
+        ne = int(np.asarray(wk["mesh"]["elem6"]).size // 6)
+        out[name] = {"elements": ne, "us_per_evaluation": 1e6 * t / reps, "launches": 8,
+                     "elements_per_s": ne * reps / t}
+        del fb, X, F
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_full(args, dev, stream, sg_params):
