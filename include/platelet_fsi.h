@@ -303,6 +303,66 @@ int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* strea
 int bonds_status(bond_ctx* ctx, long long* out_host);
 
 /* ===================================================================== *
+ * Platelet-platelet bridges GPIb-alpha - vWF - GPIb-alpha (Section 3.2)
+ *
+ * The paper models these bonds like the wall bonds and prints no equations
+ * for them.  Reading: a plasma vWF joins two receptor sites on different
+ * platelets; the bridge is one linear spring between the two sites (the
+ * form of Eq. 14) with its own spring constant, rest length and capture
+ * distance, and the rates of Eq. 12 (rupture) and Eq. 13 (formation).  A
+ * site holds at most one bond of either kind.  Per step, after the wall
+ * update (bonds_step):
+ *   rupture    every bridge i < j breaks with P_r = 1 - exp(-k_off dt),
+ *              k_off = k_off0 exp(gamma F_b / kT), F_b = sigma |x_b - l_b|;
+ *              its sites stay free until the next step;
+ *   formation  every pair i < j of free sites (no wall bond, no bridge) on
+ *              different platelets with |x_i - x_j| < d_capture succeeds
+ *              with P_f = 1 - exp(-k_on dt), k_on of Eq. 13; each site picks
+ *              its lowest-index successful partner; a bridge forms where two
+ *              sites picked each other.
+ * Draws: Philox4x32-10 with counter (i, j, step lo, purpose) and key
+ * (seed lo, seed hi ^ step hi), i < j; purpose 16 rupture, 17 formation.
+ * Pair vector x_i - x_j (i < j), minimum image in x, y, FP64.  The outcome
+ * does not depend on thread scheduling.
+ * ===================================================================== */
+typedef struct {
+    double sigma, l_b, d_capture;       /* bridge spring, rest length, capture distance */
+    double gamma, kT;                   /* Eq. 12-13 */
+    double kon0_dt, koff0_dt;           /* k_on0 dt, k_off0 dt */
+    int box_nx, box_ny;                 /* periodic lengths */
+    uint64_t seed;                      /* Philox4x32-10 key */
+} bridge_params;
+
+typedef struct bridge_ctx bridge_ctx;
+
+/* Workspace bytes for n_sites receptor sites, n_plt platelets and M nodes. */
+int bridges_query_workspace(const bridge_params* p, int n_sites, int n_plt, int M, size_t* bytes);
+/* Bridges between the receptor sites of `bonds` (its site_tri, site_w, tri
+ * and bound arrays).  node_plt: host int[M], the platelet of each node; the
+ * nodes of each platelet must be contiguous (PFSI_ERR_ARG otherwise).
+ * partner: caller-owned device int[n_sites], the other site of each bridge
+ * or -1 (symmetric; -1 everywhere to start).  The wall bonds of `bonds`
+ * skip bridged sites from now on; destroy the bridges before the bonds.
+ * ws: bridges_query_workspace bytes, 256-byte aligned.  Synchronises. */
+int bridges_create(const bridge_params* p, bond_ctx* bonds, int n_plt, const int* node_plt, int M, int* partner,
+                   void* workspace, size_t ws_bytes, bridge_ctx** out);
+int bridges_destroy(bridge_ctx* ctx);
+/* F += bridge spring forces: on site i, -sigma (|d| - l_b) d/|d| with
+ * d = x_i - x_partner, the opposite on the partner, split over each site's
+ * triangle nodes by the barycentric weights.  X: device double[3][M];
+ * F: device float[3][M]. */
+int bridges_forces(bridge_ctx* ctx, const double* X, float* F, int M, void* stream);
+/* One Monte-Carlo update of the bridges at time step `step` (after the wall
+ * update of the same step).  Enqueues 6 kernels and a memset. */
+int bridges_step(bridge_ctx* ctx, const double* X, int M, uint64_t step, void* stream);
+/* Cumulative counts, out_host[3] = {ruptures, formations, neighbour-list
+ * overflows (a platelet near more than 16 others: all its free sites were
+ * tested, so only the pruning was lost)}.  Synchronises. */
+int bridges_status(bridge_ctx* ctx, long long* out_host);
+/* The partner array given at create. */
+int bridges_partner(bridge_ctx* ctx, int** partner_dev);
+
+/* ===================================================================== *
  * Finite-element bending, Section 3.1 (Eq. 6-10)
  *
  * The membrane is covered by quadratic six-node triangles (Eq. 7):
@@ -497,6 +557,13 @@ int sim_set_surrogate(sim_ctx* ctx, sg_ctx* sg, const void* params);
  * it.  The mesh must have the simulation's node count.  The graphs are
  * recaptured. */
 int sim_set_fem_bending(sim_ctx* ctx, fem_ctx* fem, float k0);
+
+/* Adds the platelet-platelet bridges to every following step: their spring
+ * forces after the wall bond forces, their update after the wall update.
+ * The bridges must be built on the simulation's bond context; their step
+ * counter continues from the simulation's.  br = NULL removes them.  The
+ * graphs are recaptured.  Synchronises. */
+int sim_set_bridges(sim_ctx* ctx, bridge_ctx* br);
 
 /* Measurement aid (no paper counterpart): on != 0 records two CUDA events
  * around the lattice Boltzmann kernel inside the step graph (the graphs are

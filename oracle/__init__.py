@@ -73,6 +73,13 @@ class BondParams(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class BridgeParams(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("l_b", ctypes.c_double), ("d_capture", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("kT", ctypes.c_double),
+                ("kon0_dt", ctypes.c_double), ("koff0_dt", ctypes.c_double),
+                ("box_nx", ctypes.c_int), ("box_ny", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -98,7 +105,14 @@ def lib():
         L.ora_bond_forces.argtypes = [ctypes.POINTER(BondParams), ctypes.c_int, IP, DP, IP,
                                       ctypes.c_int, IP, DP, DP]
         L.ora_bonds_step.argtypes = [ctypes.POINTER(BondParams), ctypes.c_int, IP, DP, IP,
-                                     ctypes.c_int, DP, IP, IP, ctypes.c_uint64, IP]
+                                     ctypes.c_int, DP, IP, IP, ctypes.c_uint64, IP, IP]
+        L.ora_pair_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_uint32]
+        L.ora_pair_uniform.restype = ctypes.c_double
+        L.ora_bridge_forces.argtypes = [ctypes.POINTER(BridgeParams), ctypes.c_int, IP, DP, IP, ctypes.c_int, IP,
+                                        DP, DP]
+        L.ora_bridges_step.argtypes = [ctypes.POINTER(BridgeParams), ctypes.c_int, IP, DP, IP, IP, ctypes.c_int,
+                                       DP, IP, IP, ctypes.c_uint64, IP]
         _lib = L
     return _lib
 
@@ -240,14 +254,51 @@ def bond_forces(params, site_tri, site_w, tri, bound, X, F):
     return F
 
 
-def bonds_step(params, site_tri, site_w, tri, X, bound, lig_count, step):
-    """Updates bound / lig_count in place; returns (n_ruptures, n_formations)."""
+def bonds_step(params, site_tri, site_w, tri, X, bound, lig_count, step, partner=None):
+    """Updates bound / lig_count in place; returns (n_ruptures, n_formations).
+    partner: bridge partners (sites with one hold no wall bond), or None."""
     bp = bond_params(params)
     M = X.size // 3
     ev = np.zeros(2, dtype=np.int32)
     lib().ora_bonds_step(ctypes.byref(bp), site_tri.size, _i(site_tri), _d(site_w),
                          _i(np.ascontiguousarray(tri, dtype=np.int32).ravel()), M, _d(X),
-                         _i(bound), _i(lig_count), int(step), _i(ev))
+                         _i(bound), _i(lig_count), int(step), _i(partner) if partner is not None else None, _i(ev))
+    return int(ev[0]), int(ev[1])
+
+
+# ---------------------------------------------------------------- bridges
+def bridge_params(d):
+    return BridgeParams(float(d["sigma"]), float(d["l_b"]), float(d["d_capture"]), float(d["gamma"]),
+                        float(d["kT"]), float(d["kon0_dt"]), float(d["koff0_dt"]), int(d["box_nx"]),
+                        int(d["box_ny"]), int(d["seed"]))
+
+
+def pair_uniform(seed, i, j, step, purpose):
+    return lib().ora_pair_uniform(seed, i, j, step, purpose)
+
+
+def site_platelets(site_tri, tri, node_plt):
+    """Platelet of each receptor site (that of its triangle's first node)."""
+    t = np.asarray(tri, dtype=np.int32).reshape(-1, 3)
+    return np.ascontiguousarray(np.asarray(node_plt, dtype=np.int32)[t[np.asarray(site_tri), 0]])
+
+
+def bridge_forces(params, site_tri, site_w, tri, partner, X, F):
+    bp = bridge_params(params)
+    M = X.size // 3
+    lib().ora_bridge_forces(ctypes.byref(bp), site_tri.size, _i(site_tri), _d(site_w),
+                            _i(np.ascontiguousarray(tri, dtype=np.int32).ravel()), M, _i(partner), _d(X), _d(F))
+    return F
+
+
+def bridges_step(params, site_tri, site_w, tri, site_plt, X, bound, partner, step):
+    """Updates partner in place; returns (n_ruptures, n_formations)."""
+    bp = bridge_params(params)
+    M = X.size // 3
+    ev = np.zeros(2, dtype=np.int32)
+    lib().ora_bridges_step(ctypes.byref(bp), site_tri.size, _i(site_tri), _d(site_w),
+                           _i(np.ascontiguousarray(tri, dtype=np.int32).ravel()), _i(site_plt), M, _d(X),
+                           _i(bound), _i(partner), int(step), _i(ev))
     return int(ev[0]), int(ev[1])
 
 
@@ -279,6 +330,13 @@ class Sim:
         self.site_w = np.ascontiguousarray(w["sites"]["w"], dtype=np.float64).ravel()
         self.X = np.ascontiguousarray(w["X"], dtype=np.float64).ravel().copy()
         self.bound = np.ascontiguousarray(w["bound"], dtype=np.int32).copy()
+        # platelet-platelet bridges (optional)
+        self.bridgep = w.get("bridges")
+        self.partner = None
+        if self.bridgep is not None:
+            self.site_plt = site_platelets(self.site_tri, m["tri"], m["node_plt"])
+            self.partner = np.ascontiguousarray(w.get("partner", np.full(len(self.site_tri), -1)), dtype=np.int32).copy()
+        self.bridge_events = (0, 0)
         self.lig_count = np.ascontiguousarray(w["lig_count"], dtype=np.int32).copy()
         self.f = lb_init_shear(self.p)
         self.step_index = int(w.get("step0", 0))
@@ -297,6 +355,8 @@ class Sim:
             from . import fem
             self.F += fem.forces_soa(self.X, self.elem6, self.k0)
         bond_forces(self.bondp, self.site_tri, self.site_w, self.tri, self.bound, self.X, self.F)
+        if self.partner is not None:
+            bridge_forces(self.bridgep, self.site_tri, self.site_w, self.tri, self.partner, self.X, self.F)
         # 2. spread
         self.g = ib_spread(self.p, self.X, self.F)
         # 3. fluid
@@ -306,5 +366,8 @@ class Sim:
         self.X += self.U
         # 5. adhesion
         self.events = bonds_step(self.bondp, self.site_tri, self.site_w, self.tri, self.X,
-                                 self.bound, self.lig_count, self.step_index)
+                                 self.bound, self.lig_count, self.step_index, self.partner)
+        if self.partner is not None:
+            self.bridge_events = bridges_step(self.bridgep, self.site_tri, self.site_w, self.tri, self.site_plt,
+                                              self.X, self.bound, self.partner, self.step_index)
         self.step_index += 1

@@ -790,14 +790,17 @@ static int cmp_proposal(const void* a, const void* b)
  * k_on of Eq. 13; it proposes to the lowest ligand id that succeeded.  Each
  * ligand accepts proposals in ascending site id while it has fewer than
  * max_per_ligand bonds (at most 4 receptor sites per vWF).  Draws come from
- * Philox keyed by (site, step, purpose): purpose 0 rupture, 1 + slot. */
+ * Philox keyed by (site, step, purpose): purpose 0 rupture, 1 + slot.
+ * partner (may be NULL): bridge partner of each site; bridged sites are
+ * not free. */
 void ora_bonds_step(const ora_bond_params* p, int n_sites, const int* site_tri,
                     const double* site_w, const int* tri, int M, const double* X,
-                    int* bound, int* lig_count, uint64_t step, int* n_events)
+                    int* bound, int* lig_count, uint64_t step, const int* partner, int* n_events)
 {
     int n_rupt = 0, n_form = 0;
     unsigned char* was_free = (unsigned char*)malloc(n_sites > 0 ? n_sites : 1);
-    for (int s = 0; s < n_sites; ++s) was_free[s] = (bound[s] < 0);
+    /* a site bridged to another platelet holds no wall bond (one bond per site) */
+    for (int s = 0; s < n_sites; ++s) was_free[s] = (bound[s] < 0) && (!partner || partner[s] < 0);
 
     /* rupture */
     for (int s = 0; s < n_sites; ++s) {
@@ -862,6 +865,133 @@ void ora_bonds_step(const ora_bond_params* p, int n_sites, const int* site_tri,
     }
     free(props);
     free(was_free);
+    n_events[0] = n_rupt;
+    n_events[1] = n_form;
+}
+
+/* ======================================================================
+ * Platelet-platelet bridges GPIb-alpha - vWF - GPIb-alpha (Section 3.2: the
+ * paper models them "similarly" to the wall bonds and gives no equations).
+ * Reading: a plasma vWF joins two receptor sites on different platelets;
+ * the bridge is one linear spring between the two sites (Eq. 14 form) with
+ * its own rest length, capture distance and spring constant, and the rates
+ * of Eq. 12 (rupture) and Eq. 13 (formation) with those.  A site holds at
+ * most one bond of either kind (steric rule 1); a bridge vWF holds exactly
+ * two sites (rule 2 then holds).  Per step, after the wall update:
+ *   rupture    every bridge (i < j) breaks with P_r = 1 - exp(-k_off dt),
+ *              k_off of Eq. 12 with F_b = sigma |x_b - l_b|; its sites stay
+ *              free until the next step;
+ *   formation  every pair (i < j) of free sites on different platelets
+ *              closer than d_capture succeeds with P_f = 1 - exp(-k_on dt),
+ *              k_on of Eq. 13; every site picks its lowest-index successful
+ *              partner, and a bridge forms where two sites picked each other.
+ * Draws: Philox with counter (i, j, step low word, purpose) and key
+ * (seed low word, seed high word ^ step high word) for i < j; purpose 16
+ * rupture, 17 formation.  The pair vector is x_i - x_j for i < j (minimum
+ * image in x, y), evaluated in that order for either site.
+ * ==================================================================== */
+double ora_pair_uniform(uint64_t seed, uint32_t i, uint32_t j, uint64_t step, uint32_t purpose)
+{
+    uint32_t ctr[4] = {i, j, (uint32_t)step, purpose};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ (uint32_t)(step >> 32)};
+    uint32_t r[4];
+    ora_philox4x32_10(ctr, key, r);
+    uint64_t bits = ((uint64_t)r[0] << 21) | (uint64_t)(r[1] >> 11);
+    return (double)bits * (1.0 / 9007199254740992.0); /* 2^-53 */
+}
+
+/* x_i - x_j, i < j, minimum image in x and y */
+static void pair_vector(const ora_bridge_params* p, const double* ri, const double* rj, double* d)
+{
+    d[0] = min_image(ri[0] - rj[0], p->box_nx);
+    d[1] = min_image(ri[1] - rj[1], p->box_ny);
+    d[2] = ri[2] - rj[2];
+}
+
+void ora_bridge_forces(const ora_bridge_params* p, int n_sites, const int* site_tri,
+                       const double* site_w, const int* tri, int M, const int* partner,
+                       const double* X, double* F)
+{
+    for (int i = 0; i < n_sites; ++i) {
+        int j = partner[i];
+        if (j <= i) continue;
+        double ri[3], rj[3], d[3];
+        site_position(NULL, site_tri, site_w, tri, M, X, i, ri);
+        site_position(NULL, site_tri, site_w, tri, M, X, j, rj);
+        pair_vector(p, ri, rj, d);
+        double xb = norm3(d);
+        double c = -p->sigma * (xb - p->l_b) / xb;   /* force on site i is c d, on site j -c d */
+        for (int end = 0; end < 2; ++end) {
+            int s = end ? j : i;
+            double sign = end ? -1.0 : 1.0;
+            const int* t = &tri[3 * site_tri[s]];
+            double w[3] = {site_w[2 * s], site_w[2 * s + 1], 1.0 - site_w[2 * s] - site_w[2 * s + 1]};
+            for (int a = 0; a < 3; ++a)
+                for (int k = 0; k < 3; ++k) F[k * M + t[a]] += sign * w[a] * c * d[k];
+        }
+    }
+}
+
+void ora_bridges_step(const ora_bridge_params* p, int n_sites, const int* site_tri,
+                      const double* site_w, const int* tri, const int* site_plt, int M,
+                      const double* X, const int* bound, int* partner, uint64_t step, int* n_events)
+{
+    int n_rupt = 0, n_form = 0;
+    int n = n_sites > 0 ? n_sites : 1;
+    double* r = (double*)malloc(sizeof(double) * 3 * n);
+    unsigned char* is_free = (unsigned char*)malloc(n);
+    int* choice = (int*)malloc(sizeof(int) * n);
+    for (int s = 0; s < n_sites; ++s) site_position(NULL, site_tri, site_w, tri, M, X, s, &r[3 * s]);
+
+    /* rupture */
+    for (int s = 0; s < n_sites; ++s) is_free[s] = 1;
+    for (int i = 0; i < n_sites; ++i) {
+        int j = partner[i];
+        if (j < 0) continue;
+        is_free[i] = 0;
+        if (j < i) continue;
+        double d[3];
+        pair_vector(p, &r[3 * i], &r[3 * j], d);
+        double Fb = p->sigma * fabs(norm3(d) - p->l_b);
+        double koff_dt = p->koff0_dt * exp(p->gamma * Fb / p->kT);
+        double Pr = -expm1(-koff_dt);
+        if (ora_pair_uniform(p->seed, (uint32_t)i, (uint32_t)j, step, 16u) < Pr) {
+            partner[i] = -1;
+            partner[j] = -1;
+            ++n_rupt;
+        }
+    }
+    for (int s = 0; s < n_sites; ++s)
+        if (bound[s] >= 0) is_free[s] = 0;
+
+    /* formation: every site's lowest-index successful partner */
+    for (int i = 0; i < n_sites; ++i) {
+        choice[i] = -1;
+        if (!is_free[i]) continue;
+        for (int j = 0; j < n_sites; ++j) {
+            if (j == i || !is_free[j] || site_plt[j] == site_plt[i]) continue;
+            int a = i < j ? i : j, b = i < j ? j : i;
+            double d[3];
+            pair_vector(p, &r[3 * a], &r[3 * b], d);
+            double xb = norm3(d);
+            if (!(xb < p->d_capture)) continue;
+            double dev = fabs(xb - p->l_b);
+            double kon_dt = p->kon0_dt * exp(p->sigma * dev * (p->gamma - 0.5 * dev) / p->kT);
+            double Pf = -expm1(-kon_dt);
+            if (ora_pair_uniform(p->seed, (uint32_t)a, (uint32_t)b, step, 17u) < Pf && choice[i] < 0) choice[i] = j;
+        }
+    }
+    for (int i = 0; i < n_sites; ++i) {
+        int j = choice[i];
+        if (j > i && choice[j] == i) {
+            partner[i] = j;
+            partner[j] = i;
+            ++n_form;
+        }
+    }
+    free(r);
+    free(is_free);
+    free(choice);
     n_events[0] = n_rupt;
     n_events[1] = n_form;
 }

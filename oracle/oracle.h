@@ -96,7 +96,24 @@ void ora_bond_forces(const ora_bond_params* p, int n_sites, const int* site_tri,
                      const double* X, double* F);
 void ora_bonds_step(const ora_bond_params* p, int n_sites, const int* site_tri,
                     const double* site_w, const int* tri, int M, const double* X,
-                    int* bound, int* lig_count, uint64_t step, int* n_events);
+                    int* bound, int* lig_count, uint64_t step, const int* partner, int* n_events);
+
+/* ---------------- Platelet-platelet bridges (Section 3.2, "similarly") ---- */
+typedef struct {
+    double sigma, l_b, d_capture;          /* spring, rest length, capture distance */
+    double gamma, kT;                      /* Eq. 12-13 */
+    double kon0_dt, koff0_dt;
+    int box_nx, box_ny;                    /* periodic lengths */
+    uint64_t seed;
+} ora_bridge_params;
+
+double ora_pair_uniform(uint64_t seed, uint32_t i, uint32_t j, uint64_t step, uint32_t purpose);
+void ora_bridge_forces(const ora_bridge_params* p, int n_sites, const int* site_tri,
+                       const double* site_w, const int* tri, int M, const int* partner,
+                       const double* X, double* F);
+void ora_bridges_step(const ora_bridge_params* p, int n_sites, const int* site_tri,
+                      const double* site_w, const int* tri, const int* site_plt, int M,
+                      const double* X, const int* bound, int* partner, uint64_t step, int* n_events);
 
 #ifdef __cplusplus
 }

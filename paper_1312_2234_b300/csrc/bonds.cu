@@ -16,42 +16,15 @@
 // (receptor position, bond length, rates) is FP64 with explicitly rounded
 // operations in the order of the plain restatement, so that an event differs
 // only when a uniform lands within an ulp of its probability.
-#include "pfsi_internal.cuh"
+#include "adhesion.cuh"
 
 namespace pfsi {
 
 namespace {
 
-__device__ __forceinline__ double site_coord(const double* __restrict__ X, int M, int d, int a, int b,
-                                            int c, double w0, double w1)
-{
-    const double w2 = __dsub_rn(__dsub_rn(1.0, w0), w1);
-    return __dadd_rn(__dadd_rn(__dmul_rn(w0, X[d * M + a]), __dmul_rn(w1, X[d * M + b])),
-                     __dmul_rn(w2, X[d * M + c]));
-}
-
-__device__ __forceinline__ double min_image(double d, int L)
-{
-    const double Ld = (double)L;
-    return __dsub_rn(d, __dmul_rn(Ld, floor(__dadd_rn(__ddiv_rn(d, Ld), 0.5))));
-}
-
-__device__ __forceinline__ double norm3_rn(double a, double b, double c)
-{
-    return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c)));
-}
-
-struct SitePos {
-    double x, y, z;
-};
-
 __device__ __forceinline__ SitePos site_position(const BondCtx& c, const double* __restrict__ X, int M, int s)
 {
-    const int t = c.site_tri[s];
-    const int a = c.tri[3 * t], b = c.tri[3 * t + 1], cc = c.tri[3 * t + 2];
-    const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
-    return {site_coord(X, M, 0, a, b, cc, w0, w1), site_coord(X, M, 1, a, b, cc, w0, w1),
-            site_coord(X, M, 2, a, b, cc, w0, w1)};
+    return site_pos(c.site_tri, c.site_w, c.tri, X, M, s);
 }
 
 // vector from ligand `lig` to the receptor (minimum image in x, y)
@@ -61,11 +34,6 @@ __device__ __forceinline__ void bond_vector(const bond_params& p, const SitePos&
     d[0] = min_image(__dsub_rn(r.x, (double)(p.lig_i0 + li)), p.box_nx);
     d[1] = min_image(__dsub_rn(r.y, (double)(p.lig_j0 + lj)), p.box_ny);
     d[2] = __dsub_rn(r.z, p.z_wall);
-}
-
-__device__ __forceinline__ uint64_t current_step(const unsigned long long* step_dev, uint64_t step_host)
-{
-    return step_dev ? (uint64_t)*step_dev : step_host;
 }
 
 __global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __restrict__ F, int M)
@@ -79,15 +47,8 @@ __global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __
     bond_vector(c.p, r, lig, d);
     const double xb = norm3_rn(d[0], d[1], d[2]);
     const double coef = -c.p.sigma * (xb - c.p.l_b) / xb;
-    const int t = c.site_tri[s];
-    const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
-    const float w[3] = {(float)w0, (float)w1, (float)(1.0 - w0 - w1)};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int node = c.tri[3 * t + k];
-#pragma unroll
-        for (int dd = 0; dd < 3; ++dd) atomicAdd(&F[dd * M + node], w[k] * (float)(coef * d[dd]));
-    }
+    const double f[3] = {coef * d[0], coef * d[1], coef * d[2]};
+    site_add_force(c.site_tri, c.site_w, c.tri, F, M, s, f);
 }
 
 __global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
@@ -122,6 +83,7 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
         return;
     }
     if (b >= 0) return;
+    if (c.partner && c.partner[s] >= 0) return;   // bridged to another platelet: one bond per site
     const bond_params& p = c.p;
     // Out of reach of every ligand: the bond length is at least the height
     // above the wall plane (the margin covers the last-ulp rounding of the
@@ -279,6 +241,7 @@ extern "C" int bonds_create(const bond_params* p, int n_sites, const int* site_t
     c->tri = tri;
     c->bound = bound;
     c->lig_count = lig_count;
+    c->partner = nullptr;
     char* base = static_cast<char*>(ws);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     c->nprop = reinterpret_cast<int*>(base);

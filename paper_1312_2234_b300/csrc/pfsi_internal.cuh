@@ -143,6 +143,7 @@ struct BondCtx {
     int* nprop;            // [L] proposals this step
     int* cand;             // [L * kMaxCand]
     unsigned long long* counters;  // [4]: ruptures, formations, overflow, step (sim)
+    const int* partner;    // bridge partner of each site (bridges.cu) or null
 };
 constexpr int kMaxCand = 64;
 
@@ -179,6 +180,14 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
                             cudaStream_t s);
 SgCtx* sg_internal(sg_ctx* c);
 int sg_node_count(const SgCtx* c);
+
+struct BridgeCtx;
+int launch_bridge_forces(BridgeCtx* c, const double* X, float* F, int M, cudaStream_t s);
+int launch_bridges_step(BridgeCtx* c, const double* X, int M, uint64_t step_host, unsigned long long* step_dev,
+                        cudaStream_t s);
+BridgeCtx* bridge_internal(bridge_ctx* c);
+unsigned long long* bridge_step_counter(BridgeCtx* c);
+BondCtx* bridge_bonds(BridgeCtx* c);
 
 struct FemCtx;
 // Finite-element bending force (Eq. 6-10): F (+)= the nodal force; fields

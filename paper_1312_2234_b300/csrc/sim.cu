@@ -29,6 +29,7 @@ struct SimCtx {
     const void* sg_params;
     FemCtx* fem;           // finite-element bending, or null
     float fem_k0;
+    BridgeCtx* br;         // platelet-platelet bridges, or null
     // sim_step_record / sim_step_track: copy stream and per-slot events
     // (created on first use)
     cudaStream_t rec;
@@ -52,6 +53,7 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     }
     if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->F, 1, nullptr, s);
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
+    if (!rc && c->br) rc = launch_bridge_forces(c->br, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->lb_ev[0])
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[0], s, cudaEventRecordExternal), "sim: lb timing event");
@@ -60,6 +62,7 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
     if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
+    if (!rc && c->br) rc = launch_bridges_step(c->br, c->X, c->M, 0, bridge_step_counter(c->br), s);
     return rc;
 }
 
@@ -134,6 +137,7 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->trk_scratch = nullptr;
     c->fem = nullptr;
     c->fem_k0 = 0.0f;
+    c->br = nullptr;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc && bonds) {
@@ -273,6 +277,22 @@ extern "C" int sim_set_fem_bending(sim_ctx* c, fem_ctx* fem, float k0)
     drop_graphs(c);
     c->fem = f;
     c->fem_k0 = k0;
+    return PFSI_OK;
+}
+
+extern "C" int sim_set_bridges(sim_ctx* c, bridge_ctx* br)
+{
+    if (!c) return set_error(PFSI_ERR_ARG, "sim_set_bridges: bad argument");
+    BridgeCtx* b = bridge_internal(br);
+    if (b && bridge_bonds(b) != c->bonds)
+        return set_error(PFSI_ERR_ARG, "sim_set_bridges: bridges not built on the simulation's bonds");
+    drop_graphs(c);
+    c->br = b;
+    if (b) {
+        const unsigned long long step = c->step;
+        return check_cuda(cudaMemcpy(bridge_step_counter(b), &step, sizeof(step), cudaMemcpyHostToDevice),
+                          "sim_set_bridges: step counter");
+    }
     return PFSI_OK;
 }
 

@@ -54,6 +54,12 @@ class bond_params(ctypes.Structure):
                 ("seed", c_uint64)]
 
 
+class bridge_params(ctypes.Structure):
+    _fields_ = [("sigma", c_double), ("l_b", c_double), ("d_capture", c_double), ("gamma", c_double),
+                ("kT", c_double), ("kon0_dt", c_double), ("koff0_dt", c_double), ("box_nx", c_int),
+                ("box_ny", c_int), ("seed", c_uint64)]
+
+
 P = c_void_p
 _SIGS = {
     "pfsi_last_error": [ctypes.c_char_p, c_size_t],
@@ -91,6 +97,14 @@ _SIGS = {
     "sim_step_index": [P, ctypes.POINTER(c_uint64)],
     "sim_time_lb": [P, c_int],
     "sim_set_surrogate": [P, P, P],
+    "bridges_query_workspace": [ctypes.POINTER(bridge_params), c_int, c_int, c_int, ctypes.POINTER(c_size_t)],
+    "bridges_create": [ctypes.POINTER(bridge_params), P, c_int, P, c_int, P, P, c_size_t, ctypes.POINTER(P)],
+    "bridges_destroy": [P],
+    "bridges_forces": [P, P, P, c_int, P],
+    "bridges_step": [P, P, c_int, c_uint64, P],
+    "bridges_status": [P, ctypes.POINTER(c_longlong)],
+    "bridges_partner": [P, ctypes.POINTER(P)],
+    "sim_set_bridges": [P, P],
     "fem_query_workspace": [c_int, c_int, ctypes.POINTER(c_size_t)],
     "fem_create": [c_int, c_int, P, P, c_size_t, ctypes.POINTER(P)],
     "fem_destroy": [P],
@@ -507,6 +521,56 @@ class Bonds:
             self.h = None
 
 
+def bridge_params_from(d):
+    return bridge_params(float(d["sigma"]), float(d["l_b"]), float(d["d_capture"]), float(d["gamma"]),
+                         float(d["kT"]), float(d["kon0_dt"]), float(d["koff0_dt"]), int(d["box_nx"]),
+                         int(d["box_ny"]), int(d["seed"]))
+
+
+class Bridges:
+    """Platelet-platelet bridges between the receptor sites of a Bonds set
+    (which this object keeps alive: the bridges go first)."""
+
+    def __init__(self, params, bonds, node_plt, n_plt, partner=None, device="cuda"):
+        self.p = bridge_params_from(params)
+        self.bonds = bonds
+        node_plt = np.ascontiguousarray(node_plt, dtype=np.int32)
+        self.M = int(node_plt.size)
+        R = bonds.R
+        if partner is None:
+            partner = np.full(R, -1, dtype=np.int32)
+        pa = np.asarray(partner, dtype=np.int32)
+        if R and (pa.min() < -1 or pa.max() >= R):
+            raise ValueError("partner ids out of range")
+        idx = np.where(pa >= 0)[0]
+        if np.any(pa[pa[idx]] != idx) or np.any(pa[idx] == idx):
+            raise ValueError("partner array must pair distinct sites symmetrically")
+        self.partner = torch.as_tensor(np.ascontiguousarray(pa), device=device).clone()
+        nb = c_size_t()
+        _call("bridges_query_workspace", ctypes.byref(self.p), R, int(n_plt), self.M, ctypes.byref(nb))
+        self.ws = _bytes(nb.value, device)
+        h = c_void_p()
+        _call("bridges_create", ctypes.byref(self.p), bonds.h, int(n_plt), _ptr(node_plt), self.M,
+              _ptr(self.partner), _ptr(self.ws), nb.value, ctypes.byref(h))
+        self.h = h
+
+    def forces(self, X, F, stream=None):
+        _call("bridges_forces", self.h, _ptr(X), _ptr(F), self.M, _stream(stream))
+
+    def step(self, X, step, stream=None):
+        _call("bridges_step", self.h, _ptr(X), self.M, int(step), _stream(stream))
+
+    def status(self):
+        out = (c_longlong * 3)()
+        _call("bridges_status", self.h, out)
+        return tuple(int(v) for v in out)
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.bridges_destroy(self.h)
+            self.h = None
+
+
 class Simulation:
     """The coupled step on one workload (see :mod:`paper_1312_2234_b300.workload`)."""
 
@@ -536,6 +600,11 @@ class Simulation:
                             self.X, self.F, self.U, self.M, first_step)
         if self.fem is not None:
             _call("sim_set_fem_bending", self.h, self.fem.h, float(w["membrane"]["k0"]))
+        self.bridges = None
+        if w.get("bridges") is not None and self.bonds is not None:
+            self.bridges = Bridges(w["bridges"], self.bonds, w["mesh"]["node_plt"], w["mesh"]["n_plt"],
+                                   w.get("partner"), device)
+            _call("sim_set_bridges", self.h, self.bridges.h)
 
     def step(self, n=1, stream=None):
         sim_step(self.h, n, stream)

@@ -246,9 +246,20 @@ def platelet_template(level, n_sce, n_sites, a_lat, aspect, rng):
 # ---------------------------------------------------------------------------
 # Workloads
 # ---------------------------------------------------------------------------
+def bridge_params(bonds):
+    """Platelet-platelet bridge parameters from the wall-bond ones (lattice
+    units).  Reading of "treated similarly": a bridge is two GPIb-alpha - vWF
+    links in series, so its rest length and capture distance are twice the
+    single link's and its spring constant half; the kinetic constants of
+    Eq. 12-13 are the single link's."""
+    return dict(sigma=0.5 * bonds["sigma"], l_b=2.0 * bonds["l_b"], d_capture=2.0 * bonds["d_capture"],
+                gamma=bonds["gamma"], kT=bonds["kT"], kon0_dt=bonds["kon0_dt"], koff0_dt=bonds["koff0_dt"],
+                box_nx=bonds["box_nx"], box_ny=bonds["box_ny"], seed=bonds["seed"])
+
+
 def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
           patch=None, gap=0.5, z_max=None, orient="random", stiffness=1.0,
-          phys=None, centers=None):
+          phys=None, centers=None, bridges=False):
     """A channel workload in lattice units.
 
     shear: wall shear rate in 1/s (top wall moves at shear * nz * dt).
@@ -322,7 +333,7 @@ def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
                  box_nx=nx, box_ny=ny, seed=seed)
     Xsoa = np.ascontiguousarray(X.T).ravel()   # [3][M]
     st = np.concatenate(site_tri).astype(np.int32)
-    return dict(
+    w = dict(
         grid=dict(nx=nx, ny=ny, nz=nz, tau=tau, u_top=(shear * L["dt"] * nz, 0.0, 0.0),
                   body=(0.0, 0.0, 0.0)),
         dt=L["dt"], shear=shear,
@@ -337,6 +348,10 @@ def build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
         bound=np.full(len(st), -1, dtype=np.int32),
         lig_count=np.zeros(patch[2] * patch[3], dtype=np.int32),
     )
+    if bridges:
+        w["bridges"] = bridge_params(bonds)
+        w["partner"] = np.full(len(st), -1, dtype=np.int32)
+    return w
 
 
 def config_small(seed=0):
@@ -363,6 +378,20 @@ def tiny(seed=0, nx=24, ny=20, nz=18, level=1, n_sce=8, n_sites=40, n_plt=1, she
     return build(nx, ny, nz, tau, shear, n_plt, level, n_sce, n_sites, seed,
                  patch=(nx // 4, ny // 4, nx // 2, ny // 2), orient=orient, gap=gap,
                  centers=centers)
+
+
+def config_pair(seed=0, gap=0.4, nx=64, ny=48, nz=40, shear=1000.0, level=4, n_sce=800, n_sites=5000):
+    """Two interacting platelets near the wall (the platelet-platelet
+    adhesion study, Section 4.3.3): discoid platelets lying flat, the lower
+    one `gap` above the wall over the ligand patch, the upper one stacked on
+    it `gap` higher and shifted by a quarter radius in x; receptor sites on
+    both, wall bonds and platelet-platelet bridges."""
+    a = PHYSICAL["a"] / PHYSICAL["h"]
+    c = a * PHYSICAL["aspect"]
+    z0 = -0.5 + gap + c
+    centers = [(nx / 2.0 + 0.37, ny / 2.0 - 0.21, z0), (nx / 2.0 + 0.37 + 0.25 * a, ny / 2.0 - 0.21, z0 + 2 * c + gap)]
+    return build(nx, ny, nz, 0.8, shear, 2, level, n_sce, n_sites, seed, orient="flat", gap=gap,
+                 centers=centers, bridges=True)
 
 
 def config_batched(seed=0, n_chambers=64):
