@@ -943,12 +943,11 @@ void ora_bridges_step(const ora_bridge_params* p, int n_sites, const int* site_t
     int* choice = (int*)malloc(sizeof(int) * n);
     for (int s = 0; s < n_sites; ++s) site_position(NULL, site_tri, site_w, tri, M, X, s, &r[3 * s]);
 
-    /* rupture */
-    for (int s = 0; s < n_sites; ++s) is_free[s] = 1;
+    /* rupture; both sites of every bridge standing at the start of the step
+     * stay unavailable until the next one */
+    for (int s = 0; s < n_sites; ++s) is_free[s] = (partner[s] < 0);
     for (int i = 0; i < n_sites; ++i) {
         int j = partner[i];
-        if (j < 0) continue;
-        is_free[i] = 0;
         if (j < i) continue;
         double d[3];
         pair_vector(p, &r[3 * i], &r[3 * j], d);

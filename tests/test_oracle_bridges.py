@@ -147,6 +147,14 @@ def test_one_bond_per_site_and_no_reformation_in_the_same_step():
         step_pair(p, X, tri, plt, st, sw, partner, step)
         seq.append(int(partner[0]))
     assert seq == [1, -1, 1, -1]
+    # both ends of a ruptured bridge wait a step, whichever index they have:
+    # site 1 (the higher end) does not bridge to site 2 in the step its bridge broke
+    X3, tri3, plt3, st3, sw3 = sites_on_platelets([(10, 10, 5), (10.5, 10, 5), (10.5, 10.5, 5)], [0, 1, 2])
+    partner = np.array([1, 0, -1], dtype=np.int32)
+    step_pair(p, X3, tri3, plt3, st3, sw3, partner, 0)
+    assert list(partner) == [-1, -1, -1]
+    step_pair(params(kon0_dt=60.0), X3, tri3, plt3, st3, sw3, partner, 1)
+    assert list(partner) == [1, 0, -1]
     # a bridged site takes no wall bond even when one is certain
     w = {"lig_i0": 0, "lig_j0": 0, "lig_ni": 64, "lig_nj": 48, "box_nx": 64, "box_ny": 48, "max_per_ligand": 4,
          "z_wall": 4.9, "sigma": 0.05, "l_b": 0.1, "d_capture": 0.9, "gamma": 0.0, "kT": 1.0, "kon0_dt": 60.0,
