@@ -235,6 +235,7 @@ def run_native(args, rank, ws):
     extras = {}
     if not args.no_extras:
         extras["fem_bending"] = run_fem(args, w, ms_per_step, dev, flush, stream)
+        extras["platelet_pair"] = run_pair(args, dev, flush, stream)
         extras["batched"] = run_batched(args, dev, stream)
         extras["surrogate"], sg_params = run_surrogate(args, w, sim, dev, stream)
         extras["full_scale"] = run_full(args, dev, stream, sg_params)
@@ -546,6 +547,39 @@ def run_fem(args, w, ms_dihedral, dev, flush, stream):
                      "elements_per_s": ne * reps / t}
         del fb, X, F
         torch.cuda.empty_cache()
+    return out
+
+
+def run_pair(args, dev, flush, stream):
+    """Two stacked platelets over the ligand patch (the platelet-platelet
+    study): the coupled step with wall bonds and platelet-platelet bridges,
+    and without the bridges, timed like the headline (L2 flushed before every
+    step)."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    w = workload.config_pair(seed=0)
+    N = w["grid"]["nx"] * w["grid"]["ny"] * w["grid"]["nz"]
+    out = {"workload": "64x48x40 channel, shear 1000/s, two stacked platelets (2562 + 800 SCE, 5000 receptors "
+                       "each), wall bonds + platelet-platelet bridges", "cells": N, "nodes": w["M"],
+           "sites": int(len(w["sites"]["tri"]))}
+    steps = max(3, args.steps)
+    for name, wk in (("with_bridges", w), ("without_bridges", {k: v for k, v in w.items() if k != "bridges"})):
+        sim = fsi.Simulation(wk, device=dev)
+        sim.step(3)
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(1)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        step_ms = float(np.mean(ms))
+        out[name] = {"value": N / step_ms / 1e3, "unit": "MLUPS", "ms_per_step": step_ms}
+        del sim
+    out["bridge_us_per_step"] = 1e3 * (out["with_bridges"]["ms_per_step"] - out["without_bridges"]["ms_per_step"])
     return out
 
 
