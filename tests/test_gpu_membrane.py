@@ -24,7 +24,7 @@ ONLY = {"spring": ("k_spring",), "area_local": ("k_t",), "area_global": ("k_s",)
 
 
 def f32(d):
-    return {k: float(np.float32(v)) for k, v in d.items()}
+    return {k: (float(np.float32(v)) if isinstance(v, float) else v) for k, v in d.items()}
 
 
 def deformed(w, strain, seed):
