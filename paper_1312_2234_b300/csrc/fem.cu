@@ -23,9 +23,12 @@
 //   pass 3  surface divergence of g: c0.dg/dxi + c1.dg/deta; node: mean
 //           (= Lap_S K), then F_i = A_i (k0/2)(Lap_S K + 2K(K^2 - K_G)) n_i.
 //
-// Positions are FP64; every element works in coordinates relative to its
-// first corner (FP64 differences rounded to FP32), so the FP32 derivatives
-// do not lose the digits of the absolute position.
+// Positions are FP64, read as hi/lo float pairs (x = hi + lo, as the
+// membrane pass splits them; a split pass runs first when no split is
+// given).  Every element works in coordinates relative to its first corner,
+// (hi_k - hi_0) + (lo_k - lo_0) in FP32, which keeps the digits the absolute
+// position would lose and uses no FP64 arithmetic (a scarce pipe on this
+// part).
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -43,6 +46,8 @@ struct FemCtx {
     float4* nrm;        // [n] (unit normal, area)
     float4* curv;       // [n] (K, K_G, Lap_S K, -)
     float4* grad;       // [n] (surface gradient of K, -)
+    float* xh;          // [3n] own split of the positions (standalone calls)
+    float* xl;
 };
 
 namespace {
@@ -80,36 +85,6 @@ __device__ __forceinline__ void basis_derivatives(int j, float dxi[6], float det
     deta[5] = 4.0f * (z - eta);
 }
 
-struct ElemNode {
-    int idx[6];     // global nodes of the element
-    float3 d[6];    // positions relative to corner 0
-    float dxi[6], deta[6];
-    float3 a_xi, a_eta;
-};
-
-__device__ __forceinline__ void load_element(const int* __restrict__ elem, const double* __restrict__ X, int n, int e,
-                                             int j, ElemNode& E)
-{
-#pragma unroll
-    for (int k = 0; k < 6; ++k) E.idx[k] = __ldg(elem + 6 * e + k);
-    const int i0 = E.idx[0];
-    const double x0 = __ldg(X + i0), y0 = __ldg(X + n + i0), z0 = __ldg(X + 2 * n + i0);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const int i = E.idx[k];
-        E.d[k] = make_float3((float)(__ldg(X + i) - x0), (float)(__ldg(X + n + i) - y0), (float)(__ldg(X + 2 * n + i) - z0));
-    }
-    basis_derivatives(j, E.dxi, E.deta);
-    float3 ax = make_float3(0.f, 0.f, 0.f), ae = ax;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        ax = ax + E.dxi[k] * E.d[k];
-        ae = ae + E.deta[k] * E.d[k];
-    }
-    E.a_xi = ax;
-    E.a_eta = ae;
-}
-
 __device__ __forceinline__ float tri_area(float3 a, float3 b, float3 c)
 {
     const float3 n = cross3(b - a, c - a);
@@ -117,71 +92,132 @@ __device__ __forceinline__ float tri_area(float3 a, float3 b, float3 c)
 }
 
 // Columns c0, c1 of the inverse of the row matrix [a_xi; a_eta; n].
-__device__ __forceinline__ void tangential_inverse(const ElemNode& E, float3 n, float3& c0, float3& c1)
+__device__ __forceinline__ void tangential_inverse(float3 a_xi, float3 a_eta, float3 n, float3& c0, float3& c1)
 {
-    const float3 en = cross3(E.a_eta, n);
-    const float inv = 1.0f / dot3(E.a_xi, en);
+    const float3 en = cross3(a_eta, n);
+    const float inv = 1.0f / dot3(a_xi, en);
     c0 = inv * en;
-    c1 = inv * cross3(n, E.a_xi);
+    c1 = inv * cross3(n, a_xi);
 }
 
-template <int Pass>
-__global__ void __launch_bounds__(kFemThreads) k_fem_elem(FemCtx c, const double* __restrict__ X)
+// x = hi + lo, hi the FP32 rounding of x (one coordinate per thread).
+__global__ void k_fem_split(int n, const double* __restrict__ X, float* __restrict__ xh, float* __restrict__ xl)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 6 * c.ne) return;
-    const int e = t / 6, j = t - 6 * e;
-    ElemNode E;
-    load_element(c.elem, X, c.n, e, j, E);
-    float4 out;
-    if (Pass == 0) {
-        float3 nv = cross3(E.a_xi, E.a_eta);
-        nv = rsqrtf(dot3(nv, nv)) * nv;
-        // sub-triangles (0,3,5), (3,1,4), (5,4,2), (3,4,5): corners touch one,
-        // midpoints three
-        float a = 0.f;
-        if (j == 0 || j == 3 || j == 5) a += tri_area(E.d[0], E.d[3], E.d[5]);
-        if (j == 1 || j == 3 || j == 4) a += tri_area(E.d[3], E.d[1], E.d[4]);
-        if (j == 2 || j == 4 || j == 5) a += tri_area(E.d[5], E.d[4], E.d[2]);
-        if (j >= 3) a += tri_area(E.d[3], E.d[4], E.d[5]);
-        out = make_float4(nv.x, nv.y, nv.z, a * (1.0f / 3.0f));
-    } else {
-        const float3 nj = f3(c.nrm[E.idx[j]]);
-        float3 c0, c1;
-        tangential_inverse(E, nj, c0, c1);
-        if (Pass == 1) {
-            float3 dn_xi = make_float3(0.f, 0.f, 0.f), dn_eta = dn_xi;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const double x = X[i];
+    const float h = (float)x;
+    xh[i] = h;
+    xl[i] = (float)(x - (double)h);
+}
+
+// One thread per element: loads its six nodes once and writes the values of
+// all six element nodes (the loop over j is unrolled, so the basis
+// derivatives at node j are constants).
+template <int Pass>
+__global__ void __launch_bounds__(kFemThreads)
+    k_fem_elem(FemCtx c, const float* __restrict__ xh, const float* __restrict__ xl)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c.ne) return;
+    const int n = c.n;
+    int idx[6];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float3 nk = f3(c.nrm[E.idx[k]]);
-                dn_xi = dn_xi + E.dxi[k] * nk;
-                dn_eta = dn_eta + E.deta[k] * nk;
-            }
-            const float p = dot3(c0, dn_xi), q = dot3(c1, dn_eta);
-            const float r = dot3(c0, dn_eta), s = dot3(c1, dn_xi);
-            out = make_float4(0.5f * (p + q), p * q - r * s, 0.f, 0.f);
-        } else if (Pass == 2) {
-            float k_xi = 0.f, k_eta = 0.f;
+    for (int k = 0; k < 6; ++k) idx[k] = __ldg(c.elem + 6 * e + k);
+    // positions relative to corner 0: (hi_k - hi_0) + (lo_k - lo_0)
+    float3 d[6];
+    {
+        const int i0 = idx[0];
+        const float h0x = __ldg(xh + i0), h0y = __ldg(xh + n + i0), h0z = __ldg(xh + 2 * n + i0);
+        const float l0x = __ldg(xl + i0), l0y = __ldg(xl + n + i0), l0z = __ldg(xl + 2 * n + i0);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float Kk = c.curv[E.idx[k]].x;
-                k_xi += E.dxi[k] * Kk;
-                k_eta += E.deta[k] * Kk;
-            }
-            const float3 g = k_xi * c0 + k_eta * c1;
-            out = make_float4(g.x, g.y, g.z, 0.f);
-        } else {
-            float3 g_xi = make_float3(0.f, 0.f, 0.f), g_eta = g_xi;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float3 gk = f3(c.grad[E.idx[k]]);
-                g_xi = g_xi + E.dxi[k] * gk;
-                g_eta = g_eta + E.deta[k] * gk;
-            }
-            out = make_float4(dot3(c0, g_xi) + dot3(c1, g_eta), 0.f, 0.f, 0.f);
+        for (int k = 0; k < 6; ++k) {
+            const int i = idx[k];
+            d[k] = make_float3((__ldg(xh + i) - h0x) + (__ldg(xl + i) - l0x),
+                               (__ldg(xh + n + i) - h0y) + (__ldg(xl + n + i) - l0y),
+                               (__ldg(xh + 2 * n + i) - h0z) + (__ldg(xl + 2 * n + i) - l0z));
         }
     }
-    c.slot[t] = out;
+    // nodal values of the previous node pass
+    float3 nrm[6], val[6];
+    float kv[6];
+    if (Pass >= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nrm[k] = f3(c.nrm[idx[k]]);
+    }
+    if (Pass == 2) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) kv[k] = c.curv[idx[k]].x;
+    }
+    if (Pass == 3) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) val[k] = f3(c.grad[idx[k]]);
+    }
+    float area[4];
+    if (Pass == 0) {
+        // sub-triangles (0,3,5), (3,1,4), (5,4,2), (3,4,5)
+        area[0] = tri_area(d[0], d[3], d[5]);
+        area[1] = tri_area(d[3], d[1], d[4]);
+        area[2] = tri_area(d[5], d[4], d[2]);
+        area[3] = tri_area(d[3], d[4], d[5]);
+    }
+    float4* out = c.slot + 6 * (size_t)e;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        float dxi[6], deta[6];
+        basis_derivatives(j, dxi, deta);
+        float3 a_xi = make_float3(0.f, 0.f, 0.f), a_eta = a_xi;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            a_xi = a_xi + dxi[k] * d[k];
+            a_eta = a_eta + deta[k] * d[k];
+        }
+        float4 o;
+        if (Pass == 0) {
+            float3 nv = cross3(a_xi, a_eta);
+            nv = rsqrtf(dot3(nv, nv)) * nv;
+            // corners touch one sub-triangle, midpoints three
+            const float a = j == 0   ? area[0]
+                            : j == 1 ? area[1]
+                            : j == 2 ? area[2]
+                            : j == 3 ? area[0] + area[1] + area[3]
+                            : j == 4 ? area[1] + area[2] + area[3]
+                                     : area[0] + area[2] + area[3];
+            o = make_float4(nv.x, nv.y, nv.z, a * (1.0f / 3.0f));
+        } else {
+            float3 c0, c1;
+            tangential_inverse(a_xi, a_eta, nrm[j], c0, c1);
+            if (Pass == 1) {
+                float3 dn_xi = make_float3(0.f, 0.f, 0.f), dn_eta = dn_xi;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    dn_xi = dn_xi + dxi[k] * nrm[k];
+                    dn_eta = dn_eta + deta[k] * nrm[k];
+                }
+                const float p = dot3(c0, dn_xi), q = dot3(c1, dn_eta);
+                const float r = dot3(c0, dn_eta), s = dot3(c1, dn_xi);
+                o = make_float4(0.5f * (p + q), p * q - r * s, 0.f, 0.f);
+            } else if (Pass == 2) {
+                float k_xi = 0.f, k_eta = 0.f;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    k_xi += dxi[k] * kv[k];
+                    k_eta += deta[k] * kv[k];
+                }
+                const float3 g = k_xi * c0 + k_eta * c1;
+                o = make_float4(g.x, g.y, g.z, 0.f);
+            } else {
+                float3 g_xi = make_float3(0.f, 0.f, 0.f), g_eta = g_xi;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    g_xi = g_xi + dxi[k] * val[k];
+                    g_eta = g_eta + deta[k] * val[k];
+                }
+                o = make_float4(dot3(c0, g_xi) + dot3(c1, g_eta), 0.f, 0.f, 0.f);
+            }
+        }
+        out[j] = o;
+    }
 }
 
 // Node pass: fixed-order sum over the node's element nodes.  Pass 3 also
@@ -244,7 +280,7 @@ __global__ void __launch_bounds__(kFemThreads)
 }
 
 struct FemLayout {
-    size_t off, list, elem, slot, nrm, curv, grad, total;
+    size_t off, list, elem, slot, nrm, curv, grad, xh, xl, total;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -267,24 +303,34 @@ FemLayout fem_layout(int n, int ne)
     o += up256(16 * (size_t)n);
     L.grad = o;
     o += up256(16 * (size_t)n);
+    L.xh = o;
+    o += up256(12 * (size_t)n);
+    L.xl = o;
+    o += up256(12 * (size_t)n);
     L.total = o;
     return L;
 }
 
 }  // namespace
 
-int launch_fem_forces(FemCtx* c, float k0, const double* X, float* F, int accumulate, float* fields, cudaStream_t s)
+int launch_fem_forces(FemCtx* c, float k0, const double* X, const float* xh, const float* xl, float* F,
+                      int accumulate, float* fields, cudaStream_t s)
 {
-    const int ge = (6 * c->ne + kFemThreads - 1) / kFemThreads;
+    const int ge = (c->ne + kFemThreads - 1) / kFemThreads;
     const int gn = (c->n + kFemThreads - 1) / kFemThreads;
     const FemCtx v = *c;
-    k_fem_elem<0><<<ge, kFemThreads, 0, s>>>(v, X);
+    if (!xh || !xl) {
+        k_fem_split<<<(3 * c->n + kFemThreads - 1) / kFemThreads, kFemThreads, 0, s>>>(c->n, X, c->xh, c->xl);
+        xh = c->xh;
+        xl = c->xl;
+    }
+    k_fem_elem<0><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
     k_fem_node<0><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<1><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_elem<1><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
     k_fem_node<1><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<2><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_elem<2><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
     k_fem_node<2><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<3><<<ge, kFemThreads, 0, s>>>(v, X);
+    k_fem_elem<3><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
     k_fem_node<3><<<gn, kFemThreads, 0, s>>>(v, k0, F, accumulate, fields);
     return check_launch("fem bending");
 }
@@ -337,7 +383,8 @@ extern "C" int fem_create(int n_nodes, int n_elem, const int* elem6, void* ws, s
     if (rc) return rc;
     fem_ctx* c = new fem_ctx();
     c->d = FemCtx{n_nodes, n_elem, (const int*)(b + L.off), (const int*)(b + L.list), (const int*)(b + L.elem),
-                  (float4*)(b + L.slot), (float4*)(b + L.nrm), (float4*)(b + L.curv), (float4*)(b + L.grad)};
+                  (float4*)(b + L.slot), (float4*)(b + L.nrm), (float4*)(b + L.curv), (float4*)(b + L.grad),
+                  (float*)(b + L.xh), (float*)(b + L.xl)};
     c->ws = ws;
     *out = c;
     return PFSI_OK;
@@ -353,12 +400,12 @@ extern "C" int fem_bending_forces(fem_ctx* c, float k0, const double* X, float* 
 {
     if (!c || !X || !F) return set_error(PFSI_ERR_ARG, "fem_bending_forces: bad argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "fem_bending_forces: misaligned buffer");
-    return launch_fem_forces(&c->d, k0, X, F, accumulate ? 1 : 0, nullptr, as_stream(stream));
+    return launch_fem_forces(&c->d, k0, X, nullptr, nullptr, F, accumulate ? 1 : 0, nullptr, as_stream(stream));
 }
 
 extern "C" int fem_fields(fem_ctx* c, const double* X, float* fields, void* stream)
 {
     if (!c || !X || !fields) return set_error(PFSI_ERR_ARG, "fem_fields: bad argument");
     if (!aligned(X, 8) || !aligned(fields, 4)) return set_error(PFSI_ERR_ARG, "fem_fields: misaligned buffer");
-    return launch_fem_forces(&c->d, 0.0f, X, nullptr, 0, fields, as_stream(stream));
+    return launch_fem_forces(&c->d, 0.0f, X, nullptr, nullptr, nullptr, 0, fields, as_stream(stream));
 }

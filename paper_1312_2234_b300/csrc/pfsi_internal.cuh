@@ -191,9 +191,10 @@ BondCtx* bridge_bonds(BridgeCtx* c);
 
 struct FemCtx;
 // Finite-element bending force (Eq. 6-10): F (+)= the nodal force; fields
-// (nullable) receives the nodal normals, areas and curvatures.
-int launch_fem_forces(FemCtx* c, float k0, const double* X, float* F, int accumulate, float* fields,
-                      cudaStream_t s);
+// (nullable) receives the nodal normals, areas and curvatures.  xh, xl: the
+// positions split into hi/lo floats ([3][n]), or null to split X first.
+int launch_fem_forces(FemCtx* c, float k0, const double* X, const float* xh, const float* xl, float* F,
+                      int accumulate, float* fields, cudaStream_t s);
 FemCtx* fem_internal(fem_ctx* c);
 int fem_node_count(const FemCtx* c);
 

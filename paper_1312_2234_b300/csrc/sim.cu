@@ -51,7 +51,8 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     } else {
         rc = launch_membrane_forces(c->mem, c->X, c->F, s);
     }
-    if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->F, 1, nullptr, s);
+    // the membrane pass (plain or global-only) left the hi/lo split of X in mem->xh, xl
+    if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->mem->xh, c->mem->xl, c->F, 1, nullptr, s);
     if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc && c->br) rc = launch_bridge_forces(c->br, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
