@@ -150,7 +150,7 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
     const size_t N = n, T = nt, E = ne, P = np, Q = nplt;
     const size_t bytes[S_COUNT] = {
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
-        4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 16 * Q, 12 * N, 12 * N,
+        4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 24 * Q, 12 * N, 12 * N,
         64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q)};
     Layout L;
     size_t o = 0;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
     const Split X{c.xh, c.xl, c.n};
     const mem_params P = c.p;
     int plt = -1;
-    double dS = 0.0, V = 0.0;
+    ff dS{0.f, 0.f}, V6{0.f, 0.f};   // per-platelet sums, double-float (no FP64 arithmetic here)
     if (t < c.ne) {
         const int4 q = c.edge[t];
         const float4 er = c.edge_rest[t];
@@ -313,9 +313,8 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
         out[1] = make_float4(gb.x, gb.y, gb.z, tsc);
         out[2] = make_float4(gc.x, gc.y, gc.z, tsc);
         out[3] = make_float4(nn.x * (1.0f / 6.0f), nn.y * (1.0f / 6.0f), nn.z * (1.0f / 6.0f), 0.f);
-        const ff v6 = ff3_dot(X.diff(a, c.plt_anchor[plt]), ff3_cross(e1, e2));
-        dS = (double)ds;
-        V = ((double)v6.h + (double)v6.l) * (1.0 / 6.0);
+        V6 = ff3_dot(X.diff(a, c.plt_anchor[plt]), ff3_cross(e1, e2));
+        dS = ff{ds, 0.f};
     } else if (t < c.ne + c.nt + c.np) {
         const int s = t - c.ne - c.nt;
         const int i = c.pair[2 * s], j = c.pair[2 * s + 1];
@@ -333,18 +332,29 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
     if (__all_sync(0xffffffffu, plt == p0)) {
         if (p0 >= 0) {
             for (int o = 16; o > 0; o >>= 1) {
-                dS += __shfl_down_sync(0xffffffffu, dS, o);
-                V += __shfl_down_sync(0xffffffffu, V, o);
+                dS = ff_add(dS, ff{__shfl_down_sync(0xffffffffu, dS.h, o), __shfl_down_sync(0xffffffffu, dS.l, o)});
+                V6 = ff_add(V6, ff{__shfl_down_sync(0xffffffffu, V6.h, o), __shfl_down_sync(0xffffffffu, V6.l, o)});
             }
             if ((threadIdx.x & 31) == 0) {
-                atomicAdd(&c.acc[2 * p0], dS);
-                atomicAdd(&c.acc[2 * p0 + 1], V);
+                atomicAdd(&c.acc[2 * p0], (double)dS.h + (double)dS.l);
+                atomicAdd(&c.acc[2 * p0 + 1], ((double)V6.h + (double)V6.l) * (1.0 / 6.0));
             }
         }
     } else if (plt >= 0) {
-        atomicAdd(&c.acc[2 * plt], dS);
-        atomicAdd(&c.acc[2 * plt + 1], V);
+        atomicAdd(&c.acc[2 * plt], (double)dS.h + (double)dS.l);
+        atomicAdd(&c.acc[2 * plt + 1], ((double)V6.h + (double)V6.l) * (1.0 / 6.0));
     }
+}
+
+// Pass 2b: per-platelet coefficients of the global area and volume terms
+// (Eq. 4-5), k_s (S - S0)/S0 and k_v (V - V0)/V0, once per platelet.
+__global__ void k_mem_coef(MemCtx c)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.nplt) return;
+    const double* pr = c.plt_rest + 4 * p;  // S0, V0, 1/S0, 1/V0
+    c.coef[p] = make_float2((float)((double)c.p.k_s * c.acc[2 * p] * pr[2]),
+                            (float)((double)c.p.k_v * (c.acc[2 * p + 1] - pr[1]) * pr[3]));
 }
 
 // Pass 3: one thread per node sums its element contributions and applies the
@@ -372,10 +382,8 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
     }
     if (on) {
         // Eq. 4-5: F -= (k_t (S_t - S0_t)/S0_t + k_s (S - S0)/S0) dS_t/dX + k_v (V - V0)/V0 dV/dX
-        const int plt = c.node_plt[v];
-        const double* pr = c.plt_rest + 4 * plt;  // S0, V0, 1/S0, 1/V0
-        const float cSg = (float)((double)P.k_s * c.acc[2 * plt] * pr[2]);
-        const float cV = (float)((double)P.k_v * (c.acc[2 * plt + 1] - pr[1]) * pr[3]);
+        const float2 cf = c.coef[c.node_plt[v]];
+        const float cSg = cf.x, cV = cf.y;
         const int e = c.tcl_off[v + 1];
         for (int s = c.tcl_off[v] + q; s < e; s += kNodeLanes) {
             const int code = c.tcl[s];
@@ -423,6 +431,10 @@ int launch_scalars(MemCtx* c, const double* X, cudaStream_t s)
     if (nel > 0) {
         k_mem_elements<<<(nel + 255) / 256, 256, 0, s>>>(*c);
         rc = check_launch("membrane: element scalars");
+    }
+    if (!rc) {
+        k_mem_coef<<<(c->nplt + 127) / 128, 128, 0, s>>>(*c);
+        rc = check_launch("membrane: platelet coefficients");
     }
     return rc;
 }
@@ -647,6 +659,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->chunks = reinterpret_cast<const int2*>(at(S_CHUNKS));
     c->n_chunks = (int)chunks.size();
     c->acc = reinterpret_cast<double*>(at(S_ACC));
+    c->coef = reinterpret_cast<float2*>(c->acc + 2 * (size_t)nplt);
     c->xh = reinterpret_cast<float*>(at(S_XH));
     c->xl = reinterpret_cast<float*>(at(S_XL));
     c->eout = reinterpret_cast<float4*>(at(S_EOUT));

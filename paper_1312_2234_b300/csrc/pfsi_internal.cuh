@@ -123,6 +123,7 @@ struct MemCtx {
     const int* plt_anchor; // [nplt]
     // scratch, rewritten by every call
     double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
+    float2* coef;          // [nplt] k_s (S - S0)/S0, k_v (V - V0)/V0
     float* xh;             // [3n] positions, high floats
     float* xl;             // [3n] positions, low floats
     float4* eout;          // [4*ne] force on chain vertex k, i, j, l of each edge

@@ -149,3 +149,37 @@ def test_coupled_step(storage, tol_x, tol_u):
     assert np.abs(sim.U.cpu().numpy() - ora.U).max() <= tol_u * np.abs(ora.U).max()
     if sim.bonds is not None:
         assert np.array_equal(sim.bonds.bound.cpu().numpy(), ora.bound)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("dims", [(37, 23, 19), (46, 17, 13), (3, 5, 4)])
+def test_state_varying_along_x(storage, dims):
+    """A state that varies from cell to cell (the developed shear flow plus a
+    random perturbation of the stored f*neq): every pulled population comes
+    from a different value, so a wrong source column (periodic wrap, the
+    last cell of an odd row) shows.  The exported state is the oracle's
+    initial state; bounds as in test_free_steps."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    lat = fsi.Lattice(nx, ny, nz, 0.8, (4e-3, -1.5e-3, 0.0), (2e-6, 0.0, -1e-6), storage=storage)
+    lat.init_shear()
+    rng = np.random.default_rng(11)
+    live = 0 if lat.velocity().data_ptr() == lat.m[0].data_ptr() else 1   # f*neq buffer paired with the moments
+    cur = lat.f[live]
+    noise = torch.from_numpy((3e-5 * rng.standard_normal(tuple(cur.shape))).astype(np.float32)).cuda()
+    cur.copy_((cur.float() + noise * (1.0 if storage == "bf16" else 2.0 ** lat.p.fp16_exponent)).to(cur.dtype))
+    f0 = lat.export().cpu().numpy().astype(np.float64)
+    _, w = oracle.lattice()
+    p = oracle.lb_params(nx, ny, nz, f32(0.8), (f32(4e-3), f32(-1.5e-3), 0.0), (f32(2e-6), 0.0, f32(-1e-6)))
+    f = (f0 + w[:, None]).ravel()
+    n = 12
+    fneq_max = 0.0
+    for _ in range(n):
+        f, rho, v = oracle.lb_step(p, f)
+        fs = f.reshape(19, N) - w[:, None]
+        fneq_max = max(fneq_max, float(np.abs(fs - feq_shifted(rho, v.reshape(3, N))).max()))
+    lat.step(n)
+    torch.cuda.synchronize()
+    bound_f = 1e-5 * np.abs(fs).max() + n * UNIT[storage] * fneq_max
+    err_f = np.abs(lat.export().cpu().numpy() - fs).max()
+    assert err_f <= bound_f, (err_f, bound_f)
