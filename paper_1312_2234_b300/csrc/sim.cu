@@ -24,6 +24,11 @@ struct SimCtx {
     uint64_t step;
     cudaStream_t cap;
     cudaGraphExec_t exec[2];
+    // kMulti-step graphs per starting parity: each step's adhesion update runs on
+    // a side branch beside the next step's membrane pass
+    cudaGraphExec_t multi[2];
+    cudaStream_t side;
+    cudaEvent_t fork, join;
     cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
     SgCtx* sg;             // learned membrane surrogate, or null (plain solver)
     const void* sg_params;
@@ -42,7 +47,11 @@ struct SimCtx {
 
 namespace {
 
-int enqueue_step(SimCtx* c, cudaStream_t s)
+constexpr int kMulti = 4;   // steps per multi-step graph (even: the lattice parity returns)
+
+// Membrane forces of the current positions (F overwritten, then the
+// optional finite-element bending added).
+int enqueue_front(SimCtx* c, cudaStream_t s)
 {
     int rc;
     if (c->sg) {
@@ -53,7 +62,15 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     }
     // the membrane pass (plain or global-only) left the hi/lo split of X in mem->xh, xl
     if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->mem->xh, c->mem->xl, c->F, 1, nullptr, s);
-    if (!rc && c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
+    return rc;
+}
+
+// Bond and bridge forces, spreading, the lattice step, interpolation and
+// advection.
+int enqueue_middle(SimCtx* c, cudaStream_t s)
+{
+    int rc = PFSI_OK;
+    if (c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc && c->br) rc = launch_bridge_forces(c->br, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
     if (!rc && c->lb_ev[0])
@@ -62,8 +79,45 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
     if (!rc && c->lb_ev[1])
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
     if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->n_chunks, s);
-    if (!rc && c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
+    return rc;
+}
+
+// The Monte-Carlo adhesion update of the step (reads X and the bond state).
+int enqueue_adhesion(SimCtx* c, cudaStream_t s)
+{
+    int rc = PFSI_OK;
+    if (c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
     if (!rc && c->br) rc = launch_bridges_step(c->br, c->X, c->M, 0, bridge_step_counter(c->br), s);
+    return rc;
+}
+
+int enqueue_step(SimCtx* c, cudaStream_t s)
+{
+    int rc = enqueue_front(c, s);
+    if (!rc) rc = enqueue_middle(c, s);
+    if (!rc) rc = enqueue_adhesion(c, s);
+    return rc;
+}
+
+// n steps in which step k's adhesion update (reads X after step k, writes
+// only the bond and bridge state) runs on the side stream while step k + 1's
+// membrane pass (reads X, writes only F and the membrane scratch) runs on
+// `s`; step k + 1's bond forces wait for it.  Same operations on the same
+// data as n single steps.
+int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n)
+{
+    int rc = enqueue_front(c, s);
+    if (!rc) rc = enqueue_middle(c, s);
+    for (int k = 1; k < n && !rc; ++k) {
+        rc = check_cuda(cudaEventRecord(c->fork, s), "sim: fork");
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->side, c->fork, 0), "sim: fork");
+        if (!rc) rc = enqueue_adhesion(c, c->side);
+        if (!rc) rc = check_cuda(cudaEventRecord(c->join, c->side), "sim: join");
+        if (!rc) rc = enqueue_front(c, s);
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(s, c->join, 0), "sim: join");
+        if (!rc) rc = enqueue_middle(c, s);
+    }
+    if (!rc) rc = enqueue_adhesion(c, s);
     return rc;
 }
 
@@ -76,8 +130,9 @@ int enqueue_track(SimCtx* c, cudaStream_t s, int parity)
     return rc;
 }
 
-// Captures one step (track = 0) or one step plus the platelet centroids
-// (track = 1) starting at lattice parity `parity`.
+// Captures one step (track = 0), one step plus the platelet centroids
+// (track = 1) or kMulti overlapped steps (track = 2) starting at lattice
+// parity `parity`.
 int capture(SimCtx* c, int parity, int track = 0)
 {
     const int saved = c->lb->cur;
@@ -87,7 +142,9 @@ int capture(SimCtx* c, int parity, int track = 0)
         c->lb->cur = saved;
         return rc;
     }
-    const int rc_enq = track ? enqueue_track(c, c->cap, parity) : enqueue_step(c, c->cap);
+    const int rc_enq = track == 1   ? enqueue_track(c, c->cap, parity)
+                       : track == 2 ? enqueue_overlapped(c, c->cap, kMulti)
+                                    : enqueue_step(c, c->cap);
     cudaGraph_t graph = nullptr;
     rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
     c->lb->cur = saved;
@@ -96,7 +153,8 @@ int capture(SimCtx* c, int parity, int track = 0)
         return rc_enq;
     }
     if (rc) return rc;
-    rc = check_cuda(cudaGraphInstantiate(track ? &c->trk_exec[parity] : &c->exec[parity], graph, 0), "sim: instantiate");
+    cudaGraphExec_t* dst = track == 1 ? &c->trk_exec[parity] : track == 2 ? &c->multi[parity] : &c->exec[parity];
+    rc = check_cuda(cudaGraphInstantiate(dst, graph, 0), "sim: instantiate");
     cudaGraphDestroy(graph);
     return rc;
 }
@@ -108,6 +166,8 @@ void drop_graphs(SimCtx* c)
         c->exec[k] = nullptr;
         if (c->trk_exec[k]) cudaGraphExecDestroy(c->trk_exec[k]);
         c->trk_exec[k] = nullptr;
+        if (c->multi[k]) cudaGraphExecDestroy(c->multi[k]);
+        c->multi[k] = nullptr;
     }
 }
 
@@ -134,6 +194,9 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->M = M;
     c->step = first_step;
     c->exec[0] = c->exec[1] = nullptr;
+    c->multi[0] = c->multi[1] = nullptr;
+    c->side = nullptr;
+    c->fork = c->join = nullptr;
     c->trk_exec[0] = c->trk_exec[1] = nullptr;
     c->trk_scratch = nullptr;
     c->fem = nullptr;
@@ -141,6 +204,9 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->br = nullptr;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "sim_create: stream");
+    if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "sim_create: event");
+    if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "sim_create: event");
     if (!rc && bonds) {
         const unsigned long long s = first_step;
         rc = check_cuda(cudaMemcpy(bonds->counters + 3, &s, sizeof(s), cudaMemcpyHostToDevice), "sim_create: step");
@@ -158,6 +224,9 @@ extern "C" int sim_destroy(sim_ctx* c)
     if (!c) return PFSI_OK;
     drop_graphs(c);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
     for (int k = 0; k < 2; ++k)
         if (c->lb_ev[k]) cudaEventDestroy(c->lb_ev[k]);
     for (cudaEvent_t e : c->rec_ready) cudaEventDestroy(e);
@@ -171,7 +240,21 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
 {
     if (!c || nsteps < 0) return set_error(PFSI_ERR_ARG, "sim_step: bad argument");
     cudaStream_t s = as_stream(stream);
-    for (int k = 0; k < nsteps; ++k) {
+    int k = 0;
+    // kMulti steps per graph launch (not while the lattice step is being
+    // timed: those events belong to single steps)
+    while (!c->lb_ev[0] && nsteps - k >= kMulti) {
+        const int parity = c->lb->cur;
+        if (!c->multi[parity]) {
+            const int rc = capture(c, parity, 2);
+            if (rc) return rc;
+        }
+        const int rc = check_cuda(cudaGraphLaunch(c->multi[parity], s), "sim_step: graph launch");
+        if (rc) return rc;
+        c->step += kMulti;   // even: the lattice parity is unchanged
+        k += kMulti;
+    }
+    for (; k < nsteps; ++k) {
         const int parity = c->lb->cur;
         if (!c->exec[parity]) {
             const int rc = capture(c, parity);
