@@ -155,6 +155,26 @@ def test_fem_workspace_and_validation(L):
     assert "aligned" in fsi.last_error()
 
 
+def test_bridge_workspace_and_parameter_validation(L):
+    """Bridge parameters are checked on the host (capture distance, kT and
+    the periodic box positive, rates non-negative) and the workspace grows
+    with the sites, platelets and nodes."""
+    w = workload.config_pair(seed=0, level=2, n_sce=10, n_sites=100)
+    ok = fsi.bridge_params_from(w["bridges"])
+    nb = ctypes.c_size_t()
+    assert L.bridges_query_workspace(ctypes.byref(ok), 200, 2, w["M"], ctypes.byref(nb)) == 0
+    small = nb.value
+    assert small % 256 == 0
+    assert L.bridges_query_workspace(ctypes.byref(ok), 20000, 2, w["M"], ctypes.byref(nb)) == 0
+    assert nb.value > small
+    for bad in (dict(d_capture=0.0), dict(kT=0.0), dict(kon0_dt=-1.0), dict(koff0_dt=-1.0), dict(box_nx=0)):
+        p = fsi.bridge_params_from(dict(w["bridges"], **bad))
+        assert L.bridges_query_workspace(ctypes.byref(p), 200, 2, w["M"], ctypes.byref(nb)) == -1
+        assert "invalid parameters" in fsi.last_error()
+    assert L.bridges_query_workspace(ctypes.byref(ok), 200, 0, w["M"], ctypes.byref(nb)) == -1
+    assert L.bridges_query_workspace(ctypes.byref(ok), 200, 2, 0, ctypes.byref(nb)) == -1
+
+
 def test_product_path_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(fsi, "_lib", None)
     monkeypatch.setattr(fsi, "LIB_PATH", "/nonexistent/libplatelet_fsi.so")
