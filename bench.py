@@ -685,6 +685,55 @@ def run_surrogate_only(args):
     del glob
 
 
+def run_fem_only(args):
+    """The finite-element bending force alone (profiling aid): the 10-platelet
+    channel mesh (12,800 six-node elements) or, with --grid 512x256x256, the
+    full-scale mesh (640,000), event-timed per evaluation."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    w = workload.config_full(seed=0) if args.grid == "512x256x256" else workload.config_channel(seed=0)
+    fb = fsi.FemBending(w["mesh"])
+    X = torch.as_tensor(np.ascontiguousarray(w["X"], dtype=np.float64)).cuda()
+    F = torch.zeros(3 * w["M"], device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fb.forces(1e-3, X, F)
+    t = timed_steps(lambda: fb.forces(1e-3, X, F), args.steps, stream) / args.steps
+    ne = int(np.asarray(w["mesh"]["elem6"]).size // 6)
+    print(json.dumps({"kernel": "k_fem_elem + k_fem_node (8 launches) + k_fem_split", "elements": ne,
+                      "nodes": w["M"], "us_per_evaluation": 1e6 * t, "elements_per_s": ne / t}), flush=True)
+
+
+def run_bridges_only(args):
+    """The platelet-platelet bridge update alone (profiling aid) on the
+    two-stacked-platelet workload with raised kinetics (so that bridges form
+    and break every step), the nodes held fixed; event-timed per update."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    w = workload.config_pair(seed=0)
+    bp = dict(w["bridges"], sigma=0.02, kT=0.05, gamma=0.05, kon0_dt=0.3, koff0_dt=0.05)
+    st = np.ascontiguousarray(w["sites"]["tri"], dtype=np.int32)
+    sw = np.ascontiguousarray(w["sites"]["w"], dtype=np.float64).reshape(-1, 2)
+    tri = torch.as_tensor(np.ascontiguousarray(w["mesh"]["tri"], dtype=np.int32).ravel()).cuda()
+    bonds = fsi.Bonds(w["bonds"], st, sw, tri, w["bound"], w["lig_count"])
+    br = fsi.Bridges(bp, bonds, w["mesh"]["node_plt"], w["mesh"]["n_plt"])
+    X = torch.as_tensor(np.ascontiguousarray(w["X"], dtype=np.float64)).cuda()
+    stream = torch.cuda.current_stream()
+    state = {"k": 0}
+
+    def one():
+        br.step(X, state["k"])
+        state["k"] += 1
+
+    for _ in range(args.warmup):
+        one()
+    t = timed_steps(one, args.steps, stream) / args.steps
+    ev = br.status()
+    print(json.dumps({"kernel": "bridges_step (rupture, boxes, neighbours, candidate hash, choice, matching)",
+                      "sites": int(len(st)), "us_per_update": 1e6 * t, "ruptures": ev[0], "formations": ev[1],
+                      "standing": int((br.partner >= 0).sum().item()) // 2}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -692,7 +741,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
-    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate"], help="time one kernel alone")
+    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges"],
+                    help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variants")
@@ -706,6 +756,12 @@ def main():
         return
     if args.kernel == "surrogate":
         run_surrogate_only(args)
+        return
+    if args.kernel == "fem":
+        run_fem_only(args)
+        return
+    if args.kernel == "bridges":
+        run_bridges_only(args)
         return
     rank, ws = dist_setup()
     if args.impl == "reference":
