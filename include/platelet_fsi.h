@@ -44,6 +44,7 @@ extern "C" {
 #define PFSI_ERR_ARG (-1)      /* invalid argument (null pointer, bad size, misaligned buffer) */
 #define PFSI_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed */
 #define PFSI_ERR_CAPACITY (-6) /* a device-side list overflowed (see bonds_status) */
+#define PFSI_ERR_UNSTABLE (-7) /* lb_check / sim_check found a non-physical state */
 
 /* Copies the calling thread's last error message into buf (NUL-terminated,
  * truncated to len).  Returns the length of the full message. */
@@ -168,6 +169,17 @@ int lb_velocity(const lb_ctx* ctx, float** v);
  * caller's device scratch dev_scratch4 (4 doubles).
  * out_host[4] = {sum rho, sum rho ux, sum rho uy, sum rho uz}.  Synchronises. */
 int lb_moments_fp64(lb_ctx* ctx, double* dev_scratch4, double* out_host, void* stream);
+
+/* Instability check of the current state (no paper counterpart; a
+ * diagnostic to call every so many steps): counts the cells whose density or
+ * velocity is not finite (or, with 16-bit storage, whose stored f*neq is),
+ * whose density is <= 0, and whose speed |u| exceeds u_max (lattice units;
+ * the BGK scheme needs |u| well below the lattice speed of sound 1/sqrt(3)).
+ * dev_scratch4: caller's device buffer of 4 unsigned 64-bit counters.
+ * out_host[3] = {non-finite, rho <= 0, |u| > u_max}.  Returns
+ * PFSI_ERR_UNSTABLE if any count is nonzero, PFSI_OK otherwise.
+ * Synchronises. */
+int lb_check(lb_ctx* ctx, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream);
 
 /* ===================================================================== *
  * Immersed boundary, Section 3.4.2 (Eq. 33-36, 4-point cosine kernel)
@@ -557,6 +569,12 @@ int sim_set_surrogate(sim_ctx* ctx, sg_ctx* sg, const void* params);
  * it.  The mesh must have the simulation's node count.  The graphs are
  * recaptured. */
 int sim_set_fem_bending(sim_ctx* ctx, fem_ctx* fem, float k0);
+
+/* lb_check of the simulation's lattice plus a scan of the node positions:
+ * out_host[4] = {non-finite cells, rho <= 0, |u| > u_max, nodes with a
+ * non-finite position}.  Returns PFSI_ERR_UNSTABLE if any count is nonzero.
+ * dev_scratch4 as for lb_check.  Synchronises. */
+int sim_check(sim_ctx* ctx, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream);
 
 /* Adds the platelet-platelet bridges to every following step: their spring
  * forces after the wall bond forces, their update after the wall update.

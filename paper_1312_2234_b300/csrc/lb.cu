@@ -24,6 +24,7 @@
 // travels from DRAM.
 #include <algorithm>
 #include <climits>
+#include <string>
 #include <utility>
 
 #include <cuda_bf16.h>
@@ -804,6 +805,100 @@ extern "C" int lb_export(lb_ctx* c, float* f_out, void* stream)
                                                                (const NeqT<PFSI_LB_FP16>*)c->f[c->cur],
                                                                c->m[c->cur], f_out, N, inv_scale_of(p));
     return check_launch("lb_export");
+}
+
+namespace pfsi {
+namespace {
+
+// Counts of the instability check: cnt[0] non-finite, cnt[1] rho <= 0,
+// cnt[2] |u| > u_max (one atomic per thread that found something).
+__device__ __forceinline__ void check_cell(float rho, float ux, float uy, float uz, float u_max2, bool bad_store,
+                                           unsigned long long* c)
+{
+    const bool nf = bad_store || !isfinite(rho) || !isfinite(ux) || !isfinite(uy) || !isfinite(uz);
+    c[0] += nf;
+    c[1] += !nf && rho <= 0.0f;
+    c[2] += !nf && (ux * ux + uy * uy + uz * uz) > u_max2;
+}
+
+__device__ __forceinline__ void flush_counts(const unsigned long long* c, unsigned long long* cnt)
+{
+    for (int k = 0; k < 3; ++k)
+        if (c[k]) atomicAdd(&cnt[k], c[k]);
+}
+
+__global__ void k_lb_check(const float* __restrict__ f, int N, float u_max2, unsigned long long* __restrict__ cnt)
+{
+    unsigned long long c[3] = {0, 0, 0};
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+        float d = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const float fq = f[q * N + cell];
+            d += fq;
+            if (cxq(q)) mx += cxq(q) * fq;
+            if (cyq(q)) my += cyq(q) * fq;
+            if (czq(q)) mz += czq(q) * fq;
+        }
+        const float rho = 1.0f + d, inv = 1.0f / rho;
+        check_cell(rho, mx * inv, my * inv, mz * inv, u_max2, false, c);
+    }
+    flush_counts(c, cnt);
+}
+
+template <int kMode>
+__global__ void k_lb_check_mixed(const uint16_t* __restrict__ neq, const float4* __restrict__ m, int N, float u_max2,
+                                 unsigned long long* __restrict__ cnt)
+{
+    // an all-ones exponent field marks a non-finite 16-bit value
+    constexpr uint16_t kExp = kMode == PFSI_LB_BF16 ? 0x7f80u : 0x7c00u;
+    unsigned long long c[3] = {0, 0, 0};
+    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < 19; ++q) bad |= (neq[q * N + cell] & kExp) == kExp;
+        const float4 v = m[cell];
+        check_cell(1.0f + v.w, v.x, v.y, v.z, u_max2, bad, c);
+    }
+    flush_counts(c, cnt);
+}
+
+}  // namespace
+}  // namespace pfsi
+
+extern "C" int lb_check(lb_ctx* c, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream)
+{
+    if (!c || !dev_scratch4 || !out_host || !(u_max > 0.0f)) return set_error(PFSI_ERR_ARG, "lb_check: bad argument");
+    if (!aligned(dev_scratch4, 8)) return set_error(PFSI_ERR_ARG, "lb_check: scratch must be 8-byte aligned");
+    cudaStream_t s = as_stream(stream);
+    int rc = check_cuda(cudaMemsetAsync(dev_scratch4, 0, 4 * sizeof(unsigned long long), s), "lb_check: clear");
+    if (rc) return rc;
+    const int N = (int)c->N;
+    const int blocks = (N + 255) / 256 < 148 * 8 ? (N + 255) / 256 : 148 * 8;
+    const float u2 = u_max * u_max;
+    switch (c->p.storage) {
+    case PFSI_LB_BF16:
+        k_lb_check_mixed<PFSI_LB_BF16><<<blocks, 256, 0, s>>>((const uint16_t*)c->f[c->cur], c->m[c->cur], N, u2,
+                                                              dev_scratch4);
+        break;
+    case PFSI_LB_FP16:
+        k_lb_check_mixed<PFSI_LB_FP16><<<blocks, 256, 0, s>>>((const uint16_t*)c->f[c->cur], c->m[c->cur], N, u2,
+                                                              dev_scratch4);
+        break;
+    default:
+        k_lb_check<<<blocks, 256, 0, s>>>((const float*)c->f[c->cur], N, u2, dev_scratch4);
+    }
+    if ((rc = check_launch("lb_check"))) return rc;
+    unsigned long long h[4];
+    rc = check_cuda(cudaMemcpyAsync(h, dev_scratch4, sizeof(h), cudaMemcpyDeviceToHost, s), "lb_check: copy");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "lb_check: synchronise");
+    if (rc) return rc;
+    for (int k = 0; k < 3; ++k) out_host[k] = (long long)h[k];
+    if (h[0] || h[1] || h[2])
+        return set_error(PFSI_ERR_UNSTABLE, "lb_check: " + std::to_string(h[0]) + " non-finite cells, " +
+                                                std::to_string(h[1]) + " with rho <= 0, " + std::to_string(h[2]) +
+                                                " faster than u_max");
+    return PFSI_OK;
 }
 
 extern "C" int lb_moments_fp64(lb_ctx* c, double* dev_scratch4, double* out_host, void* stream)

@@ -7,6 +7,7 @@
 // capture stream and then replayed on the caller's stream, so a step costs
 // one graph launch on the host.  The Philox step index lives in device memory
 // (advanced by the last kernel of a step), so replays need no host updates.
+#include <string>
 #include <vector>
 
 #include "pfsi_internal.cuh"
@@ -351,6 +352,39 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     for (int b = 0; b < 2 && b < nsteps && !rc; ++b)
         rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_track: join");
     return rc;
+}
+
+namespace pfsi {
+namespace {
+__global__ void k_sim_check_x(const double* __restrict__ X, int n3, unsigned long long* __restrict__ cnt)
+{
+    unsigned long long c = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += gridDim.x * blockDim.x) c += !isfinite(X[t]);
+    if (c) atomicAdd(cnt, c);
+}
+}  // namespace
+}  // namespace pfsi
+
+extern "C" int sim_check(sim_ctx* c, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream)
+{
+    if (!c || !dev_scratch4 || !out_host) return set_error(PFSI_ERR_ARG, "sim_check: bad argument");
+    const int rc_lb = lb_check(static_cast<lb_ctx*>(c->lb), u_max, dev_scratch4, out_host, stream);
+    if (rc_lb != PFSI_OK && rc_lb != PFSI_ERR_UNSTABLE) return rc_lb;
+    cudaStream_t s = as_stream(stream);
+    int rc = check_cuda(cudaMemsetAsync(dev_scratch4 + 3, 0, sizeof(unsigned long long), s), "sim_check: clear");
+    const int n3 = 3 * c->M;
+    const int blocks = (n3 + 255) / 256 < 148 * 8 ? (n3 + 255) / 256 : 148 * 8;
+    if (!rc && n3 > 0) {
+        k_sim_check_x<<<blocks, 256, 0, s>>>(c->X, n3, dev_scratch4 + 3);
+        rc = check_launch("sim_check");
+    }
+    unsigned long long h = 0;
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(&h, dev_scratch4 + 3, sizeof(h), cudaMemcpyDeviceToHost, s), "sim_check: copy");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "sim_check: synchronise");
+    if (rc) return rc;
+    out_host[3] = (long long)h;
+    if (h) return set_error(PFSI_ERR_UNSTABLE, "sim_check: " + std::to_string(h) + " non-finite node coordinates");
+    return rc_lb;
 }
 
 extern "C" int sim_set_fem_bending(sim_ctx* c, fem_ctx* fem, float k0)

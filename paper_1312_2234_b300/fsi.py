@@ -74,6 +74,8 @@ _SIGS = {
     "lb_step": [P, c_int, P],
     "lb_current": [P, ctypes.POINTER(P)],
     "lb_moments_fp64": [P, P, ctypes.POINTER(c_double), P],
+    "lb_check": [P, c_float, P, ctypes.POINTER(c_longlong), P],
+    "sim_check": [P, c_float, P, ctypes.POINTER(c_longlong), P],
     "ib_spread": [P, P, P, c_int, P],
     "ib_interp": [P, P, P, c_int, c_int, P],
     "membrane_query_workspace": [c_int, c_int, P, c_int, c_int, ctypes.POINTER(c_size_t)],
@@ -165,6 +167,19 @@ def _ok(rc, what):
 
 def _call(name, *args):
     _ok(getattr(lib(), name)(*args), name)
+
+
+PFSI_ERR_UNSTABLE = -7
+
+
+def _check(name, h, u_max, scratch, n, stream=None):
+    """lb_check / sim_check: (counts, ok); a non-physical state is a result,
+    not an exception."""
+    out = (c_longlong * n)()
+    rc = getattr(lib(), name)(h, float(u_max), _ptr(scratch), out, _stream(stream))
+    if rc not in (0, PFSI_ERR_UNSTABLE):
+        _ok(rc, name)
+    return tuple(int(v) for v in out), rc == 0
 
 
 def _ptr(t):
@@ -430,6 +445,10 @@ class Lattice:
     def moments_fp64(self):
         return lb_moments_fp64(self.h, self.scratch)
 
+    def check(self, u_max=0.3):
+        """Instability check: ((non-finite cells, rho <= 0, |u| > u_max), ok)."""
+        return _check("lb_check", self.h, u_max, self.scratch, 3)
+
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
             _lib.lb_destroy(self.h)
@@ -626,6 +645,53 @@ class Simulation:
     @property
     def step_index(self):
         return sim_step_index(self.h)
+
+    def check(self, u_max=0.3):
+        """((non-finite cells, rho <= 0, |u| > u_max, non-finite node
+        coordinates), ok) of the current state."""
+        return _check("sim_check", self.h, u_max, self.lattice.scratch, 4)
+
+    def _live_populations(self):
+        lat = self.lattice
+        if not lat.mixed:
+            return {"f": lat.current()}
+        live = 0 if lat.velocity().data_ptr() == lat.m[0].data_ptr() else 1
+        return {"fneq": lat.f[live], "m": lat.m[live]}
+
+    def checkpoint(self):
+        """The state a later run needs to continue this one: the step index,
+        the lattice populations (FP32, or 16-bit f*neq with the moments), the
+        node positions, the wall-bond and bridge state.  Philox draws are keyed
+        by (site, step), so the continued run takes the same random decisions.
+        Returns a dict of host arrays (np.savez-able)."""
+        torch.cuda.synchronize()
+        ck = {"step": np.array(self.step_index, dtype=np.int64), "storage": np.array(self.lattice.storage),
+              "fp16_exponent": np.array(int(self.lattice.p.fp16_exponent)), "X": self.X.cpu().numpy()}
+        for k, v in self._live_populations().items():
+            ck[k] = v.cpu().numpy() if v.dtype != torch.bfloat16 else v.view(torch.int16).cpu().numpy()
+        if self.bonds is not None:
+            ck["bound"] = self.bonds.bound.cpu().numpy()
+            ck["lig_count"] = self.bonds.lig_count.cpu().numpy()
+        if self.bridges is not None:
+            ck["partner"] = self.bridges.partner.cpu().numpy()
+        return ck
+
+    @classmethod
+    def restore(cls, w, ck, device="cuda", **kw):
+        """A simulation of workload `w` continuing from checkpoint `ck`."""
+        sim = cls(w, device=device, first_step=int(ck["step"]), storage=str(ck["storage"]),
+                  fp16_exponent=int(ck["fp16_exponent"]), **kw)
+        for k, v in sim._live_populations().items():
+            src = torch.as_tensor(ck[k])
+            v.copy_(src.view(torch.bfloat16) if v.dtype == torch.bfloat16 else src)
+        sim.X.copy_(torch.as_tensor(ck["X"]))
+        if sim.bonds is not None:
+            sim.bonds.bound.copy_(torch.as_tensor(ck["bound"]))
+            sim.bonds.lig_count.copy_(torch.as_tensor(ck["lig_count"]))
+        if sim.bridges is not None:
+            sim.bridges.partner.copy_(torch.as_tensor(ck["partner"]))
+        torch.cuda.synchronize()
+        return sim
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:
