@@ -266,12 +266,14 @@ extern "C" int bonds_destroy(bond_ctx* c)
 
 extern "C" int bonds_forces(bond_ctx* c, const double* X, float* F, int M, void* stream)
 {
+    NvtxRange nvtx_range("bonds_forces");
     if (!c || !X || !F || M < 0) return set_error(PFSI_ERR_ARG, "bonds_forces: bad argument");
     return launch_bonds_forces(c, X, F, M, as_stream(stream));
 }
 
 extern "C" int bonds_step(bond_ctx* c, const double* X, int M, uint64_t step, void* stream)
 {
+    NvtxRange nvtx_range("bonds_step");
     if (!c || !X || M < 0) return set_error(PFSI_ERR_ARG, "bonds_step: bad argument");
     return launch_bonds_step(c, X, M, step, nullptr, as_stream(stream));
 }

@@ -742,12 +742,14 @@ extern "C" int bridges_destroy(bridge_ctx* c)
 
 extern "C" int bridges_forces(bridge_ctx* c, const double* X, float* F, int M, void* stream)
 {
+    NvtxRange nvtx_range("bridges_forces");
     if (!c || !X || !F || M < 1) return set_error(PFSI_ERR_ARG, "bridges_forces: bad argument");
     return launch_bridge_forces(c, X, F, M, as_stream(stream));
 }
 
 extern "C" int bridges_step(bridge_ctx* c, const double* X, int M, uint64_t step, void* stream)
 {
+    NvtxRange nvtx_range("bridges_step");
     if (!c || !X || M < 1) return set_error(PFSI_ERR_ARG, "bridges_step: bad argument");
     return launch_bridges_step(c, X, M, step, nullptr, as_stream(stream));
 }

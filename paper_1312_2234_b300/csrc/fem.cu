@@ -398,6 +398,7 @@ extern "C" int fem_destroy(fem_ctx* c)
 
 extern "C" int fem_bending_forces(fem_ctx* c, float k0, const double* X, float* F, int accumulate, void* stream)
 {
+    NvtxRange nvtx_range("fem_bending_forces");
     if (!c || !X || !F) return set_error(PFSI_ERR_ARG, "fem_bending_forces: bad argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "fem_bending_forces: misaligned buffer");
     return launch_fem_forces(&c->d, k0, X, nullptr, nullptr, F, accumulate ? 1 : 0, nullptr, as_stream(stream));
@@ -405,6 +406,7 @@ extern "C" int fem_bending_forces(fem_ctx* c, float k0, const double* X, float* 
 
 extern "C" int fem_fields(fem_ctx* c, const double* X, float* fields, void* stream)
 {
+    NvtxRange nvtx_range("fem_fields");
     if (!c || !X || !fields) return set_error(PFSI_ERR_ARG, "fem_fields: bad argument");
     if (!aligned(X, 8) || !aligned(fields, 4)) return set_error(PFSI_ERR_ARG, "fem_fields: misaligned buffer");
     return launch_fem_forces(&c->d, 0.0f, X, nullptr, nullptr, nullptr, 0, fields, as_stream(stream));

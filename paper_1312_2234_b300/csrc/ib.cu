@@ -384,6 +384,7 @@ using namespace pfsi;
 
 extern "C" int ib_spread(lb_ctx* c, const double* X, const float* F, int M, void* stream)
 {
+    NvtxRange nvtx_range("ib_spread");
     if (!c || M < 0 || (M > 0 && (!X || !F))) return set_error(PFSI_ERR_ARG, "ib_spread: bad argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "ib_spread: misaligned arrays");
     return launch_ib_spread(c, X, F, M, nullptr, 0, as_stream(stream));
@@ -391,6 +392,7 @@ extern "C" int ib_spread(lb_ctx* c, const double* X, const float* F, int M, void
 
 extern "C" int ib_interp(lb_ctx* c, double* X, float* U, int M, int advect, void* stream)
 {
+    NvtxRange nvtx_range("ib_interp");
     if (!c || M < 0 || (M > 0 && (!X || !U))) return set_error(PFSI_ERR_ARG, "ib_interp: bad argument");
     if (!aligned(X, 8) || !aligned(U, 4)) return set_error(PFSI_ERR_ARG, "ib_interp: misaligned arrays");
     return launch_ib_interp(c, X, U, M, advect, nullptr, 0, as_stream(stream));

@@ -685,6 +685,7 @@ extern "C" int lb_destroy(lb_ctx* ctx)
 
 extern "C" int lb_init_shear(lb_ctx* c, void* stream)
 {
+    NvtxRange nvtx_range("lb_init_shear");
     if (!c) return set_error(PFSI_ERR_ARG, "lb_init_shear: null context");
     const int N = (int)c->N;
     const int blocks = (N + 255) / 256 < 148 * 16 ? (N + 255) / 256 : 148 * 16;
@@ -709,6 +710,7 @@ extern "C" int lb_init_shear(lb_ctx* c, void* stream)
 
 extern "C" int lb_step(lb_ctx* c, int nsteps, void* stream)
 {
+    NvtxRange nvtx_range("lb_step");
     if (!c) return set_error(PFSI_ERR_ARG, "lb_step: null context");
     if (nsteps < 0) return set_error(PFSI_ERR_ARG, "lb_step: negative step count");
     for (int s = 0; s < nsteps; ++s) {
@@ -743,6 +745,7 @@ extern "C" int lb_get_shape(const lb_ctx* c, int* shape)
 
 extern "C" int lb_autotune(lb_ctx* c, int reps, void* stream, float* best_ms)
 {
+    NvtxRange nvtx_range("lb_autotune");
     if (!c || reps < 1) return set_error(PFSI_ERR_ARG, "lb_autotune: bad argument");
     cudaStream_t s = as_stream(stream);
     cudaEvent_t e0, e1;
@@ -786,6 +789,7 @@ extern "C" int lb_velocity(const lb_ctx* c, float** v)
 
 extern "C" int lb_export(lb_ctx* c, float* f_out, void* stream)
 {
+    NvtxRange nvtx_range("lb_export");
     if (!c || !f_out) return set_error(PFSI_ERR_ARG, "lb_export: null argument");
     if (!aligned(f_out, 4)) return set_error(PFSI_ERR_ARG, "lb_export: misaligned output");
     cudaStream_t s = as_stream(stream);
@@ -868,6 +872,7 @@ __global__ void k_lb_check_mixed(const uint16_t* __restrict__ neq, const float4*
 
 extern "C" int lb_check(lb_ctx* c, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream)
 {
+    NvtxRange nvtx_range("lb_check");
     if (!c || !dev_scratch4 || !out_host || !(u_max > 0.0f)) return set_error(PFSI_ERR_ARG, "lb_check: bad argument");
     if (!aligned(dev_scratch4, 8)) return set_error(PFSI_ERR_ARG, "lb_check: scratch must be 8-byte aligned");
     cudaStream_t s = as_stream(stream);
@@ -903,6 +908,7 @@ extern "C" int lb_check(lb_ctx* c, float u_max, unsigned long long* dev_scratch4
 
 extern "C" int lb_moments_fp64(lb_ctx* c, double* dev_scratch4, double* out_host, void* stream)
 {
+    NvtxRange nvtx_range("lb_moments_fp64");
     if (!c || !dev_scratch4 || !out_host) return set_error(PFSI_ERR_ARG, "lb_moments_fp64: null argument");
     if (!aligned(dev_scratch4, 8)) return set_error(PFSI_ERR_ARG, "lb_moments_fp64: scratch must be 8-byte aligned");
     cudaStream_t s = as_stream(stream);

@@ -684,6 +684,7 @@ extern "C" int membrane_set_params(mem_ctx* c, const mem_params* p)
 
 extern "C" int membrane_forces(mem_ctx* c, const double* X, float* F, void* stream)
 {
+    NvtxRange nvtx_range("membrane_forces");
     if (!c || !X || !F) return set_error(PFSI_ERR_ARG, "membrane_forces: null argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "membrane_forces: misaligned arrays");
     return launch_membrane_forces(c, X, F, as_stream(stream));
@@ -737,6 +738,7 @@ __global__ void k_centroid_finish(double* __restrict__ acc, int nplt)
 
 extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, void* stream)
 {
+    NvtxRange nvtx_range("membrane_centroids");
     if (!c || !X || !out_dev) return set_error(PFSI_ERR_ARG, "membrane_centroids: null argument");
     if (!aligned(out_dev, 8)) return set_error(PFSI_ERR_ARG, "membrane_centroids: misaligned output");
     cudaStream_t s = as_stream(stream);
@@ -751,6 +753,7 @@ extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, 
 
 extern "C" int membrane_measure(mem_ctx* c, const double* X, double* out_host, void* stream)
 {
+    NvtxRange nvtx_range("membrane_measure");
     if (!c || !X || !out_host) return set_error(PFSI_ERR_ARG, "membrane_measure: null argument");
     cudaStream_t s = as_stream(stream);
     int rc = launch_scalars(c, X, s);

@@ -239,6 +239,7 @@ extern "C" int sim_destroy(sim_ctx* c)
 
 extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
 {
+    NvtxRange nvtx_range("sim_step");
     if (!c || nsteps < 0) return set_error(PFSI_ERR_ARG, "sim_step: bad argument");
     cudaStream_t s = as_stream(stream);
     int k = 0;
@@ -271,6 +272,7 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
 
 extern "C" int sim_step_record(sim_ctx* c, int nsteps, double* dev_ring, double* host_ring, int ring, void* stream)
 {
+    NvtxRange nvtx_range("sim_step_record");
     if (!c || nsteps < 0 || !dev_ring || !host_ring || ring < 2 || ring > 64)
         return set_error(PFSI_ERR_ARG, "sim_step_record: bad argument");
     if (!aligned(dev_ring, 8) || !aligned(host_ring, 8)) return set_error(PFSI_ERR_ARG, "sim_step_record: misaligned ring");
@@ -309,6 +311,7 @@ extern "C" int sim_step_record(sim_ctx* c, int nsteps, double* dev_ring, double*
 
 extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, double* host_out, void* stream)
 {
+    NvtxRange nvtx_range("sim_step_track");
     if (!c || nsteps < 0 || !dev_scratch || !host_out) return set_error(PFSI_ERR_ARG, "sim_step_track: bad argument");
     if (!aligned(dev_scratch, 8) || !aligned(host_out, 8)) return set_error(PFSI_ERR_ARG, "sim_step_track: misaligned buffer");
     cudaStream_t s = as_stream(stream);
@@ -367,6 +370,7 @@ __global__ void k_sim_check_x(const double* __restrict__ X, int n3, unsigned lon
 
 extern "C" int sim_check(sim_ctx* c, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream)
 {
+    NvtxRange nvtx_range("sim_check");
     if (!c || !dev_scratch4 || !out_host) return set_error(PFSI_ERR_ARG, "sim_check: bad argument");
     const int rc_lb = lb_check(static_cast<lb_ctx*>(c->lb), u_max, dev_scratch4, out_host, stream);
     if (rc_lb != PFSI_OK && rc_lb != PFSI_ERR_UNSTABLE) return rc_lb;
@@ -565,6 +569,7 @@ extern "C" int batch_destroy(batch_ctx* b)
 
 extern "C" int batch_step(batch_ctx* b, int nsteps, void* stream)
 {
+    NvtxRange nvtx_range("batch_step");
     if (!b || nsteps < 0 || nsteps % b->k) return set_error(PFSI_ERR_ARG, "batch_step: nsteps must be a multiple of steps_per_graph");
     cudaStream_t s = as_stream(stream);
     for (int done = 0; done < nsteps; done += b->k) {

@@ -1381,6 +1381,7 @@ extern "C" int sg_query_work(int batch, size_t* bytes)
 extern "C" int sg_grad(const void* params, const void* feat, const float* target, int batch, int mode, float* grad,
                        double* loss, void* work, size_t work_bytes, void* stream)
 {
+    NvtxRange nvtx_range("sg_grad");
     if (!params || !feat || !target || !grad || !work || batch < 1 || (mode != PFSI_SG_BF16 && mode != PFSI_SG_FP32))
         return set_error(PFSI_ERR_ARG, "sg_grad: bad argument");
     if (batch % kTile) return set_error(PFSI_ERR_ARG, "sg_grad: batch must be a multiple of 128 (pad the rows)");
@@ -1411,6 +1412,7 @@ extern "C" int sg_work_status(void* work, int batch, int* flag)
 extern "C" int sg_adam(void* params, const float* grad, float* m, float* v, float lr, float beta1, float beta2,
                        float eps, int t, void* stream)
 {
+    NvtxRange nvtx_range("sg_adam");
     if (!params || !grad || !m || !v || t < 1 || !(lr > 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
         !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
         return set_error(PFSI_ERR_ARG, "sg_adam: bad argument");
@@ -1488,6 +1490,7 @@ extern "C" int sg_rows(const sg_ctx* c, int* rows, const int** node)
 extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* frames, float* mags,
                            void* stream)
 {
+    NvtxRange nvtx_range("sg_features");
     if (!c || !params || !X) return set_error(PFSI_ERR_ARG, "sg_features: null argument");
     const Params P = params_of(params);
     cudaStream_t s = as_stream(stream);
@@ -1510,6 +1513,7 @@ extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void*
 extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, const double* X, float* F,
                                   void* stream)
 {
+    NvtxRange nvtx_range("sg_membrane_forces");
     if (!c || !params || !mem || !X || !F) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: null argument");
     if (mem->n != c->d.n_nodes) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: node count differs");
     cudaStream_t s = as_stream(stream);
@@ -1521,6 +1525,7 @@ extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, c
 extern "C" int sg_targets(const sg_ctx* c, const void* params, const float* F, const float* frames,
                           const float* mags, float* target, void* stream)
 {
+    NvtxRange nvtx_range("sg_targets");
     if (!c || !params || !F || !target) return set_error(PFSI_ERR_ARG, "sg_targets: null argument");
     const Params P = params_of(params);
     k_sg_targets<<<(c->d.rows + 127) / 128, 128, 0, as_stream(stream)>>>(
