@@ -141,6 +141,7 @@ __device__ __forceinline__ void row_table(const Box& b, int nx, int ny, int* row
 
 __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
                                                       int M, const int2* __restrict__ chunks,
+                                                      const int* __restrict__ perm,
                                                       float4* __restrict__ g, uint32_t* __restrict__ flags,
                                                       int nx, int ny, int nz)
 {
@@ -149,8 +150,8 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
     __shared__ float wmax[kWarps];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
-    const int m = ch.x + threadIdx.x;
     const bool on = (int)threadIdx.x < ch.y;
+    const int m = on && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (on) {
@@ -244,6 +245,7 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
 
 __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
                                                       const int2* __restrict__ chunks,
+                                                      const int* __restrict__ perm,
                                                       const float4* __restrict__ v,
                                                       uint32_t* __restrict__ flags, int nx, int ny, int nz,
                                                       int advect)
@@ -251,8 +253,8 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
     extern __shared__ float4 tile4[];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
-    const int m = ch.x + threadIdx.x;
     const bool on = (int)threadIdx.x < ch.y;
+    const int m = on && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
     double x = 0.0, y = 0.0, z = 0.0;
     if (on) {
@@ -358,22 +360,22 @@ int ib_prepare()
     return rc;
 }
 
-int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, int n_chunks,
+int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, const int* perm, int n_chunks,
                      cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_spread<<<blocks, kChunk, 3 * kTileCells * sizeof(int), s>>>(X, F, M, chunks, c->g, c->flags, c->p.nx,
+    k_ib_spread<<<blocks, kChunk, 3 * kTileCells * sizeof(int), s>>>(X, F, M, chunks, perm, c->g, c->flags, c->p.nx,
                                                                       c->p.ny, c->p.nz);
     return check_launch("ib_spread");
 }
 
-int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,
+int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm, int n_chunks,
                      cudaStream_t s)
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz,
+    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, perm, velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz,
                                                    advect);
     return check_launch("ib_interp");
 }
@@ -387,7 +389,7 @@ extern "C" int ib_spread(lb_ctx* c, const double* X, const float* F, int M, void
     NvtxRange nvtx_range("ib_spread");
     if (!c || M < 0 || (M > 0 && (!X || !F))) return set_error(PFSI_ERR_ARG, "ib_spread: bad argument");
     if (!aligned(X, 8) || !aligned(F, 4)) return set_error(PFSI_ERR_ARG, "ib_spread: misaligned arrays");
-    return launch_ib_spread(c, X, F, M, nullptr, 0, as_stream(stream));
+    return launch_ib_spread(c, X, F, M, nullptr, nullptr, 0, as_stream(stream));
 }
 
 extern "C" int ib_interp(lb_ctx* c, double* X, float* U, int M, int advect, void* stream)
@@ -395,5 +397,5 @@ extern "C" int ib_interp(lb_ctx* c, double* X, float* U, int M, int advect, void
     NvtxRange nvtx_range("ib_interp");
     if (!c || M < 0 || (M > 0 && (!X || !U))) return set_error(PFSI_ERR_ARG, "ib_interp: bad argument");
     if (!aligned(X, 8) || !aligned(U, 4)) return set_error(PFSI_ERR_ARG, "ib_interp: misaligned arrays");
-    return launch_ib_interp(c, X, U, M, advect, nullptr, 0, as_stream(stream));
+    return launch_ib_interp(c, X, U, M, advect, nullptr, nullptr, 0, as_stream(stream));
 }

@@ -138,7 +138,7 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
 enum Slice {
     S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
-    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_COUNT
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_COUNT
 };
 struct Layout {
     size_t off[S_COUNT];
@@ -151,7 +151,7 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
     const size_t bytes[S_COUNT] = {
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
         4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 24 * Q, 12 * N, 12 * N,
-        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q)};
+        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -588,11 +588,39 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
         plt_rest[4 * q + 3] = V0[q] > 0.0 ? 1.0 / V0[q] : 0.0;
     }
     std::vector<uint8_t> mem_v(is_membrane, is_membrane + n);
-    // IB chunk table: runs of one platelet, at most kIbChunk nodes each
+    // IB chunk table: the nodes of each platelet in Morton order of the rest
+    // shape (10 bits per axis over the platelet's own box), cut into runs of at
+    // most kIbChunk; a chunk then covers a compact patch, and the spreading and
+    // interpolation tiles of its bounding box stay small.
+    std::vector<int> perm(n);
+    {
+        std::vector<double> lo(3 * (size_t)nplt, 1e300), hi(3 * (size_t)nplt, -1e300);
+        for (int v = 0; v < n; ++v)
+            for (int d = 0; d < 3; ++d) {
+                const double x = X0[(size_t)d * n + v];
+                lo[3 * node_plt[v] + d] = std::min(lo[3 * node_plt[v] + d], x);
+                hi[3 * node_plt[v] + d] = std::max(hi[3 * node_plt[v] + d], x);
+            }
+        std::vector<unsigned long long> key(n);
+        for (int v = 0; v < n; ++v) {
+            const int q = node_plt[v];
+            double ext = 0.0;
+            for (int d = 0; d < 3; ++d) ext = std::max(ext, hi[3 * q + d] - lo[3 * q + d]);
+            unsigned long long k = 0;
+            for (int d = 0; d < 3; ++d) {
+                const double t = ext > 0.0 ? (X0[(size_t)d * n + v] - lo[3 * q + d]) / ext : 0.0;
+                const unsigned c = (unsigned)std::min(1023.0, std::max(0.0, t * 1023.0));
+                for (int b = 0; b < 10; ++b) k |= (unsigned long long)((c >> b) & 1u) << (3 * b + d);
+            }
+            key[v] = ((unsigned long long)q << 32) | k;
+        }
+        for (int v = 0; v < n; ++v) perm[v] = v;
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    }
     std::vector<int2> chunks;
     for (int v = 0; v < n;) {
         int e = v + 1;
-        while (e < n && node_plt[e] == node_plt[v] && e - v < kIbChunk) ++e;
+        while (e < n && node_plt[perm[e]] == node_plt[perm[v]] && e - v < kIbChunk) ++e;
         chunks.push_back(make_int2(v, e - v));
         v = e;
     }
@@ -628,6 +656,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_PLT_REST, plt_rest.data(), sizeof(double) * plt_rest.size());
     if (!rc) rc = up(S_PLT_ANCHOR, anchor.data(), sizeof(int) * nplt);
     if (!rc) rc = up(S_CHUNKS, chunks.data(), sizeof(int2) * chunks.size());
+    if (!rc) rc = up(S_PERM, perm.data(), sizeof(int) * perm.size());
     if (rc) return rc;
 
     mem_ctx* c = new mem_ctx();
@@ -657,6 +686,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->plt_rest = reinterpret_cast<const double*>(at(S_PLT_REST));
     c->plt_anchor = reinterpret_cast<const int*>(at(S_PLT_ANCHOR));
     c->chunks = reinterpret_cast<const int2*>(at(S_CHUNKS));
+    c->perm = reinterpret_cast<const int*>(at(S_PERM));
     c->n_chunks = (int)chunks.size();
     c->acc = reinterpret_cast<double*>(at(S_ACC));
     c->coef = reinterpret_cast<float2*>(c->acc + 2 * (size_t)nplt);

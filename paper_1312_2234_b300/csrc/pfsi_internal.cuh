@@ -128,7 +128,8 @@ struct MemCtx {
     const int* node_plt;   // [n]
     const uint8_t* is_mem; // [n]
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
-    const int2* chunks;    // [n_chunks] (first node, count <= kIbChunk), runs of one platelet
+    const int2* chunks;    // [n_chunks] (first entry of perm, count <= kIbChunk), runs of one platelet
+    const int* perm;       // [n] nodes by platelet, in Morton order of the rest shape within each
     int n_chunks;
     int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
     const int* plt_anchor; // [nplt]
@@ -168,13 +169,15 @@ int ib_prepare();
 
 // Launchers used by sim.cu (defined next to their kernels).
 int launch_lb_step(LbCtx* c, cudaStream_t s);
-// chunks: optional device table of (first node, count <= kIbChunk) per block, used
-// by the coupled step so that no block straddles two platelets; null = fixed
-// chunks of kIbChunk consecutive nodes.
-int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, int n_chunks,
-                     cudaStream_t s);
-int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, int n_chunks,
-                     cudaStream_t s);
+// chunks: optional device table of (first entry, count <= kIbChunk) per block,
+// used by the coupled step so that no block straddles two platelets; entries
+// index perm (the nodes of each platelet in a spatially local order) when perm
+// is non-null, else the nodes themselves; null chunks = fixed chunks of
+// kIbChunk consecutive nodes.
+int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, const int* perm,
+                     int n_chunks, cudaStream_t s);
+int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm,
+                     int n_chunks, cudaStream_t s);
 int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s);
 // The global terms only (global area, volume, Morse pairs, wall): what the
 // learned surrogate does not stand for.  Writes F.

@@ -73,13 +73,13 @@ int enqueue_middle(SimCtx* c, cudaStream_t s)
     int rc = PFSI_OK;
     if (c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc && c->br) rc = launch_bridge_forces(c->br, c->X, c->F, c->M, s);
-    if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->n_chunks, s);
+    if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s);
     if (!rc && c->lb_ev[0])
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[0], s, cudaEventRecordExternal), "sim: lb timing event");
     if (!rc) rc = launch_lb_step(c->lb, s);
     if (!rc && c->lb_ev[1])
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
-    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->n_chunks, s);
+    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s);
     return rc;
 }
 
