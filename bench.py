@@ -270,8 +270,9 @@ def run_native(args, rank, ws):
         # the step's result read back every step: the platelets' centroids
         # (the quantity a user follows, e.g. for pause times)
         nplt = int(w["mesh"]["n_plt"])
-        cbuf = torch.empty(8 * nplt, dtype=torch.float64, device=dev)
-        sim.step_track(2, cbuf, torch.empty(2, 3 * nplt, dtype=torch.float64).pin_memory())  # instantiate
+        cbuf = torch.empty(40 * nplt, dtype=torch.float64, device=dev)
+        # instantiate the tracked graphs (both four-step slot groups and the single steps)
+        sim.step_track(10, cbuf, torch.empty(10, 3 * nplt, dtype=torch.float64).pin_memory())
         out = torch.empty(args.steps, 3 * nplt, dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)

@@ -239,8 +239,8 @@ int membrane_forces(mem_ctx* ctx, const double* X, float* F, void* stream);
 /* Centroid of every platelet's nodes (membrane and SCE) at positions X:
  * out_dev (device, 4 * n_plt doubles, 8-byte aligned) receives the
  * centroids in its first 3 * n_plt entries ([platelet][x, y, z]); the rest is
- * scratch.  Enqueues only (FP64 sums; the order of the platelet sums is not
- * fixed, so the last bit may differ between calls). */
+ * not written.  FP64 sums in a fixed order (one block per platelet), so
+ * repeated calls give identical bits.  Enqueues only. */
 int membrane_centroids(mem_ctx* ctx, const double* X, double* out_dev, void* stream);
 
 /* Per-platelet total area and volume of X (FP64 on the device).
@@ -547,12 +547,14 @@ int sim_step(sim_ctx* ctx, int nsteps, void* stream);
 int sim_step_record(sim_ctx* ctx, int nsteps, double* dev_ring, double* host_ring, int ring, void* stream);
 
 /* nsteps coupled steps, following the platelets: after step k the
- * centroids of all platelets (membrane_centroids, computed inside the step's
- * graph) are copied to host_out[k][n_plt][3] (pinned host memory,
+ * centroids of all platelets (membrane_centroids, computed inside the step
+ * graphs) are copied to host_out[k][n_plt][3] (pinned host memory,
  * nsteps * 3 * n_plt doubles) on the context's copy stream, overlapping the
- * next step.  dev_scratch: device, 8 * n_plt doubles (two slots), kept by the
- * context's graphs until another scratch is passed.  Returns after enqueueing;
- * `stream` is ordered after the last copy. */
+ * next steps.  Steps run four per graph where they can (one strided copy per
+ * four steps), one per graph otherwise.  dev_scratch: device, 40 * n_plt
+ * doubles (ten slots of 4 * n_plt), kept by the context's graphs until another
+ * scratch is passed.  Returns after enqueueing; `stream` is ordered after the
+ * last copy. */
 int sim_step_track(sim_ctx* ctx, int nsteps, double* dev_scratch, double* host_out, void* stream);
 
 /* Index of the next step (first_step + steps taken). */

@@ -138,7 +138,7 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
 enum Slice {
     S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
-    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_COUNT
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_PLT_RANGE, S_COUNT
 };
 struct Layout {
     size_t off[S_COUNT];
@@ -151,7 +151,7 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
     const size_t bytes[S_COUNT] = {
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
         4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 24 * Q, 12 * N, 12 * N,
-        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N};
+        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N, 8 * Q};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -624,6 +624,13 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
         chunks.push_back(make_int2(v, e - v));
         v = e;
     }
+    // each platelet's nodes are one run of perm
+    std::vector<int2> plt_range(nplt, make_int2(0, 0));
+    for (int v = 0; v < n; ++v) {
+        int2& r = plt_range[node_plt[perm[v]]];
+        if (r.y == 0) r.x = v;
+        r.y += 1;
+    }
     {
         int runs = 1;
         for (int v = 1; v < n; ++v) runs += node_plt[v] != node_plt[v - 1];
@@ -657,6 +664,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_PLT_ANCHOR, anchor.data(), sizeof(int) * nplt);
     if (!rc) rc = up(S_CHUNKS, chunks.data(), sizeof(int2) * chunks.size());
     if (!rc) rc = up(S_PERM, perm.data(), sizeof(int) * perm.size());
+    if (!rc) rc = up(S_PLT_RANGE, plt_range.data(), sizeof(int2) * plt_range.size());
     if (rc) return rc;
 
     mem_ctx* c = new mem_ctx();
@@ -687,6 +695,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->plt_anchor = reinterpret_cast<const int*>(at(S_PLT_ANCHOR));
     c->chunks = reinterpret_cast<const int2*>(at(S_CHUNKS));
     c->perm = reinterpret_cast<const int*>(at(S_PERM));
+    c->plt_range = reinterpret_cast<const int2*>(at(S_PLT_RANGE));
     c->n_chunks = (int)chunks.size();
     c->acc = reinterpret_cast<double*>(at(S_ACC));
     c->coef = reinterpret_cast<float2*>(c->acc + 2 * (size_t)nplt);
@@ -726,41 +735,33 @@ namespace {
 // Per-platelet sums of the node positions and node counts into acc[4 * nplt]
 // (x, y, z sums then counts); lanes of a warp that share a platelet reduce
 // first.
-__global__ void k_centroid_sums(const double* __restrict__ X, int n, const int* __restrict__ node_plt, int nplt,
-                                double* __restrict__ acc)
+// One block per platelet: the FP64 sum of its nodes in a fixed order
+// (strided partial sums, then a fixed-order block reduction), divided by
+// the count.
+constexpr int kCentroidThreads = 512;
+__global__ void __launch_bounds__(kCentroidThreads)
+    k_centroids(const double* __restrict__ X, int n, const int* __restrict__ perm, const int2* __restrict__ range,
+                double* __restrict__ out)
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const int plt = v < n ? node_plt[v] : -1;
-    double s[3] = {0.0, 0.0, 0.0}, cnt = 0.0;
-    if (plt >= 0) {
-        s[0] = X[v];
-        s[1] = X[n + v];
-        s[2] = X[2 * n + v];
-        cnt = 1.0;
+    const int p = blockIdx.x;
+    const int2 r = range[p];
+    double s[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int k = threadIdx.x; k < r.y; k += kCentroidThreads) {
+        const int v = perm[r.x + k];
+        s[0] += X[v];
+        s[1] += X[n + v];
+        s[2] += X[2 * n + v];
     }
-    const int p0 = __shfl_sync(0xffffffffu, plt, 0);
-    if (__all_sync(0xffffffffu, plt == p0)) {
-        if (p0 < 0) return;
-        for (int o = 16; o > 0; o >>= 1) {
-            for (int d = 0; d < 3; ++d) s[d] += __shfl_down_sync(0xffffffffu, s[d], o);
-            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            for (int d = 0; d < 3; ++d) atomicAdd(&acc[3 * p0 + d], s[d]);
-            atomicAdd(&acc[3 * nplt + p0], cnt);
-        }
-    } else if (plt >= 0) {
-        for (int d = 0; d < 3; ++d) atomicAdd(&acc[3 * plt + d], s[d]);
-        atomicAdd(&acc[3 * nplt + plt], cnt);
+    __shared__ double red[3][kCentroidThreads];
+    for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = s[d];
+    __syncthreads();
+    for (int h = kCentroidThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int d = 0; d < 3; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + h];
+        __syncthreads();
     }
-}
-
-__global__ void k_centroid_finish(double* __restrict__ acc, int nplt)
-{
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nplt) return;
-    const double c = acc[3 * nplt + p];
-    for (int d = 0; d < 3; ++d) acc[3 * p + d] = c > 0.0 ? acc[3 * p + d] / c : 0.0;
+    if (threadIdx.x < 3) out[3 * p + threadIdx.x] = r.y > 0 ? red[threadIdx.x][0] / (double)r.y : 0.0;
 }
 
 }  // namespace
@@ -772,13 +773,9 @@ extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, 
     if (!c || !X || !out_dev) return set_error(PFSI_ERR_ARG, "membrane_centroids: null argument");
     if (!aligned(out_dev, 8)) return set_error(PFSI_ERR_ARG, "membrane_centroids: misaligned output");
     cudaStream_t s = as_stream(stream);
-    int rc = check_cuda(cudaMemsetAsync(out_dev, 0, 4 * sizeof(double) * c->nplt, s), "membrane_centroids: clear");
-    if (rc) return rc;
-    k_centroid_sums<<<(c->n + 255) / 256, 256, 0, s>>>(X, c->n, c->node_plt, c->nplt, out_dev);
-    rc = check_launch("membrane_centroids");
-    if (rc) return rc;
-    k_centroid_finish<<<(c->nplt + 127) / 128, 128, 0, s>>>(out_dev, c->nplt);
-    return check_launch("membrane_centroids: finish");
+    if (c->nplt == 0) return PFSI_OK;
+    k_centroids<<<c->nplt, kCentroidThreads, 0, s>>>(X, c->n, c->perm, c->plt_range, out_dev);
+    return check_launch("membrane_centroids");
 }
 
 extern "C" int membrane_measure(mem_ctx* c, const double* X, double* out_host, void* stream)

@@ -130,6 +130,7 @@ struct MemCtx {
     const double* plt_rest;// [4*nplt] S0, V0, 1/S0, 1/V0
     const int2* chunks;    // [n_chunks] (first entry of perm, count <= kIbChunk), runs of one platelet
     const int* perm;       // [n] nodes by platelet, in Morton order of the rest shape within each
+    const int2* plt_range; // [nplt] (first entry of perm, count) of each platelet's nodes
     int n_chunks;
     int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
     const int* plt_anchor; // [nplt]

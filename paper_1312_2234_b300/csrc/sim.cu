@@ -44,6 +44,9 @@ struct SimCtx {
     // slot `parity` of trk_scratch
     double* trk_scratch;
     cudaGraphExec_t trk_exec[2];
+    // sim_step_track: kMulti overlapped steps with their centroids, per
+    // lattice parity and slot group (the groups alternate between launches)
+    cudaGraphExec_t trk_multi[2][2];
 };
 
 namespace {
@@ -105,19 +108,26 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
 // membrane pass (reads X, writes only F and the membrane scratch) runs on
 // `s`; step k + 1's bond forces wait for it.  Same operations on the same
 // data as n single steps.
-int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n)
+int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n, double* slots = nullptr)
 {
+    // slots (tracked graphs): after step k the platelet centroids go to
+    // slots + 4 n_plt k; they read X only, so they run on the side branch
+    // with the adhesion update (the last step's on the main stream)
+    const size_t slot = 4 * (size_t)c->mem->nplt;
     int rc = enqueue_front(c, s);
     if (!rc) rc = enqueue_middle(c, s);
     for (int k = 1; k < n && !rc; ++k) {
         rc = check_cuda(cudaEventRecord(c->fork, s), "sim: fork");
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->side, c->fork, 0), "sim: fork");
+        if (!rc && slots)
+            rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (k - 1) * slot, c->side);
         if (!rc) rc = enqueue_adhesion(c, c->side);
         if (!rc) rc = check_cuda(cudaEventRecord(c->join, c->side), "sim: join");
         if (!rc) rc = enqueue_front(c, s);
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(s, c->join, 0), "sim: join");
         if (!rc) rc = enqueue_middle(c, s);
     }
+    if (!rc && slots) rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (n - 1) * slot, s);
     if (!rc) rc = enqueue_adhesion(c, s);
     return rc;
 }
@@ -143,9 +153,13 @@ int capture(SimCtx* c, int parity, int track = 0)
         c->lb->cur = saved;
         return rc;
     }
-    const int rc_enq = track == 1   ? enqueue_track(c, c->cap, parity)
-                       : track == 2 ? enqueue_overlapped(c, c->cap, kMulti)
-                                    : enqueue_step(c, c->cap);
+    const int group = track - 3;   // tracked kMulti-step graphs: track = 3 + slot group
+    const int rc_enq =
+        track == 1   ? enqueue_track(c, c->cap, parity)
+        : track == 2 ? enqueue_overlapped(c, c->cap, kMulti)
+        : track >= 3 ? enqueue_overlapped(c, c->cap, kMulti,
+                                          c->trk_scratch + (size_t)(2 + group * kMulti) * 4 * c->mem->nplt)
+                     : enqueue_step(c, c->cap);
     cudaGraph_t graph = nullptr;
     rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
     c->lb->cur = saved;
@@ -154,7 +168,10 @@ int capture(SimCtx* c, int parity, int track = 0)
         return rc_enq;
     }
     if (rc) return rc;
-    cudaGraphExec_t* dst = track == 1 ? &c->trk_exec[parity] : track == 2 ? &c->multi[parity] : &c->exec[parity];
+    cudaGraphExec_t* dst = track == 1   ? &c->trk_exec[parity]
+                           : track == 2 ? &c->multi[parity]
+                           : track >= 3 ? &c->trk_multi[parity][group]
+                                        : &c->exec[parity];
     rc = check_cuda(cudaGraphInstantiate(dst, graph, 0), "sim: instantiate");
     cudaGraphDestroy(graph);
     return rc;
@@ -169,6 +186,10 @@ void drop_graphs(SimCtx* c)
         c->trk_exec[k] = nullptr;
         if (c->multi[k]) cudaGraphExecDestroy(c->multi[k]);
         c->multi[k] = nullptr;
+        for (int g = 0; g < 2; ++g) {
+            if (c->trk_multi[k][g]) cudaGraphExecDestroy(c->trk_multi[k][g]);
+            c->trk_multi[k][g] = nullptr;
+        }
     }
 }
 
@@ -196,6 +217,7 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->step = first_step;
     c->exec[0] = c->exec[1] = nullptr;
     c->multi[0] = c->multi[1] = nullptr;
+    c->trk_multi[0][0] = c->trk_multi[0][1] = c->trk_multi[1][0] = c->trk_multi[1][1] = nullptr;
     c->side = nullptr;
     c->fork = c->join = nullptr;
     c->trk_exec[0] = c->trk_exec[1] = nullptr;
@@ -320,11 +342,15 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
         for (int k = 0; k < 2; ++k) {
             if (c->trk_exec[k]) cudaGraphExecDestroy(c->trk_exec[k]);
             c->trk_exec[k] = nullptr;
+            for (int g = 0; g < 2; ++g) {
+                if (c->trk_multi[k][g]) cudaGraphExecDestroy(c->trk_multi[k][g]);
+                c->trk_multi[k][g] = nullptr;
+            }
         }
         c->trk_scratch = dev_scratch;
     }
     if (!c->rec) rc = check_cuda(cudaStreamCreateWithFlags(&c->rec, cudaStreamNonBlocking), "sim_step_track: stream");
-    while (!rc && c->rec_ready.size() < 2) {
+    while (!rc && c->rec_ready.size() < 4) {
         cudaEvent_t a = nullptr, b = nullptr;
         rc = check_cuda(cudaEventCreateWithFlags(&a, cudaEventDisableTiming), "sim_step_track: event");
         if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&b, cudaEventDisableTiming), "sim_step_track: event");
@@ -335,27 +361,53 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     }
     const int nplt = c->mem->nplt;
     const size_t bytes = (size_t)3 * nplt * sizeof(double);
-    for (int k = 0; k < nsteps && !rc; ++k) {
+    const size_t slot = (size_t)4 * nplt;
+    // events 0, 1: single-step slots 0, 1; events 2, 3: slot groups 0, 1
+    bool used[4] = {false, false, false, false};
+    int k = 0, group = 0;
+    while (!rc && !c->lb_ev[0] && nsteps - k >= kMulti) {
+        const int p = c->lb->cur;   // unchanged by kMulti (even) steps
+        if (!c->trk_multi[p][group]) rc = capture(c, p, 3 + group);
+        cudaEvent_t ready = c->rec_ready[2 + group], freed = c->rec_freed[2 + group];
+        if (!rc && used[2 + group]) rc = check_cuda(cudaStreamWaitEvent(s, freed, 0), "sim_step_track: wait");
+        if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_multi[p][group], s), "sim_step_track: graph launch");
+        if (!rc) rc = check_cuda(cudaEventRecord(ready, s), "sim_step_track: record");
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->rec, ready, 0), "sim_step_track: wait");
+        // the kMulti steps' centroids: strided slots -> consecutive host rows
+        if (!rc)
+            rc = check_cuda(cudaMemcpy2DAsync(host_out + (size_t)k * 3 * nplt, bytes,
+                                              dev_scratch + (2 + (size_t)group * kMulti) * slot, slot * sizeof(double),
+                                              bytes, kMulti, cudaMemcpyDeviceToHost, c->rec),
+                            "sim_step_track: copy");
+        if (!rc) rc = check_cuda(cudaEventRecord(freed, c->rec), "sim_step_track: record");
+        used[2 + group] = true;
+        c->step += kMulti;
+        k += kMulti;
+        group ^= 1;
+    }
+    for (; k < nsteps && !rc; ++k) {
         const int p = c->lb->cur;   // the step's graph writes slot p of the scratch
         if (!c->trk_exec[p]) rc = capture(c, p, 1);
-        if (!rc && k >= 2) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[p], 0), "sim_step_track: wait");
+        if (!rc && used[p]) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[p], 0), "sim_step_track: wait");
         if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_exec[p], s), "sim_step_track: graph launch");
         if (!rc) rc = check_cuda(cudaEventRecord(c->rec_ready[p], s), "sim_step_track: record");
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->rec, c->rec_ready[p], 0), "sim_step_track: wait");
         if (!rc)
-            rc = check_cuda(cudaMemcpyAsync(host_out + (size_t)k * 3 * nplt, dev_scratch + (size_t)p * 4 * nplt, bytes,
+            rc = check_cuda(cudaMemcpyAsync(host_out + (size_t)k * 3 * nplt, dev_scratch + (size_t)p * slot, bytes,
                                             cudaMemcpyDeviceToHost, c->rec),
                             "sim_step_track: copy");
         if (!rc) rc = check_cuda(cudaEventRecord(c->rec_freed[p], c->rec), "sim_step_track: record");
+        used[p] = true;
         if (!rc) {
             c->lb->cur ^= 1;
             c->step += 1;
         }
     }
-    for (int b = 0; b < 2 && b < nsteps && !rc; ++b)
-        rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_track: join");
+    for (int b = 0; b < 4 && !rc; ++b)
+        if (used[b]) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[b], 0), "sim_step_track: join");
     return rc;
 }
+
 
 namespace pfsi {
 namespace {
