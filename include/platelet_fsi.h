@@ -45,6 +45,7 @@ extern "C" {
 #define PFSI_ERR_CUDA (-2)     /* a CUDA runtime call or kernel launch failed */
 #define PFSI_ERR_CAPACITY (-6) /* a device-side list overflowed (see bonds_status) */
 #define PFSI_ERR_UNSTABLE (-7) /* lb_check / sim_check found a non-physical state */
+#define PFSI_ERR_TIMEOUT (-8)  /* a bounded device-side wait gave up (see pfsi_wait_selftest) */
 
 /* Copies the calling thread's last error message into buf (NUL-terminated,
  * truncated to len).  Returns the length of the full message. */
@@ -517,6 +518,15 @@ int sg_targets(const sg_ctx* ctx, const void* params, const float* F, const floa
                float* target, void* stream);
 /* Device error flag of the context's tensor-core kernels.  Synchronises. */
 int sg_status(const sg_ctx* ctx, int* flag);
+
+/* Diagnostic of the bounded device waits (no paper counterpart): one thread
+ * waits, with at most `limit` polls, for an mbarrier phase that nothing
+ * completes, using the same bounded wait the tensor-core kernels use for
+ * their MMA completion (whose timeouts they report through sg_status /
+ * sg_work_status).  Nothing asynchronous is in flight, so giving up is safe.
+ * dev_word: caller's device int.  Returns PFSI_ERR_TIMEOUT when the wait gave
+ * up (the expected outcome), PFSI_OK if the phase completed.  Synchronises. */
+int pfsi_wait_selftest(int limit, int* dev_word, void* stream);
 
 /* ===================================================================== *
  * Coupled step (Fig. 1)

@@ -317,10 +317,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Bounded wait for the completion of the phase with the given parity: false
+// after `limit` polls (the callers then record an error and stop).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit = 1 << 22)
 {
-    for (int it = 0; it < (1 << 22); ++it)
+    for (int it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -1537,4 +1538,33 @@ extern "C" int sg_status(const sg_ctx* c, int* flag)
 {
     if (!c || !flag) return set_error(PFSI_ERR_ARG, "sg_status: null argument");
     return check_cuda(cudaMemcpy(flag, c->err, sizeof(int), cudaMemcpyDeviceToHost), "sg_status");
+}
+
+namespace pfsi {
+namespace {
+// One thread waits, with `limit` polls, for the first phase of an mbarrier
+// that expects one arrival nobody makes; out[0] = 1 if the phase completed.
+__global__ void k_wait_selftest(int limit, int* out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+        out[0] = mbar_wait(&bar, 0u, limit) ? 1 : 0;
+    }
+}
+}  // namespace
+}  // namespace pfsi
+
+extern "C" int pfsi_wait_selftest(int limit, int* dev_word, void* stream)
+{
+    if (limit < 1 || !dev_word) return set_error(PFSI_ERR_ARG, "pfsi_wait_selftest: bad argument");
+    cudaStream_t s = as_stream(stream);
+    k_wait_selftest<<<1, 32, 0, s>>>(limit, dev_word);
+    int rc = check_launch("pfsi_wait_selftest");
+    int h = -1;
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(&h, dev_word, sizeof(int), cudaMemcpyDeviceToHost, s), "pfsi_wait_selftest");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "pfsi_wait_selftest");
+    if (rc) return rc;
+    return h == 1 ? PFSI_OK : set_error(PFSI_ERR_TIMEOUT, "pfsi_wait_selftest: the wait gave up after the limit");
 }

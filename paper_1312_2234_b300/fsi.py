@@ -107,6 +107,7 @@ _SIGS = {
     "bridges_status": [P, ctypes.POINTER(c_longlong)],
     "bridges_partner": [P, ctypes.POINTER(P)],
     "sim_set_bridges": [P, P],
+    "pfsi_wait_selftest": [c_int, P, P],
     "fem_query_workspace": [c_int, c_int, ctypes.POINTER(c_size_t)],
     "fem_create": [c_int, c_int, P, P, c_size_t, ctypes.POINTER(P)],
     "fem_destroy": [P],
@@ -170,6 +171,18 @@ def _call(name, *args):
 
 
 PFSI_ERR_UNSTABLE = -7
+PFSI_ERR_TIMEOUT = -8
+
+
+def wait_selftest(limit, stream=None):
+    """Bounded device wait on an mbarrier phase nothing completes, with at
+    most `limit` polls: True when it gave up (PFSI_ERR_TIMEOUT), False if the
+    phase completed."""
+    word = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = lib().pfsi_wait_selftest(int(limit), _ptr(word), _stream(stream))
+    if rc not in (0, PFSI_ERR_TIMEOUT):
+        _ok(rc, "pfsi_wait_selftest")
+    return rc == PFSI_ERR_TIMEOUT
 
 
 def _check(name, h, u_max, scratch, n, stream=None):

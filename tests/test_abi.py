@@ -180,3 +180,9 @@ def test_product_path_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(fsi, "LIB_PATH", "/nonexistent/libplatelet_fsi.so")
     with pytest.raises(RuntimeError, match="not built"):
         fsi.lib()
+
+
+def test_wait_selftest_rejects_bad_arguments():
+    L = fsi.lib()
+    assert L.pfsi_wait_selftest(0, None, None) == -1
+    assert L.pfsi_wait_selftest(5, None, None) == -1

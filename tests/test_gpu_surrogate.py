@@ -320,3 +320,14 @@ def test_features_keep_their_accuracy_at_small_deformations(amp):
     got = feat.cpu().numpy()[:sg.rows]
     assert np.max(np.abs(got[:, :18] - f_or[:, :18])) < 1e-3
     assert np.max(np.abs(mags.cpu().numpy()[:sg.rows] / mag_or - 1)) < 1e-3
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """The bounded mbarrier wait the tensor-core kernels use gives up after
+    its limit on a phase nothing completes (no asynchronous copy or MMA is in
+    flight) and reports PFSI_ERR_TIMEOUT; the context then runs the
+    tensor-core gradients as before."""
+    assert fsi.wait_selftest(1000)
+    assert fsi.wait_selftest(1)
+    torch.cuda.synchronize()
+    test_gradients_bf16_tensor_cores(128)
