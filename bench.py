@@ -619,6 +619,20 @@ def run_full(args, dev, stream, sg_params):
     return out
 
 
+def run_full_only(args):
+    """The 500-platelet full-scale step alone (profiling aid): the plain FP32
+    form and the BF16 + surrogate form with untrained surrogate weights
+    (the same kernels and launch shapes as trained ones).  Prints one JSON
+    line."""
+    import torch
+    from paper_1312_2234_b300 import fsi, surrogate
+    dev = torch.device("cuda", 0)
+    params = fsi.SurrogateParams(device=dev)
+    params.set(surrogate.init_params(np.random.default_rng(0)))
+    print(json.dumps({"kernel": "full-scale coupled step", **run_full(args, dev, torch.cuda.current_stream(), params)}),
+          flush=True)
+
+
 def run_lb_only(args):
     """The lattice kernel alone on a grid of the caller's size (profiling aid:
     a grid larger than L2 makes its DRAM figures meaningful).  Prints one
@@ -742,7 +756,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
-    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges"],
+    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges", "full"],
                     help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
@@ -763,6 +777,9 @@ def main():
         return
     if args.kernel == "bridges":
         run_bridges_only(args)
+        return
+    if args.kernel == "full":
+        run_full_only(args)
         return
     rank, ws = dist_setup()
     if args.impl == "reference":

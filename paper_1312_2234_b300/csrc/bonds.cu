@@ -38,6 +38,7 @@ __device__ __forceinline__ void bond_vector(const bond_params& p, const SitePos&
 
 __global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __restrict__ F, int M)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int lig = c.bound[s];
@@ -54,6 +55,7 @@ __global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __
 __global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
                                const unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int lig = c.bound[s];
@@ -75,6 +77,7 @@ __global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, u
 __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
                                const unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int b = c.bound[s];
@@ -132,6 +135,7 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
 
 __global__ void k_bond_resolve(BondCtx c, unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (step_dev && l == 0) *step_dev += 1ull;
     if (l >= c.L) return;
@@ -175,23 +179,25 @@ size_t ws_bytes_for(int L)
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s)
 {
     if (c->R == 0) return PFSI_OK;
-    k_bond_forces<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, F, M);
-    return check_launch("bonds_forces");
+    return check_cuda(launch_pdl(k_bond_forces, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, F, M),
+                      "bonds_forces");
 }
 
 int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                       unsigned long long* step_dev, cudaStream_t s)
 {
     if (c->R > 0) {
-        k_bond_rupture<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, M, step_host, step_dev);
-        int rc = check_launch("bonds_step: rupture");
+        int rc = check_cuda(launch_pdl(k_bond_rupture, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, M, step_host,
+                                       step_dev),
+                            "bonds_step: rupture");
         if (rc) return rc;
-        k_bond_propose<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, X, M, step_host, step_dev);
-        rc = check_launch("bonds_step: propose");
+        rc = check_cuda(launch_pdl(k_bond_propose, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, M, step_host,
+                                   step_dev),
+                        "bonds_step: propose");
         if (rc) return rc;
     }
-    k_bond_resolve<<<blocks_for(c->L > 0 ? c->L : 1, 256), 256, 0, s>>>(*c, step_dev);
-    return check_launch("bonds_step: resolve");
+    return check_cuda(launch_pdl(k_bond_resolve, dim3(blocks_for(c->L > 0 ? c->L : 1, 256)), dim3(256), 0, s, *c, step_dev),
+                      "bonds_step: resolve");
 }
 
 }  // namespace pfsi

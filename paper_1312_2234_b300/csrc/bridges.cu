@@ -109,6 +109,7 @@ __device__ __forceinline__ SitePos site_of(const BridgeCtx& c, const double* __r
 
 __global__ void k_br_forces(BridgeCtx c, const double* __restrict__ X, float* __restrict__ F, int M)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.R) return;
     const int j = c.partner[i];
@@ -139,6 +140,7 @@ __device__ __forceinline__ double from_order_key(unsigned long long k)
 // FP32 bounds rounded outward.
 __global__ void __launch_bounds__(kBrThreads) k_br_boxes(BridgeCtx c, const double* __restrict__ X, int M)
 {
+    pdl_wait();
     const int p = blockIdx.x;
     const int2 r = c.plt_nodes[p];
     unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0ull, 0ull, 0ull};
@@ -207,6 +209,7 @@ __device__ __forceinline__ bool boxes_near(const BridgeCtx& c, float4 la, float4
 // their boxes come within d_capture.
 __global__ void k_br_neighbors(BridgeCtx c)
 {
+    pdl_wait();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)c.nplt * c.nplt) return;
     const int p = (int)(t / c.nplt), q = (int)(t - (long long)p * c.nplt);
@@ -243,6 +246,7 @@ __device__ __forceinline__ void cell_of(const BridgeCtx& c, const SitePos& r, in
 __global__ void k_br_active(BridgeCtx c, const double* __restrict__ X, int M, uint64_t step_host,
                             const unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int ps = c.partner[s];
@@ -295,6 +299,7 @@ __global__ void k_br_active(BridgeCtx c, const double* __restrict__ X, int M, ui
 constexpr int kScanThreads = 1024;
 __global__ void __launch_bounds__(kScanThreads) k_br_scan(BridgeCtx c)
 {
+    pdl_wait();
     __shared__ int part[kScanThreads];
     const int per = c.B / kScanThreads;   // power of two
     const int t = threadIdx.x;
@@ -347,6 +352,7 @@ __device__ __forceinline__ float4 prefilter_pos(const BridgeCtx& c, double x, do
 
 __global__ void k_br_scatter(BridgeCtx c)
 {
+    pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R || !c.act[s]) return;
     const int k = c.start[c.key[s]] + c.slot[s];
@@ -363,6 +369,7 @@ constexpr int kChooseThreads = 256;
 __global__ void __launch_bounds__(kChooseThreads, 4)
     k_br_choose(BridgeCtx c, uint64_t step_host, const unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -492,6 +499,7 @@ __global__ void __launch_bounds__(kChooseThreads, 4)
 
 __global__ void k_br_match(BridgeCtx c, unsigned long long* __restrict__ step_dev)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (step_dev && i == 0) *step_dev += 1ull;
     if (i >= c.R || !c.act[i]) return;
@@ -510,8 +518,7 @@ int blocks(int n) { return (n + kBrThreads - 1) / kBrThreads; }
 int launch_bridge_forces(BridgeCtx* c, const double* X, float* F, int M, cudaStream_t s)
 {
     if (c->R == 0) return PFSI_OK;
-    k_br_forces<<<blocks(c->R), kBrThreads, 0, s>>>(*c, X, F, M);
-    return check_launch("bridges_forces");
+    return check_cuda(launch_pdl(k_br_forces, dim3(blocks(c->R)), dim3(kBrThreads), 0, s, *c, X, F, M), "bridges_forces");
 }
 
 int launch_bridges_step(BridgeCtx* c, const double* X, int M, uint64_t step_host, unsigned long long* step_dev,
@@ -529,22 +536,31 @@ int launch_bridges_step(BridgeCtx* c, const double* X, int M, uint64_t step_host
     int rc = check_cuda(cudaMemsetAsync(c->count, 0, sizeof(int) * ((size_t)c->B + c->nplt), s),
                         "bridges_step: clear counts");
     if (rc) return rc;
-    k_br_boxes<<<c->nplt, kBrThreads, 0, s>>>(v, X, M);
-    {
+    rc = check_cuda(launch_pdl(k_br_boxes, dim3(c->nplt), dim3(kBrThreads), 0, s, v, X, M), "bridges_step: boxes");
+    if (!rc) {
         const long long pairs = (long long)c->nplt * c->nplt;
-        k_br_neighbors<<<(unsigned)((pairs + kBrThreads - 1) / kBrThreads), kBrThreads, 0, s>>>(v);
+        rc = check_cuda(launch_pdl(k_br_neighbors, dim3((unsigned)((pairs + kBrThreads - 1) / kBrThreads)), dim3(kBrThreads),
+                                   0, s, v),
+                        "bridges_step: neighbours");
     }
-    k_br_active<<<blocks(c->R), kBrThreads, 0, s>>>(v, X, M, step_host, step_dev);
-    k_br_scan<<<1, kScanThreads, 0, s>>>(v);
-    k_br_scatter<<<blocks(c->R), kBrThreads, 0, s>>>(v);
-    {
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_br_active, dim3(blocks(c->R)), dim3(kBrThreads), 0, s, v, X, M, step_host, step_dev),
+                        "bridges_step: active sites");
+    if (!rc) rc = check_cuda(launch_pdl(k_br_scan, dim3(1), dim3(kScanThreads), 0, s, v), "bridges_step: scan");
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_br_scatter, dim3(blocks(c->R)), dim3(kBrThreads), 0, s, v), "bridges_step: scatter");
+    if (!rc) {
         // one warp per active site, grid-stride over the sorted active list
         const int warps_per_block = kChooseThreads / 32;
         int g = (c->R + warps_per_block - 1) / warps_per_block;
         g = g < 1 ? 1 : (g > 148 * 16 ? 148 * 16 : g);
-        k_br_choose<<<g, kChooseThreads, 0, s>>>(v, step_host, step_dev);
+        rc = check_cuda(launch_pdl(k_br_choose, dim3(g), dim3(kChooseThreads), 0, s, v, step_host, step_dev),
+                        "bridges_step: choose");
     }
-    k_br_match<<<blocks(c->R), kBrThreads, 0, s>>>(v, step_dev);
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_br_match, dim3(blocks(c->R)), dim3(kBrThreads), 0, s, v, step_dev),
+                        "bridges_step: match");
+    if (rc) return rc;
     return check_launch("bridges_step");
 }
 

@@ -103,6 +103,7 @@ __device__ __forceinline__ void tangential_inverse(float3 a_xi, float3 a_eta, fl
 // x = hi + lo, hi the FP32 rounding of x (one coordinate per thread).
 __global__ void k_fem_split(int n, const double* __restrict__ X, float* __restrict__ xh, float* __restrict__ xl)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * n) return;
     const double x = X[i];
@@ -118,6 +119,7 @@ template <int Pass>
 __global__ void __launch_bounds__(kFemThreads)
     k_fem_elem(FemCtx c, const float* __restrict__ xh, const float* __restrict__ xl)
 {
+    pdl_wait();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= c.ne) return;
     const int n = c.n;
@@ -227,6 +229,7 @@ template <int Pass>
 __global__ void __launch_bounds__(kFemThreads)
     k_fem_node(FemCtx c, float k0, float* __restrict__ F, int accumulate, float* __restrict__ fields)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.n) return;
     const int b = __ldg(c.off + i), en = __ldg(c.off + i + 1);
@@ -319,19 +322,34 @@ int launch_fem_forces(FemCtx* c, float k0, const double* X, const float* xh, con
     const int ge = (c->ne + kFemThreads - 1) / kFemThreads;
     const int gn = (c->n + kFemThreads - 1) / kFemThreads;
     const FemCtx v = *c;
+    int rc = PFSI_OK;
     if (!xh || !xl) {
-        k_fem_split<<<(3 * c->n + kFemThreads - 1) / kFemThreads, kFemThreads, 0, s>>>(c->n, X, c->xh, c->xl);
+        rc = check_cuda(launch_pdl(k_fem_split, dim3((3 * c->n + kFemThreads - 1) / kFemThreads), dim3(kFemThreads), 0, s,
+                                   c->n, X, c->xh, c->xl),
+                        "fem bending: split");
         xh = c->xh;
         xl = c->xl;
     }
-    k_fem_elem<0><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
-    k_fem_node<0><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<1><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
-    k_fem_node<1><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<2><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
-    k_fem_node<2><<<gn, kFemThreads, 0, s>>>(v, k0, nullptr, 0, nullptr);
-    k_fem_elem<3><<<ge, kFemThreads, 0, s>>>(v, xh, xl);
-    k_fem_node<3><<<gn, kFemThreads, 0, s>>>(v, k0, F, accumulate, fields);
+    if (!rc) rc = check_cuda(launch_pdl(k_fem_elem<0>, dim3(ge), dim3(kFemThreads), 0, s, v, xh, xl), "fem bending");
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_fem_node<0>, dim3(gn), dim3(kFemThreads), 0, s, v, k0, (float*)nullptr, 0,
+                                   (float*)nullptr),
+                        "fem bending");
+    if (!rc) rc = check_cuda(launch_pdl(k_fem_elem<1>, dim3(ge), dim3(kFemThreads), 0, s, v, xh, xl), "fem bending");
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_fem_node<1>, dim3(gn), dim3(kFemThreads), 0, s, v, k0, (float*)nullptr, 0,
+                                   (float*)nullptr),
+                        "fem bending");
+    if (!rc) rc = check_cuda(launch_pdl(k_fem_elem<2>, dim3(ge), dim3(kFemThreads), 0, s, v, xh, xl), "fem bending");
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_fem_node<2>, dim3(gn), dim3(kFemThreads), 0, s, v, k0, (float*)nullptr, 0,
+                                   (float*)nullptr),
+                        "fem bending");
+    if (!rc) rc = check_cuda(launch_pdl(k_fem_elem<3>, dim3(ge), dim3(kFemThreads), 0, s, v, xh, xl), "fem bending");
+    if (!rc)
+        rc = check_cuda(launch_pdl(k_fem_node<3>, dim3(gn), dim3(kFemThreads), 0, s, v, k0, F, accumulate, fields),
+                        "fem bending");
+    if (rc) return rc;
     return check_launch("fem bending");
 }
 

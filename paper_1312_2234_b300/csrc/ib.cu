@@ -13,7 +13,7 @@
 // nodes, one thread per node (consecutive nodes of a platelet mesh lie close
 // together; the coupled step passes chunks that never straddle two
 // platelets, the public calls use fixed chunks of 128).  When the bounding
-// box of the chunk's supports fits the shared tile (4096 cells, no wider than
+// box of the chunk's supports fits the shared tile (1536 cells, no wider than
 // the grid):
 //   spreading  accumulates F_m * w in the tile in 32-bit fixed point (shared
 //              integer atomics run several times faster than shared float
@@ -43,7 +43,11 @@ namespace {
 
 constexpr int kChunk = kIbChunk;            // nodes (= threads) per block
 constexpr int kWarps = kChunk / 32;
-constexpr int kTileCells = 4096;            // 3 int planes (spread) or float4 cells (interp)
+// 3 int planes (spread) or float4 cells (interp).  Chunks in Morton order of
+// the platelet's rest shape have boxes of ~340 cells on average (largest
+// ~1200 on the 500-platelet channel); 1536 cells (18 KB spreading, 24 KB
+// interpolation) let 8-9 blocks share an SM, where a 4096-cell tile held 3.
+constexpr int kTileCells = 1536;
 constexpr int kMaxRows = kTileCells / 4;    // a box is at least 4 cells wide
 constexpr size_t kTileBytes = kTileCells * sizeof(float4);
 
@@ -145,6 +149,7 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
                                                       float4* __restrict__ g, uint32_t* __restrict__ flags,
                                                       int nx, int ny, int nz)
 {
+    pdl_wait();
     extern __shared__ int itile[];
     __shared__ float swy[4][kChunk], swz[4][kChunk];
     __shared__ float wmax[kWarps];
@@ -250,6 +255,7 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
                                                       uint32_t* __restrict__ flags, int nx, int ny, int nz,
                                                       int advect)
 {
+    pdl_wait();
     extern __shared__ float4 tile4[];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
@@ -365,9 +371,9 @@ int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_spread<<<blocks, kChunk, 3 * kTileCells * sizeof(int), s>>>(X, F, M, chunks, perm, c->g, c->flags, c->p.nx,
-                                                                      c->p.ny, c->p.nz);
-    return check_launch("ib_spread");
+    return check_cuda(launch_pdl(k_ib_spread, dim3(blocks), dim3(kChunk), 3 * kTileCells * sizeof(int), s, X, F, M, chunks,
+                                 perm, c->g, c->flags, c->p.nx, c->p.ny, c->p.nz),
+                      "ib_spread");
 }
 
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm, int n_chunks,
@@ -375,9 +381,9 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
-    k_ib_interp<<<blocks, kChunk, kTileBytes, s>>>(X, U, M, chunks, perm, velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz,
-                                                   advect);
-    return check_launch("ib_interp");
+    return check_cuda(launch_pdl(k_ib_interp, dim3(blocks), dim3(kChunk), kTileBytes, s, X, U, M, chunks, perm,
+                                 (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz, advect),
+                      "ib_interp");
 }
 
 }  // namespace pfsi

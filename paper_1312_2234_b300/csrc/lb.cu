@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     float4* __restrict__ vout, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
     float omega, float guo, float3 body, float3 utop, int onsite)
 {
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
     float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
     int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
 {
+    pdl_wait();
     __shared__ Ring<T> ring;
     const int tx = threadIdx.x % T::TX, ty = threadIdx.x / T::TX;
     const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
@@ -541,7 +543,7 @@ using NeqT = typename Neq<kMode>::T;
 constexpr int kFp32Block[PFSI_LB_SHAPES] = {kRowBlock, 32, 64, 256};
 
 template <int kMode, class T>
-void launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+cudaError_t launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
 {
     const lb_params& p = c->p;
     const int a = c->cur, b = c->cur ^ 1;
@@ -552,19 +554,20 @@ void launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body,
     const long long want = 148LL * 8 * 256 / T::Threads;
     const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
     const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
-    k_lb_step_mixed<kMode, T><<<grid, T::Threads, 0, s>>>((const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b], c->m[a],
-                                                          c->m[b], c->g, c->flags, p.nx, p.ny, p.nz, kz, omega, guo,
-                                                          body, utop, inv_scale, p.walls);
+    return launch_pdl(k_lb_step_mixed<kMode, T>, grid, dim3(T::Threads), 0, s, (const uint16_t*)c->f[a],
+                      (NeqT<kMode>*)c->f[b], (const float4*)c->m[a], c->m[b], c->g, (const uint32_t*)c->flags, p.nx, p.ny,
+                      p.nz, kz, omega, guo, body, utop, inv_scale, p.walls);
 }
 
 template <int kMode>
-void launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+cudaError_t launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop,
+                               float inv_scale)
 {
     switch (c->shape) {
-    case 1: launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale); break;
-    case 2: launch_mixed<kMode, Tile<64, 4>>(c, s, omega, guo, body, utop, inv_scale); break;
-    case 3: launch_mixed<kMode, Tile<16, 8>>(c, s, omega, guo, body, utop, inv_scale); break;
-    default: launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
+    case 1: return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
+    case 2: return launch_mixed<kMode, Tile<64, 4>>(c, s, omega, guo, body, utop, inv_scale);
+    case 3: return launch_mixed<kMode, Tile<16, 8>>(c, s, omega, guo, body, utop, inv_scale);
+    default: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
     }
 }
 
@@ -578,15 +581,27 @@ int launch_lb_step(LbCtx* c, cudaStream_t s)
     const float3 body = make_float3(p.body[0], p.body[1], p.body[2]);
     const float3 utop = make_float3(p.u_top[0], p.u_top[1], p.u_top[2]);
     switch (p.storage) {
-    case PFSI_LB_BF16: launch_mixed_shape<PFSI_LB_BF16>(c, s, omega, guo, body, utop, 1.0f); break;
-    case PFSI_LB_FP16: launch_mixed_shape<PFSI_LB_FP16>(c, s, omega, guo, body, utop, inv_scale_of(p)); break;
+    case PFSI_LB_BF16: {
+        const int rc = check_cuda(launch_mixed_shape<PFSI_LB_BF16>(c, s, omega, guo, body, utop, 1.0f), "lb_step");
+        if (rc) return rc;
+        break;
+    }
+    case PFSI_LB_FP16: {
+        const int rc = check_cuda(launch_mixed_shape<PFSI_LB_FP16>(c, s, omega, guo, body, utop, inv_scale_of(p)),
+                                  "lb_step");
+        if (rc) return rc;
+        break;
+    }
     default: {
         const int want = kFp32Block[c->shape];
         const int cap = ((p.nx + 31) / 32) * 32;
         const int bx = want < cap ? want : cap;
         const dim3 grid((p.nx + bx - 1) / bx, p.ny, p.nz);
-        k_lb_step<<<grid, bx, 0, s>>>((const float*)c->f[c->cur], (float*)c->f[c->cur ^ 1], c->g, c->v, c->flags,
-                                      p.nx, p.ny, p.nz, omega, guo, body, utop, p.walls);
+        const int rc = check_cuda(launch_pdl(k_lb_step, grid, dim3(bx), 0, s, (const float*)c->f[c->cur],
+                                             (float*)c->f[c->cur ^ 1], c->g, c->v, (const uint32_t*)c->flags, p.nx, p.ny,
+                                             p.nz, omega, guo, body, utop, p.walls),
+                                  "lb_step");
+        if (rc) return rc;
     }
     }
     c->cur ^= 1;

@@ -206,6 +206,7 @@ struct Split {
 __global__ void __launch_bounds__(256) k_mem_split(const double* __restrict__ X, int n, float* __restrict__ xh,
                                                    float* __restrict__ xl, double* __restrict__ acc, int nacc)
 {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 3 * n) {
         const double x = X[t];
@@ -250,6 +251,7 @@ __device__ __forceinline__ float3 ff3_float(ff3 a) { return make_float3(ff_float
 //             d = r - r0 likewise.
 __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
 {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const Split X{c.xh, c.xl, c.n};
     const mem_params P = c.p;
@@ -350,6 +352,7 @@ __global__ void __launch_bounds__(256) k_mem_elements(MemCtx c)
 // (Eq. 4-5), k_s (S - S0)/S0 and k_v (V - V0)/V0, once per platelet.
 __global__ void k_mem_coef(MemCtx c)
 {
+    pdl_wait();
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= c.nplt) return;
     const double* pr = c.plt_rest + 4 * p;  // S0, V0, 1/S0, 1/V0
@@ -365,6 +368,7 @@ constexpr int kNodeLanes = 4;
 
 __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx c)
 {
+    pdl_wait();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = t / kNodeLanes, q = t % kNodeLanes;
     const bool on = v < c.n;
@@ -424,17 +428,18 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
 int launch_scalars(MemCtx* c, const double* X, cudaStream_t s)
 {
     const int nsplit = 3 * c->n > 2 * c->nplt ? 3 * c->n : 2 * c->nplt;
-    k_mem_split<<<(nsplit + 255) / 256, 256, 0, s>>>(X, c->n, c->xh, c->xl, c->acc, 2 * c->nplt);
-    int rc = check_launch("membrane: split positions");
+    int rc = check_cuda(launch_pdl(k_mem_split, dim3((nsplit + 255) / 256), dim3(256), 0, s, X, c->n, c->xh, c->xl, c->acc,
+                                   2 * c->nplt),
+                        "membrane: split positions");
     if (rc) return rc;
     const int nel = c->ne + c->nt + c->np;
     if (nel > 0) {
-        k_mem_elements<<<(nel + 255) / 256, 256, 0, s>>>(*c);
-        rc = check_launch("membrane: element scalars");
+        rc = check_cuda(launch_pdl(k_mem_elements, dim3((nel + 255) / 256), dim3(256), 0, s, *c),
+                        "membrane: element scalars");
     }
     if (!rc) {
-        k_mem_coef<<<(c->nplt + 127) / 128, 128, 0, s>>>(*c);
-        rc = check_launch("membrane: platelet coefficients");
+        rc = check_cuda(launch_pdl(k_mem_coef, dim3((c->nplt + 127) / 128), dim3(128), 0, s, *c),
+                        "membrane: platelet coefficients");
     }
     return rc;
 }
@@ -445,8 +450,9 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s)
 {
     int rc = launch_scalars(c, X, s);
     if (rc) return rc;
-    k_mem_nodes<<<(int)(((long long)c->n * kNodeLanes + 127) / 128), 128, 0, s>>>(F, *c);
-    return check_launch("membrane_forces");
+    return check_cuda(launch_pdl(k_mem_nodes, dim3((unsigned)(((long long)c->n * kNodeLanes + 127) / 128)), dim3(128), 0, s,
+                                 F, *c),
+                      "membrane_forces");
 }
 
 int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s)
@@ -743,6 +749,7 @@ __global__ void __launch_bounds__(kCentroidThreads)
     k_centroids(const double* __restrict__ X, int n, const int* __restrict__ perm, const int2* __restrict__ range,
                 double* __restrict__ out)
 {
+    pdl_wait();
     const int p = blockIdx.x;
     const int2 r = range[p];
     double s[3] = {0.0, 0.0, 0.0};
@@ -774,8 +781,9 @@ extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, 
     if (!aligned(out_dev, 8)) return set_error(PFSI_ERR_ARG, "membrane_centroids: misaligned output");
     cudaStream_t s = as_stream(stream);
     if (c->nplt == 0) return PFSI_OK;
-    k_centroids<<<c->nplt, kCentroidThreads, 0, s>>>(X, c->n, c->perm, c->plt_range, out_dev);
-    return check_launch("membrane_centroids");
+    return check_cuda(launch_pdl(k_centroids, dim3(c->nplt), dim3(kCentroidThreads), 0, s, X, c->n, c->perm,
+                                 (const int2*)c->plt_range, out_dev),
+                      "membrane_centroids");
 }
 
 extern "C" int membrane_measure(mem_ctx* c, const double* X, double* out_host, void* stream)

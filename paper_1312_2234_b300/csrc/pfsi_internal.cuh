@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -29,6 +30,36 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// ---------------------------------------------------------------- dependent launch
+// The kernels of the coupled step are launched with programmatic stream
+// serialisation: a kernel's grid is dispatched as soon as the blocks of its
+// predecessor in the stream (or graph) have exited, without waiting for the
+// predecessor's completion to be processed, and the kernel itself calls
+// pdl_wait() before its first global memory access.  pdl_wait() returns once
+// all prerequisite grids have completed and their writes are visible, so the
+// data dependencies are those of a plain launch; only dispatch overlaps the
+// boundary (continuous channel stepping 59.2 -> 56.3 us per step).  No kernel
+// triggers its successor early: blocks dispatched ahead and held in the wait
+// made the 500-platelet step 12 % slower.  A no-op for a kernel launched
+// without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 // ---------------------------------------------------------------- D3Q19
 // Directions in the paper's numbering (0-based), fixed by Eq. 23-30:
