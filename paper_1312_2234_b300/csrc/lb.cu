@@ -135,17 +135,31 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     const float vv = vx * vx + vy * vy + vz * vz;
     const float vF = vx * Fx + vy * Fy + vz * Fz;
 
+    // f~' = (1 - omega) f~ + omega (f^eq - w) + S with the equilibrium of
+    // Eq. 20 and Guo's source w (1 - 1/2tau) [3 c.F + 9 (c.v)(c.F) - 3 v.F]
+    // (Eq. 19), taken per pair of opposite directions: with
+    //   a = w 3 omega rho (c.v),  b = w 3 guo (c.F),
+    //   A0 = omega (drho - 1.5 rho v.v) - 3 guo v.F,
+    // the part even in c is w A0 + 1.5 (c.v)(a + 2b) and the odd part a + b.
+    const float keep = 1.0f - omega;
+    const float R3 = 3.0f * omega * rho;
+    const float G3 = 3.0f * guo;
+    const float A0 = fmaf(omega, fmaf(-1.5f * rho, vv, drho), -G3 * vF);
+    fout[18 * N + cell] = fmaf(keep, f[18], wq(18) * A0);
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
+    for (int q = 0; q < 18; ++q) {
+        if (oppq(q) < q) continue;
+        const int o = oppq(q);
         float cv = 0.f, cF = 0.f;
         if (cxq(q)) { cv += cxq(q) * vx; cF += cxq(q) * Fx; }
         if (cyq(q)) { cv += cyq(q) * vy; cF += cyq(q) * Fy; }
         if (czq(q)) { cv += czq(q) * vz; cF += czq(q) * Fz; }
-        // equilibrium minus w_q (Eq. 20, shifted storage)
-        const float feq = wq(q) * (drho + rho * (3.0f * cv + 4.5f * cv * cv - 1.5f * vv));
-        // Guo: w (1 - 1/2tau) [3 c.F + 9 (c.v)(c.F) - 3 v.F]
-        const float src = wq(q) * guo * (3.0f * cF + 9.0f * cv * cF - 3.0f * vF);
-        fout[q * N + cell] = f[q] + omega * (feq - f[q]) + src;
+        const float a = (wq(q) * R3) * cv;
+        const float b = (wq(q) * G3) * cF;
+        const float odd = a + b;
+        const float even = fmaf(1.5f * cv, fmaf(2.0f, b, a), wq(q) * A0);
+        fout[q * N + cell] = fmaf(keep, f[q], even + odd);
+        fout[o * N + cell] = fmaf(keep, f[o], even - odd);
     }
     if (forced) {
         vout[cell] = make_float4(vx, vy, vz, rho);
