@@ -8,9 +8,10 @@ update) on the workload "channel": a 128x64x64 D3Q19 Couette channel at wall
 shear 1000/s (tau = 0.8), 10 platelets of 2562 membrane nodes + 800 SCE
 elements with 5000 receptor sites each, randomly placed within 3 um of a
 ligand-coated wall patch.  Inputs are synthetic and seeded.  The populations
-and fields (~82 MB) fit in the 126 MB L2, so L2 is flushed (a 512 MB write)
-before every timed step; each step is timed with CUDA events on the
-launching stream.
+and fields (~82 MB) fit in the 126 MB L2, so L2 is flushed before every
+timed step (a 512 MB write, then a 256 MB read, so that the L2 holds neither
+the step's data nor dirty lines of the flush buffer); each step is timed with
+CUDA events on the launching stream.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
 replica of the workload on its own GPU (independent chambers: weak scaling,
@@ -70,6 +71,26 @@ def ncu_traffic():
     if not m or not s or s.group(1) != lb_kernel_sha():
         return None
     return float(m.group(1))
+
+
+class L2Flush:
+    """Evicts the 126 MB L2 between timed steps: writes a 512 MB buffer, then
+    (unless write_only) reads a 256 MB one, so that the L2 ends up holding
+    clean lines of an unrelated buffer.  A write alone leaves ~126 MB of
+    dirty lines whose write-backs the next step's first heavy kernel pays
+    (the channel step reads ~4 us slower that way)."""
+
+    def __init__(self, dev):
+        import torch
+        self.w = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.sink = torch.empty(1, dtype=torch.float32, device=dev)
+
+    def __call__(self, k=0, write_only=False):
+        import torch
+        self.w.fill_(float(k))
+        if not write_only:
+            torch.sum(self.r, dim=0, keepdim=True, out=self.sink)
 
 
 class ClockSampler:
@@ -201,11 +222,11 @@ def run_native(args, rank, ws):
     M = w["M"]
     sim = fsi.Simulation(w, device=dev)
     lat = sim.lattice
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush(1)
         sim.step(1)
     torch.cuda.synchronize()
 
@@ -215,7 +236,7 @@ def run_native(args, rank, ws):
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         for k in range(args.steps):
-            flush.fill_(float(k))
+            flush(k)
             starts[k].record(stream)
             sim.step(1)
             ends[k].record(stream)
@@ -247,7 +268,7 @@ def run_native(args, rank, ws):
     fsi.sim_time_lb(sim.h, True)
     lb_ms = []
     for k in range(max(args.steps, 10)):
-        flush.fill_(float(k))
+        flush(k)
         sim.step(1)
         lb_ms.append(fsi.sim_lb_ms(sim.h))
     fsi.sim_time_lb(sim.h, False)
@@ -255,6 +276,17 @@ def run_native(args, rank, ws):
     # the mean of many intervals also resolves below one tick)
     lb_s = statistics.fmean(lb_ms) / 1e3
     lb_bytes = LB_BYTES_PER_CELL * N
+    # the same steps after a write-only flush (dirty L2), for comparison
+    dirty_ms = []
+    for k in range(args.steps):
+        flush(k, write_only=True)
+        a_ev = torch.cuda.Event(enable_timing=True)
+        b_ev = torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        sim.step(1)
+        b_ev.record(stream)
+        b_ev.synchronize()
+        dirty_ms.append(a_ev.elapsed_time(b_ev))
     peaks = measured_peaks()
     if peaks:
         peak, peak_note = peaks["hbm_gbs"], "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)"
@@ -323,7 +355,9 @@ def run_native(args, rank, ws):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": N, "nodes": M, "sites": int(len(w["sites"]["tri"])),
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": "replicas",
+                   "l2": "flushed before every timed step: 512 MB written, then 256 MB read (no step data "
+                         "and no dirty lines left in L2)",
+                   "ms_per_step_write_only_flush": statistics.fmean(dirty_ms), "parallelism": "replicas",
                    "graph": "one CUDA graph launch per step"},
         "node_updates_per_s": ws * M * args.steps / total_s,
         "roofline": {"bound": "hbm", "kernel": "k_lb_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -353,14 +387,14 @@ def run_mixed(args, w, storage, dev, flush, stream, snap, ws):
     N = g["nx"] * g["ny"] * g["nz"]
     sim = fsi.Simulation(w, device=dev, storage=storage)
     for _ in range(args.warmup):
-        flush.fill_(1.0)
+        flush(1)
         sim.step(1)
     torch.cuda.synchronize()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier(ws)
     for k in range(args.steps):
-        flush.fill_(float(k))
+        flush(k)
         starts[k].record(stream)
         sim.step(1)
         ends[k].record(stream)
@@ -378,7 +412,7 @@ def run_mixed(args, w, storage, dev, flush, stream, snap, ws):
     fsi.sim_time_lb(sim.h, True)
     lb_ms = []
     for k in range(max(args.steps, 10)):
-        flush.fill_(float(k))
+        flush(k)
         sim.step(1)
         lb_ms.append(fsi.sim_lb_ms(sim.h))
     fsi.sim_time_lb(sim.h, False)
@@ -527,7 +561,7 @@ def run_fem(args, w, ms_dihedral, dev, flush, stream):
     sim.step(3)
     ms = []
     for k in range(steps):
-        flush.fill_(float(k))
+        flush(k)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -574,7 +608,7 @@ def run_pair(args, dev, flush, stream):
         sim.step(3)
         ms = []
         for k in range(steps):
-            flush.fill_(float(k))
+            flush(k)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -650,7 +684,7 @@ def run_lb_only(args):
     lat.init_shear()
     N = nx * ny * nz
     per_cell = LB_BYTES_PER_CELL if args.storage == "fp32" else LB_BYTES_PER_CELL_MIXED
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush("cuda")
     small = per_cell * N < 2 * 126e6
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -658,7 +692,7 @@ def run_lb_only(args):
     ms = []
     for k in range(args.steps):
         if small:
-            flush.fill_(float(k))
+            flush(k)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
