@@ -443,22 +443,30 @@ __global__ void k_lb_export_mixed(std::integer_sequence<int, Q...>, const typena
 __global__ void k_lb_init_shear(float* __restrict__ f, int nx, int ny, int nz, double tau,
                                 double ux_top, double uy_top, int onsite)
 {
-    const int N = nx * ny * nz;
-    const double H = onsite ? (double)(nz - 1) : (double)nz, z0 = onsite ? 0.0 : 0.5;
-    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
-        const int k = cell / (nx * ny);
+    // The profile depends on the height k = blockIdx.y alone: the block's
+    // first 19 threads evaluate the plane's populations in FP64 once, then the
+    // block streams them to its share of the plane's cells.
+    __shared__ float val[19];
+    const int N = nx * ny * nz, plane = nx * ny;
+    const int k = blockIdx.y;
+    if (threadIdx.x < 19) {
+        const int q = threadIdx.x;
+        const double H = onsite ? (double)(nz - 1) : (double)nz, z0 = onsite ? 0.0 : 0.5;
         const double dux = ux_top / H, duy = uy_top / H;
         const double ux = dux * (k + z0), uy = duy * (k + z0);
         const double uu = ux * ux + uy * uy;
+        const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
+        const double cu = cxq(q) * ux + cyq(q) * uy;
+        const double feq = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        const double qgrad = (double)czq(q) * (cxq(q) * dux + cyq(q) * duy);
+        const double fneq_post = -(tau - 1.0) * w * 3.0 * qgrad;
+        val[q] = (float)(feq + fneq_post);
+    }
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += gridDim.x * blockDim.x) {
+        const int cell = k * plane + i;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
-            const double cu = cxq(q) * ux + cyq(q) * uy;
-            const double feq = w * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-            const double qgrad = (double)czq(q) * (cxq(q) * dux + cyq(q) * duy);
-            const double fneq_post = -(tau - 1.0) * w * 3.0 * qgrad;
-            f[q * N + cell] = (float)(feq + fneq_post);
-        }
+        for (int q = 0; q < 19; ++q) f[q * N + cell] = val[q];
     }
 }
 
@@ -496,18 +504,25 @@ __global__ void k_lb_init_shear_mixed(typename Neq<kMode>::T* __restrict__ nout,
                                       int ny, int nz, double tau, double ux_top, double uy_top, float inv_scale,
                                       int onsite)
 {
-    const int N = nx * ny * nz;
+    // per plane k = blockIdx.y, as k_lb_init_shear
+    __shared__ typename Neq<kMode>::T val[19];
+    const int N = nx * ny * nz, plane = nx * ny;
+    const int k = blockIdx.y;
     const double H = onsite ? (double)(nz - 1) : (double)nz, z0 = onsite ? 0.0 : 0.5;
-    for (int cell = blockIdx.x * blockDim.x + threadIdx.x; cell < N; cell += gridDim.x * blockDim.x) {
-        const int k = cell / (nx * ny);
-        const double dux = ux_top / H, duy = uy_top / H;
-        mout[cell] = make_float4((float)(dux * (k + z0)), (float)(duy * (k + z0)), 0.f, 0.f);
+    const double dux = ux_top / H, duy = uy_top / H;
+    if (threadIdx.x < 19) {
+        const int q = threadIdx.x;
+        const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
+        const double qgrad = (double)czq(q) * (cxq(q) * dux + cyq(q) * duy);
+        val[q] = Neq<kMode>::put((float)(-(tau - 1.0) * w * 3.0 * qgrad), 1.0f / inv_scale);
+    }
+    const float4 m = make_float4((float)(dux * (k + z0)), (float)(duy * (k + z0)), 0.f, 0.f);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += gridDim.x * blockDim.x) {
+        const int cell = k * plane + i;
+        mout[cell] = m;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
-            const double qgrad = (double)czq(q) * (cxq(q) * dux + cyq(q) * duy);
-            nout[q * N + cell] = Neq<kMode>::put((float)(-(tau - 1.0) * w * 3.0 * qgrad), 1.0f / inv_scale);
-        }
+        for (int q = 0; q < 19; ++q) nout[q * N + cell] = val[q];
     }
 }
 
@@ -716,9 +731,9 @@ extern "C" int lb_init_shear(lb_ctx* c, void* stream)
 {
     NvtxRange nvtx_range("lb_init_shear");
     if (!c) return set_error(PFSI_ERR_ARG, "lb_init_shear: null context");
-    const int N = (int)c->N;
-    const int blocks = (N + 255) / 256 < 148 * 16 ? (N + 255) / 256 : 148 * 16;
     const lb_params& p = c->p;
+    const int plane = p.nx * p.ny;
+    const dim3 blocks((plane + 255) / 256 < 32 ? (plane + 255) / 256 : 32, p.nz);
     cudaStream_t s = as_stream(stream);
     const double tau = p.tau, ux = p.u_top[0], uy = p.u_top[1];
     switch (p.storage) {
