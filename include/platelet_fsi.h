@@ -315,6 +315,41 @@ int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* strea
  * 64 in arrival order were considered) and returns PFSI_ERR_CAPACITY. */
 int bonds_status(bond_ctx* ctx, long long* out_host);
 
+/* --------------------------------------------------------------------- *
+ * Tether (pause-time) tracking (Section 4.2).  Reading: a platelet is
+ * tethered after a step's adhesion update when at least one of its
+ * receptor sites holds a wall bond; a tether event runs from the first such
+ * update to the first later update after which it holds none, and its pause
+ * time is the number of updates it spanned (a bond that forms in step s and
+ * breaks in step s + 2 gives a pause of 2 steps).  One block per platelet
+ * counts its bound sites in a fixed order and updates, on the device:
+ *   state[p]   the step count at which platelet p's current tether began,
+ *              or -1 when it is free (caller-owned int64 [n_plt]; initialise
+ *              it to -1, or to a saved state when a run continues);
+ *   pauses[]   completed pause times in steps, appended in no fixed order
+ *              (caller-owned int64 [capacity]);
+ *   count[0]   the number of completed events (caller-owned uint64; events
+ *              past `capacity` are counted but not stored).
+ * "Step count" is the number of completed steps: after the update of step s
+ * it is s + 1. */
+typedef struct tether_ctx tether_ctx;
+
+/* Workspace bytes for n_sites sites on n_plt platelets. */
+int tether_query_workspace(int n_sites, int n_plt, size_t* bytes);
+
+/* site_plt: host int32 [n_sites], the platelet of every site of `bonds`
+ * (0 <= site_plt < n_plt).  ws: device workspace of tether_query_workspace
+ * bytes (the per-platelet site lists).  The context keeps the pointers of
+ * bonds, state, pauses and count (all caller-owned).  Synchronises. */
+int tether_create(const bond_ctx* bonds, int n_plt, const int* site_plt, void* ws, size_t ws_bytes, long long* state,
+                  long long* pauses, int capacity, unsigned long long* count, tether_ctx** out);
+int tether_destroy(tether_ctx* ctx);
+
+/* Update after the bonds_step of step `step` (the step count is step + 1).
+ * In a simulation (sim_set_tether) the update runs inside the step after the
+ * adhesion update instead. */
+int tether_update(tether_ctx* ctx, uint64_t step, void* stream);
+
 /* ===================================================================== *
  * Platelet-platelet bridges GPIb-alpha - vWF - GPIb-alpha (Section 3.2)
  *
@@ -594,6 +629,11 @@ int sim_check(sim_ctx* ctx, float u_max, unsigned long long* dev_scratch4, long 
  * counter continues from the simulation's.  br = NULL removes them.  The
  * graphs are recaptured.  Synchronises. */
 int sim_set_bridges(sim_ctx* ctx, bridge_ctx* br);
+
+/* Track tethers (pause times) in the step: the update of `tr` (whose bonds
+ * must be the simulation's) runs after every step's adhesion update; null
+ * turns tracking off.  The step graphs are rebuilt on the next step. */
+int sim_set_tether(sim_ctx* ctx, tether_ctx* tr);
 
 /* Measurement aid (no paper counterpart): on != 0 records two CUDA events
  * around the lattice Boltzmann kernel inside the step graph (the graphs are

@@ -16,6 +16,8 @@
 // (receptor position, bond length, rates) is FP64 with explicitly rounded
 // operations in the order of the plain restatement, so that an event differs
 // only when a uniform lands within an ulp of its probability.
+#include <vector>
+
 #include "adhesion.cuh"
 
 namespace pfsi {
@@ -165,6 +167,33 @@ __global__ void k_bond_resolve(BondCtx c, unsigned long long* __restrict__ step_
     if (acc) atomicAdd(&c.counters[1], (unsigned long long)acc);
 }
 
+// Tether tracking (Section 4.2): one block per platelet counts its bound
+// sites (integer sum: exact in any order), then thread 0 opens or closes the
+// platelet's tether event.
+constexpr int kTetherThreads = 128;
+
+__global__ void __launch_bounds__(kTetherThreads) k_tether(TetherCtx t, const int* __restrict__ bound,
+                                                           const unsigned long long* __restrict__ now_dev,
+                                                           uint64_t now_host)
+{
+    pdl_wait();
+    const int p = blockIdx.x;
+    const int b = t.off[p], e = t.off[p + 1];
+    int n = 0;
+    for (int k = b + (int)threadIdx.x; k < e; k += kTetherThreads) n += bound[t.sites[k]] >= 0;
+    const bool tethered = __syncthreads_count(n > 0) > 0;
+    if (threadIdx.x != 0) return;
+    const long long now = (long long)(now_dev ? *now_dev : now_host);
+    const long long start = t.state[p];
+    if (tethered && start < 0) {
+        t.state[p] = now;
+    } else if (!tethered && start >= 0) {
+        const unsigned long long slot = atomicAdd(t.count, 1ull);
+        if (slot < (unsigned long long)t.cap) t.pauses[slot] = now - start;
+        t.state[p] = -1;
+    }
+}
+
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
 // workspace: nprop[L], cand[L * kMaxCand], counters[4]
@@ -200,9 +229,91 @@ int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                       "bonds_step: resolve");
 }
 
+int launch_tether_update(const TetherCtx* c, const unsigned long long* now_dev, uint64_t now_host, cudaStream_t s)
+{
+    if (c->nplt == 0) return PFSI_OK;
+    return check_cuda(launch_pdl(k_tether, dim3(c->nplt), dim3(kTetherThreads), 0, s, *c, (const int*)c->bonds->bound,
+                                 now_dev, now_host),
+                      "tether_update");
+}
+
 }  // namespace pfsi
 
 using namespace pfsi;
+
+struct tether_ctx : pfsi::TetherCtx {};
+
+const pfsi::TetherCtx* pfsi::tether_internal(const tether_ctx* t) { return t; }
+
+static size_t tether_ws_bytes(int n_sites, int n_plt)
+{
+    return (sizeof(int) * ((size_t)n_plt + 1) + 255) / 256 * 256 + sizeof(int) * (size_t)n_sites;
+}
+
+extern "C" int tether_query_workspace(int n_sites, int n_plt, size_t* bytes)
+{
+    if (!bytes || n_sites < 0 || n_plt < 0) return set_error(PFSI_ERR_ARG, "tether_query_workspace: bad argument");
+    *bytes = tether_ws_bytes(n_sites, n_plt);
+    return PFSI_OK;
+}
+
+extern "C" int tether_create(const bond_ctx* bonds, int n_plt, const int* site_plt, void* ws, size_t ws_bytes,
+                             long long* state, long long* pauses, int capacity, unsigned long long* count,
+                             tether_ctx** out)
+{
+    if (!bonds || !out || n_plt < 0 || capacity < 0 || !ws || !count || (n_plt > 0 && !state) ||
+        (capacity > 0 && !pauses) || (bonds->R > 0 && !site_plt))
+        return set_error(PFSI_ERR_ARG, "tether_create: bad argument");
+    if (!aligned(ws, 256) || !aligned(state, 8) || !aligned(pauses, 8) || !aligned(count, 8))
+        return set_error(PFSI_ERR_ARG, "tether_create: misaligned buffer");
+    const int R = bonds->R;
+    if (ws_bytes < tether_ws_bytes(R, n_plt)) return set_error(PFSI_ERR_ARG, "tether_create: workspace too small");
+    // sites grouped by platelet (counting sort, ascending site ids within a platelet)
+    std::vector<int> off((size_t)n_plt + 1, 0), sites((size_t)R);
+    for (int s = 0; s < R; ++s) {
+        if (site_plt[s] < 0 || site_plt[s] >= n_plt)
+            return set_error(PFSI_ERR_ARG, "tether_create: site platelet out of range");
+        ++off[site_plt[s] + 1];
+    }
+    for (int p = 0; p < n_plt; ++p) off[p + 1] += off[p];
+    {
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (int s = 0; s < R; ++s) sites[fill[site_plt[s]]++] = s;
+    }
+    char* base = static_cast<char*>(ws);
+    int* d_off = reinterpret_cast<int*>(base);
+    int* d_sites = reinterpret_cast<int*>(base + (sizeof(int) * ((size_t)n_plt + 1) + 255) / 256 * 256);
+    int rc = check_cuda(cudaMemcpy(d_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice),
+                        "tether_create: copy");
+    if (!rc && R > 0)
+        rc = check_cuda(cudaMemcpy(d_sites, sites.data(), sizeof(int) * (size_t)R, cudaMemcpyHostToDevice),
+                        "tether_create: copy");
+    if (rc) return rc;
+    tether_ctx* c = new tether_ctx();
+    c->bonds = bonds;
+    c->nplt = n_plt;
+    c->off = d_off;
+    c->sites = d_sites;
+    c->state = state;
+    c->pauses = pauses;
+    c->cap = capacity;
+    c->count = count;
+    *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int tether_destroy(tether_ctx* c)
+{
+    delete c;
+    return PFSI_OK;
+}
+
+extern "C" int tether_update(tether_ctx* c, uint64_t step, void* stream)
+{
+    NvtxRange nvtx_range("tether_update");
+    if (!c) return set_error(PFSI_ERR_ARG, "tether_update: null context");
+    return launch_tether_update(c, nullptr, step + 1, as_stream(stream));
+}
 
 static int check_bond_params(const bond_params* p, const char* who)
 {

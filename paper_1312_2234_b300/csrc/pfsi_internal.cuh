@@ -192,6 +192,21 @@ struct BondCtx {
 };
 constexpr int kMaxCand = 64;
 
+// Tether (pause-time) tracker over a bond context (bonds.cu).
+struct TetherCtx {
+    const BondCtx* bonds;
+    int nplt;
+    const int* off;               // [nplt + 1] per-platelet runs of `sites` (workspace)
+    const int* sites;             // [R] site ids grouped by platelet, ascending within a platelet
+    long long* state;             // caller [nplt]: step count at the tether's start, or -1
+    long long* pauses;            // caller [cap]
+    int cap;
+    unsigned long long* count;    // caller [1]
+};
+const TetherCtx* tether_internal(const tether_ctx* t);
+// After the adhesion update: the step count is *now_dev if now_dev, else now_host.
+int launch_tether_update(const TetherCtx* c, const unsigned long long* now_dev, uint64_t now_host, cudaStream_t s);
+
 // Nodes per block of the IB kernels (also the largest chunk of the membrane's
 // chunk table).
 constexpr int kIbChunk = 128;

@@ -36,6 +36,7 @@ struct SimCtx {
     FemCtx* fem;           // finite-element bending, or null
     float fem_k0;
     BridgeCtx* br;         // platelet-platelet bridges, or null
+    const TetherCtx* tether;  // pause-time tracking, or null
     // sim_step_record / sim_step_track: copy stream and per-slot events
     // (created on first use)
     cudaStream_t rec;
@@ -92,6 +93,8 @@ int enqueue_adhesion(SimCtx* c, cudaStream_t s)
     int rc = PFSI_OK;
     if (c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
     if (!rc && c->br) rc = launch_bridges_step(c->br, c->X, c->M, 0, bridge_step_counter(c->br), s);
+    // tethers after the wall update; the bond step counter now counts this step
+    if (!rc && c->tether) rc = launch_tether_update(c->tether, c->bonds->counters + 3, 0, s);
     return rc;
 }
 
@@ -225,6 +228,7 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->fem = nullptr;
     c->fem_k0 = 0.0f;
     c->br = nullptr;
+    c->tether = nullptr;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "sim_create: stream");
@@ -467,6 +471,17 @@ extern "C" int sim_set_bridges(sim_ctx* c, bridge_ctx* br)
         return check_cuda(cudaMemcpy(bridge_step_counter(b), &step, sizeof(step), cudaMemcpyHostToDevice),
                           "sim_set_bridges: step counter");
     }
+    return PFSI_OK;
+}
+
+extern "C" int sim_set_tether(sim_ctx* c, tether_ctx* tr)
+{
+    if (!c) return set_error(PFSI_ERR_ARG, "sim_set_tether: null context");
+    const TetherCtx* t = tether_internal(tr);
+    if (t && (!c->bonds || t->bonds != c->bonds))
+        return set_error(PFSI_ERR_ARG, "sim_set_tether: tracker not built on the simulation's bonds");
+    drop_graphs(c);
+    c->tether = t;
     return PFSI_OK;
 }
 

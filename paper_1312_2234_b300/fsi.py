@@ -92,6 +92,11 @@ _SIGS = {
     "bonds_destroy": [P],
     "bonds_forces": [P, P, P, c_int, P],
     "bonds_step": [P, P, c_int, c_uint64, P],
+    "tether_query_workspace": [c_int, c_int, ctypes.POINTER(c_size_t)],
+    "tether_create": [P, c_int, P, P, c_size_t, P, P, c_int, P, ctypes.POINTER(P)],
+    "tether_destroy": [P],
+    "tether_update": [P, c_uint64, P],
+    "sim_set_tether": [P, P],
     "bonds_status": [P, ctypes.POINTER(c_longlong)],
     "sim_create": [P, P, P, P, P, P, c_int, c_uint64, ctypes.POINTER(P)],
     "sim_destroy": [P],
@@ -553,6 +558,50 @@ class Bonds:
             self.h = None
 
 
+class Tethers:
+    """Tether (pause-time) tracking over a Bonds object (Section 4.2): per
+    platelet the step count at which its current tether began (-1: free) and
+    the pause times, in steps, of completed tether events.  site_plt: the
+    platelet of every site (host array); state: optional saved per-platelet
+    state (a continued run)."""
+
+    def __init__(self, bonds, site_plt, n_plt, capacity=1 << 20, state=None, device="cuda"):
+        sp = np.ascontiguousarray(site_plt, dtype=np.int32)
+        if len(sp) != bonds.R:
+            raise ValueError("one platelet id per receptor site")
+        self.bonds = bonds                   # the tracker reads its bond state
+        self.n_plt = int(n_plt)
+        st = np.full(self.n_plt, -1, dtype=np.int64) if state is None else np.asarray(state, dtype=np.int64)
+        self.state = torch.as_tensor(st, device=device).clone()
+        self.pause_buf = torch.zeros(max(int(capacity), 1), dtype=torch.int64, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        n = c_size_t()
+        _call("tether_query_workspace", bonds.R, self.n_plt, ctypes.byref(n))
+        self.ws = _bytes(n.value, device)
+        h = P()
+        _call("tether_create", bonds.h, self.n_plt, _ptr(sp), _ptr(self.ws), n.value, _ptr(self.state),
+              _ptr(self.pause_buf), int(capacity), _ptr(self.count), ctypes.byref(h))
+        self.h = h
+
+    def update(self, step, stream=None):
+        """After the bonds_step of step `step`."""
+        _call("tether_update", self.h, int(step), _stream(stream))
+
+    def pauses(self):
+        """Completed pause times in steps, sorted (the device appends them in
+        no fixed order)."""
+        n = min(int(self.count.item()), self.pause_buf.numel())
+        return np.sort(self.pause_buf[:n].cpu().numpy())
+
+    def events(self):
+        return int(self.count.item())
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.tether_destroy(self.h)
+            self.h = None
+
+
 def bridge_params_from(d):
     return bridge_params(float(d["sigma"]), float(d["l_b"]), float(d["d_capture"]), float(d["gamma"]),
                          float(d["kT"]), float(d["kon0_dt"]), float(d["koff0_dt"]), int(d["box_nx"]),
@@ -606,7 +655,10 @@ class Bridges:
 class Simulation:
     """The coupled step on one workload (see :mod:`paper_1312_2234_b300.workload`)."""
 
-    def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None, tune=False):
+    def __init__(self, w, device="cuda", first_step=0, storage="fp32", fp16_exponent=None, tune=False,
+                 track_tethers=0):
+        """track_tethers: capacity of the pause-time record (0: no tether
+        tracking; see Tethers)."""
         g = w["grid"]
         self.lattice = Lattice(g["nx"], g["ny"], g["nz"], g["tau"], g["u_top"], g.get("body", (0, 0, 0)), device,
                                storage, fp16_exponent, g.get("walls", 0))
@@ -637,6 +689,12 @@ class Simulation:
             self.bridges = Bridges(w["bridges"], self.bonds, w["mesh"]["node_plt"], w["mesh"]["n_plt"],
                                    w.get("partner"), device)
             _call("sim_set_bridges", self.h, self.bridges.h)
+        self.tethers = None
+        if track_tethers and self.bonds is not None:
+            tri = np.asarray(w["mesh"]["tri"], dtype=np.int64).reshape(-1, 3)
+            site_plt = np.asarray(w["mesh"]["node_plt"])[tri[np.asarray(w["sites"]["tri"]), 0]]
+            self.tethers = Tethers(self.bonds, site_plt, w["mesh"]["n_plt"], int(track_tethers), device=device)
+            _call("sim_set_tether", self.h, self.tethers.h)
 
     def step(self, n=1, stream=None):
         sim_step(self.h, n, stream)
@@ -674,7 +732,7 @@ class Simulation:
     def checkpoint(self):
         """The state a later run needs to continue this one: the step index,
         the lattice populations (FP32, or 16-bit f*neq with the moments), the
-        node positions, the wall-bond and bridge state.  Philox draws are keyed
+        node positions, the wall-bond and bridge state and the open tethers.  Philox draws are keyed
         by (site, step), so the continued run takes the same random decisions.
         Returns a dict of host arrays (np.savez-able)."""
         torch.cuda.synchronize()
@@ -687,6 +745,8 @@ class Simulation:
             ck["lig_count"] = self.bonds.lig_count.cpu().numpy()
         if self.bridges is not None:
             ck["partner"] = self.bridges.partner.cpu().numpy()
+        if self.tethers is not None:
+            ck["tether_state"] = self.tethers.state.cpu().numpy()
         return ck
 
     @classmethod
@@ -703,6 +763,8 @@ class Simulation:
             sim.bonds.lig_count.copy_(torch.as_tensor(ck["lig_count"]))
         if sim.bridges is not None:
             sim.bridges.partner.copy_(torch.as_tensor(ck["partner"]))
+        if sim.tethers is not None and "tether_state" in ck:
+            sim.tethers.state.copy_(torch.as_tensor(ck["tether_state"]))
         torch.cuda.synchronize()
         return sim
 

@@ -186,3 +186,15 @@ def test_wait_selftest_rejects_bad_arguments():
     L = fsi.lib()
     assert L.pfsi_wait_selftest(0, None, None) == -1
     assert L.pfsi_wait_selftest(5, None, None) == -1
+
+
+def test_tether_calls_validate_their_arguments():
+    L = fsi.lib()
+    n = ctypes.c_size_t()
+    assert L.tether_query_workspace(-1, 2, ctypes.byref(n)) == -1
+    assert L.tether_query_workspace(10, 3, None) == -1
+    assert L.tether_query_workspace(10, 3, ctypes.byref(n)) == 0 and n.value >= 4 * 4 + 4 * 10
+    h = ctypes.c_void_p()
+    assert L.tether_create(None, 3, None, None, 0, None, None, 0, None, ctypes.byref(h)) == -1
+    assert L.tether_update(None, 0, None) == -1
+    assert L.sim_set_tether(None, None) == -1
