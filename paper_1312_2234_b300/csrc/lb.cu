@@ -402,15 +402,25 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
             const float VV = vx * vx + vy * vy + vz * vz;                           // 9 v.v
             const float P0 = fmaf(-rho / 6.0f, VV, drho);                            // drho - 1.5 rho v.v
             const float vF3 = (vx * F3.x + vy * F3.y + vz * F3.z) * (1.0f / 3.0f);  // 3 v.F
+            // post-collision minus equilibrium, (1 - omega)(f - f^eq) + S, with
+            // (f^eq - w)/w = P0 + rho (cv + cv^2/2) and S/(w guo) = cF (1 + cv) - vF3
+            // (cv = 3 c.v, cF = 3 c.F), per pair of opposite directions: with
+            //   a = -keep w rho cv,  b = w guo cF,  E0 = -keep P0 - guo vF3,
+            // the part even in c is w E0 + cv (a/2 + b), the odd part a + b.
+            const float E0 = fmaf(-keep, P0, -guo * vF3);
+            nout[18 * N + cell] = Neq<kMode>::put(fmaf(keep, f[18], wq(18) * E0), scale);
 #pragma unroll
-            for (int q = 0; q < 19; ++q) {
-                const float cv = c_dot(q, vx, vy, vz);        // 3 c.v
-                const float cF = c_dot(q, F3.x, F3.y, F3.z);  // 3 c.F
-                const float feq = fmaf(rho, fmaf(0.5f * cv, cv, cv), P0);    // (f^eq - w) / w
-                const float src = fmaf(cF, cv, cF - vF3);                     // S / (w guo)
-                // post-collision minus equilibrium: (1 - omega)(f - f^eq) + S
-                const float neq = fmaf(keep, f[q], fmaf(-keep * wq(q), feq, (wq(q) * guo) * src));
-                nout[q * N + cell] = Neq<kMode>::put(neq, scale);
+            for (int q = 0; q < 18; ++q) {
+                if (oppq(q) < q) continue;
+                const int o = oppq(q);
+                const float cv = c_dot(q, vx, vy, vz);
+                const float cF = c_dot(q, F3.x, F3.y, F3.z);
+                const float a = (-keep * wq(q)) * rho * cv;
+                const float b = (wq(q) * guo) * cF;
+                const float odd = a + b;
+                const float even = fmaf(cv, fmaf(0.5f, a, b), wq(q) * E0);
+                nout[q * N + cell] = Neq<kMode>::put(fmaf(keep, f[q], even + odd), scale);
+                nout[o * N + cell] = Neq<kMode>::put(fmaf(keep, f[o], even - odd), scale);
             }
             mout[cell] = make_float4(vx * (1.0f / 3.0f), vy * (1.0f / 3.0f), vz * (1.0f / 3.0f), drho);
             if (forced) g[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
