@@ -253,9 +253,13 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
                                                       const int* __restrict__ perm,
                                                       const float4* __restrict__ v,
                                                       uint32_t* __restrict__ flags, int nx, int ny, int nz,
-                                                      int advect)
+                                                      int advect, NextSplit next)
 {
     pdl_wait();
+    if (next.acc) {   // the next membrane pass accumulates into cleared sums
+        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        if (t < next.nacc) next.acc[t] = 0.0;
+    }
     extern __shared__ float4 tile4[];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
@@ -348,9 +352,16 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
     U[M + m] = uy;
     U[2 * M + m] = uz;
     if (advect) {
-        X[m] = x + (double)ux;
-        X[M + m] = y + (double)uy;
-        X[2 * M + m] = z + (double)uz;
+        const double xn[3] = {x + (double)ux, y + (double)uy, z + (double)uz};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            X[d * M + m] = xn[d];
+            if (next.h) {   // the hi/lo split the membrane pass would form from X
+                const float h = __double2float_rn(xn[d]);
+                next.h[d * M + m] = h;
+                next.l[d * M + m] = __double2float_rn(xn[d] - (double)h);
+            }
+        }
     }
 }
 
@@ -377,12 +388,14 @@ int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int
 }
 
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm, int n_chunks,
-                     cudaStream_t s)
+                     cudaStream_t s, NextSplit next)
 {
     if (M == 0) return PFSI_OK;
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
+    if (next.acc && (long long)blocks * kChunk < next.nacc)
+        return set_error(PFSI_ERR_ARG, "ib_interp: fewer threads than per-platelet sums to clear");
     return check_cuda(launch_pdl(k_ib_interp, dim3(blocks), dim3(kChunk), kTileBytes, s, X, U, M, chunks, perm,
-                                 (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz, advect),
+                                 (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz, advect, next),
                       "ib_interp");
 }
 

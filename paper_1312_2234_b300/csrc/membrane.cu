@@ -425,13 +425,16 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
     F[2 * n + v] = fz;
 }
 
-int launch_scalars(MemCtx* c, const double* X, cudaStream_t s)
+int launch_scalars(MemCtx* c, const double* X, cudaStream_t s, bool presplit = false)
 {
-    const int nsplit = 3 * c->n > 2 * c->nplt ? 3 * c->n : 2 * c->nplt;
-    int rc = check_cuda(launch_pdl(k_mem_split, dim3((nsplit + 255) / 256), dim3(256), 0, s, X, c->n, c->xh, c->xl, c->acc,
-                                   2 * c->nplt),
+    int rc = PFSI_OK;
+    if (!presplit) {
+        const int nsplit = 3 * c->n > 2 * c->nplt ? 3 * c->n : 2 * c->nplt;
+        rc = check_cuda(launch_pdl(k_mem_split, dim3((nsplit + 255) / 256), dim3(256), 0, s, X, c->n, c->xh, c->xl,
+                                   c->acc, 2 * c->nplt),
                         "membrane: split positions");
-    if (rc) return rc;
+        if (rc) return rc;
+    }
     const int nel = c->ne + c->nt + c->np;
     if (nel > 0) {
         rc = check_cuda(launch_pdl(k_mem_elements, dim3((nel + 255) / 256), dim3(256), 0, s, *c),
@@ -446,16 +449,16 @@ int launch_scalars(MemCtx* c, const double* X, cudaStream_t s)
 
 }  // namespace
 
-int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s)
+int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
 {
-    int rc = launch_scalars(c, X, s);
+    int rc = launch_scalars(c, X, s, presplit);
     if (rc) return rc;
     return check_cuda(launch_pdl(k_mem_nodes, dim3((unsigned)(((long long)c->n * kNodeLanes + 127) / 128)), dim3(128), 0, s,
                                  F, *c),
                       "membrane_forces");
 }
 
-int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s)
+int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
 {
     MemCtx g = *c;
     g.p.k_spring = 0.f;
@@ -463,7 +466,7 @@ int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s)
     g.p.k_b = 0.f;
     g.ne = 0;            // element ids start at the triangles
     g.skip_edges = 1;
-    return launch_membrane_forces(&g, X, F, s);
+    return launch_membrane_forces(&g, X, F, s, presplit);
 }
 
 }  // namespace pfsi

@@ -223,12 +223,23 @@ int launch_lb_step(LbCtx* c, cudaStream_t s);
 // kIbChunk consecutive nodes.
 int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, const int* perm,
                      int n_chunks, cudaStream_t s);
+// split (optional, with advect): the next membrane pass's input -- the hi/lo
+// float split of the advected X into split_h/split_l [3][M] and the
+// per-platelet sums acc[0..nacc) cleared -- so that pass can skip its own.
+struct NextSplit {
+    float* h = nullptr;
+    float* l = nullptr;
+    double* acc = nullptr;
+    int nacc = 0;
+};
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm,
-                     int n_chunks, cudaStream_t s);
-int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s);
+                     int n_chunks, cudaStream_t s, NextSplit split = NextSplit());
+// presplit: mem->xh, xl hold the split of X and the per-platelet sums are
+// clear (written by the previous step's interpolation): no split pass.
+int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
 // The global terms only (global area, volume, Morse pairs, wall): what the
 // learned surrogate does not stand for.  Writes F.
-int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s);
+int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
 // step_dev: device step counter (advanced by one after the update) or null
 // to use step_host.

@@ -55,15 +55,16 @@ namespace {
 constexpr int kMulti = 4;   // steps per multi-step graph (even: the lattice parity returns)
 
 // Membrane forces of the current positions (F overwritten, then the
-// optional finite-element bending added).
-int enqueue_front(SimCtx* c, cudaStream_t s)
+// optional finite-element bending added).  presplit: the previous step's
+// interpolation left the hi/lo split of X and cleared the per-platelet sums.
+int enqueue_front(SimCtx* c, cudaStream_t s, bool presplit = false)
 {
     int rc;
     if (c->sg) {
-        rc = launch_membrane_global(c->mem, c->X, c->F, s);
+        rc = launch_membrane_global(c->mem, c->X, c->F, s, presplit);
         if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->mem->xh, c->mem->xl, c->F, s);
     } else {
-        rc = launch_membrane_forces(c->mem, c->X, c->F, s);
+        rc = launch_membrane_forces(c->mem, c->X, c->F, s, presplit);
     }
     // the membrane pass (plain or global-only) left the hi/lo split of X in mem->xh, xl
     if (!rc && c->fem) rc = launch_fem_forces(c->fem, c->fem_k0, c->X, c->mem->xh, c->mem->xl, c->F, 1, nullptr, s);
@@ -71,8 +72,9 @@ int enqueue_front(SimCtx* c, cudaStream_t s)
 }
 
 // Bond and bridge forces, spreading, the lattice step, interpolation and
-// advection.
-int enqueue_middle(SimCtx* c, cudaStream_t s)
+// advection.  split_next: the interpolation also prepares the next membrane
+// pass's input (see NextSplit), which then runs with presplit.
+int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false)
 {
     int rc = PFSI_OK;
     if (c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
@@ -83,7 +85,15 @@ int enqueue_middle(SimCtx* c, cudaStream_t s)
     if (!rc) rc = launch_lb_step(c->lb, s);
     if (!rc && c->lb_ev[1])
         rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
-    if (!rc) rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s);
+    NextSplit next;
+    if (split_next) {
+        next.h = c->mem->xh;
+        next.l = c->mem->xl;
+        next.acc = c->mem->acc;
+        next.nacc = 2 * c->mem->nplt;
+    }
+    if (!rc)
+        rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s, next);
     return rc;
 }
 
@@ -109,8 +119,10 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
 // n steps in which step k's adhesion update (reads X after step k, writes
 // only the bond and bridge state) runs on the side stream while step k + 1's
 // membrane pass (reads X, writes only F and the membrane scratch) runs on
-// `s`; step k + 1's bond forces wait for it.  Same operations on the same
-// data as n single steps.
+// `s`; step k + 1's bond forces wait for it.  Step k's interpolation also
+// forms the hi/lo split of its advected X (the same FP64 operations as the
+// split pass) for step k + 1's membrane pass, which skips its split.  Same
+// results as n single steps.
 int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n, double* slots = nullptr)
 {
     // slots (tracked graphs): after step k the platelet centroids go to
@@ -118,7 +130,7 @@ int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n, double* slots = nullptr
     // with the adhesion update (the last step's on the main stream)
     const size_t slot = 4 * (size_t)c->mem->nplt;
     int rc = enqueue_front(c, s);
-    if (!rc) rc = enqueue_middle(c, s);
+    if (!rc) rc = enqueue_middle(c, s, n > 1);
     for (int k = 1; k < n && !rc; ++k) {
         rc = check_cuda(cudaEventRecord(c->fork, s), "sim: fork");
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->side, c->fork, 0), "sim: fork");
@@ -126,9 +138,9 @@ int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n, double* slots = nullptr
             rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (k - 1) * slot, c->side);
         if (!rc) rc = enqueue_adhesion(c, c->side);
         if (!rc) rc = check_cuda(cudaEventRecord(c->join, c->side), "sim: join");
-        if (!rc) rc = enqueue_front(c, s);
+        if (!rc) rc = enqueue_front(c, s, true);
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(s, c->join, 0), "sim: join");
-        if (!rc) rc = enqueue_middle(c, s);
+        if (!rc) rc = enqueue_middle(c, s, k + 1 < n);
     }
     if (!rc && slots) rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (n - 1) * slot, s);
     if (!rc) rc = enqueue_adhesion(c, s);
