@@ -82,21 +82,25 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
     pdl_wait();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
+    // the site's state, triangle and weights are loaded together (the height
+    // test below needs all but the state)
     const int b = c.bound[s];
+    const int t = __ldg(c.site_tri + s);
+    const double w0 = __ldg(c.site_w + 2 * s), w1 = __ldg(c.site_w + 2 * s + 1);
+    const int bridged = c.partner ? c.partner[s] : -1;
     if (b == -2) {
         c.bound[s] = -1;
         return;
     }
     if (b >= 0) return;
-    if (c.partner && c.partner[s] >= 0) return;   // bridged to another platelet: one bond per site
+    if (bridged >= 0) return;   // bridged to another platelet: one bond per site
     const bond_params& p = c.p;
     // Out of reach of every ligand: the bond length is at least the height
     // above the wall plane (the margin covers the last-ulp rounding of the
     // norm), so skipping here cannot change a decision.
     {
-        const int t = c.site_tri[s];
-        const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
-        const double z = site_coord(X, M, 2, c.tri[3 * t], c.tri[3 * t + 1], c.tri[3 * t + 2], w0, w1);
+        const double z = site_coord(X, M, 2, __ldg(c.tri + 3 * t), __ldg(c.tri + 3 * t + 1), __ldg(c.tri + 3 * t + 2),
+                                    w0, w1);
         if (fabs(__dsub_rn(z, p.z_wall)) > p.d_capture * (1.0 + 1e-12)) return;
     }
     const uint64_t step = current_step(step_dev, step_host);

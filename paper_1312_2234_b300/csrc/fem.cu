@@ -233,8 +233,25 @@ __global__ void __launch_bounds__(kFemThreads)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.n) return;
     const int b = __ldg(c.off + i), en = __ldg(c.off + i + 1);
+    // a vertex lies in ~6 elements, an edge midpoint in 2: the first six list
+    // entries, then their slots, are loaded together; sums in list order
+    constexpr int kPre = 6;
+    int li[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) li[u] = b + u < en ? __ldg(c.list + b + u) : -1;
+    float4 pv[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) pv[u] = li[u] >= 0 ? c.slot[li[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = b; k < en; ++k) {
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (li[u] >= 0) {
+            s.x += pv[u].x;
+            s.y += pv[u].y;
+            s.z += pv[u].z;
+            s.w += pv[u].w;
+        }
+    for (int k = b + kPre; k < en; ++k) {
         const float4 v = c.slot[__ldg(c.list + k)];
         s.x += v.x;
         s.y += v.y;
