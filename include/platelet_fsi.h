@@ -592,8 +592,10 @@ int sim_step(sim_ctx* ctx, int nsteps, void* stream);
 int sim_step_record(sim_ctx* ctx, int nsteps, double* dev_ring, double* host_ring, int ring, void* stream);
 
 /* nsteps coupled steps, following the platelets: after step k the
- * centroids of all platelets (membrane_centroids, computed inside the step
- * graphs) are copied to host_out[k][n_plt][3] (pinned host memory,
+ * centroids of all platelets (the mean node position of each, computed
+ * inside the step graphs from FP64 sums that the interpolation pass forms
+ * per chunk of nodes, added in a fixed order) are copied to
+ * host_out[k][n_plt][3] (pinned host memory,
  * nsteps * 3 * n_plt doubles) on the context's copy stream, overlapping the
  * next steps.  Steps run four per graph where they can (one strided copy per
  * four steps), one per graph otherwise.  dev_scratch: device, 40 * n_plt

@@ -248,6 +248,8 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
     }
 }
 
+// kPart: also write the block's sum of the advected X (next.part)
+template <bool kPart>
 __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
                                                       const int2* __restrict__ chunks,
                                                       const int* __restrict__ perm,
@@ -305,28 +307,28 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
                 if (i0 + u * kChunk < cells) tile4[i0 + u * kChunk] = val[u];
         }
         __syncthreads();
-        if (!on) return;
-        const int ox = s.bx - b.x0, oy = s.by - b.y0, oz = s.bz - b.z0;
+        if (on) {
+            const int ox = s.bx - b.x0, oy = s.by - b.y0, oz = s.bz - b.z0;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int k = oz + c;
-            if (k < 0 || k >= b.ez) continue;
+            for (int c = 0; c < 4; ++c) {
+                const int k = oz + c;
+                if (k < 0 || k >= b.ez) continue;
 #pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const float wyz = s.wy[bb] * s.wz[c];
-                const float4* row = tile4 + (k * b.ey + oy + bb) * b.ex + ox;
+                for (int bb = 0; bb < 4; ++bb) {
+                    const float wyz = s.wy[bb] * s.wz[c];
+                    const float4* row = tile4 + (k * b.ey + oy + bb) * b.ex + ox;
 #pragma unroll
-                for (int aa = 0; aa < 4; ++aa) {
-                    const float w = s.wx[aa] * wyz;
-                    const float4 vv = row[aa];
-                    ux += w * vv.x;
-                    uy += w * vv.y;
-                    uz += w * vv.z;
+                    for (int aa = 0; aa < 4; ++aa) {
+                        const float w = s.wx[aa] * wyz;
+                        const float4 vv = row[aa];
+                        ux += w * vv.x;
+                        uy += w * vv.y;
+                        uz += w * vv.z;
+                    }
                 }
             }
         }
-    } else {
-        if (!on) return;
+    } else if (on) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const int k = s.bz + c;
@@ -348,19 +350,41 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
             }
         }
     }
-    U[m] = ux;
-    U[M + m] = uy;
-    U[2 * M + m] = uz;
-    if (advect) {
-        const double xn[3] = {x + (double)ux, y + (double)uy, z + (double)uz};
+    double xn[3] = {0.0, 0.0, 0.0};
+    if (on) {
+        U[m] = ux;
+        U[M + m] = uy;
+        U[2 * M + m] = uz;
+        if (advect) {
+            xn[0] = x + (double)ux;
+            xn[1] = y + (double)uy;
+            xn[2] = z + (double)uz;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                X[d * M + m] = xn[d];
+                if (next.h) {   // the hi/lo split the membrane pass would form from X
+                    const float h = __double2float_rn(xn[d]);
+                    next.h[d * M + m] = h;
+                    next.l[d * M + m] = __double2float_rn(xn[d] - (double)h);
+                }
+            }
+        }
+    }
+    if (kPart && advect) {   // the block's sum of the advected X, fixed order
+        __shared__ double wsum[kWarps][3];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            X[d * M + m] = xn[d];
-            if (next.h) {   // the hi/lo split the membrane pass would form from X
-                const float h = __double2float_rn(xn[d]);
-                next.h[d * M + m] = h;
-                next.l[d * M + m] = __double2float_rn(xn[d] - (double)h);
-            }
+            double t = xn[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+            if (lane == 0) wsum[warp][d] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double t = 0.0;
+            for (int w = 0; w < kWarps; ++w) t += wsum[w][threadIdx.x];
+            next.part[3 * blockIdx.x + threadIdx.x] = t;
         }
     }
 }
@@ -372,7 +396,12 @@ int ib_prepare()
     int rc = check_cuda(cudaFuncSetAttribute(k_ib_spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileBytes),
                         "ib: shared memory size");
     if (!rc)
-        rc = check_cuda(cudaFuncSetAttribute(k_ib_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileBytes),
+        rc = check_cuda(cudaFuncSetAttribute(k_ib_interp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTileBytes),
+                        "ib: shared memory size");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_ib_interp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTileBytes),
                         "ib: shared memory size");
     return rc;
 }
@@ -394,8 +423,11 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
     const int blocks = chunks ? n_chunks : (M + kChunk - 1) / kChunk;
     if (next.acc && (long long)blocks * kChunk < next.nacc)
         return set_error(PFSI_ERR_ARG, "ib_interp: fewer threads than per-platelet sums to clear");
-    return check_cuda(launch_pdl(k_ib_interp, dim3(blocks), dim3(kChunk), kTileBytes, s, X, U, M, chunks, perm,
-                                 (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny, c->p.nz, advect, next),
+    if (next.part && !chunks)
+        return set_error(PFSI_ERR_ARG, "ib_interp: chunk sums need the chunk table");
+    return check_cuda(launch_pdl(next.part ? k_ib_interp<true> : k_ib_interp<false>, dim3(blocks), dim3(kChunk), kTileBytes,
+                                 s, X, U, M, chunks, perm, (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny,
+                                 c->p.nz, advect, next),
                       "ib_interp");
 }
 

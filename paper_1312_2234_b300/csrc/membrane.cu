@@ -138,7 +138,7 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
 enum Slice {
     S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
-    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_PLT_RANGE, S_COUNT
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_PLT_RANGE, S_PLT_CHUNKS, S_CPART, S_COUNT
 };
 struct Layout {
     size_t off[S_COUNT];
@@ -151,7 +151,8 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
     const size_t bytes[S_COUNT] = {
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
         4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 24 * Q, 12 * N, 12 * N,
-        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N, 8 * Q};
+        64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N, 8 * Q, 8 * Q,
+        24 * ((N + kIbChunk - 1) / kIbChunk + Q)};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -688,6 +689,13 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
         if (r.y == 0) r.x = v;
         r.y += 1;
     }
+    // and one run of chunks
+    std::vector<int2> plt_chunks(nplt, make_int2(0, 0));
+    for (int ci = 0; ci < (int)chunks.size(); ++ci) {
+        int2& r = plt_chunks[node_plt[perm[chunks[ci].x]]];
+        if (r.y == 0) r.x = ci;
+        r.y += 1;
+    }
     {
         int runs = 1;
         for (int v = 1; v < n; ++v) runs += node_plt[v] != node_plt[v - 1];
@@ -722,6 +730,7 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_CHUNKS, chunks.data(), sizeof(int2) * chunks.size());
     if (!rc) rc = up(S_PERM, perm.data(), sizeof(int) * perm.size());
     if (!rc) rc = up(S_PLT_RANGE, plt_range.data(), sizeof(int2) * plt_range.size());
+    if (!rc) rc = up(S_PLT_CHUNKS, plt_chunks.data(), sizeof(int2) * plt_chunks.size());
     if (rc) return rc;
 
     mem_ctx* c = new mem_ctx();
@@ -753,6 +762,8 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->chunks = reinterpret_cast<const int2*>(at(S_CHUNKS));
     c->perm = reinterpret_cast<const int*>(at(S_PERM));
     c->plt_range = reinterpret_cast<const int2*>(at(S_PLT_RANGE));
+    c->plt_chunks = reinterpret_cast<const int2*>(at(S_PLT_CHUNKS));
+    c->cpart = reinterpret_cast<double*>(at(S_CPART));
     c->n_chunks = (int)chunks.size();
     c->acc = reinterpret_cast<double*>(at(S_ACC));
     c->coef = reinterpret_cast<float2*>(c->acc + 2 * (size_t)nplt);
@@ -822,7 +833,41 @@ __global__ void __launch_bounds__(kCentroidThreads)
     if (threadIdx.x < 3) out[3 * p + threadIdx.x] = r.y > 0 ? red[threadIdx.x][0] / (double)r.y : 0.0;
 }
 
+// Platelet centroids from the chunk sums of the advected positions that the
+// interpolation pass wrote (part[3 chunk + d], FP64 sums over the chunk's
+// nodes): one warp per platelet, lane l adding chunks l, l + 32, ... of it,
+// then a fixed shuffle tree (deterministic).
+__global__ void __launch_bounds__(128) k_centroids_from_chunks(const double* __restrict__ part,
+                                                               const int2* __restrict__ plt_chunks,
+                                                               const int2* __restrict__ range, int nplt,
+                                                               double* __restrict__ out)
+{
+    pdl_wait();
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (p >= nplt) return;   // whole warps
+    const int2 r = plt_chunks[p];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int k = lane; k < r.y; k += 32)
+        for (int d = 0; d < 3; ++d) s[d] += part[3 * (r.x + k) + d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[d] += __shfl_down_sync(0xffffffffu, s[d], o);
+    if (lane == 0) {
+        const int cnt = range[p].y;
+        for (int d = 0; d < 3; ++d) out[3 * p + d] = cnt > 0 ? s[d] / (double)cnt : 0.0;
+    }
+}
+
 }  // namespace
+
+int launch_centroids_from_chunks(MemCtx* c, double* out, cudaStream_t s)
+{
+    if (c->nplt == 0) return PFSI_OK;
+    return check_cuda(launch_pdl(k_centroids_from_chunks, dim3((c->nplt + 3) / 4), dim3(128), 0, s,
+                                 (const double*)c->cpart, c->plt_chunks, (const int2*)c->plt_range, c->nplt, out),
+                      "platelet centroids");
+}
 }  // namespace pfsi
 
 extern "C" int membrane_centroids(mem_ctx* c, const double* X, double* out_dev, void* stream)

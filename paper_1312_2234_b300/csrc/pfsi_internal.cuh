@@ -162,6 +162,8 @@ struct MemCtx {
     const int2* chunks;    // [n_chunks] (first entry of perm, count <= kIbChunk), runs of one platelet
     const int* perm;       // [n] nodes by platelet, in Morton order of the rest shape within each
     const int2* plt_range; // [nplt] (first entry of perm, count) of each platelet's nodes
+    const int2* plt_chunks;// [nplt] (first chunk, count) of each platelet's chunks
+    double* cpart;         // [3 * n_chunks] per-chunk sums of the advected positions (tracking)
     int n_chunks;
     int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
     const int* plt_anchor; // [nplt]
@@ -223,15 +225,22 @@ int launch_lb_step(LbCtx* c, cudaStream_t s);
 // kIbChunk consecutive nodes.
 int launch_ib_spread(LbCtx* c, const double* X, const float* F, int M, const int2* chunks, const int* perm,
                      int n_chunks, cudaStream_t s);
-// split (optional, with advect): the next membrane pass's input -- the hi/lo
-// float split of the advected X into split_h/split_l [3][M] and the
-// per-platelet sums acc[0..nacc) cleared -- so that pass can skip its own.
+// next (optional, with advect): the next membrane pass's input -- the hi/lo
+// float split of the advected X into h/l [3][M] and the per-platelet sums
+// acc[0..nacc) cleared -- so that pass can skip its own; and, with part, the
+// FP64 sum of the advected X over each block's nodes (part[3 block + d],
+// fixed order), from which launch_centroids_from_chunks forms the platelet
+// centroids.
 struct NextSplit {
     float* h = nullptr;
     float* l = nullptr;
     double* acc = nullptr;
     int nacc = 0;
+    double* part = nullptr;
 };
+// Platelet centroids (out[3 p + d]) from the chunk sums of the last
+// interpolation pass run with NextSplit::part = mem->cpart.
+int launch_centroids_from_chunks(MemCtx* c, double* out, cudaStream_t s);
 int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int2* chunks, const int* perm,
                      int n_chunks, cudaStream_t s, NextSplit split = NextSplit());
 // presplit: mem->xh, xl hold the split of X and the per-platelet sums are

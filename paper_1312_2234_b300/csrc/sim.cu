@@ -74,7 +74,7 @@ int enqueue_front(SimCtx* c, cudaStream_t s, bool presplit = false)
 // Bond and bridge forces, spreading, the lattice step, interpolation and
 // advection.  split_next: the interpolation also prepares the next membrane
 // pass's input (see NextSplit), which then runs with presplit.
-int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false)
+int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false, bool track = false)
 {
     int rc = PFSI_OK;
     if (c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
@@ -92,6 +92,7 @@ int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false)
         next.acc = c->mem->acc;
         next.nacc = 2 * c->mem->nplt;
     }
+    if (track) next.part = c->mem->cpart;   // chunk sums for the platelet centroids
     if (!rc)
         rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s, next);
     return rc;
@@ -108,10 +109,10 @@ int enqueue_adhesion(SimCtx* c, cudaStream_t s)
     return rc;
 }
 
-int enqueue_step(SimCtx* c, cudaStream_t s)
+int enqueue_step(SimCtx* c, cudaStream_t s, bool track = false)
 {
     int rc = enqueue_front(c, s);
-    if (!rc) rc = enqueue_middle(c, s);
+    if (!rc) rc = enqueue_middle(c, s, false, track);
     if (!rc) rc = enqueue_adhesion(c, s);
     return rc;
 }
@@ -126,33 +127,34 @@ int enqueue_step(SimCtx* c, cudaStream_t s)
 int enqueue_overlapped(SimCtx* c, cudaStream_t s, int n, double* slots = nullptr)
 {
     // slots (tracked graphs): after step k the platelet centroids go to
-    // slots + 4 n_plt k; they read X only, so they run on the side branch
-    // with the adhesion update (the last step's on the main stream)
+    // slots + 4 n_plt k, formed from the chunk sums of step k's
+    // interpolation; they run on the side branch with the adhesion update
+    // (the last step's on the main stream)
     const size_t slot = 4 * (size_t)c->mem->nplt;
+    const bool track = slots != nullptr;
     int rc = enqueue_front(c, s);
-    if (!rc) rc = enqueue_middle(c, s, n > 1);
+    if (!rc) rc = enqueue_middle(c, s, n > 1, track);
     for (int k = 1; k < n && !rc; ++k) {
         rc = check_cuda(cudaEventRecord(c->fork, s), "sim: fork");
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->side, c->fork, 0), "sim: fork");
-        if (!rc && slots)
-            rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (k - 1) * slot, c->side);
+        // step k's centroids from the chunk sums its interpolation wrote (read
+        // before step k + 1's interpolation rewrites them: the join comes first)
+        if (!rc && track) rc = launch_centroids_from_chunks(c->mem, slots + (k - 1) * slot, c->side);
         if (!rc) rc = enqueue_adhesion(c, c->side);
         if (!rc) rc = check_cuda(cudaEventRecord(c->join, c->side), "sim: join");
         if (!rc) rc = enqueue_front(c, s, true);
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(s, c->join, 0), "sim: join");
-        if (!rc) rc = enqueue_middle(c, s, k + 1 < n);
+        if (!rc) rc = enqueue_middle(c, s, k + 1 < n, track);
     }
-    if (!rc && slots) rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, slots + (n - 1) * slot, s);
+    if (!rc && track) rc = launch_centroids_from_chunks(c->mem, slots + (n - 1) * slot, s);
     if (!rc) rc = enqueue_adhesion(c, s);
     return rc;
 }
 
 int enqueue_track(SimCtx* c, cudaStream_t s, int parity)
 {
-    int rc = enqueue_step(c, s);
-    if (!rc)
-        rc = membrane_centroids(static_cast<mem_ctx*>(c->mem), c->X, c->trk_scratch + (size_t)parity * 4 * c->mem->nplt,
-                                s);
+    int rc = enqueue_step(c, s, true);
+    if (!rc) rc = launch_centroids_from_chunks(c->mem, c->trk_scratch + (size_t)parity * 4 * c->mem->nplt, s);
     return rc;
 }
 
