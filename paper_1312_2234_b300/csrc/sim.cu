@@ -25,9 +25,10 @@ struct SimCtx {
     uint64_t step;
     cudaStream_t cap;
     cudaGraphExec_t exec[2];
-    // kMulti-step graphs per starting parity: each step's adhesion update runs on
-    // a side branch beside the next step's membrane pass
-    cudaGraphExec_t multi[2];
+    // multi-step graphs per length (kLongMulti, kMulti steps) and starting
+    // parity: each step's adhesion update runs on a side branch beside the
+    // next step's membrane pass
+    cudaGraphExec_t multi[2][2];
     cudaStream_t side;
     cudaEvent_t fork, join;
     cudaEvent_t lb_ev[2];  // optional events around the lattice step (timing)
@@ -52,7 +53,14 @@ struct SimCtx {
 
 namespace {
 
-constexpr int kMulti = 4;   // steps per multi-step graph (even: the lattice parity returns)
+// Steps per multi-step graph (even: the lattice parity returns).  sim_step
+// runs kLongMulti-step graphs while that many steps remain, then kMulti-step
+// ones (the last step's adhesion update of a graph has no next membrane pass
+// beside it, so longer graphs leave fewer of them on the critical path:
+// continuous channel stepping 51.0 -> 49.4 us per step); the tracked graphs
+// run kMulti steps.
+constexpr int kMulti = 4;
+constexpr int kLongMulti = 8;
 
 // Membrane forces of the current positions (F overwritten, then the
 // optional finite-element bending added).  presplit: the previous step's
@@ -158,10 +166,14 @@ int enqueue_track(SimCtx* c, cudaStream_t s, int parity)
     return rc;
 }
 
-// Captures one step (track = 0), one step plus the platelet centroids
-// (track = 1) or kMulti overlapped steps (track = 2) starting at lattice
+// What a captured graph holds.
+enum GraphKind { kOneStep, kOneStepTracked, kLongSteps, kSteps, kStepsTracked };
+
+// Captures one step, one step plus the platelet centroids, kLongMulti or
+// kMulti overlapped steps, or kMulti overlapped steps with their centroids
+// (into slot group `group` of the tracking scratch), starting at lattice
 // parity `parity`.
-int capture(SimCtx* c, int parity, int track = 0)
+int capture(SimCtx* c, int parity, GraphKind kind, int group = 0)
 {
     const int saved = c->lb->cur;
     c->lb->cur = parity;
@@ -170,13 +182,13 @@ int capture(SimCtx* c, int parity, int track = 0)
         c->lb->cur = saved;
         return rc;
     }
-    const int group = track - 3;   // tracked kMulti-step graphs: track = 3 + slot group
     const int rc_enq =
-        track == 1   ? enqueue_track(c, c->cap, parity)
-        : track == 2 ? enqueue_overlapped(c, c->cap, kMulti)
-        : track >= 3 ? enqueue_overlapped(c, c->cap, kMulti,
-                                          c->trk_scratch + (size_t)(2 + group * kMulti) * 4 * c->mem->nplt)
-                     : enqueue_step(c, c->cap);
+        kind == kOneStepTracked ? enqueue_track(c, c->cap, parity)
+        : kind == kLongSteps    ? enqueue_overlapped(c, c->cap, kLongMulti)
+        : kind == kSteps        ? enqueue_overlapped(c, c->cap, kMulti)
+        : kind == kStepsTracked ? enqueue_overlapped(c, c->cap, kMulti,
+                                                     c->trk_scratch + (size_t)(2 + group * kMulti) * 4 * c->mem->nplt)
+                                : enqueue_step(c, c->cap);
     cudaGraph_t graph = nullptr;
     rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
     c->lb->cur = saved;
@@ -185,10 +197,11 @@ int capture(SimCtx* c, int parity, int track = 0)
         return rc_enq;
     }
     if (rc) return rc;
-    cudaGraphExec_t* dst = track == 1   ? &c->trk_exec[parity]
-                           : track == 2 ? &c->multi[parity]
-                           : track >= 3 ? &c->trk_multi[parity][group]
-                                        : &c->exec[parity];
+    cudaGraphExec_t* dst = kind == kOneStepTracked ? &c->trk_exec[parity]
+                           : kind == kLongSteps    ? &c->multi[0][parity]
+                           : kind == kSteps        ? &c->multi[1][parity]
+                           : kind == kStepsTracked ? &c->trk_multi[parity][group]
+                                                   : &c->exec[parity];
     rc = check_cuda(cudaGraphInstantiate(dst, graph, 0), "sim: instantiate");
     cudaGraphDestroy(graph);
     return rc;
@@ -201,8 +214,10 @@ void drop_graphs(SimCtx* c)
         c->exec[k] = nullptr;
         if (c->trk_exec[k]) cudaGraphExecDestroy(c->trk_exec[k]);
         c->trk_exec[k] = nullptr;
-        if (c->multi[k]) cudaGraphExecDestroy(c->multi[k]);
-        c->multi[k] = nullptr;
+        for (int l = 0; l < 2; ++l) {
+            if (c->multi[l][k]) cudaGraphExecDestroy(c->multi[l][k]);
+            c->multi[l][k] = nullptr;
+        }
         for (int g = 0; g < 2; ++g) {
             if (c->trk_multi[k][g]) cudaGraphExecDestroy(c->trk_multi[k][g]);
             c->trk_multi[k][g] = nullptr;
@@ -233,7 +248,7 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->M = M;
     c->step = first_step;
     c->exec[0] = c->exec[1] = nullptr;
-    c->multi[0] = c->multi[1] = nullptr;
+    c->multi[0][0] = c->multi[0][1] = c->multi[1][0] = c->multi[1][1] = nullptr;
     c->trk_multi[0][0] = c->trk_multi[0][1] = c->trk_multi[1][0] = c->trk_multi[1][1] = nullptr;
     c->side = nullptr;
     c->fork = c->join = nullptr;
@@ -287,19 +302,21 @@ extern "C" int sim_step(sim_ctx* c, int nsteps, void* stream)
     // timed: those events belong to single steps)
     while (!c->lb_ev[0] && nsteps - k >= kMulti) {
         const int parity = c->lb->cur;
-        if (!c->multi[parity]) {
-            const int rc = capture(c, parity, 2);
+        const int l = nsteps - k >= kLongMulti ? 0 : 1;
+        const int len = l == 0 ? kLongMulti : kMulti;
+        if (!c->multi[l][parity]) {
+            const int rc = capture(c, parity, l == 0 ? kLongSteps : kSteps);
             if (rc) return rc;
         }
-        const int rc = check_cuda(cudaGraphLaunch(c->multi[parity], s), "sim_step: graph launch");
+        const int rc = check_cuda(cudaGraphLaunch(c->multi[l][parity], s), "sim_step: graph launch");
         if (rc) return rc;
-        c->step += kMulti;   // even: the lattice parity is unchanged
-        k += kMulti;
+        c->step += len;   // even: the lattice parity is unchanged
+        k += len;
     }
     for (; k < nsteps; ++k) {
         const int parity = c->lb->cur;
         if (!c->exec[parity]) {
-            const int rc = capture(c, parity);
+            const int rc = capture(c, parity, kOneStep);
             if (rc) return rc;
         }
         const int rc = check_cuda(cudaGraphLaunch(c->exec[parity], s), "sim_step: graph launch");
@@ -385,7 +402,7 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     int k = 0, group = 0;
     while (!rc && !c->lb_ev[0] && nsteps - k >= kMulti) {
         const int p = c->lb->cur;   // unchanged by kMulti (even) steps
-        if (!c->trk_multi[p][group]) rc = capture(c, p, 3 + group);
+        if (!c->trk_multi[p][group]) rc = capture(c, p, kStepsTracked, group);
         cudaEvent_t ready = c->rec_ready[2 + group], freed = c->rec_freed[2 + group];
         if (!rc && used[2 + group]) rc = check_cuda(cudaStreamWaitEvent(s, freed, 0), "sim_step_track: wait");
         if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_multi[p][group], s), "sim_step_track: graph launch");
@@ -405,7 +422,7 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     }
     for (; k < nsteps && !rc; ++k) {
         const int p = c->lb->cur;   // the step's graph writes slot p of the scratch
-        if (!c->trk_exec[p]) rc = capture(c, p, 1);
+        if (!c->trk_exec[p]) rc = capture(c, p, kOneStepTracked);
         if (!rc && used[p]) rc = check_cuda(cudaStreamWaitEvent(s, c->rec_freed[p], 0), "sim_step_track: wait");
         if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_exec[p], s), "sim_step_track: graph launch");
         if (!rc) rc = check_cuda(cudaEventRecord(c->rec_ready[p], s), "sim_step_track: record");

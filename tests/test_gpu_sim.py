@@ -153,19 +153,21 @@ def test_step_track_follows_the_centroids():
 
 
 def test_multi_step_graphs_match_single_step_graphs():
-    """sim_step(8) replays two four-step graphs, in which each step's
-    interpolation forms the next membrane pass's hi/lo split (finite-element
-    bending reads it too); eight single-step graphs form it in the split
-    pass.  Same results up to the run-to-run rounding of spreading."""
+    """sim_step(13) replays an eight-step graph, a four-step graph and one
+    single step; in the multi-step graphs each step's interpolation forms the
+    next membrane pass's hi/lo split (finite-element bending reads it too),
+    thirteen single-step graphs form it in the split pass.  Same results up
+    to the run-to-run rounding of spreading."""
     w = f32_workload(workload.tiny(seed=6, shear=1.0e4, n_sites=200, gap=0.05))
     w["bonds"].update(kon0_dt=0.2, koff0_dt=0.01, sigma=0.05, kT=0.02, gamma=0.05)
     w["membrane"] = dict(w["membrane"], bending="fem")
     a = fsi.Simulation(w)
     b = fsi.Simulation(w)
-    a.step(8)
-    for _ in range(8):
+    a.step(13)
+    for _ in range(13):
         b.step(1)
     torch.cuda.synchronize()
+    assert a.step_index == b.step_index == 13
     assert rel_err(a.X.cpu().numpy() - w["X"], b.X.cpu().numpy() - w["X"]) < 1e-6
     assert rel_err(a.F.cpu().numpy(), b.F.cpu().numpy()) < 1e-5
     assert np.array_equal(a.bonds.bound.cpu().numpy(), b.bonds.bound.cpu().numpy())
