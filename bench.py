@@ -309,9 +309,9 @@ def run_native(args, rank, ws):
         # the step's result read back every step: the platelets' centroids
         # (the quantity a user follows, e.g. for pause times)
         nplt = int(w["mesh"]["n_plt"])
-        cbuf = torch.empty(40 * nplt, dtype=torch.float64, device=dev)
-        # instantiate the tracked graphs (both four-step slot groups and the single steps)
-        sim.step_track(10, cbuf, torch.empty(10, 3 * nplt, dtype=torch.float64).pin_memory())
+        cbuf = torch.empty(72 * nplt, dtype=torch.float64, device=dev)
+        # instantiate the tracked graphs (both eight-step slot groups and the single steps)
+        sim.step_track(18, cbuf, torch.empty(18, 3 * nplt, dtype=torch.float64).pin_memory())
         out = torch.empty(args.steps, 3 * nplt, dtype=torch.float64).pin_memory()
         # three repetitions of the whole run (upload, set-up, steps, read-back);
         # the median of their times

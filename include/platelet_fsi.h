@@ -597,9 +597,9 @@ int sim_step_record(sim_ctx* ctx, int nsteps, double* dev_ring, double* host_rin
  * per chunk of nodes, added in a fixed order) are copied to
  * host_out[k][n_plt][3] (pinned host memory,
  * nsteps * 3 * n_plt doubles) on the context's copy stream, overlapping the
- * next steps.  Steps run four per graph where they can (one strided copy per
- * four steps), one per graph otherwise.  dev_scratch: device, 40 * n_plt
- * doubles (ten slots of 4 * n_plt), kept by the context's graphs until another
+ * next steps.  Steps run eight per graph where they can (one strided copy per
+ * eight steps), one per graph otherwise.  dev_scratch: device, 72 * n_plt
+ * doubles (18 slots of 4 * n_plt), kept by the context's graphs until another
  * scratch is passed.  Returns after enqueueing; `stream` is ordered after the
  * last copy. */
 int sim_step_track(sim_ctx* ctx, int nsteps, double* dev_scratch, double* host_out, void* stream);

@@ -46,7 +46,7 @@ struct SimCtx {
     // slot `parity` of trk_scratch
     double* trk_scratch;
     cudaGraphExec_t trk_exec[2];
-    // sim_step_track: kMulti overlapped steps with their centroids, per
+    // sim_step_track: kLongMulti overlapped steps with their centroids, per
     // lattice parity and slot group (the groups alternate between launches)
     cudaGraphExec_t trk_multi[2][2];
 };
@@ -58,7 +58,7 @@ namespace {
 // ones (the last step's adhesion update of a graph has no next membrane pass
 // beside it, so longer graphs leave fewer of them on the critical path:
 // continuous channel stepping 51.0 -> 49.4 us per step); the tracked graphs
-// run kMulti steps.
+// run kLongMulti steps.
 constexpr int kMulti = 4;
 constexpr int kLongMulti = 8;
 
@@ -170,7 +170,7 @@ int enqueue_track(SimCtx* c, cudaStream_t s, int parity)
 enum GraphKind { kOneStep, kOneStepTracked, kLongSteps, kSteps, kStepsTracked };
 
 // Captures one step, one step plus the platelet centroids, kLongMulti or
-// kMulti overlapped steps, or kMulti overlapped steps with their centroids
+// kMulti overlapped steps, or kLongMulti overlapped steps with their centroids
 // (into slot group `group` of the tracking scratch), starting at lattice
 // parity `parity`.
 int capture(SimCtx* c, int parity, GraphKind kind, int group = 0)
@@ -186,8 +186,8 @@ int capture(SimCtx* c, int parity, GraphKind kind, int group = 0)
         kind == kOneStepTracked ? enqueue_track(c, c->cap, parity)
         : kind == kLongSteps    ? enqueue_overlapped(c, c->cap, kLongMulti)
         : kind == kSteps        ? enqueue_overlapped(c, c->cap, kMulti)
-        : kind == kStepsTracked ? enqueue_overlapped(c, c->cap, kMulti,
-                                                     c->trk_scratch + (size_t)(2 + group * kMulti) * 4 * c->mem->nplt)
+        : kind == kStepsTracked ? enqueue_overlapped(c, c->cap, kLongMulti,
+                                                     c->trk_scratch + (size_t)(2 + group * kLongMulti) * 4 * c->mem->nplt)
                                 : enqueue_step(c, c->cap);
     cudaGraph_t graph = nullptr;
     rc = check_cuda(cudaStreamEndCapture(c->cap, &graph), "sim: end capture");
@@ -400,24 +400,24 @@ extern "C" int sim_step_track(sim_ctx* c, int nsteps, double* dev_scratch, doubl
     // events 0, 1: single-step slots 0, 1; events 2, 3: slot groups 0, 1
     bool used[4] = {false, false, false, false};
     int k = 0, group = 0;
-    while (!rc && !c->lb_ev[0] && nsteps - k >= kMulti) {
-        const int p = c->lb->cur;   // unchanged by kMulti (even) steps
+    while (!rc && !c->lb_ev[0] && nsteps - k >= kLongMulti) {
+        const int p = c->lb->cur;   // unchanged by kLongMulti (even) steps
         if (!c->trk_multi[p][group]) rc = capture(c, p, kStepsTracked, group);
         cudaEvent_t ready = c->rec_ready[2 + group], freed = c->rec_freed[2 + group];
         if (!rc && used[2 + group]) rc = check_cuda(cudaStreamWaitEvent(s, freed, 0), "sim_step_track: wait");
         if (!rc) rc = check_cuda(cudaGraphLaunch(c->trk_multi[p][group], s), "sim_step_track: graph launch");
         if (!rc) rc = check_cuda(cudaEventRecord(ready, s), "sim_step_track: record");
         if (!rc) rc = check_cuda(cudaStreamWaitEvent(c->rec, ready, 0), "sim_step_track: wait");
-        // the kMulti steps' centroids: strided slots -> consecutive host rows
+        // the kLongMulti steps' centroids: strided slots -> consecutive host rows
         if (!rc)
             rc = check_cuda(cudaMemcpy2DAsync(host_out + (size_t)k * 3 * nplt, bytes,
-                                              dev_scratch + (2 + (size_t)group * kMulti) * slot, slot * sizeof(double),
-                                              bytes, kMulti, cudaMemcpyDeviceToHost, c->rec),
+                                              dev_scratch + (2 + (size_t)group * kLongMulti) * slot, slot * sizeof(double),
+                                              bytes, kLongMulti, cudaMemcpyDeviceToHost, c->rec),
                             "sim_step_track: copy");
         if (!rc) rc = check_cuda(cudaEventRecord(freed, c->rec), "sim_step_track: record");
         used[2 + group] = true;
-        c->step += kMulti;
-        k += kMulti;
+        c->step += kLongMulti;
+        k += kLongMulti;
         group ^= 1;
     }
     for (; k < nsteps && !rc; ++k) {

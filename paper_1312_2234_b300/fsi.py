@@ -709,7 +709,7 @@ class Simulation:
 
     def step_track(self, n, dev_scratch, host_out, stream=None):
         """n steps; after step k the platelet centroids go to host_out[k]
-        (pinned, [n][n_plt][3] float64) through dev_scratch (device, 40 n_plt)."""
+        (pinned, [n][n_plt][3] float64) through dev_scratch (device, 72 n_plt)."""
         assert host_out.is_pinned() and host_out.shape[0] >= n
         _call("sim_step_track", self.h, int(n), _ptr(dev_scratch), _ptr(host_out), _stream(stream))
 

@@ -134,13 +134,13 @@ def test_step_record_copies_every_step():
 def test_step_track_follows_the_centroids():
     """sim_step_track: after step k, host_out[k] holds each platelet's node
     centroid, as stepping one at a time and averaging X per platelet (the
-    tracked run mixes four-step graphs and single steps)."""
+    tracked run mixes eight-step graphs and single steps)."""
     w = workload.tiny(seed=8, shear=2.0e4, n_plt=2, centers=[(6.3, 9.6, 2.2), (17.4, 9.9, 3.1)], orient="flat")
     a = fsi.Simulation(w)
     b = fsi.Simulation(w)
     M = w["M"]
-    n, nplt = 11, 2   # two four-step graphs (both slot groups), then three single steps
-    scratch = torch.empty(40 * nplt, dtype=torch.float64, device="cuda")
+    n, nplt = 19, 2   # two eight-step graphs (both slot groups), then three single steps
+    scratch = torch.empty(72 * nplt, dtype=torch.float64, device="cuda")
     out = torch.zeros(n, nplt, 3, dtype=torch.float64).pin_memory()
     a.step_track(n, scratch, out)
     torch.cuda.synchronize()
