@@ -57,6 +57,17 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
+// A node takes part only if all its coordinates lie within +-1e8 lattice units
+// (false for NaN): the integer cell indices of its support then cannot
+// overflow.  A run that blew up leaves such nodes out (no force spread, no
+// velocity interpolated) instead of indexing outside the grid; sim_check
+// reports the state.
+constexpr double kFar = 1e8;
+__device__ __forceinline__ bool in_range(double x, double y, double z)
+{
+    return fabs(x) < kFar && fabs(y) < kFar && fabs(z) < kFar;
+}
+
 struct Node {
     int bx, by, bz;                 // unwrapped cell of support offset 0 on each axis
     float wx[4], wy[4], wz[4];
@@ -155,12 +166,17 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
     __shared__ float wmax[kWarps];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
-    const bool on = (int)threadIdx.x < ch.y;
-    const int m = on && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
+    const bool in_chunk = (int)threadIdx.x < ch.y;
+    const int m = in_chunk && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
     float fx = 0.f, fy = 0.f, fz = 0.f;
+    bool on = false;
+    if (in_chunk) {
+        const double x = X[m], y = X[M + m], z = X[2 * M + m];
+        on = in_range(x, y, z);
+        if (on) node_support(x, y, z, s);
+    }
     if (on) {
-        node_support(X[m], X[M + m], X[2 * M + m], s);
         fx = F[m];
         fy = F[M + m];
         fz = F[2 * M + m];
@@ -265,15 +281,17 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
     extern __shared__ float4 tile4[];
     __shared__ int rowbase[kMaxRows];
     const int2 ch = block_chunk(chunks, M);
-    const bool on = (int)threadIdx.x < ch.y;
-    const int m = on && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
+    const bool in_chunk = (int)threadIdx.x < ch.y;
+    const int m = in_chunk && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
     double x = 0.0, y = 0.0, z = 0.0;
-    if (on) {
+    bool on = false;
+    if (in_chunk) {
         x = X[m];
         y = X[M + m];
         z = X[2 * M + m];
-        node_support(x, y, z, s);
+        on = in_range(x, y, z);
+        if (on) node_support(x, y, z, s);
     }
     const Box b = block_box(s, on, nx, ny, nz);
     float ux = 0.f, uy = 0.f, uz = 0.f;

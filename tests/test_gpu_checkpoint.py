@@ -89,3 +89,21 @@ def test_checkpoint_resume_continues_the_run(storage, tmp_path):
     assert np.array_equal(b.bonds.lig_count.cpu().numpy(), a.bonds.lig_count.cpu().numpy())
     assert np.array_equal(b.bridges.partner.cpu().numpy(), a.bridges.partner.cpu().numpy())
     assert (a.bonds.bound.cpu().numpy() >= 0).any() and (a.bridges.partner.cpu().numpy() >= 0).any()
+
+
+def test_blown_up_positions_are_left_out_not_indexed():
+    """Nodes whose coordinates are not finite or lie far outside the grid (a
+    run that blew up) take no part in spreading and interpolation -- their
+    support cells would overflow the integer cell indices -- so the step
+    completes, and sim_check reports the state."""
+    w = workload.tiny(seed=2, shear=2.0e4)
+    sim = fsi.Simulation(w)
+    sim.step(2)
+    M = sim.M
+    sim.X[3] = float("nan")
+    sim.X[M + 7] = 1.0e30
+    sim.X[2 * M + 11] = -3.0e12
+    sim.step(5)
+    torch.cuda.synchronize()
+    counts, ok = sim.check(0.3)
+    assert not ok and counts[3] >= 1
