@@ -740,6 +740,15 @@ static double min_image(double d, int L)
 }
 
 /* Vector from the ligand to the receptor (minimum image in x, y). */
+/* Offset a of a ligand node from the site's node, shifted by whole box
+ * lengths into the window 1 - r .. r. */
+static int window_offset(int a, int box, int r)
+{
+    while (a > r) a -= box;
+    while (a < 1 - r) a += box;
+    return a;
+}
+
 static void bond_vector(const ora_bond_params* p, const double* r, int lig, double* d)
 {
     int li = lig % p->lig_ni, lj = lig / p->lig_ni;
@@ -784,13 +793,19 @@ static int cmp_proposal(const void* a, const void* b)
  * the existing bonds first, then formation (the per-step order stated with
  * the flow chart); a site that ruptures this step stays free until the
  * next.  Rupture: P_r = 1 - exp(-k_off dt) with the Bell rate of Eq. 12,
- * F_b = sigma |x_b - l_b|.  Formation: each free site tests the ligands of
- * the 2x2 lattice nodes around it (slot 2*dj + di) that are closer than the
- * capture distance and below capacity, with P_f = 1 - exp(-k_on dt) and
- * k_on of Eq. 13; it proposes to the lowest ligand id that succeeded.  Each
+ * F_b = sigma |x_b - l_b|.  Formation (Section 3.2: a receptor can bind a
+ * ligand within the capture distance): each free site tests every ligand of
+ * the patch, in ascending ligand id, that is closer than d_capture (minimum
+ * image in x, y) and below capacity, with P_f = 1 - exp(-k_on dt) and k_on
+ * of Eq. 13; it proposes to the lowest ligand id that succeeded.  Each
  * ligand accepts proposals in ascending site id while it has fewer than
  * max_per_ligand bonds (at most 4 receptor sites per vWF).  Draws come from
- * Philox keyed by (site, step, purpose): purpose 0 rupture, 1 + slot.
+ * Philox keyed by (site, step, purpose): purpose 0 rupture; a candidate's
+ * draw is named by the ligand's place in the 2r x 2r block of lattice nodes
+ * around the site, r = ceil(d_capture): purpose 1 + (dj + r - 1) 2r +
+ * (di + r - 1) with (di, dj) = ligand node - floor(site), wrapped into
+ * 1 - r .. r (every ligand in reach lies in that block; for d_capture <= 1
+ * the block is the 2x2 nodes around the site, purposes 1..4).
  * partner (may be NULL): bridge partner of each site; bridged sites are
  * not free. */
 void ora_bonds_step(const ora_bond_params* p, int n_sites, const int* site_tri,
@@ -825,27 +840,30 @@ void ora_bonds_step(const ora_bond_params* p, int n_sites, const int* site_tri,
         if (!was_free[s]) continue;
         double r[3];
         site_position(p, site_tri, site_w, tri, M, X, s, r);
+        /* a bond is at least as long as the height above the wall plane:
+         * no ligand is in reach above d_capture (exact for any d_capture) */
+        if (!(fabs(r[2] - p->z_wall) < p->d_capture)) continue;
         double xw = r[0] - (double)p->box_nx * floor(r[0] / (double)p->box_nx);
         double yw = r[1] - (double)p->box_ny * floor(r[1] / (double)p->box_ny);
         int i0 = (int)floor(xw), j0 = (int)floor(yw);
+        int rw = (int)ceil(p->d_capture);
+        if (rw < 1) rw = 1;
         int best = -1;
-        for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-                int gi = (i0 + di) % p->box_nx, gj = (j0 + dj) % p->box_ny;
-                if (gi < p->lig_i0 || gi >= p->lig_i0 + p->lig_ni) continue;
-                if (gj < p->lig_j0 || gj >= p->lig_j0 + p->lig_nj) continue;
-                int lig = (gj - p->lig_j0) * p->lig_ni + (gi - p->lig_i0);
-                if (lig_count[lig] >= p->max_per_ligand) continue;
-                double d[3];
-                bond_vector(p, r, lig, d);
-                double xb = norm3(d);
-                if (!(xb < p->d_capture)) continue;
-                double dev = fabs(xb - p->l_b);
-                double kon_dt = p->kon0_dt * exp(p->sigma * dev * (p->gamma - 0.5 * dev) / p->kT);
-                double Pf = -expm1(-kon_dt);
-                double u = ora_uniform(p->seed, (uint32_t)s, step, (uint32_t)(1 + 2 * dj + di));
-                if (u < Pf && (best < 0 || lig < best)) best = lig;
-            }
+        for (int lig = 0; lig < p->lig_ni * p->lig_nj; ++lig) {
+            if (lig_count[lig] >= p->max_per_ligand) continue;
+            double d[3];
+            bond_vector(p, r, lig, d);
+            double xb = norm3(d);
+            if (!(xb < p->d_capture)) continue;
+            double dev = fabs(xb - p->l_b);
+            double kon_dt = p->kon0_dt * exp(p->sigma * dev * (p->gamma - 0.5 * dev) / p->kT);
+            double Pf = -expm1(-kon_dt);
+            int di = window_offset(p->lig_i0 + lig % p->lig_ni - i0, p->box_nx, rw);
+            int dj = window_offset(p->lig_j0 + lig / p->lig_ni - j0, p->box_ny, rw);
+            uint32_t purpose = (uint32_t)(1 + (dj + rw - 1) * 2 * rw + (di + rw - 1));
+            double u = ora_uniform(p->seed, (uint32_t)s, step, purpose);
+            if (u < Pf && best < 0) best = lig;   /* ascending id: the first success is the lowest */
+        }
         if (best >= 0) {
             props[np].lig = best;
             props[np].site = s;

@@ -170,3 +170,81 @@ def test_bond_force_eq14(oracle_lib):
     d = r - np.array([1, 1, -0.5])
     f = -2.5 * (np.linalg.norm(d) - 0.64) * d / np.linalg.norm(d)
     assert np.allclose(F.reshape(3, 3).T, np.outer([0.2, 0.5, 0.3], f), atol=1e-15)
+
+
+def _brute_force_first_ligand(p, pts):
+    """Every ligand node of the patch at its minimum-image distance from each
+    point: the ids in reach (ascending) per point, by a scan of the whole
+    patch."""
+    li = np.arange(p["lig_ni"] * p["lig_nj"])
+    gx = p["lig_i0"] + li % p["lig_ni"]
+    gy = p["lig_j0"] + li // p["lig_ni"]
+    out = []
+    for x, y, z in pts:
+        dx = x - gx
+        dx -= p["box_nx"] * np.round(dx / p["box_nx"])
+        dy = y - gy
+        dy -= p["box_ny"] * np.round(dy / p["box_ny"])
+        d = np.sqrt(dx * dx + dy * dy + (z - p["z_wall"]) ** 2)
+        out.append(li[d < p["d_capture"]])
+    return out
+
+
+def test_capture_beyond_one_spacing_matches_brute_force(oracle_lib):
+    """d_capture = 1.7 lattice spacings (128 nm at a lattice spacing of
+    75 nm): a free site may reach up to a few dozen ligands, outside the 2x2
+    nodes around it.  With P_f = 1 every free site proposes to the lowest
+    ligand id within reach, and each ligand takes the four lowest site ids:
+    the same bonds as a scan of the whole patch, including across the
+    periodic seam (patch columns 0..7 of a 10-wide box)."""
+    p = bond_params(lig_ni=8, lig_nj=7, box_nx=10, box_ny=9, d_capture=1.7, l_b=1.0, kon0_dt=1e6)
+    rng = np.random.default_rng(3)
+    n = 400
+    pts = np.column_stack([rng.uniform(0, 10, n), rng.uniform(0, 9, n), rng.uniform(-0.5, 1.4, n)])
+    pts[:20, 0] += 10.0 * rng.integers(-2, 3, 20)          # unwrapped coordinates
+    X, tri, st, sw = sites_at(pts)
+    bound = np.full(n, -1, np.int32)
+    lig = np.zeros(p["lig_ni"] * p["lig_nj"], np.int32)
+    oracle_lib.bonds_step(p, st, sw, tri, X, bound, lig, 0)
+    reach = _brute_force_first_ligand(p, pts)
+    # the case the 2x2 block would miss occurs: a lowest in-reach ligand
+    # outside the nodes floor(x) + {0, 1}, floor(y) + {0, 1}
+    outside = 0
+    for (x, y, _), ids in zip(pts, reach):
+        if len(ids):
+            l0 = ids[0]
+            di = (p["lig_i0"] + l0 % p["lig_ni"] - math.floor(x % 10)) % 10
+            dj = (p["lig_j0"] + l0 // p["lig_ni"] - math.floor(y % 9)) % 9
+            outside += not (di in (0, 1) and dj in (0, 1))
+    assert outside > 20 and max(len(r) for r in reach) > 4
+    want = np.full(n, -1, np.int32)
+    taken = np.zeros_like(lig)
+    for s in range(n):                          # ascending site id per ligand
+        if len(reach[s]) and taken[reach[s][0]] < 4:
+            want[s] = reach[s][0]
+            taken[reach[s][0]] += 1
+    assert np.array_equal(bound, want)
+    assert np.array_equal(lig, taken)
+
+
+def test_every_candidate_in_reach_draws_once(oracle_lib):
+    """With sigma = 0, k_on = k_on0 for every candidate, so a site with n
+    ligands in reach proposes with probability 1 - (1 - p)^n and picks the
+    k-th lowest of them with probability p (1 - p)^(k-1): n independent
+    draws, one per ligand, the lowest id kept.  At d_capture = 1.5 a site
+    0.1 above the wall plane over a node centre reaches 9 ligands (offsets
+    in {-1, 0, 1}^2); with capacity unlimited 20000 sites give the law."""
+    p = bond_params(d_capture=1.5, sigma=0.0, kon0_dt=0.15)
+    n = 20000
+    X, tri, st, sw = sites_at([[4.0, 4.0, -0.5 + 0.1]] * n)
+    bound = np.full(n, -1, np.int32)
+    lig = np.full(64, -10 ** 6, np.int32)
+    oracle_lib.bonds_step(p, st, sw, tri, X, bound, lig, 7)
+    reach = _brute_force_first_ligand(p, [[4.0, 4.0, -0.4]])[0]
+    assert len(reach) == 9
+    P = -math.expm1(-p["kon0_dt"])
+    probs = [P * (1 - P) ** k for k in range(9)] + [(1 - P) ** 9]
+    counts = [int((bound == l).sum()) for l in reach] + [int((bound < 0).sum())]
+    exp = np.array(probs) * n
+    chi2 = float((((np.array(counts) - exp) ** 2) / exp).sum())
+    assert chi2 < 33.7, (counts, exp)      # 9 d.o.f., p ~ 1e-4
