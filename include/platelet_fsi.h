@@ -187,13 +187,17 @@ int lb_check(lb_ctx* ctx, float u_max, unsigned long long* dev_scratch4, long lo
  * ===================================================================== */
 /* g[cell] += F_m phi(x - X_m) phi(y - Y_m) phi(z - Z_m) over the 4x4x4
  * support of every node (Eq. 34-35, h = 1); the support wraps in x, y and is
- * cut at the walls.  Sets the row flags of the cells touched.
+ * cut at the walls.  Sets the row flags of the cells touched.  A node with a
+ * coordinate that is not finite or lies 1e8 lattice units or more from the
+ * origin spreads nothing.
  * X: device double[3][M] (structure of arrays), F: device float[3][M]. */
 int ib_spread(lb_ctx* ctx, const double* X, const float* F, int M, void* stream);
 
 /* U_m = sum over the support of v phi phi phi (Eq. 33) with v from the last
  * lb_step; if advect != 0, X += U (Eq. 31, forward Euler, dt = 1).  Clears
- * the row flags of the cells visited.  U: device float[3][M]. */
+ * the row flags of the cells visited.  A node with a coordinate that is not
+ * finite or lies 1e8 lattice units or more from the origin gets U = NaN and
+ * keeps its position.  U: device float[3][M]. */
 int ib_interp(lb_ctx* ctx, double* X, float* U, int M, int advect, void* stream);
 
 /* ===================================================================== *
@@ -260,8 +264,10 @@ int membrane_measure(mem_ctx* ctx, const double* X, double* out_host, void* stre
  * the library holds until the process exits.  It allocates and frees nothing.
  * Contexts with more than PFSI_STATIC_MAX_PLATELETS platelets are rejected
  * with PFSI_ERR_ARG.  The first call on a device (with that device current)
- * looks up the array's device address; make that first call before any stream
- * capture.  Every call shares the one array and clears it first: calls that
+ * looks up the array's device address and keeps it until the process exits;
+ * make that first call before any stream capture, and do not call this entry
+ * point after cudaDeviceReset (the reloaded array may live at another address
+ * than the one kept).  Every call shares the one array and clears it first: calls that
  * overlap on the GPU (other streams or host threads) race and must be
  * serialised by the caller.  Synchronises on `stream`. */
 #define PFSI_STATIC_MAX_PLATELETS 8192
@@ -275,7 +281,8 @@ typedef struct {
     int box_nx, box_ny;                 /* periodic lengths */
     int max_per_ligand;                 /* receptor sites per vWF (4), 1..32 */
     double z_wall;
-    double sigma, l_b, d_capture;       /* Eq. 13-14; d_capture < 1 */
+    double sigma, l_b, d_capture;       /* Eq. 13-14; 0 < d_capture <= 8 and
+                                           2 ceil(d_capture) <= box_nx, box_ny */
     double gamma, kT;                   /* Eq. 12-13 */
     double kon0_dt, koff0_dt;           /* k_on0 dt, k_off0 dt */
     uint64_t seed;                      /* Philox4x32-10 key */
@@ -301,12 +308,15 @@ int bonds_forces(bond_ctx* ctx, const double* X, float* F, int M, void* stream);
 
 /* One Monte-Carlo update at time step `step`: rupture of bound sites with
  * P_r = 1 - exp(-k_off dt), Bell k_off (Eq. 12); then each site free at the
- * start of the step tests the ligands of the 2x2 nodes around it that are
- * within d_capture and below capacity with P_f = 1 - exp(-k_on dt), k_on of
- * Eq. 13, proposing to the lowest ligand id that succeeded; each ligand
- * accepts proposals in ascending site id up to max_per_ligand.  Uniforms
- * come from Philox4x32-10 keyed by seed with counter (site, step lo, step
- * hi, purpose): purpose 0 rupture, 1 + (2 dj + di) formation. */
+ * start of the step tests every ligand within d_capture (minimum image in
+ * x, y) and below capacity with P_f = 1 - exp(-k_on dt), k_on of Eq. 13,
+ * proposing to the lowest ligand id that succeeded; each ligand accepts
+ * proposals in ascending site id up to max_per_ligand.  Uniforms come from
+ * Philox4x32-10 keyed by seed with counter (site, step lo, step hi,
+ * purpose): purpose 0 rupture; a candidate ligand at node (i0 + di,
+ * j0 + dj), (i0, j0) = floor of the site's wrapped (x, y), r =
+ * ceil(d_capture), di and dj in 1 - r .. r, draws with purpose
+ * 1 + (dj + r - 1) 2r + (di + r - 1) (for d_capture <= 1: 1 + 2 dj + di). */
 int bonds_step(bond_ctx* ctx, const double* X, int M, uint64_t step, void* stream);
 
 /* Cumulative event counts and overflow status.  out_host[3] = {ruptures,
@@ -620,9 +630,13 @@ int sim_set_surrogate(sim_ctx* ctx, sg_ctx* sg, const void* params);
 int sim_set_fem_bending(sim_ctx* ctx, fem_ctx* fem, float k0);
 
 /* lb_check of the simulation's lattice plus a scan of the node positions:
- * out_host[4] = {non-finite cells, rho <= 0, |u| > u_max, nodes with a
- * non-finite position}.  Returns PFSI_ERR_UNSTABLE if any count is nonzero.
- * dev_scratch4 as for lb_check.  Synchronises. */
+ * out_host[4] = {non-finite cells, rho <= 0, |u| > u_max, node coordinates
+ * (entries of X) that are not finite or lie 1e8 lattice units or more from
+ * the origin}.  Nodes with such a coordinate take no part in spreading and
+ * interpolation (their support cells would overflow the cell indices): ib_interp
+ * sets their velocity to NaN and leaves their position as it is.  Returns
+ * PFSI_ERR_UNSTABLE if any count is nonzero.  dev_scratch4 as for lb_check.
+ * Synchronises. */
 int sim_check(sim_ctx* ctx, float u_max, unsigned long long* dev_scratch4, long long* out_host, void* stream);
 
 /* Adds the platelet-platelet bridges to every following step: their spring

@@ -3,9 +3,10 @@
 // Per step, three kernels:
 //   rupture  (one thread per site)    bound sites break with P_r = 1 - exp(-k_off dt),
 //                                     k_off = k_off0 exp(gamma F_b / kT), F_b = sigma |x_b - l_b| (Eq. 12)
-//   propose  (one thread per site)    sites free at the start of the step test the
-//                                     ligands of the 2x2 lattice nodes around them
-//                                     (within d_capture, below capacity) with
+//   propose  (one thread per site)    sites free at the start of the step test every
+//                                     ligand within d_capture and below capacity (all
+//                                     lie in the 2r x 2r lattice nodes around the site,
+//                                     r = ceil(d_capture); 2x2 for d_capture <= 1) with
 //                                     P_f = 1 - exp(-k_on dt), k_on of Eq. 13, and
 //                                     propose to the lowest ligand id that succeeded
 //   resolve  (one thread per ligand)  accepts its proposals in ascending site id up
@@ -16,6 +17,8 @@
 // (receptor position, bond length, rates) is FP64 with explicitly rounded
 // operations in the order of the plain restatement, so that an event differs
 // only when a uniform lands within an ulp of its probability.
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "adhesion.cuh"
@@ -76,6 +79,36 @@ __global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, u
     }
 }
 
+// Candidate (di, dj) of the window around node (i0, j0): the ligand there,
+// if it is in the patch, below capacity and in reach, gets its own draw
+// (purpose 1 + (dj + r - 1) 2r + (di + r - 1)); the lowest successful
+// ligand id is kept in best.
+__device__ __forceinline__ void propose_candidate(const BondCtx& c, const SitePos& r, int s, uint64_t step, int i0,
+                                                  int j0, int di, int dj, int rw, int& best)
+{
+    const bond_params& p = c.p;
+    int gi = (i0 + di) % p.box_nx, gj = (j0 + dj) % p.box_ny;
+    if (gi < 0) gi += p.box_nx;
+    if (gj < 0) gj += p.box_ny;
+    if (gi < p.lig_i0 || gi >= p.lig_i0 + p.lig_ni) return;
+    if (gj < p.lig_j0 || gj >= p.lig_j0 + p.lig_nj) return;
+    const int lig = (gj - p.lig_j0) * p.lig_ni + (gi - p.lig_i0);
+    if (c.lig_count[lig] >= p.max_per_ligand) return;
+    double d[3];
+    bond_vector(p, r, lig, d);
+    const double xb = norm3_rn(d[0], d[1], d[2]);
+    if (!(xb < p.d_capture)) return;
+    const double dev = fabs(__dsub_rn(xb, p.l_b));
+    const double ex = __ddiv_rn(__dmul_rn(__dmul_rn(p.sigma, dev), __dsub_rn(p.gamma, __dmul_rn(0.5, dev))), p.kT);
+    const double kon_dt = __dmul_rn(p.kon0_dt, exp(ex));
+    const double Pf = -expm1(-kon_dt);
+    const double u = uniform53(p.seed, (uint32_t)s, step, (uint32_t)(1 + (dj + rw - 1) * 2 * rw + (di + rw - 1)));
+    if (u < Pf && (best < 0 || lig < best)) best = lig;
+}
+
+// kR: the window half-width r at compile time (1: d_capture <= 1, the
+// configurations' 0.64), or 0 to take it from the context at run time.
+template <int kR>
 __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
                                const unsigned long long* __restrict__ step_dev)
 {
@@ -109,27 +142,17 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
     const double xw = __dsub_rn(r.x, __dmul_rn(bx, floor(__ddiv_rn(r.x, bx))));
     const double yw = __dsub_rn(r.y, __dmul_rn(by, floor(__ddiv_rn(r.y, by))));
     const int i0 = (int)floor(xw), j0 = (int)floor(yw);
+    const int rw = kR > 0 ? kR : c.window;
     int best = -1;
+    if (kR > 0) {
 #pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
+        for (int dj = 1 - kR; dj <= kR; ++dj)
 #pragma unroll
-        for (int di = 0; di < 2; ++di) {
-            const int gi = (i0 + di) % p.box_nx, gj = (j0 + dj) % p.box_ny;
-            if (gi < p.lig_i0 || gi >= p.lig_i0 + p.lig_ni) continue;
-            if (gj < p.lig_j0 || gj >= p.lig_j0 + p.lig_nj) continue;
-            const int lig = (gj - p.lig_j0) * p.lig_ni + (gi - p.lig_i0);
-            if (c.lig_count[lig] >= p.max_per_ligand) continue;
-            double d[3];
-            bond_vector(p, r, lig, d);
-            const double xb = norm3_rn(d[0], d[1], d[2]);
-            if (!(xb < p.d_capture)) continue;
-            const double dev = fabs(__dsub_rn(xb, p.l_b));
-            const double ex = __ddiv_rn(__dmul_rn(__dmul_rn(p.sigma, dev), __dsub_rn(p.gamma, __dmul_rn(0.5, dev))), p.kT);
-            const double kon_dt = __dmul_rn(p.kon0_dt, exp(ex));
-            const double Pf = -expm1(-kon_dt);
-            const double u = uniform53(p.seed, (uint32_t)s, step, (uint32_t)(1 + 2 * dj + di));
-            if (u < Pf && (best < 0 || lig < best)) best = lig;
-        }
+            for (int di = 1 - kR; di <= kR; ++di) propose_candidate(c, r, s, step, i0, j0, di, dj, rw, best);
+    } else {
+        for (int dj = 1 - rw; dj <= rw; ++dj)
+            for (int di = 1 - rw; di <= rw; ++di) propose_candidate(c, r, s, step, i0, j0, di, dj, rw, best);
+    }
     if (best >= 0) {
         const int slot = atomicAdd(&c.nprop[best], 1);
         if (slot < kMaxCand)
@@ -224,8 +247,8 @@ int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                                        step_dev),
                             "bonds_step: rupture");
         if (rc) return rc;
-        rc = check_cuda(launch_pdl(k_bond_propose, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, M, step_host,
-                                   step_dev),
+        rc = check_cuda(launch_pdl(c->window == 1 ? k_bond_propose<1> : k_bond_propose<0>, dim3(blocks_for(c->R, 256)),
+                                   dim3(256), 0, s, *c, X, M, step_host, step_dev),
                         "bonds_step: propose");
         if (rc) return rc;
     }
@@ -327,8 +350,12 @@ static int check_bond_params(const bond_params* p, const char* who)
         return set_error(PFSI_ERR_ARG, std::string(who) + ": ligand patch outside the box");
     if (p->max_per_ligand < 1 || p->max_per_ligand > 32)
         return set_error(PFSI_ERR_ARG, std::string(who) + ": max_per_ligand must be 1..32");
-    if (!(p->d_capture < 1.0))
-        return set_error(PFSI_ERR_ARG, std::string(who) + ": d_capture must be below one lattice spacing");
+    // every ligand in reach lies in the 2r x 2r nodes around a site; each
+    // must appear there once
+    if (!(p->d_capture > 0.0) || !(p->d_capture <= 8.0) || 2 * (int)std::ceil(p->d_capture) > p->box_nx ||
+        2 * (int)std::ceil(p->d_capture) > p->box_ny)
+        return set_error(PFSI_ERR_ARG, std::string(who) + ": d_capture must be in (0, 8] and 2 ceil(d_capture) "
+                                                          "at most the box lengths");
     if (!(p->kT > 0.0)) return set_error(PFSI_ERR_ARG, std::string(who) + ": kT must be positive");
     return PFSI_OK;
 }
@@ -355,6 +382,7 @@ extern "C" int bonds_create(const bond_params* p, int n_sites, const int* site_t
     if (ws_bytes < ws_bytes_for(L)) return set_error(PFSI_ERR_ARG, "bonds_create: workspace too small");
     bond_ctx* c = new bond_ctx();
     c->p = *p;
+    c->window = std::max(1, (int)std::ceil(p->d_capture));
     c->R = n_sites;
     c->L = L;
     c->site_tri = site_tri;

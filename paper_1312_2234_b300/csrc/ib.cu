@@ -57,15 +57,14 @@ __device__ __forceinline__ int wrap(int i, int n)
     return i < 0 ? i + n : i;
 }
 
-// A node takes part only if all its coordinates lie within +-1e8 lattice units
-// (false for NaN): the integer cell indices of its support then cannot
-// overflow.  A run that blew up leaves such nodes out (no force spread, no
-// velocity interpolated) instead of indexing outside the grid; sim_check
-// reports the state.
-constexpr double kFar = 1e8;
+// A node takes part only if all its coordinates lie within +-kFarCoord
+// lattice units (false for NaN): the integer cell indices of its support then
+// cannot overflow.  A run that blew up leaves such nodes out (no force
+// spread; its velocity reads NaN and its position is not advected) instead of
+// indexing outside the grid; sim_check reports the state.
 __device__ __forceinline__ bool in_range(double x, double y, double z)
 {
-    return fabs(x) < kFar && fabs(y) < kFar && fabs(z) < kFar;
+    return coord_in_range(x) && coord_in_range(y) && coord_in_range(z);
 }
 
 struct Node {
@@ -369,6 +368,28 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
         }
     }
     double xn[3] = {0.0, 0.0, 0.0};
+    if (in_chunk && !on) {
+        // left out: its velocity reads NaN and its position stays as it is
+        // (also in the split and the block's position sum), so that neither
+        // U nor a platelet centroid looks valid; sim_check counts it
+        const float qnan = __int_as_float(0x7fffffff);
+        U[m] = qnan;
+        U[M + m] = qnan;
+        U[2 * M + m] = qnan;
+        if (advect) {
+            xn[0] = x;
+            xn[1] = y;
+            xn[2] = z;
+            if (next.h) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    const float h = __double2float_rn(xn[d]);
+                    next.h[d * M + m] = h;
+                    next.l[d * M + m] = __double2float_rn(xn[d] - (double)h);
+                }
+            }
+        }
+    }
     if (on) {
         U[m] = ux;
         U[M + m] = uy;

@@ -181,6 +181,7 @@ struct BondCtx {
     bond_params p;
     int R;                 // sites
     int L;                 // ligands
+    int window;            // r = ceil(d_capture) >= 1: ligands in reach lie in the 2r x 2r nodes around a site
     const int* site_tri;
     const double* site_w;
     const int* tri;
@@ -208,6 +209,13 @@ struct TetherCtx {
 const TetherCtx* tether_internal(const tether_ctx* t);
 // After the adhesion update: the step count is *now_dev if now_dev, else now_host.
 int launch_tether_update(const TetherCtx* c, const unsigned long long* now_dev, uint64_t now_host, cudaStream_t s);
+
+// A node coordinate takes part in spreading and interpolation only if it lies
+// within +-kFarCoord lattice units (false for NaN): the integer cell indices
+// of its support then cannot overflow.  sim_check counts the coordinates
+// outside that range (a run that blew up).
+constexpr double kFarCoord = 1e8;
+__device__ __forceinline__ bool coord_in_range(double x) { return fabs(x) < kFarCoord; }
 
 // Nodes per block of the IB kernels (also the largest chunk of the membrane's
 // chunk table).

@@ -449,7 +449,7 @@ namespace {
 __global__ void k_sim_check_x(const double* __restrict__ X, int n3, unsigned long long* __restrict__ cnt)
 {
     unsigned long long c = 0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += gridDim.x * blockDim.x) c += !isfinite(X[t]);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n3; t += gridDim.x * blockDim.x) c += !coord_in_range(X[t]);
     if (c) atomicAdd(cnt, c);
 }
 }  // namespace
@@ -474,7 +474,9 @@ extern "C" int sim_check(sim_ctx* c, float u_max, unsigned long long* dev_scratc
     if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "sim_check: synchronise");
     if (rc) return rc;
     out_host[3] = (long long)h;
-    if (h) return set_error(PFSI_ERR_UNSTABLE, "sim_check: " + std::to_string(h) + " non-finite node coordinates");
+    if (h)
+        return set_error(PFSI_ERR_UNSTABLE,
+                         "sim_check: " + std::to_string(h) + " node coordinates non-finite or beyond 1e8 lattice units");
     return rc_lb;
 }
 

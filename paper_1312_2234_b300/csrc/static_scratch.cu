@@ -14,7 +14,9 @@
 // GPU that loads this library until the process exits.  Its name, in host
 // code, is only a host-side stand-in: the device address is looked up once
 // per device with cudaGetSymbolAddress (on the first call made while that
-// device is current) and passed to the kernels.
+// device is current), kept until the process exits and passed to the
+// kernels.  A cudaDeviceReset unloads the module; the address kept from
+// before it is then stale, so the entry point must not be used after one.
 #include <mutex>
 
 #include "pfsi_internal.cuh"

@@ -128,7 +128,14 @@ def test_bond_workspace_query_and_validation(L):
     p.lig_i0 = 30
     with pytest.raises(RuntimeError, match="patch"):
         fsi.bonds_query_workspace(p, 100)
-    p = fsi.bond_params_from(dict(w["bonds"], d_capture=1.5))
+    # capture beyond one lattice spacing is accepted (the 2r x 2r window)
+    assert fsi.bonds_query_workspace(fsi.bond_params_from(dict(w["bonds"], d_capture=1.5)), 100) > 0
+    for bad in (0.0, -0.5, 8.5, float("nan"), 16.5):
+        p = fsi.bond_params_from(dict(w["bonds"], d_capture=bad))
+        with pytest.raises(RuntimeError, match="d_capture"):
+            fsi.bonds_query_workspace(p, 100)
+    # the window must fit the box once: 2 ceil(d_capture) <= box lengths
+    p = fsi.bond_params_from(dict(w["bonds"], d_capture=4.5, box_nx=9, lig_i0=0, lig_ni=8))
     with pytest.raises(RuntimeError, match="d_capture"):
         fsi.bonds_query_workspace(p, 100)
 

@@ -79,3 +79,26 @@ def test_bond_forces_parity():
     Fg = Fd.cpu().numpy()
     assert np.max(np.abs(F)) > 0
     assert np.max(np.abs(Fg - F)) < 1e-5 * np.max(np.abs(F))
+
+
+@pytest.mark.parametrize("d_capture", [1.0, 1.7])
+def test_events_bit_exact_capture_beyond_one_spacing(d_capture):
+    """Capture distances of one and more lattice spacings (128 nm on a finer
+    lattice): each site's candidates come from the 2r x 2r nodes around it
+    (r = ceil(d_capture); 4 x 4 at 1.7), every draw and event as the
+    oracle's scan of the whole patch."""
+    w = sheet_workload(kon0_dt=0.05, koff0_dt=0.05, sigma=0.05, kT=0.02, gamma=0.05, d_capture=d_capture,
+                       l_b=0.8 * d_capture)
+    b, bound, hist = run_both(w, 30)
+    nr = sum(h[0] for h in hist)
+    nf = sum(h[1] for h in hist)
+    assert nf > 100 and nr > 20, (nr, nf)
+    rc, counters = b.status()
+    assert rc == 0 and counters[0] == nr and counters[1] == nf
+
+
+def test_capture_distance_argument_checks():
+    w = sheet_workload()
+    for bad in (0.0, -1.0, 8.5, float("nan")):
+        with pytest.raises(RuntimeError):
+            run_both(dict(w, bonds=dict(w["bonds"], d_capture=bad)), 1)

@@ -95,15 +95,62 @@ def test_blown_up_positions_are_left_out_not_indexed():
     """Nodes whose coordinates are not finite or lie far outside the grid (a
     run that blew up) take no part in spreading and interpolation -- their
     support cells would overflow the integer cell indices -- so the step
-    completes, and sim_check reports the state."""
+    completes, and sim_check counts exactly the planted coordinates, NaN or
+    far but finite."""
     w = workload.tiny(seed=2, shear=2.0e4)
     sim = fsi.Simulation(w)
     sim.step(2)
     M = sim.M
-    sim.X[3] = float("nan")
     sim.X[M + 7] = 1.0e30
     sim.X[2 * M + 11] = -3.0e12
+    sim.X[19] = 1.0e8
+    counts, ok = sim.check(0.3)
+    assert not ok and counts[3] == 3, counts
     sim.step(5)
     torch.cuda.synchronize()
     counts, ok = sim.check(0.3)
-    assert not ok and counts[3] >= 1
+    assert not ok and counts[3] == 3, counts
+    U = sim.U.reshape(3, M).cpu().numpy()
+    assert np.isnan(U[:, [7, 11, 19]]).all()
+    sim.X[3] = float("nan")
+    counts, ok = sim.check(0.3)
+    assert not ok and counts[3] == 4, counts
+
+
+def test_left_out_nodes_do_not_disturb_the_others():
+    """Spreading and interpolation with a few nodes planted far away give the
+    other nodes the same result as a run without the planted nodes whose
+    force is zero (their chunks keep the tile of the nodes in range), within
+    the run-to-run rounding of spreading; the planted nodes read U = NaN and
+    keep their positions."""
+    w = workload.config_channel(seed=0)
+    M = w["M"]
+    runs = []
+    rng = np.random.default_rng(4)
+    F = torch.as_tensor(rng.standard_normal(3 * M).astype(np.float32) * 1e-4).cuda()
+    planted = np.array([5, 1300, 20000])
+    F.reshape(3, M)[:, planted] = 0.0
+    for plant in (False, True):
+        lat = fsi.Lattice(w["grid"]["nx"], w["grid"]["ny"], w["grid"]["nz"], w["grid"]["tau"], w["grid"]["u_top"])
+        lat.init_shear()
+        X = torch.as_tensor(np.ascontiguousarray(w["X"])).cuda()
+        if plant:
+            X.reshape(3, M)[0, planted[0]] = float("nan")
+            X.reshape(3, M)[1, planted[1]] = 2.0e8
+            X.reshape(3, M)[2, planted[2]] = -1.0e20
+        Xs = X.clone()
+        U = torch.zeros(3 * M, device="cuda")
+        fsi.ib_spread(lat.h, X, F, M)
+        fsi.lb_step(lat.h, 1)
+        fsi.ib_interp(lat.h, X, U, M, advect=True)
+        torch.cuda.synchronize()
+        runs.append((lat.export().cpu().numpy(), U.reshape(3, M).cpu().numpy(), X.reshape(3, M).cpu().numpy(),
+                     Xs.reshape(3, M).cpu().numpy()))
+    (f0, U0, X0, _), (f1, U1, X1, Xs1) = runs
+    keep = np.ones(M, bool)
+    keep[planted] = False
+    assert rel(f1, f0) < 1e-6
+    assert rel(U1[:, keep], U0[:, keep]) < 1e-6
+    assert np.isfinite(U1[:, keep]).all() and np.isnan(U1[:, planted]).all()
+    assert np.array_equal(X1[:, planted], Xs1[:, planted], equal_nan=True)
+    assert rel(X1[:, keep] - Xs1[:, keep], X0[:, keep] - runs[0][3][:, keep]) < 1e-6

@@ -11,9 +11,10 @@ previous field by the element size again: a few u for normals and areas,
 ~10 u for K and K_G, ~100 u for Lap_S K and the force (three derivative
 levels of the positions), each relative to the field's largest value.
 Measured on the deformed channel meshes: 3e-7 (normals), 2e-7 (areas),
-9e-7 (K), 1.8e-6 (K_G), 5.3e-6 (Lap_S K), 5.1e-6 (force); the bounds below
-are about ten times the u-counts (1e-6, 2e-5, 5e-5).  The coupled step keeps
-the 1e-5 bound of the other coupled parity tests (measured 3e-7 .. 6e-7)."""
+1.1e-6 (K), 1.9e-6 (K_G), 6.3e-6 (Lap_S K), 6.5e-6 (force).  The membrane
+fields are held to the 1e-5 relative bound of the other membrane parity
+tests (1e-6 for normals and areas); the coupled step keeps the same 1e-5
+(measured 3e-7 .. 6e-7)."""
 import numpy as np
 import pytest
 import torch
@@ -71,8 +72,8 @@ def test_fields_and_forces_match_the_oracle():
     errs["F"] = rel(F.reshape(3, -1).T.cpu().numpy(), Fr)
     print("fem rel errors", errs)
     assert errs["n"] < 1e-6 and errs["A"] < 1e-6
-    assert errs["K"] < 2e-5 and errs["KG"] < 2e-5
-    assert errs["lapK"] < 5e-5 and errs["F"] < 5e-5
+    assert errs["K"] < 1e-5 and errs["KG"] < 1e-5
+    assert errs["lapK"] < 1e-5 and errs["F"] < 1e-5
     # SCE nodes (no element) get nothing
     assert float(F.reshape(3, -1)[:, torch.as_tensor(~mem).cuda()].abs().max()) == 0.0
 
@@ -91,7 +92,8 @@ def test_far_from_the_origin_and_accumulate():
     fb.forces(k0, Xd, F0)
     fb.forces(k0, Xf, F1)
     scale = float(F0.abs().max())
-    assert float((F1 - F0).abs().max()) < 5e-5 * scale
+    print("fem translated rel change", float((F1 - F0).abs().max()) / scale)
+    assert float((F1 - F0).abs().max()) < 1e-5 * scale
     base = torch.randn_like(F0)
     F2 = base.clone()
     fb.forces(k0, Xd, F2, accumulate=True)

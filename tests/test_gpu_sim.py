@@ -28,16 +28,28 @@ def rel_err(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def compare(w, steps, tol=TOL):
+def compare(w, steps, tol=TOL, checkpoints=()):
+    """Runs both sides `steps` steps and compares every field at the end
+    within `tol`; checkpoints: (step, tol) pairs compared on the way."""
     w = f32_workload(w)
     sim = fsi.Simulation(w)
     ora = oracle.Sim(w)
-    X0 = w["X"].copy()
-    sim.step(steps)
-    for _ in range(steps):
-        ora.step()
-    torch.cuda.synchronize()
+    done = 0
+    for n, t in sorted(checkpoints) + [(steps, tol)]:
+        sim.step(n - done)
+        for _ in range(n - done):
+            ora.step()
+        done = n
+        torch.cuda.synchronize()
+        check_fields(w, sim, ora, n, t)
+    return sim, ora
+
+
+def check_fields(w, sim, ora, steps, tol):
+    X0 = w["X"]
     Xg = sim.X.cpu().numpy()
+    print("step %d: displacement %.2e velocity %.2e" % (steps, rel_err(Xg - X0, ora.X - X0),
+                                                         rel_err(sim.U.cpu().numpy(), ora.U)))
     assert rel_err(Xg - X0, ora.X - X0) < tol
     assert rel_err(sim.U.cpu().numpy(), ora.U) < tol
     # FP32 forces at the tiny strains of a coupled run: relative bound plus an
@@ -53,19 +65,39 @@ def compare(w, steps, tol=TOL):
     fg = sim.lattice.current().cpu().numpy()
     assert rel_err(fg, ora.f.reshape(19, -1) - wq[:, None]) < tol
     assert sim.step_index == steps
-    return sim, ora
 
 
 def test_tiny_many_steps():
     compare(workload.tiny(seed=3, shear=3.0e4), 200)
 
 
-def test_small_config_window():
-    compare(workload.config_small(seed=0), 100)
+def test_small_config_full_run():
+    """The small configuration for its full 1000 coupled steps (32x32x64,
+    one platelet of 642 + 200 SCE nodes, 100 receptor sites over a 16x16
+    ligand patch) and the same bond state as the oracle's.
+
+    Tolerance over the run: every field within 1e-5 after 300 steps, 5e-5
+    after 1000.  The FP32 collision rounds every population of a cell a few
+    times per step (~2^-24 of the largest shifted population, 3.6e-6 at the
+    moving wall); in this flow all cells of a plane hold the same values, so
+    the roundings are coherent across the plane instead of averaging out,
+    and under the platelet's slowly varying force field they add up in the
+    momentum, which the walls remove only on the viscous time nz^2/nu ~
+    40,000 steps.  Measured: the deviation grows linearly, 1.5e-8 of the
+    largest population and 4e-8 of the largest node velocity per step (1.6e-5
+    and 3.9e-5 after 1000 steps; a float32 restatement of the collision on
+    the host reproduces the growth to two digits, an FP64 one does not show
+    it).  The windows of the other coupled tests (<= 200 steps) stay at 1e-5."""
+    sim, ora = compare(workload.config_small(seed=0), 1000, tol=5e-5, checkpoints=[(300, TOL)])
+    assert np.array_equal(sim.bonds.bound.cpu().numpy(), ora.bound)
+    assert np.array_equal(sim.bonds.lig_count.cpu().numpy(), ora.lig_count)
 
 
-def test_channel_config_sampled_window():
-    compare(workload.config_channel(seed=0), 3)
+def test_channel_config_window():
+    """The 128x64x64 channel with 10 platelets (33,620 nodes, 50,000 sites)
+    over a 20-step window (the oracle takes ~0.5 s per step)."""
+    sim, ora = compare(workload.config_channel(seed=0), 20)
+    assert np.array_equal(sim.bonds.bound.cpu().numpy(), ora.bound)
 
 
 def test_bonds_in_coupled_run():
