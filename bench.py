@@ -4,14 +4,16 @@
 
 One step = one pass of the whole hot path (membrane forces + wall term, bond
 forces, spreading, lattice Boltzmann, interpolation + advection, adhesion
-update) on the workload "channel": a 128x64x64 D3Q19 Couette channel at wall
-shear 1000/s (tau = 0.8), 10 platelets of 2562 membrane nodes + 800 SCE
-elements with 5000 receptor sites each, randomly placed within 3 um of a
-ligand-coated wall patch.  Inputs are synthetic and seeded.  The populations
-and fields (~82 MB) fit in the 126 MB L2, so L2 is flushed before every
-timed step (a 512 MB write, then a 256 MB read, so that the L2 holds neither
-the step's data nor dirty lines of the flush buffer); each step is timed with
-CUDA events on the launching stream.
+update) on the full-scale workload: a 512x256x256 D3Q19 Couette channel
+(33.5 M cells) at wall shear 3000/s (tau = 0.8), 500 platelets of 2562
+membrane nodes + 800 SCE elements with 5000 receptor sites each, ligands on
+the whole bottom wall.  Inputs are synthetic and seeded.  The state (~7 GB)
+is far larger than the 126 MB L2, so no flush is needed between steps; the
+K timed steps run back to back through sim_step and are timed with CUDA
+events on the launching stream.  `value` is the plain FP32 form; the
+16-bit-storage and surrogate forms run beside it on the same workload.
+The 128x64x64 channel (10 platelets; its state fits in L2, so L2 is flushed
+before each of its steps) is reported as a secondary line.
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
 replica of the workload on its own GPU (independent chambers: weak scaling,
@@ -35,8 +37,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "coupled MLUPS + membrane-node updates/s, % HBM roofline, vs plain FP32"
-WORKLOAD = ("channel 128x64x64 D3Q19 Couette, shear 1000/s, tau 0.8; 10 platelets x (2562 membrane nodes "
-            "+ 800 SCE), 5000 receptor sites each, ligand patch 64x32; plain FP32 (FP64 positions)")
+WORKLOAD = ("full scale 512x256x256 D3Q19 Couette channel (33.5 M cells), shear 3000/s, tau 0.8; 500 platelets x "
+            "(2562 membrane nodes + 800 SCE), 5000 receptor sites each, ligands on the whole bottom wall; plain "
+            "FP32 populations (FP64 positions)")
+CHANNEL = ("channel 128x64x64 D3Q19 Couette, shear 1000/s, tau 0.8; 10 platelets x (2562 membrane nodes "
+           "+ 800 SCE), 5000 receptor sites each, ligand patch 64x32; plain FP32 (FP64 positions)")
+# accelerated adhesion kinetics (lattice units) of the full-scale comparison of
+# the storage and membrane forms, so that bonds form within the timed window
+FAST_KINETICS = dict(kon0_dt=0.05, koff0_dt=0.005, sigma=0.02, kT=0.05, gamma=0.05)
 LB_BYTES_PER_CELL = 152          # 19 float loads + 19 float stores
 LB_BYTES_PER_CELL_MIXED = 108    # 19 16-bit f^neq + one float4 (v, rho - 1), each read and written
 KERNELS_PER_STEP = 11            # split, elements, coef, nodes, bond forces, spread, lb, interp, rupture, propose, resolve
@@ -63,17 +71,17 @@ def lb_kernel_sha():
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the lattice kernel from the committed ncu
+def ncu_traffic(name="lb_step_full_512x256x256.md"):
+    """DRAM bytes per launch of the lattice kernel from a committed ncu
     summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "lb_step_channel_128x64x64.md")
+    path = os.path.join(ROOT, "profiles", name)
     try:
         txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    s = re.search(r"lb_source_sha:\s*([0-9a-f]+)", txt)
-    if not m or not s or s.group(1) != lb_kernel_sha():
+    sh = re.search(r"lb_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not sh or sh.group(1) != lb_kernel_sha():
         return None
     return float(m.group(1))
 
@@ -171,28 +179,52 @@ def barrier(ws: int):
         dist.barrier()
 
 
-def cpu_baseline(w, steps):
-    """The oracle as it stands, single-threaded, on a bounded sample (the
-    first `steps` steps of the same workload)."""
+SAMPLE = ("1/16 of the full-scale channel along x: 32x256x256 cells (2.1 M), 31 platelets of the same kind "
+          "(2562 + 800 SCE, 5000 receptor sites each) at the same density, shear 3000/s, ligands on the whole "
+          "bottom wall (workload.config_full_sample)")
+
+
+def cpu_baseline(threads):
+    """The oracle as it stands on a bounded sample of the workload (SAMPLE):
+    one coupled step after one untimed step, once on all host cores (its
+    loops over independent cells and nodes run on OpenMP threads; the rest
+    is serial) and once on one core."""
     import oracle
+    from paper_1312_2234_b300 import workload
+    w = workload.config_full_sample(seed=0)
     sim = oracle.Sim(w)
+    oracle.set_threads(threads)
     sim.step()                      # untimed first step
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        sim.step()
-    dt = time.perf_counter() - t0
     N = w["grid"]["nx"] * w["grid"]["ny"] * w["grid"]["nz"]
-    return {"value": N * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d coupled steps of the same workload (after one untimed step), %.1f s" % (steps, dt),
-            "node_updates_per_s": w["M"] * steps / dt}
+    legs = {}
+    for n in (threads, 1):
+        oracle.set_threads(n)
+        t0 = time.perf_counter()
+        sim.step()
+        legs[n] = time.perf_counter() - t0
+    oracle.set_threads(threads)
+    dt = legs[threads]
+    return {"value": N / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": "%s: one coupled step after one untimed step, %.2f s on %d threads (OpenMP over the "
+                      "lattice cells and the interpolated nodes; membrane, spreading and bonds serial)"
+                      % (SAMPLE, dt, threads),
+            "node_updates_per_s": w["M"] / dt,
+            "single_thread": {"value": N / legs[1] / 1e6, "unit": "MLUPS", "cores": 1,
+                              "seconds_per_step": legs[1], "node_updates_per_s": w["M"] / legs[1]},
+            "nproc": os.cpu_count()}
 
 
 def run_reference(args, rank, ws):
+    """The oracle on the host cores (OpenMP over all of them) on the native
+    arm's workload, metric and unit: each step one coupled oracle step of a
+    bounded sample of the workload (SAMPLE)."""
     from paper_1312_2234_b300 import workload
     import oracle
     if rank != 0:
         return
-    w = workload.config_channel(seed=0)
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    w = workload.config_full_sample(seed=0)
     N = w["grid"]["nx"] * w["grid"]["ny"] * w["grid"]["nz"]
     sim = oracle.Sim(w)
     for _ in range(args.warmup):
@@ -205,11 +237,11 @@ def run_reference(args, rank, ws):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "cells": N, "nodes": w["M"],
-                                            "parallelism": "single host thread"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": SAMPLE, "cells": N, "nodes": w["M"],
+                                            "parallelism": "%d host threads (OpenMP)" % threads},
             "node_updates_per_s": w["M"] * args.steps / dt,
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d coupled steps after %d untimed" % (args.steps, args.warmup)},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                             "sample": "%s; %d coupled steps after %d untimed" % (SAMPLE, args.steps, args.warmup)},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -221,164 +253,108 @@ def run_native(args, rank, ws):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workload.config_channel(seed=0)
+    stream = torch.cuda.current_stream()
+    t_build = time.perf_counter()
+    w = workload.config_full(seed=0)
+    log("full-scale workload built in %.1f s" % (time.perf_counter() - t_build))
     g = w["grid"]
     N = g["nx"] * g["ny"] * g["nz"]
     M = w["M"]
     sim = fsi.Simulation(w, device=dev)
-    lat = sim.lattice
-    flush = L2Flush(dev)
-    stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        flush(1)
-        sim.step(1)
+    sim.step(args.warmup)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # the timed region: K steps back to back (sim_step replays eight-step
+    # graphs, then four-step and single-step ones); the ~7 GB state does not
+    # fit in L2, so consecutive steps re-read it from HBM
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
-        for k in range(args.steps):
-            flush(k)
-            starts[k].record(stream)
-            sim.step(1)
-            ends[k].record(stream)
+        start.record(stream)
+        sim.step(args.steps)
+        end.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_s = reduce_max(sum(step_ms) / 1e3, ws)
+    total_s = reduce_max(start.elapsed_time(end) / 1e3, ws)
     ms_per_step = 1e3 * total_s / args.steps
 
-    # the same workload on mixed-precision lattice storage, timed the same
-    # way, and its deviation from this FP32 run after the same number of
-    # steps from the same initial state
-    snap = {"X": sim.X.cpu().numpy(), "U": sim.U.cpu().numpy(),
-            "bound": sim.bonds.bound.cpu().numpy() if sim.bonds else None}
-    mixed = {} if args.no_mixed else {s: run_mixed(args, w, s, dev, flush, stream, snap, ws)
-                                      for s in ("bf16", "fp16")}
-    extras = {}
-    if not args.no_extras:
-        extras["fem_bending"] = run_fem(args, w, ms_per_step, dev, flush, stream)
-        extras["platelet_pair"] = run_pair(args, dev, flush, stream)
-        extras["batched"] = run_batched(args, dev, stream)
-        extras["surrogate"], sg_params = run_surrogate(args, w, sim, dev, stream)
-        extras["full_scale"] = run_full(args, dev, stream, sg_params)
-
-    # the dominant kernel where it runs: after the timed region, the same steps
-    # with two CUDA events recorded around the lattice kernel inside the step
-    # graph (cold L2 after each flush); the host waits for each step here,
-    # which is why these steps are not the timed ones
-    fsi.sim_time_lb(sim.h, True)
-    lb_ms = []
-    for k in range(max(args.steps, 10)):
-        flush(k)
-        sim.step(1)
-        lb_ms.append(fsi.sim_lb_ms(sim.h))
-    fsi.sim_time_lb(sim.h, False)
-    # the average launch duration (the event timer ticks in ~1 us steps, so
-    # the mean of many intervals also resolves below one tick)
-    lb_s = statistics.fmean(lb_ms) / 1e3
-    lb_bytes = LB_BYTES_PER_CELL * N
-    # the same steps after a write-only flush (dirty L2), for comparison
-    dirty_ms = []
-    for k in range(args.steps):
-        flush(k, write_only=True)
+    # the same steps one graph launch each, timed one by one (no overlap of
+    # one step's adhesion update with the next step's membrane pass)
+    single_ms = []
+    for _ in range(args.steps):
         a_ev = torch.cuda.Event(enable_timing=True)
         b_ev = torch.cuda.Event(enable_timing=True)
         a_ev.record(stream)
-        sim.step(1)
+        fsi.sim_step(sim.h, 1)
         b_ev.record(stream)
         b_ev.synchronize()
-        dirty_ms.append(a_ev.elapsed_time(b_ev))
+        single_ms.append(a_ev.elapsed_time(b_ev))
+
+    # the dominant kernel where it runs: the same single steps with two CUDA
+    # events recorded around the lattice kernel inside the step graph
+    fsi.sim_time_lb(sim.h, True)
+    lb_ms = []
+    for _ in range(max(args.steps, 10)):
+        sim.step(1)
+        lb_ms.append(fsi.sim_lb_ms(sim.h))
+    fsi.sim_time_lb(sim.h, False)
+    # the average launch duration (the event timer ticks in ~1 us steps)
+    lb_s = statistics.fmean(lb_ms) / 1e3
+    lb_bytes = LB_BYTES_PER_CELL * N
     peaks = measured_peaks()
     if peaks:
-        peak, peak_note = peaks["hbm_gbs"], "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, burst)"
+        peak, peak_note = peaks["hbm_gbs"], "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
     else:
         peak, peak_note = 6400.0, "fallback 6.4 TB/s"
     achieved = lb_bytes / lb_s / 1e9
     traffic = ncu_traffic()
+    e2e = run_e2e(args, w, sim, dev, stream, ws)
+    del sim
+    torch.cuda.empty_cache()
 
-    # end to end through the public API with host buffers: upload the
-    # initial state from pinned memory, step, read the positions back each
-    # step (the trajectory a user records), all inside the timed region;
-    # every rank takes part (the time is the maximum over ranks)
-    if True:
-        hostX = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
-        # the step's result read back every step: the platelets' centroids
-        # (the quantity a user follows, e.g. for pause times)
-        nplt = int(w["mesh"]["n_plt"])
-        cbuf = torch.empty(72 * nplt, dtype=torch.float64, device=dev)
-        # instantiate the tracked graphs (both eight-step slot groups and the single steps)
-        sim.step_track(18, cbuf, torch.empty(18, 3 * nplt, dtype=torch.float64).pin_memory())
-        out = torch.empty(args.steps, 3 * nplt, dtype=torch.float64).pin_memory()
-        # three repetitions of the whole run (upload, set-up, steps, read-back);
-        # the median of their times
-        runs = []
-        for _ in range(3):
-            torch.cuda.synchronize()
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            sim.X.copy_(hostX, non_blocking=True)   # the platelets' state comes from the host
-            lat.init_shear()                         # the flow is set up on the device
-            sim.step_track(args.steps, cbuf, out)
-            t1.record(stream)
-            t1.synchronize()
-            runs.append(t0.elapsed_time(t1) / 1e3)
-        e2e_s = reduce_max(statistics.median(runs), ws)
-        h2d = hostX.numel() * 8 / args.steps
-        # the full positions of every step instead, through sim_step_record
-        # (device snapshot + copy on the library's copy stream): bound by the
-        # host link
-        ring = 4
-        dev_ring = torch.empty(ring, 3 * M, dtype=torch.float64, device=dev)
-        outX = torch.empty(ring, 3 * M, dtype=torch.float64).pin_memory()
-        torch.cuda.synchronize()
-        t2 = torch.cuda.Event(enable_timing=True)
-        t3 = torch.cuda.Event(enable_timing=True)
-        t2.record(stream)
-        sim.step_record(args.steps, dev_ring, outX)
-        t3.record(stream)
-        t3.synchronize()
-        pos_s = reduce_max(t2.elapsed_time(t3) / 1e3, ws)
-        e2e = {"value": ws * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(3 * nplt * 8),
-               "note": "node positions uploaded from pinned memory and the developed flow initialised on the "
-                       "device inside the timed region (upload bytes amortised per step); every step's "
-                       "platelet centroids read back to pinned host memory; one continuous run, no L2 "
-                       "flush between steps; median of three such runs",
-               "with_positions_every_step": {
-                   "value": ws * N * args.steps / pos_s / 1e6, "unit": "MLUPS",
-                   "d2h_bytes_per_step": int(3 * M * 8),
-                   "d2h_gbs": 3 * M * 8 * args.steps / pos_s / 1e9,
-                   "note": "all node positions of every step copied to pinned host memory on a second "
-                           "stream (sim_step_record); the device-to-host link bounds it"}}
+    channel, sim_c, w_c = run_channel(args, dev, stream, ws)
+    extras = {"channel": channel}
+    forms = {}
+    if not args.no_extras:
+        flush = L2Flush(dev)
+        extras["fem_bending"] = run_fem(args, w_c, channel["ms_per_step"], dev, flush, stream, w)
+        extras["platelet_pair"] = run_pair(args, dev, flush, stream)
+        del flush
+        torch.cuda.empty_cache()
+        extras["batched"] = run_batched(args, dev, stream)
+        extras["surrogate"], sg_params = run_surrogate(args, w_c, sim_c, dev, stream)
+        del sim_c
+        torch.cuda.empty_cache()
+        if not args.no_mixed:
+            forms = run_forms(args, w, dev, stream, sg_params, ws)
 
     if rank != 0:
         return
-    base = cpu_baseline(w, args.cpu_steps) if args.cpu_steps > 0 else None
+    base = cpu_baseline(os.cpu_count() or 1) if args.cpu_steps > 0 else None
     value = ws * N * args.steps / total_s / 1e6
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": N, "nodes": M, "sites": int(len(w["sites"]["tri"])),
-                   "l2": "flushed before every timed step: 512 MB written, then 256 MB read (no step data "
-                         "and no dirty lines left in L2)",
-                   "ms_per_step_write_only_flush": statistics.fmean(dirty_ms), "parallelism": "replicas",
-                   "graph": "one CUDA graph launch per step"},
+                   "ligands": int(w["bonds"]["lig_ni"] * w["bonds"]["lig_nj"]),
+                   "l2": "no flush: the state (~7 GB of populations, fields and platelets) is far larger than "
+                         "the 126 MB L2",
+                   "parallelism": "replicas",
+                   "graph": "sim_step(K): eight-step CUDA graphs (each step's adhesion update beside the next "
+                            "step's membrane pass), then four-step and single-step graphs",
+                   "single_step_graph_ms": statistics.fmean(single_ms)},
         "node_updates_per_s": ws * M * args.steps / total_s,
         "roofline": {"bound": "hbm", "kernel": "k_lb_step", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note,
                      "algorithmic_bytes_per_launch": lb_bytes, "launch_ms": 1e3 * lb_s,
                      "launch_ms_median": statistics.median(lb_ms),
-                     "timing": "mean over as many steps as timed of CUDA events recorded around the "
-                               "kernel inside the step graph (cold L2 after each flush; includes the "
-                               "graph's event-node latency)"},
-        "lb_share_of_step": (1e3 * lb_s) / ms_per_step,
-        "mixed_precision": {k: dict(v, vs_fp32=v["value"] / value) for k, v in mixed.items()},
+                     "timing": "mean over %d single steps of CUDA events recorded around the kernel inside "
+                               "the step graph (includes the graph's event-node latency)" % len(lb_ms)},
+        "lb_share_of_step": (1e3 * lb_s) / statistics.fmean(single_ms),
+        "mixed_precision": forms,
         "configurations": extras,
         "cpu_baseline": base,
         "e2e": e2e,
@@ -386,6 +362,118 @@ def run_native(args, rank, ws):
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, w, sim, dev, stream, ws):
+    """End to end through the public API with host buffers: the node
+    positions come from pinned host memory and the developed flow is set up
+    on the device inside the timed region, then sim_step_track steps the
+    simulation and copies every step's platelet centroids to pinned host
+    memory; and the same steps with all node positions of every step copied
+    to the host (sim_step_record)."""
+    import torch
+    g = w["grid"]
+    N = g["nx"] * g["ny"] * g["nz"]
+    M = w["M"]
+    lat = sim.lattice
+    hostX = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
+    nplt = int(w["mesh"]["n_plt"])
+    cbuf = torch.empty(72 * nplt, dtype=torch.float64, device=dev)
+    # instantiate the tracked graphs (both eight-step slot groups and the single steps)
+    sim.step_track(18, cbuf, torch.empty(18, 3 * nplt, dtype=torch.float64).pin_memory())
+    out = torch.empty(args.steps, 3 * nplt, dtype=torch.float64).pin_memory()
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        sim.X.copy_(hostX, non_blocking=True)   # the platelets' state comes from the host
+        lat.init_shear()                         # the flow is set up on the device
+        sim.step_track(args.steps, cbuf, out)
+        t1.record(stream)
+        t1.synchronize()
+        runs.append(t0.elapsed_time(t1) / 1e3)
+    e2e_s = reduce_max(statistics.median(runs), ws)
+    h2d = hostX.numel() * 8 / args.steps
+    ring = 4
+    dev_ring = torch.empty(ring, 3 * M, dtype=torch.float64, device=dev)
+    outX = torch.empty(ring, 3 * M, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t2 = torch.cuda.Event(enable_timing=True)
+    t3 = torch.cuda.Event(enable_timing=True)
+    t2.record(stream)
+    sim.step_record(args.steps, dev_ring, outX)
+    t3.record(stream)
+    t3.synchronize()
+    pos_s = reduce_max(t2.elapsed_time(t3) / 1e3, ws)
+    return {"value": ws * N * args.steps / e2e_s / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(3 * nplt * 8),
+            "note": "node positions uploaded from pinned memory and the developed flow initialised on the "
+                    "device inside the timed region (upload bytes amortised per step); every step's "
+                    "platelet centroids read back to pinned host memory; one continuous run of the timed "
+                    "steps; median of three such runs",
+            "with_positions_every_step": {
+                "value": ws * N * args.steps / pos_s / 1e6, "unit": "MLUPS",
+                "d2h_bytes_per_step": int(3 * M * 8),
+                "d2h_gbs": 3 * M * 8 * args.steps / pos_s / 1e9,
+                "note": "all node positions of every step copied to pinned host memory on a second "
+                        "stream (sim_step_record); the device-to-host link bounds it"}}
+
+
+def run_channel(args, dev, stream, ws):
+    """The 128x64x64 channel with 10 platelets: L2 flushed before every
+    step (its state fits in L2), single steps timed with CUDA events; its
+    lattice kernel's roofline (L2-resident writes), and the same workload
+    on 16-bit population storage with its deviation from this FP32 run."""
+    import torch
+    from paper_1312_2234_b300 import fsi, workload
+    w = workload.config_channel(seed=0)
+    g = w["grid"]
+    N = g["nx"] * g["ny"] * g["nz"]
+    sim = fsi.Simulation(w, device=dev)
+    flush = L2Flush(dev)
+    for _ in range(args.warmup):
+        flush(1)
+        sim.step(1)
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(args.steps):
+        flush(k)
+        a_ev = torch.cuda.Event(enable_timing=True)
+        b_ev = torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        sim.step(1)
+        b_ev.record(stream)
+        b_ev.synchronize()
+        ms.append(a_ev.elapsed_time(b_ev))
+    step_ms = statistics.fmean(ms)
+    snap = {"X": sim.X.cpu().numpy(), "U": sim.U.cpu().numpy(),
+            "bound": sim.bonds.bound.cpu().numpy() if sim.bonds else None}
+    fsi.sim_time_lb(sim.h, True)
+    lb_ms = []
+    for k in range(max(args.steps, 10)):
+        flush(k)
+        sim.step(1)
+        lb_ms.append(fsi.sim_lb_ms(sim.h))
+    fsi.sim_time_lb(sim.h, False)
+    lb_s = statistics.fmean(lb_ms) / 1e3
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
+    achieved = LB_BYTES_PER_CELL * N / lb_s / 1e9
+    mixed = {} if args.no_mixed else {s: run_mixed(args, w, s, dev, flush, stream, snap, ws)
+                                      for s in ("bf16", "fp16")}
+    out = {"workload": CHANNEL, "cells": N, "nodes": w["M"], "sites": int(len(w["sites"]["tri"])),
+           "value": N * len(ms) / (sum(ms) / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": step_ms,
+           "l2": "L2-resident state: flushed before every step (512 MB written, then 256 MB read)",
+           "lb_kernel": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "launch_ms": 1e3 * lb_s, "traffic": ncu_traffic("lb_step_channel_128x64x64.md"),
+                         "note": "L2-resident: the kernel's writes stay in the 126 MB L2"},
+           "mixed_precision": {k: dict(v, vs_fp32=v["value"] / (N * len(ms) / (sum(ms) / 1e3) / 1e6))
+                               for k, v in mixed.items()}}
+    del flush
+    torch.cuda.empty_cache()
+    return out, sim, w
 
 
 def run_mixed(args, w, storage, dev, flush, stream, snap, ws):
@@ -558,7 +646,7 @@ def run_surrogate(args, w_channel, sim_channel, dev, stream):
     return out, params
 
 
-def run_fem(args, w, ms_dihedral, dev, flush, stream):
+def run_fem(args, w, ms_dihedral, dev, flush, stream, w_full=None):
     """The channel's coupled step with the finite-element bending of Eq. 6-10
     in place of the dihedral term (timed like the headline: L2 flushed before
     every step), and the bending term alone on the channel's and on the full
@@ -585,7 +673,9 @@ def run_fem(args, w, ms_dihedral, dev, flush, stream):
            "coupled": {"value": N / step_ms / 1e3, "unit": "MLUPS", "ms_per_step": step_ms,
                        "vs_dihedral": ms_dihedral / step_ms}}
     del sim
-    for name, wk in (("channel_mesh", w), ("full_scale_mesh", workload.config_full(seed=0))):
+    if w_full is None:
+        w_full = workload.config_full(seed=0)
+    for name, wk in (("channel_mesh", w), ("full_scale_mesh", w_full)):
         fb = fsi.FemBending(wk["mesh"], device=dev)
         X = torch.as_tensor(np.ascontiguousarray(wk["X"], dtype=np.float64), device=dev)
         F = torch.zeros(3 * wk["M"], dtype=torch.float32, device=dev)
@@ -634,53 +724,77 @@ def run_pair(args, dev, flush, stream):
     return out
 
 
-def run_full(args, dev, stream, sg_params):
-    """Full scale: 512x256x256 channel (33.5 M cells), 500 platelets with SCE
-    and receptors, shear 3000/s: the plain FP32 form against BF16 populations
-    with the learned surrogate (Philox bonds in both)."""
+def run_forms(args, w, dev, stream, sg_params, ws):
+    """The full-scale workload in its storage and membrane forms, all at the
+    accelerated adhesion kinetics FAST_KINETICS (so that bonds form within
+    the window): plain FP32, BF16 and FP16 f^neq storage with the plain
+    membrane, and BF16 storage with the learned surrogate (plain solver for
+    the global terms).  Each form runs W + K steps from the same state, the
+    last K timed back to back; the 16-bit and surrogate forms are compared
+    with the FP32 form after the same steps: node velocity and displacement,
+    and the bond state (bond counts and sites whose state differs)."""
     import torch
-    from paper_1312_2234_b300 import fsi, workload
-    w5 = workload.config_full(seed=0)
-    N = w5["grid"]["nx"] * w5["grid"]["ny"] * w5["grid"]["nz"]
-    steps, warm = 3, 3
-    out = {"workload": "512x256x256 channel, shear 3000/s, 500 platelets x (2562 + 800 SCE), 5000 receptors each",
-           "cells": N, "nodes": w5["M"], "sites": int(len(w5["sites"]["tri"])), "steps": steps}
-    snap = None
-    for mode in ("fp32_plain", "bf16_surrogate"):
-        storage = "fp32" if mode == "fp32_plain" else "bf16"
-        sim = fsi.Simulation(w5, device=dev, storage=storage, tune=storage != "fp32")
-        if mode == "bf16_surrogate":
-            sg5 = fsi.Surrogate(w5["mesh"], "bf16", device=dev)
-            fsi.sim_set_surrogate(sim, sg5, sg_params)
-        sim.step(warm)
-        t = timed_steps(lambda: sim.step(1), steps, stream)
-        out[mode] = {"value": N * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps}
+    from paper_1312_2234_b300 import fsi
+    g = w["grid"]
+    N = g["nx"] * g["ny"] * g["nz"]
+    wk = dict(w, bonds=dict(w["bonds"], **FAST_KINETICS))
+    out = {"workload": WORKLOAD, "kinetics": dict(FAST_KINETICS, note="accelerated, lattice units"),
+           "steps": args.steps, "warmup": args.warmup}
+    ref = None
+    X0 = np.ascontiguousarray(w["X"])
+    for form in ("fp32", "bf16", "fp16", "bf16_surrogate"):
+        storage = "fp32" if form == "fp32" else form.split("_")[0]
+        sim = fsi.Simulation(wk, device=dev, storage=storage, tune=storage != "fp32")
+        if form.endswith("surrogate"):
+            sg = fsi.Surrogate(wk["mesh"], "bf16", device=dev)
+            fsi.sim_set_surrogate(sim, sg, sg_params)
+        sim.step(args.warmup)
+        t = timed_steps(lambda: sim.step(args.steps), 1, stream)
+        t = reduce_max(t, ws)
+        X = sim.X.cpu().numpy()
         U = sim.U.cpu().numpy()
-        bonds = int((sim.bonds.bound >= 0).sum().item()) if sim.bonds is not None else 0
-        if snap is None:
-            snap = (U, bonds)
+        bound = sim.bonds.bound.cpu().numpy()
+        r = {"value": ws * N * args.steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / args.steps,
+             "bonds": int((bound >= 0).sum())}
+        if storage != "fp32":
+            r["fp16_exponent" if storage == "fp16" else "shape"] = (
+                int(sim.lattice.p.fp16_exponent) if storage == "fp16" else int(sim.shape))
+        if ref is None:
+            ref = (X, U, bound)
         else:
-            out[mode]["node_velocity_rel_vs_fp32"] = float(np.abs(U - snap[0]).max() / max(np.abs(snap[0]).max(), 1e-30))
-            out[mode]["bonds"] = bonds
-            out[mode]["bonds_fp32"] = snap[1]
+            dX = ref[0] - X0
+            r["error_vs_fp32"] = {
+                "node_velocity_rel": float(np.abs(U - ref[1]).max() / max(np.abs(ref[1]).max(), 1e-30)),
+                "displacement_rel": float(np.abs(X - ref[0]).max() / max(np.abs(dX).max(), 1e-30)),
+                "bonds_fp32": int((ref[2] >= 0).sum()), "bonds": r["bonds"],
+                "bond_count_rel": abs(r["bonds"] - int((ref[2] >= 0).sum())) / max(int((ref[2] >= 0).sum()), 1),
+                "sites_differing": int((bound != ref[2]).sum())}
+        if form.endswith("surrogate"):
+            r["surrogate_status"] = sg.status()
+            del sg
+        out[form] = r
         del sim
         torch.cuda.empty_cache()
-    out["vs_fp32"] = out["bf16_surrogate"]["value"] / out["fp32_plain"]["value"]
+    for form in ("bf16", "fp16", "bf16_surrogate"):
+        out[form]["vs_fp32"] = out[form]["value"] / out["fp32"]["value"]
     return out
 
 
 def run_full_only(args):
-    """The 500-platelet full-scale step alone (profiling aid): the plain FP32
-    form and the BF16 + surrogate form with untrained surrogate weights
+    """The full-scale step alone in its forms (profiling aid): plain FP32,
+    16-bit storage and BF16 + surrogate with untrained surrogate weights
     (the same kernels and launch shapes as trained ones).  Prints one JSON
     line."""
     import torch
-    from paper_1312_2234_b300 import fsi, surrogate
+    from paper_1312_2234_b300 import fsi, surrogate, workload
     dev = torch.device("cuda", 0)
     params = fsi.SurrogateParams(device=dev)
-    params.set(surrogate.init_params(np.random.default_rng(0)))
-    print(json.dumps({"kernel": "full-scale coupled step", **run_full(args, dev, torch.cuda.current_stream(), params)}),
-          flush=True)
+    p = surrogate.init_params(np.random.default_rng(0))
+    p["W3"] *= 1e-3     # a small untrained network keeps the run physical
+    params.set(p)
+    w = workload.config_full(seed=0)
+    print(json.dumps({"kernel": "full-scale coupled step",
+                      **run_forms(args, w, dev, torch.cuda.current_stream(), params, 1)}), flush=True)
 
 
 def run_lb_only(args):
@@ -802,17 +916,18 @@ def run_bridges_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps timed for cpu_baseline (0: skip)")
+    ap.add_argument("--cpu-steps", type=int, default=1, help="0: skip the oracle's cpu_baseline leg")
     ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges", "full"],
                     help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision variants")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage and surrogate forms")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, surrogate and full-scale configurations")
+                    help="skip the secondary configurations (FEM bending, platelet pair, batched, surrogate, "
+                         "the full-scale forms)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

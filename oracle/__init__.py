@@ -42,7 +42,7 @@ def build(force: bool = False) -> str:
     ):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+            ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
              "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
         )
         os.replace(tmp, _LIB_PATH)
@@ -84,6 +84,8 @@ def lib():
     global _lib
     if _lib is None:
         L = ctypes.CDLL(build())
+        L.ora_set_threads.argtypes = [ctypes.c_int]
+        L.ora_get_threads.restype = ctypes.c_int
         L.ora_philox4x32_10.argtypes = [UP, UP, UP]
         L.ora_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
         L.ora_uniform.restype = ctypes.c_double
@@ -128,6 +130,16 @@ def _i(a):
 
 
 # ---------------------------------------------------------------- Philox
+def set_threads(n):
+    """Host threads of the oracle's parallel loops (lattice step, initial
+    state, interpolation); results do not depend on the count."""
+    lib().ora_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().ora_get_threads())
+
+
 def philox4x32_10(ctr, key):
     c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
     k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])

@@ -13,12 +13,21 @@
  * Readings of garbled or silent passages are listed in the design notes of
  * the repository; each is marked "reading:" where it is used below.
  * No blocking, fusion or reordering beyond the equations is done here.
+ * The loops over independent cells (lattice step, initial state) and nodes
+ * (interpolation) may run on several host threads (OpenMP, ora_set_threads):
+ * each iteration writes only its own outputs, so the results do not depend
+ * on the thread count.
  */
 #include "oracle.h"
 
+#include <omp.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Host threads used by the parallel loops (at least 1). */
+void ora_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }
+int ora_get_threads(void) { return omp_get_max_threads(); }
 
 /* ======================================================================
  * Philox4x32-10 counter-based generator, written from its published
@@ -141,6 +150,7 @@ void ora_lb_init_shear(const ora_lb_params* p, double* f)
     double H = p->walls ? (double)(p->nz - 1) : (double)p->nz;
     double z0 = p->walls ? 0.0 : 0.5;
     double dudz[3] = {p->u_top[0] / H, p->u_top[1] / H, 0.0};
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < p->nz; ++k)
         for (int j = 0; j < p->ny; ++j)
             for (int i = 0; i < p->nx; ++i) {
@@ -215,6 +225,7 @@ void ora_lb_step(const ora_lb_params* p, const double* f_in, const double* g,
 {
     long N = (long)p->nx * p->ny * p->nz;
     const double zero[3] = {0.0, 0.0, 0.0};
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < p->nz; ++k)
         for (int j = 0; j < p->ny; ++j)
             for (int i = 0; i < p->nx; ++i) {
@@ -297,6 +308,7 @@ void ora_ib_spread(const ora_lb_params* p, int M, const double* X, const double*
 void ora_ib_interp(const ora_lb_params* p, int M, const double* X, const double* v, double* U)
 {
     long N = (long)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
     for (int m = 0; m < M; ++m) {
         double x = X[m], y = X[M + m], z = X[2 * M + m];
         int bx = (int)floor(x) - 1, by = (int)floor(y) - 1, bz = (int)floor(z) - 1;

@@ -22,6 +22,11 @@
 extern "C" {
 #endif
 
+/* Host threads of the parallel loops over independent cells and nodes
+ * (results do not depend on the count). */
+void ora_set_threads(int n);
+int ora_get_threads(void);
+
 /* ---------------- Philox4x32-10 (Salmon et al., SC'11) ---------------- */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 /* 53-bit uniform in [0,1) from counter (site, step_lo, step_hi, purpose). */

@@ -422,5 +422,16 @@ def config_surrogate(seed=0):
 def config_full(seed=0, n_plt=500):
     """Full scale: 512x256x256 channel (33.5 M cells) at wall shear 3000/s,
     500 platelets of 2562 membrane nodes and 800 SCE elements with 5000
-    receptor sites each."""
-    return build(512, 256, 256, 0.8, 3000.0, n_plt, 4, 800, 5000, seed)
+    receptor sites each, ligands on every node of the bottom wall (the
+    configuration names no patch; with the whole wall adhesive, the sites
+    that start within the capture distance can bind)."""
+    return build(512, 256, 256, 0.8, 3000.0, n_plt, 4, 800, 5000, seed, patch=(0, 0, 512, 256))
+
+
+def config_full_sample(seed=0, nx=32):
+    """A bounded sample of the full-scale workload for host timings: the same
+    256 x 256 cross section, shear and platelet kind, nx cells long instead of
+    512 (periodic in x), with the same number of platelets per cell
+    (500 nx / 512, rounded) and ligands on the whole bottom wall."""
+    n_plt = max(1, int(round(500 * nx / 512)))
+    return build(nx, 256, 256, 0.8, 3000.0, n_plt, 4, 800, 5000, seed, patch=(0, 0, nx, 256))

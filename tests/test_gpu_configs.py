@@ -162,3 +162,87 @@ def test_full_scale_invariants():
 
     # surrogate force on sampled nodes
     check_surrogate_sampled(w, X.cpu().numpy(), p, n_sample=300)
+
+
+def lattice_block(f, nx, ny, i, j, k0, wq):
+    """The 3x3x3 block of full populations (FP64, f~ + w) around column
+    (i, j), planes k0 .. k0 + 2, periodic in x and y: [19][3][3][3]."""
+    ii = (np.arange(i - 1, i + 2) % nx)
+    jj = (np.arange(j - 1, j + 2) % ny)
+    b = f[:, k0:k0 + 3][:, :, jj][:, :, :, ii].astype(np.float64)
+    return b + wq[:, None, None, None]
+
+
+def test_full_scale_sampled_parity():
+    """Sampled outputs at the full size, in the launch configuration the
+    benchmark times (512x256x256 lattice, 500 platelets): the lattice step
+    of cells in the bulk, on both walls and under the platelets' spread
+    force, each recomputed by the oracle from its 3x3x3 neighbourhood (a cell
+    pulls only from its neighbours, so the oracle's step of the block gives
+    the centre cell's exact FP64 result); and the membrane force of whole
+    platelets, each by the oracle's membrane of that platelet alone.  Bounds
+    as in the element-wise tests: 1e-5 of the largest population or force."""
+    w = f32_workload(workload.config_full(seed=0))
+    g = w["grid"]
+    nx, ny, nz = g["nx"], g["ny"], g["nz"]
+    N = nx * ny * nz
+    M = w["M"]
+    sim = fsi.Simulation(w)
+    sim.step(3)                                  # the platelets disturb the flow
+    # membrane forces on a deformed state, then spread them and take one
+    # lattice step on the simulation's own lattice
+    rng = np.random.default_rng(7)
+    Xh = sim.X.cpu().numpy() + 0.01 * rng.standard_normal(3 * M)
+    X = torch.from_numpy(Xh).cuda()
+    F = torch.zeros(3 * M, device="cuda")
+    fsi.membrane_forces(sim.membrane.h, X, F)
+    lat = sim.lattice
+    fsi.ib_spread(lat.h, X, F, M)
+    torch.cuda.synchronize()
+    f_pre = lat.current().cpu().numpy().reshape(19, nz, ny, nx)
+    gf = lat.g[:, :3].cpu().numpy().astype(np.float64).T.reshape(3, nz, ny, nx)
+    fsi.lb_step(lat.h, 1)
+    torch.cuda.synchronize()
+    f_post = lat.current().cpu().numpy().reshape(19, nz, ny, nx)
+    _, wq = oracle.lattice()
+    wq = np.asarray(wq)
+    scale = float(np.abs(f_post).max())
+    forced = np.argwhere(np.abs(gf).sum(0) > 0)
+    cells = [tuple(c) for c in forced[rng.choice(len(forced), 120, replace=False)]]
+    cells += [(int(rng.integers(1, nz - 1)), int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(120)]
+    cells += [(0, int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(40)]
+    cells += [(nz - 1, int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(40)]
+    worst = 0.0
+    for (k, j, i) in cells:
+        k0 = min(max(k - 1, 0), nz - 3)
+        kc = k - k0
+        p = oracle.lb_params(3, 3, 3, g["tau"], g["u_top"])
+        fb = lattice_block(f_pre, nx, ny, i, j, k0, wq)
+        gb = gf[:, k0:k0 + 3][:, :, (np.arange(j - 1, j + 2) % ny)][:, :, :, (np.arange(i - 1, i + 2) % nx)]
+        out, _, _ = oracle.lb_step(p, np.ascontiguousarray(fb).ravel(), np.ascontiguousarray(gb).ravel())
+        want = out.reshape(19, 3, 3, 3)[:, kc, 1, 1] - wq
+        worst = max(worst, float(np.abs(f_post[:, k, j, i] - want).max()))
+    print("full-scale lattice sampled parity: %d cells (%d forced), max err %.2e of max |f~|"
+          % (len(cells), 120, worst / scale))
+    assert worst < 1e-5 * scale
+
+    # membrane: whole platelets by the oracle's membrane of that platelet alone
+    m = w["mesh"]
+    plt = np.asarray(m["node_plt"])
+    tri = np.asarray(m["tri"]).reshape(-1, 3)
+    pairs = np.asarray(m["pairs"]).reshape(-1, 2)
+    Fg = F.cpu().numpy().reshape(3, M)
+    X0 = np.asarray(m["X0"]).reshape(3, M)
+    Xd = Xh.reshape(3, M)
+    for pid in (0, 137, 499):
+        nodes = np.nonzero(plt == pid)[0]
+        lo, hi = nodes[0], nodes[-1] + 1
+        assert np.array_equal(nodes, np.arange(lo, hi))
+        t = tri[(tri >= lo).all(1) & (tri < hi).all(1)] - lo
+        pr = pairs[(pairs >= lo).all(1) & (pairs < hi).all(1)] - lo
+        mesh = oracle.Mesh(np.ascontiguousarray(X0[:, lo:hi]).ravel(), t, pr, np.zeros(hi - lo, np.int32),
+                           np.asarray(m["is_membrane"])[lo:hi], 1)
+        Fo = mesh.forces(w["membrane"], np.ascontiguousarray(Xd[:, lo:hi]).ravel()).reshape(3, -1)
+        err = rel(Fg[:, lo:hi], Fo)
+        print("full-scale membrane parity, platelet %d: %.2e" % (pid, err))
+        assert err < 1e-5

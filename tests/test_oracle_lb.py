@@ -208,3 +208,24 @@ def test_onsite_walls_impose_the_wall_velocity(oracle_lib):
     _, rho_b, v_b = oracle_lib.lb_step(pb, f)
     inner = slice(2, nz - 2)
     assert np.array_equal(v.reshape(3, nz, ny, nx)[:, inner], v_b.reshape(3, nz, ny, nx)[:, inner])
+
+
+def test_thread_count_does_not_change_results(oracle_lib):
+    """The oracle's parallel loops (independent cells and nodes) give the
+    same bits on one host thread and on several."""
+    p = oracle_lib.lb_params(23, 17, 11, 0.8, (3e-3, 1e-3, 0.0))
+    rng = np.random.default_rng(5)
+    f0 = oracle_lib.lb_init_shear(p)
+    g = 1e-5 * rng.standard_normal(3 * 23 * 17 * 11)
+    X = np.vstack([rng.uniform(0, 23, 300), rng.uniform(0, 17, 300), rng.uniform(-0.4, 10.4, 300)]).ravel()
+    out = []
+    for n in (1, 4):
+        oracle_lib.set_threads(n)
+        f = oracle_lib.lb_init_shear(p)
+        f1, rho, v = oracle_lib.lb_step(p, f, g)
+        U = oracle_lib.ib_interp(p, X, v)
+        out.append((f, f1, rho, v, U))
+    oracle_lib.set_threads(1)
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][0], f0)
