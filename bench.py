@@ -62,13 +62,18 @@ def measured_peaks():
 
 
 def lb_kernel_sha():
-    """Hash of the FP32 lattice kernel's source: from the on-site wall helper
-    it calls to the end of k_lb_step (the rest of lb.cu does not change the
-    kernel the traffic figure was measured on)."""
-    src = open(os.path.join(ROOT, "paper_1312_2234_b300", "csrc", "lb.cu")).read()
-    a = src.index("template <int s>\n__device__ __forceinline__ void onsite_wall")
-    b = src.index("\n}\n", src.index("k_lb_step(", a)) + 3
-    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    """Hash of the FP32 lattice kernel's source: the on-site wall helper it
+    calls (csrc/pfsi_internal.cuh) and k_lb_step (csrc/lb.cu); the rest of
+    those files does not change the kernel the traffic figure was measured
+    on."""
+    csrc = os.path.join(ROOT, "paper_1312_2234_b300", "csrc")
+    hdr = open(os.path.join(csrc, "pfsi_internal.cuh")).read()
+    a = hdr.index("template <int s>\n__device__ __forceinline__ void onsite_wall")
+    b = hdr.index("\n}\n", a) + 3
+    src = open(os.path.join(csrc, "lb.cu")).read()
+    c = src.index("__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(")
+    d = src.index("\n}\n", c) + 3
+    return hashlib.sha256((hdr[a:b] + src[c:d]).encode()).hexdigest()[:16]
 
 
 def ncu_traffic(name="lb_step_full_512x256x256.md"):
@@ -806,6 +811,8 @@ def run_lb_only(args):
 
     nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
     lat = fsi.Lattice(nx, ny, nz, 0.8, (1e-3, 0.0, 0.0), storage=args.storage)
+    if args.shape is not None:
+        fsi.lb_set_shape(lat, args.shape)
     lat.init_shear()
     N = nx * ny * nz
     per_cell = LB_BYTES_PER_CELL if args.storage == "fp32" else LB_BYTES_PER_CELL_MIXED
@@ -829,7 +836,8 @@ def run_lb_only(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6400.0
     gbs = per_cell * N / t / 1e9
-    print(json.dumps({"kernel": "k_lb_step", "storage": args.storage, "grid": [nx, ny, nz], "cells": N, "median_ms": 1e3 * t,
+    print(json.dumps({"kernel": "k_lb_step", "storage": args.storage, "shape": fsi.lb_get_shape(lat), "grid": [nx, ny, nz],
+                      "cells": N, "median_ms": 1e3 * t,
                       "min_ms": min(ms), "GLUPS": N / t / 1e9, "GBps": gbs, "peak_GBps": peak,
                       "frac": gbs / peak, "l2_flushed": small}), flush=True)
 
@@ -924,6 +932,7 @@ def main():
                     help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
+    ap.add_argument("--shape", type=int, default=None, help="launch shape of --kernel lb (lb_set_shape)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 16-bit storage and surrogate forms")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the secondary configurations (FEM bending, platelet pair, batched, surrogate, "

@@ -109,21 +109,29 @@ int lb_create(const lb_params* p, float* f_a, float* f_b, float* g, float* v,
               uint32_t* row_flags, lb_ctx** out);
 
 /* Mixed-precision storage (p->storage = PFSI_LB_BF16 or PFSI_LB_FP16; no
- * paper counterpart, a storage choice): each cell keeps its post-collision
- * non-equilibrium part f*neq_q = (1 - 1/tau)(f_q - f_q^eq) + S_q in 16 bits
- * (fneq_a/fneq_b, [q][cell]) and its (v, rho - 1) in FP32 (m_a/m_b, float4
- * per cell), 108 B per cell per step instead of 152.  A pulling cell rebuilds
- * each incoming population as f_q^eq(rho, v of the source cell) + f*neq_q.
+ * paper counterpart, a storage choice): each cell keeps its (v, rho - 1) in
+ * FP32 (m_a/m_b, float4 per cell) and, in 16 bits (fneq_a/fneq_b,
+ * [slot][cell]), the deviation of its post-collision populations from
+ * E_q = w_q (P + c_q.J + (c_q.J)^2 / 2), J = 3 rho v, P = rho - 1 -
+ * 1.5 rho v.v: f*neq_q = f*_q - E_q, which is (1 - 1/tau)(f_q - f_q^eq) +
+ * S_q + w_q rho (1 - rho)(3 c_q.v)^2 / 2 (E_q is the equilibrium of Eq. 20
+ * but for the last term).  The slots hold the directions grouped by c_z:
+ * slots 0..8 = directions 0, 1, 2, 3, 6, 7, 10, 11, 18 (c_z = 0), 9..13 =
+ * 4, 8, 12, 14, 16 (c_z = +1), 14..18 = their opposites 5, 13, 9, 17, 15.
+ * 108 B per cell per step instead of 152.  A
+ * pulling cell rebuilds each incoming population as E_q(source) + f*neq_q.
  * The moments buffer of the current state is the velocity field that
  * ib_interp reads (every cell; no row-flag velocity output).  Same step as
- * lb_create otherwise.  All buffers 16-byte aligned; g and the flags are
- * cleared (synchronises). */
+ * lb_create otherwise.  When nx is a multiple of 8 the step moves its tiles
+ * with TMA (tensor maps of the four buffers are encoded here; the buffers
+ * must stay where they are for the life of the context).  All buffers
+ * 16-byte aligned; g and the flags are cleared (synchronises). */
 int lb_create_mixed(const lb_params* p, void* fneq_a, void* fneq_b, float* m_a, float* m_b, float* g,
                     uint32_t* row_flags, lb_ctx** out);
 
 /* The current post-collision state as FP32 shifted populations f - w_q,
  * [q][cell], into f_out (device, 19 * n_cells floats): a copy for FP32
- * storage, the reconstruction f_eq(rho, v) + f*neq for mixed storage. */
+ * storage, the reconstruction E_q(rho, v) + f*neq_q for mixed storage. */
 int lb_export(lb_ctx* ctx, float* f_out, void* stream);
 int lb_destroy(lb_ctx* ctx);
 
@@ -141,10 +149,12 @@ int lb_init_shear(lb_ctx* ctx, void* stream);
 int lb_step(lb_ctx* ctx, int nsteps, void* stream);
 
 /* Launch shape of lb_step (no paper counterpart; the result does not depend
- * on it).  FP32 storage: threads per block along x, shape 0..3 = 128, 32,
- * 64, 256 (capped at nx rounded up to 32).  Mixed storage: the (x, y) column
- * tile of the marching kernel, shape 0..3 = 32x8, 32x4, 64x4, 16x8.  Default
- * 0. */
+ * on it beyond FP32 rounding).  FP32 storage: threads per block along x,
+ * shape 0..3 = 128, 32, 64, 256 (capped at nx rounded up to 32).  Mixed
+ * storage: the (x, y) column tile of the marching kernel; with nx a multiple
+ * of 8, shape 0, 1 = the kernel with plain loads and 32x4, 32x8 columns and
+ * 2, 3 = the TMA-staged kernel with 32x8, 32x4 columns; otherwise shape 0..3
+ * = plain loads with 32x8, 32x4, 64x4, 16x8.  Default 0. */
 #define PFSI_LB_SHAPES 4
 int lb_set_shape(lb_ctx* ctx, int shape);
 int lb_get_shape(const lb_ctx* ctx, int* shape);

@@ -15,13 +15,15 @@
 // kernel, the force (16 B read, 16 B cleared) and the velocity (16 B).
 //
 // Mixed storage keeps, per cell, the post-collision non-equilibrium part
-// f*neq_q = f*_q - f_q^eq(rho, v) in 16 bits and m = (v, rho - 1) in FP32
-// (108 B per cell per step).  The state is the same as the FP32 one up to
-// the rounding of f*neq: a pulling cell rebuilds f*_q of its source cell as
-// f_q^eq(m of the source) + f*neq_q, collides in FP32 exactly as above and
-// stores its own f*neq and m.  The 18 neighbour moments a cell reads are
-// shared with its neighbours and come from L1/L2; only the own cell's m
-// travels from DRAM.
+// f*neq_q = f*_q - E_q(m) in 16 bits and m = (v, rho - 1) in FP32 (108 B per
+// cell per step), E_q the split of pfsi_internal.cuh (the equilibrium of
+// Eq. 20 up to w_q rho (1 - rho) (3 c.v)^2 / 2).  The state is the same as
+// the FP32 one up to the rounding of f*neq: a pulling cell rebuilds f*_q of
+// its source cell as E_q(m of the source) + f*neq_q, collides in FP32 exactly
+// as above and stores its own f*neq and m.  The 18 neighbour moments a cell
+// reads are shared with its neighbours; only the own cell's m travels from
+// DRAM.  lb_tma.cu holds the TMA-staged kernel of this storage; the kernel
+// here serves grids whose rows do not start on 16-byte boundaries.
 #include <algorithm>
 #include <climits>
 #include <string>
@@ -38,41 +40,6 @@ namespace {
 
 constexpr int kRowBlock = 128;     // default threads per block along x (FP32 kernel)
 constexpr int kMaxRowBlock = 256;
-
-// On-site velocity wall (Eq. 23-30, Hecht and Harting) on shifted
-// populations f~ = f - w: s = +1 at the bottom (k = 0), -1 at the top
-// (k = nz - 1, the mirror image); the populations with c_z = s entering the
-// fluid are set from the known ones so that the node carries the wall
-// velocity vw.  With the shift, rho = (1 + S~)/(1 - s vz), S~ = sum over
-// c_z = 0 of f~ + 2 sum over c_z = -s of f~ (the weights of those sets add up
-// to 1), and N_x = 1/2 sum over c_z = 0 of c_x f~ - rho vx / 3 (Eq. 29).
-template <int s>
-__device__ __forceinline__ void onsite_wall(float* f, float3 vw)
-{
-    float S = 0.f, jx = 0.f, jy = 0.f;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        if (czq(q) == 0) {
-            S += f[q];
-            if (cxq(q)) jx += cxq(q) * f[q];
-            if (cyq(q)) jy += cyq(q) * f[q];
-        } else if (czq(q) == -s) {
-            S += 2.0f * f[q];
-        }
-    }
-    const float rho = (1.0f + S) / (1.0f - s * vw.z);
-    const float Nx = 0.5f * jx - rho * vw.x * (1.0f / 3.0f);
-    const float Ny = 0.5f * jy - rho * vw.y * (1.0f / 3.0f);
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        if (czq(q) != s) continue;
-        const float cv = cxq(q) * vw.x + cyq(q) * vw.y + czq(q) * vw.z;
-        if (cxq(q) == 0 && cyq(q) == 0)
-            f[q] = f[oppq(q)] + rho * cv * (1.0f / 3.0f);
-        else
-            f[q] = f[oppq(q)] + rho * cv * (1.0f / 6.0f) - cxq(q) * Nx - cyq(q) * Ny;
-    }
-}
 
 __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     const float* __restrict__ fin, float* __restrict__ fout, float4* __restrict__ g,
@@ -184,18 +151,6 @@ struct Neq<PFSI_LB_FP16> {
     static __device__ __forceinline__ T put(float x, float scale) { return __float2half_rn(x * scale); }
 };
 
-// f_q^eq(rho, v) - w_q (Eq. 20) from m = (v, rho - 1).
-template <int q>
-__device__ __forceinline__ float feq_shifted(float4 m)
-{
-    float cv = 0.f;
-    if (cxq(q)) cv += cxq(q) * m.x;
-    if (cyq(q)) cv += cyq(q) * m.y;
-    if (czq(q)) cv += czq(q) * m.z;
-    const float vv = m.x * m.x + m.y * m.y + m.z * m.z;
-    return wq(q) * (m.w + (1.0f + m.w) * (3.0f * cv + 4.5f * cv * cv - 1.5f * vv));
-}
-
 // Mixed kernel blocking: a block takes a 32 x 8 (x, y) column of cells and
 // marches it through kz consecutive planes.  The moments of the column plus
 // a one-cell halo are kept for the planes k - 1, k, k + 1 in a shared ring
@@ -204,11 +159,9 @@ __device__ __forceinline__ float feq_shifted(float4 m)
 // ~(340 / 256)(kz + 2) / kz times per step instead of 19 times through L1.
 // A warp is one tile row.
 //
-// The ring holds each cell's moments in the form the rebuild wants:
-// with V = 3v and P = (rho - 1) - 1.5 rho v.v,
-//   f_q^eq - w_q = w_q (P + rho (c.V)(1 + (c.V)/2)),
-// four operations per pulled population.  The collision uses the same
-// factoring (and 3F for the source term).
+// The ring holds each cell's record in the form the rebuild wants, (P, J)
+// of split_record, so that E_q costs three operations per pulled
+// population.
 template <int TX_, int TY_>
 struct Tile {
     static constexpr int TX = TX_, TY = TY_;
@@ -221,8 +174,7 @@ constexpr int kSlots = 4;
 
 template <class T>
 struct Ring {
-    float4 pv[kSlots][T::Plane];   // (P, Vx, Vy, Vz)
-    float rho[kSlots][T::Plane];
+    float4 pj[kSlots][T::Plane];   // (P, Jx, Jy, Jz)
 };
 
 template <class T>
@@ -241,35 +193,18 @@ __device__ __forceinline__ void halo_store(Ring<T>& ring, int slot, const float4
 #pragma unroll
     for (int u = 0; u < T::Halo; ++u) {
         const int h = threadIdx.x + u * T::Threads;
-        if (h < T::Plane) {
-            const float4 m = r[u];
-            const float rho = 1.0f + m.w;
-            const float vv = m.x * m.x + m.y * m.y + m.z * m.z;
-            ring.pv[slot][h] = make_float4(m.w - 1.5f * rho * vv, 3.0f * m.x, 3.0f * m.y, 3.0f * m.z);
-            ring.rho[slot][h] = rho;
-        }
+        if (h < T::Plane) ring.pj[slot][h] = split_record(r[u]);
     }
 }
 
-__device__ __forceinline__ float c_dot(int q, float x, float y, float z)
-{
-    float s = 0.f;
-    if (cxq(q)) s += cxq(q) * x;
-    if (cyq(q)) s += cyq(q) * y;
-    if (czq(q)) s += czq(q) * z;
-    return s;
-}
-
-// f_q^eq - w_q of a ring cell, for direction q.
+// E_q of a ring cell, for direction q.
 template <int q, class T>
 __device__ __forceinline__ float feq_ring(const Ring<T>& ring, int slot, int h)
 {
-    const float4 a = ring.pv[slot][h];
-    const float cv = c_dot(q, a.y, a.z, a.w);
-    return wq(q) * fmaf(ring.rho[slot][h], fmaf(0.5f * cv, cv, cv), a.x);
+    return wq(q) * split_eq<q>(ring.pj[slot][h]);
 }
 
-// f[q] += f_q^eq of the source cell (bounce-back: the own cell's opposite
+// f[q] += E_q of the source cell (bounce-back: the own cell's opposite
 // population, plus the moving-wall term at the top).  sm, s0, sp: ring slots
 // of the planes k - 1, k, k + 1.
 template <int q, class T>
@@ -301,11 +236,11 @@ __device__ __forceinline__ void load_neq(const uint16_t* __restrict__ nin, uint3
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         if ((czq(q) == 1 && k == 0) || (czq(q) == -1 && k == nz - 1)) {
-            raw[q] = nin[oppq(q) * N + cell];
+            raw[q] = nin[nslot(oppq(q)) * N + cell];
         } else {
             const int sx = cxq(q) == 1 ? xm : (cxq(q) == -1 ? xp : i);
             const int sy = cyq(q) == 1 ? ym : (cyq(q) == -1 ? yp : j);
-            raw[q] = nin[q * N + ((k - czq(q)) * ny + sy) * nx + sx];
+            raw[q] = nin[nslot(q) * N + ((k - czq(q)) * ny + sy) * nx + sx];
         }
     }
 }
@@ -315,6 +250,32 @@ __device__ __forceinline__ float neq_value(uint32_t raw, float inv_scale)
 {
     if (kMode == PFSI_LB_BF16) return __uint_as_float(raw << 16);
     return __half2float(__ushort_as_half((unsigned short)raw)) * inv_scale;
+}
+
+// Stored values of the pair (q, opposite of q) of one cell: the part even
+// in c is w E0 + cv (h + b), the odd part a + b (see k_lb_step_mixed).
+template <int kMode, int q>
+__device__ __forceinline__ void store_pair(typename Neq<kMode>::T* __restrict__ nout, int N, int cell, const float* f,
+                                           float vx, float vy, float vz, float3 F3, float rk, float rh, float keep,
+                                           float E0, float guo, float scale)
+{
+    if (q == 18 || oppq(q) < q) return;
+    const float cv = cdot<q>(vx, vy, vz), cF = cdot<q>(F3.x, F3.y, F3.z);
+    const float wcv = wq(q) * cv;
+    const float a = rk * wcv;
+    const float b = (wq(q) * guo) * cF;
+    const float odd = a + b;
+    const float even = fmaf(cv, fmaf(rh, wcv, b), wq(q) * E0);
+    nout[nslot(q) * N + cell] = Neq<kMode>::put(fmaf(keep, f[q], even + odd), scale);
+    nout[nslot(oppq(q)) * N + cell] = Neq<kMode>::put(fmaf(keep, f[oppq(q)], even - odd), scale);
+}
+
+template <int kMode, int... Q>
+__device__ __forceinline__ void store_pairs(std::integer_sequence<int, Q...>, typename Neq<kMode>::T* __restrict__ nout,
+                                            int N, int cell, const float* f, float vx, float vy, float vz, float3 F3,
+                                            float rk, float rh, float keep, float E0, float guo, float scale)
+{
+    (store_pair<kMode, Q>(nout, N, cell, f, vx, vy, vz, F3, rk, rh, keep, E0, guo, scale), ...);
 }
 
 template <int kMode, class T>
@@ -402,26 +363,18 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
             const float VV = vx * vx + vy * vy + vz * vz;                           // 9 v.v
             const float P0 = fmaf(-rho / 6.0f, VV, drho);                            // drho - 1.5 rho v.v
             const float vF3 = (vx * F3.x + vy * F3.y + vz * F3.z) * (1.0f / 3.0f);  // 3 v.F
-            // post-collision minus equilibrium, (1 - omega)(f - f^eq) + S, with
-            // (f^eq - w)/w = P0 + rho (cv + cv^2/2) and S/(w guo) = cF (1 + cv) - vF3
-            // (cv = 3 c.v, cF = 3 c.F), per pair of opposite directions: with
-            //   a = -keep w rho cv,  b = w guo cF,  E0 = -keep P0 - guo vF3,
-            // the part even in c is w E0 + cv (a/2 + b), the odd part a + b.
+            // stored f* - E = (1 - omega)(f - f^eq) + S + (f^eq - E), with
+            // (f^eq - w)/w = P0 + rho (cv + cv^2/2), S/(w guo) = cF (1 + cv) - vF3
+            // and (f^eq - E)/w = rho (1 - rho) cv^2 / 2 (cv = 3 c.v, cF = 3 c.F),
+            // per pair of opposite directions: with
+            //   a = -keep w rho cv,  h = w rho cv (omega - rho) / 2,  b = w guo cF,
+            //   E0 = -keep P0 - guo vF3,
+            // the part even in c is w E0 + cv (h + b), the odd part a + b.
             const float E0 = fmaf(-keep, P0, -guo * vF3);
-            nout[18 * N + cell] = Neq<kMode>::put(fmaf(keep, f[18], wq(18) * E0), scale);
-#pragma unroll
-            for (int q = 0; q < 18; ++q) {
-                if (oppq(q) < q) continue;
-                const int o = oppq(q);
-                const float cv = c_dot(q, vx, vy, vz);
-                const float cF = c_dot(q, F3.x, F3.y, F3.z);
-                const float a = (-keep * wq(q)) * rho * cv;
-                const float b = (wq(q) * guo) * cF;
-                const float odd = a + b;
-                const float even = fmaf(cv, fmaf(0.5f, a, b), wq(q) * E0);
-                nout[q * N + cell] = Neq<kMode>::put(fmaf(keep, f[q], even + odd), scale);
-                nout[o * N + cell] = Neq<kMode>::put(fmaf(keep, f[o], even - odd), scale);
-            }
+            const float rh = 0.5f * rho * (omega - rho);
+            nout[nslot(18) * N + cell] = Neq<kMode>::put(fmaf(keep, f[18], wq(18) * E0), scale);
+            store_pairs<kMode>(std::make_integer_sequence<int, 18>{}, nout, N, cell, f, vx, vy, vz, F3,
+                               -keep * rho, rh, keep, E0, guo, scale);
             mout[cell] = make_float4(vx * (1.0f / 3.0f), vy * (1.0f / 3.0f), vz * (1.0f / 3.0f), drho);
             if (forced) g[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -434,7 +387,7 @@ template <int kMode, int q>
 __device__ __forceinline__ void export_q(const typename Neq<kMode>::T* __restrict__ nin, float4 m,
                                          float* __restrict__ fout, int N, int cell, float inv_scale)
 {
-    fout[q * N + cell] = feq_shifted<q>(m) + Neq<kMode>::get(nin[q * N + cell], inv_scale);
+    fout[q * N + cell] = wq(q) * split_eq<q>(split_record(m)) + Neq<kMode>::get(nin[nslot(q) * N + cell], inv_scale);
 }
 
 template <int kMode, int... Q>
@@ -532,7 +485,7 @@ __global__ void k_lb_init_shear_mixed(typename Neq<kMode>::T* __restrict__ nout,
         const int cell = k * plane + i;
         mout[cell] = m;
 #pragma unroll
-        for (int q = 0; q < 19; ++q) nout[q * N + cell] = val[q];
+        for (int q = 0; q < 19; ++q) nout[nslot(q) * N + cell] = val[q];
     }
 }
 
@@ -550,10 +503,11 @@ __global__ void k_lb_moments_mixed(const typename Neq<kMode>::T* __restrict__ ni
         double sd = 0, mx = 0, my = 0, mz = 0;
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
+            // E_q of the split (pfsi_internal.cuh) in FP64: P + c.J + (c.J)^2 / 2
             const double w = q < 6 ? 1.0 / 18.0 : (q < 18 ? 1.0 / 36.0 : 1.0 / 3.0);
-            const double cv = cxq(q) * vx + cyq(q) * vy + czq(q) * vz;
-            const double fq = w * (d + (1.0 + d) * (3.0 * cv + 4.5 * cv * cv - 1.5 * vv)) +
-                              (double)Neq<kMode>::get(nin[q * N + cell], inv_scale);
+            const double cj = 3.0 * (1.0 + d) * (cxq(q) * vx + cyq(q) * vy + czq(q) * vz);
+            const double fq = w * (d - 1.5 * (1.0 + d) * vv + cj + 0.5 * cj * cj) +
+                              (double)Neq<kMode>::get(nin[nslot(q) * N + cell], inv_scale);
             sd += fq;
             mx += cxq(q) * fq;
             my += cyq(q) * fq;
@@ -602,6 +556,16 @@ template <int kMode>
 cudaError_t launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop,
                                float inv_scale)
 {
+    if (c->tma) {
+        // shapes 0, 1: this kernel with 32 x 4 or 32 x 8 columns (the faster
+        // on B300); 2, 3: the TMA-staged kernel with 32 x 8 or 32 x 4 columns
+        switch (c->shape) {
+        case 0: return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
+        case 1: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
+        case 2: return lb_tma_launch(c, c->tma, 0, s, omega, guo, body, utop, inv_scale);
+        default: return lb_tma_launch(c, c->tma, 1, s, omega, guo, body, utop, inv_scale);
+        }
+    }
     switch (c->shape) {
     case 1: return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
     case 2: return launch_mixed<kMode, Tile<64, 4>>(c, s, omega, guo, body, utop, inv_scale);
@@ -699,10 +663,13 @@ int create_common(const char* who, const lb_params* p, void* f_a, void* f_b, flo
     c->m[0] = reinterpret_cast<float4*>(m_a);
     c->m[1] = reinterpret_cast<float4*>(m_b);
     c->flags = row_flags;
+    c->tma = nullptr;
+    if (p->storage != PFSI_LB_FP32) c->tma = lb_tma_create(c);
     rc = check_cuda(cudaMemsetAsync(c->g, 0, sz.g_bytes, 0), "lb_create: clear g");
     if (!rc) rc = check_cuda(cudaMemsetAsync(c->flags, 0, sz.flag_bytes, 0), "lb_create: clear flags");
     if (!rc) rc = check_cuda(cudaStreamSynchronize(0), "lb_create: synchronise");
     if (rc) {
+        lb_tma_destroy(c->tma);
         delete c;
         return rc;
     }
@@ -733,6 +700,7 @@ extern "C" int lb_create_mixed(const lb_params* p, void* fneq_a, void* fneq_b, f
 
 extern "C" int lb_destroy(lb_ctx* ctx)
 {
+    if (ctx) lb_tma_destroy(ctx->tma);
     delete ctx;
     return PFSI_OK;
 }

@@ -97,6 +97,93 @@ __host__ __device__ __forceinline__ constexpr float wq(int q)
     return q < 6 ? (1.0f / 18.0f) : q < 18 ? (1.0f / 36.0f) : (1.0f / 3.0f);
 }
 
+// On-site velocity wall (Eq. 23-30, Hecht and Harting) on shifted
+// populations f~ = f - w: s = +1 at the bottom (k = 0), -1 at the top
+// (k = nz - 1, the mirror image); the populations with c_z = s entering the
+// fluid are set from the known ones so that the node carries the wall
+// velocity vw.  With the shift, rho = (1 + S~)/(1 - s vz), S~ = sum over
+// c_z = 0 of f~ + 2 sum over c_z = -s of f~ (the weights of those sets add up
+// to 1), and N_x = 1/2 sum over c_z = 0 of c_x f~ - rho vx / 3 (Eq. 29).
+template <int s>
+__device__ __forceinline__ void onsite_wall(float* f, float3 vw)
+{
+    float S = 0.f, jx = 0.f, jy = 0.f;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (czq(q) == 0) {
+            S += f[q];
+            if (cxq(q)) jx += cxq(q) * f[q];
+            if (cyq(q)) jy += cyq(q) * f[q];
+        } else if (czq(q) == -s) {
+            S += 2.0f * f[q];
+        }
+    }
+    const float rho = (1.0f + S) / (1.0f - s * vw.z);
+    const float Nx = 0.5f * jx - rho * vw.x * (1.0f / 3.0f);
+    const float Ny = 0.5f * jy - rho * vw.y * (1.0f / 3.0f);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        if (czq(q) != s) continue;
+        const float cv = cxq(q) * vw.x + cyq(q) * vw.y + czq(q) * vw.z;
+        if (cxq(q) == 0 && cyq(q) == 0)
+            f[q] = f[oppq(q)] + rho * cv * (1.0f / 3.0f);
+        else
+            f[q] = f[oppq(q)] + rho * cv * (1.0f / 6.0f) - cxq(q) * Nx - cyq(q) * Ny;
+    }
+}
+
+// Mixed storage keeps a cell's 19 stored values in slot order, grouped by
+// c_z so that each group of a plane is one contiguous block of the [slot][cell]
+// array: slots 0..8 the directions with c_z = 0, 9..13 those with c_z = +1,
+// 14..18 their opposites in the same order (slot 14 + i holds the opposite
+// of slot 9 + i).
+__host__ __device__ __forceinline__ constexpr int nslot(int q)
+{
+    return q <= 3 ? q
+           : q == 6 ? 4 : q == 7 ? 5 : q == 10 ? 6 : q == 11 ? 7 : q == 18 ? 8
+           : q == 4 ? 9 : q == 8 ? 10 : q == 12 ? 11 : q == 14 ? 12 : q == 16 ? 13
+           : q == 5 ? 14 : q == 13 ? 15 : q == 9 ? 16 : q == 17 ? 17 : 18;
+}
+
+// Mixed storage (16-bit f*neq): a population is split as f*_q = E_q(m) +
+// stored_q, with the moment record m = (v, rho - 1) of its cell and
+// E_q = w_q (P + c.J + (c.J)^2 / 2), J = 3 rho v, P = rho - 1 - 1.5 rho v.v.
+// E_q differs from the equilibrium of Eq. 20 only by w_q rho (1 - rho)
+// (3 c.v)^2 / 2; the collision (which uses the equilibrium of Eq. 20) writes
+// f*_q - E_q.  Every kernel that rebuilds populations uses these two
+// functions, so the split is the same everywhere.
+// record (v, rho - 1) -> (P, J): P = rho - 1 - 1.5 rho v.v, J = 3 rho v.
+__device__ __forceinline__ float4 split_record(float4 m)
+{
+    const float r3 = fmaf(3.0f, m.w, 3.0f);
+    const float vv = fmaf(m.x, m.x, fmaf(m.y, m.y, m.z * m.z));
+    return make_float4(fmaf(-0.5f * r3, vv, m.w), r3 * m.x, r3 * m.y, r3 * m.z);
+}
+
+// c_q . (x, y, z) with the nonzero terms only (a sum started from 0.f would
+// keep an addition for the sign of zero)
+template <int q>
+__device__ __forceinline__ float cdot(float x, float y, float z)
+{
+    constexpr int cx = cxq(q), cy = cyq(q), cz = czq(q);
+    const float a = cx > 0 ? x : -x, b = cy > 0 ? y : -y, c = cz > 0 ? z : -z;
+    if (cx != 0 && cy != 0) return a + b;
+    if (cx != 0 && cz != 0) return a + c;
+    if (cy != 0 && cz != 0) return b + c;
+    if (cx != 0) return a;
+    if (cy != 0) return b;
+    if (cz != 0) return c;
+    return 0.f;
+}
+
+// E_q / w_q of a record: P + c.J + (c.J)^2 / 2
+template <int q>
+__device__ __forceinline__ float split_eq(float4 r)
+{
+    const float cj = cdot<q>(r.y, r.z, r.w);
+    return fmaf(cj, fmaf(cj, 0.5f, 1.0f), r.x);
+}
+
 // ---------------------------------------------------------------- Philox
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds, multipliers 0xD2511F53,
 // 0xCD9E8D57, key schedule by the Weyl constants 0x9E3779B9, 0xBB67AE85.
@@ -133,7 +220,19 @@ struct LbCtx {
     float4* m[2];        // mixed storage: (v, rho - 1) of every cell, with f[]
     uint32_t* flags;
     int shape;           // launch shape of lb_step (0: default), see lb_set_shape
+    struct LbTma* tma;   // mixed storage: tensor maps of the TMA-staged kernel (lb_tma.cu), or null
 };
+
+// TMA-staged step of the mixed storage (lb_tma.cu): usable when the row
+// pitch of the 16-bit tensor is a multiple of 16 bytes (nx % 8 == 0).
+bool lb_tma_supported(const LbCtx* c);
+struct LbTma* lb_tma_create(const LbCtx* c);   // null if unsupported or the driver lacks TMA encoding
+void lb_tma_destroy(struct LbTma* t);
+// tile: 0 = 32 x 8 columns, 1 = 32 x 4
+cudaError_t lb_tma_launch(const LbCtx* c, const struct LbTma* t, int tile, cudaStream_t s, float omega, float guo,
+                          float3 body, float3 utop, float inv_scale);
+// bit 0: a bounded wait of the TMA-staged kernel gave up (since the last clear)
+int lb_tma_status(unsigned int* out, bool clear);
 
 // Velocity field the interpolation reads after a lattice step.
 inline float4* velocity_field(const LbCtx* c) { return c->p.storage ? c->m[c->cur] : c->v; }

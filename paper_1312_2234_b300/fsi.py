@@ -969,6 +969,12 @@ def lb_set_shape(lat, shape):
     _call("lb_set_shape", lat.h, int(shape))
 
 
+def lb_get_shape(lat):
+    sh = c_int()
+    _call("lb_get_shape", lat.h, ctypes.byref(sh))
+    return sh.value
+
+
 class Batch:
     """Independent chambers stepped by one CUDA graph launch (each chamber's
     kernels on a parallel branch)."""

@@ -12,7 +12,10 @@ rounding of force spreading, whose tile sums are added with FP32 atomics in
 no fixed order (1e-6 of the largest entry).  With 16-bit population storage
 such a difference can move a stored f*neq across a rounding boundary: one
 BF16 step is at most 2^-7 of the stored value, so the populations agree to
-2^-7 of the largest population (positions and bond states as for FP32)."""
+2^-7 of the largest population, and a node velocity can move by up to that
+step, 2^-7 max|f*neq| (~9e-6 x 2^-7 in this fast shear flow, against node
+velocities ~1e-4): positions within 1e-4 of the largest displacement
+(measured 8e-6), bond states as for FP32."""
 import numpy as np
 import pytest
 import torch
@@ -82,7 +85,8 @@ def test_checkpoint_resume_continues_the_run(storage, tmp_path):
     torch.cuda.synchronize()
     assert a.step_index == b.step_index == 8
     X0 = w["X"]
-    assert rel(b.X.cpu().numpy() - X0, a.X.cpu().numpy() - X0) < 1e-6
+    tol_x = 1e-6 if storage == "fp32" else 1e-4
+    assert rel(b.X.cpu().numpy() - X0, a.X.cpu().numpy() - X0) < tol_x
     tol_f = 1e-6 if storage == "fp32" else 2.0 ** -7
     assert rel(b.lattice.export().cpu().numpy(), a.lattice.export().cpu().numpy()) < tol_f
     assert np.array_equal(b.bonds.bound.cpu().numpy(), a.bonds.bound.cpu().numpy())

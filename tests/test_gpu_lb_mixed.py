@@ -183,3 +183,68 @@ def test_state_varying_along_x(storage, dims):
     bound_f = 1e-5 * np.abs(fs).max() + n * UNIT[storage] * fneq_max
     err_f = np.abs(lat.export().cpu().numpy() - fs).max()
     assert err_f <= bound_f, (err_f, bound_f)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+@pytest.mark.parametrize("dims", [(48, 17, 13), (8, 5, 4), (64, 9, 6), (16, 3, 5), (40, 24, 7)])
+def test_launch_shapes_rows_on_16_byte_boundaries(storage, shape, dims):
+    """Grids whose x rows start on 16-byte boundaries (nx a multiple of 8):
+    shapes 0 and 1 run the kernel with plain loads (32x4 and 32x8 columns),
+    2 and 3 the TMA-staged kernel (32x8 and 32x4 columns).  Columns wider or taller than the grid,
+    partial columns at the far edges, the periodic halo of every edge column
+    and both wall planes; a state that varies from cell to cell and a
+    flagged force, against the oracle with the bounds of test_free_steps."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    lat = fsi.Lattice(nx, ny, nz, 0.8, (4e-3, -1.5e-3, 0.0), (2e-6, 0.0, -1e-6), storage=storage)
+    fsi.lb_set_shape(lat, shape)
+    lat.init_shear()
+    rng = np.random.default_rng(13)
+    live = 0 if lat.velocity().data_ptr() == lat.m[0].data_ptr() else 1
+    cur = lat.f[live]
+    noise = torch.from_numpy((3e-5 * rng.standard_normal(tuple(cur.shape))).astype(np.float32)).cuda()
+    cur.copy_((cur.float() + noise * (1.0 if storage == "bf16" else 2.0 ** lat.p.fp16_exponent)).to(cur.dtype))
+    f0 = lat.export().cpu().numpy().astype(np.float64)
+    flags = (rng.uniform(size=ny * nz) < 0.4).astype(np.int32)
+    g = np.zeros((N, 4), np.float32)
+    rows = np.repeat(flags, nx).astype(bool)
+    g[rows, :3] = (1e-5 * rng.standard_normal((rows.sum(), 3))).astype(np.float32)
+    g64 = np.ascontiguousarray(g[:, :3].astype(np.float64).T).ravel()
+    _, w = oracle.lattice()
+    p = oracle.lb_params(nx, ny, nz, f32(0.8), (f32(4e-3), f32(-1.5e-3), 0.0), (f32(2e-6), 0.0, f32(-1e-6)))
+    f = (f0 + w[:, None]).ravel()
+    n = 6
+    fneq_max = 0.0
+    for _ in range(n):
+        lat.g.copy_(torch.from_numpy(g))
+        lat.flags.copy_(torch.from_numpy(flags))
+        lat.step(1)
+        f, rho, v = oracle.lb_step(p, f, g64)
+        fs = f.reshape(19, N) - w[:, None]
+        fneq_max = max(fneq_max, float(np.abs(fs - feq_shifted(rho, v.reshape(3, N))).max()))
+    torch.cuda.synchronize()
+    bound_f = 1e-5 * np.abs(fs).max() + n * UNIT[storage] * fneq_max
+    err_f = np.abs(lat.export().cpu().numpy() - fs).max()
+    assert err_f <= bound_f, (err_f, bound_f)
+    m = lat.velocity().cpu().numpy()
+    assert np.abs(m[:, :3].T - v.reshape(3, N)).max() <= 10 * bound_f
+    assert np.all(lat.g.cpu().numpy()[rows] == 0)
+    assert fsi.lb_get_shape(lat) == shape
+
+
+def test_shapes_share_one_state():
+    """The TMA-staged kernel and the plain-load kernel read and write the
+    same stored state: alternating them step by step matches one kernel
+    throughout to the rounding of the 16-bit values."""
+    dims = (64, 24, 10)
+    runs = []
+    for order in ([0] * 8, [0, 2, 1, 3, 0, 2, 1, 3]):
+        lat = fsi.Lattice(*dims, 0.8, (4e-3, 0.0, 0.0), storage="bf16")
+        lat.init_shear()
+        for s in order:
+            fsi.lb_set_shape(lat, s)
+            lat.step(1)
+        runs.append(lat.export().cpu().numpy())
+    scale = np.abs(runs[0]).max()
+    assert np.abs(runs[0] - runs[1]).max() <= 1e-5 * scale
