@@ -550,9 +550,12 @@ def timed_steps(step, steps, stream):
 def run_batched(args, dev, stream):
     """64 independent chambers of uneven sizes (48..128 per side), one
     platelet each: stepped one chamber at a time (one graph launch per
-    chamber), then as one batch (one graph launch for all chambers), with
-    FP32 populations and with 16-bit f^neq storage (launch shapes tuned per
-    chamber)."""
+    chamber), then as one batch (one graph launch for all chambers per step,
+    every kernel of the step one launch for all 64 chambers; the lattice
+    update one persistent launch per storage mode, its column shapes and
+    grid tuned), with FP32 populations and with 16-bit f^neq storage.  The
+    lattice-only batched step (lb_batch_step on the 64 lattices) is timed
+    too, against the HBM roofline."""
     import torch
     from paper_1312_2234_b300 import fsi, workload
     ws_ = workload.config_batched(seed=0)
@@ -562,8 +565,10 @@ def run_batched(args, dev, stream):
     out = {"workload": "64 chambers, sides 48..128, shear 500..3000/s, 2000..25000 receptors, stiffness x0.5..2, "
                        "one platelet (2562 + 800 SCE) each", "cells": cells, "nodes": nodes, "steps": steps,
            "l2": "working set far above L2 (no flush)"}
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6400.0
     for storage in ("fp32", "bf16", "fp16"):
-        sims = [fsi.Simulation(w, device=dev, storage=storage, tune=storage != "fp32") for w in ws_]
+        sims = [fsi.Simulation(w, device=dev, storage=storage) for w in ws_]
         if storage == "fp32":
             for _ in range(warm):
                 for sm in sims:
@@ -571,16 +576,42 @@ def run_batched(args, dev, stream):
             t = timed_steps(lambda: [sm.step(1) for sm in sims], steps, stream)
             out["fp32_one_launch_per_chamber"] = {"value": cells * steps / t / 1e6, "unit": "MLUPS",
                                                   "ms_per_step": 1e3 * t / steps}
-        batch = fsi.Batch(sims, steps_per_graph=1)
+        batch = fsi.Batch(sims, steps_per_graph=1, tune=True)
         batch.step(warm)
         t = timed_steps(lambda: batch.step(1), steps, stream)
         out[storage + "_batched"] = {"value": cells * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps,
                                      "node_updates_per_s": nodes * steps / t}
-        if storage != "fp32":
-            out[storage + "_batched"]["shapes"] = sorted({int(sm.shape) for sm in sims})
         del batch, sims
         torch.cuda.empty_cache()
+        # the lattice update alone: the same 64 lattices in one LatticeBatch
+        lats = [fsi.Lattice(w["grid"]["nx"], w["grid"]["ny"], w["grid"]["nz"], w["grid"]["tau"], w["grid"]["u_top"],
+                            device=dev, storage=storage) for w in ws_]
+        for lat in lats:
+            lat.init_shear()
+        lb = fsi.LatticeBatch(lats)
+        lb.autotune(reps=3)
+        lb.step(warm)
+        t = timed_steps(lambda: lb.step(1), steps, stream)
+        per_cell = LB_BYTES_PER_CELL if storage == "fp32" else LB_BYTES_PER_CELL_MIXED
+        gbs = per_cell * cells / (t / steps) / 1e9
+        out[storage + "_lattice_batch"] = {"value": cells * steps / t / 1e6, "unit": "MLUPS",
+                                           "ms_per_step": 1e3 * t / steps, "bytes_per_cell": per_cell,
+                                           "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+        if storage != "fp32":
+            shp = lb.shapes()
+            out[storage + "_lattice_batch"]["shapes"] = {n: shp.count(i) for i, n in
+                                                         enumerate(("32x8", "64x4", "16x16"))}
+        del lb, lats
+        torch.cuda.empty_cache()
     return out
+
+
+def run_batched_only(args):
+    import torch
+    torch.cuda.init()
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream()
+    print(json.dumps(run_batched(args, dev, stream)))
 
 
 def run_surrogate(args, w_channel, sim_channel, dev, stream):
@@ -928,7 +959,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=1, help="0: skip the oracle's cpu_baseline leg")
-    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges", "full"],
+    ap.add_argument("--kernel", default=None, choices=[None, "lb", "surrogate", "fem", "bridges", "full", "batch"],
                     help="time one kernel alone")
     ap.add_argument("--grid", default="256x128x128", help="grid of --kernel lb")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"], help="lattice storage of --kernel lb")
@@ -954,6 +985,9 @@ def main():
         return
     if args.kernel == "full":
         run_full_only(args)
+        return
+    if args.kernel == "batch":
+        run_batched_only(args)
         return
     rank, ws = dist_setup()
     if args.impl == "reference":

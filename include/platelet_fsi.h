@@ -673,20 +673,83 @@ int sim_lb_ms(sim_ctx* ctx, float* ms);
 /* ===================================================================== *
  * Batches of independent chambers (no paper counterpart)
  * ===================================================================== */
+typedef struct lb_batch lb_batch;
+
+/* A batch of n lattices of any sizes and storage modes (all at the same
+ * buffer parity; the lattices stay owned by the caller and must outlive the
+ * batch).  lb_batch_step advances every lattice by one lb_step per step with
+ * ONE kernel launch per storage mode present: the cells of all lattices are
+ * cut into tiles (FP32: 256 consecutive cells in x-fastest order; mixed
+ * storage: (x, y) columns of 32x8, 64x4 or 16x16 cells over up to 16
+ * planes, the shape picked per lattice), listed lattice after lattice, and
+ * a persistent grid of as many 256-thread blocks as are resident on the GPU
+ * at once walks the list.  Every tile runs the per-cell arithmetic of
+ * lb_step, so each lattice's populations are bit-identical to lb_step on it
+ * alone.  The initial column shape of a mixed lattice is the one with the
+ * fewest threads counting idle ones in ragged columns (and a quarter per
+ * ring cell). */
+int lb_batch_create(lb_ctx* const* lattices, int n, lb_batch** out);
+int lb_batch_destroy(lb_batch* b);
+int lb_batch_step(lb_batch* b, int nsteps, void* stream);
+/* Autotuner of the batch: for each mixed-storage lattice, times every
+ * column shape on that lattice alone (`reps` launches after one untimed
+ * launch, CUDA events on `stream`) and keeps the fastest; then, per storage
+ * mode, times the batched launch with 1 .. (resident blocks) blocks per SM
+ * and keeps the fastest grid (until lb_batch_set_grid); returns in
+ * *ms_per_step (may be NULL) the time of one batched step.  The timed
+ * launches read the current buffers and write the others without advancing
+ * the parity, so the state is left unchanged as long as no spread force is
+ * pending (g zero: true after lb_init_shear and between coupled steps; the
+ * step that consumes g clears it).  Synchronises. */
+int lb_batch_autotune(lb_batch* b, int reps, void* stream, float* ms_per_step);
+/* Grid of the batched launches: blocks_per_sm blocks per SM (0, the
+ * default: every block that fits, so the grid is persistent over the tile
+ * list; fewer leave SM slots to kernels on other streams).  No effect on
+ * results. */
+int lb_batch_set_grid(lb_batch* b, int blocks_per_sm);
+/* Column shape per lattice (0: 32x8, 1: 64x4, 2: 16x16; -1 for FP32):
+ * shapes[n] read or set (set ignores the FP32 entries; an entry outside
+ * 0..2 for a mixed lattice is PFSI_ERR_ARG and changes nothing).  The
+ * shapes do not change any cell's arithmetic. */
+int lb_batch_get_shapes(const lb_batch* b, int* shapes);
+int lb_batch_set_shapes(lb_batch* b, const int* shapes);
+
 typedef struct batch_ctx batch_ctx;
 
 /* A batch of n chambers, each a sim_ctx of its own (own lattice, mesh,
  * bonds, parameters; all at the same lattice-buffer parity).  batch_step
- * replays one CUDA graph that holds steps_per_graph steps of every chamber,
- * each chamber's kernels on a parallel branch, so one launch advances all
- * chambers and their kernels run concurrently.  Each chamber's results are
- * those of sim_step on it alone.  The sims stay owned by the caller and must
- * outlive the batch; do not step them on their own while the batch is in
- * use. */
+ * replays one CUDA graph that holds steps_per_graph steps of every chamber.
+ * The chambers are dealt into groups of about equal cell counts (largest
+ * lattice first, each to the group with the fewest cells so far; one group
+ * unless batch_set_layout says otherwise), each group an independent chain
+ * of the graph.  Per step of a group whose chambers have no learned
+ * surrogate, finite-element bending, bridges or tethers, EVERY kernel of the
+ * step is one launch for all the group's chambers: membrane passes, bond
+ * forces, spreading, the lattice step (one batched launch per storage mode,
+ * as lb_batch_step), interpolation, bond rupture, proposal and resolution.
+ * A group with such a chamber runs each chamber's kernels before and after
+ * the lattice step on parallel branches (greatest stream priority; the
+ * lattice launches take the least, so the branches' kernels get freed SM
+ * slots first).  Each
+ * chamber's results are those of sim_step on it alone (spreading sums up to
+ * the order of its FP32 atomics).  The sims stay owned by the caller and
+ * must outlive the batch; stepping one on its own makes the next batch_step
+ * fail (PFSI_ERR_ARG: the lattice-buffer parities differ). */
 int batch_create(sim_ctx** sims, int n, int steps_per_graph, batch_ctx** out);
 int batch_destroy(batch_ctx* ctx);
 /* nsteps (a multiple of steps_per_graph) steps of every chamber. */
 int batch_step(batch_ctx* ctx, int nsteps, void* stream);
+/* Layout of the step graph (no effect on results): `groups` chamber groups
+ * (>= 1, capped at n) and the lattice launches' grid, blocks_per_sm blocks
+ * per SM (0: every block that fits, a persistent grid over the tile list).
+ * Resets the column shapes to their defaults (batch_autotune picks them);
+ * the graphs are captured again at the next batch_step. */
+int batch_set_layout(batch_ctx* ctx, int groups, int blocks_per_sm);
+/* lb_batch_autotune on each group's lattices (between steps: the state is
+ * unchanged); *lb_ms_per_step = the sum of the groups' batched lattice step
+ * times.  The graphs are captured again at the next batch_step.
+ * Synchronises. */
+int batch_autotune(batch_ctx* ctx, int reps, void* stream, float* lb_ms_per_step);
 
 #ifdef __cplusplus
 }

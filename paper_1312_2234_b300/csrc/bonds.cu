@@ -41,10 +41,10 @@ __device__ __forceinline__ void bond_vector(const bond_params& p, const SitePos&
     d[2] = __dsub_rn(r.z, p.z_wall);
 }
 
-__global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __restrict__ F, int M)
+__device__ __forceinline__ void bond_forces(const BondCtx& c, const double* __restrict__ X, float* __restrict__ F,
+                                            int M, int bx)
 {
-    pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = bx * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int lig = c.bound[s];
     if (lig < 0) return;
@@ -57,11 +57,17 @@ __global__ void k_bond_forces(BondCtx c, const double* __restrict__ X, float* __
     site_add_force(c.site_tri, c.site_w, c.tri, F, M, s, f);
 }
 
-__global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
-                               const unsigned long long* __restrict__ step_dev)
+__global__ void k_bond_forces(const __grid_constant__ BondCtx c, const double* __restrict__ X, float* __restrict__ F,
+                              int M)
 {
     pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    bond_forces(c, X, F, M, blockIdx.x);
+}
+
+__device__ __forceinline__ void bond_rupture(const BondCtx& c, const double* __restrict__ X, int M, uint64_t step_host,
+                                             const unsigned long long* __restrict__ step_dev, int bx)
+{
+    const int s = bx * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     const int lig = c.bound[s];
     if (lig < 0) return;
@@ -77,6 +83,13 @@ __global__ void k_bond_rupture(BondCtx c, const double* __restrict__ X, int M, u
         atomicSub(&c.lig_count[lig], 1);
         atomicAdd(&c.counters[0], 1ull);
     }
+}
+
+__global__ void k_bond_rupture(const __grid_constant__ BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
+                               const unsigned long long* __restrict__ step_dev)
+{
+    pdl_wait();
+    bond_rupture(c, X, M, step_host, step_dev, blockIdx.x);
 }
 
 // Candidate (di, dj) of the window around node (i0, j0): the ligand there,
@@ -109,11 +122,10 @@ __device__ __forceinline__ void propose_candidate(const BondCtx& c, const SitePo
 // kR: the window half-width r at compile time (1: d_capture <= 1, the
 // configurations' 0.64), or 0 to take it from the context at run time.
 template <int kR>
-__global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
-                               const unsigned long long* __restrict__ step_dev)
+__device__ __forceinline__ void bond_propose(const BondCtx& c, const double* __restrict__ X, int M, uint64_t step_host,
+                                             const unsigned long long* __restrict__ step_dev, int blk)
 {
-    pdl_wait();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blk * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
     // the site's state, triangle and weights are loaded together (the height
     // test below needs all but the state)
@@ -162,10 +174,17 @@ __global__ void k_bond_propose(BondCtx c, const double* __restrict__ X, int M, u
     }
 }
 
-__global__ void k_bond_resolve(BondCtx c, unsigned long long* __restrict__ step_dev)
+template <int kR>
+__global__ void k_bond_propose(const __grid_constant__ BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
+                               const unsigned long long* __restrict__ step_dev)
 {
     pdl_wait();
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    bond_propose<kR>(c, X, M, step_host, step_dev, blockIdx.x);
+}
+
+__device__ __forceinline__ void bond_resolve(const BondCtx& c, unsigned long long* __restrict__ step_dev, int bx)
+{
+    const int l = bx * blockDim.x + threadIdx.x;
     if (step_dev && l == 0) *step_dev += 1ull;
     if (l >= c.L) return;
     const int n = c.nprop[l];
@@ -192,6 +211,53 @@ __global__ void k_bond_resolve(BondCtx c, unsigned long long* __restrict__ step_
     c.lig_count[l] = cnt;
     c.nprop[l] = 0;
     if (acc) atomicAdd(&c.counters[1], (unsigned long long)acc);
+}
+
+__global__ void k_bond_resolve(const __grid_constant__ BondCtx c, unsigned long long* __restrict__ step_dev)
+{
+    pdl_wait();
+    bond_resolve(c, step_dev, blockIdx.x);
+}
+
+// The bond kernels over several chambers, one launch each (see Multi).
+struct BondArgs {
+    BondCtx c;
+    const double* X;
+    float* F;
+    int M;
+    unsigned long long* step_dev;
+};
+
+__global__ void k_bond_forces_multi(const __grid_constant__ Multi<BondArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const BondArgs& a = t.a[e];
+    bond_forces(a.c, a.X, a.F, a.M, blockIdx.x - t.first[e]);
+}
+
+__global__ void k_bond_rupture_multi(const __grid_constant__ Multi<BondArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const BondArgs& a = t.a[e];
+    bond_rupture(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e]);
+}
+
+template <int kR>
+__global__ void k_bond_propose_multi(const __grid_constant__ Multi<BondArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const BondArgs& a = t.a[e];
+    bond_propose<kR>(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e]);
+}
+
+__global__ void k_bond_resolve_multi(const __grid_constant__ Multi<BondArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    bond_resolve(t.a[e].c, t.a[e].step_dev, blockIdx.x - t.first[e]);
 }
 
 // Tether tracking (Section 4.2): one block per platelet counts its bound
@@ -254,6 +320,46 @@ int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
     }
     return check_cuda(launch_pdl(k_bond_resolve, dim3(blocks_for(c->L > 0 ? c->L : 1, 256)), dim3(256), 0, s, *c, step_dev),
                       "bonds_step: resolve");
+}
+
+int launch_bonds_forces_multi(const Chamber* ch, int n, cudaStream_t s)
+{
+    std::vector<Multi<BondArgs>> lists;
+    for (int i = 0; i < n; ++i)
+        if (ch[i].bonds)
+            multi_push(lists, BondArgs{*ch[i].bonds, ch[i].X, ch[i].F, ch[i].M, nullptr}, blocks_for(ch[i].bonds->R, 256));
+    int rc = PFSI_OK;
+    for (const auto& t : lists)
+        if (!rc) rc = check_cuda(launch_pdl(k_bond_forces_multi, dim3(t.blocks()), dim3(256), 0, s, t), "bonds_forces");
+    return rc;
+}
+
+// Rupture, proposal and resolution of every chamber's bonds; each chamber's
+// Philox step index is its device counter (counters[3]), advanced by its
+// resolution pass.
+int launch_bonds_step_multi(const Chamber* ch, int n, cudaStream_t s)
+{
+    std::vector<Multi<BondArgs>> sites, prop1, prop0, ligs;
+    for (int i = 0; i < n; ++i) {
+        BondCtx* c = ch[i].bonds;
+        if (!c) continue;
+        const BondArgs a{*c, ch[i].X, nullptr, ch[i].M, c->counters + 3};
+        multi_push(sites, a, blocks_for(c->R, 256));
+        multi_push(c->window == 1 ? prop1 : prop0, a, blocks_for(c->R, 256));
+        multi_push(ligs, a, blocks_for(c->L > 0 ? c->L : 1, 256));
+    }
+    int rc = PFSI_OK;
+    for (const auto& t : sites)
+        if (!rc) rc = check_cuda(launch_pdl(k_bond_rupture_multi, dim3(t.blocks()), dim3(256), 0, s, t), "bonds_step: rupture");
+    for (const auto& t : prop1)
+        if (!rc)
+            rc = check_cuda(launch_pdl(k_bond_propose_multi<1>, dim3(t.blocks()), dim3(256), 0, s, t), "bonds_step: propose");
+    for (const auto& t : prop0)
+        if (!rc)
+            rc = check_cuda(launch_pdl(k_bond_propose_multi<0>, dim3(t.blocks()), dim3(256), 0, s, t), "bonds_step: propose");
+    for (const auto& t : ligs)
+        if (!rc) rc = check_cuda(launch_pdl(k_bond_resolve_multi, dim3(t.blocks()), dim3(256), 0, s, t), "bonds_step: resolve");
+    return rc;
 }
 
 int launch_tether_update(const TetherCtx* c, const unsigned long long* now_dev, uint64_t now_host, cudaStream_t s)

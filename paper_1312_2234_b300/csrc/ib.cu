@@ -134,10 +134,10 @@ __device__ Box block_box(const Node& s, bool on, int nx, int ny, int nz)
     return box;
 }
 
-__device__ __forceinline__ int2 block_chunk(const int2* __restrict__ chunks, int M)
+__device__ __forceinline__ int2 block_chunk(const int2* __restrict__ chunks, int M, int bx)
 {
-    if (chunks) return chunks[blockIdx.x];
-    const int m0 = blockIdx.x * kChunk;
+    if (chunks) return chunks[bx];
+    const int m0 = bx * kChunk;
     return make_int2(m0, min(kChunk, M - m0));
 }
 
@@ -153,18 +153,16 @@ __device__ __forceinline__ void row_table(const Box& b, int nx, int ny, int* row
     }
 }
 
-__global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
-                                                      int M, const int2* __restrict__ chunks,
-                                                      const int* __restrict__ perm,
-                                                      float4* __restrict__ g, uint32_t* __restrict__ flags,
-                                                      int nx, int ny, int nz)
+__device__ __forceinline__ void ib_spread_block(const double* __restrict__ X, const float* __restrict__ F, int M,
+                                                const int2* __restrict__ chunks, const int* __restrict__ perm,
+                                                float4* __restrict__ g, uint32_t* __restrict__ flags, int nx, int ny,
+                                                int nz, int bx)
 {
-    pdl_wait();
     extern __shared__ int itile[];
     __shared__ float swy[4][kChunk], swz[4][kChunk];
     __shared__ float wmax[kWarps];
     __shared__ int rowbase[kMaxRows];
-    const int2 ch = block_chunk(chunks, M);
+    const int2 ch = block_chunk(chunks, M, bx);
     const bool in_chunk = (int)threadIdx.x < ch.y;
     const int m = in_chunk && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
@@ -263,23 +261,29 @@ __global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__
     }
 }
 
-// kPart: also write the block's sum of the advected X (next.part)
-template <bool kPart>
-__global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
-                                                      const int2* __restrict__ chunks,
-                                                      const int* __restrict__ perm,
-                                                      const float4* __restrict__ v,
-                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz,
-                                                      int advect, NextSplit next)
+__global__ void __launch_bounds__(kChunk) k_ib_spread(const double* __restrict__ X, const float* __restrict__ F,
+                                                      int M, const int2* __restrict__ chunks,
+                                                      const int* __restrict__ perm, float4* __restrict__ g,
+                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz)
 {
     pdl_wait();
+    ib_spread_block(X, F, M, chunks, perm, g, flags, nx, ny, nz, blockIdx.x);
+}
+
+// kPart: also write the block's sum of the advected X (next.part)
+template <bool kPart>
+__device__ __forceinline__ void ib_interp_block(double* __restrict__ X, float* __restrict__ U, int M,
+                                                const int2* __restrict__ chunks, const int* __restrict__ perm,
+                                                const float4* __restrict__ v, uint32_t* __restrict__ flags, int nx,
+                                                int ny, int nz, int advect, const NextSplit& next, int bx)
+{
     if (next.acc) {   // the next membrane pass accumulates into cleared sums
-        const int t = blockIdx.x * blockDim.x + threadIdx.x;
+        const int t = bx * blockDim.x + threadIdx.x;
         if (t < next.nacc) next.acc[t] = 0.0;
     }
     extern __shared__ float4 tile4[];
     __shared__ int rowbase[kMaxRows];
-    const int2 ch = block_chunk(chunks, M);
+    const int2 ch = block_chunk(chunks, M, bx);
     const bool in_chunk = (int)threadIdx.x < ch.y;
     const int m = in_chunk && perm ? perm[ch.x + threadIdx.x] : ch.x + threadIdx.x;
     Node s;
@@ -423,9 +427,63 @@ __global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, fl
         if (threadIdx.x < 3) {
             double t = 0.0;
             for (int w = 0; w < kWarps; ++w) t += wsum[w][threadIdx.x];
-            next.part[3 * blockIdx.x + threadIdx.x] = t;
+            next.part[3 * bx + threadIdx.x] = t;
         }
     }
+}
+
+template <bool kPart>
+__global__ void __launch_bounds__(kChunk) k_ib_interp(double* __restrict__ X, float* __restrict__ U, int M,
+                                                      const int2* __restrict__ chunks,
+                                                      const int* __restrict__ perm,
+                                                      const float4* __restrict__ v,
+                                                      uint32_t* __restrict__ flags, int nx, int ny, int nz,
+                                                      int advect, const __grid_constant__ NextSplit next)
+{
+    pdl_wait();
+    ib_interp_block<kPart>(X, U, M, chunks, perm, v, flags, nx, ny, nz, advect, next, blockIdx.x);
+}
+
+// Spreading and interpolation over several chambers, one launch each (see
+// Multi): each chamber's share of the grid takes its nodes' chunks on its
+// own lattice.
+struct SpreadArgs {
+    const double* X;
+    const float* F;
+    int M;
+    const int2* chunks;
+    const int* perm;
+    float4* g;
+    uint32_t* flags;
+    int nx, ny, nz;
+};
+struct InterpArgs {
+    double* X;
+    float* U;
+    int M;
+    const int2* chunks;
+    const int* perm;
+    const float4* v;
+    uint32_t* flags;
+    int nx, ny, nz;
+};
+
+__global__ void __launch_bounds__(kChunk) k_ib_spread_multi(const __grid_constant__ Multi<SpreadArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const SpreadArgs& a = t.a[e];
+    ib_spread_block(a.X, a.F, a.M, a.chunks, a.perm, a.g, a.flags, a.nx, a.ny, a.nz, blockIdx.x - t.first[e]);
+}
+
+__global__ void __launch_bounds__(kChunk) k_ib_interp_multi(const __grid_constant__ Multi<InterpArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const InterpArgs& a = t.a[e];
+    const NextSplit none;
+    ib_interp_block<false>(a.X, a.U, a.M, a.chunks, a.perm, a.v, a.flags, a.nx, a.ny, a.nz, 1, none,
+                           blockIdx.x - t.first[e]);
 }
 
 }  // namespace
@@ -440,6 +498,14 @@ int ib_prepare()
                         "ib: shared memory size");
     if (!rc)
         rc = check_cuda(cudaFuncSetAttribute(k_ib_interp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTileBytes),
+                        "ib: shared memory size");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_ib_spread_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kTileBytes),
+                        "ib: shared memory size");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_ib_interp_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kTileBytes),
                         "ib: shared memory size");
     return rc;
@@ -468,6 +534,41 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
                                  s, X, U, M, chunks, perm, (const float4*)velocity_field(c), c->flags, c->p.nx, c->p.ny,
                                  c->p.nz, advect, next),
                       "ib_interp");
+}
+
+int launch_ib_spread_multi(const Chamber* ch, int n, cudaStream_t s)
+{
+    std::vector<Multi<SpreadArgs>> lists;
+    for (int i = 0; i < n; ++i) {
+        const LbCtx* c = ch[i].lb;
+        const MemCtx* m = ch[i].mem;
+        multi_push(lists, SpreadArgs{ch[i].X, ch[i].F, ch[i].M, m->chunks, m->perm, c->g, c->flags, c->p.nx, c->p.ny,
+                                     c->p.nz},
+                   ch[i].M > 0 ? m->n_chunks : 0);
+    }
+    int rc = PFSI_OK;
+    for (const auto& t : lists)
+        if (!rc)
+            rc = check_cuda(launch_pdl(k_ib_spread_multi, dim3(t.blocks()), dim3(kChunk), 3 * kTileCells * sizeof(int), s, t),
+                            "ib_spread");
+    return rc;
+}
+
+int launch_ib_interp_multi(const Chamber* ch, int n, cudaStream_t s)
+{
+    std::vector<Multi<InterpArgs>> lists;
+    for (int i = 0; i < n; ++i) {
+        const LbCtx* c = ch[i].lb;
+        const MemCtx* m = ch[i].mem;
+        multi_push(lists, InterpArgs{ch[i].X, ch[i].U, ch[i].M, m->chunks, m->perm, velocity_field(c), c->flags,
+                                     c->p.nx, c->p.ny, c->p.nz},
+                   ch[i].M > 0 ? m->n_chunks : 0);
+    }
+    int rc = PFSI_OK;
+    for (const auto& t : lists)
+        if (!rc)
+            rc = check_cuda(launch_pdl(k_ib_interp_multi, dim3(t.blocks()), dim3(kChunk), kTileBytes, s, t), "ib_interp");
+    return rc;
 }
 
 }  // namespace pfsi

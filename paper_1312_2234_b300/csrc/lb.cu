@@ -28,6 +28,7 @@
 #include <climits>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -41,15 +42,13 @@ namespace {
 constexpr int kRowBlock = 128;     // default threads per block along x (FP32 kernel)
 constexpr int kMaxRowBlock = 256;
 
-__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
-    const float* __restrict__ fin, float* __restrict__ fout, float4* __restrict__ g,
-    float4* __restrict__ vout, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
-    float omega, float guo, float3 body, float3 utop, int onsite)
+// Stream-collide of cell (i, j, k) with FP32 shifted populations: the body
+// of k_lb_step and of the batched k_lb_step_batch.
+__device__ __forceinline__ void fp32_cell(const float* __restrict__ fin, float* __restrict__ fout,
+                                          float4* __restrict__ g, float4* __restrict__ vout,
+                                          const uint32_t* __restrict__ flags, int nx, int ny, int nz, int i, int j,
+                                          int k, float omega, float guo, float3 body, float3 utop, int onsite)
 {
-    pdl_wait();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y, k = blockIdx.z;
-    if (i >= nx) return;
     const int N = nx * ny * nz;
     const int row = k * ny + j;
     const int cell = row * nx + i;
@@ -99,8 +98,8 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
     const float vx = (mx + 0.5f * Fx) * irho;
     const float vy = (my + 0.5f * Fy) * irho;
     const float vz = (mz + 0.5f * Fz) * irho;
-    const float vv = vx * vx + vy * vy + vz * vz;
-    const float vF = vx * Fx + vy * Fy + vz * Fz;
+    const float vv = fmaf(vx, vx, fmaf(vy, vy, vz * vz));
+    const float vF = fmaf(vx, Fx, fmaf(vy, Fy, vz * Fz));
 
     // f~' = (1 - omega) f~ + omega (f^eq - w) + S with the equilibrium of
     // Eq. 20 and Guo's source w (1 - 1/2tau) [3 c.F + 9 (c.v)(c.F) - 3 v.F]
@@ -123,7 +122,7 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
         if (czq(q)) { cv += czq(q) * vz; cF += czq(q) * Fz; }
         const float a = (wq(q) * R3) * cv;
         const float b = (wq(q) * G3) * cF;
-        const float odd = a + b;
+        const float odd = fmaf(wq(q) * R3, cv, b);
         const float even = fmaf(1.5f * cv, fmaf(2.0f, b, a), wq(q) * A0);
         fout[q * N + cell] = fmaf(keep, f[q], even + odd);
         fout[o * N + cell] = fmaf(keep, f[o], even - odd);
@@ -132,6 +131,17 @@ __global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
         vout[cell] = make_float4(vx, vy, vz, rho);
         g[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+}
+
+__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(
+    const float* __restrict__ fin, float* __restrict__ fout, float4* __restrict__ g,
+    float4* __restrict__ vout, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
+    float omega, float guo, float3 body, float3 utop, int onsite)
+{
+    pdl_wait();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    fp32_cell(fin, fout, g, vout, flags, nx, ny, nz, i, blockIdx.y, blockIdx.z, omega, guo, body, utop, onsite);
 }
 
 // 16-bit encodings of f*neq: BF16 as is, FP16 scaled by 2^s (get takes
@@ -197,13 +207,6 @@ __device__ __forceinline__ void halo_store(Ring<T>& ring, int slot, const float4
     }
 }
 
-// E_q of a ring cell, for direction q.
-template <int q, class T>
-__device__ __forceinline__ float feq_ring(const Ring<T>& ring, int slot, int h)
-{
-    return wq(q) * split_eq<q>(ring.pj[slot][h]);
-}
-
 // f[q] += E_q of the source cell (bounce-back: the own cell's opposite
 // population, plus the moving-wall term at the top).  sm, s0, sp: ring slots
 // of the planes k - 1, k, k + 1.
@@ -212,12 +215,13 @@ __device__ __forceinline__ void add_feq(float* f, const Ring<T>& ring, int sm, i
                                         int nz, float3 utop)
 {
     if (czq(q) == 1 && k == 0) {
-        f[q] += feq_ring<oppq(q)>(ring, s0, own);
+        f[q] = fmaf(wq(q), split_eq<oppq(q)>(ring.pj[s0][own]), f[q]);
     } else if (czq(q) == -1 && k == nz - 1) {
         const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
-        f[q] += feq_ring<oppq(q)>(ring, s0, own) + 6.0f * wq(q) * cu;
+        f[q] = fmaf(wq(q), split_eq<oppq(q)>(ring.pj[s0][own]), fmaf(6.0f * wq(q), cu, f[q]));
     } else {
-        f[q] += feq_ring<q>(ring, czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0), own - cyq(q) * T::HX - cxq(q));
+        f[q] = fmaf(wq(q), split_eq<q>(ring.pj[czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0)][own - cyq(q) * T::HX - cxq(q)]),
+                    f[q]);
     }
 }
 
@@ -253,7 +257,7 @@ __device__ __forceinline__ float neq_value(uint32_t raw, float inv_scale)
 }
 
 // Stored values of the pair (q, opposite of q) of one cell: the part even
-// in c is w E0 + cv (h + b), the odd part a + b (see k_lb_step_mixed).
+// in c is w E0 + cv (h + b), the odd part a + b (see mixed_column).
 template <int kMode, int q>
 __device__ __forceinline__ void store_pair(typename Neq<kMode>::T* __restrict__ nout, int N, int cell, const float* f,
                                            float vx, float vy, float vz, float3 F3, float rk, float rh, float keep,
@@ -262,9 +266,8 @@ __device__ __forceinline__ void store_pair(typename Neq<kMode>::T* __restrict__ 
     if (q == 18 || oppq(q) < q) return;
     const float cv = cdot<q>(vx, vy, vz), cF = cdot<q>(F3.x, F3.y, F3.z);
     const float wcv = wq(q) * cv;
-    const float a = rk * wcv;
     const float b = (wq(q) * guo) * cF;
-    const float odd = a + b;
+    const float odd = fmaf(rk, wcv, b);
     const float even = fmaf(cv, fmaf(rh, wcv, b), wq(q) * E0);
     nout[nslot(q) * N + cell] = Neq<kMode>::put(fmaf(keep, f[q], even + odd), scale);
     nout[nslot(oppq(q)) * N + cell] = Neq<kMode>::put(fmaf(keep, f[oppq(q)], even - odd), scale);
@@ -278,17 +281,18 @@ __device__ __forceinline__ void store_pairs(std::integer_sequence<int, Q...>, ty
     (store_pair<kMode, Q>(nout, N, cell, f, vx, vy, vz, F3, rk, rh, keep, E0, guo, scale), ...);
 }
 
+// One column of the mixed step: the (x, y) tile at (x0, y0) marched through
+// the planes z0 <= k < z1 (the body of k_lb_step_mixed and of the batched
+// k_lb_step_batch_mixed).  The ring is free again when it returns.
 template <int kMode, class T>
-__global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
-    const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
-    float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
-    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
+__device__ __forceinline__ void mixed_column(Ring<T>& ring, const uint16_t* __restrict__ nin,
+                                             typename Neq<kMode>::T* __restrict__ nout,
+                                             const float4* __restrict__ min_, float4* __restrict__ mout,
+                                             float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx,
+                                             int ny, int nz, int x0, int y0, int z0, int z1, float omega, float guo,
+                                             float3 body, float3 utop, float inv_scale, int onsite)
 {
-    pdl_wait();
-    __shared__ Ring<T> ring;
     const int tx = threadIdx.x % T::TX, ty = threadIdx.x / T::TX;
-    const int x0 = blockIdx.x * T::TX, y0 = blockIdx.y * T::TY;
-    const int z0 = blockIdx.z * kz, z1 = min(z0 + kz, nz);
     const int i = x0 + tx, j = y0 + ty;
     const bool live = i < nx && j < ny;
     const int N = nx * ny * nz;
@@ -360,9 +364,9 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
             const float vx = fmaf(F3.x, 1.0f / 6.0f, mx) * i3rho;
             const float vy = fmaf(F3.y, 1.0f / 6.0f, my) * i3rho;
             const float vz = fmaf(F3.z, 1.0f / 6.0f, mz) * i3rho;
-            const float VV = vx * vx + vy * vy + vz * vz;                           // 9 v.v
-            const float P0 = fmaf(-rho / 6.0f, VV, drho);                            // drho - 1.5 rho v.v
-            const float vF3 = (vx * F3.x + vy * F3.y + vz * F3.z) * (1.0f / 3.0f);  // 3 v.F
+            const float VV = fmaf(vx, vx, fmaf(vy, vy, vz * vz));                   // 9 v.v
+            const float P0 = fmaf(rho * (-1.0f / 6.0f), VV, drho);                   // drho - 1.5 rho v.v
+            const float vF3 = fmaf(vx, F3.x, fmaf(vy, F3.y, vz * F3.z)) * (1.0f / 3.0f);  // 3 v.F
             // stored f* - E = (1 - omega)(f - f^eq) + S + (f^eq - E), with
             // (f^eq - w)/w = P0 + rho (cv + cv^2/2), S/(w guo) = cF (1 + cv) - vF3
             // and (f^eq - E)/w = rho (1 - rho) cv^2 / 2 (cv = 3 c.v, cF = 3 c.F),
@@ -381,6 +385,19 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
         if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
         __syncthreads();
     }
+}
+
+template <int kMode, class T>
+__global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
+    const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
+    float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
+    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
+{
+    pdl_wait();
+    __shared__ Ring<T> ring;
+    const int z0 = blockIdx.z * kz;
+    mixed_column<kMode, T>(ring, nin, nout, min_, mout, g, flags, nx, ny, nz, blockIdx.x * T::TX, blockIdx.y * T::TY,
+                           z0, min(z0 + kz, nz), omega, guo, body, utop, inv_scale, onsite);
 }
 
 template <int kMode, int q>
@@ -574,6 +591,110 @@ cudaError_t launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched step: one launch per storage kind steps every chamber of a batch.
+// The chambers' cells are cut into tiles listed chamber after chamber; a
+// persistent grid (as many blocks as fit on the GPU at once) walks the list,
+// block b taking tiles b, b + grid, b + 2 grid, ...  Each tile is computed by
+// the same per-cell code as the single-chamber kernels, so a chamber stepped
+// in a batch gets bit-identical populations.  The list travels as a kernel
+// parameter (__grid_constant__): its block-uniform fields are read from the
+// constant bank as the single-chamber kernels read theirs, instead of
+// occupying registers.
+
+// Tile list entry of one chamber: its buffers for one lattice-buffer parity,
+// its parameters and its place in the list.
+struct LbChamber {
+    const void* fin;       // populations read (FP32 shifted f, or 16-bit f*neq)
+    void* fout;            // populations written
+    const float4* min;     // mixed: moment records read
+    float4* mout;          // mixed: moment records written; FP32: (v, rho) of the forced rows
+    float4* g;
+    const uint32_t* flags;
+    float3 body, utop;
+    float omega, guo, inv_scale;
+    int nx, ny, nz, onsite;
+    int tile0;             // first tile of the chamber in the list
+    int shape;             // mixed: column tile (kBatchTX x kBatchTY)
+    int tiles_x, tiles_y;  // mixed: columns along x and along y
+    int kz;                // mixed: planes per column
+};
+
+// Chambers per launch: a kind with more chambers takes several launches.
+constexpr int kTableMax = 128;
+
+struct LbTable {
+    int n, ntiles;
+    LbChamber ch[kTableMax];
+};
+static_assert(sizeof(LbTable) <= 32000, "the tile list must fit the kernel parameter space");
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchFp32Tile = kBatchThreads;      // FP32: consecutive cells (flat order) per tile
+constexpr int kBatchShapes = 3;                     // mixed column tiles, 256 threads each
+constexpr int kBatchTX[kBatchShapes] = {32, 64, 16};
+constexpr int kBatchTY[kBatchShapes] = {8, 4, 16};
+constexpr int kBatchKz = 16;                        // mixed: planes per column
+constexpr int kBatchPlane = 66 * 6;                 // largest ring plane of the three shapes (64 x 4)
+static_assert(Tile<32, 8>::Plane <= kBatchPlane && Tile<64, 4>::Plane <= kBatchPlane &&
+                  Tile<16, 16>::Plane <= kBatchPlane,
+              "ring storage must hold every shape's plane");
+
+// Chamber of tile t: the list is sorted by tile0 and a block's tiles only
+// grow, so the search moves forward from the previous tile's chamber.
+__device__ __forceinline__ int chamber_of(const LbTable& tab, int t, int c)
+{
+    while (c + 1 < tab.n && tab.ch[c + 1].tile0 <= t) ++c;
+    return c;
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_lb_step_batch(const __grid_constant__ LbTable tab)
+{
+    int c = 0;
+    for (int t = blockIdx.x; t < tab.ntiles; t += gridDim.x) {
+        c = chamber_of(tab, t, c);
+        const LbChamber& ch = tab.ch[c];
+        const int nx = ch.nx, plane = nx * ch.ny;
+        const int cell = (t - ch.tile0) * kBatchFp32Tile + (int)threadIdx.x;
+        if (cell >= plane * ch.nz) continue;
+        const int k = cell / plane, r = cell - k * plane;
+        const int j = r / nx, i = r - j * nx;
+        fp32_cell((const float*)ch.fin, (float*)ch.fout, ch.g, ch.mout, ch.flags, nx, ch.ny, ch.nz, i, j, k,
+                  ch.omega, ch.guo, ch.body, ch.utop, ch.onsite);
+    }
+}
+
+template <int kMode, int S>
+__device__ __forceinline__ void batch_column(float4* ring_mem, const LbChamber& ch, int tx, int ty, int z0)
+{
+    using T = Tile<kBatchTX[S], kBatchTY[S]>;
+    mixed_column<kMode, T>(*reinterpret_cast<Ring<T>*>(ring_mem), (const uint16_t*)ch.fin,
+                           (typename Neq<kMode>::T*)ch.fout, ch.min, ch.mout, ch.g, ch.flags, ch.nx, ch.ny, ch.nz,
+                           tx * T::TX, ty * T::TY, z0, min(z0 + ch.kz, ch.nz), ch.omega, ch.guo, ch.body, ch.utop,
+                           ch.inv_scale, ch.onsite);
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kBatchThreads, 768 / kBatchThreads) k_lb_step_batch_mixed(
+    const __grid_constant__ LbTable tab)
+{
+    __shared__ float4 ring_mem[kSlots * kBatchPlane];
+    int c = 0;
+    for (int t = blockIdx.x; t < tab.ntiles; t += gridDim.x) {
+        c = chamber_of(tab, t, c);
+        const LbChamber& ch = tab.ch[c];
+        // tiles of a chamber: x fastest, then y, then the column's plane range
+        const int u = t - ch.tile0, per_range = ch.tiles_x * ch.tiles_y;
+        const int tz = u / per_range, r = u - tz * per_range;
+        const int ty = r / ch.tiles_x, tx = r - ty * ch.tiles_x;
+        switch (ch.shape) {   // uniform over the block
+        case 1: batch_column<kMode, 1>(ring_mem, ch, tx, ty, tz * ch.kz); break;
+        case 2: batch_column<kMode, 2>(ring_mem, ch, tx, ty, tz * ch.kz); break;
+        default: batch_column<kMode, 0>(ring_mem, ch, tx, ty, tz * ch.kz);
+        }
+    }
+}
+
 }  // namespace
 
 int launch_lb_step(LbCtx* c, cudaStream_t s)
@@ -609,6 +730,317 @@ int launch_lb_step(LbCtx* c, cudaStream_t s)
     }
     c->cur ^= 1;
     return check_launch("lb_step");
+}
+
+// Host side of a batch: per storage kind, the tile lists of its chambers for
+// each lattice-buffer parity (one list per launch of up to kTableMax
+// chambers).
+struct LbBatch {
+    std::vector<LbCtx*> lat;
+    struct Kind {
+        std::vector<int> members;          // indices into lat, in list order
+        std::vector<int> shapes;           // mixed: column shape per member
+        std::vector<LbTable> tab[2];       // per parity of the buffers read
+        int sms = 0, per_sm = 0;           // SMs, resident blocks of the kernel per SM
+        int tuned = 0;                     // blocks per SM the autotuner picked (0: none)
+        int grid = 0;                      // blocks of the persistent grid
+    } kind[3];                             // PFSI_LB_FP32, PFSI_LB_BF16, PFSI_LB_FP16
+    int blocks_per_sm = 0;                 // grid: this many blocks per SM (0: every resident block)
+    int priority = 0;                      // launch priority (cudaLaunchAttributePriority)
+};
+
+namespace {
+
+// Columns of a mixed chamber for a batch shape, and the shape the batch
+// starts from before tuning: the fewest threads per chamber counting idle
+// ones in ragged columns and a quarter thread per ring cell.
+long long batch_cost(const lb_params& p, int shape)
+{
+    const long long tx = (p.nx + kBatchTX[shape] - 1) / kBatchTX[shape];
+    const long long ty = (p.ny + kBatchTY[shape] - 1) / kBatchTY[shape];
+    return tx * ty * (4 * kBatchThreads + (kBatchTX[shape] + 2) * (kBatchTY[shape] + 2));
+}
+
+int batch_default_shape(const lb_params& p)
+{
+    int best = 0;
+    for (int s = 1; s < kBatchShapes; ++s)
+        if (batch_cost(p, s) < batch_cost(p, best)) best = s;
+    return best;
+}
+
+LbChamber chamber_entry(const LbCtx* c, int parity, int shape)
+{
+    const lb_params& p = c->p;
+    LbChamber e = {};
+    e.fin = c->f[parity];
+    e.fout = c->f[parity ^ 1];
+    e.min = p.storage ? c->m[parity] : nullptr;
+    e.mout = p.storage ? c->m[parity ^ 1] : c->v;
+    e.g = c->g;
+    e.flags = c->flags;
+    e.body = make_float3(p.body[0], p.body[1], p.body[2]);
+    e.utop = make_float3(p.u_top[0], p.u_top[1], p.u_top[2]);
+    e.omega = 1.0f / p.tau;
+    e.guo = 1.0f - 0.5f / p.tau;
+    e.inv_scale = inv_scale_of(p);
+    e.nx = p.nx;
+    e.ny = p.ny;
+    e.nz = p.nz;
+    e.onsite = p.walls;
+    e.shape = shape;
+    if (p.storage) {
+        e.tiles_x = (p.nx + kBatchTX[shape] - 1) / kBatchTX[shape];
+        e.tiles_y = (p.ny + kBatchTY[shape] - 1) / kBatchTY[shape];
+        e.kz = std::min(kBatchKz, p.nz);
+    }
+    return e;
+}
+
+long long chamber_tiles(const LbChamber& e, int mode)
+{
+    if (mode == PFSI_LB_FP32) return ((long long)e.nx * e.ny * e.nz + kBatchFp32Tile - 1) / kBatchFp32Tile;
+    return (long long)e.tiles_x * e.tiles_y * ((e.nz + e.kz - 1) / e.kz);
+}
+
+// Rebuilds both parities' lists of one kind from the chambers' shapes.
+int batch_upload(LbBatch* b, int mode, const std::vector<int>& shapes)
+{
+    LbBatch::Kind& K = b->kind[mode];
+    K.shapes = shapes;
+    for (int par = 0; par < 2; ++par) {
+        K.tab[par].clear();
+        for (size_t u = 0; u < K.members.size(); ++u) {
+            if (u % kTableMax == 0) {
+                K.tab[par].emplace_back();
+                K.tab[par].back().n = 0;
+                K.tab[par].back().ntiles = 0;
+            }
+            LbTable& T = K.tab[par].back();
+            LbChamber e = chamber_entry(b->lat[K.members[u]], par, shapes[u]);
+            e.tile0 = T.ntiles;
+            const long long tiles = (long long)T.ntiles + chamber_tiles(e, mode);
+            if (tiles > INT_MAX) return set_error(PFSI_ERR_ARG, "lb_batch: too many tiles for one launch");
+            T.ch[T.n++] = e;
+            T.ntiles = (int)tiles;
+        }
+    }
+    return PFSI_OK;
+}
+
+template <typename K>
+int resident_blocks(K kernel, LbBatch::Kind& kind)
+{
+    int dev = 0;
+    int rc = check_cuda(cudaGetDevice(&dev), "lb_batch: device");
+    if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&kind.sms, cudaDevAttrMultiProcessorCount, dev), "lb_batch: SMs");
+    if (!rc)
+        rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&kind.per_sm, kernel, kBatchThreads, 0),
+                        "lb_batch: occupancy");
+    kind.per_sm = std::max(kind.per_sm, 1);
+    return rc;
+}
+
+void size_grids(LbBatch* b)
+{
+    for (auto& K : b->kind) {
+        const int want = K.tuned > 0 ? K.tuned : b->blocks_per_sm;
+        K.grid = K.sms * (want > 0 ? std::min(want, K.per_sm) : K.per_sm);
+    }
+}
+
+// One launch of kind `mode` over the list `tab` (no parity flip), at the
+// batch's launch priority.
+cudaError_t batch_launch_kind(const LbBatch* b, const LbBatch::Kind& K, int mode, const LbTable& tab,
+                              cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = b->priority;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::max(1, std::min(K.grid, tab.ntiles)));
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    switch (mode) {
+    case PFSI_LB_BF16: return cudaLaunchKernelEx(&cfg, k_lb_step_batch_mixed<PFSI_LB_BF16>, tab);
+    case PFSI_LB_FP16: return cudaLaunchKernelEx(&cfg, k_lb_step_batch_mixed<PFSI_LB_FP16>, tab);
+    default: return cudaLaunchKernelEx(&cfg, k_lb_step_batch, tab);
+    }
+}
+
+}  // namespace
+
+void lb_batch_free(LbBatch* b) { delete b; }
+
+int lb_batch_build(LbCtx* const* lat, int n, LbBatch** out)
+{
+    if (!lat || n < 1 || !out) return set_error(PFSI_ERR_ARG, "lb_batch: bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!lat[i]) return set_error(PFSI_ERR_ARG, "lb_batch: null lattice");
+        if (lat[i]->cur != lat[0]->cur)
+            return set_error(PFSI_ERR_ARG, "lb_batch: lattices must be at the same buffer parity");
+        for (int j = 0; j < i; ++j)
+            if (lat[j] == lat[i]) return set_error(PFSI_ERR_ARG, "lb_batch: a lattice appears twice");
+    }
+    LbBatch* b = new LbBatch();
+    b->lat.assign(lat, lat + n);
+    int rc = PFSI_OK;
+    for (int mode = 0; mode < 3 && !rc; ++mode) {
+        LbBatch::Kind& K = b->kind[mode];
+        std::vector<int> shapes;
+        for (int i = 0; i < n; ++i)
+            if (lat[i]->p.storage == mode) {
+                K.members.push_back(i);
+                shapes.push_back(mode ? batch_default_shape(lat[i]->p) : 0);
+            }
+        if (K.members.empty()) continue;
+        rc = batch_upload(b, mode, shapes);
+        if (!rc)
+            rc = mode == PFSI_LB_BF16   ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_BF16>, K)
+                 : mode == PFSI_LB_FP16 ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_FP16>, K)
+                                        : resident_blocks(k_lb_step_batch, K);
+    }
+    size_grids(b);
+    if (rc) {
+        lb_batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return PFSI_OK;
+}
+
+int launch_lb_batch(LbBatch* b, cudaStream_t s)
+{
+    const int parity = b->lat[0]->cur;
+    for (const LbCtx* c : b->lat)
+        if (c->cur != parity) return set_error(PFSI_ERR_ARG, "lb_batch: lattices are at different buffer parities");
+    for (int mode = 0; mode < 3; ++mode)
+        for (const LbTable& T : b->kind[mode].tab[parity]) {
+            const int rc = check_cuda(batch_launch_kind(b, b->kind[mode], mode, T, s), "lb_batch: launch");
+            if (rc) return rc;
+        }
+    for (LbCtx* c : b->lat) c->cur ^= 1;
+    return PFSI_OK;
+}
+
+// Per mixed chamber, times each column shape on that chamber alone and
+// keeps the fastest; then, per storage kind, times the batched launch with
+// 1 .. (resident blocks) blocks per SM and keeps the fastest grid.  The launches read
+// the current buffers and write the others without taking the parity
+// forward, so the state is unchanged provided no spread force is pending
+// (g is zero between coupled steps: the step that consumes it clears it).
+int lb_batch_tune(LbBatch* b, int reps, cudaStream_t s, float* ms_out)
+{
+    if (!b || reps < 1) return set_error(PFSI_ERR_ARG, "lb_batch_tune: bad argument");
+    const int parity = b->lat[0]->cur;
+    for (const LbCtx* c : b->lat)
+        if (c->cur != parity) return set_error(PFSI_ERR_ARG, "lb_batch: lattices are at different buffer parities");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = check_cuda(cudaEventCreate(&e0), "lb_batch_tune: event");
+    if (!rc) rc = check_cuda(cudaEventCreate(&e1), "lb_batch_tune: event");
+    // mean time of `reps` launches of the lists after one warm-up
+    auto time_launches = [&](const LbBatch::Kind& K, int mode, const std::vector<LbTable>& tabs, float* ms) {
+        int r = PFSI_OK;
+        for (const LbTable& T : tabs)
+            if (!r) r = check_cuda(batch_launch_kind(b, K, mode, T, s), "lb_batch_tune: launch");
+        if (!r) r = check_cuda(cudaEventRecord(e0, s), "lb_batch_tune: record");
+        for (int k = 0; k < reps && !r; ++k)
+            for (const LbTable& T : tabs)
+                if (!r) r = check_cuda(batch_launch_kind(b, K, mode, T, s), "lb_batch_tune: launch");
+        if (!r) r = check_cuda(cudaEventRecord(e1, s), "lb_batch_tune: record");
+        if (!r) r = check_cuda(cudaEventSynchronize(e1), "lb_batch_tune: synchronise");
+        if (!r) r = check_cuda(cudaEventElapsedTime(ms, e0, e1), "lb_batch_tune: elapsed");
+        *ms /= reps;
+        return r;
+    };
+    std::vector<LbTable> one(1);
+    for (int mode = 1; mode < 3 && !rc; ++mode) {
+        LbBatch::Kind& K = b->kind[mode];
+        std::vector<int> shapes;
+        for (size_t u = 0; u < K.members.size() && !rc; ++u) {
+            const LbCtx* c = b->lat[K.members[u]];
+            int best = 0;
+            float best_ms = 0.f;
+            for (int shape = 0; shape < kBatchShapes && !rc; ++shape) {
+                LbChamber e = chamber_entry(c, parity, shape);
+                e.tile0 = 0;
+                one[0].n = 1;
+                one[0].ntiles = (int)chamber_tiles(e, mode);
+                one[0].ch[0] = e;
+                float ms = 0.f;
+                rc = time_launches(K, mode, one, &ms);
+                if (!rc && (shape == 0 || ms < best_ms)) {
+                    best = shape;
+                    best_ms = ms;
+                }
+            }
+            shapes.push_back(best);
+        }
+        if (!rc && !K.members.empty()) rc = batch_upload(b, mode, shapes);
+    }
+    // then the grid of each kind: 1 .. resident blocks per SM
+    float total = 0.f;
+    for (int mode = 0; mode < 3 && !rc; ++mode) {
+        LbBatch::Kind& K = b->kind[mode];
+        if (K.members.empty()) continue;
+        int best = 0;
+        float best_ms = 0.f;
+        for (int per = K.per_sm; per >= 1 && !rc; --per) {
+            K.tuned = per;
+            size_grids(b);
+            float ms = 0.f;
+            rc = time_launches(K, mode, K.tab[parity], &ms);
+            if (!rc && (best == 0 || ms < best_ms)) {
+                best = per;
+                best_ms = ms;
+            }
+        }
+        K.tuned = best;
+        size_grids(b);
+        total += best_ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!rc && ms_out) *ms_out = total;
+    return rc;
+}
+
+int lb_batch_assign_shapes(LbBatch* b, const int* shapes)
+{
+    for (size_t i = 0; i < b->lat.size(); ++i)
+        if (b->lat[i]->p.storage && (shapes[i] < 0 || shapes[i] >= kBatchShapes))
+            return set_error(PFSI_ERR_ARG, "lb_batch_set_shapes: shape out of range");
+    for (int mode = 1; mode < 3; ++mode) {
+        const LbBatch::Kind& K = b->kind[mode];
+        if (K.members.empty()) continue;
+        std::vector<int> s;
+        for (int i : K.members) s.push_back(shapes[i]);
+        const int rc = batch_upload(b, mode, s);
+        if (rc) return rc;
+    }
+    return PFSI_OK;
+}
+
+int lb_batch_configure_grid(LbBatch* b, int blocks_per_sm, int priority)
+{
+    if (blocks_per_sm < 0) return set_error(PFSI_ERR_ARG, "lb_batch_set_grid: negative blocks per SM");
+    b->blocks_per_sm = blocks_per_sm;
+    b->priority = priority;
+    for (auto& K : b->kind) K.tuned = 0;
+    size_grids(b);
+    return PFSI_OK;
+}
+
+int lb_batch_shapes(const LbBatch* b, int* shapes)
+{
+    for (size_t i = 0; i < b->lat.size(); ++i) shapes[i] = -1;
+    for (int mode = 1; mode < 3; ++mode) {
+        const LbBatch::Kind& K = b->kind[mode];
+        for (size_t u = 0; u < K.members.size(); ++u) shapes[K.members[u]] = K.shapes[u];
+    }
+    return PFSI_OK;
 }
 
 }  // namespace pfsi
@@ -800,6 +1232,65 @@ extern "C" int lb_autotune(lb_ctx* c, int reps, void* stream, float* best_ms)
     c->shape = best;
     if (!rc && best_ms) *best_ms = best_t;
     return rc;
+}
+
+struct lb_batch {
+    pfsi::LbBatch* impl;
+};
+
+extern "C" int lb_batch_create(lb_ctx* const* lattices, int n, lb_batch** out)
+{
+    if (!lattices || !out) return set_error(PFSI_ERR_ARG, "lb_batch_create: null argument");
+    std::vector<LbCtx*> lat(lattices, lattices + std::max(n, 0));
+    LbBatch* impl = nullptr;
+    const int rc = lb_batch_build(lat.data(), n, &impl);
+    if (rc) return rc;
+    *out = new lb_batch{impl};
+    return PFSI_OK;
+}
+
+extern "C" int lb_batch_step(lb_batch* b, int nsteps, void* stream)
+{
+    NvtxRange nvtx_range("lb_batch_step");
+    if (!b || nsteps < 0) return set_error(PFSI_ERR_ARG, "lb_batch_step: bad argument");
+    for (int k = 0; k < nsteps; ++k) {
+        const int rc = launch_lb_batch(b->impl, as_stream(stream));
+        if (rc) return rc;
+    }
+    return PFSI_OK;
+}
+
+extern "C" int lb_batch_autotune(lb_batch* b, int reps, void* stream, float* ms_per_step)
+{
+    NvtxRange nvtx_range("lb_batch_autotune");
+    if (!b) return set_error(PFSI_ERR_ARG, "lb_batch_autotune: null batch");
+    return lb_batch_tune(b->impl, reps, as_stream(stream), ms_per_step);
+}
+
+extern "C" int lb_batch_get_shapes(const lb_batch* b, int* shapes)
+{
+    if (!b || !shapes) return set_error(PFSI_ERR_ARG, "lb_batch_get_shapes: null argument");
+    return lb_batch_shapes(b->impl, shapes);
+}
+
+extern "C" int lb_batch_set_shapes(lb_batch* b, const int* shapes)
+{
+    if (!b || !shapes) return set_error(PFSI_ERR_ARG, "lb_batch_set_shapes: null argument");
+    return lb_batch_assign_shapes(b->impl, shapes);
+}
+
+extern "C" int lb_batch_set_grid(lb_batch* b, int blocks_per_sm)
+{
+    if (!b) return set_error(PFSI_ERR_ARG, "lb_batch_set_grid: null batch");
+    return lb_batch_configure_grid(b->impl, blocks_per_sm, b->impl->priority);
+}
+
+extern "C" int lb_batch_destroy(lb_batch* b)
+{
+    if (!b) return PFSI_OK;
+    lb_batch_free(b->impl);
+    delete b;
+    return PFSI_OK;
 }
 
 extern "C" int lb_velocity(const lb_ctx* c, float** v)

@@ -358,17 +358,14 @@ __device__ __forceinline__ void pull(float* f, const uint16_t* st, const float4*
     if (bb) {
         const float4 rec = ring[r0 + (ty + 1) * T::HX + tx + 1];
         const uint16_t raw = tile[(ty + 1) * T::WX + tx + 8];
-        float e = wq(oppq(q)) * split_eq<oppq(q)>(rec);
+        float e = neq_get<kMode>(raw, inv_scale);
         if (kWall == 2) e = fmaf(6.0f * wq(q), cxq(q) * utop.x + cyq(q) * utop.y, e);
-        f[q] = e + neq_get<kMode>(raw, inv_scale);
+        f[q] = fmaf(wq(oppq(q)), split_eq<oppq(q)>(rec), e);
     } else {
         const int slot = czq(q) == 1 ? rm : (czq(q) == -1 ? rp : r0);
         const float4 rec = ring[slot + (ty + 1 - cyq(q)) * T::HX + tx + 1 - cxq(q)];
         const uint16_t raw = tile[(ty + 1 - cyq(q)) * T::WX + tx + 8 - cxq(q)];
-        if (kMode == PFSI_LB_BF16)
-            f[q] = fmaf(wq(q), split_eq<q>(rec), neq_get<kMode>(raw, inv_scale));
-        else
-            f[q] = fmaf(__half2float(__ushort_as_half(raw)), inv_scale, wq(q) * split_eq<q>(rec));
+        f[q] = fmaf(wq(q), split_eq<q>(rec), neq_get<kMode>(raw, inv_scale));
     }
 }
 
@@ -390,9 +387,8 @@ __device__ __forceinline__ void pair_out(uint16_t* out, int o, const float* f, f
     if (q == 18 || oppq(q) < q) return;
     const float cv = cdot<q>(vx, vy, vz), cF = cdot<q>(F3.x, F3.y, F3.z);
     const float wcv = wq(q) * cv;
-    const float av = rk * wcv;
     const float b = (wq(q) * guo) * cF;
-    const float odd = av + b;
+    const float odd = fmaf(rk, wcv, b);
     const float even = fmaf(cv, fmaf(rh, wcv, b), wq(q) * E0);
     out[nslot(q) * (T::OutNeqBytes / 2) + o] = neq_put<kMode>(fmaf(keep, f[q], even + odd), scale);
     out[nslot(oppq(q)) * (T::OutNeqBytes / 2) + o] = neq_put<kMode>(fmaf(keep, f[oppq(q)], even - odd), scale);
@@ -449,7 +445,7 @@ __device__ __forceinline__ void cell_step(const StepArgs& a, char* smem, int buf
     const float vy = fmaf(F3.y, 1.0f / 6.0f, my) * i3rho;
     const float vz = fmaf(F3.z, 1.0f / 6.0f, mz) * i3rho;
     const float VV = fmaf(vx, vx, fmaf(vy, vy, vz * vz));                   // 9 v.v
-    const float P0 = fmaf(-rho / 6.0f, VV, drho);                            // drho - 1.5 rho v.v
+    const float P0 = fmaf(rho * (-1.0f / 6.0f), VV, drho);                   // drho - 1.5 rho v.v
     const float vF3 = fmaf(vx, F3.x, fmaf(vy, F3.y, vz * F3.z)) * (1.0f / 3.0f);  // 3 v.F
     const float keep = 1.0f - a.omega;
     // stored = f* - E = (1 - omega)(f - f^eq) + S + (f^eq - E): per pair of

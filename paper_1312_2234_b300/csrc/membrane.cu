@@ -204,11 +204,10 @@ struct Split {
 };
 
 // Pass 1: split FP64 positions into hi/lo floats; clear the per-platelet sums.
-__global__ void __launch_bounds__(256) k_mem_split(const double* __restrict__ X, int n, float* __restrict__ xh,
-                                                   float* __restrict__ xl, double* __restrict__ acc, int nacc)
+__device__ __forceinline__ void mem_split(const double* __restrict__ X, int n, float* __restrict__ xh,
+                                          float* __restrict__ xl, double* __restrict__ acc, int nacc, int bx)
 {
-    pdl_wait();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bx * blockDim.x + threadIdx.x;
     if (t < 3 * n) {
         const double x = X[t];
         const float h = __double2float_rn(x);
@@ -216,6 +215,13 @@ __global__ void __launch_bounds__(256) k_mem_split(const double* __restrict__ X,
         xl[t] = __double2float_rn(x - (double)h);
     }
     if (t < nacc) acc[t] = 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_mem_split(const double* __restrict__ X, int n, float* __restrict__ xh,
+                                                   float* __restrict__ xl, double* __restrict__ acc, int nacc)
+{
+    pdl_wait();
+    mem_split(X, n, xh, xl, acc, nacc, blockIdx.x);
 }
 
 // Torsion gradient of the chain r1-r2-r3-r4 (Blondel and Karplus 1996), FP32,
@@ -253,10 +259,9 @@ __device__ __forceinline__ float3 ff3_float(ff3 a) { return make_float3(ff_float
 // At most 48 registers (five blocks of 256 per SM; 8 bytes spilled): the
 // channel's 178,000 elements then fit one wave, and the 500-platelet step is
 // 24 us faster than at the 58 registers the compiler picks unbounded.
-__global__ void __launch_bounds__(256, 5) k_mem_elements(MemCtx c)
+__device__ __forceinline__ void mem_elements(const MemCtx& c, int bx)
 {
-    pdl_wait();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bx * blockDim.x + threadIdx.x;
     const Split X{c.xh, c.xl, c.n};
     const mem_params P = c.p;
     int plt = -1;
@@ -352,16 +357,27 @@ __global__ void __launch_bounds__(256, 5) k_mem_elements(MemCtx c)
     }
 }
 
-// Pass 2b: per-platelet coefficients of the global area and volume terms
-// (Eq. 4-5), k_s (S - S0)/S0 and k_v (V - V0)/V0, once per platelet.
-__global__ void k_mem_coef(MemCtx c)
+__global__ void __launch_bounds__(256, 5) k_mem_elements(const __grid_constant__ MemCtx c)
 {
     pdl_wait();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    mem_elements(c, blockIdx.x);
+}
+
+// Pass 2b: per-platelet coefficients of the global area and volume terms
+// (Eq. 4-5), k_s (S - S0)/S0 and k_v (V - V0)/V0, once per platelet.
+__device__ __forceinline__ void mem_coef(const MemCtx& c, int bx)
+{
+    const int p = bx * blockDim.x + threadIdx.x;
     if (p >= c.nplt) return;
     const double* pr = c.plt_rest + 4 * p;  // S0, V0, 1/S0, 1/V0
     c.coef[p] = make_float2((float)((double)c.p.k_s * c.acc[2 * p] * pr[2]),
                             (float)((double)c.p.k_v * (c.acc[2 * p + 1] - pr[1]) * pr[3]));
+}
+
+__global__ void k_mem_coef(const __grid_constant__ MemCtx c)
+{
+    pdl_wait();
+    mem_coef(c, blockIdx.x);
 }
 
 // Pass 3: one thread per node sums its element contributions and applies the
@@ -373,10 +389,9 @@ __global__ void k_mem_coef(MemCtx c)
 // waits for each list entry, then its slot: channel step 61.8 -> 59.8 us).
 constexpr int kNodeLanes = 4;
 
-__global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx c)
+__device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c, int bx)
 {
-    pdl_wait();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = bx * blockDim.x + threadIdx.x;
     const int v = t / kNodeLanes, q = t % kNodeLanes;
     const bool on = v < c.n;
     const int n = c.n;
@@ -474,6 +489,59 @@ __global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, MemCtx
     F[2 * n + v] = fz;
 }
 
+__global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, const __grid_constant__ MemCtx c)
+{
+    pdl_wait();
+    mem_nodes(F, c, blockIdx.x);
+}
+
+// The four passes over several chambers' membranes, one launch each (see
+// Multi): the same per-thread code, each chamber's share of the grid
+// indexing its own elements and nodes.
+struct SplitArgs {
+    const double* X;
+    int n;
+    float* xh;
+    float* xl;
+    double* acc;
+    int nacc;
+};
+struct NodesArgs {
+    float* F;
+    MemCtx c;
+};
+
+__global__ void __launch_bounds__(256) k_mem_split_multi(const __grid_constant__ Multi<SplitArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    const SplitArgs& a = t.a[e];
+    mem_split(a.X, a.n, a.xh, a.xl, a.acc, a.nacc, blockIdx.x - t.first[e]);
+}
+
+__global__ void __launch_bounds__(256, 5) k_mem_elements_multi(const __grid_constant__ Multi<MemCtx> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    mem_elements(t.a[e], blockIdx.x - t.first[e]);
+}
+
+__global__ void k_mem_coef_multi(const __grid_constant__ Multi<MemCtx> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    mem_coef(t.a[e], blockIdx.x - t.first[e]);
+}
+
+__global__ void __launch_bounds__(128) k_mem_nodes_multi(const __grid_constant__ Multi<NodesArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    mem_nodes(t.a[e].F, t.a[e].c, blockIdx.x - t.first[e]);
+}
+
+int node_blocks(const MemCtx* c) { return (int)(((long long)c->n * kNodeLanes + 127) / 128); }
+
 int launch_scalars(MemCtx* c, const double* X, cudaStream_t s, bool presplit = false)
 {
     int rc = PFSI_OK;
@@ -502,8 +570,7 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
 {
     int rc = launch_scalars(c, X, s, presplit);
     if (rc) return rc;
-    return check_cuda(launch_pdl(k_mem_nodes, dim3((unsigned)(((long long)c->n * kNodeLanes + 127) / 128)), dim3(128), 0, s,
-                                 F, *c),
+    return check_cuda(launch_pdl(k_mem_nodes, dim3(node_blocks(c)), dim3(128), 0, s, F, *c),
                       "membrane_forces");
 }
 
@@ -516,6 +583,32 @@ int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s,
     g.ne = 0;            // element ids start at the triangles
     g.skip_edges = 1;
     return launch_membrane_forces(&g, X, F, s, presplit);
+}
+
+int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)
+{
+    std::vector<Multi<SplitArgs>> split;
+    std::vector<Multi<MemCtx>> elems, coef;
+    std::vector<Multi<NodesArgs>> nodes;
+    for (int i = 0; i < n; ++i) {
+        MemCtx* c = ch[i].mem;
+        const int nsplit = 3 * c->n > 2 * c->nplt ? 3 * c->n : 2 * c->nplt;
+        multi_push(split, SplitArgs{ch[i].X, c->n, c->xh, c->xl, c->acc, 2 * c->nplt}, (nsplit + 255) / 256);
+        multi_push(elems, *c, (c->ne + c->nt + c->np + 255) / 256);
+        multi_push(coef, *c, (c->nplt + 127) / 128);
+        multi_push(nodes, NodesArgs{ch[i].F, *c}, node_blocks(c));
+    }
+    int rc = PFSI_OK;
+    for (const auto& t : split)
+        if (!rc) rc = check_cuda(launch_pdl(k_mem_split_multi, dim3(t.blocks()), dim3(256), 0, s, t), "membrane: split");
+    for (const auto& t : elems)
+        if (!rc)
+            rc = check_cuda(launch_pdl(k_mem_elements_multi, dim3(t.blocks()), dim3(256), 0, s, t), "membrane: elements");
+    for (const auto& t : coef)
+        if (!rc) rc = check_cuda(launch_pdl(k_mem_coef_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: coef");
+    for (const auto& t : nodes)
+        if (!rc) rc = check_cuda(launch_pdl(k_mem_nodes_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: nodes");
+    return rc;
 }
 
 }  // namespace pfsi

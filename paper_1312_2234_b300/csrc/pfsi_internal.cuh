@@ -7,6 +7,7 @@
 
 #include <string>
 #include <utility>
+#include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -59,6 +60,52 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+
+// ---------------------------------------------------------------- multi-chamber launches
+// A batch of chambers runs each of its kernels as ONE launch over all of
+// them: entry e of the launch's list owns the blocks first[e] <= b <
+// first[e + 1] of the grid and holds that chamber's arguments, and the
+// kernel body sees b - first[e] as its block index.  The list travels as a
+// kernel parameter (__grid_constant__, read through the constant bank), at
+// most kMax entries per launch (a longer batch takes several launches).
+template <class A, int kMax = 64>
+struct Multi {
+    static constexpr int Max = kMax;
+    int n = 0;
+    int first[kMax + 1] = {0};
+    A a[kMax];
+    bool full() const { return n == kMax; }
+    void add(const A& args, int blocks)
+    {
+        a[n] = args;
+        first[n + 1] = first[n] + blocks;
+        ++n;
+    }
+    int blocks() const { return first[n]; }
+};
+
+// Entry of block b (binary search; entries own at least one block).
+template <class A, int kMax>
+__device__ __forceinline__ int multi_entry(const Multi<A, kMax>& t, int b)
+{
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.first[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Adds (args, blocks) to the last list of `lists` (a new one when it is full
+// or there is none); entries of zero blocks are left out.
+template <class A, int kMax>
+inline void multi_push(std::vector<Multi<A, kMax>>& lists, const A& args, int blocks)
+{
+    if (blocks <= 0) return;
+    if (lists.empty() || lists.back().full()) lists.emplace_back();
+    lists.back().add(args, blocks);
 }
 
 // ---------------------------------------------------------------- D3Q19
@@ -119,8 +166,8 @@ __device__ __forceinline__ void onsite_wall(float* f, float3 vw)
         }
     }
     const float rho = (1.0f + S) / (1.0f - s * vw.z);
-    const float Nx = 0.5f * jx - rho * vw.x * (1.0f / 3.0f);
-    const float Ny = 0.5f * jy - rho * vw.y * (1.0f / 3.0f);
+    const float Nx = fmaf(rho * vw.x, -1.0f / 3.0f, 0.5f * jx);
+    const float Ny = fmaf(rho * vw.y, -1.0f / 3.0f, 0.5f * jy);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         if (czq(q) != s) continue;
@@ -234,6 +281,18 @@ cudaError_t lb_tma_launch(const LbCtx* c, const struct LbTma* t, int tile, cudaS
 // bit 0: a bounded wait of the TMA-staged kernel gave up (since the last clear)
 int lb_tma_status(unsigned int* out, bool clear);
 
+// Batched lattice step (lb.cu): one persistent launch per storage kind walks
+// the tile list of every chamber of the batch.
+struct LbBatch;
+int lb_batch_build(LbCtx* const* lat, int n, LbBatch** out);
+void lb_batch_free(LbBatch* b);
+int launch_lb_batch(LbBatch* b, cudaStream_t s);      // one step of every chamber (parities advance)
+int lb_batch_tune(LbBatch* b, int reps, cudaStream_t s, float* ms_out);   // state unchanged
+int lb_batch_shapes(const LbBatch* b, int* shapes);   // per chamber; -1 for FP32 chambers
+int lb_batch_assign_shapes(LbBatch* b, const int* shapes);
+// grid of blocks_per_sm blocks per SM (0: every resident block); launch priority
+int lb_batch_configure_grid(LbBatch* b, int blocks_per_sm, int priority);
+
 // Velocity field the interpolation reads after a lattice step.
 inline float4* velocity_field(const LbCtx* c) { return c->p.storage ? c->m[c->cur] : c->v; }
 
@@ -345,6 +404,25 @@ struct NextSplit {
     int nacc = 0;
     double* part = nullptr;
 };
+// One chamber of a batch, as the multi-chamber launches take it (Multi):
+// each of these runs its kernels for all n chambers as one launch per kernel
+// (per kMax chambers), with the per-chamber results of the single-chamber
+// launch functions above.
+struct Chamber {
+    LbCtx* lb;
+    MemCtx* mem;
+    BondCtx* bonds;   // or null
+    double* X;
+    float* F;
+    float* U;
+    int M;
+};
+int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s);   // F overwritten
+int launch_bonds_forces_multi(const Chamber* ch, int n, cudaStream_t s);
+int launch_bonds_step_multi(const Chamber* ch, int n, cudaStream_t s);        // step index: counters[3]
+int launch_ib_spread_multi(const Chamber* ch, int n, cudaStream_t s);
+int launch_ib_interp_multi(const Chamber* ch, int n, cudaStream_t s);         // advects X
+
 // Platelet centroids (out[3 p + d]) from the chunk sums of the last
 // interpolation pass run with NextSplit::part = mem->cpart.
 int launch_centroids_from_chunks(MemCtx* c, double* out, cudaStream_t s);

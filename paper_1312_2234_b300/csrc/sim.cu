@@ -7,6 +7,7 @@
 // capture stream and then replayed on the caller's stream, so a step costs
 // one graph launch on the host.  The Philox step index lives in device memory
 // (advanced by the last kernel of a step), so replays need no host updates.
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -79,20 +80,22 @@ int enqueue_front(SimCtx* c, cudaStream_t s, bool presplit = false)
     return rc;
 }
 
-// Bond and bridge forces, spreading, the lattice step, interpolation and
-// advection.  split_next: the interpolation also prepares the next membrane
-// pass's input (see NextSplit), which then runs with presplit.
-int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false, bool track = false)
+// Bond and bridge forces and spreading: the part of a step before the
+// lattice Boltzmann update.
+int enqueue_pre_lb(SimCtx* c, cudaStream_t s)
 {
     int rc = PFSI_OK;
     if (c->bonds) rc = launch_bonds_forces(c->bonds, c->X, c->F, c->M, s);
     if (!rc && c->br) rc = launch_bridge_forces(c->br, c->X, c->F, c->M, s);
     if (!rc) rc = launch_ib_spread(c->lb, c->X, c->F, c->M, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s);
-    if (!rc && c->lb_ev[0])
-        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[0], s, cudaEventRecordExternal), "sim: lb timing event");
-    if (!rc) rc = launch_lb_step(c->lb, s);
-    if (!rc && c->lb_ev[1])
-        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
+    return rc;
+}
+
+// Interpolation and advection after the lattice step.  split_next: the
+// interpolation also prepares the next membrane pass's input (see
+// NextSplit), which then runs with presplit.
+int enqueue_post_lb(SimCtx* c, cudaStream_t s, bool split_next = false, bool track = false)
+{
     NextSplit next;
     if (split_next) {
         next.h = c->mem->xh;
@@ -101,8 +104,20 @@ int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false, bool trac
         next.nacc = 2 * c->mem->nplt;
     }
     if (track) next.part = c->mem->cpart;   // chunk sums for the platelet centroids
-    if (!rc)
-        rc = launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s, next);
+    return launch_ib_interp(c->lb, c->X, c->U, c->M, 1, c->mem->chunks, c->mem->perm, c->mem->n_chunks, s, next);
+}
+
+// Bond and bridge forces, spreading, the lattice step, interpolation and
+// advection.
+int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false, bool track = false)
+{
+    int rc = enqueue_pre_lb(c, s);
+    if (!rc && c->lb_ev[0])
+        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[0], s, cudaEventRecordExternal), "sim: lb timing event");
+    if (!rc) rc = launch_lb_step(c->lb, s);
+    if (!rc && c->lb_ev[1])
+        rc = check_cuda(cudaEventRecordWithFlags(c->lb_ev[1], s, cudaEventRecordExternal), "sim: lb timing event");
+    if (!rc) rc = enqueue_post_lb(c, s, split_next, track);
     return rc;
 }
 
@@ -565,31 +580,131 @@ extern "C" int sim_step_index(const sim_ctx* c, uint64_t* out)
 
 // ---------------------------------------------------------------------------
 // Batches of independent chambers: one CUDA graph holds `k` steps of every
-// chamber, each chamber's kernel chain captured on its own stream (a parallel
-// branch of the graph), so a single graph launch runs all chambers
-// concurrently and the GPU overlaps their kernels.
+// chamber.  The chambers are dealt into groups of about equal cell counts;
+// each group is an independent chain of the graph.  In a plain group (no
+// chamber with a learned surrogate, finite-element bending, bridges or
+// tethers) every kernel of a step is ONE launch for all the group's
+// chambers (Multi lists; the lattice update as one batched launch per
+// storage mode, LbBatch), so a step of any number of chambers is about a
+// dozen kernel nodes.  Otherwise each chamber's kernels before the lattice
+// update run on a branch of their own, the branches join, the batched
+// lattice launch runs, and each chamber's interpolation and adhesion update
+// run on branches again; the branch streams have the greatest priority and
+// the lattice launches the least (the graph keeps both), so the block
+// scheduler gives a freed SM slot to a waiting small kernel first.  Per
+// chamber chains (no groups) keep each chamber's whole step, its own
+// lattice launch included, on its branch.
 namespace pfsi {
 
 struct BatchCtx {
     std::vector<SimCtx*> sims;
     int k;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> join;
+    std::vector<cudaStream_t> streams;   // per chamber
+    std::vector<cudaEvent_t> join;       // per chamber
     cudaStream_t cap;
     cudaEvent_t fork;
     cudaGraphExec_t exec[2];
+    int blocks_per_sm;                   // lattice launches' grid (0: every resident block)
+    std::vector<std::vector<int>> group; // chambers of each group, in batch order
+    std::vector<LbBatch*> lb;            // per group
+    std::vector<cudaStream_t> gs;        // per group's chain (group 0: cap)
+    std::vector<cudaEvent_t> gjoin;      // per group
 };
 
 namespace {
 
-void batch_free(BatchCtx* b)
+// Chamber groups of a new batch (batch_set_layout changes them).
+constexpr int kBatchGroups = 1;
+
+void batch_drop_graphs(BatchCtx* b)
 {
     for (int k = 0; k < 2; ++k)
-        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        if (b->exec[k]) {
+            cudaGraphExecDestroy(b->exec[k]);
+            b->exec[k] = nullptr;
+        }
+}
+
+void batch_drop_groups(BatchCtx* b)
+{
+    for (LbBatch* l : b->lb) lb_batch_free(l);
+    for (size_t g = 1; g < b->gs.size(); ++g) cudaStreamDestroy(b->gs[g]);
+    for (cudaEvent_t e : b->gjoin) cudaEventDestroy(e);
+    b->lb.clear();
+    b->gs.clear();
+    b->gjoin.clear();
+    b->group.clear();
+}
+
+void batch_free(BatchCtx* b)
+{
+    batch_drop_graphs(b);
+    batch_drop_groups(b);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
+}
+
+// Deals the chambers into `groups` groups (largest lattice first, each to
+// the group with the fewest cells so far) and builds each group's lattice
+// batch, chain stream and join event.
+int batch_make_groups(BatchCtx* b, int groups, int blocks_per_sm)
+{
+    batch_drop_graphs(b);
+    batch_drop_groups(b);
+    const int n = (int)b->sims.size();
+    b->blocks_per_sm = blocks_per_sm;
+    if (groups == 0) return PFSI_OK;   // per-chamber chains (see batch_capture)
+    groups = std::min(groups, n);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->sims[x]->lb->N > b->sims[y]->lb->N; });
+    std::vector<long long> load(groups, 0);
+    std::vector<int> owner(n);
+    for (int i : order) {
+        const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[i] = g;
+        load[g] += b->sims[i]->lb->N;
+    }
+    b->group.assign(groups, {});
+    for (int i = 0; i < n; ++i) b->group[owner[i]].push_back(i);
+    int least = 0, greatest = 0;
+    int rc = check_cuda(cudaDeviceGetStreamPriorityRange(&least, &greatest), "batch: priorities");
+    for (int g = 0; g < groups && !rc; ++g) {
+        std::vector<LbCtx*> lat;
+        for (int i : b->group[g]) lat.push_back(b->sims[i]->lb);
+        LbBatch* l = nullptr;
+        rc = lb_batch_build(lat.data(), (int)lat.size(), &l);
+        if (rc) break;
+        b->lb.push_back(l);
+        rc = lb_batch_configure_grid(l, blocks_per_sm, least);
+        cudaStream_t st = b->cap;
+        if (!rc && g > 0) rc = check_cuda(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "batch: stream");
+        if (rc) break;
+        b->gs.push_back(st);
+        cudaEvent_t e = nullptr;
+        rc = check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch: event");
+        if (!rc) b->gjoin.push_back(e);
+    }
+    return rc;
+}
+
+// The branches of one phase of group g: fork from the group's chain stream,
+// `phase` on each of its chambers' streams, join back.
+template <typename Phase>
+int batch_branches(BatchCtx* b, int g, Phase phase)
+{
+    cudaStream_t chain = b->gs[g];
+    int rc = check_cuda(cudaEventRecord(b->fork, chain), "batch: fork");
+    for (int i : b->group[g]) {
+        if (rc) break;
+        rc = check_cuda(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "batch: branch");
+        if (!rc) rc = phase(b->sims[i], b->streams[i]);
+        if (!rc) rc = check_cuda(cudaEventRecord(b->join[i], b->streams[i]), "batch: join");
+        if (!rc) rc = check_cuda(cudaStreamWaitEvent(chain, b->join[i], 0), "batch: join");
+    }
+    return rc;
 }
 
 int batch_capture(BatchCtx* b, int parity)
@@ -599,19 +714,70 @@ int batch_capture(BatchCtx* b, int parity)
         saved.push_back(c->lb->cur);
         c->lb->cur = parity;
     }
+    const int groups = (int)b->group.size();
     int rc = check_cuda(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal), "batch: begin capture");
     int rc_enq = PFSI_OK;
     if (!rc) {
         rc_enq = check_cuda(cudaEventRecord(b->fork, b->cap), "batch: fork");
-        for (size_t i = 0; i < b->sims.size() && !rc_enq; ++i) {
+        // no groups: each chamber's whole step chain (its own lattice
+        // launch included) on its branch
+        for (size_t i = 0; i < b->sims.size() && groups == 0 && !rc_enq; ++i) {
             rc_enq = check_cuda(cudaStreamWaitEvent(b->streams[i], b->fork, 0), "batch: branch");
             for (int s = 0; s < b->k && !rc_enq; ++s) rc_enq = enqueue_step(b->sims[i], b->streams[i]);
             if (!rc_enq) rc_enq = check_cuda(cudaEventRecord(b->join[i], b->streams[i]), "batch: join");
             if (!rc_enq) rc_enq = check_cuda(cudaStreamWaitEvent(b->cap, b->join[i], 0), "batch: join");
         }
+        for (int g = 1; g < groups && !rc_enq; ++g)
+            rc_enq = check_cuda(cudaStreamWaitEvent(b->gs[g], b->fork, 0), "batch: group");
+        // plain groups (no surrogate, finite-element bending, bridges or
+        // tethers in any chamber) launch every kernel once for all chambers
+        std::vector<std::vector<Chamber>> plain(groups);
+        for (int g = 0; g < groups; ++g) {
+            for (int i : b->group[g]) {
+                const SimCtx* c = b->sims[i];
+                if (c->sg || c->fem || c->br || c->tether) {
+                    plain[g].clear();
+                    break;
+                }
+                plain[g].push_back(Chamber{c->lb, c->mem, c->bonds, c->X, c->F, c->U, c->M});
+            }
+        }
+        for (int s = 0; s < b->k && !rc_enq; ++s)
+            for (int g = 0; g < groups && !rc_enq; ++g) {
+                if (!plain[g].empty()) {
+                    const Chamber* ch = plain[g].data();
+                    const int n = (int)plain[g].size();
+                    cudaStream_t st = b->gs[g];
+                    rc_enq = launch_membrane_forces_multi(ch, n, st);
+                    if (!rc_enq) rc_enq = launch_bonds_forces_multi(ch, n, st);
+                    if (!rc_enq) rc_enq = launch_ib_spread_multi(ch, n, st);
+                    if (!rc_enq) rc_enq = launch_lb_batch(b->lb[g], st);
+                    if (!rc_enq) rc_enq = launch_ib_interp_multi(ch, n, st);
+                    if (!rc_enq) rc_enq = launch_bonds_step_multi(ch, n, st);
+                    continue;
+                }
+                rc_enq = batch_branches(b, g, [](SimCtx* c, cudaStream_t st) {
+                    int r = enqueue_front(c, st);
+                    if (!r) r = enqueue_pre_lb(c, st);
+                    return r;
+                });
+                if (!rc_enq) rc_enq = launch_lb_batch(b->lb[g], b->gs[g]);   // advances the group's parities
+                if (!rc_enq)
+                    rc_enq = batch_branches(b, g, [](SimCtx* c, cudaStream_t st) {
+                        int r = enqueue_post_lb(c, st);
+                        if (!r) r = enqueue_adhesion(c, st);
+                        return r;
+                    });
+            }
+        for (int g = 1; g < groups && !rc_enq; ++g) {
+            rc_enq = check_cuda(cudaEventRecord(b->gjoin[g], b->gs[g]), "batch: group join");
+            if (!rc_enq) rc_enq = check_cuda(cudaStreamWaitEvent(b->cap, b->gjoin[g], 0), "batch: group join");
+        }
         cudaGraph_t graph = nullptr;
         rc = check_cuda(cudaStreamEndCapture(b->cap, &graph), "batch: end capture");
-        if (!rc && !rc_enq) rc = check_cuda(cudaGraphInstantiate(&b->exec[parity], graph, 0), "batch: instantiate");
+        if (!rc && !rc_enq)
+            rc = check_cuda(cudaGraphInstantiateWithFlags(&b->exec[parity], graph, cudaGraphInstantiateFlagUseNodePriority),
+                            "batch: instantiate");
         if (graph) cudaGraphDestroy(graph);
     }
     for (size_t i = 0; i < b->sims.size(); ++i) b->sims[i]->lb->cur = saved[i];
@@ -639,17 +805,20 @@ extern "C" int batch_create(sim_ctx** sims, int n, int steps_per_graph, batch_ct
     b->cap = nullptr;
     b->fork = nullptr;
     b->exec[0] = b->exec[1] = nullptr;
-    int rc = check_cuda(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch_create: stream");
+    int least = 0, greatest = 0;
+    int rc = check_cuda(cudaDeviceGetStreamPriorityRange(&least, &greatest), "batch_create: priorities");
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking), "batch_create: stream");
     if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "batch_create: event");
     for (int i = 0; i < n && !rc; ++i) {
         b->sims.push_back(sims[i]);
         cudaStream_t s = nullptr;
         cudaEvent_t e = nullptr;
-        rc = check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "batch_create: stream");
+        rc = check_cuda(cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, greatest), "batch_create: stream");
         if (!rc) b->streams.push_back(s);
         if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch_create: event");
         if (!rc) b->join.push_back(e);
     }
+    if (!rc) rc = batch_make_groups(b, kBatchGroups, 0);
     if (rc) {
         batch_free(b);
         delete b;
@@ -657,6 +826,12 @@ extern "C" int batch_create(sim_ctx** sims, int n, int steps_per_graph, batch_ct
     }
     *out = b;
     return PFSI_OK;
+}
+
+extern "C" int batch_set_layout(batch_ctx* b, int groups, int blocks_per_sm)
+{
+    if (!b || groups < 0 || blocks_per_sm < 0) return set_error(PFSI_ERR_ARG, "batch_set_layout: bad argument");
+    return batch_make_groups(b, groups, blocks_per_sm);
 }
 
 extern "C" int batch_destroy(batch_ctx* b)
@@ -674,6 +849,9 @@ extern "C" int batch_step(batch_ctx* b, int nsteps, void* stream)
     cudaStream_t s = as_stream(stream);
     for (int done = 0; done < nsteps; done += b->k) {
         const int parity = b->sims[0]->lb->cur;
+        for (SimCtx* c : b->sims)
+            if (c->lb->cur != parity)
+                return set_error(PFSI_ERR_ARG, "batch_step: a chamber was stepped on its own (parities differ)");
         if (!b->exec[parity]) {
             const int rc = batch_capture(b, parity);
             if (rc) return rc;
@@ -686,4 +864,20 @@ extern "C" int batch_step(batch_ctx* b, int nsteps, void* stream)
         }
     }
     return PFSI_OK;
+}
+
+extern "C" int batch_autotune(batch_ctx* b, int reps, void* stream, float* lb_ms_per_step)
+{
+    NvtxRange nvtx_range("batch_autotune");
+    if (!b) return set_error(PFSI_ERR_ARG, "batch_autotune: null batch");
+    float total = 0.f;
+    int rc = PFSI_OK;
+    for (LbBatch* l : b->lb) {
+        float ms = 0.f;
+        if (!rc) rc = lb_batch_tune(l, reps, as_stream(stream), &ms);
+        total += ms;
+    }
+    batch_drop_graphs(b);   // the kernel nodes hold the old tile counts
+    if (!rc && lb_ms_per_step) *lb_ms_per_step = total;
+    return rc;
 }

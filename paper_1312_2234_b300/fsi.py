@@ -127,6 +127,15 @@ _SIGS = {
     "batch_create": [P, c_int, c_int, ctypes.POINTER(P)],
     "batch_destroy": [P],
     "batch_step": [P, c_int, P],
+    "batch_autotune": [P, c_int, P, ctypes.POINTER(ctypes.c_float)],
+    "batch_set_layout": [P, c_int, c_int],
+    "lb_batch_set_grid": [P, c_int],
+    "lb_batch_create": [P, c_int, ctypes.POINTER(P)],
+    "lb_batch_destroy": [P],
+    "lb_batch_step": [P, c_int, P],
+    "lb_batch_autotune": [P, c_int, P, ctypes.POINTER(ctypes.c_float)],
+    "lb_batch_get_shapes": [P, ctypes.POINTER(c_int)],
+    "lb_batch_set_shapes": [P, ctypes.POINTER(c_int)],
     "sg_params_bytes": [ctypes.POINTER(c_size_t)],
     "sg_sync_shadows": [P, P],
     "sg_query_work": [c_int, ctypes.POINTER(c_size_t)],
@@ -975,20 +984,75 @@ def lb_get_shape(lat):
     return sh.value
 
 
-class Batch:
-    """Independent chambers stepped by one CUDA graph launch (each chamber's
-    kernels on a parallel branch)."""
+class LatticeBatch:
+    """Lattices of any sizes and storage modes stepped together: one
+    persistent kernel launch per storage mode and step (lb_batch_step)."""
 
-    def __init__(self, sims, steps_per_graph=1):
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        arr = (c_void_p * len(self.lattices))(*[lat.h.value if isinstance(lat.h, c_void_p) else lat.h
+                                                 for lat in self.lattices])
+        h = c_void_p()
+        _call("lb_batch_create", ctypes.cast(arr, c_void_p), len(self.lattices), ctypes.byref(h))
+        self.h = h
+
+    def step(self, n=1, stream=None):
+        _call("lb_batch_step", self.h, int(n), _stream(stream))
+
+    def autotune(self, reps=5, stream=None):
+        """Picks each mixed lattice's column shape by timing; the state is
+        unchanged (no spread force pending).  Returns ms per batched step."""
+        ms = ctypes.c_float()
+        _call("lb_batch_autotune", self.h, int(reps), _stream(stream), ctypes.byref(ms))
+        return ms.value
+
+    def set_grid(self, blocks_per_sm):
+        """blocks per SM of the batched launches (0: every resident block)."""
+        _call("lb_batch_set_grid", self.h, int(blocks_per_sm))
+
+    def shapes(self):
+        out = (c_int * len(self.lattices))()
+        _call("lb_batch_get_shapes", self.h, out)
+        return list(out)
+
+    def set_shapes(self, shapes):
+        _call("lb_batch_set_shapes", self.h, (c_int * len(self.lattices))(*[int(s) for s in shapes]))
+
+    def __del__(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.lb_batch_destroy(self.h)
+            self.h = None
+
+
+class Batch:
+    """Independent chambers stepped by one CUDA graph launch: each chamber's
+    small kernels on parallel branches, the lattice update of all chambers
+    as one batched launch per storage mode."""
+
+    def __init__(self, sims, steps_per_graph=1, tune=False):
+        """tune: pick the mixed chambers' column shapes by timing (between
+        steps; the state is unchanged)."""
         self.sims = list(sims)
         arr = (c_void_p * len(self.sims))(*[s.h.value if isinstance(s.h, c_void_p) else s.h for s in self.sims])
         h = c_void_p()
         _call("batch_create", ctypes.cast(arr, c_void_p), len(self.sims), int(steps_per_graph), ctypes.byref(h))
         self.h = h
         self.k = steps_per_graph
+        self.lb_ms = self.autotune() if tune else None
 
     def step(self, n=1, stream=None):
         _call("batch_step", self.h, int(n), _stream(stream))
+
+    def set_layout(self, groups, blocks_per_sm=0):
+        """Chamber groups of the step graph and the lattice launches' blocks
+        per SM (0: persistent grid of every resident block)."""
+        _call("batch_set_layout", self.h, int(groups), int(blocks_per_sm))
+
+    def autotune(self, reps=5, stream=None):
+        """Returns ms per batched lattice step after tuning."""
+        ms = ctypes.c_float()
+        _call("batch_autotune", self.h, int(reps), _stream(stream), ctypes.byref(ms))
+        return ms.value
 
     def __del__(self):
         if getattr(self, "h", None) is not None and _lib is not None:

@@ -182,6 +182,21 @@ def test_bridge_workspace_and_parameter_validation(L):
     assert L.bridges_query_workspace(ctypes.byref(ok), 200, 2, 0, ctypes.byref(nb)) == -1
 
 
+def test_lattice_batch_validates_its_arguments(L):
+    h = ctypes.c_void_p()
+    assert L.lb_batch_create(None, 2, ctypes.byref(h)) == -1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert L.lb_batch_create(ctypes.cast(arr, ctypes.c_void_p), 0, ctypes.byref(h)) == -1
+    assert L.lb_batch_create(ctypes.cast(arr, ctypes.c_void_p), 1, ctypes.byref(h)) == -1
+    assert "null lattice" in fsi.last_error()
+    assert L.lb_batch_step(None, 1, None) == -1
+    assert L.lb_batch_autotune(None, 1, None, None) == -1
+    assert L.lb_batch_get_shapes(None, None) == -1
+    assert L.lb_batch_set_shapes(None, None) == -1
+    assert L.lb_batch_destroy(None) == 0
+    assert L.batch_autotune(None, 1, None, None) == -1
+
+
 def test_product_path_fails_loudly_without_the_library(monkeypatch):
     monkeypatch.setattr(fsi, "_lib", None)
     monkeypatch.setattr(fsi, "LIB_PATH", "/nonexistent/libplatelet_fsi.so")

@@ -1,5 +1,6 @@
-"""Batches of independent chambers (one CUDA graph per step holding every
-chamber's kernels as parallel branches) and the launch-shape autotuner.
+"""Batches of independent chambers (one CUDA graph per step: each kernel of
+the step one launch for a group of chambers, the lattice update one batched
+launch per storage mode) and the launch-shape autotuners.
 
 A chamber stepped inside a batch computes what it computes alone: the same
 kernels on its own buffers.  Force spreading adds tile sums with
@@ -37,13 +38,17 @@ def small_chambers():
             f32_workload(workload.tiny(seed=3, nx=19, ny=26, nz=16, shear=1.0e4))]
 
 
-@pytest.mark.parametrize("k", [1, 2])
-def test_batch_matches_individual_chambers_and_oracle(k):
+@pytest.mark.parametrize("k,layout", [(1, None), (2, None), (1, (1, 0)), (2, (2, 3)), (1, (0, 0))])
+def test_batch_matches_individual_chambers_and_oracle(k, layout):
+    """layout (groups, blocks per SM): one group (every kernel one launch for
+    all chambers), two groups, per-chamber chains; None: the default."""
     ws = small_chambers()
     storage = ["fp32", "bf16", "fp32"]
     batched = [fsi.Simulation(w, storage=s) for w, s in zip(ws, storage)]
     alone = [fsi.Simulation(w, storage=s) for w, s in zip(ws, storage)]
     batch = fsi.Batch(batched, steps_per_graph=k)
+    if layout is not None:
+        batch.set_layout(*layout)
     steps = 4
     batch.step(steps)
     for s in alone:
@@ -65,6 +70,40 @@ def test_batch_matches_individual_chambers_and_oracle(k):
         X0 = ws[i]["X"]
         assert rel(batched[i].X.cpu().numpy() - X0, ora.X - X0) < 1e-5
         assert rel(batched[i].U.cpu().numpy(), ora.U) < 1e-5
+
+
+@pytest.mark.parametrize("groups", [1, 2])
+def test_group_with_a_finite_element_chamber(groups):
+    """A chamber with the finite-element bending keeps its group on
+    per-chamber branches (the plain groups launch each kernel once for all
+    their chambers); every chamber still matches its lone steps."""
+    ws = small_chambers()
+    w = workload.tiny(seed=4, level=2, n_sce=20, n_sites=60, shear=3.0e4)
+    w["membrane"] = dict(w["membrane"], bending="fem", k0=100.0 * w["membrane"]["k0"])
+    ws.append(f32_workload(w))
+    batched = [fsi.Simulation(w) for w in ws]
+    alone = [fsi.Simulation(w) for w in ws]
+    batch = fsi.Batch(batched, steps_per_graph=2)
+    batch.set_layout(groups, 0)
+    batch.step(4)
+    for s in alone:
+        s.step(4)
+    torch.cuda.synchronize()
+    for w, a, b in zip(ws, batched, alone):
+        X0 = w["X"]
+        assert rel(a.X.cpu().numpy() - X0, b.X.cpu().numpy() - X0) < 1e-6
+        assert rel(a.U.cpu().numpy(), b.U.cpu().numpy()) < 1e-6
+        if a.bonds is not None:
+            assert np.array_equal(a.bonds.bound.cpu().numpy(), b.bonds.bound.cpu().numpy())
+
+
+def test_a_chamber_stepped_alone_stops_the_batch():
+    sims = [fsi.Simulation(w) for w in small_chambers()[:2]]
+    batch = fsi.Batch(sims)
+    batch.step(1)
+    sims[0].step(1)
+    with pytest.raises(RuntimeError, match="parit"):
+        batch.step(1)
 
 
 @pytest.mark.parametrize("storage", ["fp32", "bf16", "fp16"])
