@@ -600,7 +600,7 @@ def run_batched(args, dev, stream):
         if storage != "fp32":
             shp = lb.shapes()
             out[storage + "_lattice_batch"]["shapes"] = {n: shp.count(i) for i, n in
-                                                         enumerate(("32x8", "64x4", "16x16"))}
+                                                         enumerate(("pair 64x4", "32x4", "16x8"))}
         del lb, lats
         torch.cuda.empty_cache()
     return out

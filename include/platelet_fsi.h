@@ -149,12 +149,14 @@ int lb_init_shear(lb_ctx* ctx, void* stream);
 int lb_step(lb_ctx* ctx, int nsteps, void* stream);
 
 /* Launch shape of lb_step (no paper counterpart; the result does not depend
- * on it beyond FP32 rounding).  FP32 storage: threads per block along x,
+ * on it: every shape runs the same per-cell operation sequence and gives
+ * bit-identical populations).  FP32 storage: threads per block along x,
  * shape 0..3 = 128, 32, 64, 256 (capped at nx rounded up to 32).  Mixed
- * storage: the (x, y) column tile of the marching kernel; with nx a multiple
- * of 8, shape 0, 1 = the kernel with plain loads and 32x4, 32x8 columns and
- * 2, 3 = the TMA-staged kernel with 32x8, 32x4 columns; otherwise shape 0..3
- * = plain loads with 32x8, 32x4, 64x4, 16x8.  Default 0. */
+ * storage: the (x, y) column tile of the marching kernels; shape 0, 1 = the
+ * pair kernel (a thread takes two x-adjacent cells, packed FP32x2
+ * arithmetic) with 64x4, 64x8 columns; 2 = the one-cell kernel with 32x8
+ * columns; 3 = the TMA-staged kernel with 32x8 columns when nx is a
+ * multiple of 8, else the one-cell kernel with 32x4.  Default 0. */
 #define PFSI_LB_SHAPES 4
 int lb_set_shape(lb_ctx* ctx, int shape);
 int lb_get_shape(const lb_ctx* ctx, int* shape);
@@ -679,11 +681,11 @@ typedef struct lb_batch lb_batch;
  * buffer parity; the lattices stay owned by the caller and must outlive the
  * batch).  lb_batch_step advances every lattice by one lb_step per step with
  * ONE kernel launch per storage mode present: the cells of all lattices are
- * cut into tiles (FP32: 256 consecutive cells in x-fastest order; mixed
- * storage: (x, y) columns of 32x8, 64x4 or 16x16 cells over up to 16
- * planes, the shape picked per lattice), listed lattice after lattice, and
- * a persistent grid of as many 256-thread blocks as are resident on the GPU
- * at once walks the list.  Every tile runs the per-cell arithmetic of
+ * cut into tiles (FP32: 256 consecutive cells in x-fastest order, 256-thread
+ * blocks; mixed storage: (x, y) columns over up to 16 planes, 128-thread
+ * blocks, the column shape picked per lattice), listed lattice after
+ * lattice, and a persistent grid of as many blocks as are resident on the
+ * GPU at once walks the list.  Every tile runs the per-cell arithmetic of
  * lb_step, so each lattice's populations are bit-identical to lb_step on it
  * alone.  The initial column shape of a mixed lattice is the one with the
  * fewest threads counting idle ones in ragged columns (and a quarter per
@@ -707,7 +709,8 @@ int lb_batch_autotune(lb_batch* b, int reps, void* stream, float* ms_per_step);
  * list; fewer leave SM slots to kernels on other streams).  No effect on
  * results. */
 int lb_batch_set_grid(lb_batch* b, int blocks_per_sm);
-/* Column shape per lattice (0: 32x8, 1: 64x4, 2: 16x16; -1 for FP32):
+/* Column shape per lattice (0: the pair kernel's 64x4, 1: the one-cell
+ * kernel's 32x4, 2: its 16x8; -1 for FP32):
  * shapes[n] read or set (set ignores the FP32 entries; an entry outside
  * 0..2 for a mixed lattice is PFSI_ERR_ARG and changes nothing).  The
  * shapes do not change any cell's arithmetic. */

@@ -342,13 +342,17 @@ __device__ __forceinline__ void mixed_column(Ring<T>& ring, const uint16_t* __re
                 if (k == nz - 1) onsite_wall<-1>(f, utop);
             }
 
-            float drho = 0.f, mx = 0.f, my = 0.f, mz = 0.f;
+            // moments per pair of opposite directions (the order every
+            // 16-bit kernel uses, so that they agree bit for bit)
+            float drho = f[18], mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
-            for (int q = 0; q < 19; ++q) {
-                drho += f[q];
-                if (cxq(q)) mx += cxq(q) * f[q];
-                if (cyq(q)) my += cyq(q) * f[q];
-                if (czq(q)) mz += czq(q) * f[q];
+            for (int q = 0; q < 18; ++q) {
+                if (oppq(q) < q) continue;
+                const float s = f[q] + f[oppq(q)], d = f[q] - f[oppq(q)];
+                drho += s;
+                if (cxq(q)) mx = cxq(q) > 0 ? mx + d : mx - d;
+                if (cyq(q)) my = cyq(q) > 0 ? my + d : my - d;
+                if (czq(q)) mz = czq(q) > 0 ? mz + d : mz - d;
             }
             const float rho = 1.0f + drho;
             float3 F3 = F3b;
@@ -398,6 +402,332 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
     const int z0 = blockIdx.z * kz;
     mixed_column<kMode, T>(ring, nin, nout, min_, mout, g, flags, nx, ny, nz, blockIdx.x * T::TX, blockIdx.y * T::TY,
                            z0, min(z0 + kz, nz), omega, guo, body, utop, inv_scale, onsite);
+}
+
+// ---------------------------------------------------------------------------
+// Pair kernel of the mixed storage: a thread takes two x-adjacent cells of a
+// row, (x0 + 2 tx, x0 + 2 tx + 1) of a 64 x TY tile marched through kz
+// planes like the kernel above (same ring of moment records, 32 x TY
+// threads).  The two cells share their address arithmetic (the second
+// cell's values sit 2 bytes after the first's), with an even nx their
+// 16-bit values along x move as one 32-bit word per direction, and each
+// floating-point operation of the step runs on both cells as one packed
+// FP32x2 instruction (add, mul, fma .rn .f32x2: per lane the rounding of
+// the scalar operation).  Every lane follows the operation sequence of
+// mixed_column exactly, so the two kernels give bit-identical populations.
+template <int TY_>
+struct PairTile {
+    static constexpr int TX = 64, TY = TY_;
+    static constexpr int HX = TX + 2, HY = TY + 2;
+    static constexpr int Plane = HX * HY;
+    static constexpr int Threads = 32 * TY;
+    static constexpr int Halo = (Plane + Threads - 1) / Threads;
+};
+
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one fma with the exact product -1 b: the rounding of a - b, and
+// no separate negation of the packed operand
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(dup2(-1.0f), b, a); }
+
+// s a + t b for s, t = +-1 (the products exact): the rounding of the sum
+template <int s, int t>
+__device__ __forceinline__ float2 signed_sum2(float2 a, float2 b)
+{
+    if (s > 0) return t > 0 ? add2(a, b) : sub2(a, b);
+    if (t > 0) return sub2(b, a);
+    return sub2(mul2(dup2(-1.0f), a), b);   // (-a) + (-b), signed zeros included
+}
+template <int s>
+__device__ __forceinline__ float2 signed2(float2 a)
+{
+    return s > 0 ? a : mul2(dup2(-1.0f), a);
+}
+
+// c_q . (x, y, z) of both cells: per lane the value of cdot
+template <int q>
+__device__ __forceinline__ float2 cdot2(float2 x, float2 y, float2 z)
+{
+    constexpr int cx = cxq(q), cy = cyq(q), cz = czq(q);
+    if (cx != 0 && cy != 0) return signed_sum2<cx, cy>(x, y);
+    if (cx != 0 && cz != 0) return signed_sum2<cx, cz>(x, z);
+    if (cy != 0 && cz != 0) return signed_sum2<cy, cz>(y, z);
+    if (cx != 0) return signed2<cx>(x);
+    if (cy != 0) return signed2<cy>(y);
+    if (cz != 0) return signed2<cz>(z);
+    return dup2(0.f);
+}
+
+// f*neq of direction q that the two cells of plane k pull, as floats
+// (bounce-back: the own cells' opposite slot).  wall: 0 an interior plane,
+// 1 the bottom plane (k = 0), 2 the top plane (k = nz - 1).  kWord: the two
+// values along x sit in one aligned 32-bit word (even nx; i1 = i0 + 1 in
+// the same row).
+template <int kMode, int q, bool kWord>
+__device__ __forceinline__ float2 pull_pair(const uint16_t* __restrict__ nin, int N, int k, int nx, int ny, int j,
+                                            int ym, int yp, int i0, int i1, int xm0, int xm1, int xp0, int xp1,
+                                            float inv_scale, int wall)
+{
+    const bool bounce = (czq(q) == 1 && wall == 1) || (czq(q) == -1 && wall == 2);
+    const int sy = cyq(q) == 1 ? ym : (cyq(q) == -1 ? yp : j);
+    const uint16_t* row = bounce ? nin + nslot(oppq(q)) * N + (k * ny + j) * nx
+                                 : nin + nslot(q) * N + ((k - czq(q)) * ny + sy) * nx;
+    const bool straight = bounce || cxq(q) == 0;   // both sources at i0, i1
+    if (kWord && straight) {   // (kWord: i0 even, the word aligned)
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(row + i0);
+        if constexpr (kMode == PFSI_LB_BF16)
+            return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+        return mul2(__half22float2(*reinterpret_cast<const __half2*>(&w)), dup2(inv_scale));
+    }
+    const int a = straight ? i0 : (cxq(q) == 1 ? xm0 : xp0);
+    const int b = straight ? i1 : (cxq(q) == 1 ? xm1 : xp1);
+    const uint32_t r0 = row[a], r1 = row[b];
+    if constexpr (kMode == PFSI_LB_BF16) return make_float2(__uint_as_float(r0 << 16), __uint_as_float(r1 << 16));
+    return mul2(make_float2(__half2float(__ushort_as_half((unsigned short)r0)),
+                            __half2float(__ushort_as_half((unsigned short)r1))),
+                dup2(inv_scale));
+}
+
+// F += E_q of the source cells (as add_feq, both cells: own, own + 1)
+template <int q, class T>
+__device__ __forceinline__ void add_feq2(float2& F, const Ring<T>& ring, int sm, int s0, int sp, int own, float3 utop,
+                                         int wall)
+{
+    if (czq(q) == 1 && wall == 1) {
+        const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
+        F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)), F);
+    } else if (czq(q) == -1 && wall == 2) {
+        const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
+        const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
+        F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)),
+                 fma2(dup2(6.0f * wq(q)), dup2(cu), F));
+    } else {
+        const int slot = czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0);
+        const int src = own - cyq(q) * T::HX - cxq(q);
+        const float4 a = ring.pj[slot][src], b = ring.pj[slot][src + 1];
+        // E / w = P + cj (1 + cj / 2), both cells at once
+        const float2 cj = make_float2(cdot<q>(a.y, a.z, a.w), cdot<q>(b.y, b.z, b.w));
+        const float2 e = fma2(cj, fma2(cj, dup2(0.5f), dup2(1.0f)), make_float2(a.x, b.x));
+        F = fma2(dup2(wq(q)), e, F);
+    }
+}
+
+template <int kMode, bool kWord, class T, int... Q>
+__device__ __forceinline__ void pull_all2(std::integer_sequence<int, Q...>, float2* F, const uint16_t* __restrict__ nin,
+                                          int N, int k, int nx, int ny, int j, int ym, int yp, int i0, int i1,
+                                          int xm0, int xm1, int xp0, int xp1, float inv_scale, const Ring<T>& ring,
+                                          int sm, int s0, int sp, int own, float3 utop, int wall)
+{
+    ((F[Q] = pull_pair<kMode, Q, kWord>(nin, N, k, nx, ny, j, ym, yp, i0, i1, xm0, xm1, xp0, xp1, inv_scale, wall)),
+     ...);
+    (add_feq2<Q, T>(F[Q], ring, sm, s0, sp, own, utop, wall), ...);
+}
+
+// Stores the two cells' values of one slot (a 32-bit word when kWord).
+template <int kMode, bool kWord>
+__device__ __forceinline__ void put_pair(typename Neq<kMode>::T* __restrict__ out, int i0, int i1, bool live1,
+                                         float2 x, float scale)
+{
+    uint32_t w;
+    if constexpr (kMode == PFSI_LB_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+        w = *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const float2 y = mul2(x, dup2(scale));
+        const __half2 h = __floats2half2_rn(y.x, y.y);
+        w = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    uint16_t* o = reinterpret_cast<uint16_t*>(out);
+    if constexpr (kWord) {
+        *reinterpret_cast<uint32_t*>(o + i0) = w;
+    } else {
+        o[i0] = (uint16_t)(w & 0xffffu);
+        if (live1) o[i1] = (uint16_t)(w >> 16);
+    }
+}
+
+// Stored values of the pair (q, opposite of q) of both cells (store_pair).
+template <int kMode, bool kWord, int q>
+__device__ __forceinline__ void store_pair2(typename Neq<kMode>::T* __restrict__ nout, int N, int base, int i0, int i1,
+                                            bool live1, const float2* F, float2 vx, float2 vy, float2 vz, float2 Fx,
+                                            float2 Fy, float2 Fz, float2 rk, float2 rh, float2 keep, float2 E0,
+                                            float guo, float scale)
+{
+    if (q == 18 || oppq(q) < q) return;
+    const float2 cv = cdot2<q>(vx, vy, vz), cF = cdot2<q>(Fx, Fy, Fz);
+    const float2 wcv = mul2(dup2(wq(q)), cv);
+    const float2 b = mul2(dup2(wq(q) * guo), cF);
+    const float2 odd = fma2(rk, wcv, b);
+    const float2 even = fma2(cv, fma2(rh, wcv, b), mul2(dup2(wq(q)), E0));
+    put_pair<kMode, kWord>(nout + nslot(q) * N + base, i0, i1, live1, fma2(keep, F[q], add2(even, odd)), scale);
+    put_pair<kMode, kWord>(nout + nslot(oppq(q)) * N + base, i0, i1, live1, fma2(keep, F[oppq(q)], sub2(even, odd)),
+                           scale);
+}
+
+template <int kMode, bool kWord, int... Q>
+__device__ __forceinline__ void store_pairs2(std::integer_sequence<int, Q...>, typename Neq<kMode>::T* __restrict__ nout,
+                                             int N, int base, int i0, int i1, bool live1, const float2* F, float2 vx,
+                                             float2 vy, float2 vz, float2 Fx, float2 Fy, float2 Fz, float2 rk,
+                                             float2 rh, float2 keep, float2 E0, float guo, float scale)
+{
+    (store_pair2<kMode, kWord, Q>(nout, N, base, i0, i1, live1, F, vx, vy, vz, Fx, Fy, Fz, rk, rh, keep, E0, guo,
+                                  scale),
+     ...);
+}
+
+// One plane k of the pair kernel's column (both cells live or the second
+// repeating the first); wall as pull_pair.  (With the wall a template
+// argument, one body per kind of plane, the compiler hoists the interior
+// body's loads and spills some 700 bytes a thread.)
+template <int kMode, bool kWord, class T>
+__device__ __forceinline__ void pair_plane(const Ring<T>& ring, const uint16_t* __restrict__ nin,
+                                           typename Neq<kMode>::T* __restrict__ nout, float4* __restrict__ mout,
+                                           float4* __restrict__ g, const uint32_t* __restrict__ flags, int N, int nx,
+                                           int ny, int k, int j, int ym, int yp, int i0, int i1, bool live1, int xm0,
+                                           int xm1, int xp0, int xp1, int own, float omega, float keep, float guo,
+                                           float3 F3b, float3 utop, float inv_scale, float scale, int onsite,
+                                           int wall)
+{
+    const int row = k * ny + j;
+    const int base = row * nx;   // the cells are base + i0, base + i1
+    float2 F[19];
+    pull_all2<kMode, kWord, T>(std::make_integer_sequence<int, 19>{}, F, nin, N, k, nx, ny, j, ym, yp, i0, i1, xm0,
+                               xm1, xp0, xp1, inv_scale, ring, (k + 3) & 3, k & 3, (k + 1) & 3, own, utop, wall);
+    if (wall != 0 && onsite) {
+        float fa[19], fb[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            fa[q] = F[q].x;
+            fb[q] = F[q].y;
+        }
+        if (wall == 1) {
+            onsite_wall<1>(fa, make_float3(0.f, 0.f, 0.f));
+            onsite_wall<1>(fb, make_float3(0.f, 0.f, 0.f));
+        } else {
+            onsite_wall<-1>(fa, utop);
+            onsite_wall<-1>(fb, utop);
+        }
+#pragma unroll
+        for (int q = 0; q < 19; ++q) F[q] = make_float2(fa[q], fb[q]);
+    }
+
+    // moments per pair of opposite directions (mixed_column's order)
+    float2 drho = F[18], mx = dup2(0.f), my = dup2(0.f), mz = dup2(0.f);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        if (oppq(q) < q) continue;
+        const float2 sq = add2(F[q], F[oppq(q)]), d = sub2(F[q], F[oppq(q)]);
+        drho = add2(drho, sq);
+        if (cxq(q)) mx = cxq(q) > 0 ? add2(mx, d) : sub2(mx, d);
+        if (cyq(q)) my = cyq(q) > 0 ? add2(my, d) : sub2(my, d);
+        if (czq(q)) mz = czq(q) > 0 ? add2(mz, d) : sub2(mz, d);
+    }
+    const float2 rho = add2(dup2(1.0f), drho);
+    float2 Fx = dup2(F3b.x), Fy = dup2(F3b.y), Fz = dup2(F3b.z);
+    const bool forced = flags[row] != 0u;
+    float4 g0, g1;
+    if (forced) {
+        g0 = g[base + i0];
+        g1 = g[base + i1];
+        Fx = fma2(dup2(3.0f), make_float2(g0.x, g1.x), Fx);
+        Fy = fma2(dup2(3.0f), make_float2(g0.y, g1.y), Fy);
+        Fz = fma2(dup2(3.0f), make_float2(g0.z, g1.z), Fz);
+    }
+    const float2 i3rho = make_float2(3.0f / rho.x, 3.0f / rho.y);
+    const float2 vx = mul2(fma2(Fx, dup2(1.0f / 6.0f), mx), i3rho);
+    const float2 vy = mul2(fma2(Fy, dup2(1.0f / 6.0f), my), i3rho);
+    const float2 vz = mul2(fma2(Fz, dup2(1.0f / 6.0f), mz), i3rho);
+    const float2 VV = fma2(vx, vx, fma2(vy, vy, mul2(vz, vz)));
+    const float2 P0 = fma2(mul2(rho, dup2(-1.0f / 6.0f)), VV, drho);
+    const float2 vF3 = mul2(fma2(vx, Fx, fma2(vy, Fy, mul2(vz, Fz))), dup2(1.0f / 3.0f));
+    const float2 E0 = fma2(dup2(-keep), P0, mul2(dup2(-guo), vF3));
+    const float2 rh = mul2(mul2(dup2(0.5f), rho), sub2(dup2(omega), rho));
+    const float2 rk = mul2(dup2(-keep), rho);
+    put_pair<kMode, kWord>(nout + nslot(18) * N + base, i0, i1, live1,
+                           fma2(dup2(keep), F[18], mul2(dup2(wq(18)), E0)), scale);
+    store_pairs2<kMode, kWord>(std::make_integer_sequence<int, 18>{}, nout, N, base, i0, i1, live1, F, vx, vy,
+                               vz, Fx, Fy, Fz, rk, rh, dup2(keep), E0, guo, scale);
+    const float2 third = dup2(1.0f / 3.0f);
+    const float2 ux = mul2(vx, third), uy = mul2(vy, third), uz = mul2(vz, third);
+    mout[base + i0] = make_float4(ux.x, uy.x, uz.x, drho.x);
+    if (live1) mout[base + i1] = make_float4(ux.y, uy.y, uz.y, drho.y);
+    if (forced) {
+        g[base + i0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (live1) g[base + i1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int kMode, bool kWord, class T>
+__device__ __forceinline__ void mixed_pair_column(Ring<T>& ring, const uint16_t* __restrict__ nin,
+                                                  typename Neq<kMode>::T* __restrict__ nout,
+                                                  const float4* __restrict__ min_, float4* __restrict__ mout,
+                                                  float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx,
+                                                  int ny, int nz, int x0, int y0, int z0, int z1, float omega,
+                                                  float guo, float3 body, float3 utop, float inv_scale, int onsite)
+{
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int j = y0 + ty;
+    const int i0 = x0 + 2 * tx;
+    const bool live0 = i0 < nx && j < ny;
+    const bool live1 = i0 + 1 < nx && j < ny;
+    const int i1 = live1 ? i0 + 1 : i0;   // a missing second cell repeats the first (nothing stored)
+    const int N = nx * ny * nz;
+    const int plane_cells = nx * ny;
+    const int xm0 = (i0 == 0) ? nx - 1 : i0 - 1, xm1 = (i1 == 0) ? nx - 1 : i1 - 1;
+    const int xp0 = (i0 >= nx - 1) ? 0 : i0 + 1, xp1 = (i1 >= nx - 1) ? 0 : i1 + 1;
+    const int ym = (j == 0) ? ny - 1 : j - 1;
+    const int yp = (j >= ny - 1) ? 0 : j + 1;
+    const float keep = 1.0f - omega;
+    const float scale = 1.0f / inv_scale;
+    const int own = (ty + 1) * T::HX + 2 * tx + 1;
+
+    int off[T::Halo];
+#pragma unroll
+    for (int u = 0; u < T::Halo; ++u) {
+        const int h = threadIdx.x + u * T::Threads;
+        const int hy = h / T::HX, hx = h - hy * T::HX;
+        int gx = x0 + hx - 1, gy = y0 + hy - 1;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        off[u] = h < T::Plane ? gy * nx + gx : -1;
+    }
+
+    float4 r[T::Halo];
+    for (int p = max(z0 - 1, 0); p <= min(z0 + 1, nz - 1); ++p) {
+        halo_load<T>(min_, p, plane_cells, off, r);
+        halo_store<T>(ring, p & 3, r);
+    }
+    __syncthreads();
+
+    const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
+    for (int k = z0; k < z1; ++k) {
+        const bool pre = k + 2 < nz && k + 2 <= z1;
+        if (pre) halo_load<T>(min_, k + 2, plane_cells, off, r);
+        if (live0)
+            pair_plane<kMode, kWord, T>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1, live1, xm0,
+                                        xm1, xp0, xp1, own, omega, keep, guo, F3b, utop, inv_scale, scale, onsite,
+                                        k == 0 ? 1 : (k == nz - 1 ? 2 : 0));
+        if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
+        __syncthreads();
+    }
+}
+
+// At most 128 registers a thread (two blocks of 256 threads per SM, four of
+// 128): unbounded, the compiler takes up to 168 and leaves one block per SM.
+template <int kMode, bool kWord, class T>
+__global__ void __launch_bounds__(T::Threads, 512 / T::Threads) k_lb_step_pair(
+    const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
+    float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
+    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
+{
+    pdl_wait();
+    __shared__ Ring<T> ring;
+    const int z0 = blockIdx.z * kz;
+    mixed_pair_column<kMode, kWord, T>(ring, nin, nout, min_, mout, g, flags, nx, ny, nz, blockIdx.x * T::TX,
+                                       blockIdx.y * T::TY, z0, min(z0 + kz, nz), omega, guo, body, utop, inv_scale,
+                                       onsite);
 }
 
 template <int kMode, int q>
@@ -569,25 +899,35 @@ cudaError_t launch_mixed(LbCtx* c, cudaStream_t s, float omega, float guo, float
                       p.nz, kz, omega, guo, body, utop, inv_scale, p.walls);
 }
 
+template <int kMode, class T>
+cudaError_t launch_pair(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+{
+    const lb_params& p = c->p;
+    const int a = c->cur, b = c->cur ^ 1;
+    const int tiles = ((p.nx + T::TX - 1) / T::TX) * ((p.ny + T::TY - 1) / T::TY);
+    const long long want = 148LL * 8 * 256 / T::Threads;
+    const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
+    const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
+    auto kernel = p.nx % 2 == 0 ? k_lb_step_pair<kMode, true, T> : k_lb_step_pair<kMode, false, T>;
+    return launch_pdl(kernel, grid, dim3(T::Threads), 0, s, (const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b],
+                      (const float4*)c->m[a], c->m[b], c->g, (const uint32_t*)c->flags, p.nx, p.ny, p.nz, kz, omega,
+                      guo, body, utop, inv_scale, p.walls);
+}
+
 template <int kMode>
 cudaError_t launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop,
                                float inv_scale)
 {
-    if (c->tma) {
-        // shapes 0, 1: this kernel with 32 x 4 or 32 x 8 columns (the faster
-        // on B300); 2, 3: the TMA-staged kernel with 32 x 8 or 32 x 4 columns
-        switch (c->shape) {
-        case 0: return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
-        case 1: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
-        case 2: return lb_tma_launch(c, c->tma, 0, s, omega, guo, body, utop, inv_scale);
-        default: return lb_tma_launch(c, c->tma, 1, s, omega, guo, body, utop, inv_scale);
-        }
-    }
+    // shapes 0, 1: the pair kernel with 64 x 4 or 64 x 8 columns; 2: the
+    // one-cell kernel with 32 x 8 columns; 3: the TMA-staged kernel with
+    // 32 x 8 columns where it applies, else the one-cell kernel with 32 x 4
     switch (c->shape) {
-    case 1: return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
-    case 2: return launch_mixed<kMode, Tile<64, 4>>(c, s, omega, guo, body, utop, inv_scale);
-    case 3: return launch_mixed<kMode, Tile<16, 8>>(c, s, omega, guo, body, utop, inv_scale);
-    default: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
+    case 0: return launch_pair<kMode, PairTile<4>>(c, s, omega, guo, body, utop, inv_scale);
+    case 1: return launch_pair<kMode, PairTile<8>>(c, s, omega, guo, body, utop, inv_scale);
+    case 2: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
+    default:
+        if (c->tma) return lb_tma_launch(c, c->tma, 0, s, omega, guo, body, utop, inv_scale);
+        return launch_mixed<kMode, Tile<32, 4>>(c, s, omega, guo, body, utop, inv_scale);
     }
 }
 
@@ -629,16 +969,20 @@ struct LbTable {
 };
 static_assert(sizeof(LbTable) <= 32000, "the tile list must fit the kernel parameter space");
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;                 // FP32 blocks
 constexpr int kBatchFp32Tile = kBatchThreads;      // FP32: consecutive cells (flat order) per tile
-constexpr int kBatchShapes = 3;                     // mixed column tiles, 256 threads each
-constexpr int kBatchTX[kBatchShapes] = {32, 64, 16};
-constexpr int kBatchTY[kBatchShapes] = {8, 4, 16};
+constexpr int kBatchMixedThreads = 128;            // mixed-storage blocks
+// mixed column tiles of 128 threads: the pair kernel's 64 x 4 (two cells a
+// thread), the one-cell kernel's 32 x 4 and 16 x 8
+constexpr int kBatchShapes = 3;
+constexpr int kBatchTX[kBatchShapes] = {64, 32, 16};
+constexpr int kBatchTY[kBatchShapes] = {4, 4, 8};
 constexpr int kBatchKz = 16;                        // mixed: planes per column
 constexpr int kBatchPlane = 66 * 6;                 // largest ring plane of the three shapes (64 x 4)
-static_assert(Tile<32, 8>::Plane <= kBatchPlane && Tile<64, 4>::Plane <= kBatchPlane &&
-                  Tile<16, 16>::Plane <= kBatchPlane,
-              "ring storage must hold every shape's plane");
+static_assert(PairTile<4>::Plane <= kBatchPlane && Tile<32, 4>::Plane <= kBatchPlane &&
+                  Tile<16, 8>::Plane <= kBatchPlane && PairTile<4>::Threads == kBatchMixedThreads &&
+                  Tile<32, 4>::Threads == kBatchMixedThreads && Tile<16, 8>::Threads == kBatchMixedThreads,
+              "ring storage must hold every shape's plane; every shape takes the block");
 
 // Chamber of tile t: the list is sorted by tile0 and a block's tiles only
 // grow, so the search moves forward from the previous tile's chamber.
@@ -667,16 +1011,32 @@ __global__ void __launch_bounds__(kBatchThreads) k_lb_step_batch(const __grid_co
 template <int kMode, int S>
 __device__ __forceinline__ void batch_column(float4* ring_mem, const LbChamber& ch, int tx, int ty, int z0)
 {
-    using T = Tile<kBatchTX[S], kBatchTY[S]>;
-    mixed_column<kMode, T>(*reinterpret_cast<Ring<T>*>(ring_mem), (const uint16_t*)ch.fin,
-                           (typename Neq<kMode>::T*)ch.fout, ch.min, ch.mout, ch.g, ch.flags, ch.nx, ch.ny, ch.nz,
-                           tx * T::TX, ty * T::TY, z0, min(z0 + ch.kz, ch.nz), ch.omega, ch.guo, ch.body, ch.utop,
-                           ch.inv_scale, ch.onsite);
+    const int z1 = min(z0 + ch.kz, ch.nz);
+    if constexpr (S == 0) {
+        using T = PairTile<4>;
+        auto& ring = *reinterpret_cast<Ring<T>*>(ring_mem);
+        if (ch.nx % 2 == 0)
+            mixed_pair_column<kMode, true, T>(ring, (const uint16_t*)ch.fin, (typename Neq<kMode>::T*)ch.fout, ch.min,
+                                              ch.mout, ch.g, ch.flags, ch.nx, ch.ny, ch.nz, tx * T::TX, ty * T::TY,
+                                              z0, z1, ch.omega, ch.guo, ch.body, ch.utop, ch.inv_scale, ch.onsite);
+        else
+            mixed_pair_column<kMode, false, T>(ring, (const uint16_t*)ch.fin, (typename Neq<kMode>::T*)ch.fout,
+                                               ch.min, ch.mout, ch.g, ch.flags, ch.nx, ch.ny, ch.nz, tx * T::TX,
+                                               ty * T::TY, z0, z1, ch.omega, ch.guo, ch.body, ch.utop, ch.inv_scale,
+                                               ch.onsite);
+    } else {
+        using T = Tile<kBatchTX[S], kBatchTY[S]>;
+        mixed_column<kMode, T>(*reinterpret_cast<Ring<T>*>(ring_mem), (const uint16_t*)ch.fin,
+                               (typename Neq<kMode>::T*)ch.fout, ch.min, ch.mout, ch.g, ch.flags, ch.nx, ch.ny, ch.nz,
+                               tx * T::TX, ty * T::TY, z0, z1, ch.omega, ch.guo, ch.body, ch.utop, ch.inv_scale,
+                               ch.onsite);
+    }
 }
 
+// At most 128 registers (four blocks of 128 threads per SM), the pair
+// kernel's budget.
 template <int kMode>
-__global__ void __launch_bounds__(kBatchThreads, 768 / kBatchThreads) k_lb_step_batch_mixed(
-    const __grid_constant__ LbTable tab)
+__global__ void __launch_bounds__(kBatchMixedThreads, 4) k_lb_step_batch_mixed(const __grid_constant__ LbTable tab)
 {
     __shared__ float4 ring_mem[kSlots * kBatchPlane];
     int c = 0;
@@ -752,13 +1112,14 @@ struct LbBatch {
 namespace {
 
 // Columns of a mixed chamber for a batch shape, and the shape the batch
-// starts from before tuning: the fewest threads per chamber counting idle
-// ones in ragged columns and a quarter thread per ring cell.
+// starts from before tuning: the least work per chamber counting idle cells
+// in ragged columns (a pair-kernel thread takes two) and a quarter of a
+// cell per ring record.
 long long batch_cost(const lb_params& p, int shape)
 {
     const long long tx = (p.nx + kBatchTX[shape] - 1) / kBatchTX[shape];
     const long long ty = (p.ny + kBatchTY[shape] - 1) / kBatchTY[shape];
-    return tx * ty * (4 * kBatchThreads + (kBatchTX[shape] + 2) * (kBatchTY[shape] + 2));
+    return tx * ty * (4 * kBatchMixedThreads * (shape == 0 ? 2 : 1) + (kBatchTX[shape] + 2) * (kBatchTY[shape] + 2));
 }
 
 int batch_default_shape(const lb_params& p)
@@ -829,13 +1190,13 @@ int batch_upload(LbBatch* b, int mode, const std::vector<int>& shapes)
 }
 
 template <typename K>
-int resident_blocks(K kernel, LbBatch::Kind& kind)
+int resident_blocks(K kernel, int threads, LbBatch::Kind& kind)
 {
     int dev = 0;
     int rc = check_cuda(cudaGetDevice(&dev), "lb_batch: device");
     if (!rc) rc = check_cuda(cudaDeviceGetAttribute(&kind.sms, cudaDevAttrMultiProcessorCount, dev), "lb_batch: SMs");
     if (!rc)
-        rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&kind.per_sm, kernel, kBatchThreads, 0),
+        rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&kind.per_sm, kernel, threads, 0),
                         "lb_batch: occupancy");
     kind.per_sm = std::max(kind.per_sm, 1);
     return rc;
@@ -859,7 +1220,7 @@ cudaError_t batch_launch_kind(const LbBatch* b, const LbBatch::Kind& K, int mode
     attr[0].val.priority = b->priority;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(std::max(1, std::min(K.grid, tab.ntiles)));
-    cfg.blockDim = dim3(kBatchThreads);
+    cfg.blockDim = dim3(mode == PFSI_LB_FP32 ? kBatchThreads : kBatchMixedThreads);
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
@@ -898,9 +1259,9 @@ int lb_batch_build(LbCtx* const* lat, int n, LbBatch** out)
         if (K.members.empty()) continue;
         rc = batch_upload(b, mode, shapes);
         if (!rc)
-            rc = mode == PFSI_LB_BF16   ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_BF16>, K)
-                 : mode == PFSI_LB_FP16 ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_FP16>, K)
-                                        : resident_blocks(k_lb_step_batch, K);
+            rc = mode == PFSI_LB_BF16   ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_BF16>, kBatchMixedThreads, K)
+                 : mode == PFSI_LB_FP16 ? resident_blocks(k_lb_step_batch_mixed<PFSI_LB_FP16>, kBatchMixedThreads, K)
+                                        : resident_blocks(k_lb_step_batch, kBatchThreads, K);
     }
     size_grids(b);
     if (rc) {

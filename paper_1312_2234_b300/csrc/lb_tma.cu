@@ -421,16 +421,16 @@ __device__ __forceinline__ void cell_step(const StepArgs& a, char* smem, int buf
         if (kWall == 2) onsite_wall<-1>(f, a.utop);
     }
 
-    // moments per pair of opposite directions
+    // moments per pair of opposite directions (the order of every 16-bit kernel)
     float drho = f[18], mx = 0.f, my = 0.f, mz = 0.f;
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         if (oppq(q) < q) continue;
         const float s = f[q] + f[oppq(q)], d = f[q] - f[oppq(q)];
         drho += s;
-        if (cxq(q)) mx = fmaf((float)cxq(q), d, mx);
-        if (cyq(q)) my = fmaf((float)cyq(q), d, my);
-        if (czq(q)) mz = fmaf((float)czq(q), d, mz);
+        if (cxq(q)) mx = cxq(q) > 0 ? mx + d : mx - d;
+        if (cyq(q)) my = cyq(q) > 0 ? my + d : my - d;
+        if (czq(q)) mz = czq(q) > 0 ? mz + d : mz - d;
     }
     const float rho = 1.0f + drho;
     float3 F3 = make_float3(3.0f * a.body.x, 3.0f * a.body.y, 3.0f * a.body.z);

@@ -14,7 +14,7 @@ from paper_1312_2234_b300 import fsi, workload
 pytestmark = pytest.mark.gpu
 
 # (nx, ny, nz, storage, walls): ragged in x and y for every column shape
-# (32x8, 64x4, 16x16), nz below and above the 16-plane column depth, a
+# (pair 64x4, 32x4, 16x8), nz below and above the 16-plane column depth, a
 # two-plane lattice, both wall modes
 SPECS = [(53, 37, 29, "fp32", 0), (48, 40, 36, "bf16", 0), (33, 19, 17, "fp16", 1), (64, 8, 3, "bf16", 1),
          (17, 70, 21, "fp32", 1), (100, 27, 40, "fp16", 0), (7, 5, 2, "bf16", 0), (130, 3, 18, "fp32", 0)]

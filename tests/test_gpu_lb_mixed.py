@@ -190,8 +190,9 @@ def test_state_varying_along_x(storage, dims):
 @pytest.mark.parametrize("dims", [(48, 17, 13), (8, 5, 4), (64, 9, 6), (16, 3, 5), (40, 24, 7)])
 def test_launch_shapes_rows_on_16_byte_boundaries(storage, shape, dims):
     """Grids whose x rows start on 16-byte boundaries (nx a multiple of 8):
-    shapes 0 and 1 run the kernel with plain loads (32x4 and 32x8 columns),
-    2 and 3 the TMA-staged kernel (32x8 and 32x4 columns).  Columns wider or taller than the grid,
+    shapes 0 and 1 run the pair kernel (64x4 and 64x8 columns, two cells a
+    thread), 2 the one-cell kernel (32x8 columns), 3 the TMA-staged kernel
+    (32x8 columns).  Columns wider or taller than the grid,
     partial columns at the far edges, the periodic halo of every edge column
     and both wall planes; a state that varies from cell to cell and a
     flagged force, against the oracle with the bounds of test_free_steps."""
@@ -234,17 +235,56 @@ def test_launch_shapes_rows_on_16_byte_boundaries(storage, shape, dims):
 
 
 def test_shapes_share_one_state():
-    """The TMA-staged kernel and the plain-load kernel read and write the
-    same stored state: alternating them step by step matches one kernel
-    throughout to the rounding of the 16-bit values."""
+    """All 16-bit kernels read and write the same stored state with the same
+    per-cell operation sequence: alternating them step by step gives the
+    populations of one kernel bit for bit."""
     dims = (64, 24, 10)
     runs = []
-    for order in ([0] * 8, [0, 2, 1, 3, 0, 2, 1, 3]):
+    for order in ([2] * 8, [0, 2, 1, 3, 0, 2, 1, 3]):
         lat = fsi.Lattice(*dims, 0.8, (4e-3, 0.0, 0.0), storage="bf16")
         lat.init_shear()
         for s in order:
             fsi.lb_set_shape(lat, s)
             lat.step(1)
         runs.append(lat.export().cpu().numpy())
-    scale = np.abs(runs[0]).max()
-    assert np.abs(runs[0] - runs[1]).max() <= 1e-5 * scale
+    assert np.array_equal(runs[0], runs[1])
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("walls", [0, 1])
+@pytest.mark.parametrize("dims", [(64, 24, 10), (54, 20, 9), (53, 17, 13), (130, 7, 5), (3, 5, 4), (1, 4, 3)])
+def test_every_shape_bit_identical(storage, walls, dims):
+    """Every launch shape (pair kernel with 64x4 and 64x8 columns, one-cell
+    kernel, TMA-staged kernel or the one-cell kernel with 32x4 columns) gives
+    the same populations and moment records bit for bit: even nx (the pair
+    kernel's 32-bit words; a multiple of 8 also takes the TMA kernel), odd
+    nx (the last pair of a row has one cell), more than two pair columns
+    along x, grids narrower than one column, both wall modes, a state that
+    varies from cell to cell and flagged forces, over 4 steps."""
+    nx, ny, nz = dims
+    N = nx * ny * nz
+    rng = np.random.default_rng(nx * 100 + ny)
+    flags = (rng.uniform(size=ny * nz) < 0.4).astype(np.int32)
+    g = np.zeros((N, 4), np.float32)
+    rows = np.repeat(flags, nx).astype(bool)
+    g[rows, :3] = (1e-5 * rng.standard_normal((rows.sum(), 3))).astype(np.float32)
+    noise = (3e-5 * rng.standard_normal((19, N))).astype(np.float32)
+    out = []
+    for shape in range(4):
+        lat = fsi.Lattice(nx, ny, nz, 0.8, (4e-3, -1.5e-3, 0.0), (2e-6, 0.0, -1e-6), storage=storage, walls=walls)
+        fsi.lb_set_shape(lat, shape)
+        lat.init_shear()
+        live = 0 if lat.velocity().data_ptr() == lat.m[0].data_ptr() else 1
+        cur = lat.f[live]
+        scale = 1.0 if storage == "bf16" else 2.0 ** lat.p.fp16_exponent
+        cur.copy_((cur.float() + torch.from_numpy(noise).cuda() * scale).to(cur.dtype))
+        for _ in range(4):
+            lat.g.copy_(torch.from_numpy(g))
+            lat.flags.copy_(torch.from_numpy(flags))
+            lat.step(1)
+        torch.cuda.synchronize()
+        out.append((lat.export().cpu().numpy(), lat.velocity().cpu().numpy()))
+    for f, m in out[1:]:
+        assert np.array_equal(f, out[0][0])
+        assert np.array_equal(m, out[0][1])
+    assert np.isfinite(out[0][0]).all()
