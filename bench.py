@@ -63,16 +63,17 @@ def measured_peaks():
 
 def lb_kernel_sha():
     """Hash of the FP32 lattice kernel's source: the on-site wall helper it
-    calls (csrc/pfsi_internal.cuh) and k_lb_step (csrc/lb.cu); the rest of
-    those files does not change the kernel the traffic figure was measured
-    on."""
+    calls (csrc/pfsi_internal.cuh), its per-cell body fp32_cell and the
+    kernel k_lb_step (csrc/lb.cu); the rest of those files does not change
+    the kernel the traffic figure was measured on."""
     csrc = os.path.join(ROOT, "paper_1312_2234_b300", "csrc")
     hdr = open(os.path.join(csrc, "pfsi_internal.cuh")).read()
     a = hdr.index("template <int s>\n__device__ __forceinline__ void onsite_wall")
     b = hdr.index("\n}\n", a) + 3
     src = open(os.path.join(csrc, "lb.cu")).read()
-    c = src.index("__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(")
-    d = src.index("\n}\n", c) + 3
+    c = src.index("__device__ __forceinline__ void fp32_cell(")
+    c2 = src.index("__global__ void __launch_bounds__(kMaxRowBlock) k_lb_step(")
+    d = src.index("\n}\n", c2) + 3
     return hashlib.sha256((hdr[a:b] + src[c:d]).encode()).hexdigest()[:16]
 
 
