@@ -250,8 +250,20 @@ int membrane_set_params(mem_ctx* ctx, const mem_params* p);
 
 /* F = -grad(H_SCE + H_area + H_volume + H_bend + H_Morse) + F_wall  (Eq. 11,
  * read with the minus sign of Eq. 3).  X: device double[3][n_nodes]; F:
- * device float[3][n_nodes], overwritten. */
+ * device float[3][n_nodes], overwritten.  Two implementations (no paper
+ * counterpart; the same per-element arithmetic, summed per node in another
+ * order): three passes through per-element force slots in the workspace
+ * (the default), or the fused pass, one block per platelet with the
+ * platelet's positions and 64-bit fixed-point force accumulators in shared
+ * memory (exact sums: forces independent of scheduling), which applies when
+ * each platelet's edges, triangles and Morse pairs form one run of the
+ * element lists and its nodes fit (about 4,700 nodes). */
 int membrane_forces(mem_ctx* ctx, const double* X, float* F, void* stream);
+/* path 0 (the default): the three passes; 1: the fused pass where it
+ * applies.  membrane_get_path: *fused = 1 if membrane_forces runs the fused
+ * pass. */
+int membrane_set_path(mem_ctx* ctx, int path);
+int membrane_get_path(const mem_ctx* ctx, int* fused);
 
 /* Centroid of every platelet's nodes (membrane and SCE) at positions X:
  * out_dev (device, 4 * n_plt doubles, 8-byte aligned) receives the

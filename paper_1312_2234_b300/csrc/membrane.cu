@@ -138,7 +138,7 @@ int build_topology(int n, int nt, const int* tri, int np, const int* pairs, Topo
 enum Slice {
     S_TRI, S_TRI_PLT, S_TRI_REST, S_EDGE, S_EDGE_REST, S_EDGE_PHI0, S_PAIR, S_PAIR_REST, S_ESL_OFF,
     S_ESL, S_TCL_OFF, S_TCL, S_PSL_OFF, S_PSL, S_NODE_PLT, S_IS_MEM, S_PLT_REST, S_PLT_ANCHOR, S_ACC,
-    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_PLT_RANGE, S_PLT_CHUNKS, S_CPART, S_COUNT
+    S_XH, S_XL, S_EOUT, S_TOUT, S_POUT, S_CHUNKS, S_PERM, S_PLT_RANGE, S_PLT_CHUNKS, S_CPART, S_PLT_SPAN, S_COUNT
 };
 struct Layout {
     size_t off[S_COUNT];
@@ -152,7 +152,7 @@ Layout make_layout(int n, int nt, int ne, int np, int nplt, size_t n_esl, size_t
         12 * T, 4 * T, 32 * T, 16 * E, 16 * E, 16 * E, 8 * P, 16 * P, 4 * (N + 1), 4 * n_esl,
         4 * (N + 1), 4 * n_tcl, 4 * (N + 1), 4 * n_psl, 4 * N, N, 32 * Q, 4 * Q, 24 * Q, 12 * N, 12 * N,
         64 * E, 64 * T, 16 * P, 8 * ((N + kIbChunk - 1) / kIbChunk + Q), 4 * N, 8 * Q, 8 * Q,
-        24 * ((N + kIbChunk - 1) / kIbChunk + Q)};
+        24 * ((N + kIbChunk - 1) / kIbChunk + Q), 32 * Q};
     Layout L;
     size_t o = 0;
     for (int s = 0; s < S_COUNT; ++s) {
@@ -259,6 +259,88 @@ __device__ __forceinline__ float3 ff3_float(ff3 a) { return make_float3(ff_float
 // At most 48 registers (five blocks of 256 per SM; 8 bytes spilled): the
 // channel's 178,000 elements then fit one wave, and the 500-platelet step is
 // 24 us faster than at the 58 registers the compiler picks unbounded.
+// One edge's contributions: out[0..3] = the force on chain vertex k, i, j, l
+// (spring on i, j; bending -dE/dphi grad phi on all four); a boundary edge
+// (q.w < 0) has the spring only, out[0] = out[3] = 0.  q: indices into X.
+__device__ __forceinline__ void edge_forces(const Split& X, int4 q, float4 er, const float4* __restrict__ phi0, int e,
+                                            const mem_params& P, float3 out[4])
+{
+    const ff3 dij = X.diff(q.y, q.x);
+    const float qs = ff3_sqnorm_minus(dij, {er.x, er.y});
+    const float r = sqrtf(er.x + qs);
+    const float spring = P.k_spring * (qs / (r + er.z)) / r;
+    const float3 r3 = ff3_float(dij);
+    const float3 fs = make_float3(spring * r3.x, spring * r3.y, spring * r3.z);
+    if (q.w >= 0) {
+        float dE = 0.f;
+        const ff3 Fv = X.diff(q.z, q.x), H = X.diff(q.w, q.y);
+        if (P.k_b != 0.f) {
+            const ff3 G = ff3_neg(dij);
+            const ff3 A = ff3_cross(Fv, G), B = ff3_cross(H, G);
+            const ff x = ff3_dot(A, B);
+            const ff y = ff_mul(ff_sqrt(ff_add({er.x, er.y}, {qs, 0.f})), ff3_dot(H, A));
+            const float4 ph = phi0[e];
+            const ff num = ff_sub(ff_mul(y, {ph.x, ph.y}), ff_mul(x, {ph.z, ph.w}));
+            dE = P.k_b * ff_float(num) / sqrtf(x.h * x.h + y.h * y.h);
+        }
+        float3 g[4];
+        const float3 r1 = ff3_float(Fv), r4 = f3sub(ff3_float(H), make_float3(-r3.x, -r3.y, -r3.z));
+        torsion_grad(r1, r3, r4, g);
+        out[0] = make_float3(-dE * g[0].x, -dE * g[0].y, -dE * g[0].z);
+        out[1] = make_float3(fs.x - dE * g[1].x, fs.y - dE * g[1].y, fs.z - dE * g[1].z);
+        out[2] = make_float3(-fs.x - dE * g[2].x, -fs.y - dE * g[2].y, -fs.z - dE * g[2].z);
+        out[3] = make_float3(-dE * g[3].x, -dE * g[3].y, -dE * g[3].z);
+    } else {
+        out[0] = out[3] = make_float3(0.f, 0.f, 0.f);
+        out[1] = fs;
+        out[2] = make_float3(-fs.x, -fs.y, -fs.z);
+    }
+}
+
+// One triangle's area change S_t - S0_t (ds), its local coefficient
+// k_t (S_t - S0_t)/S0_t (tsc), the corner gradients dS_t/dX (g[0..2]), the
+// unnormalised normal e1 x e2 (nn) and 6 times the tetrahedron volume over
+// the anchor o (V6).  a, b, cc, o: indices into X.
+struct TriTerms {
+    float ds, tsc;
+    float3 g[3], nn;
+    ff V6;
+};
+__device__ __forceinline__ TriTerms tri_terms(const Split& X, int a, int b, int cc, int o, float4 r0, float4 r1,
+                                              const mem_params& P)
+{
+    TriTerms T;
+    const ff3 e1 = X.diff(b, a), e2 = X.diff(cc, a);
+    const float da = ff3_sqnorm_minus(e1, {r0.x, r0.y});
+    const float db = ff3_sqnorm_minus(e2, {r0.z, r0.w});
+    const float dc = ff3_dot_minus(e1, e2, {r1.x, r1.y});
+    const float four = da * (r0.z + db) + r0.x * db - dc * ((r1.x + dc) + r1.x);
+    const float S0 = r1.z, dS2 = 0.25f * four;
+    T.ds = dS2 / (sqrtf(S0 * S0 + dS2) + S0);
+    T.tsc = P.k_t * T.ds * r1.w;
+    const float3 f1 = ff3_float(e1), f2 = ff3_float(e2);
+    T.nn = f3cross(f1, f2);
+    const float inv = 0.5f * rsqrtf(f3dot(T.nn, T.nn));
+    const float3 nh = make_float3(T.nn.x * inv, T.nn.y * inv, T.nn.z * inv);  // nhat / 2
+    T.g[0] = f3cross(nh, f3sub(f2, f1));
+    T.g[1] = f3cross(nh, make_float3(-f2.x, -f2.y, -f2.z));
+    T.g[2] = f3cross(nh, f1);
+    T.V6 = ff3_dot(X.diff(a, o), ff3_cross(e1, e2));
+    return T;
+}
+
+// Morse force on the first node of a pair (the second takes its opposite).
+__device__ __forceinline__ float3 pair_force(const Split& X, int i, int j, float4 pr, const mem_params& P)
+{
+    const ff3 d = X.diff(j, i);
+    const float qs = ff3_sqnorm_minus(d, {pr.x, pr.y});
+    const float r = sqrtf(pr.x + qs);
+    const float ad = P.morse_a * (qs / (r + pr.z));
+    const float sc = 2.0f * P.morse_D * P.morse_a * (-expm1f(-ad)) * expf(-ad) / r;
+    const float3 R = ff3_float(d);
+    return make_float3(sc * R.x, sc * R.y, sc * R.z);
+}
+
 __device__ __forceinline__ void mem_elements(const MemCtx& c, int bx)
 {
     const int t = bx * blockDim.x + threadIdx.x;
@@ -268,75 +350,30 @@ __device__ __forceinline__ void mem_elements(const MemCtx& c, int bx)
     ff dS{0.f, 0.f}, V6{0.f, 0.f};   // per-platelet sums, double-float (no FP64 arithmetic here)
     if (t < c.ne) {
         const int4 q = c.edge[t];
-        const float4 er = c.edge_rest[t];
-        const ff3 dij = X.diff(q.y, q.x);
-        const float qs = ff3_sqnorm_minus(dij, {er.x, er.y});
-        const float r = sqrtf(er.x + qs);
-        const float spring = P.k_spring * (qs / (r + er.z)) / r;
-        const float3 r3 = ff3_float(dij);
-        const float3 fs = make_float3(spring * r3.x, spring * r3.y, spring * r3.z);
+        float3 f[4];
+        edge_forces(X, q, c.edge_rest[t], c.edge_phi0, t, P, f);
         float4* out = c.eout + 4 * (size_t)t;
         if (q.w >= 0) {
-            float dE = 0.f;
-            const ff3 Fv = X.diff(q.z, q.x), H = X.diff(q.w, q.y);
-            if (P.k_b != 0.f) {
-                const ff3 G = ff3_neg(dij);
-                const ff3 A = ff3_cross(Fv, G), B = ff3_cross(H, G);
-                const ff x = ff3_dot(A, B);
-                const ff y = ff_mul(ff_sqrt(ff_add({er.x, er.y}, {qs, 0.f})), ff3_dot(H, A));
-                const float4 ph = c.edge_phi0[t];
-                const ff num = ff_sub(ff_mul(y, {ph.x, ph.y}), ff_mul(x, {ph.z, ph.w}));
-                dE = P.k_b * ff_float(num) / sqrtf(x.h * x.h + y.h * y.h);
-            }
-            float3 g[4];
-            const float3 r1 = ff3_float(Fv), r4 = f3sub(ff3_float(H), make_float3(-r3.x, -r3.y, -r3.z));
-            torsion_grad(r1, r3, r4, g);
-            out[0] = make_float4(-dE * g[0].x, -dE * g[0].y, -dE * g[0].z, 0.f);
-            out[1] = make_float4(fs.x - dE * g[1].x, fs.y - dE * g[1].y, fs.z - dE * g[1].z, 0.f);
-            out[2] = make_float4(-fs.x - dE * g[2].x, -fs.y - dE * g[2].y, -fs.z - dE * g[2].z, 0.f);
-            out[3] = make_float4(-dE * g[3].x, -dE * g[3].y, -dE * g[3].z, 0.f);
-        } else {
-            out[1] = make_float4(fs.x, fs.y, fs.z, 0.f);
-            out[2] = make_float4(-fs.x, -fs.y, -fs.z, 0.f);
+            out[0] = make_float4(f[0].x, f[0].y, f[0].z, 0.f);
+            out[3] = make_float4(f[3].x, f[3].y, f[3].z, 0.f);
         }
+        out[1] = make_float4(f[1].x, f[1].y, f[1].z, 0.f);
+        out[2] = make_float4(f[2].x, f[2].y, f[2].z, 0.f);
     } else if (t < c.ne + c.nt) {
         const int k = t - c.ne;
-        const int a = c.tri[3 * k], b = c.tri[3 * k + 1], cc = c.tri[3 * k + 2];
         plt = c.tri_plt[k];
-        const float4 r0 = c.tri_rest[2 * k], r1 = c.tri_rest[2 * k + 1];
-        const ff3 e1 = X.diff(b, a), e2 = X.diff(cc, a);
-        const float da = ff3_sqnorm_minus(e1, {r0.x, r0.y});
-        const float db = ff3_sqnorm_minus(e2, {r0.z, r0.w});
-        const float dc = ff3_dot_minus(e1, e2, {r1.x, r1.y});
-        const float four = da * (r0.z + db) + r0.x * db - dc * ((r1.x + dc) + r1.x);
-        const float S0 = r1.z, dS2 = 0.25f * four;
-        const float ds = dS2 / (sqrtf(S0 * S0 + dS2) + S0);
-        const float tsc = P.k_t * ds * r1.w;
-        const float3 f1 = ff3_float(e1), f2 = ff3_float(e2);
-        const float3 nn = f3cross(f1, f2);
-        const float inv = 0.5f * rsqrtf(f3dot(nn, nn));
-        const float3 nh = make_float3(nn.x * inv, nn.y * inv, nn.z * inv);  // nhat / 2
-        const float3 ga = f3cross(nh, f3sub(f2, f1));
-        const float3 gb = f3cross(nh, make_float3(-f2.x, -f2.y, -f2.z));
-        const float3 gc = f3cross(nh, f1);
+        const TriTerms T = tri_terms(X, c.tri[3 * k], c.tri[3 * k + 1], c.tri[3 * k + 2], c.plt_anchor[plt],
+                                     c.tri_rest[2 * k], c.tri_rest[2 * k + 1], P);
         float4* out = c.tout + 4 * (size_t)k;
-        out[0] = make_float4(ga.x, ga.y, ga.z, tsc);
-        out[1] = make_float4(gb.x, gb.y, gb.z, tsc);
-        out[2] = make_float4(gc.x, gc.y, gc.z, tsc);
-        out[3] = make_float4(nn.x * (1.0f / 6.0f), nn.y * (1.0f / 6.0f), nn.z * (1.0f / 6.0f), 0.f);
-        V6 = ff3_dot(X.diff(a, c.plt_anchor[plt]), ff3_cross(e1, e2));
-        dS = ff{ds, 0.f};
+#pragma unroll
+        for (int r = 0; r < 3; ++r) out[r] = make_float4(T.g[r].x, T.g[r].y, T.g[r].z, T.tsc);
+        out[3] = make_float4(T.nn.x * (1.0f / 6.0f), T.nn.y * (1.0f / 6.0f), T.nn.z * (1.0f / 6.0f), 0.f);
+        V6 = T.V6;
+        dS = ff{T.ds, 0.f};
     } else if (t < c.ne + c.nt + c.np) {
         const int s = t - c.ne - c.nt;
-        const int i = c.pair[2 * s], j = c.pair[2 * s + 1];
-        const float4 pr = c.pair_rest[s];
-        const ff3 d = X.diff(j, i);
-        const float qs = ff3_sqnorm_minus(d, {pr.x, pr.y});
-        const float r = sqrtf(pr.x + qs);
-        const float ad = P.morse_a * (qs / (r + pr.z));
-        const float sc = 2.0f * P.morse_D * P.morse_a * (-expm1f(-ad)) * expf(-ad) / r;
-        const float3 R = ff3_float(d);
-        c.pout[s] = make_float4(sc * R.x, sc * R.y, sc * R.z, 0.f);
+        const float3 f = pair_force(X, c.pair[2 * s], c.pair[2 * s + 1], c.pair_rest[s], P);
+        c.pout[s] = make_float4(f.x, f.y, f.z, 0.f);
     }
     // per-platelet sums; triangles of a platelet are contiguous
     const int p0 = __shfl_sync(0xffffffffu, plt, 0);
@@ -542,6 +579,220 @@ __global__ void __launch_bounds__(128) k_mem_nodes_multi(const __grid_constant__
 
 int node_blocks(const MemCtx* c) { return (int)(((long long)c->n * kNodeLanes + 127) / 128); }
 
+// ------------------------------------------------------------------ fused pass
+// One block per platelet does all three passes for its nodes: the hi/lo
+// split of its positions (or the presplit one) goes to shared memory; a
+// first sweep over its triangles sums the area change and the volume
+// (double-float per thread, then a fixed-order block reduction), which gives
+// the platelet's global coefficients; then its edges, triangles (again, now
+// with the coefficients) and Morse pairs add their vertex forces into
+// per-node shared accumulators, and each node adds the wall term and writes
+// F once.  The accumulators are 64-bit fixed point (2^-48 force units, each
+// contribution clamped to +-256 units, far beyond any force of the model:
+// ~1e-3 at 3 % strain): integer addition is exact, so the sums do not depend
+// on the order the atomics land in, and 64-bit integer shared atomics are
+// native where FP32 shared atomics loop on compare-and-swap.  The
+// per-element arithmetic is that of the element pass (edge_forces,
+// tri_terms, pair_force).  No per-element force slots go through global
+// memory: at full scale those were ~820 MB written and read back per step.
+constexpr int kFusedThreads = 1024;
+constexpr size_t kFusedBytesPerNode = 3 * sizeof(long long) + 6 * sizeof(float);   // accumulators, hi, lo
+constexpr size_t kFusedScratch = 2 * (kFusedThreads / 32) * sizeof(ff) + 64;
+constexpr size_t kFusedMaxSmem = 227 * 1024;
+constexpr float kFixedScale = 0x1p48f, kFixedUnit = 0x1p-48f, kFixedClamp = 256.0f;
+
+__device__ __forceinline__ unsigned long long to_fixed(float f)
+{
+    return (unsigned long long)__float2ll_rn(fminf(fmaxf(f, -kFixedClamp), kFixedClamp) * kFixedScale);
+}
+__device__ __forceinline__ void fadd3(unsigned long long* acc, int nn, int u, float3 f)
+{
+    atomicAdd(acc + u, to_fixed(f.x));
+    atomicAdd(acc + nn + u, to_fixed(f.y));
+    atomicAdd(acc + 2 * nn + u, to_fixed(f.z));
+}
+__device__ __forceinline__ void fsub3(unsigned long long* acc, int nn, int u, float3 f)
+{
+    fadd3(acc, nn, u, make_float3(-f.x, -f.y, -f.z));
+}
+
+__device__ __forceinline__ void mem_fused(const MemCtx& c, const double* __restrict__ X, float* __restrict__ F,
+                                          int presplit, int p)
+{
+    extern __shared__ __align__(16) unsigned long long fsm[];
+    const int4 s0 = c.plt_span[2 * p], s1 = c.plt_span[2 * p + 1];
+    const int v0 = s0.x, nn = s0.y, e0 = s0.z, ne = s0.w, t0 = s1.x, nt = s1.y, q0 = s1.z, nq = s1.w;
+    const int n = c.n;
+    unsigned long long* acc = fsm;                       // [3][nn] fixed-point force accumulators
+    float* hx = reinterpret_cast<float*>(fsm + 3 * nn);  // [3][nn] high floats
+    float* lx = hx + 3 * nn;                             // [3][nn] low floats
+    ff* red = reinterpret_cast<ff*>(lx + 3 * nn);        // [2][warps]
+    float* cf = reinterpret_cast<float*>(red + 2 * (kFusedThreads / 32));   // the two coefficients
+    const mem_params P = c.p;
+
+    for (int u = threadIdx.x; u < nn; u += kFusedThreads) {
+        const int v = v0 + u;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float h, l;
+            if (presplit) {
+                h = c.xh[d * n + v];
+                l = c.xl[d * n + v];
+            } else {   // the split pass's arithmetic; the split also stays in xh, xl
+                const double x = X[d * n + v];
+                h = __double2float_rn(x);
+                l = __double2float_rn(x - (double)h);
+                c.xh[d * n + v] = h;
+                c.xl[d * n + v] = l;
+            }
+            hx[d * nn + u] = h;
+            lx[d * nn + u] = l;
+            acc[d * nn + u] = 0ull;
+        }
+    }
+    __syncthreads();
+    const Split Xs{hx, lx, nn};   // local node indices v - v0
+    const int o = c.plt_anchor[p] - v0;
+
+    // sweep 1: the platelet's area change and volume
+    ff dS{0.f, 0.f}, V6{0.f, 0.f};
+    for (int k = threadIdx.x; k < nt; k += kFusedThreads) {
+        const int t = t0 + k;
+        const TriTerms T = tri_terms(Xs, c.tri[3 * t] - v0, c.tri[3 * t + 1] - v0, c.tri[3 * t + 2] - v0, o,
+                                     c.tri_rest[2 * t], c.tri_rest[2 * t + 1], P);
+        dS = ff_add(dS, ff{T.ds, 0.f});
+        V6 = ff_add(V6, T.V6);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        dS = ff_add(dS, ff{__shfl_down_sync(0xffffffffu, dS.h, off), __shfl_down_sync(0xffffffffu, dS.l, off)});
+        V6 = ff_add(V6, ff{__shfl_down_sync(0xffffffffu, V6.h, off), __shfl_down_sync(0xffffffffu, V6.l, off)});
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[warp] = dS;
+        red[kFusedThreads / 32 + warp] = V6;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, V = 0.0;
+        for (int w = 0; w < kFusedThreads / 32; ++w) {
+            S += (double)red[w].h + (double)red[w].l;
+            V += (double)red[kFusedThreads / 32 + w].h + (double)red[kFusedThreads / 32 + w].l;
+        }
+        V *= 1.0 / 6.0;
+        const double* pr = c.plt_rest + 4 * p;  // S0, V0, 1/S0, 1/V0
+        const float2 k2 = make_float2((float)((double)P.k_s * S * pr[2]), (float)((double)P.k_v * (V - pr[1]) * pr[3]));
+        c.acc[2 * p] = S;
+        c.acc[2 * p + 1] = V;
+        c.coef[p] = k2;
+        cf[0] = k2.x;
+        cf[1] = k2.y;
+    }
+    __syncthreads();
+    const float cSg = cf[0], cV = cf[1];
+
+    // sweep 2: vertex forces into the accumulators
+    for (int k = threadIdx.x; k < ne; k += kFusedThreads) {
+        const int e = e0 + k;
+        int4 q = c.edge[e];
+        q.x -= v0;
+        q.y -= v0;
+        float3 f[4];
+        if (q.w >= 0) {
+            q.z -= v0;
+            q.w -= v0;
+        }
+        edge_forces(Xs, q, c.edge_rest[e], c.edge_phi0, e, P, f);
+        fadd3(acc, nn, q.x, f[1]);
+        fadd3(acc, nn, q.y, f[2]);
+        if (q.w >= 0) {
+            fadd3(acc, nn, q.z, f[0]);
+            fadd3(acc, nn, q.w, f[3]);
+        }
+    }
+    // Eq. 4-5: F -= (k_t (S_t - S0_t)/S0_t + k_s (S - S0)/S0) dS_t/dX + k_v (V - V0)/V0 dV/dX
+    for (int k = threadIdx.x; k < nt; k += kFusedThreads) {
+        const int t = t0 + k;
+        const int a = c.tri[3 * t] - v0, b = c.tri[3 * t + 1] - v0, cc = c.tri[3 * t + 2] - v0;
+        const TriTerms T = tri_terms(Xs, a, b, cc, o, c.tri_rest[2 * t], c.tri_rest[2 * t + 1], P);
+        const float cS = T.tsc + cSg;
+        const float3 n6 = make_float3(T.nn.x * (1.0f / 6.0f), T.nn.y * (1.0f / 6.0f), T.nn.z * (1.0f / 6.0f));
+        const int corner[3] = {a, b, cc};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            fsub3(acc, nn, corner[r],
+                  make_float3(cS * T.g[r].x + cV * n6.x, cS * T.g[r].y + cV * n6.y, cS * T.g[r].z + cV * n6.z));
+    }
+    for (int k = threadIdx.x; k < nq; k += kFusedThreads) {
+        const int s = q0 + k;
+        const int i = c.pair[2 * s] - v0, j = c.pair[2 * s + 1] - v0;
+        const float3 f = pair_force(Xs, i, j, c.pair_rest[s], P);
+        fadd3(acc, nn, i, f);
+        fsub3(acc, nn, j, f);
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < nn; u += kFusedThreads) {
+        const int v = v0 + u;
+        float fz = __ll2float_rn((long long)acc[2 * nn + u]) * kFixedUnit;
+        if (c.is_mem[v] && P.rep_F0 != 0.f) {   // wall repulsion on surface nodes (Section 3.4.1)
+            const float eps = fmaxf((hx[2 * nn + u] - P.z_wall) + lx[2 * nn + u], P.rep_eps_min);
+            fz += P.rep_F0 * P.rep_tau / expm1f(P.rep_tau * eps);
+        }
+        F[v] = __ll2float_rn((long long)acc[u]) * kFixedUnit;
+        F[n + v] = __ll2float_rn((long long)acc[nn + u]) * kFixedUnit;
+        F[2 * n + v] = fz;
+    }
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mem_fused(const __grid_constant__ MemCtx c,
+                                                               const double* __restrict__ X, float* __restrict__ F,
+                                                               int presplit)
+{
+    pdl_wait();
+    mem_fused(c, X, F, presplit, blockIdx.x);
+}
+
+// The fused pass over several chambers' platelets, one launch (see Multi):
+// entry e owns one block per platelet of its chamber.
+struct FusedArgs {
+    MemCtx c;
+    const double* X;
+    float* F;
+};
+static_assert(sizeof(Multi<FusedArgs>) <= 32000, "the list must fit the kernel parameter space");
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_mem_fused_multi(const __grid_constant__ Multi<FusedArgs> t)
+{
+    pdl_wait();
+    const int e = multi_entry(t, blockIdx.x);
+    mem_fused(t.a[e].c, t.a[e].X, t.a[e].F, 0, blockIdx.x - t.first[e]);
+}
+
+size_t fused_smem(const MemCtx* c) { return (size_t)c->span_max_nodes * kFusedBytesPerNode + kFusedScratch; }
+
+// The fused pass runs when path 1 asks for it, for the plain membrane
+// (springs and bending included) of a mesh that groups its elements by
+// platelet.  It is not the default: at full scale it takes as long as the
+// three passes (533 against 461 us; 463 with FP32 shared atomics, whose
+// order is not fixed), because the double-float element arithmetic, not
+// the slot traffic, bounds both; a block per platelet also leaves a
+// 10-platelet channel on ten SMs (131 against 18 us).  Its sums are exact,
+// so its forces do not depend on scheduling.
+bool uses_fused(const MemCtx* c) { return c->plt_span && !c->skip_edges && c->path == 1; }
+
+int fused_prepare()
+{
+    int rc = check_cuda(cudaFuncSetAttribute(k_mem_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kFusedMaxSmem),
+                        "membrane: fused pass shared memory");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_mem_fused_multi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kFusedMaxSmem),
+                        "membrane: fused pass shared memory");
+    return rc;
+}
+
 int launch_scalars(MemCtx* c, const double* X, cudaStream_t s, bool presplit = false)
 {
     int rc = PFSI_OK;
@@ -568,6 +819,10 @@ int launch_scalars(MemCtx* c, const double* X, cudaStream_t s, bool presplit = f
 
 int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
 {
+    if (uses_fused(c))
+        return check_cuda(launch_pdl(k_mem_fused, dim3(c->nplt), dim3(kFusedThreads), fused_smem(c), s, *c, X, F,
+                                     presplit ? 1 : 0),
+                          "membrane_forces: fused pass");
     int rc = launch_scalars(c, X, s, presplit);
     if (rc) return rc;
     return check_cuda(launch_pdl(k_mem_nodes, dim3(node_blocks(c)), dim3(128), 0, s, F, *c),
@@ -590,8 +845,17 @@ int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)
     std::vector<Multi<SplitArgs>> split;
     std::vector<Multi<MemCtx>> elems, coef;
     std::vector<Multi<NodesArgs>> nodes;
+    std::vector<Multi<FusedArgs>> fused;
+    std::vector<size_t> fused_bytes;
     for (int i = 0; i < n; ++i) {
         MemCtx* c = ch[i].mem;
+        if (uses_fused(c)) {
+            const bool fresh = fused.empty() || fused.back().full();
+            multi_push(fused, FusedArgs{*c, ch[i].X, ch[i].F}, c->nplt);
+            if (fresh) fused_bytes.push_back(0);
+            fused_bytes.back() = std::max(fused_bytes.back(), fused_smem(c));
+            continue;
+        }
         const int nsplit = 3 * c->n > 2 * c->nplt ? 3 * c->n : 2 * c->nplt;
         multi_push(split, SplitArgs{ch[i].X, c->n, c->xh, c->xl, c->acc, 2 * c->nplt}, (nsplit + 255) / 256);
         multi_push(elems, *c, (c->ne + c->nt + c->np + 255) / 256);
@@ -608,6 +872,10 @@ int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)
         if (!rc) rc = check_cuda(launch_pdl(k_mem_coef_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: coef");
     for (const auto& t : nodes)
         if (!rc) rc = check_cuda(launch_pdl(k_mem_nodes_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: nodes");
+    for (size_t u = 0; u < fused.size() && !rc; ++u)
+        rc = check_cuda(launch_pdl(k_mem_fused_multi, dim3(fused[u].blocks()), dim3(kFusedThreads), fused_bytes[u], s,
+                                   fused[u]),
+                        "membrane: fused pass");
     return rc;
 }
 
@@ -795,6 +1063,46 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
         if (runs != nplt)
             return set_error(PFSI_ERR_ARG, "membrane_create: the nodes of each platelet must be contiguous");
     }
+    // per-platelet spans of nodes, edges, triangles and Morse pairs for the
+    // fused pass: usable when each platelet's elements are one run and its
+    // positions and force accumulators fit in shared memory
+    std::vector<int4> span(2 * (size_t)nplt, make_int4(0, 0, 0, 0));
+    bool spans_ok = true;
+    int span_max = 0;
+    {
+        // (first, count) of each platelet's run of elements into dst[2 q + at].z, .w
+        auto runs_of = [&](int count, auto owner, int4* dst, int at) {
+            std::vector<int> seen(nplt, 0);
+            for (int e = 0; e < count;) {
+                const int q = owner(e);
+                int f = e + 1;
+                while (f < count && owner(f) == q) ++f;
+                if (seen[q]) spans_ok = false;   // a platelet's elements in two runs
+                seen[q] = 1;
+                dst[2 * q + at].z = e;
+                dst[2 * q + at].w = f - e;
+                e = f;
+            }
+        };
+        for (int v = 0; v < n;) {
+            int f = v + 1;
+            while (f < n && node_plt[f] == node_plt[v]) ++f;
+            span[2 * node_plt[v]].x = v;
+            span[2 * node_plt[v]].y = f - v;
+            span_max = std::max(span_max, f - v);
+            v = f;
+        }
+        runs_of(ne, [&](int e) { return node_plt[T.edge[e].x]; }, span.data(), 0);
+        std::vector<int4> tp(2 * (size_t)nplt, make_int4(0, 0, 0, 0));
+        runs_of(nt, [&](int t) { return node_plt[tri[3 * t]]; }, tp.data(), 0);
+        runs_of(np, [&](int s) { return node_plt[pairs[2 * s]]; }, tp.data(), 1);
+        for (int q = 0; q < nplt; ++q) {
+            span[2 * q + 1] = make_int4(tp[2 * q].z, tp[2 * q].w, tp[2 * q + 1].z, tp[2 * q + 1].w);
+        }
+        for (int s = 0; s < np && spans_ok; ++s)
+            if (node_plt[pairs[2 * s]] != node_plt[pairs[2 * s + 1]]) spans_ok = false;
+        if ((size_t)span_max * kFusedBytesPerNode + kFusedScratch > kFusedMaxSmem) spans_ok = false;
+    }
 
     char* base = static_cast<char*>(ws);
     auto up = [&](int slice, const void* src, size_t bytes) -> int {
@@ -824,6 +1132,8 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     if (!rc) rc = up(S_PERM, perm.data(), sizeof(int) * perm.size());
     if (!rc) rc = up(S_PLT_RANGE, plt_range.data(), sizeof(int2) * plt_range.size());
     if (!rc) rc = up(S_PLT_CHUNKS, plt_chunks.data(), sizeof(int2) * plt_chunks.size());
+    if (!rc) rc = up(S_PLT_SPAN, span.data(), sizeof(int4) * span.size());
+    if (!rc && spans_ok) rc = fused_prepare();
     if (rc) return rc;
 
     mem_ctx* c = new mem_ctx();
@@ -865,7 +1175,24 @@ extern "C" int membrane_create(const mem_params* p, int n, int nt, const int* tr
     c->eout = reinterpret_cast<float4*>(at(S_EOUT));
     c->tout = reinterpret_cast<float4*>(at(S_TOUT));
     c->pout = reinterpret_cast<float4*>(at(S_POUT));
+    c->plt_span = spans_ok ? reinterpret_cast<const int4*>(at(S_PLT_SPAN)) : nullptr;
+    c->span_max_nodes = span_max;
+    c->path = 0;
     *out = c;
+    return PFSI_OK;
+}
+
+extern "C" int membrane_set_path(mem_ctx* c, int path)
+{
+    if (!c || path < 0 || path > 1) return set_error(PFSI_ERR_ARG, "membrane_set_path: bad argument");
+    c->path = path;
+    return PFSI_OK;
+}
+
+extern "C" int membrane_get_path(const mem_ctx* c, int* fused)
+{
+    if (!c || !fused) return set_error(PFSI_ERR_ARG, "membrane_get_path: null argument");
+    *fused = uses_fused(c) ? 1 : 0;
     return PFSI_OK;
 }
 

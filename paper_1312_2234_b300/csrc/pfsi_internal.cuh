@@ -325,6 +325,12 @@ struct MemCtx {
     int n_chunks;
     int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
     const int* plt_anchor; // [nplt]
+    // per platelet (first node, nodes, first edge, edges), (first triangle,
+    // triangles, first Morse pair, pairs) for the fused pass, or null when
+    // the mesh does not group its elements by platelet
+    const int4* plt_span;  // [2*nplt]
+    int span_max_nodes;    // nodes of the largest platelet
+    int path;              // 0: the three passes, 1: the fused pass where it applies
     // scratch, rewritten by every call
     double* acc;           // [2*nplt] sum of (S_t - S0_t), sum of tetrahedron volumes
     float2* coef;          // [nplt] k_s (S - S0)/S0, k_v (V - V0)/V0

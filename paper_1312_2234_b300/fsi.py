@@ -84,6 +84,8 @@ _SIGS = {
     "membrane_destroy": [P],
     "membrane_set_params": [P, ctypes.POINTER(mem_params)],
     "membrane_forces": [P, P, P, P],
+    "membrane_set_path": [P, c_int],
+    "membrane_get_path": [P, ctypes.POINTER(c_int)],
     "membrane_measure": [P, P, ctypes.POINTER(c_double), P],
     "membrane_measure_static": [P, P, ctypes.POINTER(c_double), P],
     "membrane_centroids": [P, P, P, P],
@@ -509,6 +511,17 @@ class Membrane:
 
     def forces(self, X, F):
         membrane_forces(self.h, X, F)
+
+    def set_path(self, path):
+        """0: the three passes through per-element slots (default); 1: the
+        fused per-platelet pass with exact fixed-point sums, where it applies."""
+        _call("membrane_set_path", self.h, int(path))
+
+    @property
+    def fused(self):
+        v = c_int()
+        _call("membrane_get_path", self.h, ctypes.byref(v))
+        return bool(v.value)
 
     def measure(self, X):
         return membrane_measure(self.h, X, self.n_plt)

@@ -37,8 +37,10 @@ def deformed(w, strain, seed):
     return np.ascontiguousarray(X).ravel()
 
 
-def setup(w, params):
+def setup(w, params, path=0):
     mem = fsi.Membrane(params, w["mesh"])
+    mem.set_path(path)
+    assert mem.fused == (path == 1)
     om = oracle.Mesh(w["mesh"]["X0"], w["mesh"]["tri"], w["mesh"]["pairs"], w["mesh"]["node_plt"],
                      w["mesh"]["is_membrane"], w["mesh"]["n_plt"])
     return mem, om
@@ -62,14 +64,16 @@ def small_workload():
                           gap=0.02, centers=[(16.0, 16.0, -0.5 + 0.02 + 1.25)])
 
 
+# path 0: the three passes through slots; 1: the fused per-platelet pass
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("term", TERMS)
-def test_each_term(term):
+def test_each_term(term, path):
     w = small_workload()
     base = f32(w["membrane"])
     params = dict(base, **{k: 0.0 for k in OFF})
     for k in ONLY[term]:
         params[k] = base[k]
-    mem, om = setup(w, params)
+    mem, om = setup(w, params, path)
     X = deformed(w, 0.03, 5)
     F = gpu_forces(mem, X)
     Fo = om.forces(params, X)
@@ -77,11 +81,12 @@ def test_each_term(term):
     assert rel_err(F, Fo) < 1e-5, term
 
 
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("which", ["small", "channel"])
-def test_total_force_and_measure(which):
+def test_total_force_and_measure(which, path):
     w = small_workload() if which == "small" else workload.config_channel()
     params = f32(w["membrane"])
-    mem, om = setup(w, params)
+    mem, om = setup(w, params, path)
     X = deformed(w, 0.02, 6)
     assert rel_err(gpu_forces(mem, X), om.forces(params, X)) < 1e-5
     SV = mem.measure(torch.from_numpy(X).cuda())
@@ -90,10 +95,41 @@ def test_total_force_and_measure(which):
     assert np.allclose(SV[:, 1], V, rtol=1e-6)
 
 
-def test_rest_shape_force_free():
+@pytest.mark.parametrize("path", [0, 1])
+def test_rest_shape_force_free(path):
     w = workload.build(32, 32, 64, 0.8, 100.0, 1, 3, 200, 100, 0, orient="random", gap=3.0)
     params = dict(f32(w["membrane"]), rep_F0=0.0)
-    mem, _ = setup(w, params)
+    mem, _ = setup(w, params, path)
     F0 = gpu_forces(mem, w["X"])
     F1 = gpu_forces(mem, deformed(w, 0.01, 1))
     assert np.max(np.abs(F0)) < 1e-4 * np.max(np.abs(F1))
+
+
+def test_fused_pass_falls_back_when_elements_are_not_grouped():
+    """A mesh whose Morse pairs of one platelet come in two runs (or whose
+    platelets exceed the shared memory) runs the three passes even with
+    path 1; the forces still match the oracle, and the two paths agree on
+    the grouped mesh to FP32 summation order (1e-6 of the largest force);
+    the fused pass's exact sums give the same bits on a repeated call."""
+    w = workload.config_channel()
+    params = f32(w["membrane"])
+    X = deformed(w, 0.02, 7)
+    fused, _ = setup(w, params, 1)
+    three, om = setup(w, params, 0)
+    assert np.array_equal(gpu_forces(fused, X), gpu_forces(fused, X))
+    Fo = om.forces(params, X)
+    assert rel_err(gpu_forces(fused, X), gpu_forces(three, X)) < 1e-6
+    mesh = dict(w["mesh"])
+    pairs = np.asarray(mesh["pairs"]).reshape(-1, 2)
+    n_first = int(np.sum(np.asarray(mesh["node_plt"])[pairs[:, 0]] == 0))
+    assert n_first > 2
+    order = np.r_[np.arange(1, n_first, 2), np.arange(n_first, len(pairs)), np.arange(0, n_first, 2)]
+    mesh["pairs"] = pairs[order]
+    mem = fsi.Membrane(params, mesh)
+    mem.set_path(1)
+    assert not mem.fused
+    assert rel_err(gpu_forces(mem, X), Fo) < 1e-5
+    big = workload.build(64, 64, 64, 0.8, 100.0, 1, 5, 0, 0, 0, orient="flat", gap=3.0)
+    big_mem = fsi.Membrane(f32(big["membrane"]), big["mesh"])
+    big_mem.set_path(1)
+    assert not big_mem.fused
