@@ -152,11 +152,14 @@ int lb_step(lb_ctx* ctx, int nsteps, void* stream);
  * on it: every shape runs the same per-cell operation sequence and gives
  * bit-identical populations).  FP32 storage: threads per block along x,
  * shape 0..3 = 128, 32, 64, 256 (capped at nx rounded up to 32).  Mixed
- * storage: the (x, y) column tile of the marching kernels; shape 0, 1 = the
- * pair kernel (a thread takes two x-adjacent cells, packed FP32x2
- * arithmetic) with 64x4, 64x8 columns; 2 = the one-cell kernel with 32x8
- * columns; 3 = the TMA-staged kernel with 32x8 columns when nx is a
- * multiple of 8, else the one-cell kernel with 32x4.  Default 0. */
+ * storage: the kernel and (x, y) column tile of the marching kernels.  nx a
+ * multiple of 8: shape 0 = the staged pair kernel (a thread takes two
+ * x-adjacent cells, packed FP32x2 arithmetic, each interior plane's 16-bit
+ * values copied to shared memory by cp.async) with 64x4 columns, 1 = the
+ * pair kernel (global pulls) with 64x4, 2 = the one-cell kernel with 32x8,
+ * 3 = the TMA-staged kernel with 32x8 (the one-cell kernel with 32x4 where
+ * the driver lacks TMA encoding).  Otherwise: 0, 1 = the pair kernel with
+ * 64x4, 64x8; 2, 3 = the one-cell kernel with 32x8, 32x4.  Default 0. */
 #define PFSI_LB_SHAPES 4
 int lb_set_shape(lb_ctx* ctx, int shape);
 int lb_get_shape(const lb_ctx* ctx, int* shape);

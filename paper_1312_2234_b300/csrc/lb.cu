@@ -461,16 +461,15 @@ __device__ __forceinline__ float2 cdot2(float2 x, float2 y, float2 z)
 }
 
 // f*neq of direction q that the two cells of plane k pull, as floats
-// (bounce-back: the own cells' opposite slot).  wall: 0 an interior plane,
-// 1 the bottom plane (k = 0), 2 the top plane (k = nz - 1).  kWord: the two
+// (bounce-back at k = 0 and nz - 1: the own cells' opposite slot).  kWord: the two
 // values along x sit in one aligned 32-bit word (even nx; i1 = i0 + 1 in
 // the same row).
 template <int kMode, int q, bool kWord>
-__device__ __forceinline__ float2 pull_pair(const uint16_t* __restrict__ nin, int N, int k, int nx, int ny, int j,
-                                            int ym, int yp, int i0, int i1, int xm0, int xm1, int xp0, int xp1,
-                                            float inv_scale, int wall)
+__device__ __forceinline__ float2 pull_pair(const uint16_t* __restrict__ nin, int N, int k, int nz, int nx, int ny,
+                                            int j, int ym, int yp, int i0, int i1, int xm0, int xm1, int xp0,
+                                            int xp1, float inv_scale)
 {
-    const bool bounce = (czq(q) == 1 && wall == 1) || (czq(q) == -1 && wall == 2);
+    const bool bounce = (czq(q) == 1 && k == 0) || (czq(q) == -1 && k == nz - 1);
     const int sy = cyq(q) == 1 ? ym : (cyq(q) == -1 ? yp : j);
     const uint16_t* row = bounce ? nin + nslot(oppq(q)) * N + (k * ny + j) * nx
                                  : nin + nslot(q) * N + ((k - czq(q)) * ny + sy) * nx;
@@ -492,13 +491,13 @@ __device__ __forceinline__ float2 pull_pair(const uint16_t* __restrict__ nin, in
 
 // F += E_q of the source cells (as add_feq, both cells: own, own + 1)
 template <int q, class T>
-__device__ __forceinline__ void add_feq2(float2& F, const Ring<T>& ring, int sm, int s0, int sp, int own, float3 utop,
-                                         int wall)
+__device__ __forceinline__ void add_feq2(float2& F, const Ring<T>& ring, int sm, int s0, int sp, int own, int k,
+                                         int nz, float3 utop)
 {
-    if (czq(q) == 1 && wall == 1) {
+    if (czq(q) == 1 && k == 0) {
         const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
         F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)), F);
-    } else if (czq(q) == -1 && wall == 2) {
+    } else if (czq(q) == -1 && k == nz - 1) {
         const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
         const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
         F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)),
@@ -516,13 +515,54 @@ __device__ __forceinline__ void add_feq2(float2& F, const Ring<T>& ring, int sm,
 
 template <int kMode, bool kWord, class T, int... Q>
 __device__ __forceinline__ void pull_all2(std::integer_sequence<int, Q...>, float2* F, const uint16_t* __restrict__ nin,
-                                          int N, int k, int nx, int ny, int j, int ym, int yp, int i0, int i1,
-                                          int xm0, int xm1, int xp0, int xp1, float inv_scale, const Ring<T>& ring,
-                                          int sm, int s0, int sp, int own, float3 utop, int wall)
+                                          int N, int k, int nz, int nx, int ny, int j, int ym, int yp, int i0,
+                                          int i1, int xm0, int xm1, int xp0, int xp1, float inv_scale,
+                                          const Ring<T>& ring, int sm, int s0, int sp, int own, float3 utop)
 {
-    ((F[Q] = pull_pair<kMode, Q, kWord>(nin, N, k, nx, ny, j, ym, yp, i0, i1, xm0, xm1, xp0, xp1, inv_scale, wall)),
+    ((F[Q] = pull_pair<kMode, Q, kWord>(nin, N, k, nz, nx, ny, j, ym, yp, i0, i1, xm0, xm1, xp0, xp1, inv_scale)),
      ...);
-    (add_feq2<Q, T>(F[Q], ring, sm, s0, sp, own, utop, wall), ...);
+    (add_feq2<Q, T>(F[Q], ring, sm, s0, sp, own, k, nz, utop), ...);
+}
+
+// Staged windows of the 16-bit values (k_lb_step_staged): per slot (slot
+// order) the TY source rows of its direction (y0 - c_y .. y0 - c_y + TY - 1,
+// wrapped) of kWinX values starting 8 cells left of the column
+// (x0 - 8 .. x0 + 71, wrapped per 16-byte chunk).
+constexpr int kWinX = 80;
+constexpr int kWinChunks = kWinX / 8;
+
+// f*neq of direction q that the two cells pull on an interior plane, from
+// the window: the cells' sources sit at row ty, values 8 + 2 tx - c_x and
+// 9 + 2 tx - c_x of the direction's slot (win already points at row ty,
+// value 2 tx).
+template <int kMode, int q, int TY>
+__device__ __forceinline__ float2 pull_staged(const uint16_t* __restrict__ win, float inv_scale)
+{
+    const uint16_t* p = win + nslot(q) * TY * kWinX + 8 - cxq(q);
+    uint32_t r0, r1;
+    if (cxq(q) == 0) {   // an aligned word
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(p);
+        if constexpr (kMode == PFSI_LB_BF16)
+            return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+        r0 = w & 0xffffu;
+        r1 = w >> 16;
+    } else {
+        r0 = p[0];
+        r1 = p[1];
+    }
+    if constexpr (kMode == PFSI_LB_BF16) return make_float2(__uint_as_float(r0 << 16), __uint_as_float(r1 << 16));
+    return mul2(make_float2(__half2float(__ushort_as_half((unsigned short)r0)),
+                            __half2float(__ushort_as_half((unsigned short)r1))),
+                dup2(inv_scale));
+}
+
+template <int kMode, class T, int... Q>
+__device__ __forceinline__ void pull_all_staged(std::integer_sequence<int, Q...>, float2* F,
+                                                const uint16_t* __restrict__ win, float inv_scale,
+                                                const Ring<T>& ring, int sm, int s0, int sp, int own, float3 utop)
+{
+    ((F[Q] = pull_staged<kMode, Q, T::TY>(win, inv_scale)), ...);
+    (add_feq2<Q, T>(F[Q], ring, sm, s0, sp, own, 1, 3, utop), ...);   // an interior plane
 }
 
 // Stores the two cells' values of one slot (a 32-bit word when kWord).
@@ -578,31 +618,38 @@ __device__ __forceinline__ void store_pairs2(std::integer_sequence<int, Q...>, t
 }
 
 // One plane k of the pair kernel's column (both cells live or the second
-// repeating the first); wall as pull_pair.  (With the wall a template
-// argument, one body per kind of plane, the compiler hoists the interior
-// body's loads and spills some 700 bytes a thread.)
-template <int kMode, bool kWord, class T>
+// repeating the first); the walls are the planes k = 0 and nz - 1.  (With
+// the wall a template argument, one body per kind of plane, the compiler
+// hoists the interior body's loads and spills some 700 bytes a thread;
+// passed as a wall code computed from k it made the kernel half again
+// slower.)  kStaged: an interior plane pulled from the staged window.
+template <int kMode, bool kWord, class T, bool kStaged = false>
 __device__ __forceinline__ void pair_plane(const Ring<T>& ring, const uint16_t* __restrict__ nin,
                                            typename Neq<kMode>::T* __restrict__ nout, float4* __restrict__ mout,
                                            float4* __restrict__ g, const uint32_t* __restrict__ flags, int N, int nx,
                                            int ny, int k, int j, int ym, int yp, int i0, int i1, bool live1, int xm0,
                                            int xm1, int xp0, int xp1, int own, float omega, float keep, float guo,
                                            float3 F3b, float3 utop, float inv_scale, float scale, int onsite,
-                                           int wall)
+                                           int nz, const uint16_t* __restrict__ win = nullptr)
 {
     const int row = k * ny + j;
     const int base = row * nx;   // the cells are base + i0, base + i1
     float2 F[19];
-    pull_all2<kMode, kWord, T>(std::make_integer_sequence<int, 19>{}, F, nin, N, k, nx, ny, j, ym, yp, i0, i1, xm0,
-                               xm1, xp0, xp1, inv_scale, ring, (k + 3) & 3, k & 3, (k + 1) & 3, own, utop, wall);
-    if (wall != 0 && onsite) {
+    if constexpr (kStaged)   // an interior plane (wall == 0), pulled from the staged window
+        pull_all_staged<kMode, T>(std::make_integer_sequence<int, 19>{}, F, win, inv_scale, ring, (k + 3) & 3, k & 3,
+                                  (k + 1) & 3, own, utop);
+    else
+        pull_all2<kMode, kWord, T>(std::make_integer_sequence<int, 19>{}, F, nin, N, k, nz, nx, ny, j, ym, yp, i0,
+                                   i1, xm0, xm1, xp0, xp1, inv_scale, ring, (k + 3) & 3, k & 3, (k + 1) & 3, own,
+                                   utop);
+    if (onsite && (k == 0 || k == nz - 1)) {
         float fa[19], fb[19];
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
             fa[q] = F[q].x;
             fb[q] = F[q].y;
         }
-        if (wall == 1) {
+        if (k == 0) {
             onsite_wall<1>(fa, make_float3(0.f, 0.f, 0.f));
             onsite_wall<1>(fb, make_float3(0.f, 0.f, 0.f));
         } else {
@@ -708,7 +755,7 @@ __device__ __forceinline__ void mixed_pair_column(Ring<T>& ring, const uint16_t*
         if (live0)
             pair_plane<kMode, kWord, T>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1, live1, xm0,
                                         xm1, xp0, xp1, own, omega, keep, guo, F3b, utop, inv_scale, scale, onsite,
-                                        k == 0 ? 1 : (k == nz - 1 ? 2 : 0));
+                                        nz);
         if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
         __syncthreads();
     }
@@ -728,6 +775,153 @@ __global__ void __launch_bounds__(T::Threads, 512 / T::Threads) k_lb_step_pair(
     mixed_pair_column<kMode, kWord, T>(ring, nin, nout, min_, mout, g, flags, nx, ny, nz, blockIdx.x * T::TX,
                                        blockIdx.y * T::TY, z0, min(z0 + kz, nz), omega, guo, body, utop, inv_scale,
                                        onsite);
+}
+
+// Staged pair kernel (nx a multiple of 8): the pair kernel's column with the
+// 16-bit values of each interior plane copied to shared memory first.  The
+// window of plane k + 1 (slots with c_z = 0 from plane k + 1, c_z = +1 from
+// k, c_z = -1 from k + 2; each slot the TY rows its direction pulls from) is
+// copied with cp.async (16-byte chunks, wrapped periodically per chunk in x
+// and per row in y) while plane k computes, so
+// the pulls become shared-memory loads at compile-time offsets and the
+// per-direction address arithmetic and wall selects of the global pulls go
+// away.  The two wall planes take the global pulls (bounce-back).  Every
+// lane runs the operation sequence of mixed_column.
+template <int TY>
+__host__ __device__ constexpr int staged_copies()
+{
+    return 19 * TY * kWinChunks;
+}
+template <class T>
+__host__ __device__ constexpr size_t staged_smem()
+{
+    return sizeof(Ring<T>) + 2 * (size_t)staged_copies<T::TY>() * 16;   // ring, two windows
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int kMode, class T>
+__device__ __forceinline__ void mixed_staged_column(char* smem, const uint16_t* __restrict__ nin,
+                                                    typename Neq<kMode>::T* __restrict__ nout,
+                                                    const float4* __restrict__ min_, float4* __restrict__ mout,
+                                                    float4* __restrict__ g, const uint32_t* __restrict__ flags,
+                                                    int nx, int ny, int nz, int x0, int y0, int z0, int z1,
+                                                    float omega, float guo, float3 body, float3 utop,
+                                                    float inv_scale, int onsite)
+{
+    Ring<T>& ring = *reinterpret_cast<Ring<T>*>(smem);
+    uint16_t* winbuf = reinterpret_cast<uint16_t*>(smem + sizeof(Ring<T>));
+    constexpr int kCopies = (staged_copies<T::TY>() + T::Threads - 1) / T::Threads;
+    constexpr int kWinElems = staged_copies<T::TY>() * 8;   // values per buffer
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int j = y0 + ty;
+    const int i0 = x0 + 2 * tx;
+    const bool live0 = i0 < nx && j < ny;
+    const bool live1 = live0;   // nx even: i0 + 1 < nx whenever i0 < nx
+    const int i1 = i0 + 1;
+    const int N = nx * ny * nz;
+    const int plane_cells = nx * ny;
+    const int xm0 = (i0 == 0) ? nx - 1 : i0 - 1, xm1 = i0;
+    const int xp0 = i1, xp1 = (i1 >= nx - 1) ? 0 : i1 + 1;
+    const int ym = (j == 0) ? ny - 1 : j - 1;
+    const int yp = (j >= ny - 1) ? 0 : j + 1;
+    const float keep = 1.0f - omega;
+    const float scale = 1.0f / inv_scale;
+    const int own = (ty + 1) * T::HX + 2 * tx + 1;
+
+    // this thread's window chunks: value offsets without the plane term
+    // (copy u = threadIdx.x + m Threads is slot s, row r, chunk c; the
+    // chunks of a buffer are laid out in u order)
+    int coff[kCopies];
+    const int cx0 = (x0 >> 3) - 1, nchunk = nx >> 3;
+#pragma unroll
+    for (int m = 0; m < kCopies; ++m) {
+        const int u = threadIdx.x + m * T::Threads;
+        const int sl = u / (T::TY * kWinChunks), rc = u - sl * T::TY * kWinChunks;
+        const int r = rc / kWinChunks, c = rc - r * kWinChunks;
+        int cy = 0;   // c_y of the slot's direction
+#pragma unroll
+        for (int q = 0; q < 19; ++q)
+            if (nslot(q) == sl) cy = cyq(q);
+        int gy = y0 - cy + r;
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        int gc = cx0 + c;
+        gc = gc < 0 ? gc + nchunk : (gc >= nchunk ? gc % nchunk : gc);
+        const int dz = sl < 9 ? 0 : (sl < 14 ? -1 : 1);   // slot groups c_z = 0, +1, -1
+        coff[m] = u < staged_copies<T::TY>() ? sl * N + dz * plane_cells + gy * nx + gc * 8 : -1;
+    }
+    // copies of the window of plane kk (interior) into buffer b
+    auto stage = [&](int kk, int b) {
+        uint16_t* dst = winbuf + b * kWinElems;
+#pragma unroll
+        for (int m = 0; m < kCopies; ++m)
+            if (coff[m] >= 0)
+                cp_async16(dst + (threadIdx.x + m * T::Threads) * 8, nin + coff[m] + kk * plane_cells);
+        cp_async_commit();
+    };
+    const bool interior0 = z0 > 0 && z0 < nz - 1;
+    if (interior0) stage(z0, z0 & 1);
+
+    int off[T::Halo];
+#pragma unroll
+    for (int u = 0; u < T::Halo; ++u) {
+        const int h = threadIdx.x + u * T::Threads;
+        const int hy = h / T::HX, hx = h - hy * T::HX;
+        int gx = x0 + hx - 1, gy = y0 + hy - 1;
+        gx = gx < 0 ? gx + nx : (gx >= nx ? gx % nx : gx);
+        gy = gy < 0 ? gy + ny : (gy >= ny ? gy % ny : gy);
+        off[u] = h < T::Plane ? gy * nx + gx : -1;
+    }
+    float4 r[T::Halo];
+    for (int p = max(z0 - 1, 0); p <= min(z0 + 1, nz - 1); ++p) {
+        halo_load<T>(min_, p, plane_cells, off, r);
+        halo_store<T>(ring, p & 3, r);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
+    for (int k = z0; k < z1; ++k) {
+        // the next plane's window: its buffer was last read by plane k - 1,
+        // which every thread has finished (barrier at the end of k - 1)
+        if (k + 1 < z1 && k + 1 < nz - 1) stage(k + 1, (k + 1) & 1);
+        const bool pre = k + 2 < nz && k + 2 <= z1;
+        if (pre) halo_load<T>(min_, k + 2, plane_cells, off, r);
+        if (live0) {
+            if (k != 0 && k != nz - 1)
+                pair_plane<kMode, true, T, true>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1,
+                                                 live1, xm0, xm1, xp0, xp1, own, omega, keep, guo, F3b, utop,
+                                                 inv_scale, scale, 0, 3,
+                                                 winbuf + (k & 1) * kWinElems + ty * kWinX + 2 * tx);
+            else
+                pair_plane<kMode, true, T>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1, live1,
+                                           xm0, xm1, xp0, xp1, own, omega, keep, guo, F3b, utop, inv_scale, scale,
+                                           onsite, nz);
+        }
+        if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
+        cp_async_wait_all();   // the next plane's window has landed (this thread's copies)
+        __syncthreads();       // ... and everyone's
+    }
+}
+
+template <int kMode, class T>
+__global__ void __launch_bounds__(T::Threads, 512 / T::Threads) k_lb_step_staged(
+    const uint16_t* __restrict__ nin, typename Neq<kMode>::T* __restrict__ nout, const float4* __restrict__ min_,
+    float4* __restrict__ mout, float4* __restrict__ g, const uint32_t* __restrict__ flags, int nx, int ny, int nz,
+    int kz, float omega, float guo, float3 body, float3 utop, float inv_scale, int onsite)
+{
+    pdl_wait();
+    extern __shared__ __align__(16) char staged_sm[];
+    const int z0 = blockIdx.z * kz;
+    mixed_staged_column<kMode, T>(staged_sm, nin, nout, min_, mout, g, flags, nx, ny, nz, blockIdx.x * T::TX,
+                                  blockIdx.y * T::TY, z0, min(z0 + kz, nz), omega, guo, body, utop, inv_scale,
+                                  onsite);
 }
 
 template <int kMode, int q>
@@ -914,16 +1108,45 @@ cudaError_t launch_pair(LbCtx* c, cudaStream_t s, float omega, float guo, float3
                       guo, body, utop, inv_scale, p.walls);
 }
 
+template <int kMode, class T>
+cudaError_t launch_staged(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop, float inv_scale)
+{
+    const lb_params& p = c->p;
+    const int a = c->cur, b = c->cur ^ 1;
+    const int tiles = ((p.nx + T::TX - 1) / T::TX) * ((p.ny + T::TY - 1) / T::TY);
+    const long long want = 148LL * 8 * 256 / T::Threads;
+    const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
+    const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
+    static bool attr = false;   // one context's first launch sets the kernel's shared-memory limit
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_lb_step_staged<kMode, T>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)staged_smem<T>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(k_lb_step_staged<kMode, T>, grid, dim3(T::Threads), staged_smem<T>(), s,
+                      (const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b], (const float4*)c->m[a], c->m[b], c->g,
+                      (const uint32_t*)c->flags, p.nx, p.ny, p.nz, kz, omega, guo, body, utop, inv_scale, p.walls);
+}
+
 template <int kMode>
 cudaError_t launch_mixed_shape(LbCtx* c, cudaStream_t s, float omega, float guo, float3 body, float3 utop,
                                float inv_scale)
 {
-    // shapes 0, 1: the pair kernel with 64 x 4 or 64 x 8 columns; 2: the
-    // one-cell kernel with 32 x 8 columns; 3: the TMA-staged kernel with
-    // 32 x 8 columns where it applies, else the one-cell kernel with 32 x 4
+    // nx a multiple of 8: shape 0 the staged pair kernel (64 x 4 columns),
+    // 1 the pair kernel (64 x 4), 2 the one-cell kernel (32 x 8), 3 the
+    // TMA-staged kernel (32 x 8) where its tensor maps exist, else the
+    // one-cell kernel (32 x 4).  Otherwise: 0, 1 the pair kernel (64 x 4,
+    // 64 x 8), 2, 3 the one-cell kernel (32 x 8, 32 x 4).
+    const bool staged = c->p.nx % 8 == 0;
     switch (c->shape) {
-    case 0: return launch_pair<kMode, PairTile<4>>(c, s, omega, guo, body, utop, inv_scale);
-    case 1: return launch_pair<kMode, PairTile<8>>(c, s, omega, guo, body, utop, inv_scale);
+    case 0:
+        if (staged) return launch_staged<kMode, PairTile<4>>(c, s, omega, guo, body, utop, inv_scale);
+        return launch_pair<kMode, PairTile<4>>(c, s, omega, guo, body, utop, inv_scale);
+    case 1:
+        if (staged) return launch_pair<kMode, PairTile<4>>(c, s, omega, guo, body, utop, inv_scale);
+        return launch_pair<kMode, PairTile<8>>(c, s, omega, guo, body, utop, inv_scale);
     case 2: return launch_mixed<kMode, Tile<32, 8>>(c, s, omega, guo, body, utop, inv_scale);
     default:
         if (c->tma) return lb_tma_launch(c, c->tma, 0, s, omega, guo, body, utop, inv_scale);

@@ -190,9 +190,10 @@ def test_state_varying_along_x(storage, dims):
 @pytest.mark.parametrize("dims", [(48, 17, 13), (8, 5, 4), (64, 9, 6), (16, 3, 5), (40, 24, 7)])
 def test_launch_shapes_rows_on_16_byte_boundaries(storage, shape, dims):
     """Grids whose x rows start on 16-byte boundaries (nx a multiple of 8):
-    shapes 0 and 1 run the pair kernel (64x4 and 64x8 columns, two cells a
-    thread), 2 the one-cell kernel (32x8 columns), 3 the TMA-staged kernel
-    (32x8 columns).  Columns wider or taller than the grid,
+    shape 0 runs the staged pair kernel (64x4 columns, two cells a thread,
+    the 16-bit values of interior planes staged in shared memory), 1 the pair
+    kernel (64x4), 2 the one-cell kernel (32x8 columns), 3 the TMA-staged
+    kernel (32x8 columns).  Columns wider or taller than the grid,
     partial columns at the far edges, the periodic halo of every edge column
     and both wall planes; a state that varies from cell to cell and a
     flagged force, against the oracle with the bounds of test_free_steps."""
@@ -252,15 +253,18 @@ def test_shapes_share_one_state():
 
 @pytest.mark.parametrize("storage", ["bf16", "fp16"])
 @pytest.mark.parametrize("walls", [0, 1])
-@pytest.mark.parametrize("dims", [(64, 24, 10), (54, 20, 9), (53, 17, 13), (130, 7, 5), (3, 5, 4), (1, 4, 3)])
+@pytest.mark.parametrize("dims", [(64, 24, 10), (136, 9, 3), (8, 5, 4), (16, 3, 5), (8, 2, 2), (54, 20, 9),
+                                  (53, 17, 13), (130, 7, 5), (3, 5, 4), (1, 4, 3)])
 def test_every_shape_bit_identical(storage, walls, dims):
-    """Every launch shape (pair kernel with 64x4 and 64x8 columns, one-cell
-    kernel, TMA-staged kernel or the one-cell kernel with 32x4 columns) gives
+    """Every launch shape (staged pair, pair, one-cell and TMA-staged kernels
+    where nx is a multiple of 8; pair and one-cell kernels otherwise) gives
     the same populations and moment records bit for bit: even nx (the pair
-    kernel's 32-bit words; a multiple of 8 also takes the TMA kernel), odd
-    nx (the last pair of a row has one cell), more than two pair columns
-    along x, grids narrower than one column, both wall modes, a state that
-    varies from cell to cell and flagged forces, over 4 steps."""
+    kernel's 32-bit words; a multiple of 8 takes the staged kernels, with
+    windows wrapped per chunk at both x edges and per row in y; one interior
+    plane, none), odd nx (the last pair of a row has one cell), more than
+    two pair columns along x, grids narrower than one column, both wall
+    modes, a state that varies from cell to cell and flagged forces, over 4
+    steps."""
     nx, ny, nz = dims
     N = nx * ny * nz
     rng = np.random.default_rng(nx * 100 + ny)
