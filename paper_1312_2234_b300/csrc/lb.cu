@@ -630,7 +630,7 @@ __device__ __forceinline__ void pair_plane(const Ring<T>& ring, const uint16_t* 
                                            int ny, int k, int j, int ym, int yp, int i0, int i1, bool live1, int xm0,
                                            int xm1, int xp0, int xp1, int own, float omega, float keep, float guo,
                                            float3 F3b, float3 utop, float inv_scale, float scale, int onsite,
-                                           int nz, const uint16_t* __restrict__ win = nullptr)
+                                           int nz, uint32_t row_flag, const uint16_t* __restrict__ win = nullptr)
 {
     const int row = k * ny + j;
     const int base = row * nx;   // the cells are base + i0, base + i1
@@ -673,7 +673,7 @@ __device__ __forceinline__ void pair_plane(const Ring<T>& ring, const uint16_t* 
     }
     const float2 rho = add2(dup2(1.0f), drho);
     float2 Fx = dup2(F3b.x), Fy = dup2(F3b.y), Fz = dup2(F3b.z);
-    const bool forced = flags[row] != 0u;
+    const bool forced = row_flag != 0u;   // flags[row], loaded a plane ahead by the caller
     float4 g0, g1;
     if (forced) {
         g0 = g[base + i0];
@@ -749,13 +749,17 @@ __device__ __forceinline__ void mixed_pair_column(Ring<T>& ring, const uint16_t*
     __syncthreads();
 
     const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
+    // the row flag of the next plane is loaded one plane ahead
+    uint32_t flag_next = live0 ? flags[z0 * ny + j] : 0u;
     for (int k = z0; k < z1; ++k) {
+        const uint32_t flag = flag_next;
+        if (live0 && k + 1 < z1) flag_next = flags[(k + 1) * ny + j];
         const bool pre = k + 2 < nz && k + 2 <= z1;
         if (pre) halo_load<T>(min_, k + 2, plane_cells, off, r);
         if (live0)
             pair_plane<kMode, kWord, T>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1, live1, xm0,
                                         xm1, xp0, xp1, own, omega, keep, guo, F3b, utop, inv_scale, scale, onsite,
-                                        nz);
+                                        nz, flag);
         if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
         __syncthreads();
     }
@@ -887,7 +891,11 @@ __device__ __forceinline__ void mixed_staged_column(char* smem, const uint16_t* 
     __syncthreads();
 
     const float3 F3b = make_float3(3.0f * body.x, 3.0f * body.y, 3.0f * body.z);
+    // the row flag of the next plane is loaded one plane ahead
+    uint32_t flag_next = live0 ? flags[z0 * ny + j] : 0u;
     for (int k = z0; k < z1; ++k) {
+        const uint32_t flag = flag_next;
+        if (live0 && k + 1 < z1) flag_next = flags[(k + 1) * ny + j];
         // the next plane's window: its buffer was last read by plane k - 1,
         // which every thread has finished (barrier at the end of k - 1)
         if (k + 1 < z1 && k + 1 < nz - 1) stage(k + 1, (k + 1) & 1);
@@ -897,12 +905,12 @@ __device__ __forceinline__ void mixed_staged_column(char* smem, const uint16_t* 
             if (k != 0 && k != nz - 1)
                 pair_plane<kMode, true, T, true>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1,
                                                  live1, xm0, xm1, xp0, xp1, own, omega, keep, guo, F3b, utop,
-                                                 inv_scale, scale, 0, 3,
+                                                 inv_scale, scale, 0, 3, flag,
                                                  winbuf + (k & 1) * kWinElems + ty * kWinX + 2 * tx);
             else
                 pair_plane<kMode, true, T>(ring, nin, nout, mout, g, flags, N, nx, ny, k, j, ym, yp, i0, i1, live1,
                                            xm0, xm1, xp0, xp1, own, omega, keep, guo, F3b, utop, inv_scale, scale,
-                                           onsite, nz);
+                                           onsite, nz, flag);
         }
         if (pre) halo_store<T>(ring, (k + 2) & 3, r);   // slot of plane k - 2: no longer read
         cp_async_wait_all();   // the next plane's window has landed (this thread's copies)
