@@ -1125,17 +1125,25 @@ cudaError_t launch_staged(LbCtx* c, cudaStream_t s, float omega, float guo, floa
     const long long want = 148LL * 8 * 256 / T::Threads;
     const int kz = (int)std::min<long long>(32, std::max<long long>(2, ((long long)tiles * p.nz + want - 1) / want));
     const dim3 grid((p.nx + T::TX - 1) / T::TX, (p.ny + T::TY - 1) / T::TY, (p.nz + kz - 1) / kz);
-    static bool attr = false;   // one context's first launch sets the kernel's shared-memory limit
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_lb_step_staged<kMode, T>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)staged_smem<T>());
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     return launch_pdl(k_lb_step_staged<kMode, T>, grid, dim3(T::Threads), staged_smem<T>(), s,
                       (const uint16_t*)c->f[a], (NeqT<kMode>*)c->f[b], (const float4*)c->m[a], c->m[b], c->g,
                       (const uint32_t*)c->flags, p.nx, p.ny, p.nz, kz, omega, guo, body, utop, inv_scale, p.walls);
+}
+
+// The staged kernels' dynamic shared memory limit (above the 48 KB default),
+// set for the current device when a mixed-storage context is created.
+int staged_prepare()
+{
+    int rc = check_cuda(cudaFuncSetAttribute(k_lb_step_staged<PFSI_LB_BF16, PairTile<4>>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)staged_smem<PairTile<4>>()),
+                        "lb: staged kernel shared memory");
+    if (!rc)
+        rc = check_cuda(cudaFuncSetAttribute(k_lb_step_staged<PFSI_LB_FP16, PairTile<4>>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)staged_smem<PairTile<4>>()),
+                        "lb: staged kernel shared memory");
+    return rc;
 }
 
 template <int kMode>
@@ -1675,6 +1683,7 @@ int create_common(const char* who, const lb_params* p, void* f_a, void* f_b, flo
         !aligned(m_b, 16) || !aligned(row_flags, 4))
         return set_error(PFSI_ERR_ARG, std::string(who) + ": buffers must be 16-byte aligned");
     rc = ib_prepare();
+    if (!rc && p->storage != PFSI_LB_FP32) rc = staged_prepare();
     if (rc) return rc;
     lb_ctx* c = new lb_ctx();
     c->p = *p;
