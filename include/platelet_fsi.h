@@ -492,44 +492,54 @@ int fem_fields(fem_ctx* ctx, const double* X, float* fields, void* stream);
 /* ===================================================================== *
  * Learned membrane surrogate (no paper counterpart)
  *
- * A per-node network 27 -> 128 -> 128 -> 3 (GELU, tanh form) stands for the
- * local membrane terms of Section 3.1: edge springs (Eq. 3), the local area
- * term (Eq. 4, second term) and dihedral bending.  The global area term,
- * volume (Eq. 5), Morse pairs and wall repulsion stay exact.  Inputs of node
- * i, from its one-ring n_0..n_{d-1} (d <= 6, counter-clockwise seen from
- * outside, starting at the neighbour of smallest index), e_k = X[n_k] - X[i],
- * the frame R (rows x, y, z: z along sum e_k x e_{k+1}, x along e_0 projected
- * on the tangent plane), the same on the rest shape (R0, e0_k) and the length
- * l = mean |e0_k|:  with delta_k = (R e_k - R0 e0_k)/l and mag = |delta|,
- * delta_k / mag (18; 0 at rest), R0 mean(e0_k)/l (3), |e0_k|/l (6,
- * rest-length ratios), each times in_scale; the local force is
- * R^T (output * mag * out_scale): zero at rest, homogeneous of degree one in
- * the deformation (the linear-elastic response).
+ * A per-node network 42 -> 128 -> 128 -> 18 (GELU, tanh form) sets the
+ * element stresses of the local membrane terms of Section 3.1: edge springs
+ * (Eq. 2-3), the local area term (Eq. 4, second term) and dihedral bending.
+ * The global area term, volume (Eq. 5), Morse pairs and wall repulsion stay
+ * exact.  The local energy is split into node shares: node i with one-ring
+ * n_0..n_{d-1} (3 <= d <= 6, counter-clockwise seen from outside, starting at
+ * the neighbour of smallest index) owns, per slot k, half the spring of the
+ * spoke (i, n_k), a third of the area term of the fan triangle
+ * (i, n_k, n_{k+1}) and half the bending of the spoke (torsion of the chain
+ * n_{k+1} - i - n_k - n_{k-1}).  Its 18 element strains are
+ * x_s = (L - L0)/L0, x_a = (S - S0)/S0 and x_b = phi - phi0; the network sees
+ * their direction x * in_scale / |x * in_scale| (inputs 0..17: six
+ * stretches, six area strains, six bending angles) and the rest descriptors
+ * L0/l, S0/l^2, cos phi0, sin phi0 of each slot ((r - in_shift) * in_scale,
+ * inputs 18..41; l = mean rest spoke length), zero for empty slots.  Its
+ * output o sets the stresses y = x * m * out_scale * o with the rest moduli
+ * scales m = (L0^2, S0, 1), and the local force is
+ * F = - sum_i sum_j y_j dx_j/dX (exact strain gradients; each row adds to its
+ * node and its one-ring with atomic adds).  The exact stresses are
+ * (k_spring/2) L0^2 x_s, (k_t/3) S0 x_a and (k_b/2) sin x_b.
  *
  * Parameters: one caller-owned device buffer of PFSI_SG_PARAM_BYTES
  * (256-byte aligned): PFSI_SG_N_FLOATS floats at offset 0 (the trained block
- * of PFSI_SG_N_TRAINED floats, then in_scale[32], out_scale[16]), then at the
- * next 256-byte boundary the BF16 copies the tensor cores read (refresh with
- * sg_sync_shadows after writing the floats).  Weights are row-major
- * [outputs][inputs]; padding rows/columns (inputs 27..31, outputs 3..15)
- * must be zero and stay zero under training.
+ * of PFSI_SG_N_TRAINED floats, then in_shift[64], in_scale[64],
+ * out_scale[32], tgt_scale[32]), then at the next 256-byte boundary the BF16
+ * copies the tensor cores read (refresh with sg_sync_shadows after writing
+ * the floats).  Weights are row-major [outputs][inputs]; padding rows and
+ * columns (inputs 42..63, outputs 18..31) must be zero and stay zero under
+ * training.
  * ===================================================================== */
-#define PFSI_SG_IN 27
-#define PFSI_SG_IN_PAD 32
+#define PFSI_SG_IN 42
+#define PFSI_SG_IN_PAD 64
 #define PFSI_SG_HID 128
-#define PFSI_SG_OUT 3
-#define PFSI_SG_OUT_PAD 16
-#define PFSI_SG_W1 0          /* [128][32] */
-#define PFSI_SG_B1 4096       /* [128] */
-#define PFSI_SG_W2 4224       /* [128][128] */
-#define PFSI_SG_B2 20608      /* [128] */
-#define PFSI_SG_W3 20736      /* [16][128] */
-#define PFSI_SG_B3 22784      /* [16] */
-#define PFSI_SG_N_TRAINED 22800
-#define PFSI_SG_IN_SCALE 22800  /* [32] */
-#define PFSI_SG_OUT_SCALE 22832 /* [16] */
-#define PFSI_SG_N_FLOATS 22848
-#define PFSI_SG_PARAM_BYTES 173312
+#define PFSI_SG_OUT 18
+#define PFSI_SG_OUT_PAD 32
+#define PFSI_SG_W1 0          /* [128][64] */
+#define PFSI_SG_B1 8192       /* [128] */
+#define PFSI_SG_W2 8320       /* [128][128] */
+#define PFSI_SG_B2 24704      /* [128] */
+#define PFSI_SG_W3 24832      /* [32][128] */
+#define PFSI_SG_B3 28928      /* [32] */
+#define PFSI_SG_N_TRAINED 28960
+#define PFSI_SG_IN_SHIFT 28960  /* [64] */
+#define PFSI_SG_IN_SCALE 29024  /* [64] */
+#define PFSI_SG_OUT_SCALE 29088 /* [32] */
+#define PFSI_SG_TGT_SCALE 29120 /* [32] */
+#define PFSI_SG_N_FLOATS 29152
+#define PFSI_SG_PARAM_BYTES 215040
 #define PFSI_SG_BF16 0  /* BF16 operands on the tensor cores (tcgen05), FP32 accumulation */
 #define PFSI_SG_FP32 1  /* FP32 on CUDA cores: check mode */
 
@@ -540,14 +550,14 @@ int sg_params_bytes(size_t* bytes);
  * backward pass reads) from the FP32 block. */
 int sg_sync_shadows(void* params, void* stream);
 
-/* Training.  feat: [batch][32] scaled inputs (BF16 for PFSI_SG_BF16, float
- * for PFSI_SG_FP32; 16-byte aligned), target: float [batch][3] (local-frame
- * force / out_scale), batch a multiple of 128 (pad with zero rows: they add
- * nothing to the gradients but count in the mean).  Writes grad
- * (PFSI_SG_N_TRAINED floats, the trained-block layout) and, if loss is not
- * NULL, the device double *loss = mean over batch and 3 components of the
- * squared error.  work: sg_query_work(batch) bytes, 256-byte aligned.
- * Deterministic (fixed reduction order). */
+/* Training.  feat: [batch][64] inputs (BF16 for PFSI_SG_BF16, float for
+ * PFSI_SG_FP32; 16-byte aligned), target: float [batch][36], per row
+ * a[18] then b[18] (sg_targets), batch a multiple of 128 (pad with zero
+ * rows: they add nothing to the gradients but count in the mean).  Writes
+ * grad (PFSI_SG_N_TRAINED floats, the trained-block layout) and, if loss is
+ * not NULL, the device double *loss = mean over the batch and the 18
+ * outputs of (a o - b)^2.  work: sg_query_work(batch) bytes, 256-byte
+ * aligned.  Deterministic (fixed reduction order). */
 int sg_query_work(int batch, size_t* bytes);
 int sg_grad(const void* params, const void* feat, const float* target, int batch, int mode, float* grad,
             double* loss, void* work, size_t work_bytes, void* stream);
@@ -573,21 +583,21 @@ int sg_destroy(sg_ctx* ctx);
 /* Number of surrogate nodes (rows) and, optionally, the device array of their
  * node ids (rows padded to a multiple of 128 with -1). */
 int sg_rows(const sg_ctx* ctx, int* rows, const int** node);
-/* Scaled inputs of every surrogate node at positions X (double[3][n]) into
- * feat ([rows][32]; BF16 or float by the context's mode; NULL: the
- * context's own buffer), frames (float [rows][9], rows of R; NULL: own) and
- * mags (float [rows], deformation magnitude; NULL: own). */
-int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* frames, float* mags,
-                void* stream);
+/* Inputs of every surrogate node at positions X (double[3][n]) into feat
+ * ([rows][64]; BF16 or float by the context's mode; NULL: the context's own
+ * buffer), its element strains into xs (float [rows][18]; NULL: own) and the
+ * rest moduli scales (L0^2, S0, 1) into ms (float [rows][18]; NULL: own). */
+int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* xs, float* ms, void* stream);
 /* F = exact global terms (membrane_forces with the spring, local-area and
  * bending coefficients set to zero) + surrogate local forces. */
 int sg_membrane_forces(sg_ctx* ctx, const void* params, mem_ctx* mem, const double* X, float* F, void* stream);
-/* Training targets from a force field F (float[3][n], e.g. membrane_forces
- * with only the local coefficients): target[r] = (R F[node_r]) /
- * (mag_r out_scale), 0 where mag_r = 0, float [rows][3]; frames and mags
- * from sg_features (NULL: the context's own). */
-int sg_targets(const sg_ctx* ctx, const void* params, const float* F, const float* frames, const float* mags,
-               float* target, void* stream);
+/* Training record of every row from its strains xs and moduli scales ms
+ * (sg_features; NULL: the context's own) and the membrane coefficients of
+ * the local terms: the exact stresses y (k_spring/2 L0^2 x_s, k_t/3 S0 x_a,
+ * k_b/2 sin x_b) give target[r] = (a[18], b[18]) with a = x m tgt_scale and
+ * b = y tgt_scale / out_scale; float [rows][36]. */
+int sg_targets(const sg_ctx* ctx, const void* params, float k_spring, float k_t, float k_b, const float* xs,
+               const float* ms, float* target, void* stream);
 /* Device error flag of the context's tensor-core kernels.  Synchronises. */
 int sg_status(const sg_ctx* ctx, int* flag);
 

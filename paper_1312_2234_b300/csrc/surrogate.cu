@@ -1,16 +1,21 @@
 // surrogate.cu -- learned membrane-force surrogate for sm_103a (no paper
-// counterpart: a 27 -> 128 -> 128 -> 3 GELU network that stands for the local
-// membrane terms of Section 3.1, springs Eq. 3, local area Eq. 4, bending).
+// counterpart: a 42 -> 128 -> 128 -> 18 GELU network that sets the element
+// stresses of the local membrane terms of Section 3.1, springs Eq. 2-3, local
+// area Eq. 4, bending).
 //
-// Features: one thread per membrane node gathers its one-ring (<= 6 cyclic
-// neighbours), builds the local frame (z along the one-ring normal
-// sum e_k x e_{k+1}, x along the first edge projected on the tangent plane)
-// and writes 27 scaled inputs (the direction of the edge-vector deviations
-// from the rest one-ring in the local frames; the rest curvature normal and
-// the rest-length ratios, which describe the rest one-ring), the frame and
-// the deformation magnitude, by which the network output is multiplied: the
-// surrogate force is zero at rest and homogeneous of degree one in the
-// deformation, as the local membrane forces are in the linear-elastic range.
+// The local energy is split into node shares: membrane node i owns, per
+// one-ring slot k, half the spring of its spoke (i, n_k), a third of the area
+// term of its fan triangle (i, n_k, n_{k+1}) and half the bending of its
+// spoke (torsion of n_{k+1} - i - n_k - n_{k-1}).  One thread per node gathers
+// the one-ring (split hi/lo positions), forms the 18 element strains
+// (stretch (L - L0)/L0, area (S - S0)/S0, bending angle phi - phi0) from
+// small quantities only (the edge change d = e - e0 from the split positions,
+// L^2 - L0^2 = d.(2 e0 + d), |c|^2 - |c0|^2 = dc.(2 c0 + dc)), and feeds the
+// network their direction and the slot's rest descriptors.  The output sets
+// the stresses y = x * m * out_scale * o (m = L0^2, S0, 1), and the node's
+// force contributions y dx/dX (exact strain gradients: spoke unit vectors,
+// triangle area gradients, torsion gradients) go to the node and its
+// one-ring by atomic adds.
 //
 // Dense layers: one tcgen05 kernel, C = A B^T with both operands BF16 and
 // K-contiguous in global memory (every layer of the forward and backward pass
@@ -23,15 +28,14 @@
 // commits them to an mbarrier per stage (two stages: the next chunk loads
 // while the tensor core works), and every thread then reads its row back
 // with tcgen05.ld and applies a fused epilogue (bias + GELU, GELU' product,
-// output projection to the force, or a split-K partial).  Waits on the
-// mbarriers are bounded; a timeout sets an error flag and the CTA frees its
-// TMEM and returns.
+// output layer, or a split-K partial).  Waits on the mbarriers are bounded;
+// a timeout sets an error flag and the CTA frees its TMEM and returns.
 //
 // Inference inside the coupled step is one persistent kernel per step: each
 // CTA keeps W1, W2, W3 in shared memory and, per 128-node tile, computes the
-// features into a shared input tile, runs the three layers through TMEM
-// (the GELU epilogues write BF16 activations back to shared memory for the
-// next MMA) and adds R^T (output * out_scale) to the node forces.
+// strains and inputs into a shared input tile, runs the three layers through
+// TMEM (the GELU epilogues write BF16 activations back to shared memory for
+// the next MMA) and scatters the stress forces.
 //
 // An FP32 check path runs the same layer sequence with the same epilogues on
 // CUDA cores (plain dot products, FP32 activations), so the training pipeline
@@ -62,9 +66,13 @@ constexpr int kMaxSplit = 148;
 static_assert(PFSI_SG_W1 == 0 && PFSI_SG_B1 == PFSI_SG_W1 + kHid * kInPad && PFSI_SG_W2 == PFSI_SG_B1 + kHid &&
                   PFSI_SG_B2 == PFSI_SG_W2 + kHid * kHid && PFSI_SG_W3 == PFSI_SG_B2 + kHid &&
                   PFSI_SG_B3 == PFSI_SG_W3 + kOutPad * kHid && PFSI_SG_N_TRAINED == PFSI_SG_B3 + kOutPad &&
-                  PFSI_SG_IN_SCALE == PFSI_SG_N_TRAINED && PFSI_SG_OUT_SCALE == PFSI_SG_IN_SCALE + kInPad &&
-                  PFSI_SG_N_FLOATS == PFSI_SG_OUT_SCALE + kOutPad,
+                  PFSI_SG_IN_SHIFT == PFSI_SG_N_TRAINED && PFSI_SG_IN_SCALE == PFSI_SG_IN_SHIFT + kInPad &&
+                  PFSI_SG_OUT_SCALE == PFSI_SG_IN_SCALE + kInPad && PFSI_SG_TGT_SCALE == PFSI_SG_OUT_SCALE + kOutPad &&
+                  PFSI_SG_N_FLOATS == PFSI_SG_TGT_SCALE + kOutPad,
               "parameter layout");
+constexpr int kStrain = 18;    // element strains per row (= outputs)
+constexpr int kTgt = 2 * kStrain;
+static_assert(kOut == kStrain && kIn == kStrain + 24 && kIn < kInPad, "input layout");
 constexpr size_t kShadowOff = ((size_t)PFSI_SG_N_FLOATS * 4 + 255) / 256 * 256;
 constexpr int hW1 = 0, hW2 = hW1 + kHid * kInPad, hW3 = hW2 + kHid * kHid, hW2t = hW3 + kOutPad * kHid,
               hW3t = hW2t + kHid * kHid, nShadow = hW3t + kHid * kOutPad;
@@ -273,29 +281,6 @@ struct EpiPartial {
     }
 };
 
-// surrogate force: F[node] += R^T (o * out_scale), o = acc + b3 (columns 0..2)
-struct EpiForce {
-    const float* bias;
-    const float* out_scale;
-    const float* frames;   // [rows][9] rows x, y, z of R
-    const float* mags;     // [rows] deformation magnitude
-    const int* node;       // [rows] node id, -1 for padding rows
-    float* F;              // [3][n]
-    int n;
-    __device__ void row3(int row, float o0, float o1, float o2) const
-    {
-        const int v = node[row];
-        if (v < 0) return;
-        const float* R = frames + (size_t)row * 9;
-        const float mg = mags[row];
-        const float a = (o0 + bias[0]) * mg * out_scale[0], b = (o1 + bias[1]) * mg * out_scale[1],
-                    c = (o2 + bias[2]) * mg * out_scale[2];
-        F[v] += R[0] * a + R[3] * b + R[6] * c;
-        F[n + v] += R[1] * a + R[4] * b + R[7] * c;
-        F[2 * n + v] += R[2] * a + R[5] * b + R[8] * c;
-    }
-};
-
 // ------------------------------------------------------------------ tcgen05 / mbarrier helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -494,22 +479,10 @@ __global__ void k_gemm_f32(const float* __restrict__ A, long long sar, long long
     epi(row, n, acc, blockIdx.y);
 }
 
-__global__ void k_gemm_f32_force(const float* __restrict__ A, const float* __restrict__ W3, int rows, EpiForce epi)
-{
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= rows) return;
-    float o[3];
-    for (int j = 0; j < 3; ++j) {
-        float acc = 0.f;
-        for (int k = 0; k < kHid; ++k) acc = fmaf(A[(size_t)row * kHid + k], W3[j * kHid + k], acc);
-        o[j] = acc;
-    }
-    epi.row3(row, o[0], o[1], o[2]);
-}
-
 // ------------------------------------------------------------------ loss, reductions, Adam
-// dO = 2 (O - T) / (3 B) in columns 0..2 (zero in 3..15), row-major and
-// transposed; loss += sum (O - T)^2 / (3 B).
+// Stress error per output: e = a o - b (target row: a[18], b[18]);
+// dO = 2 a e / (18 B) in columns 0..17 (zero in 18..31), row-major and
+// transposed; loss += sum e^2 / (18 B).
 template <class T>
 __global__ void k_sg_loss(const float* __restrict__ O, const float* __restrict__ target, int B, int rows,
                           T* __restrict__ dO, T* __restrict__ dOt, double* __restrict__ loss)
@@ -520,8 +493,9 @@ __global__ void k_sg_loss(const float* __restrict__ O, const float* __restrict__
         for (int n = 0; n < kOutPad; ++n) {
             float d = 0.f;
             if (n < kOut && row < B) {
-                const float e = O[(size_t)row * kOutPad + n] - target[(size_t)row * kOut + n];
-                d = 2.0f * e / (3.0f * (float)B);
+                const float a = target[(size_t)row * kTgt + n], b = target[(size_t)row * kTgt + kStrain + n];
+                const float e = fmaf(a, O[(size_t)row * kOutPad + n], -b);
+                d = 2.0f * a * e / ((float)kOut * (float)B);
                 sq += (double)e * (double)e;
             }
             dO[(size_t)row * kOutPad + n] = to_t<T>(d);
@@ -529,7 +503,7 @@ __global__ void k_sg_loss(const float* __restrict__ O, const float* __restrict__
         }
     }
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
-    if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(loss, sq / (3.0 * (double)B));
+    if ((threadIdx.x & 31) == 0 && sq != 0.0) atomicAdd(loss, sq / ((double)kOut * (double)B));
 }
 
 // out[r] = sum over c < cols of M[r * ld + c] (one warp per row, fixed order)
@@ -553,7 +527,7 @@ __global__ void k_reduce_splits(const float* __restrict__ part, int splits, int 
     out[i] = s;
 }
 
-// features [rows][32] -> transposed copy [32][rows]
+// inputs [rows][64] -> transposed copy [64][rows]
 template <class T>
 __global__ void k_transpose_in(const T* __restrict__ X, int rows, T* __restrict__ Xt)
 {
@@ -608,120 +582,230 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b)
 {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ float3 axpy3(float a, float3 x, float3 y)
-{
-    return make_float3(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z));
-}
 __device__ __forceinline__ float3 add3(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 scale3(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
 
-// (1 + eps)^(-1/2) - 1 without cancellation
-__device__ __forceinline__ float rsqrt1p_m1(float eps)
+// a[i] for a runtime i in [0, 6) (selects: the array stays in registers)
+__device__ __forceinline__ float3 pick6(const float3 (&a)[6], int i)
 {
-    const float r = sqrtf(1.0f + eps);
-    return -eps / (r * (1.0f + r));
+    float3 r = a[0];
+#pragma unroll
+    for (int j = 1; j < 6; ++j)
+        if (i == j) r = a[j];
+    return r;
+}
+__device__ __forceinline__ void sub_at6(float3 (&a)[6], int i, float3 v)
+{
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        if (i == j) a[j] = sub3(a[j], v);
 }
 
-// Scaled inputs f[32], frame R[9] (rows x, y, z) and deformation magnitude
-// of surrogate row r.  xh, xl: positions split into hi/lo floats, [3][n].
+// One row's one-ring: node, neighbours (-1 beyond the degree), degree and
+// the current spoke vectors e_k = X[n_k] - X[v].
+struct RowRing {
+    int v, deg;
+    int nb[6];
+    float3 e[6];
+};
+
+// Torsion of the chain r1 - 0 - r3 - r4 (points relative to the second):
+// F = r1, G = -r3, H = r4 - r3, A = F x G, B = H x G,
+// cos = A.B / (|A||B|), sin = (B x A).G / (|A||B||G|).
+__device__ __forceinline__ void torsion_cs(float3 r1, float3 r3, float3 r4, float& c, float& s)
+{
+    const float3 G = scale3(-1.f, r3), H = sub3(r4, r3);
+    const float3 A = cross3(r1, G), B = cross3(H, G);
+    const float ab = sqrtf(dot3(A, A) * dot3(B, B));
+    c = dot3(A, B) / ab;
+    s = dot3(cross3(B, A), G) / (ab * sqrtf(dot3(G, G)));
+}
+
+// Its gradient with respect to the four points (Blondel and Karplus 1996).
+__device__ __forceinline__ void torsion_grad(float3 r1, float3 r3, float3 r4, float3 g[4])
+{
+    const float3 G = scale3(-1.f, r3), H = sub3(r4, r3);
+    const float3 A = cross3(r1, G), B = cross3(H, G);
+    const float A2 = dot3(A, A), B2 = dot3(B, B), gn = sqrtf(dot3(G, G));
+    const float FG = dot3(r1, G) / (A2 * gn), HG = dot3(H, G) / (B2 * gn);
+    const float ka = gn / A2, kb = gn / B2;
+    g[0] = scale3(-ka, A);
+    g[3] = scale3(kb, B);
+    g[1] = sub3(scale3(ka + FG, A), scale3(HG, B));
+    g[2] = add3(scale3(-FG, A), scale3(HG - kb, B));
+}
+
+// Element strains x[18] of surrogate row r (stretch, area strain and bending
+// angle of slots 0..5; zero for empty slots), its one-ring, and the rest
+// values of its slots.  xh, xl: positions split into hi/lo floats, [3][n].
 //
-// The deformation delta_k = (R e_k - R0 e0_k)/l is a small difference of
-// O(1) vectors, so it is formed from small quantities only: d_k = e_k - e0_k
-// from the split positions and the split rest edge (exact to ~1e-7 of |d_k|),
-// and the frame change dR = R - R0 to first and second order in d (the
-// normal change from dnu = sum d_k x e0_{k+1} + e0_k x d_{k+1} + d_k x d_{k+1},
-// renormalised without cancellation, then the same for the x axis); then
-// delta_k = (R d_k + dR e0_k)/l.  The inputs keep their relative accuracy down
-// to deformations of ~1e-7 of an edge (FP32 alone would bottom out at ~1e-7
-// absolute).
-__device__ __forceinline__ void node_features(const float* __restrict__ xh, const float* __restrict__ xl,
-                                              const SgDev& d, int r, const float* __restrict__ in_scale, float* f,
-                                              float* R, float& mag)
+// The strains are small differences of O(1) quantities, so they are formed
+// from small quantities only: d_k = e_k - e0_k from the split positions and
+// the split rest edge (exact to ~1e-7 of |d_k|), L^2 - L0^2 = d.(2 e0 + d),
+// and for the fan triangle (c = e_k x e_{k+1}) |c|^2 - |c0|^2 = dc.(2 c0 + dc)
+// with dc = d_k x e0_{k+1} + e0_k x d_{k+1} + d_k x d_{k+1}.  The bending
+// angle is atan2 of sin and cos of phi - phi0 (absolute error ~1e-7).
+__device__ __forceinline__ void row_strains(const float* __restrict__ xh, const float* __restrict__ xl,
+                                            const SgDev& d, int r, RowRing& g, float* x, float* L0, float* S0,
+                                            float* cph, float* sph, float& inv_l)
 {
     const int n = d.n_nodes;
     const int v = d.node[r];
     float rest[64];
 #pragma unroll
     for (int q = 0; q < 4; ++q) load16(d.rest + 64 * (size_t)r + 16 * q, rest + 16 * q);
-    const float* e0h = rest;        // rest edges, hi parts [6][3]
-    const float* e0l = rest + 18;   // lo parts
-    const float3 x0 = f3(rest + 36), y0 = f3(rest + 39), z0 = f3(rest + 42);
-    const float nu0 = rest[45], a0n = rest[46], inv_l = rest[47];
     float3 dk[6], e0[6];
     int deg = 0;
+    g.v = v;
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         const int nb = d.ring[6 * r + k];
-        e0[k] = f3(e0h + 3 * k);
+        g.nb[k] = nb;
+        e0[k] = f3(rest + 3 * k);
         if (nb >= 0) {
             float c[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const ff e = ff_diff(xh[a * n + nb], xl[a * n + nb], xh[a * n + v], xl[a * n + v]);
-                c[a] = (e.h - e0h[3 * k + a]) + (e.l - e0l[3 * k + a]);
+                c[a] = (e.h - rest[3 * k + a]) + (e.l - rest[18 + 3 * k + a]);
             }
             dk[k] = make_float3(c[0], c[1], c[2]);
             deg = k + 1;
         } else {
             dk[k] = make_float3(0.f, 0.f, 0.f);
         }
+        g.e[k] = add3(e0[k], dk[k]);
+        cph[k] = rest[36 + k];
+        sph[k] = rest[42 + k];
+        L0[k] = rest[48 + k];
+        S0[k] = rest[54 + k];
     }
-    // normal change
-    float3 dnu = make_float3(0.f, 0.f, 0.f);
+    g.deg = deg;
+    inv_l = rest[60];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
         if (k < deg) {
-            // cyclic successor with static indices (keeps the arrays in registers)
-            const float3 en = (k < 5 && k + 1 < deg) ? e0[k < 5 ? k + 1 : 0] : e0[0];
-            const float3 dn = (k < 5 && k + 1 < deg) ? dk[k < 5 ? k + 1 : 0] : dk[0];
-            dnu = add3(dnu, add3(cross3(dk[k], en), add3(cross3(e0[k], dn), cross3(dk[k], dn))));
+            // stretch of spoke k
+            const float dl2 = dot3(dk[k], add3(scale3(2.f, e0[k]), dk[k]));
+            const float L = sqrtf(dot3(g.e[k], g.e[k]));
+            x[k] = dl2 / ((L + L0[k]) * L0[k]);
+            // area strain of the fan triangle (v, n_k, n_{k+1}); static
+            // indices for the cyclic successor keep the arrays in registers
+            const bool last = !(k < 5 && k + 1 < deg);
+            const float3 e0n = last ? e0[0] : e0[k < 5 ? k + 1 : 0];
+            const float3 dn = last ? dk[0] : dk[k < 5 ? k + 1 : 0];
+            const float3 c0 = cross3(e0[k], e0n);
+            const float3 dc = add3(add3(cross3(dk[k], e0n), cross3(e0[k], dn)), cross3(dk[k], dn));
+            const float dS2 = dot3(dc, add3(scale3(2.f, c0), dc));
+            const float3 cc = add3(c0, dc);
+            const float S = 0.5f * sqrtf(dot3(cc, cc));
+            x[6 + k] = dS2 / (4.0f * (S + S0[k]) * S0[k]);
+            // bending angle of spoke k: chain n_{k+1} - v - n_k - n_{k-1}
+            const float3 en = last ? g.e[0] : g.e[k < 5 ? k + 1 : 0];
+            const float3 ep = k > 0 ? g.e[k > 0 ? k - 1 : 0] : pick6(g.e, deg - 1);
+            float c, s;
+            torsion_cs(en, g.e[k], ep, c, s);
+            x[12 + k] = atan2f(fmaf(s, cph[k], -c * sph[k]), fmaf(c, cph[k], s * sph[k]));
+        } else {
+            x[k] = x[6 + k] = x[12 + k] = 0.f;
         }
     }
-    const float3 nu0v = make_float3(nu0 * z0.x, nu0 * z0.y, nu0 * z0.z);
-    const float sz = rsqrt1p_m1((2.0f * dot3(nu0v, dnu) + dot3(dnu, dnu)) / (nu0 * nu0));
-    const float3 dz = axpy3(sz, z0, make_float3(dnu.x * (1.0f + sz) / nu0, dnu.y * (1.0f + sz) / nu0,
-                                                dnu.z * (1.0f + sz) / nu0));
-    const float3 z = add3(z0, dz);
-    // x axis change: a = e_0 - (e_0.z) z, a0 = |a0| x0
-    const float3 ef = add3(e0[0], dk[0]);
-    const float ez = dot3(ef, z);
-    const float dez = dot3(e0[0], dz) + dot3(dk[0], z);
-    const float3 da = add3(dk[0], add3(make_float3(-dez * z0.x, -dez * z0.y, -dez * z0.z),
-                                       make_float3(-ez * dz.x, -ez * dz.y, -ez * dz.z)));
-    const float3 a0v = make_float3(a0n * x0.x, a0n * x0.y, a0n * x0.z);
-    const float sx = rsqrt1p_m1((2.0f * dot3(a0v, da) + dot3(da, da)) / (a0n * a0n));
-    const float3 dx = axpy3(sx, x0, make_float3(da.x * (1.0f + sx) / a0n, da.y * (1.0f + sx) / a0n,
-                                                da.z * (1.0f + sx) / a0n));
-    const float3 x = add3(x0, dx);
-    const float3 dy = add3(add3(cross3(dz, x0), cross3(z0, dx)), cross3(dz, dx));
-    const float3 y = add3(y0, dy);
+}
+
+// Network inputs f[64] of a row: the strain direction x s / |x s| (inputs
+// 0..17) and the slots' rest descriptors L0/l, S0/l^2, cos phi0, sin phi0
+// ((r - shift) * scale, inputs 18..41), zero for empty slots and beyond 41.
+__device__ __forceinline__ void row_inputs(const float* x, int deg, const float* L0, const float* S0,
+                                           const float* cph, const float* sph, float inv_l,
+                                           const float* __restrict__ shift, const float* __restrict__ scale, float* f)
+{
     float mm = 0.f;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        if (k < deg) {
-            f[3 * k + 0] = (dot3(x, dk[k]) + dot3(dx, e0[k])) * inv_l;
-            f[3 * k + 1] = (dot3(y, dk[k]) + dot3(dy, e0[k])) * inv_l;
-            f[3 * k + 2] = (dot3(z, dk[k]) + dot3(dz, e0[k])) * inv_l;
-        } else {
-            f[3 * k + 0] = f[3 * k + 1] = f[3 * k + 2] = 0.f;
-        }
-        mm = fmaf(f[3 * k], f[3 * k], fmaf(f[3 * k + 1], f[3 * k + 1], fmaf(f[3 * k + 2], f[3 * k + 2], mm)));
-        f[21 + k] = rest[51 + k];
+    for (int j = 0; j < kStrain; ++j) {
+        f[j] = x[j] * scale[j];
+        mm = fmaf(f[j], f[j], mm);
     }
-    // deformation: direction (inputs 0..17) and magnitude
-    mag = sqrtf(mm);
-    const float inv = mag > 0.f ? 1.0f / mag : 0.f;
+    const float inv = mm > 0.f ? 1.0f / sqrtf(mm) : 0.f;
 #pragma unroll
-    for (int k = 0; k < 18; ++k) f[k] *= inv;
-    f[18] = rest[48];
-    f[19] = rest[49];
-    f[20] = rest[50];
+    for (int j = 0; j < kStrain; ++j) f[j] *= inv;
 #pragma unroll
-    for (int k = kIn; k < kInPad; ++k) f[k] = 0.f;
+    for (int k = 0; k < 6; ++k) {
+        const float raw[4] = {L0[k] * inv_l, S0[k] * inv_l * inv_l, cph[k], sph[k]};
 #pragma unroll
-    for (int k = 0; k < kInPad; ++k) f[k] *= in_scale[k];
-    R[0] = x.x; R[1] = x.y; R[2] = x.z;
-    R[3] = y.x; R[4] = y.y; R[5] = y.z;
-    R[6] = z.x; R[7] = z.y; R[8] = z.z;
+        for (int q = 0; q < 4; ++q) {
+            const int j = kStrain + 6 * q + k;
+            f[j] = k < deg ? (raw[q] - shift[j]) * scale[j] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int j = kIn; j < kInPad; ++j) f[j] = 0.f;
+}
+
+// Factors q of the stresses' strain gradients: y_j dx_j/dX = (q_j o_j) G_j
+// with G = e/L (spring, at n_k), the area gradient (area), the torsion
+// gradient (bending): q_s = x_s L0 out_s (y_s / L0), q_a = x_a out_a
+// (y_a / S0), q_b = x_b out_b.
+__device__ __forceinline__ void stress_factors(const float* x, const float* L0, const float* __restrict__ out,
+                                               float* q)
+{
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        q[k] = x[k] * L0[k] * out[k];
+        q[6 + k] = x[6 + k] * out[6 + k];
+        q[12 + k] = x[12 + k] * out[12 + k];
+    }
+}
+
+// F -= sum_j p_j G_j of one row (p = q o), added to the node and its
+// one-ring with atomic adds.  Area gradient of corner a of the fan triangle
+// (v, n_k, n_{k+1}): (1/2) nhat x (P_{a+2} - P_{a+1}).
+__device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, float* __restrict__ F, int n)
+{
+    float3 Fi = make_float3(0.f, 0.f, 0.f);
+    float3 Fn[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Fn[k] = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k < g.deg) {
+            const bool last = !(k < 5 && k + 1 < g.deg);
+            const int kn = last ? 0 : k + 1;
+            const int kp = k > 0 ? k - 1 : g.deg - 1;
+            const float3 ek = g.e[k];
+            const float3 en = last ? g.e[0] : g.e[k < 5 ? k + 1 : 0];
+            const float3 ep = k > 0 ? g.e[k > 0 ? k - 1 : 0] : pick6(g.e, g.deg - 1);
+            // spring: -y_s dx_s/dX_{n_k} = -q_s o_s e/L, the opposite at v
+            const float3 fs = scale3(p[k] / sqrtf(dot3(ek, ek)), ek);
+            Fn[k] = sub3(Fn[k], fs);
+            Fi = add3(Fi, fs);
+            // area: nhat x (.) / 2 with nhat = c / |c|
+            const float3 c = cross3(ek, en);
+            const float h = 0.5f * p[6 + k] / sqrtf(dot3(c, c));
+            Fi = sub3(Fi, scale3(h, cross3(c, sub3(en, ek))));
+            Fn[k] = add3(Fn[k], scale3(h, cross3(c, en)));
+            sub_at6(Fn, kn, scale3(h, cross3(c, ek)));
+            // bending: chain n_{k+1} - v - n_k - n_{k-1}
+            float3 tg[4];
+            torsion_grad(en, ek, ep, tg);
+            const float pb = p[12 + k];
+            sub_at6(Fn, kn, scale3(pb, tg[0]));
+            Fi = sub3(Fi, scale3(pb, tg[1]));
+            Fn[k] = sub3(Fn[k], scale3(pb, tg[2]));
+            sub_at6(Fn, kp, scale3(pb, tg[3]));
+        }
+    }
+    atomicAdd(F + g.v, Fi.x);
+    atomicAdd(F + n + g.v, Fi.y);
+    atomicAdd(F + 2 * n + g.v, Fi.z);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (k < g.deg) {
+            const int u = g.nb[k];
+            atomicAdd(F + u, Fn[k].x);
+            atomicAdd(F + n + u, Fn[k].y);
+            atomicAdd(F + 2 * n + u, Fn[k].z);
+        }
 }
 
 // FP64 positions -> hi/lo float split, [3][n] each
@@ -736,36 +820,83 @@ __global__ void k_sg_split(const double* __restrict__ X, int n3, float* __restri
     }
 }
 
+// Inputs (feat [rows][64]), strains (xs [rows][18]) and rest moduli scales
+// (ms [rows][18]: L0^2, S0, 1; zero for empty slots) of every row.
 template <class T>
 __global__ void k_sg_features(const float* __restrict__ xh, const float* __restrict__ xl, SgDev d,
-                              const float* __restrict__ in_scale, T* __restrict__ feat, float* __restrict__ frames,
-                              float* __restrict__ mags)
+                              const float* __restrict__ P, T* __restrict__ feat, float* __restrict__ xs,
+                              float* __restrict__ ms)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
-    float f[kInPad], R[9], mag;
-    node_features(xh, xl, d, r, in_scale, f, R, mag);
-    mags[r] = mag;
-    store16(feat + (size_t)r * kInPad, f);
-    store16(feat + (size_t)r * kInPad + 16, f + 16);
-    float* fr = frames + 9 * (size_t)r;
+    RowRing g;
+    float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l;
+    row_strains(xh, xl, d, r, g, x, L0, S0, cph, sph, inv_l);
+    float f[kInPad];
+    row_inputs(x, g.deg, L0, S0, cph, sph, inv_l, P + PFSI_SG_IN_SHIFT, P + PFSI_SG_IN_SCALE, f);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) fr[k] = R[k];
+    for (int q = 0; q < kInPad / 16; ++q) store16(feat + (size_t)r * kInPad + 16 * q, f + 16 * q);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool on = k < g.deg;
+        xs[(size_t)kStrain * r + k] = x[k];
+        xs[(size_t)kStrain * r + 6 + k] = x[6 + k];
+        xs[(size_t)kStrain * r + 12 + k] = x[12 + k];
+        ms[(size_t)kStrain * r + k] = on ? L0[k] * L0[k] : 0.f;
+        ms[(size_t)kStrain * r + 6 + k] = on ? S0[k] : 0.f;
+        ms[(size_t)kStrain * r + 12 + k] = on ? 1.f : 0.f;
+    }
+}
+
+// Training record of every row: the exact stresses y (cs m x, ca m x,
+// cb sin x) give a = x m t and b = y t / out_scale.
+__global__ void k_sg_targets(SgDev d, const float* __restrict__ P, float cs, float ca, float cb,
+                             const float* __restrict__ xs, const float* __restrict__ ms, float* __restrict__ target)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    const float* out = P + PFSI_SG_OUT_SCALE;
+    const float* tg = P + PFSI_SG_TGT_SCALE;
+    for (int j = 0; j < kStrain; ++j) {
+        const float x = xs[(size_t)kStrain * r + j], m = ms[(size_t)kStrain * r + j];
+        const float y = j < 6 ? cs * m * x : (j < 12 ? ca * m * x : cb * m * sinf(x));
+        target[(size_t)kTgt * r + j] = x * m * tg[j];
+        target[(size_t)kTgt * r + kStrain + j] = y * tg[j] / out[j];
+    }
+}
+
+// FP32 check path, output layer and forces: o = W3 h2 + b3 (CUDA cores),
+// then the row's stress forces.
+__global__ void k_sg_f32_forces(const float* __restrict__ xh, const float* __restrict__ xl, SgDev d,
+                                const float* __restrict__ P, const float* __restrict__ H2, float* __restrict__ F)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.rows) return;
+    RowRing g;
+    float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l, q[kStrain];
+    row_strains(xh, xl, d, r, g, x, L0, S0, cph, sph, inv_l);
+    stress_factors(x, L0, P + PFSI_SG_OUT_SCALE, q);
+    for (int j = 0; j < kStrain; ++j) {
+        float acc = P[PFSI_SG_B3 + j];
+        for (int k = 0; k < kHid; ++k) acc = fmaf(H2[(size_t)r * kHid + k], P[PFSI_SG_W3 + j * kHid + k], acc);
+        q[j] *= acc;
+    }
+    row_scatter(g, q, F, d.n_nodes);
 }
 
 // ------------------------------------------------------------------ fused inference
 // Persistent kernel, one CTA of four warpgroups per SM.  Each warpgroup is an
-// independent pipeline over 128-row tiles: it computes the tile's features
-// into its shared input tile A0 (128 x 32), runs the three layers through its
-// 128 TMEM columns (each layer's accumulator overwrites the previous one
-// once the GELU epilogue has read it back; the epilogue writes the BF16
-// activations into its shared hidden tile A1, 128 x 128, for the next MMA)
-// and adds R^T (output * out_scale) to the node forces.  W1, W2, W3 sit once
+// independent pipeline over 128-row tiles: it computes the tile's strains and
+// inputs into its shared input tile A0 (128 x 64), runs the three layers
+// through its 128 TMEM columns (each layer's accumulator overwrites the
+// previous one once the GELU epilogue has read it back; the epilogue writes
+// the BF16 activations into its shared hidden tile A1, 128 x 144, for the
+// next MMA) and scatters the stress forces of its rows.  W1, W2, W3 sit once
 // per CTA in shared memory in the core-matrix layout, with the biases folded
-// in as an extra K column (the input tile carries a 1 in column 27, the
+// in as an extra K column (the input tile carries a 1 in column 42, the
 // hidden tile in column 128; K of the hidden layers is padded to 144), so the
 // epilogue is the GELU alone.  Four pipelines per SM keep the tensor core
-// busy while the others gather features or run their epilogues.
+// busy while the others gather their rows or run their epilogues.
 constexpr int kInferWG = 4;
 constexpr int kKb = kHid + 16;                 // hidden K with the bias column (128) and zero padding
 constexpr int kInferW1 = 0;
@@ -832,7 +963,7 @@ __device__ __forceinline__ bool wg_and(bool v, int id)
 
 __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* __restrict__ xh,
                                                                   const float* __restrict__ xl, SgDev d, Params P,
-                                                                  EpiForce ef, int* __restrict__ err)
+                                                                  float* __restrict__ F, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bars[kInferWG];
@@ -845,16 +976,16 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
         fence_barrier_init();
     }
     if (threadIdx.x < 32) tmem_alloc(&tmem_sh, 512);
-    // weights with the biases folded in: input 27 of A0 and column 128 of the
-    // hidden tile are 1, so W1[:, 27] = b1, W2[:, 128] = b2, W3[:, 128] = b3
+    // weights with the biases folded in: input 42 of A0 and column 128 of the
+    // hidden tile are 1, so W1[:, 42] = b1, W2[:, 128] = b2, W3[:, 128] = b3
     load_core(smem + kInferW1, P.h + hW1, kInPad, kHid, kInPad / 8, kInPad / 8);
     load_core(smem + kInferW2, P.h + hW2, kHid, kHid, kHid / 8, kKb / 8);
     load_core(smem + kInferW3, P.h + hW3, kHid, kOutPad, kHid / 8, kKb / 8);
     __syncthreads();
     if (threadIdx.x < kHid) {
         const int r = threadIdx.x;
-        reinterpret_cast<bf16*>(smem + kInferW1 + (((r >> 3) * (kInPad / 8) + 3) << 7) + ((r & 7) << 4))[3] =
-            __float2bfloat16_rn(P.p[PFSI_SG_B1 + r]);
+        reinterpret_cast<bf16*>(smem + kInferW1 + (((r >> 3) * (kInPad / 8) + (kIn >> 3)) << 7) +
+                                ((r & 7) << 4))[kIn & 7] = __float2bfloat16_rn(P.p[PFSI_SG_B1 + r]);
         put_bias_group(smem + kInferW2, kKb / 8, r, kHid / 8, P.p[PFSI_SG_B2 + r], true);
         if (r < kOutPad) put_bias_group(smem + kInferW3, kKb / 8, r, kHid / 8, P.p[PFSI_SG_B3 + r], true);
     }
@@ -874,16 +1005,23 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
     const int n_tiles = d.rows_pad / kTile;
     for (int tile = blockIdx.x * kInferWG + wg; tile < n_tiles; tile += gridDim.x * kInferWG) {
         const int row = tile * kTile + t;
-        float f[kInPad], R[9], mag = 0.f;
+        float f[kInPad], q[kStrain];
+        RowRing g;
+        g.deg = 0;
         if (row < d.rows) {
-            node_features(xh, xl, d, row, P.p + PFSI_SG_IN_SCALE, f, R, mag);
+            float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l;
+            row_strains(xh, xl, d, row, g, x, L0, S0, cph, sph, inv_l);
+            row_inputs(x, g.deg, L0, S0, cph, sph, inv_l, P.p + PFSI_SG_IN_SHIFT, P.p + PFSI_SG_IN_SCALE, f);
+            stress_factors(x, L0, P.p + PFSI_SG_OUT_SCALE, q);
         } else {
 #pragma unroll
             for (int k = 0; k < kInPad; ++k) f[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < kStrain; ++k) q[k] = 0.f;
         }
         f[kIn] = 1.0f;   // bias input
-        put_row16(A0, kInPad / 8, t, 0, f);
-        put_row16(A0, kInPad / 8, t, 16, f + 16);
+#pragma unroll
+        for (int c = 0; c < kInPad / 16; ++c) put_row16(A0, kInPad / 8, t, 16 * c, f + 16 * c);
         for (int layer = 0; layer < 3; ++layer) {
             fence_proxy_async();
             tc_fence_before();
@@ -892,8 +1030,8 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
                 tc_fence_after();
                 if (layer == 0) {
                     for (int j = 0; j < kInPad / 16; ++j)
-                        mma_bf16(tmem, smem_desc(sA0 + 256 * j, 128, 512), smem_desc(sW1 + 256 * j, 128, 512),
-                                 idesc_bf16(kHid), j > 0 ? 1u : 0u);
+                        mma_bf16(tmem, smem_desc(sA0 + 256 * j, 128, 128 * (kInPad / 8)),
+                                 smem_desc(sW1 + 256 * j, 128, 128 * (kInPad / 8)), idesc_bf16(kHid), j > 0 ? 1u : 0u);
                 } else {
                     const uint32_t sW = layer == 1 ? sW2 : sW3;
                     const uint32_t idesc = idesc_bf16(layer == 1 ? kHid : kOutPad);
@@ -924,16 +1062,17 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
             if (layer == 0) put_bias_group(A1, kKb / 8, t, kHid / 8, 1.0f, true);
         }
         if (!ok) break;
-        float o[16];
-        tmem_ld16(lanes, o);
-        if (row < d.rows) {
-            const int v = ef.node[row];
-            const float a = o[0] * mag * ef.out_scale[0], b = o[1] * mag * ef.out_scale[1],
-                        c = o[2] * mag * ef.out_scale[2];
-            ef.F[v] += R[0] * a + R[3] * b + R[6] * c;
-            ef.F[ef.n + v] += R[1] * a + R[4] * b + R[7] * c;
-            ef.F[2 * ef.n + v] += R[2] * a + R[5] * b + R[8] * c;
+        // output o (bias included) -> stresses -> forces of the tile's rows
+        {
+            float o[16];
+            tmem_ld16(lanes, o);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) q[j] *= o[j];
+            tmem_ld16(lanes + 16u, o);
+#pragma unroll
+            for (int j = 16; j < kStrain; ++j) q[j] *= o[j - 16];
         }
+        if (row < d.rows) row_scatter(g, q, F, d.n_nodes);
     }
     if (!ok && t == 0) atomicExch(err, 1);
     tc_fence_before();
@@ -942,23 +1081,6 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
         tc_fence_after();
         tmem_dealloc(tmem_sh, 512);
     }
-}
-
-// Training targets: target[r] = (R F[node]) / (mag out_scale) (local frame;
-// zero where the node is undeformed).
-__global__ void k_sg_targets(SgDev d, const float* __restrict__ F, const float* __restrict__ frames,
-                             const float* __restrict__ mags, const float* __restrict__ out_scale,
-                             float* __restrict__ target)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d.rows) return;
-    const int v = d.node[r], n = d.n_nodes;
-    const float fx = F[v], fy = F[n + v], fz = F[2 * n + v];
-    const float* R = frames + 9 * (size_t)r;
-    const float inv = mags[r] > 0.f ? 1.0f / mags[r] : 0.f;
-    target[3 * (size_t)r + 0] = (R[0] * fx + R[1] * fy + R[2] * fz) * inv / out_scale[0];
-    target[3 * (size_t)r + 1] = (R[3] * fx + R[4] * fy + R[5] * fz) * inv / out_scale[1];
-    target[3 * (size_t)r + 2] = (R[6] * fx + R[7] * fy + R[8] * fz) * inv / out_scale[2];
 }
 
 // ------------------------------------------------------------------ host side
@@ -979,9 +1101,9 @@ int prepare_tc()
     int rc = smem_attr<128, EpiHidden<bf16>>();
     if (!rc) rc = smem_attr<128, EpiBack<bf16>>();
     if (!rc) rc = smem_attr<128, EpiPartial>();
-    if (!rc) rc = smem_attr<16, EpiOut>();
-    if (!rc) rc = smem_attr<16, EpiPartial>();
-    if (!rc) rc = smem_attr<32, EpiPartial>();
+    if (!rc) rc = smem_attr<kOutPad, EpiOut>();
+    if (!rc) rc = smem_attr<kOutPad, EpiPartial>();
+    if (!rc) rc = smem_attr<kInPad, EpiPartial>();
     if (!rc)
         rc = check_cuda(cudaFuncSetAttribute(k_sg_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kInferSmem),
                         "surrogate: shared memory");
@@ -1019,16 +1141,16 @@ int used_splits(int K, int splits)
 
 // Training workspace for a batch of `rows` (multiple of 128) samples.
 struct Work {
-    void* Xt;       // [32][rows]
+    void* Xt;       // [64][rows]
     float* Z1;      // [rows][128]
     float* Z2;
     void* H1;       // [rows][128]
     void* H2;
     void* H1t;      // [128][rows]
     void* H2t;
-    float* O;       // [rows][16]
-    void* dO;       // [rows][16]
-    void* dOt;      // [16][rows]
+    float* O;       // [rows][32]
+    void* dO;       // [rows][32]
+    void* dOt;      // [32][rows]
     void* dZ2;      // [rows][128]
     void* dZ2t;     // [128][rows]
     void* dZ1t;     // [128][rows]
@@ -1041,8 +1163,8 @@ struct Work {
 Work work_layout(void* base, int rows)
 {
     const size_t R = rows;
-    const size_t sizes[] = {4 * 32 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R,
-                            4 * 128 * R, 4 * 16 * R, 4 * 16 * R, 4 * 16 * R, 4 * 128 * R, 4 * 128 * R,
+    const size_t sizes[] = {4 * kInPad * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R, 4 * 128 * R,
+                            4 * 128 * R, 4 * kOutPad * R, 4 * kOutPad * R, 4 * kOutPad * R, 4 * 128 * R, 4 * 128 * R,
                             4 * 128 * R, 4 * (size_t)kMaxSplit * 128 * 128, 8, 4};
     void* ptr[16];
     size_t o = 0;
@@ -1085,7 +1207,7 @@ int grad_bf16(Params P, const bf16* X, const float* target, int B, int rows, flo
     if ((rc = gemm_tc<128>(H1, kHid, P.h + hW2, kHid, rows, kHid, 1,
                            EpiHidden<bf16>{P.p + PFSI_SG_B2, w.Z2, H2, H2t, rows}, w.err, s)))
         return rc;
-    if ((rc = gemm_tc<16>(H2, kHid, P.h + hW3, kHid, rows, kHid, 1, EpiOut{P.p + PFSI_SG_B3, w.O}, w.err, s)))
+    if ((rc = gemm_tc<kOutPad>(H2, kHid, P.h + hW3, kHid, rows, kHid, 1, EpiOut{P.p + PFSI_SG_B3, w.O}, w.err, s)))
         return rc;
     if ((rc = check_cuda(cudaMemsetAsync(w.loss, 0, sizeof(double), s), "surrogate: clear loss"))) return rc;
     k_sg_loss<bf16><<<(rows + 127) / 128, 128, 0, s>>>(w.O, target, B, rows, dO, dOt, w.loss);
@@ -1100,7 +1222,8 @@ int grad_bf16(Params P, const bf16* X, const float* target, int B, int rows, flo
     // weight gradients, split over the batch
     const int sp = splits_for(rows);
     const int u = used_splits(rows, sp);
-    if ((rc = gemm_tc<16>(H2t, rows, dOt, rows, kHid, rows, sp, EpiPartial{w.part, kHid, kOutPad * kHid, true}, w.err, s)))
+    if ((rc = gemm_tc<kOutPad>(H2t, rows, dOt, rows, kHid, rows, sp, EpiPartial{w.part, kHid, kOutPad * kHid, true},
+                               w.err, s)))
         return rc;
     k_reduce_splits<<<(kOutPad * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kOutPad * kHid, g + PFSI_SG_W3);
     if ((rc = check_launch("surrogate: reduce"))) return rc;
@@ -1108,7 +1231,8 @@ int grad_bf16(Params P, const bf16* X, const float* target, int B, int rows, flo
         return rc;
     k_reduce_splits<<<(kHid * kHid + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kHid, g + PFSI_SG_W2);
     if ((rc = check_launch("surrogate: reduce"))) return rc;
-    if ((rc = gemm_tc<32>(dZ1t, rows, Xt, rows, kHid, rows, sp, EpiPartial{w.part, kInPad, kHid * kInPad, false}, w.err, s)))
+    if ((rc = gemm_tc<kInPad>(dZ1t, rows, Xt, rows, kHid, rows, sp, EpiPartial{w.part, kInPad, kHid * kInPad, false},
+                              w.err, s)))
         return rc;
     k_reduce_splits<<<(kHid * kInPad + 255) / 256, 256, 0, s>>>(w.part, u, kHid * kInPad, g + PFSI_SG_W1);
     if ((rc = check_launch("surrogate: reduce"))) return rc;
@@ -1222,55 +1346,60 @@ int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned 
             err = "one-ring does not close";
             return PFSI_ERR_ARG;
         }
-        // rest frame (FP64)
-        double e[6][3], nu[3] = {0, 0, 0};
+        // rest record (FP64 geometry): e0_k split hi/lo (0..35), cos and sin of
+        // the rest bending angle of each spoke (36..47), L0_k (48..53), S0_k
+        // of the fan triangles (54..59), 1/l with l the mean L0 (60)
+        double e[6][3];
         for (int q = 0; q < d; ++q)
             for (int c = 0; c < 3; ++c) e[q][c] = P(ring[q], c) - P(i, c);
-        for (int q = 0; q < d; ++q) {
-            const double* a = e[q];
-            const double* b = e[(q + 1) % d];
-            nu[0] += a[1] * b[2] - a[2] * b[1];
-            nu[1] += a[2] * b[0] - a[0] * b[2];
-            nu[2] += a[0] * b[1] - a[1] * b[0];
-        }
-        const double nn = std::sqrt(nu[0] * nu[0] + nu[1] * nu[1] + nu[2] * nu[2]);
-        if (!(nn > 0)) {
-            err = "degenerate rest one-ring";
-            return PFSI_ERR_ARG;
-        }
-        const double z[3] = {nu[0] / nn, nu[1] / nn, nu[2] / nn};
-        const double ez = e[0][0] * z[0] + e[0][1] * z[1] + e[0][2] * z[2];
-        double x[3] = {e[0][0] - ez * z[0], e[0][1] - ez * z[1], e[0][2] - ez * z[2]};
-        const double xn = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-        for (double& c : x) c /= xn;
-        const double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
-        double L[6], ell = 0, mean[3] = {0, 0, 0};
-        for (int q = 0; q < d; ++q) {
-            L[q] = std::sqrt(e[q][0] * e[q][0] + e[q][1] * e[q][1] + e[q][2] * e[q][2]);
-            ell += L[q] / d;
-            for (int c = 0; c < 3; ++c) mean[c] += e[q][c] / d;
-        }
-        // rest record: e0_k split hi/lo (0..35), R0 rows (36..44), |nu0|, |a0|,
-        // 1/l (45..47), kappa0 (48..50), rest-length ratios (51..56)
+        auto cross = [](const double* a, const double* b, double* r) {
+            r[0] = a[1] * b[2] - a[2] * b[1];
+            r[1] = a[2] * b[0] - a[0] * b[2];
+            r[2] = a[0] * b[1] - a[1] * b[0];
+        };
+        auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
         float r64[64] = {};
-        for (int q = 0; q < d; ++q)
+        double ell = 0;
+        for (int q = 0; q < d; ++q) {
+            const double* en = e[(q + 1) % d];
+            const double* ep = e[(q + d - 1) % d];
+            const double L = std::sqrt(dot(e[q], e[q]));
+            double cc[3];
+            cross(e[q], en, cc);
+            const double S = 0.5 * std::sqrt(dot(cc, cc));
+            if (!(L > 0) || !(S > 0)) {
+                err = "degenerate rest one-ring";
+                return PFSI_ERR_ARG;
+            }
+            // torsion of n_{q+1} - i - n_q - n_{q-1}, points relative to i:
+            // F = e_{q+1}, G = -e_q, H = e_{q-1} - e_q
+            double G[3], H[3], A[3], B[3], BA[3];
+            for (int c = 0; c < 3; ++c) {
+                G[c] = -e[q][c];
+                H[c] = ep[c] - e[q][c];
+            }
+            cross(en, G, A);
+            cross(H, G, B);
+            cross(B, A, BA);
+            const double ab = std::sqrt(dot(A, A) * dot(B, B));
+            if (!(ab > 0)) {
+                err = "degenerate rest one-ring";
+                return PFSI_ERR_ARG;
+            }
+            const double cphi = dot(A, B) / ab, sphi = dot(BA, G) / (ab * L);
+            const double phi = std::atan2(sphi, cphi);
             for (int c = 0; c < 3; ++c) {
                 const float h = (float)e[q][c];
                 r64[3 * q + c] = h;
                 r64[18 + 3 * q + c] = (float)(e[q][c] - (double)h);
             }
-        for (int c = 0; c < 3; ++c) {
-            r64[36 + c] = (float)x[c];
-            r64[39 + c] = (float)y[c];
-            r64[42 + c] = (float)z[c];
+            r64[36 + q] = (float)std::cos(phi);
+            r64[42 + q] = (float)std::sin(phi);
+            r64[48 + q] = (float)L;
+            r64[54 + q] = (float)S;
+            ell += L / d;
         }
-        r64[45] = (float)nn;
-        r64[46] = (float)xn;
-        r64[47] = (float)(1.0 / ell);
-        r64[48] = (float)((x[0] * mean[0] + x[1] * mean[1] + x[2] * mean[2]) / ell);
-        r64[49] = (float)((y[0] * mean[0] + y[1] * mean[1] + y[2] * mean[2]) / ell);
-        r64[50] = (float)((z[0] * mean[0] + z[1] * mean[1] + z[2] * mean[2]) / ell);
-        for (int q = 0; q < d; ++q) r64[51 + q] = (float)(L[q] / ell);
+        r64[60] = (float)(1.0 / ell);
         R.node.push_back(i);
         for (int q = 0; q < 6; ++q) R.ring.push_back(ring[q]);
         R.rest.insert(R.rest.end(), r64, r64 + 64);
@@ -1283,14 +1412,14 @@ int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned 
 }
 
 struct SgLayout {
-    size_t node, ring, rest, feat, frames, mags, h1, h2, xh, xl, err, total;
+    size_t node, ring, rest, feat, xs, ms, h1, h2, xh, xl, err, total;
 };
 // rows: surrogate rows; n: mesh nodes
 SgLayout sg_layout(int rows, int n)
 {
     const size_t Rp = ((size_t)rows + kTile - 1) / kTile * kTile;
-    const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 64 * Rp, 4 * 32 * Rp, 4 * 9 * Rp, 4 * Rp, 4 * 128 * Rp,
-                            4 * 128 * Rp, 12 * (size_t)n, 12 * (size_t)n, 4};
+    const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 64 * Rp, 4 * kInPad * Rp, 4 * kStrain * Rp, 4 * kStrain * Rp,
+                            4 * 128 * Rp, 4 * 128 * Rp, 12 * (size_t)n, 12 * (size_t)n, 4};
     size_t off[11], o = 0;
     for (int i = 0; i < 11; ++i) {
         off[i] = o;
@@ -1306,9 +1435,9 @@ struct SgCtx {
     int mode;
     void* ws;
     SgLayout L;
-    bf16* feat;       // [rows_pad][32] (BF16 mode) / float (FP32 mode)
-    float* frames;    // [rows_pad][9]
-    float* mags;      // [rows_pad]
+    bf16* feat;       // [rows_pad][64] (BF16 mode) / float (FP32 mode)
+    float* xs;        // [rows_pad][18] element strains
+    float* ms;        // [rows_pad][18] rest moduli scales
     float* xh;        // [3][n] split positions (standalone feature calls)
     float* xl;
     void* h1;         // [rows_pad][128]
@@ -1322,11 +1451,10 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
 {
     const Params P = params_of(params);
     const int rows = c->d.rows_pad;
-    EpiForce ef{P.p + PFSI_SG_B3, P.p + PFSI_SG_OUT_SCALE, c->frames, c->mags, c->d.node, F, c->d.n_nodes};
     int rc;
     if (c->mode == PFSI_SG_FP32) {
-        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p + PFSI_SG_IN_SCALE,
-                                                                     (float*)c->feat, c->frames, c->mags);
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p, (float*)c->feat, c->xs,
+                                                                     c->ms);
         if ((rc = check_launch("surrogate: features"))) return rc;
         float *H1 = (float*)c->h1, *H2 = (float*)c->h2;
         if ((rc = gemm_f32((const float*)c->feat, kInPad, 1, P.p + PFSI_SG_W1, kInPad, 1, rows, kHid, kInPad, 1,
@@ -1335,13 +1463,13 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
         if ((rc = gemm_f32(H1, kHid, 1, P.p + PFSI_SG_W2, kHid, 1, rows, kHid, kHid, 1,
                            EpiHidden<float>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, s)))
             return rc;
-        k_gemm_f32_force<<<(rows + 127) / 128, 128, 0, s>>>(H2, P.p + PFSI_SG_W3, rows, ef);
-        return check_launch("surrogate: FP32 output layer");
+        k_sg_f32_forces<<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p, H2, F);
+        return check_launch("surrogate: FP32 output layer and forces");
     }
     const int tiles = rows / kTile;
     const int want = (tiles + kInferWG - 1) / kInferWG;
     const int grid = want < 148 ? want : 148;
-    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(xh, xl, c->d, P, ef, c->err);
+    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(xh, xl, c->d, P, F, c->err);
     return check_launch("surrogate: fused inference");
 }
 
@@ -1463,8 +1591,8 @@ extern "C" int sg_create(int n_nodes, int n_tri, const int* tri, const double* X
     c->ws = ws;
     c->L = L;
     c->feat = (bf16*)(b + L.feat);
-    c->frames = (float*)(b + L.frames);
-    c->mags = (float*)(b + L.mags);
+    c->xs = (float*)(b + L.xs);
+    c->ms = (float*)(b + L.ms);
     c->xh = (float*)(b + L.xh);
     c->xl = (float*)(b + L.xl);
     c->h1 = b + L.h1;
@@ -1488,25 +1616,25 @@ extern "C" int sg_rows(const sg_ctx* c, int* rows, const int** node)
     return PFSI_OK;
 }
 
-extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* frames, float* mags,
+extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void* feat, float* xs, float* ms,
                            void* stream)
 {
     NvtxRange nvtx_range("sg_features");
     if (!c || !params || !X) return set_error(PFSI_ERR_ARG, "sg_features: null argument");
     const Params P = params_of(params);
     cudaStream_t s = as_stream(stream);
-    float* fr = frames ? frames : c->frames;
-    float* mg = mags ? mags : c->mags;
     const int n3 = 3 * c->d.n_nodes;
     k_sg_split<<<(n3 + 255) / 256, 256, 0, s>>>(X, n3, c->xh, c->xl);
     int rc = check_launch("sg_features: split");
     if (rc) return rc;
+    float* x = xs ? xs : c->xs;
+    float* m = ms ? ms : c->ms;
     if (c->mode == PFSI_SG_FP32) {
-        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(
-            c->xh, c->xl, c->d, P.p + PFSI_SG_IN_SCALE, feat ? (float*)feat : (float*)c->feat, fr, mg);
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p,
+                                                                     feat ? (float*)feat : (float*)c->feat, x, m);
     } else {
-        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p + PFSI_SG_IN_SCALE,
-                                                                    feat ? (bf16*)feat : c->feat, fr, mg);
+        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p,
+                                                                    feat ? (bf16*)feat : c->feat, x, m);
     }
     return check_launch("sg_features");
 }
@@ -1523,14 +1651,14 @@ extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, c
     return launch_surrogate_forces(c, params, mem->xh, mem->xl, F, s);
 }
 
-extern "C" int sg_targets(const sg_ctx* c, const void* params, const float* F, const float* frames,
-                          const float* mags, float* target, void* stream)
+extern "C" int sg_targets(const sg_ctx* c, const void* params, float k_spring, float k_t, float k_b, const float* xs,
+                          const float* ms, float* target, void* stream)
 {
     NvtxRange nvtx_range("sg_targets");
-    if (!c || !params || !F || !target) return set_error(PFSI_ERR_ARG, "sg_targets: null argument");
+    if (!c || !params || !target) return set_error(PFSI_ERR_ARG, "sg_targets: null argument");
     const Params P = params_of(params);
     k_sg_targets<<<(c->d.rows + 127) / 128, 128, 0, as_stream(stream)>>>(
-        c->d, F, frames ? frames : c->frames, mags ? mags : c->mags, P.p + PFSI_SG_OUT_SCALE, target);
+        c->d, P.p, 0.5f * k_spring, k_t / 3.0f, 0.5f * k_b, xs ? xs : c->xs, ms ? ms : c->ms, target);
     return check_launch("sg_targets");
 }
 

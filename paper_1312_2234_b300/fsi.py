@@ -150,7 +150,7 @@ _SIGS = {
     "sg_rows": [P, ctypes.POINTER(c_int), ctypes.POINTER(P)],
     "sg_features": [P, P, P, P, P, P, P],
     "sg_membrane_forces": [P, P, P, P, P, P],
-    "sg_targets": [P, P, P, P, P, P, P],
+    "sg_targets": [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P, P],
     "sg_status": [P, ctypes.POINTER(c_int)],
     "sim_lb_ms": [P, ctypes.POINTER(ctypes.c_float)],
 }
@@ -833,8 +833,9 @@ class FemBending:
 # ---------------------------------------------------------------- learned membrane surrogate
 SG_BF16, SG_FP32 = 0, 1
 SG_MODE = {"bf16": SG_BF16, "fp32": SG_FP32}
-SG = dict(IN=27, IN_PAD=32, HID=128, OUT=3, OUT_PAD=16, W1=0, B1=4096, W2=4224, B2=20608, W3=20736, B3=22784,
-          N_TRAINED=22800, IN_SCALE=22800, OUT_SCALE=22832, N_FLOATS=22848, PARAM_BYTES=173312)
+SG = dict(IN=42, IN_PAD=64, HID=128, OUT=18, OUT_PAD=32, W1=0, B1=8192, W2=8320, B2=24704, W3=24832, B3=28928,
+          N_TRAINED=28960, IN_SHIFT=28960, IN_SCALE=29024, OUT_SCALE=29088, TGT_SCALE=29120, N_FLOATS=29152,
+          PARAM_BYTES=215040)
 
 
 class SurrogateParams:
@@ -854,38 +855,46 @@ class SurrogateParams:
         self.device = device
 
     def set(self, p):
-        """p: dict of numpy arrays W1 [128][27], b1, W2, b2, W3 [3][128], b3,
-        in_scale [27], out_scale [3] (the reference's layout)."""
+        """p: dict of numpy arrays W1 [128][42], b1, W2, b2, W3 [18][128], b3,
+        in_shift [42], in_scale [42], out_scale [18], tgt_scale [18] (the
+        reference's layout)."""
+        ni, no = SG["IN"], SG["OUT"]
         f = np.zeros(SG["N_FLOATS"], np.float32)
-        W1 = np.zeros((128, 32), np.float32)
-        W1[:, :27] = p["W1"]
+        W1 = np.zeros((128, SG["IN_PAD"]), np.float32)
+        W1[:, :ni] = p["W1"]
         f[SG["W1"]:SG["B1"]] = W1.ravel()
         f[SG["B1"]:SG["W2"]] = p["b1"]
         f[SG["W2"]:SG["B2"]] = np.asarray(p["W2"], np.float32).ravel()
         f[SG["B2"]:SG["W3"]] = p["b2"]
-        W3 = np.zeros((16, 128), np.float32)
-        W3[:3] = p["W3"]
+        W3 = np.zeros((SG["OUT_PAD"], 128), np.float32)
+        W3[:no] = p["W3"]
         f[SG["W3"]:SG["B3"]] = W3.ravel()
-        f[SG["B3"]:SG["B3"] + 3] = p["b3"]
-        f[SG["IN_SCALE"]:SG["IN_SCALE"] + 27] = p["in_scale"]
-        f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + 3] = p["out_scale"]
+        f[SG["B3"]:SG["B3"] + no] = p["b3"]
+        f[SG["IN_SHIFT"]:SG["IN_SHIFT"] + ni] = p.get("in_shift", np.zeros(ni))
+        f[SG["IN_SCALE"]:SG["IN_SCALE"] + ni] = p["in_scale"]
+        f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + no] = p["out_scale"]
+        f[SG["TGT_SCALE"]:SG["TGT_SCALE"] + no] = p.get("tgt_scale", np.ones(no))
         self.floats.copy_(torch.from_numpy(f))
         _call("sg_sync_shadows", _ptr(self.buf), None)
 
     def get(self):
+        ni, no, nip, nop = SG["IN"], SG["OUT"], SG["IN_PAD"], SG["OUT_PAD"]
         f = self.floats.cpu().numpy().astype(np.float64)
-        return dict(W1=f[SG["W1"]:SG["B1"]].reshape(128, 32)[:, :27].copy(), b1=f[SG["B1"]:SG["W2"]].copy(),
+        return dict(W1=f[SG["W1"]:SG["B1"]].reshape(128, nip)[:, :ni].copy(), b1=f[SG["B1"]:SG["W2"]].copy(),
                     W2=f[SG["W2"]:SG["B2"]].reshape(128, 128).copy(), b2=f[SG["B2"]:SG["W3"]].copy(),
-                    W3=f[SG["W3"]:SG["B3"]].reshape(16, 128)[:3].copy(), b3=f[SG["B3"]:SG["B3"] + 3].copy(),
-                    in_scale=f[SG["IN_SCALE"]:SG["IN_SCALE"] + 27].copy(),
-                    out_scale=f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + 3].copy())
+                    W3=f[SG["W3"]:SG["B3"]].reshape(nop, 128)[:no].copy(), b3=f[SG["B3"]:SG["B3"] + no].copy(),
+                    in_shift=f[SG["IN_SHIFT"]:SG["IN_SHIFT"] + ni].copy(),
+                    in_scale=f[SG["IN_SCALE"]:SG["IN_SCALE"] + ni].copy(),
+                    out_scale=f[SG["OUT_SCALE"]:SG["OUT_SCALE"] + no].copy(),
+                    tgt_scale=f[SG["TGT_SCALE"]:SG["TGT_SCALE"] + no].copy())
 
     def grads(self):
         """The last gradient as a dict in the reference's layout."""
+        ni, no, nip, nop = SG["IN"], SG["OUT"], SG["IN_PAD"], SG["OUT_PAD"]
         g = self.grad.cpu().numpy().astype(np.float64)
-        return dict(W1=g[SG["W1"]:SG["B1"]].reshape(128, 32)[:, :27].copy(), b1=g[SG["B1"]:SG["W2"]].copy(),
+        return dict(W1=g[SG["W1"]:SG["B1"]].reshape(128, nip)[:, :ni].copy(), b1=g[SG["B1"]:SG["W2"]].copy(),
                     W2=g[SG["W2"]:SG["B2"]].reshape(128, 128).copy(), b2=g[SG["B2"]:SG["W3"]].copy(),
-                    W3=g[SG["W3"]:SG["B3"]].reshape(16, 128)[:3].copy(), b3=g[SG["B3"]:SG["B3"] + 3].copy())
+                    W3=g[SG["W3"]:SG["B3"]].reshape(nop, 128)[:no].copy(), b3=g[SG["B3"]:SG["B3"] + no].copy())
 
 
 class SurrogateBatch:
@@ -943,18 +952,22 @@ class Surrogate:
         self.device = device
 
     def features(self, params, X, stream=None):
-        """(feat [rows_pad][32] BF16 or float, frames [rows_pad][9], mags [rows_pad])."""
+        """(feat [rows_pad][64] BF16 or float, strains xs [rows_pad][18],
+        rest moduli scales ms [rows_pad][18])."""
         dt = torch.bfloat16 if self.mode == "bf16" else torch.float32
-        feat = torch.zeros(self.rows_pad, 32, dtype=dt, device=self.device)
-        frames = torch.zeros(self.rows_pad, 9, dtype=torch.float32, device=self.device)
-        mags = torch.zeros(self.rows_pad, dtype=torch.float32, device=self.device)
-        _call("sg_features", self.h, _ptr(params.buf), _ptr(X), _ptr(feat), _ptr(frames), _ptr(mags),
-              _stream(stream))
-        return feat, frames, mags
+        feat = torch.zeros(self.rows_pad, SG["IN_PAD"], dtype=dt, device=self.device)
+        xs = torch.zeros(self.rows_pad, SG["OUT"], dtype=torch.float32, device=self.device)
+        ms = torch.zeros(self.rows_pad, SG["OUT"], dtype=torch.float32, device=self.device)
+        _call("sg_features", self.h, _ptr(params.buf), _ptr(X), _ptr(feat), _ptr(xs), _ptr(ms), _stream(stream))
+        return feat, xs, ms
 
-    def targets(self, params, F, frames, mags, stream=None):
-        t = torch.zeros(self.rows_pad, 3, dtype=torch.float32, device=self.device)
-        _call("sg_targets", self.h, _ptr(params.buf), _ptr(F), _ptr(frames), _ptr(mags), _ptr(t), _stream(stream))
+    def targets(self, params, membrane_params, xs, ms, stream=None):
+        """Training records [rows_pad][36] (a, b) of the plain local terms'
+        stresses (membrane_params: k_spring, k_t, k_b)."""
+        t = torch.zeros(self.rows_pad, 2 * SG["OUT"], dtype=torch.float32, device=self.device)
+        q = membrane_params
+        _call("sg_targets", self.h, _ptr(params.buf), float(q["k_spring"]), float(q["k_t"]), float(q["k_b"]),
+              _ptr(xs), _ptr(ms), _ptr(t), _stream(stream))
         return t
 
     def forces(self, params, membrane, X, F, stream=None):

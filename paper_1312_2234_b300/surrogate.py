@@ -1,26 +1,32 @@
 """Training and use of the learned membrane-force surrogate.
 
-The network (27 -> 128 -> 128 -> 3, GELU) stands for the local membrane terms
-(springs, local area, bending); the CUDA library computes its features, its
+The network (42 -> 128 -> 128 -> 18, GELU) sets the element stresses of the
+local membrane terms (springs, local area, bending) in a node-share split of
+their energy; the CUDA library computes its element strains and inputs, its
 forward and backward passes (BF16 tensor cores, or FP32 in check mode), Adam,
-and the surrogate force inside the coupled step.  This module only organises
-the data: membrane states from the plain method's trajectories (plus random
-perturbations of them, so that the training set also covers deformations
-larger than a short run reaches), the per-input and per-output scales, the
-batches, and the judge that compares the surrogate with the plain solver and
-falls back to it.
+the training records (the plain terms' stresses at a state), and the
+surrogate force inside the coupled step (stresses times the exact strain
+gradients).  This module only organises the data: membrane states from the
+plain method's trajectories (plus random perturbations of them, so that the
+training set also covers deformations a short run does not reach), the
+input, output and target scales, the batches, and the judge that compares
+the surrogate with the plain solver and falls back to it.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import torch
 
 from . import fsi
 
+N_IN, N_HID, N_OUT = 42, 128, 18
+
 
 def local_params(params):
     """Membrane coefficients of the local terms only (springs, local area,
-    bending): the force the surrogate is trained to reproduce."""
+    bending): the force the surrogate stands for."""
     q = dict(params)
     for k in ("k_s", "k_v", "morse_D", "rep_F0"):
         q[k] = 0.0
@@ -28,12 +34,15 @@ def local_params(params):
 
 
 def init_params(rng, in_scale=None, out_scale=None):
-    """Weights with variance 1/fan_in, zero biases (reference layout)."""
-    p = dict(W1=rng.standard_normal((128, 27)) / np.sqrt(27.0), b1=np.zeros(128),
-             W2=rng.standard_normal((128, 128)) / np.sqrt(128.0), b2=np.zeros(128),
-             W3=rng.standard_normal((3, 128)) / np.sqrt(128.0), b3=np.zeros(3))
-    p["in_scale"] = np.ones(27) if in_scale is None else np.asarray(in_scale, float)
-    p["out_scale"] = np.ones(3) if out_scale is None else np.asarray(out_scale, float)
+    """Weights with variance 1/fan_in, zero biases, zero input shifts, unit
+    target scales (reference layout)."""
+    p = dict(W1=rng.standard_normal((N_HID, N_IN)) / np.sqrt(N_IN), b1=np.zeros(N_HID),
+             W2=rng.standard_normal((N_HID, N_HID)) / np.sqrt(N_HID), b2=np.zeros(N_HID),
+             W3=rng.standard_normal((N_OUT, N_HID)) / np.sqrt(N_HID), b3=np.zeros(N_OUT))
+    p["in_shift"] = np.zeros(N_IN)
+    p["in_scale"] = np.ones(N_IN) if in_scale is None else np.asarray(in_scale, float)
+    p["out_scale"] = np.ones(N_OUT) if out_scale is None else np.asarray(out_scale, float)
+    p["tgt_scale"] = np.ones(N_OUT)
     return p
 
 
@@ -57,16 +66,16 @@ def perturbed_states(X_list, mesh, amplitudes, copies, rng):
 
 
 class Dataset:
-    """Features and local-frame targets of many membrane states, on the GPU."""
+    """Inputs and training records (stress targets) of many membrane states,
+    on the GPU.  membrane_params: the chamber's membrane coefficients (the
+    local ones, k_spring, k_t and k_b, give the stresses)."""
 
-    def __init__(self, sg, params, membrane_local, states, device="cuda"):
+    def __init__(self, sg, params, membrane_params, states, device="cuda"):
         feats, targets = [], []
-        F = torch.zeros(3 * sg.n, dtype=torch.float32, device=device)
         for X in states:
             Xd = torch.as_tensor(X, device=device)
-            feat, frames, mags = sg.features(params, Xd)
-            membrane_local.forces(Xd, F)
-            t = sg.targets(params, F, frames, mags)
+            feat, xs, ms = sg.features(params, Xd)
+            t = sg.targets(params, membrane_params, xs, ms)
             feats.append(feat[:sg.rows])
             targets.append(t[:sg.rows])
         self.feat = torch.cat(feats)
@@ -76,27 +85,74 @@ class Dataset:
         return self.feat.shape[0]
 
 
-def fit_scales(sg, params, membrane_local, states):
-    """Per-input and per-output scales from raw (unit-scale) statistics:
-    in_scale = 1 / std of each input over the states (1 where constant),
-    out_scale = std of each local force component."""
+KINDS = (slice(0, 6), slice(6, 12), slice(12, 18))   # stretch, area, bending outputs
+
+
+def fit_scales(sg, params, membrane_params, states):
+    """Rest-descriptor, output and target scales from raw (unit-scale)
+    statistics over the states, per kind of slot (the six slots of a kind
+    share them): shift and scale of a rest descriptor = its mean and 1 / its
+    std (1 where it does not vary); out_scale = the
+    least-squares modulus sum(y x m) / sum((x m)^2), so that the stresses are
+    about x m out_scale and the network output about 1; tgt_scale =
+    1 / rms(x m)."""
     p = params.get()
-    p["in_scale"] = np.ones(27)
-    p["out_scale"] = np.ones(3)
+    p["in_shift"] = np.zeros(N_IN)
+    p["in_scale"] = np.ones(N_IN)
+    p["out_scale"] = np.ones(N_OUT)
+    p["tgt_scale"] = np.ones(N_OUT)
     params.set(p)
-    raw = Dataset(sg, params, membrane_local, states)
-    f = raw.feat.float().cpu().numpy()[:, :27]
-    t = raw.target.cpu().numpy()
-    sd = f.std(0)
-    p["in_scale"] = np.where(sd > 1e-12, 1.0 / np.maximum(sd, 1e-30), 1.0)
-    ts = t.std(0)
-    p["out_scale"] = np.where(ts > 0, ts, 1.0)
+    raw = Dataset(sg, params, membrane_params, states)
+    f = raw.feat.float().cpu().numpy().astype(np.float64)
+    t = raw.target.cpu().numpy().astype(np.float64)
+    a, b = t[:, :N_OUT], t[:, N_OUT:]
+    present = f[:, 18:24] != 0          # L0/l > 0 in every present slot
+    for q in range(4):
+        cols = slice(18 + 6 * q, 24 + 6 * q)
+        v = f[:, cols][present]
+        mu, sd = float(v.mean()), float(v.std())
+        p["in_shift"][cols] = mu
+        p["in_scale"][cols] = 1.0 / sd if sd > 1e-6 * max(1.0, abs(mu)) else 1.0
+    for kind in KINDS:
+        ak, bk = a[:, kind][present], b[:, kind][present]
+        den = float(np.sum(ak * ak))
+        p["out_scale"][kind] = float(np.sum(ak * bk)) / den if den > 0 else 1.0
+        rms = math.sqrt(den / max(1, ak.size))
+        p["tgt_scale"][kind] = 1.0 / rms if rms > 0 else 1.0
     params.set(p)
     return p
 
 
-def train(params, data, steps, batch=1024, lr=1e-3, mode="bf16", seed=0, log_every=0):
-    """Adam on random batches of the dataset.  Returns [(step, loss)]."""
+def fit_strain_scales(sg, params, states):
+    """in_scale of the strain directions: 1 / rms of each kind's strains over
+    the states (present slots)."""
+    p = params.get()
+    sums = np.zeros(3)
+    counts = np.zeros(3)
+    for X in states:
+        feat, xs, ms = sg.features(params, torch.as_tensor(X, device=params.device))
+        x = xs[:sg.rows].cpu().numpy().astype(np.float64)
+        on = ms[:sg.rows, :6].cpu().numpy() > 0
+        for q, kind in enumerate(KINDS):
+            sums[q] += float(np.sum(x[:, kind][on] ** 2))
+            counts[q] += on.sum()
+    for q, kind in enumerate(KINDS):
+        rms = math.sqrt(sums[q] / max(1.0, counts[q]))
+        p["in_scale"][kind] = 1.0 / rms if rms > 0 else 1.0
+    params.set(p)
+    return p
+
+
+def prepare(sg, params, membrane_params, states):
+    """All scales (fit_scales, then fit_strain_scales) and the dataset."""
+    fit_scales(sg, params, membrane_params, states)
+    fit_strain_scales(sg, params, states)
+    return Dataset(sg, params, membrane_params, states)
+
+
+def train(params, data, steps, batch=1024, lr=1e-3, mode="bf16", seed=0, log_every=0, decay=True):
+    """Adam on random batches of the dataset (learning rate decayed to 2 % of
+    lr on a cosine schedule when decay).  Returns [(step, loss)]."""
     g = torch.Generator(device=data.feat.device)
     g.manual_seed(seed)
     B = fsi.SurrogateBatch(batch, device=data.feat.device)
@@ -107,7 +163,8 @@ def train(params, data, steps, batch=1024, lr=1e-3, mode="bf16", seed=0, log_eve
         feat = data.feat.index_select(0, idx).contiguous()
         tgt = data.target.index_select(0, idx).contiguous()
         loss = B.grad(params, feat, tgt, mode)
-        fsi.sg_adam(params, lr)
+        rate = lr * (0.02 + 0.98 * 0.5 * (1.0 + math.cos(math.pi * it / max(1, steps)))) if decay else lr
+        fsi.sg_adam(params, rate)
         if log_every and (it % log_every == 0 or it == steps - 1):
             hist.append((it, float(loss.item())))
     return hist

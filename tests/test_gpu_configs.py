@@ -73,7 +73,12 @@ def check_surrogate_sampled(w, X, params_np, n_sample=400, seed=0):
     pr = dict(params_np)
     for k in ("W1", "W2", "W3"):
         pr[k] = bf16_round(params_np[k])
-    ref = mlp.predict_forces(pr, X.reshape(3, n).T, m["X0"].reshape(3, n).T, ring, deg, nodes)
+    # a node's force comes from its own row and its neighbours' rows
+    Xn, X0n = X.reshape(3, n).T, m["X0"].reshape(3, n).T
+    ref = np.zeros((len(nodes), 3))
+    for q, v in enumerate(nodes):
+        rows = np.concatenate([[v], ring[v, :deg[v]]])
+        ref[q] = mlp.predict_forces(pr, Xn, X0n, ring, deg, rows)[v]
     assert sg.status() == 0
     # the global terms cancel to FP32 rounding of the larger of the two force
     # fields: bound the comparison by that as well
@@ -97,7 +102,7 @@ def test_surrogate_channel_full_size():
     _, wq = oracle.lattice()
     assert rel(sim.lattice.current().cpu().numpy(), ora.f.reshape(19, -1) - wq[:, None]) < 1e-5
     rng = np.random.default_rng(1)
-    p = surrogate.init_params(rng, in_scale=rng.uniform(0.5, 2, 27), out_scale=rng.uniform(0.5, 2, 3))
+    p = surrogate.init_params(rng, in_scale=rng.uniform(0.5, 2, 42), out_scale=rng.uniform(0.5, 2, 18))
     check_surrogate_sampled(w, sim.X.cpu().numpy(), p)
 
 
