@@ -613,13 +613,15 @@ struct RowRing {
 // Torsion of the chain r1 - 0 - r3 - r4 (points relative to the second):
 // F = r1, G = -r3, H = r4 - r3, A = F x G, B = H x G,
 // cos = A.B / (|A||B|), sin = (B x A).G / (|A||B||G|).
+// (The surrogate's geometry uses the hardware reciprocal square root and the
+// fast division intrinsic, ~2 ulp each.)
 __device__ __forceinline__ void torsion_cs(float3 r1, float3 r3, float3 r4, float& c, float& s)
 {
     const float3 G = scale3(-1.f, r3), H = sub3(r4, r3);
     const float3 A = cross3(r1, G), B = cross3(H, G);
-    const float ab = sqrtf(dot3(A, A) * dot3(B, B));
-    c = dot3(A, B) / ab;
-    s = dot3(cross3(B, A), G) / (ab * sqrtf(dot3(G, G)));
+    const float iab = rsqrtf(dot3(A, A) * dot3(B, B));
+    c = dot3(A, B) * iab;
+    s = dot3(cross3(B, A), G) * iab * rsqrtf(dot3(G, G));
 }
 
 // Its gradient with respect to the four points (Blondel and Karplus 1996).
@@ -627,9 +629,10 @@ __device__ __forceinline__ void torsion_grad(float3 r1, float3 r3, float3 r4, fl
 {
     const float3 G = scale3(-1.f, r3), H = sub3(r4, r3);
     const float3 A = cross3(r1, G), B = cross3(H, G);
-    const float A2 = dot3(A, A), B2 = dot3(B, B), gn = sqrtf(dot3(G, G));
-    const float FG = dot3(r1, G) / (A2 * gn), HG = dot3(H, G) / (B2 * gn);
-    const float ka = gn / A2, kb = gn / B2;
+    const float G2 = dot3(G, G), rg = rsqrtf(G2), gn = G2 * rg;
+    const float iA = __fdividef(1.0f, dot3(A, A)), iB = __fdividef(1.0f, dot3(B, B));
+    const float FG = dot3(r1, G) * iA * rg, HG = dot3(H, G) * iB * rg;
+    const float ka = gn * iA, kb = gn * iB;
     g[0] = scale3(-ka, A);
     g[3] = scale3(kb, B);
     g[1] = sub3(scale3(ka + FG, A), scale3(HG, B));
@@ -638,7 +641,8 @@ __device__ __forceinline__ void torsion_grad(float3 r1, float3 r3, float3 r4, fl
 
 // Element strains x[18] of surrogate row r (stretch, area strain and bending
 // angle of slots 0..5; zero for empty slots), its one-ring, and the rest
-// values of its slots.  xh, xl: positions split into hi/lo floats, [3][n].
+// values of its slots.  xa, xb: positions split into hi/lo floats, [n] (x, y,
+// z, 0).
 //
 // The strains are small differences of O(1) quantities, so they are formed
 // from small quantities only: d_k = e_k - e0_k from the split positions and
@@ -646,12 +650,12 @@ __device__ __forceinline__ void torsion_grad(float3 r1, float3 r3, float3 r4, fl
 // and for the fan triangle (c = e_k x e_{k+1}) |c|^2 - |c0|^2 = dc.(2 c0 + dc)
 // with dc = d_k x e0_{k+1} + e0_k x d_{k+1} + d_k x d_{k+1}.  The bending
 // angle is atan2 of sin and cos of phi - phi0 (absolute error ~1e-7).
-__device__ __forceinline__ void row_strains(const float* __restrict__ xh, const float* __restrict__ xl,
+__device__ __forceinline__ void row_strains(const float4* __restrict__ xa, const float4* __restrict__ xb,
                                             const SgDev& d, int r, RowRing& g, float* x, float* L0, float* S0,
                                             float* cph, float* sph, float& inv_l)
 {
-    const int n = d.n_nodes;
     const int v = d.node[r];
+    const float4 vh = xa[v], vl = xb[v];
     float rest[64];
 #pragma unroll
     for (int q = 0; q < 4; ++q) load16(d.rest + 64 * (size_t)r + 16 * q, rest + 16 * q);
@@ -664,13 +668,12 @@ __device__ __forceinline__ void row_strains(const float* __restrict__ xh, const 
         g.nb[k] = nb;
         e0[k] = f3(rest + 3 * k);
         if (nb >= 0) {
-            float c[3];
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const ff e = ff_diff(xh[a * n + nb], xl[a * n + nb], xh[a * n + v], xl[a * n + v]);
-                c[a] = (e.h - rest[3 * k + a]) + (e.l - rest[18 + 3 * k + a]);
-            }
-            dk[k] = make_float3(c[0], c[1], c[2]);
+            const float4 uh = xa[nb], ul = xb[nb];
+            const ff ex = ff_diff(uh.x, ul.x, vh.x, vl.x), ey = ff_diff(uh.y, ul.y, vh.y, vl.y),
+                     ez = ff_diff(uh.z, ul.z, vh.z, vl.z);
+            dk[k] = make_float3((ex.h - rest[3 * k]) + (ex.l - rest[18 + 3 * k]),
+                                (ey.h - rest[3 * k + 1]) + (ey.l - rest[18 + 3 * k + 1]),
+                                (ez.h - rest[3 * k + 2]) + (ez.l - rest[18 + 3 * k + 2]));
             deg = k + 1;
         } else {
             dk[k] = make_float3(0.f, 0.f, 0.f);
@@ -688,8 +691,9 @@ __device__ __forceinline__ void row_strains(const float* __restrict__ xh, const 
         if (k < deg) {
             // stretch of spoke k
             const float dl2 = dot3(dk[k], add3(scale3(2.f, e0[k]), dk[k]));
-            const float L = sqrtf(dot3(g.e[k], g.e[k]));
-            x[k] = dl2 / ((L + L0[k]) * L0[k]);
+            const float L2 = dot3(g.e[k], g.e[k]);
+            const float L = L2 * rsqrtf(L2);
+            x[k] = __fdividef(dl2, (L + L0[k]) * L0[k]);
             // area strain of the fan triangle (v, n_k, n_{k+1}); static
             // indices for the cyclic successor keep the arrays in registers
             const bool last = !(k < 5 && k + 1 < deg);
@@ -699,8 +703,9 @@ __device__ __forceinline__ void row_strains(const float* __restrict__ xh, const 
             const float3 dc = add3(add3(cross3(dk[k], e0n), cross3(e0[k], dn)), cross3(dk[k], dn));
             const float dS2 = dot3(dc, add3(scale3(2.f, c0), dc));
             const float3 cc = add3(c0, dc);
-            const float S = 0.5f * sqrtf(dot3(cc, cc));
-            x[6 + k] = dS2 / (4.0f * (S + S0[k]) * S0[k]);
+            const float c2 = dot3(cc, cc);
+            const float S = 0.5f * c2 * rsqrtf(c2);
+            x[6 + k] = __fdividef(dS2, 4.0f * (S + S0[k]) * S0[k]);
             // bending angle of spoke k: chain n_{k+1} - v - n_k - n_{k-1}
             const float3 en = last ? g.e[0] : g.e[k < 5 ? k + 1 : 0];
             const float3 ep = k > 0 ? g.e[k > 0 ? k - 1 : 0] : pick6(g.e, deg - 1);
@@ -726,7 +731,7 @@ __device__ __forceinline__ void row_inputs(const float* x, int deg, const float*
         f[j] = x[j] * scale[j];
         mm = fmaf(f[j], f[j], mm);
     }
-    const float inv = mm > 0.f ? 1.0f / sqrtf(mm) : 0.f;
+    const float inv = mm > 0.f ? rsqrtf(mm) : 0.f;
 #pragma unroll
     for (int j = 0; j < kStrain; ++j) f[j] *= inv;
 #pragma unroll
@@ -776,12 +781,12 @@ __device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, fl
             const float3 en = last ? g.e[0] : g.e[k < 5 ? k + 1 : 0];
             const float3 ep = k > 0 ? g.e[k > 0 ? k - 1 : 0] : pick6(g.e, g.deg - 1);
             // spring: -y_s dx_s/dX_{n_k} = -q_s o_s e/L, the opposite at v
-            const float3 fs = scale3(p[k] / sqrtf(dot3(ek, ek)), ek);
+            const float3 fs = scale3(p[k] * rsqrtf(dot3(ek, ek)), ek);
             Fn[k] = sub3(Fn[k], fs);
             Fi = add3(Fi, fs);
             // area: nhat x (.) / 2 with nhat = c / |c|
             const float3 c = cross3(ek, en);
-            const float h = 0.5f * p[6 + k] / sqrtf(dot3(c, c));
+            const float h = 0.5f * p[6 + k] * rsqrtf(dot3(c, c));
             Fi = sub3(Fi, scale3(h, cross3(c, sub3(en, ek))));
             Fn[k] = add3(Fn[k], scale3(h, cross3(c, en)));
             sub_at6(Fn, kn, scale3(h, cross3(c, ek)));
@@ -820,10 +825,20 @@ __global__ void k_sg_split(const double* __restrict__ X, int n3, float* __restri
     }
 }
 
+// hi/lo split positions [3][n] -> per-node float4 pairs (x, y, z, 0)
+__global__ void k_sg_pack(const float* __restrict__ xh, const float* __restrict__ xl, int n, float4* __restrict__ xa,
+                          float4* __restrict__ xb)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    xa[t] = make_float4(xh[t], xh[n + t], xh[2 * n + t], 0.f);
+    xb[t] = make_float4(xl[t], xl[n + t], xl[2 * n + t], 0.f);
+}
+
 // Inputs (feat [rows][64]), strains (xs [rows][18]) and rest moduli scales
 // (ms [rows][18]: L0^2, S0, 1; zero for empty slots) of every row.
 template <class T>
-__global__ void k_sg_features(const float* __restrict__ xh, const float* __restrict__ xl, SgDev d,
+__global__ void k_sg_features(const float4* __restrict__ xa, const float4* __restrict__ xb, SgDev d,
                               const float* __restrict__ P, T* __restrict__ feat, float* __restrict__ xs,
                               float* __restrict__ ms)
 {
@@ -831,7 +846,7 @@ __global__ void k_sg_features(const float* __restrict__ xh, const float* __restr
     if (r >= d.rows) return;
     RowRing g;
     float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l;
-    row_strains(xh, xl, d, r, g, x, L0, S0, cph, sph, inv_l);
+    row_strains(xa, xb, d, r, g, x, L0, S0, cph, sph, inv_l);
     float f[kInPad];
     row_inputs(x, g.deg, L0, S0, cph, sph, inv_l, P + PFSI_SG_IN_SHIFT, P + PFSI_SG_IN_SCALE, f);
 #pragma unroll
@@ -867,14 +882,14 @@ __global__ void k_sg_targets(SgDev d, const float* __restrict__ P, float cs, flo
 
 // FP32 check path, output layer and forces: o = W3 h2 + b3 (CUDA cores),
 // then the row's stress forces.
-__global__ void k_sg_f32_forces(const float* __restrict__ xh, const float* __restrict__ xl, SgDev d,
+__global__ void k_sg_f32_forces(const float4* __restrict__ xa, const float4* __restrict__ xb, SgDev d,
                                 const float* __restrict__ P, const float* __restrict__ H2, float* __restrict__ F)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
     RowRing g;
     float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l, q[kStrain];
-    row_strains(xh, xl, d, r, g, x, L0, S0, cph, sph, inv_l);
+    row_strains(xa, xb, d, r, g, x, L0, S0, cph, sph, inv_l);
     stress_factors(x, L0, P + PFSI_SG_OUT_SCALE, q);
     for (int j = 0; j < kStrain; ++j) {
         float acc = P[PFSI_SG_B3 + j];
@@ -961,13 +976,20 @@ __device__ __forceinline__ bool wg_and(bool v, int id)
     return r != 0;
 }
 
-__global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* __restrict__ xh,
-                                                                  const float* __restrict__ xl, SgDev d, Params P,
+__global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float4* __restrict__ xa,
+                                                                  const float4* __restrict__ xb, SgDev d, Params P,
                                                                   float* __restrict__ F, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bars[kInferWG];
     __shared__ uint32_t tmem_sh;
+    // input shift and scale, output scale (read by every row)
+    __shared__ float s_shift[kInPad], s_scale[kInPad], s_out[kOutPad];
+    for (int i = threadIdx.x; i < kInPad; i += blockDim.x) {
+        s_shift[i] = P.p[PFSI_SG_IN_SHIFT + i];
+        s_scale[i] = P.p[PFSI_SG_IN_SCALE + i];
+    }
+    for (int i = threadIdx.x; i < kOutPad; i += blockDim.x) s_out[i] = P.p[PFSI_SG_OUT_SCALE + i];
     const int wg = threadIdx.x >> 7, t = threadIdx.x & (kTile - 1);
     const int bar_id = 1 + wg;
     uint64_t* bar = &bars[wg];
@@ -1010,9 +1032,9 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float* _
         g.deg = 0;
         if (row < d.rows) {
             float x[kStrain], L0[6], S0[6], cph[6], sph[6], inv_l;
-            row_strains(xh, xl, d, row, g, x, L0, S0, cph, sph, inv_l);
-            row_inputs(x, g.deg, L0, S0, cph, sph, inv_l, P.p + PFSI_SG_IN_SHIFT, P.p + PFSI_SG_IN_SCALE, f);
-            stress_factors(x, L0, P.p + PFSI_SG_OUT_SCALE, q);
+            row_strains(xa, xb, d, row, g, x, L0, S0, cph, sph, inv_l);
+            row_inputs(x, g.deg, L0, S0, cph, sph, inv_l, s_shift, s_scale, f);
+            stress_factors(x, L0, s_out, q);
         } else {
 #pragma unroll
             for (int k = 0; k < kInPad; ++k) f[k] = 0.f;
@@ -1412,20 +1434,22 @@ int build_rings(int n, int nt, const int* tri, const double* X0, const unsigned 
 }
 
 struct SgLayout {
-    size_t node, ring, rest, feat, xs, ms, h1, h2, xh, xl, err, total;
+    size_t node, ring, rest, feat, xs, ms, h1, h2, xh, xl, xa, xb, err, total;
 };
 // rows: surrogate rows; n: mesh nodes
 SgLayout sg_layout(int rows, int n)
 {
     const size_t Rp = ((size_t)rows + kTile - 1) / kTile * kTile;
     const size_t sizes[] = {4 * Rp, 4 * 6 * Rp, 4 * 64 * Rp, 4 * kInPad * Rp, 4 * kStrain * Rp, 4 * kStrain * Rp,
-                            4 * 128 * Rp, 4 * 128 * Rp, 12 * (size_t)n, 12 * (size_t)n, 4};
-    size_t off[11], o = 0;
-    for (int i = 0; i < 11; ++i) {
+                            4 * 128 * Rp, 4 * 128 * Rp, 12 * (size_t)n, 12 * (size_t)n, 16 * (size_t)n,
+                            16 * (size_t)n, 4};
+    constexpr int kParts = sizeof(sizes) / sizeof(sizes[0]);
+    size_t off[kParts], o = 0;
+    for (int i = 0; i < kParts; ++i) {
         off[i] = o;
         o += (sizes[i] + 255) / 256 * 256;
     }
-    return {off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], off[8], off[9], off[10], o};
+    return {off[0], off[1], off[2], off[3], off[4], off[5], off[6], off[7], off[8], off[9], off[10], off[11], off[12], o};
 }
 
 }  // namespace
@@ -1440,6 +1464,8 @@ struct SgCtx {
     float* ms;        // [rows_pad][18] rest moduli scales
     float* xh;        // [3][n] split positions (standalone feature calls)
     float* xl;
+    float4* xa;       // [n] split positions per node (hi, lo)
+    float4* xb;
     void* h1;         // [rows_pad][128]
     void* h2;
     int* err;
@@ -1451,10 +1477,12 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
 {
     const Params P = params_of(params);
     const int rows = c->d.rows_pad;
-    int rc;
+    k_sg_pack<<<(c->d.n_nodes + 255) / 256, 256, 0, s>>>(xh, xl, c->d.n_nodes, c->xa, c->xb);
+    int rc = check_launch("surrogate: positions");
+    if (rc) return rc;
     if (c->mode == PFSI_SG_FP32) {
-        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p, (float*)c->feat, c->xs,
-                                                                     c->ms);
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p, (float*)c->feat,
+                                                                     c->xs, c->ms);
         if ((rc = check_launch("surrogate: features"))) return rc;
         float *H1 = (float*)c->h1, *H2 = (float*)c->h2;
         if ((rc = gemm_f32((const float*)c->feat, kInPad, 1, P.p + PFSI_SG_W1, kInPad, 1, rows, kHid, kInPad, 1,
@@ -1463,13 +1491,13 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
         if ((rc = gemm_f32(H1, kHid, 1, P.p + PFSI_SG_W2, kHid, 1, rows, kHid, kHid, 1,
                            EpiHidden<float>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, s)))
             return rc;
-        k_sg_f32_forces<<<(c->d.rows + 127) / 128, 128, 0, s>>>(xh, xl, c->d, P.p, H2, F);
+        k_sg_f32_forces<<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p, H2, F);
         return check_launch("surrogate: FP32 output layer and forces");
     }
     const int tiles = rows / kTile;
     const int want = (tiles + kInferWG - 1) / kInferWG;
     const int grid = want < 148 ? want : 148;
-    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(xh, xl, c->d, P, F, c->err);
+    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(c->xa, c->xb, c->d, P, F, c->err);
     return check_launch("surrogate: fused inference");
 }
 
@@ -1595,6 +1623,8 @@ extern "C" int sg_create(int n_nodes, int n_tri, const int* tri, const double* X
     c->ms = (float*)(b + L.ms);
     c->xh = (float*)(b + L.xh);
     c->xl = (float*)(b + L.xl);
+    c->xa = (float4*)(b + L.xa);
+    c->xb = (float4*)(b + L.xb);
     c->h1 = b + L.h1;
     c->h2 = b + L.h2;
     c->err = (int*)(b + L.err);
@@ -1627,13 +1657,15 @@ extern "C" int sg_features(sg_ctx* c, const void* params, const double* X, void*
     k_sg_split<<<(n3 + 255) / 256, 256, 0, s>>>(X, n3, c->xh, c->xl);
     int rc = check_launch("sg_features: split");
     if (rc) return rc;
+    k_sg_pack<<<(c->d.n_nodes + 255) / 256, 256, 0, s>>>(c->xh, c->xl, c->d.n_nodes, c->xa, c->xb);
+    if ((rc = check_launch("sg_features: positions"))) return rc;
     float* x = xs ? xs : c->xs;
     float* m = ms ? ms : c->ms;
     if (c->mode == PFSI_SG_FP32) {
-        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p,
+        k_sg_features<float><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p,
                                                                      feat ? (float*)feat : (float*)c->feat, x, m);
     } else {
-        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xh, c->xl, c->d, P.p,
+        k_sg_features<bf16><<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p,
                                                                     feat ? (bf16*)feat : c->feat, x, m);
     }
     return check_launch("sg_features");

@@ -51,11 +51,17 @@ def bf16_round(a):
     return t.numpy().astype(np.float64)
 
 
-def check_surrogate_sampled(w, X, params_np, n_sample=400, seed=0):
+def check_surrogate_sampled(w, X, params_np, n_sample=400, seed=0, amp=3e-3):
     """Surrogate force (exact global terms removed) on sampled nodes against
-    the reference network evaluated node by node on the BF16-rounded weights."""
+    the reference network evaluated node by node on the BF16-rounded weights,
+    at X plus a deformation of the membrane nodes (Gaussian, amp lattice
+    units): the surrogate's bending angles are accurate to ~1e-7 absolute, so
+    a state a few steps from rest (strains ~1e-7) would compare rounding."""
     m = w["mesh"]
     n = w["M"]
+    mem_nodes = np.asarray(m["is_membrane"]).astype(bool)
+    D = np.random.default_rng(seed + 1).standard_normal((3, n)) * mem_nodes
+    X = (np.asarray(X).reshape(3, n) + amp * D).ravel()
     sg = fsi.Surrogate(m, "bf16")
     params = fsi.SurrogateParams()
     params.set(params_np)
