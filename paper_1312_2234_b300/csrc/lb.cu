@@ -197,13 +197,40 @@ __device__ __forceinline__ void halo_load(const float4* __restrict__ m, int k, i
         if (off[u] >= 0) r[u] = plane[off[u]];
 }
 
+// Ring position of halo cell h (row-major over the tile plus halo).  The
+// two-cell tiles (PairTile) keep each row's odd-x and even-x halo cells in
+// two halves (odd first): a thread's two cells are x-adjacent, so with a
+// row-major ring the 32 lanes of a warp would read records 32 bytes apart
+// (twice the shared-memory wavefronts); split by parity, the lanes read
+// consecutive records for every direction.
+template <int TY_>
+struct PairTile;
+template <class T>
+struct IsPairTile {
+    static constexpr bool value = false;
+};
+template <int TY>
+struct IsPairTile<PairTile<TY>> {
+    static constexpr bool value = true;
+};
+template <class T>
+__device__ __forceinline__ int ring_pos(int h)
+{
+    if constexpr (IsPairTile<T>::value) {
+        const int hy = h / T::HX, hx = h - hy * T::HX;
+        return hy * T::HX + ((hx & 1) ? (hx >> 1) : T::HX / 2 + (hx >> 1));
+    } else {
+        return h;
+    }
+}
+
 template <class T>
 __device__ __forceinline__ void halo_store(Ring<T>& ring, int slot, const float4* r)
 {
 #pragma unroll
     for (int u = 0; u < T::Halo; ++u) {
         const int h = threadIdx.x + u * T::Threads;
-        if (h < T::Plane) ring.pj[slot][h] = split_record(r[u]);
+        if (h < T::Plane) ring.pj[slot][ring_pos<T>(h)] = split_record(r[u]);
     }
 }
 
@@ -418,7 +445,7 @@ __global__ void __launch_bounds__(T::Threads, 768 / T::Threads) k_lb_step_mixed(
 template <int TY_>
 struct PairTile {
     static constexpr int TX = 64, TY = TY_;
-    static constexpr int HX = TX + 2, HY = TY + 2;
+    static constexpr int HX = TX + 2, HY = TY + 2;   // HX even: the parity halves of a ring row are equal
     static constexpr int Plane = HX * HY;
     static constexpr int Threads = 32 * TY;
     static constexpr int Halo = (Plane + Threads - 1) / Threads;
@@ -489,23 +516,34 @@ __device__ __forceinline__ float2 pull_pair(const uint16_t* __restrict__ nin, in
                 dup2(inv_scale));
 }
 
-// F += E_q of the source cells (as add_feq, both cells: own, own + 1)
+// Offset in the parity-split ring row of the halo cell dx cells right of a
+// thread's first cell (halo x = 2 tx + 1 + dx, dx in -1..2), from the
+// thread's base (ty + 1) HX + tx.
+template <class T, int dx>
+__device__ __forceinline__ constexpr int pair_off()
+{
+    return ((1 + dx) & 1) ? ((1 + dx) >> 1) : T::HX / 2 + ((1 + dx) >> 1);
+}
+
+// F += E_q of the source cells (as add_feq, both cells; own = the thread's
+// ring base (ty + 1) HX + tx)
 template <int q, class T>
 __device__ __forceinline__ void add_feq2(float2& F, const Ring<T>& ring, int sm, int s0, int sp, int own, int k,
                                          int nz, float3 utop)
 {
     if (czq(q) == 1 && k == 0) {
-        const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
+        const float4 a = ring.pj[s0][own + pair_off<T, 0>()], b = ring.pj[s0][own + pair_off<T, 1>()];
         F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)), F);
     } else if (czq(q) == -1 && k == nz - 1) {
         const float cu = cxq(q) * utop.x + cyq(q) * utop.y;
-        const float4 a = ring.pj[s0][own], b = ring.pj[s0][own + 1];
+        const float4 a = ring.pj[s0][own + pair_off<T, 0>()], b = ring.pj[s0][own + pair_off<T, 1>()];
         F = fma2(dup2(wq(q)), make_float2(split_eq<oppq(q)>(a), split_eq<oppq(q)>(b)),
                  fma2(dup2(6.0f * wq(q)), dup2(cu), F));
     } else {
         const int slot = czq(q) == 1 ? sm : (czq(q) == -1 ? sp : s0);
-        const int src = own - cyq(q) * T::HX - cxq(q);
-        const float4 a = ring.pj[slot][src], b = ring.pj[slot][src + 1];
+        const int src = own - cyq(q) * T::HX;
+        const float4 a = ring.pj[slot][src + pair_off<T, -cxq(q)>()],
+                     b = ring.pj[slot][src + pair_off<T, 1 - cxq(q)>()];
         // E / w = P + cj (1 + cj / 2), both cells at once
         const float2 cj = make_float2(cdot<q>(a.y, a.z, a.w), cdot<q>(b.y, b.z, b.w));
         const float2 e = fma2(cj, fma2(cj, dup2(0.5f), dup2(1.0f)), make_float2(a.x, b.x));
@@ -728,7 +766,7 @@ __device__ __forceinline__ void mixed_pair_column(Ring<T>& ring, const uint16_t*
     const int yp = (j >= ny - 1) ? 0 : j + 1;
     const float keep = 1.0f - omega;
     const float scale = 1.0f / inv_scale;
-    const int own = (ty + 1) * T::HX + 2 * tx + 1;
+    const int own = (ty + 1) * T::HX + tx;   // ring base of the thread's cells (parity-split rows)
 
     int off[T::Halo];
 #pragma unroll
@@ -837,7 +875,7 @@ __device__ __forceinline__ void mixed_staged_column(char* smem, const uint16_t* 
     const int yp = (j >= ny - 1) ? 0 : j + 1;
     const float keep = 1.0f - omega;
     const float scale = 1.0f / inv_scale;
-    const int own = (ty + 1) * T::HX + 2 * tx + 1;
+    const int own = (ty + 1) * T::HX + tx;   // ring base of the thread's cells (parity-split rows)
 
     // this thread's window chunks: value offsets without the plane term
     // (copy u = threadIdx.x + m Threads is slot s, row r, chunk c; the
