@@ -391,7 +391,7 @@ __device__ __forceinline__ void mixed_column(Ring<T>& ring, const uint16_t* __re
                 F3.z = fmaf(3.0f, gg.z, F3.z);
             }
             // V = 3v = 3 (m + F/2) / rho; F3 = 3F
-            const float i3rho = 3.0f / rho;
+            const float i3rho = __fdividef(3.0f, rho);   // fast division (~2 ulp), as every 16-bit kernel
             const float vx = fmaf(F3.x, 1.0f / 6.0f, mx) * i3rho;
             const float vy = fmaf(F3.y, 1.0f / 6.0f, my) * i3rho;
             const float vz = fmaf(F3.z, 1.0f / 6.0f, mz) * i3rho;
@@ -720,7 +720,7 @@ __device__ __forceinline__ void pair_plane(const Ring<T>& ring, const uint16_t* 
         Fy = fma2(dup2(3.0f), make_float2(g0.y, g1.y), Fy);
         Fz = fma2(dup2(3.0f), make_float2(g0.z, g1.z), Fz);
     }
-    const float2 i3rho = make_float2(3.0f / rho.x, 3.0f / rho.y);
+    const float2 i3rho = make_float2(__fdividef(3.0f, rho.x), __fdividef(3.0f, rho.y));   // fast division (~2 ulp), as every 16-bit kernel
     const float2 vx = mul2(fma2(Fx, dup2(1.0f / 6.0f), mx), i3rho);
     const float2 vy = mul2(fma2(Fy, dup2(1.0f / 6.0f), my), i3rho);
     const float2 vz = mul2(fma2(Fz, dup2(1.0f / 6.0f), mz), i3rho);

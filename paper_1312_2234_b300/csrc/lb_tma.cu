@@ -440,7 +440,7 @@ __device__ __forceinline__ void cell_step(const StepArgs& a, char* smem, int buf
         F3.z = fmaf(3.0f, gg.z, F3.z);
     }
     // V = 3v = 3 (m + F/2) / rho; F3 = 3F
-    const float i3rho = 3.0f / rho;
+    const float i3rho = __fdividef(3.0f, rho);   // fast division (~2 ulp), as every 16-bit kernel
     const float vx = fmaf(F3.x, 1.0f / 6.0f, mx) * i3rho;
     const float vy = fmaf(F3.y, 1.0f / 6.0f, my) * i3rho;
     const float vz = fmaf(F3.z, 1.0f / 6.0f, mz) * i3rho;
