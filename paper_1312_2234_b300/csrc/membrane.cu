@@ -364,10 +364,12 @@ __device__ __forceinline__ void mem_elements(const MemCtx& c, int bx)
         plt = c.tri_plt[k];
         const TriTerms T = tri_terms(X, c.tri[3 * k], c.tri[3 * k + 1], c.tri[3 * k + 2], c.plt_anchor[plt],
                                      c.tri_rest[2 * k], c.tri_rest[2 * k + 1], P);
-        float4* out = c.tout + 4 * (size_t)k;
+        if (!c.tri_sums_only) {
+            float4* out = c.tout + 4 * (size_t)k;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) out[r] = make_float4(T.g[r].x, T.g[r].y, T.g[r].z, T.tsc);
-        out[3] = make_float4(T.nn.x * (1.0f / 6.0f), T.nn.y * (1.0f / 6.0f), T.nn.z * (1.0f / 6.0f), 0.f);
+            for (int r = 0; r < 3; ++r) out[r] = make_float4(T.g[r].x, T.g[r].y, T.g[r].z, T.tsc);
+            out[3] = make_float4(T.nn.x * (1.0f / 6.0f), T.nn.y * (1.0f / 6.0f), T.nn.z * (1.0f / 6.0f), 0.f);
+        }
         V6 = T.V6;
         dS = ff{T.ds, 0.f};
     } else if (t < c.ne + c.nt + c.np) {
@@ -439,7 +441,7 @@ __device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c
         // flight together; sums in list order, longer lists finish in loops
         constexpr int kE = 3, kT = 2, kP = 2;
         const int eb = c.esl_off[v] + q, ee = c.skip_edges ? eb : c.esl_off[v + 1];
-        const int tb = c.tcl_off[v] + q, te = c.tcl_off[v + 1];
+        const int tb = c.tcl_off[v] + q, te = c.skip_tris ? tb : c.tcl_off[v + 1];
         const int pb = c.psl_off[v] + q, pe = c.psl_off[v + 1];
         int ei[kE], ti[kT], pi[kP];
 #pragma unroll
@@ -838,6 +840,23 @@ int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s,
     g.ne = 0;            // element ids start at the triangles
     g.skip_edges = 1;
     return launch_membrane_forces(&g, X, F, s, presplit);
+}
+
+int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
+{
+    MemCtx g = *c;
+    g.p.k_spring = 0.f;
+    g.p.k_t = 0.f;
+    g.p.k_b = 0.f;
+    g.ne = 0;            // element ids start at the triangles
+    g.skip_edges = 1;
+    g.skip_tris = 1;     // the nodes take no triangle slots ...
+    g.tri_sums_only = 1; // ... and the triangles write none, only the per-platelet sums
+    if (g.np > 0) return launch_membrane_forces(&g, X, F, s, presplit);
+    // no Morse pairs: F starts at zero and the caller adds the wall term
+    int rc = launch_scalars(&g, X, s, presplit);
+    if (!rc) rc = check_cuda(cudaMemsetAsync(F, 0, sizeof(float) * 3 * (size_t)g.n, s), "membrane: clear forces");
+    return rc;
 }
 
 int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)

@@ -324,6 +324,8 @@ struct MemCtx {
     double* cpart;         // [3 * n_chunks] per-chunk sums of the advected positions (tracking)
     int n_chunks;
     int skip_edges;        // nonzero: edge elements (springs, bending) are neither computed nor gathered
+    int skip_tris;         // nonzero: the nodes gather no triangle slots (global area and volume elsewhere)
+    int tri_sums_only;     // nonzero: triangles add to the per-platelet sums but write no slots
     const int* plt_anchor; // [nplt]
     // per platelet (first node, nodes, first edge, edges), (first triangle,
     // triangles, first Morse pair, pairs) for the fused pass, or null when
@@ -440,6 +442,13 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
 // The global terms only (global area, volume, Morse pairs, wall): what the
 // learned surrogate does not stand for.  Writes F.
 int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
+// Morse pairs and wall repulsion into F (overwritten; a mesh without Morse
+// pairs gets F = 0 and leaves the wall term to the caller too), and the
+// per-platelet coefficients k_s (S - S0)/S0, k_v (V - V0)/V0 into c->coef:
+// the global area and volume forces themselves are left to the caller (the
+// surrogate applies them per node from its one-ring).  Also splits X into
+// c->xh, c->xl.
+int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
 // step_dev: device step counter (advanced by one after the update) or null
 // to use step_host.
@@ -447,10 +456,10 @@ int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
                       unsigned long long* step_dev, cudaStream_t s);
 
 struct SgCtx;
-// Adds the surrogate's local membrane forces to F; xh, xl: the positions split
-// into hi/lo floats ([3][n], as the membrane passes leave them).
-int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const float* xl, float* F,
-                            cudaStream_t s);
+// Adds the surrogate's local membrane forces and the exact global area and
+// volume forces to F, after launch_membrane_remainder(mem) (which leaves the
+// split positions mem->xh, xl and the platelet coefficients mem->coef).
+int launch_surrogate_forces(SgCtx* c, const void* params, const MemCtx* mem, float* F, cudaStream_t s);
 SgCtx* sg_internal(sg_ctx* c);
 int sg_node_count(const SgCtx* c);
 

@@ -70,8 +70,8 @@ int enqueue_front(SimCtx* c, cudaStream_t s, bool presplit = false)
 {
     int rc;
     if (c->sg) {
-        rc = launch_membrane_global(c->mem, c->X, c->F, s, presplit);
-        if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->mem->xh, c->mem->xl, c->F, s);
+        rc = launch_membrane_remainder(c->mem, c->X, c->F, s, presplit);
+        if (!rc) rc = launch_surrogate_forces(c->sg, c->sg_params, c->mem, c->F, s);
     } else {
         rc = launch_membrane_forces(c->mem, c->X, c->F, s, presplit);
     }

@@ -762,10 +762,49 @@ __device__ __forceinline__ void stress_factors(const float* x, const float* L0, 
     }
 }
 
+// The exact global area and volume terms of a row's own node: the platelet's
+// coefficients cS = k_s (S - S0)/S0, cV = k_v (V - V0)/V0 and the node's
+// position relative to the platelet's anchor (Eq. 4-5: F_v -= cS dS/dX_v +
+// cV dV/dX_v, summed over the node's fan triangles).
+struct RowGlobal {
+    float cS, cV;
+    float3 r;
+    float wall;     // z force of the wall repulsion (Section 3.4.1) when the surrogate applies it, else 0
+};
+
+// The membrane context's data the global terms read.
+struct GlobalArgs {
+    const float2* coef;     // [nplt] (cS, cV)
+    const int* node_plt;    // [n]
+    const int* anchor;      // [nplt]
+    int wall;               // nonzero: add the wall repulsion (a mesh without Morse pairs)
+    float rep_F0, rep_tau, rep_eps_min, z_wall;
+};
+
+__device__ __forceinline__ RowGlobal row_global(const float4* __restrict__ xa, const float4* __restrict__ xb,
+                                                const GlobalArgs& ga, int v)
+{
+    const int q = ga.node_plt[v];
+    const float2 cf = ga.coef[q];
+    const int o = ga.anchor[q];
+    const float4 vh = xa[v], vl = xb[v], oh = xa[o], ol = xb[o];
+    const ff dx = ff_diff(vh.x, vl.x, oh.x, ol.x), dy = ff_diff(vh.y, vl.y, oh.y, ol.y),
+             dz = ff_diff(vh.z, vl.z, oh.z, ol.z);
+    float wall = 0.f;
+    if (ga.wall && ga.rep_F0 != 0.f) {   // the plain nodes pass's term, F0 tau / (e^{tau eps} - 1)
+        const float eps = fmaxf((vh.z - ga.z_wall) + vl.z, ga.rep_eps_min);
+        wall = ga.rep_F0 * ga.rep_tau / expm1f(ga.rep_tau * eps);
+    }
+    return {cf.x, cf.y, make_float3(dx.h + dx.l, dy.h + dy.l, dz.h + dz.l), wall};
+}
+
 // F -= sum_j p_j G_j of one row (p = q o), added to the node and its
-// one-ring with atomic adds.  Area gradient of corner a of the fan triangle
-// (v, n_k, n_{k+1}): (1/2) nhat x (P_{a+2} - P_{a+1}).
-__device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, float* __restrict__ F, int n)
+// one-ring with atomic adds, plus the node's global area and volume terms.
+// Area gradient of corner a of the fan triangle (v, n_k, n_{k+1}):
+// (1/2) nhat x (P_{a+2} - P_{a+1}); volume gradient of corner v:
+// (1/6) (P_{n_k} - o) x (P_{n_{k+1}} - o) = (1/6) (c + r x (e_{k+1} - e_k)).
+__device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, const RowGlobal& gl,
+                                            float* __restrict__ F, int n)
 {
     float3 Fi = make_float3(0.f, 0.f, 0.f);
     float3 Fn[6];
@@ -784,10 +823,14 @@ __device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, fl
             const float3 fs = scale3(p[k] * rsqrtf(dot3(ek, ek)), ek);
             Fn[k] = sub3(Fn[k], fs);
             Fi = add3(Fi, fs);
-            // area: nhat x (.) / 2 with nhat = c / |c|
+            // area: nhat x (.) / 2 with nhat = c / |c| (the own corner also
+            // takes the global area coefficient), and the own volume term
             const float3 c = cross3(ek, en);
-            const float h = 0.5f * p[6 + k] * rsqrtf(dot3(c, c));
-            Fi = sub3(Fi, scale3(h, cross3(c, sub3(en, ek))));
+            const float ic = rsqrtf(dot3(c, c));
+            const float h = 0.5f * p[6 + k] * ic;
+            const float3 de = sub3(en, ek);
+            Fi = sub3(Fi, scale3(0.5f * (p[6 + k] + gl.cS) * ic, cross3(c, de)));
+            Fi = sub3(Fi, scale3(gl.cV * (1.0f / 6.0f), add3(c, cross3(gl.r, de))));
             Fn[k] = add3(Fn[k], scale3(h, cross3(c, en)));
             sub_at6(Fn, kn, scale3(h, cross3(c, ek)));
             // bending: chain n_{k+1} - v - n_k - n_{k-1}
@@ -802,7 +845,7 @@ __device__ __forceinline__ void row_scatter(const RowRing& g, const float* p, fl
     }
     atomicAdd(F + g.v, Fi.x);
     atomicAdd(F + n + g.v, Fi.y);
-    atomicAdd(F + 2 * n + g.v, Fi.z);
+    atomicAdd(F + 2 * n + g.v, Fi.z + gl.wall);
 #pragma unroll
     for (int k = 0; k < 6; ++k)
         if (k < g.deg) {
@@ -883,7 +926,8 @@ __global__ void k_sg_targets(SgDev d, const float* __restrict__ P, float cs, flo
 // FP32 check path, output layer and forces: o = W3 h2 + b3 (CUDA cores),
 // then the row's stress forces.
 __global__ void k_sg_f32_forces(const float4* __restrict__ xa, const float4* __restrict__ xb, SgDev d,
-                                const float* __restrict__ P, const float* __restrict__ H2, float* __restrict__ F)
+                                const float* __restrict__ P, const float* __restrict__ H2, GlobalArgs ga,
+                                float* __restrict__ F)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d.rows) return;
@@ -896,7 +940,7 @@ __global__ void k_sg_f32_forces(const float4* __restrict__ xa, const float4* __r
         for (int k = 0; k < kHid; ++k) acc = fmaf(H2[(size_t)r * kHid + k], P[PFSI_SG_W3 + j * kHid + k], acc);
         q[j] *= acc;
     }
-    row_scatter(g, q, F, d.n_nodes);
+    row_scatter(g, q, row_global(xa, xb, ga, g.v), F, d.n_nodes);
 }
 
 // ------------------------------------------------------------------ fused inference
@@ -978,7 +1022,8 @@ __device__ __forceinline__ bool wg_and(bool v, int id)
 
 __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float4* __restrict__ xa,
                                                                   const float4* __restrict__ xb, SgDev d, Params P,
-                                                                  float* __restrict__ F, int* __restrict__ err)
+                                                                  GlobalArgs ga, float* __restrict__ F,
+                                                                  int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ uint64_t bars[kInferWG];
@@ -1094,7 +1139,7 @@ __global__ void __launch_bounds__(kInferWG * kTile, 1) k_sg_infer(const float4* 
 #pragma unroll
             for (int j = 16; j < kStrain; ++j) q[j] *= o[j - 16];
         }
-        if (row < d.rows) row_scatter(g, q, F, d.n_nodes);
+        if (row < d.rows) row_scatter(g, q, row_global(xa, xb, ga, g.v), F, d.n_nodes);
     }
     if (!ok && t == 0) atomicExch(err, 1);
     tc_fence_before();
@@ -1472,12 +1517,13 @@ struct SgCtx {
 };
 
 // Surrogate forces added to F (the exact global terms must already be in F).
-int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const float* xl, float* F,
-                            cudaStream_t s)
+int launch_surrogate_forces(SgCtx* c, const void* params, const MemCtx* mem, float* F, cudaStream_t s)
 {
     const Params P = params_of(params);
     const int rows = c->d.rows_pad;
-    k_sg_pack<<<(c->d.n_nodes + 255) / 256, 256, 0, s>>>(xh, xl, c->d.n_nodes, c->xa, c->xb);
+    const GlobalArgs ga{mem->coef,       mem->node_plt,       mem->plt_anchor,     mem->np == 0 ? 1 : 0,
+                        mem->p.rep_F0, mem->p.rep_tau, mem->p.rep_eps_min, mem->p.z_wall};
+    k_sg_pack<<<(c->d.n_nodes + 255) / 256, 256, 0, s>>>(mem->xh, mem->xl, c->d.n_nodes, c->xa, c->xb);
     int rc = check_launch("surrogate: positions");
     if (rc) return rc;
     if (c->mode == PFSI_SG_FP32) {
@@ -1491,13 +1537,13 @@ int launch_surrogate_forces(SgCtx* c, const void* params, const float* xh, const
         if ((rc = gemm_f32(H1, kHid, 1, P.p + PFSI_SG_W2, kHid, 1, rows, kHid, kHid, 1,
                            EpiHidden<float>{P.p + PFSI_SG_B2, nullptr, H2, nullptr, 0}, s)))
             return rc;
-        k_sg_f32_forces<<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p, H2, F);
+        k_sg_f32_forces<<<(c->d.rows + 127) / 128, 128, 0, s>>>(c->xa, c->xb, c->d, P.p, H2, ga, F);
         return check_launch("surrogate: FP32 output layer and forces");
     }
     const int tiles = rows / kTile;
     const int want = (tiles + kInferWG - 1) / kInferWG;
     const int grid = want < 148 ? want : 148;
-    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(c->xa, c->xb, c->d, P, F, c->err);
+    k_sg_infer<<<grid, kInferWG * kTile, kInferSmem, s>>>(c->xa, c->xb, c->d, P, ga, F, c->err);
     return check_launch("surrogate: fused inference");
 }
 
@@ -1678,9 +1724,9 @@ extern "C" int sg_membrane_forces(sg_ctx* c, const void* params, mem_ctx* mem, c
     if (!c || !params || !mem || !X || !F) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: null argument");
     if (mem->n != c->d.n_nodes) return set_error(PFSI_ERR_ARG, "sg_membrane_forces: node count differs");
     cudaStream_t s = as_stream(stream);
-    int rc = launch_membrane_global(mem, X, F, s);   // also splits X into mem->xh, mem->xl
+    int rc = launch_membrane_remainder(mem, X, F, s);   // also splits X into mem->xh, mem->xl
     if (rc) return rc;
-    return launch_surrogate_forces(c, params, mem->xh, mem->xl, F, s);
+    return launch_surrogate_forces(c, params, mem, F, s);
 }
 
 extern "C" int sg_targets(const sg_ctx* c, const void* params, float k_spring, float k_t, float k_b, const float* xs,

@@ -194,10 +194,16 @@ def test_adam_matches_reference():
         assert np.max(np.abs(got[k] - pf[k])) < 1e-5 * max(1.0, np.abs(pf[k]).max()), k
 
 
-def test_global_terms_are_exact():
+@pytest.mark.parametrize("n_sce", [8, 0])
+def test_global_terms_are_exact(n_sce):
     """A network with zero output leaves exactly the plain solver's global
-    area, volume, Morse and wall terms."""
-    w, m, X = mesh_and_state(level=2)
+    area, volume, Morse and wall terms (the area and volume terms and, on a
+    mesh without Morse pairs, the wall term applied by the surrogate kernel
+    per node)."""
+    w = workload.tiny(seed=4, level=2, n_sce=n_sce)
+    m = w["mesh"]
+    X = w["X"] + 0.03 * np.random.default_rng(4).standard_normal(w["X"].shape)
+    assert (len(m["pairs"]) > 0) == (n_sce > 0)
     params = fsi.SurrogateParams()
     p = mlp.init_params(np.random.default_rng(2))
     p["W3"][:] = 0.0
