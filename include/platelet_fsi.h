@@ -588,8 +588,11 @@ int sg_rows(const sg_ctx* ctx, int* rows, const int** node);
  * buffer), its element strains into xs (float [rows][18]; NULL: own) and the
  * rest moduli scales (L0^2, S0, 1) into ms (float [rows][18]; NULL: own). */
 int sg_features(sg_ctx* ctx, const void* params, const double* X, void* feat, float* xs, float* ms, void* stream);
-/* F = exact global terms (membrane_forces with the spring, local-area and
- * bending coefficients set to zero) + surrogate local forces. */
+/* F = exact global terms + surrogate local forces: Morse pairs (and, on a
+ * mesh with Morse pairs, the wall term) by the plain passes, the global area
+ * and volume forces (Eq. 4-5, the platelet coefficients from the plain
+ * triangle sums) per node from its fan in the surrogate kernel, which also
+ * adds the wall term on a mesh without Morse pairs.  F is overwritten. */
 int sg_membrane_forces(sg_ctx* ctx, const void* params, mem_ctx* mem, const double* X, float* F, void* stream);
 /* Training record of every row from its strains xs and moduli scales ms
  * (sg_features; NULL: the context's own) and the membrane coefficients of

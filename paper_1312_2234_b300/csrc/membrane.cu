@@ -831,17 +831,6 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
                       "membrane_forces");
 }
 
-int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
-{
-    MemCtx g = *c;
-    g.p.k_spring = 0.f;
-    g.p.k_t = 0.f;
-    g.p.k_b = 0.f;
-    g.ne = 0;            // element ids start at the triangles
-    g.skip_edges = 1;
-    return launch_membrane_forces(&g, X, F, s, presplit);
-}
-
 int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
 {
     MemCtx g = *c;

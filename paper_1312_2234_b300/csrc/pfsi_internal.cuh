@@ -439,9 +439,6 @@ int launch_ib_interp(LbCtx* c, double* X, float* U, int M, int advect, const int
 // presplit: mem->xh, xl hold the split of X and the per-platelet sums are
 // clear (written by the previous step's interpolation): no split pass.
 int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
-// The global terms only (global area, volume, Morse pairs, wall): what the
-// learned surrogate does not stand for.  Writes F.
-int launch_membrane_global(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
 // Morse pairs and wall repulsion into F (overwritten; a mesh without Morse
 // pairs gets F = 0 and leaves the wall term to the caller too), and the
 // per-platelet coefficients k_s (S - S0)/S0, k_v (V - V0)/V0 into c->coef:
