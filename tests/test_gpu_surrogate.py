@@ -194,8 +194,8 @@ def test_adam_matches_reference():
         assert np.max(np.abs(got[k] - pf[k])) < 1e-5 * max(1.0, np.abs(pf[k]).max()), k
 
 
-@pytest.mark.parametrize("n_sce", [8, 0])
-def test_global_terms_are_exact(n_sce):
+@pytest.mark.parametrize("n_sce,mode", [(8, "bf16"), (0, "bf16"), (0, "fp32")])
+def test_global_terms_are_exact(n_sce, mode):
     """A network with zero output leaves exactly the plain solver's global
     area, volume, Morse and wall terms (the area and volume terms and, on a
     mesh without Morse pairs, the wall term applied by the surrogate kernel
@@ -209,7 +209,7 @@ def test_global_terms_are_exact(n_sce):
     p["W3"][:] = 0.0
     p["b3"][:] = 0.0
     params.set(p)
-    sg = fsi.Surrogate(m, "bf16")
+    sg = fsi.Surrogate(m, mode)
     mem = fsi.Membrane(w["membrane"], m)
     Xd = torch.as_tensor(X).cuda()
     F = torch.zeros(3 * sg.n, dtype=torch.float32, device="cuda")
