@@ -661,7 +661,8 @@ def run_surrogate(args, w_channel, sim_channel, dev, stream):
             fsi.sim_set_surrogate(sim, sg4, params)
         sim.step(warm)
         t = timed_steps(lambda: sim.step(1), steps, stream)
-        out[mode] = {"value": N * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps}
+        out[mode] = {"value": N * steps / t / 1e6, "unit": "MLUPS", "ms_per_step": 1e3 * t / steps,
+                     "node_updates_per_s": w4["M"] * steps / t}
         sim.step(after)
         final[mode] = (sim.X.clone(), sim.U.clone())
         if mode == "surrogate":
