@@ -831,6 +831,50 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
                       "membrane_forces");
 }
 
+// The remainder's node pass (Morse pairs and wall repulsion only): one thread
+// per node, its pair slots summed in list order (the first four loaded
+// together).
+__global__ void __launch_bounds__(256) k_mem_nodes_pairs(float* __restrict__ F, const __grid_constant__ MemCtx c)
+{
+    pdl_wait();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= c.n) return;
+    const int n = c.n;
+    const int pb = c.psl_off[v], pe = c.psl_off[v + 1];
+    constexpr int kP = 4;
+    int pi[kP];
+    float4 pf[kP];
+#pragma unroll
+    for (int u = 0; u < kP; ++u) pi[u] = pb + u < pe ? c.psl[pb + u] : -1;
+#pragma unroll
+    for (int u = 0; u < kP; ++u) pf[u] = pi[u] >= 0 ? c.pout[pi[u] >> 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+    for (int u = 0; u < kP; ++u)
+        if (pi[u] >= 0) {
+            const float sg = (pi[u] & 1) ? -1.f : 1.f;
+            fx += sg * pf[u].x;
+            fy += sg * pf[u].y;
+            fz += sg * pf[u].z;
+        }
+    for (int q = pb + kP; q < pe; ++q) {
+        const int code = c.psl[q];
+        const float4 f = c.pout[code >> 1];
+        const float sg = (code & 1) ? -1.f : 1.f;
+        fx += sg * f.x;
+        fy += sg * f.y;
+        fz += sg * f.z;
+    }
+    const mem_params P = c.p;
+    if (c.is_mem[v] && P.rep_F0 != 0.f) {   // wall repulsion (Section 3.4.1), as the full node pass
+        const float eps = fmaxf((c.xh[2 * n + v] - P.z_wall) + c.xl[2 * n + v], P.rep_eps_min);
+        fz += P.rep_F0 * P.rep_tau / expm1f(P.rep_tau * eps);
+    }
+    F[v] = fx;
+    F[n + v] = fy;
+    F[2 * n + v] = fz;
+}
+
 int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit)
 {
     MemCtx g = *c;
@@ -841,11 +885,13 @@ int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t
     g.skip_edges = 1;
     g.skip_tris = 1;     // the nodes take no triangle slots ...
     g.tri_sums_only = 1; // ... and the triangles write none, only the per-platelet sums
-    if (g.np > 0) return launch_membrane_forces(&g, X, F, s, presplit);
-    // no Morse pairs: F starts at zero and the caller adds the wall term
     int rc = launch_scalars(&g, X, s, presplit);
-    if (!rc) rc = check_cuda(cudaMemsetAsync(F, 0, sizeof(float) * 3 * (size_t)g.n, s), "membrane: clear forces");
-    return rc;
+    if (rc) return rc;
+    if (g.np > 0)
+        return check_cuda(launch_pdl(k_mem_nodes_pairs, dim3((g.n + 255) / 256), dim3(256), 0, s, F, g),
+                          "membrane: pairs and wall");
+    // no Morse pairs: F starts at zero and the caller adds the wall term
+    return check_cuda(cudaMemsetAsync(F, 0, sizeof(float) * 3 * (size_t)g.n, s), "membrane: clear forces");
 }
 
 int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)
