@@ -419,14 +419,18 @@ __global__ void k_mem_coef(const __grid_constant__ MemCtx c)
     mem_coef(c, blockIdx.x);
 }
 
-// Pass 3: one thread per node sums its element contributions and applies the
+// Pass 3: the lanes of a node sum its element contributions and apply the
 // per-platelet global area and volume coefficients and the wall repulsion.
 // kNodeLanes lanes per node share its element slots (strided), then reduce by
 // shuffles in a fixed order; the first lane adds the wall term and writes.
 // Each lane first loads its first list entries of all three lists, then all
 // their slots, so that its gathers are in flight together (a plain loop
 // waits for each list entry, then its slot: channel step 61.8 -> 59.8 us).
-constexpr int kNodeLanes = 4;
+// Two lanes per node, six edge, three triangle and two pair entries each in
+// flight: full-scale membrane call 474 -> 435 us against four lanes with
+// three, two and two (each lane also loads the node's list offsets and
+// coefficients; one lane with twelve, six and three: 443 us).
+constexpr int kNodeLanes = 2;
 
 __device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c, int bx)
 {
@@ -439,7 +443,7 @@ __device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c
     if (on) {
         // the lane's first entries of each list, then their slots, all in
         // flight together; sums in list order, longer lists finish in loops
-        constexpr int kE = 3, kT = 2, kP = 2;
+        constexpr int kE = 6, kT = 3, kP = 2;
         const int eb = c.esl_off[v] + q, ee = c.skip_edges ? eb : c.esl_off[v + 1];
         const int tb = c.tcl_off[v] + q, te = c.skip_tris ? tb : c.tcl_off[v + 1];
         const int pb = c.psl_off[v] + q, pe = c.psl_off[v + 1];
