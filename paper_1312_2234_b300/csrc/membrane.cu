@@ -258,7 +258,10 @@ __device__ __forceinline__ float3 ff3_float(ff3 a) { return make_float3(ff_float
 //             d = r - r0 likewise.
 // At most 48 registers (five blocks of 256 per SM; 8 bytes spilled): the
 // channel's 178,000 elements then fit one wave, and the 500-platelet step is
-// 24 us faster than at the 58 registers the compiler picks unbounded.
+// 24 us faster than at the 58 registers the compiler picks unbounded.  The
+// single-chamber kernel takes six blocks (40 registers, 24 bytes spilled):
+// full-scale step 1.596 -> 1.590 ms (seven or eight blocks spill ~160 bytes:
+// 1.614 ms).
 // One edge's contributions: out[0..3] = the force on chain vertex k, i, j, l
 // (spring on i, j; bending -dE/dphi grad phi on all four); a boundary edge
 // (q.w < 0) has the spring only, out[0] = out[3] = 0.  q: indices into X.
@@ -396,7 +399,7 @@ __device__ __forceinline__ void mem_elements(const MemCtx& c, int bx)
     }
 }
 
-__global__ void __launch_bounds__(256, 5) k_mem_elements(const __grid_constant__ MemCtx c)
+__global__ void __launch_bounds__(256, 6) k_mem_elements(const __grid_constant__ MemCtx c)
 {
     pdl_wait();
     mem_elements(c, blockIdx.x);
