@@ -9,15 +9,15 @@
 // The support wraps in x and y and is cut at the walls (cells with k outside
 // [0, nz) are skipped), so spreading and interpolation stay adjoint.
 //
-// Blocking: a block of 128 threads takes a chunk of up to 128 consecutive
+// Blocking: a block of 64 threads takes a chunk of up to 64 consecutive
 // nodes, one thread per node (consecutive nodes of a platelet mesh lie close
 // together; the coupled step passes chunks that never straddle two
-// platelets, the public calls use fixed chunks of 128).  When the bounding
-// box of the chunk's supports fits the shared tile (1536 cells, no wider than
+// platelets, the public calls use fixed chunks of 64).  When the bounding
+// box of the chunk's supports fits the shared tile (768 cells, no wider than
 // the grid):
 //   spreading  accumulates F_m * w in the tile in 32-bit fixed point (shared
 //              integer atomics run several times faster than shared float
-//              atomics on this part), scaled per block by 2^33 / (128 max|F|):
+//              atomics on this part), scaled per block by 2^33 / (64 max|F|):
 //              every weight is at most 1/8, so no cell sum can reach 2^30,
 //              and the rounding stays below ~1e-7 of the block's largest
 //              force.  Each lane starts its 16 support rows at a
@@ -43,11 +43,14 @@ namespace {
 
 constexpr int kChunk = kIbChunk;            // nodes (= threads) per block
 constexpr int kWarps = kChunk / 32;
-// 3 int planes (spread) or float4 cells (interp).  Chunks in Morton order of
-// the platelet's rest shape have boxes of ~340 cells on average (largest
-// ~1200 on the 500-platelet channel); 1536 cells (18 KB spreading, 24 KB
-// interpolation) let 8-9 blocks share an SM, where a 4096-cell tile held 3.
-constexpr int kTileCells = 1536;
+// 3 int planes (spread) or float4 cells (interp).  Chunks of 128 nodes in
+// Morton order of the platelet's rest shape have boxes of ~340 cells on
+// average (largest ~1200 on the 500-platelet channel); a 1536-cell tile let
+// 8-9 blocks share an SM where a 4096-cell tile held 3.  Chunks of 64 nodes
+// with a 768-cell tile (9 KB spreading, 12 KB interpolation) make the
+// full-scale step 1.590 -> 1.570 ms (512 cells the same; 64 nodes with 1024
+// cells 1.578, 32 nodes with 640 cells 1.598, 256 nodes with 3072 cells 1.623).
+constexpr int kTileCells = 768;
 constexpr int kMaxRows = kTileCells / 4;    // a box is at least 4 cells wide
 constexpr size_t kTileBytes = kTileCells * sizeof(float4);
 
@@ -193,7 +196,7 @@ __device__ __forceinline__ void ib_spread_block(const double* __restrict__ X, co
         float fmax = 0.f;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) fmax = fmaxf(fmax, wmax[w]);
-        const float scale = fmax > 0.f ? 8589934592.0f / ((float)kChunk * fmax) : 0.f;  // 2^33 / (128 max|F|)
+        const float scale = fmax > 0.f ? 8589934592.0f / ((float)kChunk * fmax) : 0.f;  // 2^33 / (kChunk max|F|)
         const int plane = b.ex * b.ey * b.ez;
         for (int i = threadIdx.x; i < 3 * plane; i += kChunk) itile[i] = 0;
         row_table(b, nx, ny, rowbase);

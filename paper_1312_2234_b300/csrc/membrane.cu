@@ -333,11 +333,15 @@ __device__ __forceinline__ TriTerms tri_terms(const Split& X, int a, int b, int 
 }
 
 // Morse force on the first node of a pair (the second takes its opposite).
+// A pair whose distance overflows FP32 (a node of a run that blew up, far
+// away) gets the force the oracle's FP64 gives it there, zero, instead of the
+// NaN of inf / inf.
 __device__ __forceinline__ float3 pair_force(const Split& X, int i, int j, float4 pr, const mem_params& P)
 {
     const ff3 d = X.diff(j, i);
     const float qs = ff3_sqnorm_minus(d, {pr.x, pr.y});
     const float r = sqrtf(pr.x + qs);
+    if (!(r <= 3.0e38f)) return make_float3(0.f, 0.f, 0.f);
     const float ad = P.morse_a * (qs / (r + pr.z));
     const float sc = 2.0f * P.morse_D * P.morse_a * (-expm1f(-ad)) * expf(-ad) / r;
     const float3 R = ff3_float(d);

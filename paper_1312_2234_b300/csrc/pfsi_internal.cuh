@@ -385,7 +385,7 @@ __device__ __forceinline__ bool coord_in_range(double x) { return fabs(x) < kFar
 
 // Nodes per block of the IB kernels (also the largest chunk of the membrane's
 // chunk table).
-constexpr int kIbChunk = 128;
+constexpr int kIbChunk = 64;
 
 // One-time kernel attributes (large dynamic shared memory) of the IB kernels.
 int ib_prepare();

@@ -42,9 +42,9 @@ def support_rows(X, ny, nz):
     return rows
 
 
-def expected_rows(X, nx, ny, nz, chunk=128, cap=1536):
-    """Rows the spreading kernel flags: per chunk of 128 nodes, every row of the
-    supports' bounding box when the box fits the 1536-cell tile and is no
+def expected_rows(X, nx, ny, nz, chunk=64, cap=768):
+    """Rows the spreading kernel flags: per chunk of 64 nodes, every row of the
+    supports' bounding box when the box fits the 768-cell tile and is no
     wider than the grid, else the support rows."""
     rows = set()
     for s0 in range(0, X.shape[1], chunk):
