@@ -438,6 +438,7 @@ __global__ void k_mem_coef(const __grid_constant__ MemCtx c)
 // three, two and two (each lane also loads the node's list offsets and
 // coefficients; one lane with twelve, six and three: 443 us).
 constexpr int kNodeLanes = 2;
+constexpr int kNodeThreads = 64;   // 32 nodes a block: full-scale step 1.573 -> 1.568 ms against 128
 
 __device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c, int bx)
 {
@@ -539,7 +540,7 @@ __device__ __forceinline__ void mem_nodes(float* __restrict__ F, const MemCtx& c
     F[2 * n + v] = fz;
 }
 
-__global__ void __launch_bounds__(128) k_mem_nodes(float* __restrict__ F, const __grid_constant__ MemCtx c)
+__global__ void __launch_bounds__(kNodeThreads) k_mem_nodes(float* __restrict__ F, const __grid_constant__ MemCtx c)
 {
     pdl_wait();
     mem_nodes(F, c, blockIdx.x);
@@ -583,14 +584,14 @@ __global__ void k_mem_coef_multi(const __grid_constant__ Multi<MemCtx> t)
     mem_coef(t.a[e], blockIdx.x - t.first[e]);
 }
 
-__global__ void __launch_bounds__(128) k_mem_nodes_multi(const __grid_constant__ Multi<NodesArgs> t)
+__global__ void __launch_bounds__(kNodeThreads) k_mem_nodes_multi(const __grid_constant__ Multi<NodesArgs> t)
 {
     pdl_wait();
     const int e = multi_entry(t, blockIdx.x);
     mem_nodes(t.a[e].F, t.a[e].c, blockIdx.x - t.first[e]);
 }
 
-int node_blocks(const MemCtx* c) { return (int)(((long long)c->n * kNodeLanes + 127) / 128); }
+int node_blocks(const MemCtx* c) { return (int)(((long long)c->n * kNodeLanes + kNodeThreads - 1) / kNodeThreads); }
 
 // ------------------------------------------------------------------ fused pass
 // One block per platelet does all three passes for its nodes: the hi/lo
@@ -838,7 +839,7 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
                           "membrane_forces: fused pass");
     int rc = launch_scalars(c, X, s, presplit);
     if (rc) return rc;
-    return check_cuda(launch_pdl(k_mem_nodes, dim3(node_blocks(c)), dim3(128), 0, s, F, *c),
+    return check_cuda(launch_pdl(k_mem_nodes, dim3(node_blocks(c)), dim3(kNodeThreads), 0, s, F, *c),
                       "membrane_forces");
 }
 
@@ -936,7 +937,7 @@ int launch_membrane_forces_multi(const Chamber* ch, int n, cudaStream_t s)
     for (const auto& t : coef)
         if (!rc) rc = check_cuda(launch_pdl(k_mem_coef_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: coef");
     for (const auto& t : nodes)
-        if (!rc) rc = check_cuda(launch_pdl(k_mem_nodes_multi, dim3(t.blocks()), dim3(128), 0, s, t), "membrane: nodes");
+        if (!rc) rc = check_cuda(launch_pdl(k_mem_nodes_multi, dim3(t.blocks()), dim3(kNodeThreads), 0, s, t), "membrane: nodes");
     for (size_t u = 0; u < fused.size() && !rc; ++u)
         rc = check_cuda(launch_pdl(k_mem_fused_multi, dim3(fused[u].blocks()), dim3(kFusedThreads), fused_bytes[u], s,
                                    fused[u]),
