@@ -64,8 +64,13 @@ __global__ void k_bond_forces(const __grid_constant__ BondCtx c, const double* _
     bond_forces(c, X, F, M, blockIdx.x);
 }
 
+// site_plt, plt_far (or null): a site of a platelet out of reach this step
+// (k_plt_far) that breaks goes straight to free (-1): the proposal pass,
+// which turns the ruptured state -2 into -1 without a proposal, skips that
+// platelet's blocks.
 __device__ __forceinline__ void bond_rupture(const BondCtx& c, const double* __restrict__ X, int M, uint64_t step_host,
-                                             const unsigned long long* __restrict__ step_dev, int bx)
+                                             const unsigned long long* __restrict__ step_dev, int bx,
+                                             const int* __restrict__ site_plt, const int* __restrict__ plt_far)
 {
     const int s = bx * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
@@ -79,17 +84,19 @@ __device__ __forceinline__ void bond_rupture(const BondCtx& c, const double* __r
     const double koff_dt = __dmul_rn(c.p.koff0_dt, exp(__ddiv_rn(__dmul_rn(c.p.gamma, Fb), c.p.kT)));
     const double Pr = -expm1(-koff_dt);
     if (uniform53(c.p.seed, (uint32_t)s, step, 0u) < Pr) {
-        c.bound[s] = -2;  // free, but not before the next step
+        const int q = site_plt ? site_plt[s] : -1;
+        c.bound[s] = q >= 0 && plt_far[q] ? -1 : -2;  // -2: free, but not before the next step
         atomicSub(&c.lig_count[lig], 1);
         atomicAdd(&c.counters[0], 1ull);
     }
 }
 
 __global__ void k_bond_rupture(const __grid_constant__ BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
-                               const unsigned long long* __restrict__ step_dev)
+                               const unsigned long long* __restrict__ step_dev, const int* __restrict__ site_plt,
+                               const int* __restrict__ plt_far)
 {
     pdl_wait();
-    bond_rupture(c, X, M, step_host, step_dev, blockIdx.x);
+    bond_rupture(c, X, M, step_host, step_dev, blockIdx.x, site_plt, plt_far);
 }
 
 // Candidate (di, dj) of the window around node (i0, j0): the ligand there,
@@ -121,24 +128,35 @@ __device__ __forceinline__ void propose_candidate(const BondCtx& c, const SitePo
 
 // kR: the window half-width r at compile time (1: d_capture <= 1, the
 // configurations' 0.64), or 0 to take it from the context at run time.
+// site_plt, plt_far, block_plt (or null): the sites of a platelet out of
+// reach this step (k_plt_far) return before their triangle and weights are
+// loaded, and a block of 256 sites all of one such platelet returns at once
+// (its ruptures of this step went straight to -1; between steps no site
+// holds -2).
 template <int kR>
 __device__ __forceinline__ void bond_propose(const BondCtx& c, const double* __restrict__ X, int M, uint64_t step_host,
-                                             const unsigned long long* __restrict__ step_dev, int blk)
+                                             const unsigned long long* __restrict__ step_dev, int blk,
+                                             const int* __restrict__ site_plt, const int* __restrict__ plt_far,
+                                             const int* __restrict__ block_plt)
 {
+    if (block_plt) {
+        const int pb = __ldg(block_plt + blk);
+        if (pb >= 0 && plt_far[pb]) return;
+    }
     const int s = blk * blockDim.x + threadIdx.x;
     if (s >= c.R) return;
-    // the site's state, triangle and weights are loaded together (the height
-    // test below needs all but the state)
     const int b = c.bound[s];
-    const int t = __ldg(c.site_tri + s);
-    const double w0 = __ldg(c.site_w + 2 * s), w1 = __ldg(c.site_w + 2 * s + 1);
     const int bridged = c.partner ? c.partner[s] : -1;
+    const int q = site_plt ? __ldg(site_plt + s) : -1;
     if (b == -2) {
         c.bound[s] = -1;
         return;
     }
     if (b >= 0) return;
-    if (bridged >= 0) return;   // bridged to another platelet: one bond per site
+    if (bridged >= 0) return;
+    if (q >= 0 && plt_far[q]) return;
+    const int t = __ldg(c.site_tri + s);
+    const double w0 = __ldg(c.site_w + 2 * s), w1 = __ldg(c.site_w + 2 * s + 1);
     const bond_params& p = c.p;
     // Out of reach of every ligand: the bond length is at least the height
     // above the wall plane (the margin covers the last-ulp rounding of the
@@ -176,10 +194,99 @@ __device__ __forceinline__ void bond_propose(const BondCtx& c, const double* __r
 
 template <int kR>
 __global__ void k_bond_propose(const __grid_constant__ BondCtx c, const double* __restrict__ X, int M, uint64_t step_host,
-                               const unsigned long long* __restrict__ step_dev)
+                               const unsigned long long* __restrict__ step_dev, const int* __restrict__ site_plt,
+                               const int* __restrict__ plt_far, const int* __restrict__ block_plt)
 {
     pdl_wait();
-    bond_propose<kR>(c, X, M, step_host, step_dev, blockIdx.x);
+    bond_propose<kR>(c, X, M, step_host, step_dev, blockIdx.x, site_plt, plt_far, block_plt);
+}
+
+// One block per platelet: plt_far[p] = 1 if every node of platelet p lies more
+// than d_capture (plus a margin) above the wall plane.  The sites kept by
+// launch_site_platelets are combinations of one platelet's triangle corners
+// with nonnegative weights summing to one, so a site's FP64 height is at
+// least its platelet's lowest node height less the rounding of the
+// combination (below 1e-9 while every |z| < 1e6, hence the 1e-6 margin and
+// the 1e6 limit): the proposal's per-site height test rejects every such site,
+// and skipping them changes no decision.  A NaN or far coordinate keeps its
+// platelet in.
+constexpr int kFarThreads = 512;
+__global__ void __launch_bounds__(kFarThreads)
+    k_plt_far(const FarSites f, const double* __restrict__ X, int M, double z_wall, double d_capture)
+{
+    pdl_wait();
+    const int p = blockIdx.x;
+    const int2 r = f.plt_nodes[p];
+    const double* Z = X + 2 * (size_t)M + r.x;
+    double m = INFINITY;
+    int bad = 0;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < r.y; k += kFarThreads) {
+        const double z = Z[k];
+        if (fabs(z) < 1e6)
+            m = fmin(m, z);
+        else
+            bad = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    __shared__ double wm[kFarThreads / 32];
+    __shared__ int wb[kFarThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        wm[threadIdx.x >> 5] = m;
+        wb[threadIdx.x >> 5] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kFarThreads / 32; ++w) {
+            m = fmin(m, wm[w]);
+            bad |= wb[w];
+        }
+        f.plt_far[p] = !bad && (m - z_wall > d_capture * (1.0 + 1e-12) + 1e-6);
+    }
+}
+
+__global__ void k_site_platelets(const __grid_constant__ BondCtx c, const int* __restrict__ node_plt,
+                                 int* __restrict__ site_plt)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= c.R) return;
+    const int t = c.site_tri[s];
+    const int a = c.tri[3 * t], b = c.tri[3 * t + 1], cc = c.tri[3 * t + 2];
+    const double w0 = c.site_w[2 * s], w1 = c.site_w[2 * s + 1];
+    const double w2 = __dsub_rn(__dsub_rn(1.0, w0), w1);   // as site_coord forms it
+    const int p = node_plt[a];
+    const bool one = p >= 0 && node_plt[b] == p && node_plt[cc] == p;
+    site_plt[s] = one && w0 >= 0.0 && w1 >= 0.0 && w2 >= 0.0 ? p : -1;
+}
+
+// plt_nodes[p] = (first node, nodes) of platelet p (each platelet's nodes
+// are one run of X, as the membrane mesh requires).
+__global__ void k_plt_nodes(int n, const int* __restrict__ node_plt, int2* __restrict__ plt_nodes)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int p = node_plt[v];
+    if (v == 0 || node_plt[v - 1] != p) {
+        int e = v + 1;
+        while (e < n && node_plt[e] == p) ++e;
+        plt_nodes[p] = make_int2(v, e - v);
+    }
+}
+
+// block_plt[b]: the platelet of all sites 256 b ... 256 b + 255 (the
+// proposal's block b), or -1 if they are not all of one.
+__global__ void k_block_platelets(int R, const int* __restrict__ site_plt, int* __restrict__ block_plt, int nb)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int s0 = 256 * b, s1 = min(R, s0 + 256);
+    int p = site_plt[s0];
+    for (int s = s0 + 1; s < s1 && p >= 0; ++s)
+        if (site_plt[s] != p) p = -1;
+    block_plt[b] = p;
 }
 
 __device__ __forceinline__ void bond_resolve(const BondCtx& c, unsigned long long* __restrict__ step_dev, int bx)
@@ -241,7 +348,7 @@ __global__ void k_bond_rupture_multi(const __grid_constant__ Multi<BondArgs> t)
     pdl_wait();
     const int e = multi_entry(t, blockIdx.x);
     const BondArgs& a = t.a[e];
-    bond_rupture(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e]);
+    bond_rupture(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e], nullptr, nullptr);
 }
 
 template <int kR>
@@ -250,7 +357,7 @@ __global__ void k_bond_propose_multi(const __grid_constant__ Multi<BondArgs> t)
     pdl_wait();
     const int e = multi_entry(t, blockIdx.x);
     const BondArgs& a = t.a[e];
-    bond_propose<kR>(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e]);
+    bond_propose<kR>(a.c, a.X, a.M, 0, a.step_dev, blockIdx.x - t.first[e], nullptr, nullptr, nullptr);
 }
 
 __global__ void k_bond_resolve_multi(const __grid_constant__ Multi<BondArgs> t)
@@ -305,19 +412,46 @@ int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream
                       "bonds_forces");
 }
 
+int launch_site_platelets(const BondCtx* c, const int* node_plt, int n, int nplt, int* site_plt, int* block_plt,
+                          int2* plt_nodes, cudaStream_t s)
+{
+    if (c->R == 0) return PFSI_OK;
+    int rc = check_cuda(cudaMemsetAsync(plt_nodes, 0, sizeof(int2) * (size_t)nplt, s), "site platelets");
+    if (rc) return rc;
+    k_plt_nodes<<<blocks_for(n, 256), 256, 0, s>>>(n, node_plt, plt_nodes);
+    k_site_platelets<<<blocks_for(c->R, 256), 256, 0, s>>>(*c, node_plt, site_plt);
+    const int nb = blocks_for(c->R, 256);
+    k_block_platelets<<<blocks_for(nb, 128), 128, 0, s>>>(c->R, site_plt, block_plt, nb);
+    return check_cuda(cudaGetLastError(), "site platelets");
+}
+
 int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
-                      unsigned long long* step_dev, cudaStream_t s)
+                      unsigned long long* step_dev, cudaStream_t s, const FarSites* far)
 {
     if (c->R > 0) {
-        int rc = check_cuda(launch_pdl(k_bond_rupture, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, M, step_host,
-                                       step_dev),
-                            "bonds_step: rupture");
+        const int* site_plt = nullptr;
+        const int* plt_far = nullptr;
+        const int* block_plt = nullptr;
+        int rc = PFSI_OK;
+        if (far && far->nplt > 0) {
+            rc = check_cuda(launch_pdl(k_plt_far, dim3(far->nplt), dim3(kFarThreads), 0, s, *far, X, M, c->p.z_wall,
+                                       c->p.d_capture),
+                            "bonds_step: platelets out of reach");
+            if (rc) return rc;
+            site_plt = far->site_plt;
+            plt_far = far->plt_far;
+            block_plt = far->block_plt;
+        }
+        rc = check_cuda(launch_pdl(k_bond_rupture, dim3(blocks_for(c->R, 256)), dim3(256), 0, s, *c, X, M, step_host,
+                                   step_dev, site_plt, plt_far),
+                        "bonds_step: rupture");
         if (rc) return rc;
         rc = check_cuda(launch_pdl(c->window == 1 ? k_bond_propose<1> : k_bond_propose<0>, dim3(blocks_for(c->R, 256)),
-                                   dim3(256), 0, s, *c, X, M, step_host, step_dev),
+                                   dim3(256), 0, s, *c, X, M, step_host, step_dev, site_plt, plt_far, block_plt),
                         "bonds_step: propose");
         if (rc) return rc;
     }
+
     return check_cuda(launch_pdl(k_bond_resolve, dim3(blocks_for(c->L > 0 ? c->L : 1, 256)), dim3(256), 0, s, *c, step_dev),
                       "bonds_step: resolve");
 }

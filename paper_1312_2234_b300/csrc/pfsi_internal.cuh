@@ -447,10 +447,30 @@ int launch_membrane_forces(MemCtx* c, const double* X, float* F, cudaStream_t s,
 // c->xh, c->xl.
 int launch_membrane_remainder(MemCtx* c, const double* X, float* F, cudaStream_t s, bool presplit = false);
 int launch_bonds_forces(BondCtx* c, const double* X, float* F, int M, cudaStream_t s);
+// Platelets out of the ligands' reach.  Every ligand lies on the wall plane,
+// so a site whose platelet has all its nodes more than d_capture above the
+// plane has no ligand in reach: the proposal pass skips such sites before it
+// gathers their positions (the decision is the one the per-site height test
+// takes, see k_plt_far).
+struct FarSites {
+    const int* site_plt = nullptr;   // [R] platelet of each site, -1: never skipped
+    int* plt_far = nullptr;          // [nplt] workspace: 1 if the platelet is out of reach this step
+    const int* block_plt = nullptr;  // [ceil(R / 256)] platelet of all sites of a proposal block, or -1
+    const int2* plt_nodes = nullptr; // [nplt] (first node, nodes) of each platelet
+    int nplt = 0;
+};
+// site_plt[s] = the platelet of site s's triangle, or -1 where the three
+// corners are not of one platelet or the weights (w0, w1, 1 - w0 - w1) are
+// not all nonnegative (the height bound of k_plt_far needs both);
+// block_plt[b] = the platelet of all sites 256 b ... 256 b + 255, or -1;
+// plt_nodes[p] = (first node, nodes) of platelet p, from node_plt [n].
+int launch_site_platelets(const BondCtx* c, const int* node_plt, int n, int nplt, int* site_plt, int* block_plt,
+                          int2* plt_nodes, cudaStream_t s);
 // step_dev: device step counter (advanced by one after the update) or null
-// to use step_host.
+// to use step_host.  far (or null): skip the proposals of platelets out of
+// reach, evaluated on X at the start of the update.
 int launch_bonds_step(BondCtx* c, const double* X, int M, uint64_t step_host,
-                      unsigned long long* step_dev, cudaStream_t s);
+                      unsigned long long* step_dev, cudaStream_t s, const FarSites* far = nullptr);
 
 struct SgCtx;
 // Adds the surrogate's local membrane forces and the exact global area and

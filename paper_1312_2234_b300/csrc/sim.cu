@@ -39,6 +39,12 @@ struct SimCtx {
     float fem_k0;
     BridgeCtx* br;         // platelet-platelet bridges, or null
     const TetherCtx* tether;  // pause-time tracking, or null
+    // platelets out of the ligands' reach (FarSites): per-site platelet and
+    // per-platelet flag, or null without bonds
+    int* site_plt;
+    int* plt_far;
+    int* block_plt;
+    int2* plt_nodes;
     // sim_step_record / sim_step_track: copy stream and per-slot events
     // (created on first use)
     cudaStream_t rec;
@@ -125,7 +131,17 @@ int enqueue_middle(SimCtx* c, cudaStream_t s, bool split_next = false, bool trac
 int enqueue_adhesion(SimCtx* c, cudaStream_t s)
 {
     int rc = PFSI_OK;
-    if (c->bonds) rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s);
+    if (c->bonds) {
+        FarSites far;
+        if (c->site_plt) {
+            far.site_plt = c->site_plt;
+            far.plt_far = c->plt_far;
+            far.block_plt = c->block_plt;
+            far.plt_nodes = c->plt_nodes;
+            far.nplt = c->mem->nplt;
+        }
+        rc = launch_bonds_step(c->bonds, c->X, c->M, 0, c->bonds->counters + 3, s, c->site_plt ? &far : nullptr);
+    }
     if (!rc && c->br) rc = launch_bridges_step(c->br, c->X, c->M, 0, bridge_step_counter(c->br), s);
     // tethers after the wall update; the bond step counter now counts this step
     if (!rc && c->tether) rc = launch_tether_update(c->tether, c->bonds->counters + 3, 0, s);
@@ -274,6 +290,8 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
     c->br = nullptr;
     c->tether = nullptr;
     c->lb_ev[0] = c->lb_ev[1] = nullptr;
+    c->site_plt = c->plt_far = c->block_plt = nullptr;
+    c->plt_nodes = nullptr;
     int rc = check_cuda(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "sim_create: stream");
     if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "sim_create: event");
@@ -282,7 +300,23 @@ extern "C" int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, 
         const unsigned long long s = first_step;
         rc = check_cuda(cudaMemcpy(bonds->counters + 3, &s, sizeof(s), cudaMemcpyHostToDevice), "sim_create: step");
     }
+    if (!rc && bonds && bonds->R > 0 && mem->nplt > 0) {
+        rc = check_cuda(cudaMalloc(&c->site_plt, sizeof(int) * (size_t)bonds->R), "sim_create: site platelets");
+        if (!rc) rc = check_cuda(cudaMalloc(&c->plt_far, sizeof(int) * (size_t)mem->nplt), "sim_create: site platelets");
+        if (!rc)
+            rc = check_cuda(cudaMalloc(&c->block_plt, sizeof(int) * (size_t)((bonds->R + 255) / 256)),
+                            "sim_create: site platelets");
+        if (!rc) rc = check_cuda(cudaMalloc(&c->plt_nodes, sizeof(int2) * (size_t)mem->nplt), "sim_create: site platelets");
+        if (!rc)
+            rc = launch_site_platelets(bonds, mem->node_plt, mem->n, mem->nplt, c->site_plt, c->block_plt, c->plt_nodes,
+                                       c->cap);
+        if (!rc) rc = check_cuda(cudaStreamSynchronize(c->cap), "sim_create: site platelets");
+    }
     if (rc) {
+        if (c->site_plt) cudaFree(c->site_plt);
+        if (c->plt_far) cudaFree(c->plt_far);
+        if (c->block_plt) cudaFree(c->block_plt);
+        if (c->plt_nodes) cudaFree(c->plt_nodes);
         delete c;
         return rc;
     }
@@ -303,6 +337,10 @@ extern "C" int sim_destroy(sim_ctx* c)
     for (cudaEvent_t e : c->rec_ready) cudaEventDestroy(e);
     for (cudaEvent_t e : c->rec_freed) cudaEventDestroy(e);
     if (c->rec) cudaStreamDestroy(c->rec);
+    if (c->site_plt) cudaFree(c->site_plt);
+    if (c->plt_far) cudaFree(c->plt_far);
+    if (c->block_plt) cudaFree(c->block_plt);
+    if (c->plt_nodes) cudaFree(c->plt_nodes);
     delete c;
     return PFSI_OK;
 }

@@ -110,6 +110,25 @@ def test_bonds_in_coupled_run():
     assert np.array_equal(sim.bonds.lig_count.cpu().numpy(), ora.lig_count)
 
 
+def test_bonds_with_platelets_out_of_reach():
+    """The 128x64x64 channel's platelets (seed 1: one platelet's lowest node
+    0.51 above the wall plane, the other nine 1.3 to 9.9, all beyond
+    d_capture = 0.64) over ligands on the whole bottom wall, with accelerated
+    kinetics: the coupled step skips the proposals of the platelets whose
+    every node lies beyond d_capture, and the bond state over the window is
+    still the oracle's, event for event (12 bonds)."""
+    w = workload.build(128, 64, 64, 0.8, 1000.0, 10, 4, 800, 5000, 1, patch=(0, 0, 128, 64))
+    w["bonds"].update(kon0_dt=0.2, koff0_dt=0.01, sigma=0.05, kT=0.02, gamma=0.05)
+    X = np.asarray(w["X"]).reshape(3, -1)
+    plt = np.asarray(w["mesh"]["node_plt"])
+    lift = np.array([X[2, plt == p].min() for p in range(w["mesh"]["n_plt"])]) - w["bonds"]["z_wall"]
+    assert (lift < w["bonds"]["d_capture"]).sum() == 1 and (lift > w["bonds"]["d_capture"] + 0.5).sum() == 9
+    sim, ora = compare(w, 12)
+    assert (ora.bound >= 0).sum() > 5
+    assert np.array_equal(sim.bonds.bound.cpu().numpy(), ora.bound)
+    assert np.array_equal(sim.bonds.lig_count.cpu().numpy(), ora.lig_count)
+
+
 def test_graph_replay_matches_single_calls():
     """sim_step (graph replay) against the same C-ABI calls made one by one."""
     w = f32_workload(workload.tiny(seed=5, shear=1.0e4, n_sites=200, gap=0.05))
