@@ -47,7 +47,20 @@ CHANNEL = ("channel 128x64x64 D3Q19 Couette, shear 1000/s, tau 0.8; 10 platelets
 FAST_KINETICS = dict(kon0_dt=0.05, koff0_dt=0.005, sigma=0.02, kT=0.05, gamma=0.05)
 LB_BYTES_PER_CELL = 152          # 19 float loads + 19 float stores
 LB_BYTES_PER_CELL_MIXED = 108    # 19 16-bit f^neq + one float4 (v, rho - 1), each read and written
-KERNELS_PER_STEP = 11            # split, elements, coef, nodes, bond forces, spread, lb, interp, rupture, propose, resolve
+# per step: membrane elements, coef, nodes, bond forces, spread, lb, interp,
+# out-of-reach platelets, rupture, propose, resolve; plus the hi/lo split of X
+# once per graph launch (the interpolation prepares it for the other steps)
+KERNELS_PER_STEP = 11
+
+
+def graph_launches(n):
+    """Graph launches of sim_step(n): eight-step graphs while eight steps
+    remain, then four-step ones, then single steps."""
+    g = 0
+    while n >= 4:
+        n -= 8 if n >= 8 else 4
+        g += 1
+    return g + n
 
 
 def log(*a):
@@ -364,7 +377,7 @@ def run_native(args, rank, ws):
         "configurations": extras,
         "cpu_baseline": base,
         "e2e": e2e,
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps + graph_launches(args.steps),
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
