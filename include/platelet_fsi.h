@@ -620,7 +620,13 @@ typedef struct sim_ctx sim_ctx;
 
 /* Ties a lattice, a membrane mesh and a bond set to the node arrays
  * X (double[3][M]), F, U (float[3][M]).  bonds may be NULL (no adhesion).
- * first_step is the step index of the first sim_step (Philox counter). */
+ * first_step is the step index of the first sim_step (Philox counter).
+ * With bonds, allocates and fills (synchronously) the platelet of each
+ * receptor site and of each block of 256 sites, and a per-platelet flag that
+ * each step's adhesion update sets for the platelets whose every node lies
+ * beyond the capture distance above the wall: their sites make no proposal
+ * (the per-site test would reject each of them, so the bond events are
+ * unchanged; Section 3.2). */
 int sim_create(lb_ctx* lb, mem_ctx* mem, bond_ctx* bonds, double* X, float* F, float* U, int M,
                uint64_t first_step, sim_ctx** out);
 int sim_destroy(sim_ctx* ctx);
