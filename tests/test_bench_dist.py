@@ -47,3 +47,13 @@ def test_single_rank_is_identity():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.reduce_max(3.25, 1) == 3.25
+
+
+def test_graph_launch_count():
+    """sim_step(n) runs eight-step graphs while eight steps remain, then
+    four-step ones, then single steps; the bench counts one hi/lo split per
+    graph launch on top of the per-step kernels."""
+    sys.path.insert(0, ROOT)
+    import bench
+    expect = {1: 1, 3: 3, 4: 1, 7: 4, 8: 1, 12: 2, 16: 2, 20: 3, 23: 6}
+    assert {n: bench.graph_launches(n) for n in expect} == expect
