@@ -402,9 +402,9 @@ __device__ __forceinline__ void ib_interp_block(double* __restrict__ X, float* _
         U[M + m] = uy;
         U[2 * M + m] = uz;
         if (advect) {
-            xn[0] = x + (double)ux;
-            xn[1] = y + (double)uy;
-            xn[2] = z + (double)uz;
+            xn[0] = x + widen(ux);
+            xn[1] = y + widen(uy);
+            xn[2] = z + widen(uz);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 X[d * M + m] = xn[d];

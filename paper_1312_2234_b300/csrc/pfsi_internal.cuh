@@ -381,7 +381,29 @@ int launch_tether_update(const TetherCtx* c, const unsigned long long* now_dev, 
 // of its support then cannot overflow.  sim_check counts the coordinates
 // outside that range (a run that blew up).
 constexpr double kFarCoord = 1e8;
-__device__ __forceinline__ bool coord_in_range(double x) { return fabs(x) < kFarCoord; }
+// The test on the bits (|x| as an unsigned integer orders like |x|, and NaN
+// lies above every finite value): on the integer pipes, where fabs(x) <
+// kFarCoord takes the FP64 pipe, which runs at a small fraction of the FP32
+// rate on this part.
+constexpr unsigned long long kFarCoordBits = 0x4197d78400000000ull;   // the bits of 1e8
+__device__ __forceinline__ bool coord_in_range(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) < kFarCoordBits;
+}
+// (double)u exactly, on the integer pipes for normal u and zero (every other
+// value, denormal, infinite or NaN, takes the conversion instruction).
+__device__ __forceinline__ double widen(float u)
+{
+    const unsigned int b = __float_as_uint(u);
+    const unsigned int e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) {
+        if ((b & 0x7fffffffu) == 0u) return __longlong_as_double((long long)(b & 0x80000000u) << 32);
+        return (double)u;
+    }
+    const unsigned long long r = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)r);
+}
 
 // Nodes per block of the IB kernels (also the largest chunk of the membrane's
 // chunk table).
